@@ -1,0 +1,146 @@
+/*
+ * e2.h -- C ABI of the B300 (sm_103a) library for the Epstein-Nesbet
+ * second-order energy of a multiconfigurational four-component reference.
+ *
+ * What it computes (Sec. 2.3, Eq. pt2; Sec. 2.4, Eq. pt2en):
+ *
+ *   E2_m = sum_{K in Q} |<K|H|Psi_m>|^2 / (E0_m - H_KK)
+ *
+ * with the Epstein-Nesbet zeroth-order Hamiltonian H0 = PHP + diag(QHQ)
+ * (Eq. zeroh), Psi_m = sum_L c_{m,L} |L> over the reference space P
+ * (Sec. 2.3), E0_m = <Psi_m|H|Psi_m>/<Psi_m|Psi_m>, and Q = every determinant
+ * outside P that is a single or double substitution of a P determinant
+ * (Sec. 2.3), restricted by frozen core / frozen virtual spinors (Sec. 2.5).
+ * With b > 0 the denominator takes the imaginary level shift of Sec. 2.6 and
+ * the library returns the real part: |V|^2 D^3 / (D^4 + b^2), D = E0 - H_KK.
+ *
+ * Hamiltonian (second quantisation over Kramers-unrestricted spinors):
+ *   H = sum_pq h_pq a+_p a_q + 1/4 sum_pqrs <pq||rs> a+_p a+_q a_s a_r,
+ *   <pq||rs> = (pr|qs) - (ps|qr),
+ *   (pq|rs)  = sum_{L in Coulomb set} B^L_pq B^L_rs
+ *            + lambda * sum_{L in extra set} w_L B^L_pq B^L_rs,
+ * where the extra set is the Gaunt (DCG) or Breit (DCB) factor set
+ * (Sec. 2.1, Eqs. dcb, Coulomb, breit); DC has no extra set.
+ *
+ * Spinor order: [core | active | virtual]; frozen core spinors are always
+ * occupied, frozen virtual spinors always empty.  A determinant is the
+ * product of creators in ascending spinor order acting on the vacuum.
+ *
+ * Active space: n_das subspaces of consecutive active spinors (a CAS is one
+ * subspace); P holds the active strings of n_elec electrons whose per-subspace
+ * counts n_s satisfy das_min[s] <= n_s <= das_max[s] (Sec. 2.4, Eq. DASK).
+ *
+ * Reference coefficient order (the "address" of a P determinant): allowed
+ * occupation patterns (n_1..n_k) in lexicographic order, n_1 most
+ * significant, one block per pattern; inside a block
+ *   sum_s rank_s * stride_s,  stride_1 = 1, stride_{s+1} = stride_s * C(size_s, n_s),
+ * rank_s = colex rank of the subspace-s substring: sum_j C(t_j, j) over its
+ * occupied local indices t_1 < t_2 < ... (j from 1).  For a CAS this is the
+ * colex rank of the active string.
+ *
+ * External classes: class id = 3*h + p, h = correlated core holes (0..2),
+ * p = correlated virtual particles (0..2).  Class 0 (pure active
+ * rearrangement into a non-reference pattern) exists only with n_das > 1.
+ *
+ * Memory and ownership: every array argument is caller-owned.  Device
+ * pointers must stay valid until the stream reaches the end of the call's
+ * work.  The library keeps only host-side plans inside an e2_problem.  It
+ * allocates no device memory: it works in the caller's workspace, of at least
+ * e2_workspace_size() bytes, 256-byte aligned.
+ *
+ * Complex numbers are interleaved (re, im) doubles.  Everything is FP64.
+ *
+ * Errors: argument errors return immediately with a status and enqueue no
+ * work.  No C++ exception crosses this interface.  Calls on one e2_problem
+ * must not overlap (a problem is not thread-safe).
+ */
+#ifndef E2_H
+#define E2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { E2_DC = 0, E2_DCG = 1, E2_DCB = 2 } e2_hamiltonian;
+
+typedef enum {
+  E2_OK = 0,
+  E2_ERR_INVALID_ARG = 1,
+  E2_ERR_SHAPE = 2,
+  E2_ERR_UNSUPPORTED = 3,
+  E2_ERR_WORKSPACE = 4,
+  E2_ERR_CUDA = 5,
+  E2_ERR_NONFINITE = 6
+} e2_status;
+
+#define E2_NCLASS 9
+#define E2_MAX_DAS 8
+
+/* Problem description (host memory; copied by e2_problem_create). */
+typedef struct {
+  int32_t n_core;          /* core spinors, frozen ones included (even) */
+  int32_t n_active;        /* active spinors, 1..62 */
+  int32_t n_virt;          /* virtual spinors, frozen ones included */
+  int32_t n_elec;          /* active electrons in P */
+  const uint8_t* frozen;   /* [n_core+n_active+n_virt], 1 = frozen; only core or virtual spinors may be frozen */
+  int32_t n_das;           /* 1..E2_MAX_DAS active subspaces */
+  const int32_t* das_size; /* [n_das], sums to n_active */
+  const int32_t* das_min;  /* [n_das] minimum electrons per subspace in P */
+  const int32_t* das_max;  /* [n_das] maximum electrons per subspace in P */
+  int32_t ham;             /* e2_hamiltonian */
+  int32_t L_coulomb;       /* Coulomb factor count (>= 1) */
+  int32_t L_extra;         /* Gaunt / Breit factor count (0 for DC) */
+  int32_t n_roots;         /* reference states, 1..16 */
+  double level_shift_b;    /* b >= 0 of the imaginary level shift; 0 = plain Eq. pt2 */
+  uint32_t class_mask;     /* bit c: evaluate class c (3h+p); 0x1FF = all */
+} e2_desc;
+
+/* Device inputs of one evaluation.  All device pointers, complex interleaved:
+ *   h   [n][n]           Hermitian one-electron matrix
+ *   B_c [L_coulomb][n][n] Hermitian Coulomb factors
+ *   B_x [L_extra][n][n]   Hermitian Gaunt/Breit factors (NULL if L_extra == 0)
+ *   w_x [L_extra]         real weights of the extra factors (NULL if L_extra == 0)
+ *   c   [n_roots][N_P]    reference coefficients in address order (need not be normalised)
+ */
+typedef struct {
+  const double* h;
+  const double* B_c;
+  const double* B_x;
+  const double* w_x;
+  double lambda;           /* multiplier of the extra set (1 = full Gaunt/Breit) */
+  const double* c;
+} e2_inputs;
+
+typedef struct e2_problem e2_problem;
+
+/* Validates the description and builds the host plan (occupation patterns,
+ * string-list sizes, workspace layout).  No device work.  *out is NULL on error. */
+e2_status e2_problem_create(const e2_desc* desc, e2_problem** out);
+e2_status e2_problem_destroy(e2_problem* prob);
+
+/* N_P, and the number of external determinants per class (|Q| split by
+ * class id, per root), both as computed by the plan. */
+e2_status e2_problem_info(const e2_problem* prob, int64_t* n_p, double* q_per_class /* [E2_NCLASS] or NULL */);
+
+/* Device workspace needed by e2_forward. */
+e2_status e2_workspace_size(const e2_problem* prob, size_t* bytes);
+
+/* E2 for every root.  Enqueues kernels on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream) and returns without synchronising.
+ *   E2       device [n_roots]            total second-order energy per root
+ *   E2_class device [n_roots][E2_NCLASS]  per-class contributions, or NULL
+ *   E0       device [n_roots]            reference energies, or NULL
+ * The summation order is fixed, so repeated calls give bitwise equal results. */
+e2_status e2_forward(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                     void* stream, double* E2, double* E2_class, double* E0);
+
+const char* e2_status_string(e2_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* E2_H */

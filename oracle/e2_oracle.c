@@ -569,8 +569,20 @@ static double en_term(double v2, double D, double b) {
   return v2 * D * D2 / (D2 * D2 + b * b);
 }
 
-/* E2 per root and class (class id 3*h + p).  n_coupl[cls] counts the external
-   determinants with at least one connected P determinant. */
+/* <c_m|c_m>: Sec. 2.3 takes the reference states normalised, so E2 of an
+   unnormalised c is E2 of c/|c| (each term divided by <c|c>). */
+static double c_norm(const oracle_t* P, int m) {
+  int64_t np = oracle_np((void*)P);
+  ksum_t s = {0, 0};
+  for (int64_t a = 0; a < np; ++a) {
+    cplx v = P->c[m * np + a];
+    kadd(&s, (long double)(creal(v) * creal(v) + cimag(v) * cimag(v)));
+  }
+  return (double)kval(&s);
+}
+
+/* E2 per root and class (class id 3*h + p), for Psi = c/|c|.  n_coupl[cls]
+   counts the external determinants with at least one connected P determinant. */
 int oracle_e2(void* vp, const double* E0, double* e2_class, int64_t* n_coupl) {
   oracle_t* P = (oracle_t*)vp;
   int R = P->n_roots;
@@ -583,6 +595,8 @@ int oracle_e2(void* vp, const double* E0, double* e2_class, int64_t* n_coupl) {
       int64_t nI = binom(P->ncc, h), nS = binom(P->nvc, p), nitem = nI * nS;
       if (nitem == 0) continue;
       ksum_t* part = (ksum_t*)calloc((size_t)nitem * R, sizeof(ksum_t));
+      double norm[64];
+      for (int m = 0; m < R; ++m) norm[m] = c_norm(P, m);
       int64_t* cnt = (int64_t*)calloc((size_t)nitem, sizeof(int64_t));
 #pragma omp parallel for schedule(dynamic, 1)
       for (int64_t item = 0; item < nitem; ++item) {
@@ -601,7 +615,7 @@ int oracle_e2(void* vp, const double* E0, double* e2_class, int64_t* n_coupl) {
           double hkk = hdiag(P, &K);
           for (int m = 0; m < R; ++m) {
             double v2 = creal(V[m]) * creal(V[m]) + cimag(V[m]) * cimag(V[m]);
-            kadd(&part[item * R + m], en_term(v2, E0[m] - hkk, P->b));
+            kadd(&part[item * R + m], en_term(v2, E0[m] - hkk, P->b) / norm[m]);
           }
         }
       }

@@ -282,3 +282,13 @@ def test_reference_energy_is_lowest_eigenvalue():
     H = o.hpp()
     for m in range(2):
         assert np.linalg.norm(H @ c[m] - w[m] * c[m]) < 1e-10
+
+
+def test_e2_is_invariant_to_the_scale_of_c():
+    """Sec. 2.3 normalises the reference states; an unnormalised c gives the
+    E2 of c/|c|."""
+    p = tiny_problem(2, 6, 6, 3, Lc=4, seed=18)
+    o, c, _ = _ground(p, 1)
+    e_ref = o.e2()[1]
+    o.set_c(3.7 * c)
+    np.testing.assert_allclose(o.e2()[1], e_ref, rtol=1e-14, atol=0)
