@@ -291,4 +291,4 @@ def test_e2_is_invariant_to_the_scale_of_c():
     o, c, _ = _ground(p, 1)
     e_ref = o.e2()[1]
     o.set_c(3.7 * c)
-    np.testing.assert_allclose(o.e2()[1], e_ref, rtol=1e-14, atol=0)
+    np.testing.assert_allclose(o.e2()[1], e_ref, rtol=1e-12, atol=1e-18)
