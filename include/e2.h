@@ -60,6 +60,12 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#if defined(__GNUC__)
+#define E2_API __attribute__((visibility("default")))
+#else
+#define E2_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -118,15 +124,15 @@ typedef struct e2_problem e2_problem;
 
 /* Validates the description and builds the host plan (occupation patterns,
  * string-list sizes, workspace layout).  No device work.  *out is NULL on error. */
-e2_status e2_problem_create(const e2_desc* desc, e2_problem** out);
-e2_status e2_problem_destroy(e2_problem* prob);
+E2_API e2_status e2_problem_create(const e2_desc* desc, e2_problem** out);
+E2_API e2_status e2_problem_destroy(e2_problem* prob);
 
 /* N_P, and the number of external determinants per class (|Q| split by
  * class id, per root), both as computed by the plan. */
-e2_status e2_problem_info(const e2_problem* prob, int64_t* n_p, double* q_per_class /* [E2_NCLASS] or NULL */);
+E2_API e2_status e2_problem_info(const e2_problem* prob, int64_t* n_p, double* q_per_class /* [E2_NCLASS] or NULL */);
 
 /* Device workspace needed by e2_forward. */
-e2_status e2_workspace_size(const e2_problem* prob, size_t* bytes);
+E2_API e2_status e2_workspace_size(const e2_problem* prob, size_t* bytes);
 
 /* E2 for every root.  Enqueues kernels on `stream` (a cudaStream_t; NULL = the
  * legacy default stream) and returns without synchronising.
@@ -134,10 +140,10 @@ e2_status e2_workspace_size(const e2_problem* prob, size_t* bytes);
  *   E2_class device [n_roots][E2_NCLASS]  per-class contributions, or NULL
  *   E0       device [n_roots]            reference energies, or NULL
  * The summation order is fixed, so repeated calls give bitwise equal results. */
-e2_status e2_forward(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+E2_API e2_status e2_forward(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
                      void* stream, double* E2, double* E2_class, double* E0);
 
-const char* e2_status_string(e2_status s);
+E2_API const char* e2_status_string(e2_status s);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,164 @@
+"""ctypes binding of libe2.so (argument marshalling only).
+
+Every computation runs in the library's sm_103a kernels; this module builds
+the descriptor, allocates caller-owned device memory with PyTorch and passes
+raw pointers.  It raises if the library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libe2.so")
+NCLASS = 9
+HAM = {"DC": 0, "DCG": 1, "DCB": 2}
+CLASS_NAMES = ["(0,0)", "(0,1)", "(0,2)", "(1,0)", "(1,1)", "(1,2)", "(2,0)", "(2,1)", "(2,2)"]
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n_core", C.c_int32), ("n_active", C.c_int32), ("n_virt", C.c_int32), ("n_elec", C.c_int32),
+                ("frozen", C.POINTER(C.c_uint8)), ("n_das", C.c_int32), ("das_size", C.POINTER(C.c_int32)),
+                ("das_min", C.POINTER(C.c_int32)), ("das_max", C.POINTER(C.c_int32)), ("ham", C.c_int32),
+                ("L_coulomb", C.c_int32), ("L_extra", C.c_int32), ("n_roots", C.c_int32),
+                ("level_shift_b", C.c_double), ("class_mask", C.c_uint32)]
+
+
+class _Inputs(C.Structure):
+    _fields_ = [("h", C.c_void_p), ("B_c", C.c_void_p), ("B_x", C.c_void_p), ("w_x", C.c_void_p),
+                ("lam", C.c_double), ("c", C.c_void_p)]
+
+
+_lib = None
+
+
+def load():
+    """Load libe2.so (raises OSError when it is missing)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise OSError(f"libe2.so not built: run `python -m paper_2608_11529_b300.build` ({LIB_PATH})")
+        L = C.CDLL(LIB_PATH)
+        L.e2_problem_create.argtypes = [C.POINTER(_Desc), C.POINTER(C.c_void_p)]
+        L.e2_problem_create.restype = C.c_int
+        L.e2_problem_destroy.argtypes = [C.c_void_p]
+        L.e2_problem_destroy.restype = C.c_int
+        L.e2_problem_info.argtypes = [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]
+        L.e2_problem_info.restype = C.c_int
+        L.e2_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
+        L.e2_workspace_size.restype = C.c_int
+        L.e2_forward.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]
+        L.e2_forward.restype = C.c_int
+        L.e2_status_string.argtypes = [C.c_int]
+        L.e2_status_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+class E2Error(RuntimeError):
+    pass
+
+
+def _check(st):
+    if st != 0:
+        raise E2Error(load().e2_status_string(st).decode())
+
+
+class E2Problem:
+    """A planned E2 evaluation (host plan of ``e2_problem_create``)."""
+
+    def __init__(self, n_core, n_active, n_virt, n_elec, *, frozen=None, das_size=None, das_min=None, das_max=None,
+                 ham="DC", L_coulomb=1, L_extra=0, n_roots=1, level_shift_b=0.0, class_mask=0x1FF):
+        L = load()
+        n = n_core + n_active + n_virt
+        if das_size is None:
+            das_size, das_min, das_max = [n_active], [n_elec], [n_elec]
+        self._frozen = np.ascontiguousarray(np.zeros(n, np.uint8) if frozen is None else frozen, np.uint8)
+        self._ds = np.ascontiguousarray(das_size, np.int32)
+        self._dmin = np.ascontiguousarray(das_min, np.int32)
+        self._dmax = np.ascontiguousarray(das_max, np.int32)
+        d = _Desc(n_core, n_active, n_virt, n_elec, self._frozen.ctypes.data_as(C.POINTER(C.c_uint8)), len(das_size),
+                  self._ds.ctypes.data_as(C.POINTER(C.c_int32)), self._dmin.ctypes.data_as(C.POINTER(C.c_int32)),
+                  self._dmax.ctypes.data_as(C.POINTER(C.c_int32)), HAM[ham] if isinstance(ham, str) else int(ham),
+                  L_coulomb, L_extra, n_roots, float(level_shift_b), int(class_mask))
+        h = C.c_void_p()
+        _check(L.e2_problem_create(C.byref(d), C.byref(h)))
+        self._h = h
+        self.n = n
+        self.n_roots = n_roots
+        self.L_extra = L_extra
+        n_p = C.c_int64()
+        q = np.zeros(NCLASS)
+        _check(L.e2_problem_info(self._h, C.byref(n_p), q.ctypes.data_as(C.c_void_p)))
+        self.n_p = int(n_p.value)
+        self.q_per_class = q
+        ws = C.c_size_t()
+        _check(L.e2_workspace_size(self._h, C.byref(ws)))
+        self.workspace_bytes = int(ws.value)
+        self._ws = None
+
+    @classmethod
+    def from_problem(cls, prob, class_mask=0x1FF, n_roots=None, level_shift_b=None):
+        """Plan for an ``e2_inputs.Problem``."""
+        Lx = prob.Bx.shape[0] if prob.ham != "DC" else 0
+        return cls(prob.n_core, prob.n_act, prob.n_virt, prob.n_elec, frozen=prob.frozen, das_size=prob.das_size,
+                   das_min=prob.das_min, das_max=prob.das_max, ham=prob.ham, L_coulomb=prob.Bc.shape[0], L_extra=Lx,
+                   n_roots=n_roots or prob.n_roots,
+                   level_shift_b=prob.level_shift_b if level_shift_b is None else level_shift_b,
+                   class_mask=class_mask)
+
+    def __del__(self):
+        try:
+            if self._h:
+                load().e2_problem_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def workspace(self, device):
+        """A 256-byte aligned uint8 CUDA tensor of the required size (cached)."""
+        import torch
+        if self._ws is None or self._ws.device != device:
+            raw = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=device)
+            off = (-raw.data_ptr()) % 256
+            self._ws_raw = raw
+            self._ws = raw[off:off + self.workspace_bytes]
+        return self._ws
+
+    def forward(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, stream=None, workspace=None, out=None):
+        """E2 per root.  Tensors: complex128 CUDA, contiguous.  Returns
+        (E2 [roots], E2_class [roots, 9], E0 [roots]) as float64 CUDA tensors."""
+        import torch
+        dev = c.device
+        for t in (h, B_c, c) + ((B_x,) if self.L_extra else ()):
+            if t.dtype != torch.complex128 or not t.is_contiguous() or t.device != dev:
+                raise E2Error("inputs must be contiguous complex128 tensors on one CUDA device")
+        if c.numel() != self.n_roots * self.n_p:
+            raise E2Error(f"c must hold n_roots*N_P = {self.n_roots * self.n_p} coefficients")
+        ws = self.workspace(dev) if workspace is None else workspace
+        if out is None:
+            out = (torch.empty(self.n_roots, dtype=torch.float64, device=dev),
+                   torch.empty(self.n_roots, NCLASS, dtype=torch.float64, device=dev),
+                   torch.empty(self.n_roots, dtype=torch.float64, device=dev))
+        E2, E2c, E0 = out
+        inp = _Inputs(h.data_ptr(), B_c.data_ptr(), B_x.data_ptr() if self.L_extra else None,
+                      w_x.data_ptr() if self.L_extra else None, float(lam), c.data_ptr())
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        _check(load().e2_forward(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s), E2.data_ptr(),
+                                 E2c.data_ptr(), E0.data_ptr()))
+        return E2, E2c, E0
+
+
+def device_inputs(prob, c, device="cuda"):
+    """Copy an ``e2_inputs.Problem`` and coefficients c [roots, N_P] to the device."""
+    import torch
+    t = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+    h = t(prob.h, torch.complex128)
+    Bc = t(prob.Bc, torch.complex128)
+    Bx = t(prob.Bx, torch.complex128) if prob.ham != "DC" and prob.Bx.shape[0] else None
+    wx = t(prob.wx, torch.float64) if Bx is not None else None
+    cc = t(np.atleast_2d(c), torch.complex128)
+    return dict(h=h, B_c=Bc, B_x=Bx, w_x=wx, c=cc, lam=prob.lam)

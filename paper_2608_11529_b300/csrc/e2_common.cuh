@@ -1,0 +1,73 @@
+// Internal declarations shared by the host plan and the sm_103a kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "e2.h"
+
+namespace e2 {
+
+constexpr int kMaxPat = 1024;      // occupation patterns per string list
+constexpr int kMaxKeys = 1 << 20;  // size of the pattern-key table
+constexpr int kBinomN = 65;        // binomial table is [65][65]
+
+// Active-space partition as the kernels see it.
+struct DevDas {
+  int n_das;
+  int n_act;
+  int off[E2_MAX_DAS];     // first active-local index of each subspace
+  int size[E2_MAX_DAS];
+  int keymul[E2_MAX_DAS];  // pattern key = sum_s n_s * keymul[s]
+};
+
+// One list of active strings (a union of occupation-pattern blocks).
+struct DevList {
+  int count;                // electrons per string
+  int npat;
+  int64_t n;                // strings
+  uint64_t* str;            // [n] active-local bitsets, in list order
+  const int64_t* key2off;   // [nkeys] block offset of a pattern, -1 if absent
+  const int64_t* patoff;    // [npat]
+  const int32_t* patocc;    // [npat][E2_MAX_DAS]
+  double* eA;               // [n]   sum_t eps^_t + 1/2 sum_{t!=u} G_tu over the string
+  double* U;                // [nx+1][n]  U[x][A] = sum_{t in A} G_{X(x),t}; row nx is zero
+};
+
+// Per external row of the dense classes: U-row indices of the two
+// particles (s1, s2) and two holes (i1, i2), nx when absent, and chi(e).
+struct RowInfo {
+  int32_t s1, s2, i1, i2;
+  double chi;
+};
+
+enum IntMode : int {
+  INT_W02 = 0,  // <ab||tu>          rows (a<b), cols (t<u)
+  INT_W12,      // <ab||it>          rows (i, a<b), cols t
+  INT_W21,      // <at||ij>          rows (i<j, a), cols t
+  INT_W11,      // f_ai | <at||iu>   rows (i, a), cols 0 | 1 + t*na + u
+  INT_W20,      // <tu||ij>          rows (i<j), cols (t<u)
+  INT_G22,      // |<ab||ij>|^2      rows (i<j), cols (a<b), real
+  INT_X01,      // <au||vw>          rows a, cols u*ntp + (v<w)
+  INT_X10,      // <tu||iv>          rows i, cols (t<u)*na + v
+  INT_X00       // <tu||vw>          rows (t<u), cols (v<w)
+};
+
+enum DFamily : int {
+  FAM_T = 0,  // <A| a_t |Psi>
+  FAM_TD,     // <A| a+_t |Psi>
+  FAM_TU,     // <A| a_u a_t |Psi>, t<u
+  FAM_TDUD,   // <A| a+_t a+_u |Psi>, t<u
+  FAM_TDU     // row 0: c_A (A in P); row 1+t*na+u: <A| a+_t a_u |Psi>
+};
+
+// Spinor index sets used by the kernels.
+struct DevSpace {
+  int n, n_core, n_act, n_virt, n_occ, a0, v0;
+  int ncc, nvc, nx;        // correlated core / virtual counts, nx = ncc + nvc
+  const int32_t* cc;       // [ncc] global index of correlated core spinors
+  const int32_t* vc;       // [nvc] global index of correlated virtual spinors
+};
+
+__host__ __device__ inline int64_t pairs(int64_t n) { return n * (n - 1) / 2; }
+
+}  // namespace e2

@@ -1,0 +1,869 @@
+// sm_103a kernels of the Epstein-Nesbet second-order energy (Sec. 2.3-2.6).
+//
+// Notation: i, j correlated core spinors; t, u, v, w active; a, b correlated
+// virtual; A an active string (bitset over active-local indices).
+//   <pq||rs> = (pr|qs) - (ps|qr),  (pq|rs) = sum_L wt_L B^L_pq B^L_rs
+//   G_pq = <pq||pq>,  eps^_p = h_pp + sum_{k in core} G_pk,
+//   f_pq = h_pq + sum_{k in core} <pk||qk>   (h^FC of Sec. 2 over the whole core)
+//   H_KK = E_O + e_A + chi(e) + sum_{s in S} U[s,A] - sum_{i in I} U[i,A]
+// Every class's coupling V_K = <K|H|Psi> is, up to a sign per external
+// tuple that cancels in |V_K|^2, a contraction sum_x W[e,x] D^x_A of
+// integrals with active coupling tensors D^x_A = <A|x|Psi>.
+#include <cuda_runtime.h>
+
+#include "e2_common.cuh"
+#include "e2_kernels.cuh"
+
+namespace e2 {
+
+// ------------------------------------------------------------------ helpers
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+__device__ __forceinline__ int popc_below(uint64_t A, int t) {
+  return __popcll(t ? (A & ((1ull << t) - 1)) : 0ull);
+}
+
+// 1/d: single-precision seed refined by two Newton-Raphson steps
+// (x <- x (2 - d x)); each step squares the relative error, 2^-23 -> 2^-46
+// -> below double rounding.  Valid for 1e-30 < |d| < 1e30.
+__device__ __forceinline__ double rcp_nr(double d) {
+  double r = (double)__frcp_rn(__double2float_rn(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Epstein-Nesbet term |V|^2/D, or with the imaginary level shift the real
+// part of |V|^2/(D + i b/D) = |V|^2 D^3/(D^4 + b^2) (Sec. 2.6).
+__device__ __forceinline__ double en_term(double v2, double D, double b) {
+  if (b == 0.0) return v2 * rcp_nr(D);
+  double D2 = D * D;
+  return v2 * D * D2 * rcp_nr(fma(D2, D2, b * b));
+}
+
+__device__ __forceinline__ void pair_decode(int64_t e, int& x, int& y) {
+  int64_t yy = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)e)) * 0.5);
+  while (yy > 1 && yy * (yy - 1) / 2 > e) --yy;
+  while ((yy + 1) * yy / 2 <= e) ++yy;
+  y = (int)yy;
+  x = (int)(e - yy * (yy - 1) / 2);
+}
+
+__device__ __forceinline__ int pair_index(int x, int y) { return y * (y - 1) / 2 + x; }  // x < y
+
+// Colex rank of a substring with k set bits: sum_j C(t_j, j), j = 1..k.
+__device__ __forceinline__ int64_t colex_rank(uint64_t bits, const int64_t* __restrict__ binom) {
+  int64_t r = 0;
+  int j = 0;
+  while (bits) {
+    int t = __ffsll((long long)bits) - 1;
+    bits &= bits - 1;
+    ++j;
+    r += binom[t * kBinomN + j];
+  }
+  return r;
+}
+
+__device__ __forceinline__ uint64_t colex_unrank(int64_t rank, int k, int size, const int64_t* __restrict__ binom) {
+  uint64_t out = 0;
+  int t = size - 1;
+  for (int j = k; j >= 1; --j) {
+    while (binom[t * kBinomN + j] > rank) --t;
+    out |= 1ull << t;
+    rank -= binom[t * kBinomN + j];
+    --t;
+  }
+  return out;
+}
+
+// Position of string A in list Ls, or -1 when A's pattern is not in the list.
+__device__ __forceinline__ int64_t list_addr(const DevList& Ls, const DevDas& das, const int64_t* __restrict__ binom,
+                                             uint64_t A) {
+  if (Ls.key2off == nullptr) return -1;
+  int key = 0;
+  int occ[E2_MAX_DAS];
+  for (int s = 0; s < das.n_das; ++s) {
+    uint64_t m = ((das.size[s] == 64) ? ~0ull : ((1ull << das.size[s]) - 1)) << das.off[s];
+    occ[s] = __popcll(A & m);
+    key += occ[s] * das.keymul[s];
+  }
+  int64_t off = Ls.key2off[key];
+  if (off < 0) return -1;
+  int64_t stride = 1;
+  for (int s = 0; s < das.n_das; ++s) {
+    uint64_t sub = (A >> das.off[s]) & ((das.size[s] == 64) ? ~0ull : ((1ull << das.size[s]) - 1));
+    off += colex_rank(sub, binom) * stride;
+    stride *= binom[das.size[s] * kBinomN + occ[s]];
+  }
+  return off;
+}
+
+// ------------------------------------------------------------------ setup
+
+__global__ void k_binom(int64_t* tab) {
+  for (int idx = threadIdx.x; idx < kBinomN * kBinomN; idx += blockDim.x) {
+    int n = idx / kBinomN, k = idx % kBinomN;
+    // C(n,k) by the multiplicative formula with exact integer steps
+    int64_t r = (k > n) ? 0 : 1;
+    if (k <= n) {
+      int kk = k < n - k ? k : n - k;
+      for (int j = 1; j <= kk; ++j) r = r * (n - kk + j) / j;
+    }
+    tab[idx] = r;
+  }
+}
+
+// Bo[L][p][y] = B^L_py for y < n_occ (core + active), all factor sets
+// concatenated; wt[L] = 1 (Coulomb) or lambda * w_x (Gaunt / Breit).
+__global__ void k_extract(const double2* __restrict__ Bc, const double2* __restrict__ Bx, const double* __restrict__ wx,
+                          double lambda, int Lc, int Lx, int n, int nocc, double2* __restrict__ Bo,
+                          double* __restrict__ wt, double* __restrict__ dg) {
+  int64_t total = (int64_t)(Lc + Lx) * n * nocc;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
+    int y = (int)(idx % nocc);
+    int64_t r = idx / nocc;
+    int p = (int)(r % n);
+    int L = (int)(r / n);
+    const double2* src = (L < Lc) ? Bc + (int64_t)L * n * n : Bx + (int64_t)(L - Lc) * n * n;
+    Bo[idx] = src[(int64_t)p * n + y];
+  }
+  int64_t tot2 = (int64_t)(Lc + Lx) * n;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < tot2; idx += (int64_t)gridDim.x * blockDim.x) {
+    int p = (int)(idx % n);
+    int L = (int)(idx / n);
+    const double2* src = (L < Lc) ? Bc + (int64_t)L * n * n : Bx + (int64_t)(L - Lc) * n * n;
+    dg[idx] = src[(int64_t)p * n + p].x;
+    if (p == 0) wt[L] = (L < Lc) ? 1.0 : lambda * wx[L - Lc];
+  }
+}
+
+// G_pq = (pp|qq) - (pq|qp) = sum_L wt_L (B_pp B_qq - |B_pq|^2)  (B Hermitian)
+__global__ void k_G(const double2* __restrict__ Bc, const double2* __restrict__ Bx, const double* __restrict__ wt,
+                    const double* __restrict__ dg, int Lc, int Lx, int n, double* __restrict__ G) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * n) return;
+  int p = (int)(idx / n), q = (int)(idx % n);
+  double acc = 0.0;
+  for (int L = 0; L < Lc + Lx; ++L) {
+    const double2* src = (L < Lc) ? Bc + (int64_t)L * n * n : Bx + (int64_t)(L - Lc) * n * n;
+    double2 b = src[idx];
+    double v = dg[(int64_t)L * n + p] * dg[(int64_t)L * n + q] - (b.x * b.x + b.y * b.y);
+    acc = fma(wt[L], v, acc);
+  }
+  G[idx] = (p == q) ? 0.0 : acc;
+}
+
+// f[p][y] = h_py + sum_L wt_L (B_py sum_k B_kk - sum_k B_pk B_ky), y < n_occ
+__global__ void k_fock(const double2* __restrict__ h, const double2* __restrict__ Bo, const double* __restrict__ wt,
+                       const double* __restrict__ dg, int L, int n, int nocc, int ncore, double2* __restrict__ f) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)n * nocc) return;
+  int p = (int)(idx / nocc), y = (int)(idx % nocc);
+  double2 acc = h[(int64_t)p * n + y];
+  for (int l = 0; l < L; ++l) {
+    const double2* B = Bo + (int64_t)l * n * nocc;
+    double trc = 0.0;
+    for (int k = 0; k < ncore; ++k) trc += dg[(int64_t)l * n + k];
+    double2 bpy = B[(int64_t)p * nocc + y];
+    double2 s = make_double2(bpy.x * trc, bpy.y * trc);
+    for (int k = 0; k < ncore; ++k) {
+      double2 m = cmul(B[(int64_t)p * nocc + k], B[(int64_t)k * nocc + y]);
+      s.x -= m.x;
+      s.y -= m.y;
+    }
+    acc.x = fma(wt[l], s.x, acc.x);
+    acc.y = fma(wt[l], s.y, acc.y);
+  }
+  f[idx] = acc;
+}
+
+// eps^_p = h_pp + sum_{k<ncore} G_pk ; E_O = sum_k h_kk + 1/2 sum_kl G_kl
+__global__ void k_scalars(const double2* __restrict__ h, const double* __restrict__ G, int n, int ncore,
+                          double* __restrict__ epsh, double* __restrict__ EO) {
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    double s = h[(int64_t)p * n + p].x;
+    for (int k = 0; k < ncore; ++k) s += G[(int64_t)p * n + k];
+    epsh[p] = s;
+  }
+  __shared__ double red[256];
+  double part = 0.0;
+  for (int k = threadIdx.x; k < ncore; k += blockDim.x) {
+    double s = h[(int64_t)k * n + k].x;
+    for (int l = 0; l < ncore; ++l) s += 0.5 * G[(int64_t)k * n + l];
+    part += s;
+  }
+  red[threadIdx.x] = part;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *EO = red[0];
+}
+
+// String list: unrank every entry (pattern block, then mixed radix over
+// subspaces with subspace 1 fastest, colex inside each subspace).
+__global__ void k_unrank(DevList Ls, DevDas das, const int64_t* __restrict__ binom) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= Ls.n) return;
+  int k = 0;
+  while (k + 1 < Ls.npat && Ls.patoff[k + 1] <= g) ++k;
+  int64_t r = g - Ls.patoff[k];
+  uint64_t A = 0;
+  for (int s = 0; s < das.n_das; ++s) {
+    int occ = Ls.patocc[k * E2_MAX_DAS + s];
+    int64_t cnt = binom[das.size[s] * kBinomN + occ];
+    int64_t rk = r % cnt;
+    r /= cnt;
+    A |= colex_unrank(rk, occ, das.size[s], binom) << das.off[s];
+  }
+  Ls.str[g] = A;
+}
+
+// e_A = sum_{t in A} eps^_t + 1/2 sum_{t != u in A} G_tu
+__global__ void k_eA(DevList Ls, const double* __restrict__ epsh, const double* __restrict__ G, int n, int a0) {
+  int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= Ls.n) return;
+  uint64_t A = Ls.str[g];
+  double e = 0.0;
+  for (uint64_t x = A; x; x &= x - 1) {
+    int t = __ffsll((long long)x) - 1;
+    e += epsh[a0 + t];
+    for (uint64_t y = x & (x - 1); y; y &= y - 1) {
+      int u = __ffsll((long long)y) - 1;
+      e += G[(int64_t)(a0 + t) * n + a0 + u];
+    }
+  }
+  Ls.eA[g] = e;
+}
+
+// U[x][A] = sum_{t in A} G_{X(x), t}; X = correlated core then correlated virtual.
+__global__ void k_U(DevList Ls, DevSpace sp, const double* __restrict__ G) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t total = (int64_t)(sp.nx + 1) * Ls.n;
+  if (idx >= total) return;
+  int x = (int)(idx / Ls.n);
+  int64_t g = idx % Ls.n;
+  double s = 0.0;
+  if (x < sp.nx) {
+    int p = (x < sp.ncc) ? sp.cc[x] : sp.vc[x - sp.ncc];
+    for (uint64_t A = Ls.str[g]; A; A &= A - 1) s += G[(int64_t)p * sp.n + sp.a0 + __ffsll((long long)A) - 1];
+  }
+  Ls.U[idx] = s;
+}
+
+// ------------------------------------------------------------------ integrals
+
+// B^L_pq through the compact factors: q < n_occ read directly, else
+// p < n_occ and B_pq = conj(B_qp) (Hermitian factors).
+__device__ __forceinline__ double2 Bget(const double2* __restrict__ Bo, int n, int nocc, int p, int q) {
+  if (q < nocc) return Bo[(int64_t)p * nocc + q];
+  return cconj(Bo[(int64_t)q * nocc + p]);
+}
+
+// <pq||rs> = sum_L wt_L (B_pr B_qs - B_ps B_qr)
+__device__ double2 asym(const double2* __restrict__ Bo, const double* __restrict__ wt, int L, int n, int nocc, int p,
+                        int q, int r, int s) {
+  double2 acc = make_double2(0.0, 0.0);
+  const int64_t stride = (int64_t)n * nocc;
+  for (int l = 0; l < L; ++l) {
+    const double2* B = Bo + l * stride;
+    double2 x = cmul(Bget(B, n, nocc, p, r), Bget(B, n, nocc, q, s));
+    double2 y = cmul(Bget(B, n, nocc, p, s), Bget(B, n, nocc, q, r));
+    acc.x = fma(wt[l], x.x - y.x, acc.x);
+    acc.y = fma(wt[l], x.y - y.y, acc.y);
+  }
+  return acc;
+}
+
+__global__ void k_integrals(int mode, DevSpace sp, const double2* __restrict__ Bo, const double* __restrict__ wt, int L,
+                            const double2* __restrict__ f, int64_t rows, int cols, int ld, void* out) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= rows * (int64_t)ld) return;
+  int64_t row = idx / ld;
+  int col = (int)(idx % ld);
+  const int na = sp.n_act, a0 = sp.a0, nvp = (int)pairs(sp.nvc), ntp = (int)pairs(na);
+  double2 v = make_double2(0.0, 0.0);
+  if (col < cols) {
+    int p = 0, q = 0, r = 0, s = 0, x, y;
+    bool fock = false;
+    switch (mode) {
+      case INT_W02: {
+        pair_decode(row, x, y);
+        p = sp.vc[x]; q = sp.vc[y];
+        pair_decode(col, x, y);
+        r = a0 + x; s = a0 + y;
+      } break;
+      case INT_W12: {
+        int i = (int)(row / nvp);
+        pair_decode(row % nvp, x, y);
+        p = sp.vc[x]; q = sp.vc[y]; r = sp.cc[i]; s = a0 + col;
+      } break;
+      case INT_W21: {
+        int a = (int)(row % sp.nvc);
+        pair_decode(row / sp.nvc, x, y);
+        p = sp.vc[a]; q = a0 + col; r = sp.cc[x]; s = sp.cc[y];
+      } break;
+      case INT_W11: {
+        int i = (int)(row / sp.nvc), a = (int)(row % sp.nvc);
+        if (col == 0) {
+          fock = true;
+          p = sp.vc[a]; q = sp.cc[i];
+        } else {
+          int t = (col - 1) / na, u = (col - 1) % na;
+          p = sp.vc[a]; q = a0 + t; r = sp.cc[i]; s = a0 + u;
+        }
+      } break;
+      case INT_W20: {
+        pair_decode(row, x, y);
+        r = sp.cc[x]; s = sp.cc[y];
+        pair_decode(col, x, y);
+        p = a0 + x; q = a0 + y;
+      } break;
+      case INT_G22: {
+        pair_decode(row, x, y);
+        r = sp.cc[x]; s = sp.cc[y];
+        pair_decode(col, x, y);
+        p = sp.vc[x]; q = sp.vc[y];
+      } break;
+      case INT_X01: {
+        int u = col / ntp;
+        pair_decode(col % ntp, x, y);
+        p = sp.vc[row]; q = a0 + u; r = a0 + x; s = a0 + y;
+      } break;
+      case INT_X10: {
+        int vv = col % na;
+        pair_decode(col / na, x, y);
+        p = a0 + x; q = a0 + y; r = sp.cc[row]; s = a0 + vv;
+      } break;
+      case INT_X00: {
+        pair_decode(row, x, y);
+        p = a0 + x; q = a0 + y;
+        pair_decode(col, x, y);
+        r = a0 + x; s = a0 + y;
+      } break;
+    }
+    if (fock) v = f[(int64_t)p * sp.n_occ + q];
+    else v = asym(Bo, wt, L, sp.n, sp.n_occ, p, q, r, s);
+  }
+  if (mode == INT_G22) ((double*)out)[idx] = v.x * v.x + v.y * v.y;
+  else ((double2*)out)[idx] = v;
+}
+
+// Row descriptors of the dense classes: U rows of particles / holes and
+// chi(e) = -sum_I eps^_i + [h=2] G_ij + sum_S eps^_s + [p=2] G_ab - sum_{IxS} G.
+__global__ void k_rows(int cls, DevSpace sp, const double* __restrict__ epsh, const double* __restrict__ G, int64_t M,
+                       RowInfo* __restrict__ out) {
+  int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= M) return;
+  const int nvp = (int)pairs(sp.nvc);
+  int I[2] = {-1, -1}, S[2] = {-1, -1}, x, y;
+  switch (cls) {
+    case 2: pair_decode(row, x, y); S[0] = x; S[1] = y; break;                                     // (0,2)
+    case 5: I[0] = (int)(row / nvp); pair_decode(row % nvp, x, y); S[0] = x; S[1] = y; break;      // (1,2)
+    case 7: S[0] = (int)(row % sp.nvc); pair_decode(row / sp.nvc, x, y); I[0] = x; I[1] = y; break;  // (2,1)
+    case 4: I[0] = (int)(row / sp.nvc); S[0] = (int)(row % sp.nvc); break;                           // (1,1)
+    case 6: pair_decode(row, x, y); I[0] = x; I[1] = y; break;                                     // (2,0)
+    case 1: S[0] = (int)row; break;                                                                 // (0,1)
+    case 3: I[0] = (int)row; break;                                                                 // (1,0)
+    default: break;                                                                                 // (0,0)
+  }
+  double chi = 0.0;
+  int gi[2], gs[2];
+  for (int k = 0; k < 2; ++k) {
+    gi[k] = I[k] >= 0 ? sp.cc[I[k]] : -1;
+    gs[k] = S[k] >= 0 ? sp.vc[S[k]] : -1;
+  }
+  for (int k = 0; k < 2; ++k) {
+    if (gi[k] >= 0) chi -= epsh[gi[k]];
+    if (gs[k] >= 0) chi += epsh[gs[k]];
+  }
+  if (gi[1] >= 0) chi += G[(int64_t)gi[0] * sp.n + gi[1]];
+  if (gs[1] >= 0) chi += G[(int64_t)gs[0] * sp.n + gs[1]];
+  for (int k = 0; k < 2; ++k)
+    for (int l = 0; l < 2; ++l)
+      if (gi[k] >= 0 && gs[l] >= 0) chi -= G[(int64_t)gi[k] * sp.n + gs[l]];
+  RowInfo ri;
+  ri.s1 = S[0] >= 0 ? sp.ncc + S[0] : sp.nx;
+  ri.s2 = S[1] >= 0 ? sp.ncc + S[1] : sp.nx;
+  ri.i1 = I[0] >= 0 ? I[0] : sp.nx;
+  ri.i2 = I[1] >= 0 ? I[1] : sp.nx;
+  ri.chi = chi;
+  out[row] = ri;
+}
+
+// ------------------------------------------------------------------ D tables
+
+// D[x][A] = <A| x |Psi_m> for one family over list Ls; c in P-address order.
+__global__ void k_dtable(int fam, DevList Ls, DevList Pl, DevDas das, const int64_t* __restrict__ binom,
+                         const double2* __restrict__ c, int Kp, double2* __restrict__ D) {
+  int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)Kp * Ls.n) return;
+  int xr = (int)(idx / Ls.n);
+  int64_t g = idx % Ls.n;
+  const uint64_t A = Ls.str[g];
+  const int na = das.n_act;
+  uint64_t Lb = 0;
+  int sign = 0;  // 0: zero entry
+  switch (fam) {
+    case FAM_T: {  // a_t on L = A + t
+      if (xr < na && !((A >> xr) & 1)) {
+        Lb = A | (1ull << xr);
+        sign = (popc_below(A, xr) & 1) ? -1 : 1;
+      }
+    } break;
+    case FAM_TD: {  // a+_t on L = A - t
+      if (xr < na && ((A >> xr) & 1)) {
+        Lb = A & ~(1ull << xr);
+        sign = (popc_below(A, xr) & 1) ? -1 : 1;
+      }
+    } break;
+    case FAM_TU: {  // a_u a_t on L = A + t + u
+      if (xr < (int)pairs(na)) {
+        int t, u;
+        pair_decode(xr, t, u);
+        if (!((A >> t) & 1) && !((A >> u) & 1)) {
+          Lb = A | (1ull << t) | (1ull << u);
+          int par = popc_below(Lb, t) + popc_below(Lb & ~(1ull << t), u);
+          sign = (par & 1) ? -1 : 1;
+        }
+      }
+    } break;
+    case FAM_TDUD: {  // a+_t a+_u on B = A - t - u
+      if (xr < (int)pairs(na)) {
+        int t, u;
+        pair_decode(xr, t, u);
+        if (((A >> t) & 1) && ((A >> u) & 1)) {
+          Lb = A & ~(1ull << t) & ~(1ull << u);
+          int par = popc_below(Lb, u) + popc_below(Lb, t);
+          sign = (par & 1) ? -1 : 1;
+        }
+      }
+    } break;
+    case FAM_TDU: {  // row 0: c_A ; row 1+t*na+u: a+_t a_u on L = A - t + u
+      if (xr == 0) {
+        Lb = A;
+        sign = 1;
+      } else if (xr <= na * na) {
+        int t = (xr - 1) / na, u = (xr - 1) % na;
+        if (((A >> t) & 1) && (u == t || !((A >> u) & 1))) {
+          Lb = (A & ~(1ull << t)) | (1ull << u);
+          int par = popc_below(Lb, u) + popc_below(A, t);
+          sign = (par & 1) ? -1 : 1;
+        }
+      }
+    } break;
+  }
+  double2 v = make_double2(0.0, 0.0);
+  if (sign != 0) {
+    int64_t ad = list_addr(Pl, das, binom, Lb);
+    if (ad >= 0) {
+      v = c[ad];
+      if (sign < 0) v = make_double2(-v.x, -v.y);
+    }
+  }
+  D[idx] = v;
+}
+
+// ------------------------------------------------------------------ E0
+
+// Fixed-order block sum of a per-thread double; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nw; ++k) t += sh[k];
+  return t;
+}
+
+// out[x][y] = sum_A conj(Da[x][A]) Db[y][A]  (one block per (x, y))
+__global__ void k_gram(const double2* __restrict__ Da, const double2* __restrict__ Db, int64_t n, int ny,
+                       double2* __restrict__ out) {
+  __shared__ double sh[32];
+  const int x = blockIdx.x / ny, y = blockIdx.x % ny;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t g = threadIdx.x; g < n; g += blockDim.x) acc = cfma(cconj(Da[(int64_t)x * n + g]), Db[(int64_t)y * n + g], acc);
+  double re = block_sum(acc.x, sh);
+  double im = block_sum(acc.y, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = make_double2(re, im);
+}
+
+// E0' = (sum_tu f_tu gamma_tu + sum_{x,y} <x||y> Gamma_xy) / <c|c>,
+// gamma_tu = <Psi|a+_t a_u|Psi>, Gamma_{(tu),(vw)} = <Psi|a+_t a+_u a_w a_v|Psi>.
+__global__ void k_e0(const double2* __restrict__ g1 /*[1+na*na] row 0 = <c|c>*/, const double2* __restrict__ g2,
+                     const double2* __restrict__ f, const double2* __restrict__ X00, DevSpace sp, int ntp,
+                     const double* __restrict__ EO, double* __restrict__ E0p, double* __restrict__ E0) {
+  __shared__ double sh[32];
+  const int na = sp.n_act;
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < na * na; k += blockDim.x) {
+    int t = k / na, u = k % na;
+    double2 fv = f[(int64_t)(sp.a0 + t) * sp.n_occ + sp.a0 + u];
+    double2 gv = g1[1 + k];
+    acc += fv.x * gv.x - fv.y * gv.y;
+  }
+  for (int k = threadIdx.x; k < ntp * ntp; k += blockDim.x) {
+    double2 xv = X00[k], gv = g2[k];
+    acc += xv.x * gv.x - xv.y * gv.y;
+  }
+  double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    double e = tot / g1[0].x;
+    *E0p = e;
+    *E0 = e + *EO;
+  }
+}
+
+// ------------------------------------------------------------------ dense classes
+
+// V[e,A] = sum_x W[e,x] D[x,A] on the FP64 tensor pipe (mma.sync m16n8k8 f64,
+// four real products per complex product), with the Epstein-Nesbet
+// denominator and |V|^2/D reduced in the epilogue; V is never stored.
+// CTA tile 64x64, 8 warps of 32x16, K steps of 8; one partial per CTA.
+constexpr int GBM = 64, GBN = 64, GBK = 8;
+
+__device__ __forceinline__ void mma_f64(double (&c)[4], const double (&a)[4], const double (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+d"(c[0]), "+d"(c[1]), "+d"(c[2]), "+d"(c[3])
+      : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(b[0]), "d"(b[1]));
+}
+
+__global__ void __launch_bounds__(256, 2)
+k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M, int64_t N, int Kp,
+             const RowInfo* __restrict__ rows, const double* __restrict__ U,
+             const double* __restrict__ eA, const double* __restrict__ E0p, double b, double* __restrict__ partial) {
+  __shared__ double2 sW[GBM][GBK + 1];
+  __shared__ double2 sD[GBK][GBN + 1];
+  __shared__ double sh[32];
+  // grid: x = row tiles, y = column tiles
+  const int64_t m0 = (int64_t)blockIdx.x * GBM, n0 = (int64_t)blockIdx.y * GBN;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int wm = warp >> 2, wn = warp & 3;  // warp tile: rows wm*32.., cols wn*16..
+  double cr[2][2][4], ci[2][2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) cr[a][c][e] = ci[a][c][e] = 0.0;
+
+  for (int k0 = 0; k0 < Kp; k0 += GBK) {
+    // W tile: 64 x 8, D tile: 8 x 64 complex; 256 threads x 2 each
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      int e = tid + q * 256;
+      int r = e >> 3, kk = e & 7;
+      int64_t gr = m0 + r;
+      sW[r][kk] = (gr < M) ? W[gr * Kp + k0 + kk] : make_double2(0.0, 0.0);
+      int kr = e >> 6, cc = e & 63;
+      int64_t gc = n0 + cc;
+      sD[kr][cc] = (gc < N) ? D[(int64_t)(k0 + kr) * N + gc] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    double ar[2][4], ai[2][4], br[2][2], bi[2][2], bn[2][2];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) {
+      const int rb = wm * 32 + mi * 16;
+      double2 x0 = sW[rb + g][tq], x1 = sW[rb + g + 8][tq], x2 = sW[rb + g][tq + 4], x3 = sW[rb + g + 8][tq + 4];
+      ar[mi][0] = x0.x; ar[mi][1] = x1.x; ar[mi][2] = x2.x; ar[mi][3] = x3.x;
+      ai[mi][0] = x0.y; ai[mi][1] = x1.y; ai[mi][2] = x2.y; ai[mi][3] = x3.y;
+    }
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni) {
+      const int cb = wn * 16 + ni * 8;
+      double2 y0 = sD[tq][cb + g], y1 = sD[tq + 4][cb + g];
+      br[ni][0] = y0.x; br[ni][1] = y1.x;
+      bi[ni][0] = y0.y; bi[ni][1] = y1.y;
+      bn[ni][0] = -y0.y; bn[ni][1] = -y1.y;
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) {
+        mma_f64(cr[mi][ni], ar[mi], br[ni]);
+        mma_f64(cr[mi][ni], ai[mi], bn[ni]);
+        mma_f64(ci[mi][ni], ar[mi], bi[ni]);
+        mma_f64(ci[mi][ni], ai[mi], br[ni]);
+      }
+    __syncthreads();
+  }
+
+  // epilogue: D_K = E0' - chi(e) - e_A - U[s1,A] - U[s2,A] + U[i1,A] + U[i2,A]
+  const double e0p = *E0p;
+  double acc = 0.0;
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int64_t row = m0 + wm * 32 + mi * 16 + g + hr * 8;
+      if (row >= M) continue;
+      const RowInfo ri = rows[row];
+      const double* U1 = U + (int64_t)ri.s1 * N;
+      const double* U2 = U + (int64_t)ri.s2 * N;
+      const double* U3 = U + (int64_t)ri.i1 * N;
+      const double* U4 = U + (int64_t)ri.i2 * N;
+      const double base = e0p - ri.chi;
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int hc = 0; hc < 2; ++hc) {
+          const int64_t col = n0 + wn * 16 + ni * 8 + 2 * tq + hc;
+          if (col >= N) continue;
+          const int e = hr * 2 + hc;
+          const double vr = cr[mi][ni][e], vi = ci[mi][ni][e];
+          const double Dk = base - eA[col] - U1[col] - U2[col] + U3[col] + U4[col];
+          acc += en_term(fma(vr, vr, vi * vi), Dk, b);
+        }
+    }
+  double tot = block_sum(acc, sh);
+  if (tid == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+
+// ------------------------------------------------------------------ class (2,2)
+
+// sum_{i<j, a<b, A} |<ab||ij>|^2 |c_A|^2 / D  with
+// D = E0' - e_A + U[i,A] + U[j,A] - chi_ij - (alpha_a + U[a,A]) - (alpha_b + U[b,A]) - G_ab,
+// chi_ij = -eps^_i - eps^_j + G_ij, alpha_a = eps^_a - G_ia - G_ja.
+// Grid: x = A tiles (one A per thread), y = ordered pairs of 8-wide virtual
+// blocks, z = (i<j).  One partial per CTA.
+__global__ void __launch_bounds__(256)
+k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* __restrict__ g2 /*[ncp][nvp]*/,
+          const double* __restrict__ epsh, const double* __restrict__ G, const double* __restrict__ E0p, double b,
+          int nvb, double* __restrict__ partial) {
+  __shared__ double sGab[8][8], sG2[8][8], sAl[2][8];
+  __shared__ double sh[32];
+  int ba = 0, bb = 0;
+  {
+    int yb = blockIdx.y, k = 0;
+    while (yb >= nvb - k) { yb -= nvb - k; ++k; }
+    ba = k;
+    bb = k + yb;
+  }
+  int iu, ju;
+  pair_decode(blockIdx.z, iu, ju);
+  const int gi = sp.cc[iu], gj = sp.cc[ju];
+  const int64_t nvp = pairs(sp.nvc);
+  const int tid = threadIdx.x;
+  if (tid < 64) {
+    int x = tid >> 3, y = tid & 7;
+    int a = ba * 8 + x, bq = bb * 8 + y;
+    bool ok = a < sp.nvc && bq < sp.nvc && a < bq;
+    sGab[x][y] = ok ? G[(int64_t)sp.vc[a] * sp.n + sp.vc[bq]] : 0.0;
+    sG2[x][y] = ok ? g2[(int64_t)blockIdx.z * nvp + pair_index(a, bq)] : 0.0;
+  } else if (tid < 80) {
+    int k = tid - 64, side = k >> 3, x = k & 7;
+    int a = (side ? bb : ba) * 8 + x;
+    double al = 0.0;
+    if (a < sp.nvc) {
+      int ga = sp.vc[a];
+      al = epsh[ga] - G[(int64_t)gi * sp.n + ga] - G[(int64_t)gj * sp.n + ga];
+    }
+    sAl[side][x] = al;
+  }
+  __syncthreads();
+  const int64_t A = blockIdx.x * (int64_t)blockDim.x + tid;
+  double acc = 0.0;
+  if (A < Ls.n) {
+    const double chi_ij = -epsh[gi] - epsh[gj] + G[(int64_t)gi * sp.n + gj];
+    const double ct = *E0p - Ls.eA[A] + Ls.U[(int64_t)iu * Ls.n + A] + Ls.U[(int64_t)ju * Ls.n + A] - chi_ij;
+    double pa[8], pb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      int a = ba * 8 + k, bq = bb * 8 + k;
+      pa[k] = (a < sp.nvc) ? sAl[0][k] + Ls.U[(int64_t)(sp.ncc + a) * Ls.n + A] : 0.0;
+      pb[k] = (bq < sp.nvc) ? sAl[1][k] + Ls.U[(int64_t)(sp.ncc + bq) * Ls.n + A] : 0.0;
+    }
+    double inner = 0.0;
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const double cx = ct - pa[x];
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        const double w = sG2[x][y];
+        if (w != 0.0) inner += en_term(w, cx - pb[y] - sGab[x][y], b);
+      }
+    }
+    double2 cv = c[A];
+    acc = (cv.x * cv.x + cv.y * cv.y) * inner;
+  }
+  double tot = block_sum(acc, sh);
+  if (tid == 0) partial[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tot;
+}
+
+// ------------------------------------------------------------------ gather classes
+
+// (0,1): V[a,A] = sum_t f_at D^t_A + sum_{u in A} (-1)^{#A<u} sum_{v<w} <au||vw> D^{vw}_{A-u}
+__global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
+                          const double2* __restrict__ DT /*[KpT][n12]*/, const double2* __restrict__ DTU /*[KpTU][n02]*/,
+                          const double2* __restrict__ X01, const double2* __restrict__ f, const double* __restrict__ epsh,
+                          const double* __restrict__ E0p, double b, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int a = blockIdx.y;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int na = sp.n_act, ntp = (int)pairs(na);
+  double acc = 0.0;
+  if (g < L01.n) {
+    const uint64_t A = L01.str[g];
+    const int ga = sp.vc[a];
+    double2 V = make_double2(0.0, 0.0);
+    int64_t a12 = list_addr(L12, das, binom, A);
+    if (a12 >= 0)
+      for (int t = 0; t < na; ++t) V = cfma(f[(int64_t)ga * sp.n_occ + sp.a0 + t], DT[(int64_t)t * L12.n + a12], V);
+    for (uint64_t x = A; x; x &= x - 1) {
+      const int u = __ffsll((long long)x) - 1;
+      const uint64_t B = A & ~(1ull << u);
+      const int64_t a02 = list_addr(L02, das, binom, B);
+      if (a02 < 0) continue;
+      double2 s = make_double2(0.0, 0.0);
+      const double2* Xr = X01 + ((int64_t)a * na + u) * ntp;
+      for (int w = 1; w < na; ++w) {
+        if ((B >> w) & 1) continue;
+        for (int v = 0; v < w; ++v) {
+          if ((B >> v) & 1) continue;
+          const int vw = pair_index(v, w);
+          s = cfma(Xr[vw], DTU[(int64_t)vw * L02.n + a02], s);
+        }
+      }
+      if (popc_below(A, u) & 1) s = make_double2(-s.x, -s.y);
+      V.x += s.x;
+      V.y += s.y;
+    }
+    const double Dk = *E0p - L01.eA[g] - epsh[ga] - L01.U[(int64_t)(sp.ncc + a) * L01.n + g];
+    acc = en_term(V.x * V.x + V.y * V.y, Dk, b);
+  }
+  double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+
+// (1,0): V[i,A] = sum_t f_ti D^{t+}_A + sum_{t<u in A} s(A;t,u) sum_v <tu||iv> D^v_{A-t-u}
+__global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
+                          const double2* __restrict__ DTD /*[Kp][n21]*/, const double2* __restrict__ DT /*[Kp][n12]*/,
+                          const double2* __restrict__ X10, const double2* __restrict__ f, const double* __restrict__ epsh,
+                          const double* __restrict__ E0p, double b, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int i = blockIdx.y;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int na = sp.n_act;
+  double acc = 0.0;
+  if (g < L10.n) {
+    const uint64_t A = L10.str[g];
+    const int gi = sp.cc[i];
+    double2 V = make_double2(0.0, 0.0);
+    int64_t a21 = list_addr(L21, das, binom, A);
+    if (a21 >= 0)
+      for (int t = 0; t < na; ++t) V = cfma(f[(int64_t)(sp.a0 + t) * sp.n_occ + gi], DTD[(int64_t)t * L21.n + a21], V);
+    for (uint64_t xu = A; xu; xu &= xu - 1) {
+      const int u = __ffsll((long long)xu) - 1;
+      for (uint64_t xt = A & ((1ull << u) - 1); xt; xt &= xt - 1) {
+        const int t = __ffsll((long long)xt) - 1;
+        const uint64_t B = A & ~(1ull << t) & ~(1ull << u);
+        const int64_t a12 = list_addr(L12, das, binom, B);
+        if (a12 < 0) continue;
+        const double2* Xr = X10 + ((int64_t)i * pairs(na) + pair_index(t, u)) * na;
+        double2 s = make_double2(0.0, 0.0);
+        for (int v = 0; v < na; ++v) {
+          if ((B >> v) & 1) continue;
+          s = cfma(Xr[v], DT[(int64_t)v * L12.n + a12], s);
+        }
+        if ((popc_below(B, u) + popc_below(B, t)) & 1) s = make_double2(-s.x, -s.y);
+        V.x += s.x;
+        V.y += s.y;
+      }
+    }
+    const double Dk = *E0p - L10.eA[g] + epsh[gi] + L10.U[(int64_t)i * L10.n + g];
+    acc = en_term(V.x * V.x + V.y * V.y, Dk, b);
+  }
+  double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+}
+
+// (0,0), DAS only: V[A] = sum_{tu} f_tu D^{t+u}_A + sum_{t<u in A} s(A;t,u) sum_{v<w} <tu||vw> D^{vw}_{A-t-u}
+__global__ void k_class00(DevList L00, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
+                          const double2* __restrict__ DTDU /*[Kp][n11]*/, const double2* __restrict__ DTU /*[Kp][n02]*/,
+                          const double2* __restrict__ X00, const double2* __restrict__ f, const double* __restrict__ E0p,
+                          double b, double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int na = sp.n_act, ntp = (int)pairs(na);
+  double acc = 0.0;
+  if (g < L00.n) {
+    const uint64_t A = L00.str[g];
+    double2 V = make_double2(0.0, 0.0);
+    int64_t a11 = list_addr(L11, das, binom, A);
+    if (a11 >= 0)
+      for (int t = 0; t < na; ++t)
+        for (int u = 0; u < na; ++u)
+          V = cfma(f[(int64_t)(sp.a0 + t) * sp.n_occ + sp.a0 + u], DTDU[(int64_t)(1 + t * na + u) * L11.n + a11], V);
+    for (uint64_t xu = A; xu; xu &= xu - 1) {
+      const int u = __ffsll((long long)xu) - 1;
+      for (uint64_t xt = A & ((1ull << u) - 1); xt; xt &= xt - 1) {
+        const int t = __ffsll((long long)xt) - 1;
+        const uint64_t B = A & ~(1ull << t) & ~(1ull << u);
+        const int64_t a02 = list_addr(L02, das, binom, B);
+        if (a02 < 0) continue;
+        const double2* Xr = X00 + (int64_t)pair_index(t, u) * ntp;
+        double2 s = make_double2(0.0, 0.0);
+        for (int w = 1; w < na; ++w) {
+          if ((B >> w) & 1) continue;
+          for (int v = 0; v < w; ++v) {
+            if ((B >> v) & 1) continue;
+            const int vw = pair_index(v, w);
+            s = cfma(Xr[vw], DTU[(int64_t)vw * L02.n + a02], s);
+          }
+        }
+        if ((popc_below(B, u) + popc_below(B, t)) & 1) s = make_double2(-s.x, -s.y);
+        V.x += s.x;
+        V.y += s.y;
+      }
+    }
+    const double Dk = *E0p - L00.eA[g];
+    acc = en_term(V.x * V.x + V.y * V.y, Dk, b);
+  }
+  double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// ------------------------------------------------------------------ reductions
+
+// E2_class[root][cls] = sum of the class partials in index order (one block each);
+// norm = <c|c> divides every term (Sec. 2.3 takes Psi normalised).
+__global__ void k_reduce(const double* __restrict__ partial, const int64_t* __restrict__ off, const int64_t* __restrict__ cnt,
+                         const double2* __restrict__ g1_all, int g1_stride, int n_roots, double* __restrict__ e2c) {
+  __shared__ double sh[32];
+  const int root = blockIdx.x / E2_NCLASS, cls = blockIdx.x % E2_NCLASS;
+  const int64_t o = off[root * E2_NCLASS + cls], n = cnt[cls];
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < n; k += blockDim.x) acc += partial[o + k];
+  double tot = block_sum(acc, sh);
+  if (threadIdx.x == 0) e2c[root * E2_NCLASS + cls] = tot / g1_all[(int64_t)root * g1_stride].x;
+}
+
+__global__ void k_finalize(const double* __restrict__ e2c, int n_roots, double* __restrict__ E2,
+                           const double* __restrict__ E0in, double* __restrict__ E0out) {
+  int r = threadIdx.x;
+  if (r >= n_roots) return;
+  double s = 0.0;
+  for (int k = 0; k < E2_NCLASS; ++k) s += e2c[r * E2_NCLASS + k];
+  E2[r] = s;
+  if (E0out) E0out[r] = E0in[r];
+}
+
+}  // namespace e2

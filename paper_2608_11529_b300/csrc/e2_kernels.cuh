@@ -1,0 +1,43 @@
+// Kernel entry points (defined in e2_kernels.cu), launched by e2_api.cu.
+#pragma once
+#include "e2_common.cuh"
+
+namespace e2 {
+
+__global__ void k_binom(int64_t* tab);
+__global__ void k_extract(const double2* Bc, const double2* Bx, const double* wx, double lambda, int Lc, int Lx, int n,
+                          int nocc, double2* Bo, double* wt, double* dg);
+__global__ void k_G(const double2* Bc, const double2* Bx, const double* wt, const double* dg, int Lc, int Lx, int n,
+                    double* G);
+__global__ void k_fock(const double2* h, const double2* Bo, const double* wt, const double* dg, int L, int n, int nocc,
+                       int ncore, double2* f);
+__global__ void k_scalars(const double2* h, const double* G, int n, int ncore, double* epsh, double* EO);
+__global__ void k_unrank(DevList Ls, DevDas das, const int64_t* binom);
+__global__ void k_eA(DevList Ls, const double* epsh, const double* G, int n, int a0);
+__global__ void k_U(DevList Ls, DevSpace sp, const double* G);
+__global__ void k_integrals(int mode, DevSpace sp, const double2* Bo, const double* wt, int L, const double2* f,
+                            int64_t rows, int cols, int ld, void* out);
+__global__ void k_rows(int cls, DevSpace sp, const double* epsh, const double* G, int64_t M, RowInfo* out);
+__global__ void k_dtable(int fam, DevList Ls, DevList Pl, DevDas das, const int64_t* binom, const double2* c, int Kp,
+                         double2* D);
+__global__ void k_gram(const double2* Da, const double2* Db, int64_t n, int ny, double2* out);
+__global__ void k_e0(const double2* g1, const double2* g2, const double2* f, const double2* X00, DevSpace sp, int ntp,
+                     const double* EO, double* E0p, double* E0);
+__global__ void k_class_gemm(const double2* W, const double2* D, int64_t M, int64_t N, int Kp, const RowInfo* rows,
+                             const double* U, const double* eA, const double* E0p, double b, double* partial);
+__global__ void k_class22(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
+                          const double* G, const double* E0p, double b, int nvb, double* partial);
+__global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, DevSpace sp, const int64_t* binom,
+                          const double2* DT, const double2* DTU, const double2* X01, const double2* f,
+                          const double* epsh, const double* E0p, double b, double* partial);
+__global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, DevSpace sp, const int64_t* binom,
+                          const double2* DTD, const double2* DT, const double2* X10, const double2* f,
+                          const double* epsh, const double* E0p, double b, double* partial);
+__global__ void k_class00(DevList L00, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* binom,
+                          const double2* DTDU, const double2* DTU, const double2* X00, const double2* f,
+                          const double* E0p, double b, double* partial);
+__global__ void k_reduce(const double* partial, const int64_t* off, const int64_t* cnt, const double2* g1_all,
+                         int g1_stride, int n_roots, double* e2c);
+__global__ void k_finalize(const double* e2c, int n_roots, double* E2, const double* E0in, double* E0out);
+
+}  // namespace e2
