@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Throughput of the Epstein-Nesbet second-order energy on B300.
+
+Metric: E2 perturber couplings/s (FP64).  A coupling is one external
+determinant K (per root) whose V_K = <K|H|Psi> is formed and whose
+|V_K|^2 / (E0 - H_KK) is reduced.  One step = one full e2_forward over every
+external class of the workload (all of Q), inputs resident in HBM.
+
+Default workload: the Ne-shaped DCG problem (2 core spinors, CAS 8e in 16
+active spinors = 12,870 reference determinants, 200 virtual spinors,
+400 Coulomb + 200 Gaunt factors, one root), 880,539,088 couplings per step.
+Its factor inputs (456 MB) are larger than L2 and every step re-reads them.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs the same workload on its own GPU (independent
+replicas, weak scaling); no data crosses between ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "E2 perturber couplings/s (FP64, |ΔE2|≤1e-9 Eh); fwd+bwd vs fwd time"
+WORKLOADS = {
+    "cfg2": "Ne-shaped DCG: 2 core + CAS(8e,16) + 200 virtual spinors, 400 Coulomb + 200 Gaunt factors, 1 root",
+    "cfg1": "DC: 4 core + CAS(6e,12) + 40 virtual spinors, 60 Coulomb factors, 1 root",
+}
+GEMM_CLASSES = {2: "ntp", 5: "na", 7: "na", 4: "na2p1", 6: "ntp"}
+CLASS_NAMES = ["(0,0)", "(0,1)", "(0,2)", "(1,0)", "(1,1)", "(1,2)", "(2,0)", "(2,1)", "(2,2)"]
+KERNEL_OF_CLASS = {c: "k_class_gemm" for c in GEMM_CLASSES} | {8: "k_class22", 1: "k_class01", 3: "k_class10",
+                                                                0: "k_class00"}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _kdim(prob, cls):
+    na = prob.n_act
+    return {"ntp": na * (na - 1) // 2, "na": na, "na2p1": 1 + na * na}[GEMM_CLASSES[cls]]
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-i", str(self.gpu), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path))
+    src = open(os.path.join(ROOT, "paper_2608_11529_b300", "csrc", "e2_kernels.cu"), "rb").read()
+    if rec.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec.get("bytes_per_launch", {}).get(kernel)
+
+
+def _sample_ks(prob, n, rng):
+    """n random external determinants of the workload, drawn with the class
+    sizes as weights: (holes, particles, active string)."""
+    from math import comb
+    nc = [k for k in range(prob.n_core) if not prob.frozen[k]]
+    nv = [v for v in range(prob.n_core + prob.n_act, prob.n) if not prob.frozen[v]]
+    cls, w = [], []
+    for h in range(3):
+        for p in range(3):
+            ne = prob.n_elec + h - p
+            if (h, p) == (0, 0) or ne < 0 or ne > prob.n_act:
+                continue
+            cls.append((h, p, ne))
+            w.append(comb(len(nc), h) * comb(len(nv), p) * comb(prob.n_act, ne))
+    w = np.array(w, float) / sum(w)
+    pick = rng.choice(len(cls), size=n, p=w)
+    nh, hs, npp, ps, acts = [], [], [], [], []
+    for k in pick:
+        h, p, ne = cls[k]
+        I = sorted(rng.choice(nc, size=h, replace=False).tolist()) if h else []
+        S = sorted(rng.choice(nv, size=p, replace=False).tolist()) if p else []
+        A = rng.choice(prob.n_act, size=ne, replace=False)
+        nh.append(h), npp.append(p)
+        hs.append(I + [0] * (2 - h)), ps.append(S + [0] * (2 - p))
+        acts.append(int(sum(1 << int(t) for t in A)))
+    return nh, hs, npp, ps, acts
+
+
+def oracle_rate(prob, seconds=15.0, seed=0):
+    """Couplings/s of the oracle on a bounded random sample of the workload's
+    external determinants (V_K from the explicit Q H P row and H_KK), on all
+    host cores."""
+    from oracle import Oracle
+    o = Oracle(prob, use_eri_cache=False)
+    c = prob.X0[:1] / np.linalg.norm(prob.X0[:1])
+    o.set_c(c)
+    rng = np.random.default_rng(seed)
+    E0 = np.zeros(1)
+    n = 256
+    while True:   # calibrate the sample size to about `seconds` of work
+        t0 = time.perf_counter()
+        o.couplings(E0, *_sample_ks(prob, n, rng))
+        dt = time.perf_counter() - t0
+        if dt >= 0.2 * seconds or n >= 2_000_000:
+            break
+        n *= 4
+    n = int(max(256, min(4_000_000, n * seconds / max(dt, 1e-3))))
+    args = _sample_ks(prob, n, rng)
+    t0 = time.perf_counter()
+    o.couplings(E0, *args)
+    dt = time.perf_counter() - t0
+    return n / dt, n, dt
+
+
+def run_reference(args):
+    """The oracle arm: each step times the oracle on a bounded sample of the workload."""
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from e2_inputs import make_problem
+    prob = make_problem(args.config)
+    cores = os.cpu_count()
+    for _ in range(args.warmup):
+        oracle_rate(prob, seconds=args.ref_seconds, seed=1)
+    rates, ns, dts = [], [], []
+    for s in range(args.steps):
+        r, n, dt = oracle_rate(prob, seconds=args.ref_seconds, seed=100 + s)
+        rates.append(r), ns.append(n), dts.append(dt)
+    value = sum(ns) / sum(dts)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "couplings/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / len(dts),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config], "couplings_per_step": int(sum(ns) / len(ns))},
+            "cpu_baseline": {"value": value, "unit": "couplings/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{int(sum(ns) / len(ns))} random external determinants per step "
+                                       f"(class-size weighted), V_K and H_KK each"},
+            "e2e": {"value": value, "unit": "couplings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run(args):
+    import torch
+    import torch.distributed as dist
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    import paper_2608_11529_b300 as e2
+    from e2_inputs import make_problem
+    over = dict(Lc=args.factors, Lx=args.factors // 2) if args.factors else {}
+    prob = make_problem(args.config, **over)
+    plan = e2.E2Problem.from_problem(prob)
+    couplings = float(plan.q_per_class.sum()) * plan.n_roots
+    t = e2.device_inputs(prob, prob.X0, device=dev)
+    c, E0_ref, iters = plan.reference_solve(t["h"], t["B_c"], t["c"], t["B_x"], t["w_x"], lam=t["lam"], tol=1e-10)
+    t["c"] = c
+    torch.cuda.synchronize()
+    peak_dmma, peak_dfma = e2.fp64_peak(dev)
+
+    # warm-up
+    for _ in range(args.warmup):
+        plan.forward(**t)
+    torch.cuda.synchronize()
+    launches = plan.launch_count()
+
+    # per-step event pairs around each class kernel (handles materialised here)
+    evs = []
+    for _ in range(args.steps):
+        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(9)]
+        for a, b in pairs:
+            a.record()
+            b.record()
+        evs.append(pairs)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    stream = torch.cuda.current_stream(dev)
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    start.record(stream)
+    for s in range(args.steps):
+        plan.set_events(evs[s])
+        E2, E2c, E0 = plan.forward(**t)
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if ws > 1:
+        dist.barrier()
+    plan.set_events(None)
+    ms = start.elapsed_time(end) / args.steps
+    ms_all = torch.tensor([ms], device=dev)
+    if ws > 1:
+        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
+    ms = float(ms_all.item())
+
+    # per-class kernel times (root 0) over the timed region
+    present = [k for k in range(9) if plan.q_per_class[k] > 0]
+    ktime = {k: sum(evs[s][k][0].elapsed_time(evs[s][k][1]) for s in range(args.steps)) / args.steps for k in present}
+    dom = max(ktime, key=ktime.get)
+    if dom in GEMM_CLASSES:
+        flops = 8.0 * plan.q_per_class[dom] * _kdim(prob, dom)
+        achieved = flops / (ktime[dom] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_dmma, "unit": "TFLOP/s",
+                "frac": achieved / peak_dmma, "traffic": _traffic("k_class_gemm"),
+                "kernel": f"k_class_gemm class {CLASS_NAMES[dom]}", "peak_source":
+                "measured on this GPU: mma.sync m16n8k8 f64 burst (e2_fp64_peak)",
+                "algorithmic_flops_per_launch": flops, "ms_per_launch": ktime[dom]}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": peak_dfma, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": KERNEL_OF_CLASS[dom]}
+
+    # end to end through the public API: pinned host inputs -> device, forward, E2 -> host
+    e2e = None
+    if not args.no_e2e:
+        host = {k: (v.cpu().pin_memory() if torch.is_tensor(v) else v) for k, v in t.items()}
+        h2d = sum(v.numel() * v.element_size() for v in host.values() if torch.is_tensor(v))
+        dev_in = {k: (torch.empty_like(v, device=dev) if torch.is_tensor(v) else v) for k, v in host.items()}
+        out_host = torch.empty(plan.n_roots, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            for k, v in host.items():
+                if torch.is_tensor(v):
+                    dev_in[k].copy_(v, non_blocking=True)
+            E2_, _, _ = plan.forward(**dev_in)
+            out_host.copy_(E2_, non_blocking=True)
+
+        for _ in range(2):
+            e2e_step()
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ems = s0.elapsed_time(s1) / args.steps
+        e2e = {"value": ws * couplings / (ems * 1e-3), "unit": "couplings/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": ems}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        r, n, dt = oracle_rate(prob, seconds=args.ref_seconds)
+        cpu = {"value": r, "unit": "couplings/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} random external determinants of this workload (class-size weighted), "
+                         f"V_K from the explicit Q H P row and H_KK each, {dt:.1f} s"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": ws * couplings / (ms * 1e-3), "unit": "couplings/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOADS[args.config], "couplings_per_step": int(couplings),
+                           "roots": plan.n_roots, "reference": f"device Davidson, {iters} iterations",
+                           "l2": "inputs larger than L2: the 456 MB factor set is re-read every step",
+                           "E2": float(E2.cpu()[0]), "E0": float(E0.cpu()[0]),
+                           "class_ms": {CLASS_NAMES[k]: ktime[k] for k in present}},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
+                "clocks": clk, "fp64_peaks_tflops": {"dmma": peak_dmma, "dfma": peak_dfma}}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--config", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ref-seconds", type=float, default=6.0)
+    ap.add_argument("--factors", type=int, default=0,
+                    help="override the Coulomb factor count (extra set = half); a small-memory variant with the "
+                         "same class shapes, for profiler captures")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -143,6 +143,36 @@ E2_API e2_status e2_workspace_size(const e2_problem* prob, size_t* bytes);
 E2_API e2_status e2_forward(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
                      void* stream, double* E2, double* E2_class, double* E0);
 
+/* Reference states: the n_roots lowest eigenvectors of P H P (the CASCI /
+ * DAS-CI reference of Sec. 2.2-2.3, Eq. zeroh first term), by block Davidson
+ * iteration on the device (sigma = P H c built from the same coupling
+ * tensors as the (0,0) class; preconditioner diag(H_PP)).  Convergence: every
+ * residual norm ||H x - theta x|| < tol for unit-norm x.
+ *   in->c     device [n_roots][N_P] start vectors (any full-rank block)
+ *   c_out     device [n_roots][N_P] unit-norm eigenvectors (may alias in->c)
+ *   E0_out    host   [n_roots] eigenvalues, ascending
+ *   iters_out host, iterations used (may be NULL)
+ * Synchronises `stream` (small projected problems are solved on the host).
+ * Returns E2_ERR_SHAPE if the start block is rank deficient.  The workspace
+ * must be at least e2_reference_workspace_size() bytes (it contains the
+ * e2_forward layout). */
+E2_API e2_status e2_reference_workspace_size(const e2_problem* prob, size_t* bytes);
+E2_API e2_status e2_reference_solve(e2_problem* prob, const e2_inputs* in, double tol, int max_iter, void* workspace,
+                                    size_t workspace_bytes, void* stream, double* c_out, double* E0_out, int* iters_out);
+
+/* Measurement hooks (no counterpart in the paper; used for the roofline).
+ * e2_profile_events: `events` is NULL (off) or 2*E2_NCLASS cudaEvent_t
+ * handles owned by the caller; e2_forward then records events[2c] before and
+ * events[2c+1] after the class-c kernel of root 0 on its stream.
+ * e2_fp64_peak: times FP64 tensor-pipe (mma.sync m16n8k8 f64) and FP64 FMA
+ * throughput on the current device in TFLOP/s.  Needs a device scratch of
+ * 8 * 256 * 8 * (SM count) bytes; synchronises `stream`. */
+E2_API e2_status e2_profile_events(e2_problem* prob, void* const* events);
+/* Number of kernels the last e2_forward on this problem enqueued. */
+E2_API e2_status e2_launch_count(const e2_problem* prob, int64_t* n);
+E2_API e2_status e2_fp64_peak(void* workspace, size_t workspace_bytes, void* stream, double* dmma_tflops,
+                              double* dfma_tflops);
+
 E2_API const char* e2_status_string(e2_status s);
 
 #ifdef __cplusplus

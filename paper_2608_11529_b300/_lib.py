@@ -52,6 +52,17 @@ def load():
         L.e2_forward.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p]
         L.e2_forward.restype = C.c_int
+        L.e2_reference_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
+        L.e2_reference_workspace_size.restype = C.c_int
+        L.e2_reference_solve.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_double, C.c_int, C.c_void_p, C.c_size_t,
+                                         C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
+        L.e2_reference_solve.restype = C.c_int
+        L.e2_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+        L.e2_launch_count.restype = C.c_int
+        L.e2_profile_events.argtypes = [C.c_void_p, C.c_void_p]
+        L.e2_profile_events.restype = C.c_int
+        L.e2_fp64_peak.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        L.e2_fp64_peak.restype = C.c_int
         L.e2_status_string.argtypes = [C.c_int]
         L.e2_status_string.restype = C.c_char_p
         _lib = L
@@ -98,7 +109,10 @@ class E2Problem:
         ws = C.c_size_t()
         _check(L.e2_workspace_size(self._h, C.byref(ws)))
         self.workspace_bytes = int(ws.value)
+        _check(L.e2_reference_workspace_size(self._h, C.byref(ws)))
+        self.solve_workspace_bytes = int(ws.value)
         self._ws = None
+        self._events = None
 
     @classmethod
     def from_problem(cls, prob, class_mask=0x1FF, n_roots=None, level_shift_b=None):
@@ -118,15 +132,74 @@ class E2Problem:
         except Exception:
             pass
 
-    def workspace(self, device):
-        """A 256-byte aligned uint8 CUDA tensor of the required size (cached)."""
+    def workspace(self, device, solver=False):
+        """A 256-byte aligned uint8 CUDA tensor of the required size (cached);
+        the reference solver needs the larger layout, which contains the
+        forward one."""
         import torch
-        if self._ws is None or self._ws.device != device:
-            raw = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=device)
+        need = self.solve_workspace_bytes if solver else self.workspace_bytes
+        if self._ws is None or self._ws.device != device or self._ws.numel() < need:
+            self._ws = None
+            raw = torch.empty(need + 256, dtype=torch.uint8, device=device)
             off = (-raw.data_ptr()) % 256
             self._ws_raw = raw
-            self._ws = raw[off:off + self.workspace_bytes]
+            self._ws = raw[off:off + need]
         return self._ws
+
+    def reference_solve(self, h, B_c, X0, B_x=None, w_x=None, lam=1.0, tol=1e-10, max_iter=300, stream=None):
+        """Lowest n_roots eigenvectors of P H P from start vectors X0 [roots, N_P]
+        (complex128 CUDA).  Returns (c [roots, N_P] CUDA, E0 numpy, iterations)."""
+        import torch
+        dev = X0.device
+        ws = self.workspace(dev, solver=True)
+        c = torch.empty_like(X0)
+        E0 = np.zeros(self.n_roots)
+        it = C.c_int()
+        inp = _Inputs(h.data_ptr(), B_c.data_ptr(), B_x.data_ptr() if self.L_extra else None,
+                      w_x.data_ptr() if self.L_extra else None, float(lam), X0.data_ptr())
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        _check(load().e2_reference_solve(self._h, C.byref(inp), tol, max_iter, ws.data_ptr(), ws.numel(),
+                                         C.c_void_p(s), c.data_ptr(), E0.ctypes.data_as(C.c_void_p), C.byref(it)))
+        return c, E0, int(it.value)
+
+    def launch_count(self):
+        """Kernels enqueued by the last forward()."""
+        n = C.c_int64()
+        _check(load().e2_launch_count(self._h, C.byref(n)))
+        return int(n.value)
+
+    def set_events(self, pairs):
+        """Point the class-kernel hooks at (start, end) torch.cuda.Event pairs
+        (already recorded once) or switch them off with None; no sync."""
+        if pairs is None:
+            _check(load().e2_profile_events(self._h, None))
+            return
+        arr = (C.c_void_p * (2 * NCLASS))()
+        for k, (a, b) in enumerate(pairs):
+            arr[2 * k] = a.cuda_event
+            arr[2 * k + 1] = b.cuda_event
+        self._event_arr = arr
+        _check(load().e2_profile_events(self._h, arr))
+
+    def profile(self, on=True):
+        """Record CUDA events around each class kernel of root 0 in forward();
+        returns the list of (start, end) torch.cuda.Event pairs per class."""
+        import torch
+        if not on:
+            _check(load().e2_profile_events(self._h, None))
+            self._events = None
+            return None
+        self._events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                        for _ in range(NCLASS)]
+        arr = (C.c_void_p * (2 * NCLASS))()
+        for k, (a, b) in enumerate(self._events):
+            a.record()  # materialise the handles
+            b.record()
+            arr[2 * k] = a.cuda_event
+            arr[2 * k + 1] = b.cuda_event
+        torch.cuda.synchronize()
+        _check(load().e2_profile_events(self._h, arr))
+        return self._events
 
     def forward(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, stream=None, workspace=None, out=None):
         """E2 per root.  Tensors: complex128 CUDA, contiguous.  Returns
@@ -150,6 +223,17 @@ class E2Problem:
         _check(load().e2_forward(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s), E2.data_ptr(),
                                  E2c.data_ptr(), E0.data_ptr()))
         return E2, E2c, E0
+
+
+def fp64_peak(device="cuda"):
+    """Measured FP64 tensor-pipe (mma.sync f64) and FP64 FMA TFLOP/s of the device."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    buf = torch.empty(8 * 256 * 8 * sms, dtype=torch.uint8, device=device)
+    a, b = C.c_double(), C.c_double()
+    _check(load().e2_fp64_peak(buf.data_ptr(), buf.numel(), C.c_void_p(torch.cuda.current_stream(device).cuda_stream),
+                               C.byref(a), C.byref(b)))
+    return a.value, b.value
 
 
 def device_inputs(prob, c, device="cuda"):

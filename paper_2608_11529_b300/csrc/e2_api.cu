@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <complex>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -81,6 +82,13 @@ struct e2_problem {
   std::vector<unsigned char> plan_blob;         // host image of the plan region
   // launch shapes of the sparse / elementwise classes
   int nvb;
+  // optional CUDA events around each class kernel of root 0 (bench hooks)
+  cudaEvent_t prof[2 * E2_NCLASS];
+  bool prof_on = false;
+  int64_t launches = 0;  // kernels enqueued by the last e2_forward
+  // reference solver region
+  int sv_mmax;
+  size_t o_sV, o_sS, o_sX, o_sR, o_sD, o_sT, o_sG, o_sY, solve_bytes;
 };
 
 namespace {
@@ -311,6 +319,18 @@ e2_status build_plan(e2_problem* P) {
   P->o_part = ws.take(sizeof(double) * std::max<int64_t>(tot, 1));
   P->o_e2c = ws.take(sizeof(double) * R * E2_NCLASS);
   P->ws_bytes = ws.top;
+  // reference solver (block Davidson) on top of the forward layout
+  const int64_t np_ = P->lists[P->listP].n;
+  P->sv_mmax = (int)std::min<int64_t>(np_, 10 * R + 10);
+  P->o_sV = ws.take(16 * (size_t)P->sv_mmax * np_);
+  P->o_sS = ws.take(16 * (size_t)P->sv_mmax * np_);
+  P->o_sX = ws.take(16 * (size_t)R * np_);
+  P->o_sR = ws.take(16 * (size_t)R * np_);
+  P->o_sD = ws.take(16 * (size_t)R * np_);
+  P->o_sT = ws.take(16 * (size_t)R * np_);
+  P->o_sG = ws.take(16 * (size_t)P->sv_mmax * P->sv_mmax);
+  P->o_sY = ws.take(16 * (size_t)P->sv_mmax * std::max(R, 1));
+  P->solve_bytes = ws.top;
 
   // ---- host image of the plan region
   P->plan_blob.assign(P->plan_bytes, 0);
@@ -347,6 +367,185 @@ DevList dev_list(const e2_problem* P, int li, unsigned char* ws) {
 }
 
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// kernels enqueued by the current host thread (read back as the count of one call)
+thread_local int64_t g_launches = 0;
+
+using cd = std::complex<double>;
+
+// Cyclic Jacobi for a complex Hermitian matrix A (n x n, row-major):
+// eigenvalues ascending in w, eigenvectors in the columns of V (row-major).
+// Each rotation U = [[c, s e^{i phi}], [-s e^{-i phi}, c]] in the (p,q) plane
+// zeroes A_pq = g e^{i phi}: t = s/c solves t^2 + 2 tau t - 1 = 0,
+// tau = (A_qq - A_pp) / (2 g), smaller root.
+void herm_eig(int n, std::vector<cd> A, std::vector<double>& w, std::vector<cd>& V) {
+  V.assign((size_t)n * n, cd(0.0, 0.0));
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, dia = 0.0;
+    for (int p = 0; p < n; ++p) {
+      dia += std::norm(A[(size_t)p * n + p]);
+      for (int q = p + 1; q < n; ++q) off += std::norm(A[(size_t)p * n + q]);
+    }
+    if (off <= 1e-32 * (dia + 1e-300)) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const cd apq = A[(size_t)p * n + q];
+        const double g = std::abs(apq);
+        if (g < 1e-300) continue;
+        const cd ph = apq / g;
+        const double a = A[(size_t)p * n + p].real(), bq = A[(size_t)q * n + q].real();
+        const double tau = (bq - a) / (2.0 * g);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+        const cd u00 = cs, u01 = sn * ph, u10 = -sn * std::conj(ph), u11 = cs;
+        for (int r = 0; r < n; ++r) {  // A <- A U, V <- V U
+          cd x = A[(size_t)r * n + p], y = A[(size_t)r * n + q];
+          A[(size_t)r * n + p] = x * u00 + y * u10;
+          A[(size_t)r * n + q] = x * u01 + y * u11;
+          x = V[(size_t)r * n + p];
+          y = V[(size_t)r * n + q];
+          V[(size_t)r * n + p] = x * u00 + y * u10;
+          V[(size_t)r * n + q] = x * u01 + y * u11;
+        }
+        for (int r = 0; r < n; ++r) {  // A <- U^H A
+          cd x = A[(size_t)p * n + r], y = A[(size_t)q * n + r];
+          A[(size_t)p * n + r] = std::conj(u00) * x + std::conj(u10) * y;
+          A[(size_t)q * n + r] = std::conj(u01) * x + std::conj(u11) * y;
+        }
+      }
+  }
+  std::vector<int> ord(n);
+  for (int i = 0; i < n; ++i) ord[i] = i;
+  std::sort(ord.begin(), ord.end(), [&](int x, int y) { return A[(size_t)x * n + x].real() < A[(size_t)y * n + y].real(); });
+  w.resize(n);
+  std::vector<cd> Vs((size_t)n * n);
+  for (int j = 0; j < n; ++j) {
+    w[j] = A[(size_t)ord[j] * n + ord[j]].real();
+    for (int i = 0; i < n; ++i) Vs[(size_t)i * n + j] = V[(size_t)i * n + ord[j]];
+  }
+  V.swap(Vs);
+}
+
+struct Ctx {
+  const int64_t* binom;
+  double *G, *epsh, *EO, *E0p, *E0d, *dg, *wt;
+  double2 *Bo, *f;
+  DevSpace sp;
+};
+
+Ctx ctx(const e2_problem* P, unsigned char* ws) {
+  Ctx X;
+  X.binom = (const int64_t*)(ws + P->o_binom);
+  X.G = (double*)(ws + P->o_G);
+  X.epsh = (double*)(ws + P->o_epsh);
+  X.EO = (double*)(ws + P->o_EO);
+  X.E0p = (double*)(ws + P->o_E0p);
+  X.E0d = (double*)(ws + P->o_E0);
+  X.dg = (double*)(ws + P->o_dg);
+  X.wt = (double*)(ws + P->o_wt);
+  X.Bo = (double2*)(ws + P->o_Bo);
+  X.f = (double2*)(ws + P->o_f);
+  DevSpace& sp = X.sp;
+  sp.n = P->n;
+  sp.n_core = P->d.n_core;
+  sp.n_act = P->na;
+  sp.n_virt = P->d.n_virt;
+  sp.n_occ = P->nocc;
+  sp.a0 = P->d.n_core;
+  sp.v0 = P->nocc;
+  sp.ncc = P->ncc;
+  sp.nvc = P->nvc;
+  sp.nx = P->nx;
+  sp.cc = (const int32_t*)(ws + P->o_cc);
+  sp.vc = (const int32_t*)(ws + P->o_vc);
+  return X;
+}
+
+struct Tabs {
+  double2 *DT, *DTD, *DTU, *DTDUD, *DTDU;
+};
+
+Tabs tables(const e2_problem* P, unsigned char* ws, int r) {
+  unsigned char* dr = ws + P->d_stride * r;
+  return Tabs{(double2*)(dr + P->o_DT), (double2*)(dr + P->o_DTD), (double2*)(dr + P->o_DTU),
+              (double2*)(dr + P->o_DTDUD), (double2*)(dr + P->o_DTDU)};
+}
+
+// Coupling tensors D^x_A = <A|x|c> of one reference vector c; `all` = false
+// builds only the two that the active sigma needs.
+void build_tables(const e2_problem* P, unsigned char* ws, cudaStream_t st, const double2* c, const Tabs& T, bool all) {
+  const DevList LP = dev_list(P, P->listP, ws);
+  const Ctx X = ctx(P, ws);
+  struct Spec {
+    int fam, cls, Kp;
+    double2* out;
+  } tabs[5] = {{FAM_TU, 2, P->KpTU, T.DTU}, {FAM_TDU, 4, P->Kp11, T.DTDU}, {FAM_T, 5, P->KpT, T.DT},
+               {FAM_TD, 7, P->KpT, T.DTD}, {FAM_TDUD, 6, P->KpTU, T.DTDUD}};
+  for (int k = 0; k < (all ? 5 : 2); ++k) {
+    const Spec& t = tabs[k];
+    const DevList L = dev_list(P, P->list_of[t.cls], ws);
+    if (L.n == 0) continue;
+    (k_dtable<<<blocks((int64_t)t.Kp * L.n), 256, 0, st>>>(t.fam, L, LP, P->das, X.binom, c, t.Kp, t.out), ++g_launches);
+  }
+}
+
+// Everything that depends only on the Hamiltonian and the partition:
+// binomials, compact factors, G, eps^, f, E_O, string lists with e_A and U,
+// and the active two-electron block <tu||vw>.
+e2_status setup_common(e2_problem* P, const e2_inputs* in, unsigned char* ws, cudaStream_t st) {
+  const e2_desc& d = P->d;
+  const int n = P->n, nocc = P->nocc, Lt = d.L_coulomb + d.L_extra;
+  Ctx X = ctx(P, ws);
+  if (cudaMemcpyAsync(ws + P->o_plan, P->plan_blob.data(), P->plan_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return E2_ERR_CUDA;
+  (k_binom<<<1, 256, 0, st>>>((int64_t*)(ws + P->o_binom)), ++g_launches);
+  {
+    int64_t tot = (int64_t)Lt * n * nocc;
+    unsigned g = (unsigned)std::min<int64_t>(blocks(tot), 148 * 64);
+    (k_extract<<<g, 256, 0, st>>>((const double2*)in->B_c, (const double2*)in->B_x, in->w_x, in->lambda, d.L_coulomb,
+                                 d.L_extra, n, nocc, X.Bo, X.wt, X.dg), ++g_launches);
+  }
+  (k_G<<<blocks((int64_t)n * n), 256, 0, st>>>((const double2*)in->B_c, (const double2*)in->B_x, X.wt, X.dg, d.L_coulomb,
+                                              d.L_extra, n, X.G), ++g_launches);
+  (k_fock<<<blocks((int64_t)n * nocc), 256, 0, st>>>((const double2*)in->h, X.Bo, X.wt, X.dg, Lt, n, nocc, d.n_core, X.f), ++g_launches);
+  (k_scalars<<<1, 256, 0, st>>>((const double2*)in->h, X.G, n, d.n_core, X.epsh, X.EO), ++g_launches);
+  for (size_t li = 0; li < P->lists.size(); ++li) {
+    DevList L = dev_list(P, (int)li, ws);
+    if (L.n == 0) continue;
+    (k_unrank<<<blocks(L.n), 256, 0, st>>>(L, P->das, X.binom), ++g_launches);
+    (k_eA<<<blocks(L.n), 256, 0, st>>>(L, X.epsh, X.G, n, X.sp.a0), ++g_launches);
+    (k_U<<<blocks((int64_t)(P->nx + 1) * L.n), 256, 0, st>>>(L, X.sp, X.G), ++g_launches);
+  }
+  if (P->ntp > 0)
+    (k_integrals<<<blocks((int64_t)P->ntp * P->ntp), 256, 0, st>>>(INT_X00, X.sp, X.Bo, X.wt, Lt, X.f, P->ntp, P->ntp,
+                                                                  P->ntp, ws + P->o_X00), ++g_launches);
+  return E2_OK;
+}
+
+// Integral blocks and row descriptors of the external classes.
+void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
+  const e2_desc& d = P->d;
+  const int na = P->na, Lt = d.L_coulomb + d.L_extra;
+  Ctx X = ctx(P, ws);
+  const int modes[E2_NCLASS] = {-1, -1, INT_W02, -1, INT_W11, INT_W12, INT_W20, INT_W21, -1};
+  const int cols[E2_NCLASS] = {0, 0, P->ntp, 0, 1 + na * na, na, P->ntp, na, 0};
+  for (int c = 0; c < E2_NCLASS; ++c) {
+    if (modes[c] < 0 || P->M[c] == 0 || P->part_cnt[c] == 0) continue;
+    (k_rows<<<blocks(P->M[c]), 256, 0, st>>>(c, X.sp, X.epsh, X.G, P->M[c], (RowInfo*)(ws + P->o_rows[c])), ++g_launches);
+    (k_integrals<<<blocks(P->M[c] * P->Kp[c]), 256, 0, st>>>(modes[c], X.sp, X.Bo, X.wt, Lt, X.f, P->M[c], cols[c],
+                                                             P->Kp[c], ws + P->o_W[c]), ++g_launches);
+  }
+  if (P->part_cnt[8] > 0)
+    (k_integrals<<<blocks(P->ncp * P->nvp), 256, 0, st>>>(INT_G22, X.sp, X.Bo, X.wt, Lt, X.f, P->ncp, (int)P->nvp,
+                                                         (int)P->nvp, ws + P->o_G22), ++g_launches);
+  if (P->part_cnt[1] > 0)
+    (k_integrals<<<blocks((int64_t)P->nvc * na * P->ntp), 256, 0, st>>>(INT_X01, X.sp, X.Bo, X.wt, Lt, X.f, P->nvc,
+                                                                       na * P->ntp, na * P->ntp, ws + P->o_X01), ++g_launches);
+  if (P->part_cnt[3] > 0)
+    (k_integrals<<<blocks((int64_t)P->ncc * P->ntp * na), 256, 0, st>>>(INT_X10, X.sp, X.Bo, X.wt, Lt, X.f, P->ncc,
+                                                                       P->ntp * na, P->ntp * na, ws + P->o_X10), ++g_launches);
+}
 
 }  // namespace
 
@@ -447,142 +646,241 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
   if (!workspace || workspace_bytes < P->ws_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
   cudaStream_t st = (cudaStream_t)stream_;
   unsigned char* ws = (unsigned char*)workspace;
-  const e2_desc& d = P->d;
-  const int n = P->n, nocc = P->nocc, na = P->na, R = d.n_roots, Lt = d.L_coulomb + d.L_extra;
-  const double b = d.level_shift_b;
-
-  auto W = [&](size_t o) { return (void*)(ws + o); };
-  const int64_t* binom = (const int64_t*)W(P->o_binom);
-  double* G = (double*)W(P->o_G);
-  double* epsh = (double*)W(P->o_epsh);
-  double* EO = (double*)W(P->o_EO);
-  double* E0p = (double*)W(P->o_E0p);
-  double* E0d = (double*)W(P->o_E0);
-  double* dg = (double*)W(P->o_dg);
-  double* wt = (double*)W(P->o_wt);
-  double2* Bo = (double2*)W(P->o_Bo);
-  double2* f = (double2*)W(P->o_f);
-
-  DevSpace sp;
-  sp.n = n;
-  sp.n_core = d.n_core;
-  sp.n_act = na;
-  sp.n_virt = d.n_virt;
-  sp.n_occ = nocc;
-  sp.a0 = d.n_core;
-  sp.v0 = nocc;
-  sp.ncc = P->ncc;
-  sp.nvc = P->nvc;
-  sp.nx = P->nx;
-  sp.cc = (const int32_t*)W(P->o_cc);
-  sp.vc = (const int32_t*)W(P->o_vc);
-
   cudaGetLastError();
-  if (cudaMemcpyAsync(W(P->o_plan), P->plan_blob.data(), P->plan_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-    return E2_ERR_CUDA;
-  k_binom<<<1, 256, 0, st>>>((int64_t*)W(P->o_binom));
-  {
-    int64_t tot = (int64_t)Lt * n * nocc;
-    unsigned g = (unsigned)std::min<int64_t>(blocks(tot), 148 * 64);
-    k_extract<<<g, 256, 0, st>>>((const double2*)in->B_c, (const double2*)in->B_x, in->w_x, in->lambda, d.L_coulomb,
-                                 d.L_extra, n, nocc, Bo, wt, dg);
-  }
-  k_G<<<blocks((int64_t)n * n), 256, 0, st>>>((const double2*)in->B_c, (const double2*)in->B_x, wt, dg, d.L_coulomb,
-                                              d.L_extra, n, G);
-  k_fock<<<blocks((int64_t)n * nocc), 256, 0, st>>>((const double2*)in->h, Bo, wt, dg, Lt, n, nocc, d.n_core, f);
-  k_scalars<<<1, 256, 0, st>>>((const double2*)in->h, G, n, d.n_core, epsh, EO);
-  for (size_t li = 0; li < P->lists.size(); ++li) {
-    DevList L = dev_list(P, (int)li, ws);
-    if (L.n == 0) continue;
-    k_unrank<<<blocks(L.n), 256, 0, st>>>(L, P->das, binom);
-    k_eA<<<blocks(L.n), 256, 0, st>>>(L, epsh, G, n, sp.a0);
-    k_U<<<blocks((int64_t)(P->nx + 1) * L.n), 256, 0, st>>>(L, sp, G);
-  }
-  // integral blocks
-  const int modes[E2_NCLASS] = {-1, -1, INT_W02, -1, INT_W11, INT_W12, INT_W20, INT_W21, -1};
-  const int cols[E2_NCLASS] = {0, 0, P->ntp, 0, 1 + na * na, na, P->ntp, na, 0};
-  for (int c = 0; c < E2_NCLASS; ++c) {
-    if (modes[c] < 0 || P->M[c] == 0) continue;
-    k_rows<<<blocks(P->M[c]), 256, 0, st>>>(c, sp, epsh, G, P->M[c], (RowInfo*)W(P->o_rows[c]));
-    k_integrals<<<blocks(P->M[c] * P->Kp[c]), 256, 0, st>>>(modes[c], sp, Bo, wt, Lt, f, P->M[c], cols[c], P->Kp[c],
-                                                             W(P->o_W[c]));
-  }
-  if (P->part_cnt[8] > 0)
-    k_integrals<<<blocks(P->ncp * P->nvp), 256, 0, st>>>(INT_G22, sp, Bo, wt, Lt, f, P->ncp, (int)P->nvp, (int)P->nvp,
-                                                         W(P->o_G22));
-  if (P->part_cnt[1] > 0)
-    k_integrals<<<blocks((int64_t)P->nvc * na * P->ntp), 256, 0, st>>>(INT_X01, sp, Bo, wt, Lt, f, P->nvc, na * P->ntp,
-                                                                       na * P->ntp, W(P->o_X01));
-  if (P->part_cnt[3] > 0)
-    k_integrals<<<blocks((int64_t)P->ncc * P->ntp * na), 256, 0, st>>>(INT_X10, sp, Bo, wt, Lt, f, P->ncc, P->ntp * na,
-                                                                       P->ntp * na, W(P->o_X10));
-  if (P->ntp > 0)
-    k_integrals<<<blocks((int64_t)P->ntp * P->ntp), 256, 0, st>>>(INT_X00, sp, Bo, wt, Lt, f, P->ntp, P->ntp, P->ntp,
-                                                                  W(P->o_X00));
-  // per root: coupling tensors, E0, classes
+  g_launches = 0;
+  if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
+  setup_classes(P, ws, st);
+  const e2_desc& d = P->d;
+  const int na = P->na, R = d.n_roots;
+  const double b = d.level_shift_b;
+  Ctx X = ctx(P, ws);
   const DevList LP = dev_list(P, P->listP, ws);
   DevList Lc[E2_NCLASS];
   for (int c = 0; c < E2_NCLASS; ++c) Lc[c] = dev_list(P, P->list_of[c], ws);
-  double* part = (double*)W(P->o_part);
+  double* part = (double*)(ws + P->o_part);
   for (int r = 0; r < R; ++r) {
     const double2* c = (const double2*)in->c + (int64_t)r * LP.n;
-    unsigned char* dr = ws + P->d_stride * r;
-    double2* DT = (double2*)(dr + P->o_DT);
-    double2* DTD = (double2*)(dr + P->o_DTD);
-    double2* DTU = (double2*)(dr + P->o_DTU);
-    double2* DTDUD = (double2*)(dr + P->o_DTDUD);
-    double2* DTDU = (double2*)(dr + P->o_DTDU);
-    struct T {
-      int fam, cls, Kp;
-      double2* out;
-    } tabs[5] = {{FAM_T, 5, P->KpT, DT}, {FAM_TD, 7, P->KpT, DTD}, {FAM_TU, 2, P->KpTU, DTU},
-                 {FAM_TDUD, 6, P->KpTU, DTDUD}, {FAM_TDU, 4, P->Kp11, DTDU}};
-    for (const T& t : tabs) {
-      const DevList& L = Lc[t.cls];
-      if (L.n == 0) continue;
-      k_dtable<<<blocks((int64_t)t.Kp * L.n), 256, 0, st>>>(t.fam, L, LP, P->das, binom, c, t.Kp, t.out);
-    }
+    Tabs T = tables(P, ws, r);
+    build_tables(P, ws, st, c, T, true);
     double2* g1 = (double2*)(ws + P->o_g1 + P->g_stride * r);
     double2* g2 = (double2*)(ws + P->o_g2 + P->g_stride * r);
-    k_gram<<<1 + na * na, 256, 0, st>>>(DTDU, DTDU, Lc[4].n, 1 + na * na, g1);
-    if (P->ntp > 0 && Lc[2].n > 0) k_gram<<<P->ntp * P->ntp, 256, 0, st>>>(DTU, DTU, Lc[2].n, P->ntp, g2);
+    (k_gram<<<1 + na * na, 256, 0, st>>>(T.DTDU, T.DTDU, Lc[4].n, 1 + na * na, g1), ++g_launches);
+    if (P->ntp > 0 && Lc[2].n > 0) (k_gram<<<P->ntp * P->ntp, 256, 0, st>>>(T.DTU, T.DTU, Lc[2].n, P->ntp, g2), ++g_launches);
     else cudaMemsetAsync(g2, 0, 16 * (size_t)std::max(P->ntp * P->ntp, 1), st);
-    k_e0<<<1, 256, 0, st>>>(g1, g2, f, (const double2*)W(P->o_X00), sp, P->ntp, EO, E0p + r, E0d + r);
+    (k_e0<<<1, 256, 0, st>>>(g1, g2, X.f, (const double2*)(ws + P->o_X00), X.sp, P->ntp, X.EO, X.E0p + r, X.E0d + r), ++g_launches);
 
-    double* pr = part;
-    auto poff = [&](int cls) { return pr + P->part_off[r * E2_NCLASS + cls]; };
-    const double2* Dfor[E2_NCLASS] = {nullptr, nullptr, DTU, nullptr, DTDU, DT, DTDUD, DTD, nullptr};
+    auto poff = [&](int cls) { return part + P->part_off[r * E2_NCLASS + cls]; };
+    const double2* Dfor[E2_NCLASS] = {nullptr, nullptr, T.DTU, nullptr, T.DTDU, T.DT, T.DTDUD, T.DTD, nullptr};
+    auto mark = [&](int cls, int k) {
+      if (P->prof_on && r == 0) cudaEventRecord(P->prof[2 * cls + k], st);
+    };
     for (int cls : {2, 5, 7, 4, 6}) {
       if (P->part_cnt[cls] == 0) continue;
       const DevList& L = Lc[cls];
       dim3 grid((unsigned)((P->M[cls] + 63) / 64), (unsigned)((L.n + 63) / 64));
-      k_class_gemm<<<grid, 256, 0, st>>>((const double2*)W(P->o_W[cls]), Dfor[cls], P->M[cls], L.n, P->Kp[cls],
-                                         (const RowInfo*)W(P->o_rows[cls]), L.U, L.eA, E0p + r, b, poff(cls));
+      mark(cls, 0);
+      (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Dfor[cls], P->M[cls], L.n, P->Kp[cls],
+                                         (const RowInfo*)(ws + P->o_rows[cls]), L.U, L.eA, X.E0p + r, b, poff(cls)), ++g_launches);
+      mark(cls, 1);
     }
     if (P->part_cnt[8] > 0) {
       const DevList& L = Lc[8];
       dim3 grid(blocks(L.n), (unsigned)(P->nvb * (P->nvb + 1) / 2), (unsigned)P->ncp);
-      k_class22<<<grid, 256, 0, st>>>(L, sp, c, (const double*)W(P->o_G22), epsh, G, E0p + r, b, P->nvb, poff(8));
+      mark(8, 0);
+      (k_class22<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb,
+                                      poff(8)), ++g_launches);
+      mark(8, 1);
     }
     if (P->part_cnt[1] > 0) {
       dim3 grid(blocks(Lc[1].n), (unsigned)P->nvc);
-      k_class01<<<grid, 256, 0, st>>>(Lc[1], Lc[5], Lc[2], P->das, sp, binom, DT, DTU, (const double2*)W(P->o_X01), f,
-                                      epsh, E0p + r, b, poff(1));
+      mark(1, 0);
+      (k_class01<<<grid, 256, 0, st>>>(Lc[1], Lc[5], Lc[2], P->das, X.sp, X.binom, T.DT, T.DTU,
+                                      (const double2*)(ws + P->o_X01), X.f, X.epsh, X.E0p + r, b, poff(1)), ++g_launches);
+      mark(1, 1);
     }
     if (P->part_cnt[3] > 0) {
       dim3 grid(blocks(Lc[3].n), (unsigned)P->ncc);
-      k_class10<<<grid, 256, 0, st>>>(Lc[3], Lc[7], Lc[5], P->das, sp, binom, DTD, DT, (const double2*)W(P->o_X10), f,
-                                      epsh, E0p + r, b, poff(3));
+      mark(3, 0);
+      (k_class10<<<grid, 256, 0, st>>>(Lc[3], Lc[7], Lc[5], P->das, X.sp, X.binom, T.DTD, T.DT,
+                                      (const double2*)(ws + P->o_X10), X.f, X.epsh, X.E0p + r, b, poff(3)), ++g_launches);
+      mark(3, 1);
     }
-    if (P->part_cnt[0] > 0)
-      k_class00<<<blocks(Lc[0].n), 256, 0, st>>>(Lc[0], Lc[4], Lc[2], P->das, sp, binom, DTDU, DTU,
-                                                 (const double2*)W(P->o_X00), f, E0p + r, b, poff(0));
+    if (P->part_cnt[0] > 0) {
+      mark(0, 0);
+      (k_class00<<<blocks(Lc[0].n), 256, 0, st>>>(Lc[0], Lc[4], Lc[2], P->das, X.sp, X.binom, T.DTDU, T.DTU,
+                                                 (const double2*)(ws + P->o_X00), X.f, X.E0p + r, b, poff(0)), ++g_launches);
+      mark(0, 1);
+    }
   }
-  double* e2c = E2_class ? E2_class : (double*)W(P->o_e2c);
-  k_reduce<<<R * E2_NCLASS, 256, 0, st>>>(part, (const int64_t*)W(P->o_partoff), (const int64_t*)W(P->o_partcnt),
-                                          (const double2*)(ws + P->o_g1), (int)(P->g_stride / 16), R, e2c);
-  k_finalize<<<1, 32, 0, st>>>(e2c, R, E2, E0d, E0);
+  double* e2c = E2_class ? E2_class : (double*)(ws + P->o_e2c);
+  (k_reduce<<<R * E2_NCLASS, 256, 0, st>>>(part, (const int64_t*)(ws + P->o_partoff), (const int64_t*)(ws + P->o_partcnt),
+                                          (const double2*)(ws + P->o_g1), (int)(P->g_stride / 16), R, e2c), ++g_launches);
+  (k_finalize<<<1, 32, 0, st>>>(e2c, R, E2, X.E0d, E0), ++g_launches);
+  P->launches = g_launches;
   if (cudaGetLastError() != cudaSuccess) return E2_ERR_CUDA;
+  return E2_OK;
+}
+
+e2_status e2_launch_count(const e2_problem* P, int64_t* n) {
+  if (!P || !n) return E2_ERR_INVALID_ARG;
+  *n = P->launches;
+  return E2_OK;
+}
+
+e2_status e2_profile_events(e2_problem* P, void* const* events) {
+  if (!P) return E2_ERR_INVALID_ARG;
+  P->prof_on = events != nullptr;
+  if (events)
+    for (int k = 0; k < 2 * E2_NCLASS; ++k) P->prof[k] = (cudaEvent_t)events[k];
+  return E2_OK;
+}
+
+e2_status e2_fp64_peak(void* workspace, size_t workspace_bytes, void* stream_, double* dmma_tflops,
+                       double* dfma_tflops) {
+  if (!dmma_tflops || !dfma_tflops) return E2_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nb = sms * 8, nt = 256;
+  if (!workspace || workspace_bytes < sizeof(double) * nb * nt) return E2_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream_;
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return E2_ERR_CUDA;
+  double* out = (double*)workspace;
+  const int iters = 2048;
+  float ms = 0.f;
+  (k_peak_dmma<<<nb, nt, 0, st>>>(out, iters), ++g_launches);
+  cudaEventRecord(e0, st);
+  for (int k = 0; k < 3; ++k) (k_peak_dmma<<<nb, nt, 0, st>>>(out, iters), ++g_launches);
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms, e0, e1);
+  *dmma_tflops = 3.0 * (double)nb * (nt / 32) * iters * 4 * (16.0 * 8 * 8 * 2) / (ms * 1e-3) / 1e12;
+  (k_peak_dfma<<<nb, nt, 0, st>>>(out, iters), ++g_launches);
+  cudaEventRecord(e0, st);
+  for (int k = 0; k < 3; ++k) (k_peak_dfma<<<nb, nt, 0, st>>>(out, iters), ++g_launches);
+  cudaEventRecord(e1, st);
+  cudaEventSynchronize(e1);
+  cudaEventElapsedTime(&ms, e0, e1);
+  *dfma_tflops = 3.0 * (double)nb * nt * iters * 8 * 2.0 / (ms * 1e-3) / 1e12;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
+}
+
+e2_status e2_reference_workspace_size(const e2_problem* P, size_t* bytes) {
+  if (!P || !bytes) return E2_ERR_INVALID_ARG;
+  *bytes = P->solve_bytes;
+  return E2_OK;
+}
+
+e2_status e2_reference_solve(e2_problem* P, const e2_inputs* in, double tol, int max_iter, void* workspace,
+                             size_t workspace_bytes, void* stream_, double* c_out, double* E0_out, int* iters_out) {
+  if (!P || !in || !c_out || !E0_out || !in->h || !in->B_c || !in->c) return E2_ERR_INVALID_ARG;
+  if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
+  if (!(tol > 0.0) || max_iter < 1) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < P->solve_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  cudaGetLastError();
+  if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
+  const int R = P->d.n_roots, mmax = P->sv_mmax;
+  const DevList LP = dev_list(P, P->listP, ws);
+  const int64_t np = LP.n;
+  if (np < R) return E2_ERR_SHAPE;
+  Ctx X = ctx(P, ws);
+  Tabs T = tables(P, ws, 0);
+  double2* V = (double2*)(ws + P->o_sV);
+  double2* S = (double2*)(ws + P->o_sS);
+  double2* Xv = (double2*)(ws + P->o_sX);
+  double2* Rv = (double2*)(ws + P->o_sR);
+  double2* Dv = (double2*)(ws + P->o_sD);
+  double2* Tv = (double2*)(ws + P->o_sT);
+  double2* Gd = (double2*)(ws + P->o_sG);
+  double2* Yd = (double2*)(ws + P->o_sY);
+  const DevList L11 = dev_list(P, P->list_of[4], ws), L02 = dev_list(P, P->list_of[2], ws);
+  auto sigma = [&](const double2* v, double2* s) {
+    build_tables(P, ws, st, v, T, false);
+    (k_sigma<<<blocks(np), 256, 0, st>>>(LP, L11, L02, P->das, X.sp, X.binom, T.DTDU, T.DTU,
+                                        (const double2*)(ws + P->o_X00), X.f, s), ++g_launches);
+  };
+  auto gram = [&](const double2* a, int na_, const double2* bb, int nb_) {
+    std::vector<cd> out((size_t)na_ * nb_);
+    (k_gram<<<na_ * nb_, 256, 0, st>>>(a, bb, np, nb_, Gd), ++g_launches);
+    cudaMemcpyAsync(out.data(), Gd, 16 * out.size(), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    return out;
+  };
+  auto upload = [&](const std::vector<cd>& y) {
+    cudaMemcpyAsync(Yd, y.data(), 16 * y.size(), cudaMemcpyHostToDevice, st);
+  };
+  int k = 0;
+  // copy a vector into slot k, orthogonalise it twice against slots < k, normalise, and build its sigma
+  auto append = [&](const double2* src) -> bool {
+    double2* vk = V + (int64_t)k * np;
+    if (src != vk) cudaMemcpyAsync(vk, src, 16 * (size_t)np, cudaMemcpyDeviceToDevice, st);
+    for (int pass = 0; pass < 2 && k > 0; ++pass) {
+      std::vector<cd> ov = gram(V, k, vk, 1);
+      for (auto& z : ov) z = -z;
+      upload(ov);
+      (k_lincomb<<<dim3(blocks(np), 1), 256, 0, st>>>(V, k, np, (const double2*)Yd, 1, 1, vk), ++g_launches);
+    }
+    double nrm = gram(vk, 1, vk, 1)[0].real();
+    if (!(nrm > 1e-24)) return false;
+    (k_scale<<<blocks(np), 256, 0, st>>>(vk, np, 1.0 / std::sqrt(nrm)), ++g_launches);
+    sigma(vk, S + (int64_t)k * np);
+    ++k;
+    return true;
+  };
+  for (int j = 0; j < R; ++j)
+    if (!append((const double2*)in->c + (int64_t)j * np)) return E2_ERR_SHAPE;
+  std::vector<double> w;
+  std::vector<cd> Y;
+  int it = 0;
+  for (; it < max_iter; ++it) {
+    std::vector<cd> H = gram(V, k, S, k);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j <= i; ++j) {
+        cd a = 0.5 * (H[(size_t)i * k + j] + std::conj(H[(size_t)j * k + i]));
+        H[(size_t)i * k + j] = a;
+        H[(size_t)j * k + i] = std::conj(a);
+      }
+    herm_eig(k, H, w, Y);
+    std::vector<cd> Yr((size_t)k * R);
+    for (int i = 0; i < k; ++i)
+      for (int j = 0; j < R; ++j) Yr[(size_t)i * R + j] = Y[(size_t)i * k + j];
+    upload(Yr);
+    (k_lincomb<<<dim3(blocks(np), R), 256, 0, st>>>(V, k, np, (const double2*)Yd, R, 0, Xv), ++g_launches);
+    (k_lincomb<<<dim3(blocks(np), R), 256, 0, st>>>(S, k, np, (const double2*)Yd, R, 0, Rv), ++g_launches);
+    for (int j = 0; j < R; ++j)
+      (k_residual<<<blocks(np), 256, 0, st>>>(Rv + (int64_t)j * np, Xv + (int64_t)j * np, LP.eA, np, w[j],
+                                             Dv + (int64_t)j * np), ++g_launches);
+    std::vector<cd> rn = gram(Rv, R, Rv, R);
+    bool done = true;
+    std::vector<int> open;
+    for (int j = 0; j < R; ++j)
+      if (std::sqrt(std::max(0.0, rn[(size_t)j * R + j].real())) >= tol) {
+        done = false;
+        open.push_back(j);
+      }
+    if (done) break;
+    if (k + (int)open.size() > mmax) {  // restart from the Ritz vectors
+      (k_lincomb<<<dim3(blocks(np), R), 256, 0, st>>>(S, k, np, (const double2*)Yd, R, 0, Tv), ++g_launches);
+      cudaMemcpyAsync(V, Xv, 16 * (size_t)R * np, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(S, Tv, 16 * (size_t)R * np, cudaMemcpyDeviceToDevice, st);
+      k = R;
+    }
+    int added = 0;
+    for (int j : open)
+      if (k < mmax && append(Dv + (int64_t)j * np)) ++added;
+    if (added == 0) break;
+  }
+  cudaMemcpyAsync(c_out, Xv, 16 * (size_t)R * np, cudaMemcpyDeviceToDevice, st);
+  double EOh = 0.0;
+  cudaMemcpyAsync(&EOh, X.EO, sizeof(double), cudaMemcpyDeviceToHost, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return E2_ERR_CUDA;
+  for (int j = 0; j < R; ++j) E0_out[j] = w[j] + EOh;
+  if (iters_out) *iters_out = it;
   return E2_OK;
 }
 

@@ -795,50 +795,138 @@ __global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, Dev
   if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
 
-// (0,0), DAS only: V[A] = sum_{tu} f_tu D^{t+u}_A + sum_{t<u in A} s(A;t,u) sum_{v<w} <tu||vw> D^{vw}_{A-t-u}
+// <A| H - E_O |Psi> for an n_elec-electron string A with no core hole or
+// virtual particle: sum_{tu} f_tu D^{t+u}_A + sum_{t<u in A} s(A;t,u)
+// sum_{v<w} <tu||vw> D^{vw}_{A-t-u}.  Class (0,0) evaluates it on strings of
+// non-reference patterns; the reference solver evaluates it on P (sigma = H c).
+__device__ double2 active_sigma(uint64_t A, const DevList& L11, const DevList& L02, const DevDas& das,
+                                const DevSpace& sp, const int64_t* __restrict__ binom, const double2* __restrict__ DTDU,
+                                const double2* __restrict__ DTU, const double2* __restrict__ X00,
+                                const double2* __restrict__ f) {
+  const int na = sp.n_act, ntp = (int)pairs(na);
+  double2 V = make_double2(0.0, 0.0);
+  int64_t a11 = list_addr(L11, das, binom, A);
+  if (a11 >= 0)
+    for (int t = 0; t < na; ++t)
+      for (int u = 0; u < na; ++u)
+        V = cfma(f[(int64_t)(sp.a0 + t) * sp.n_occ + sp.a0 + u], DTDU[(int64_t)(1 + t * na + u) * L11.n + a11], V);
+  for (uint64_t xu = A; xu; xu &= xu - 1) {
+    const int u = __ffsll((long long)xu) - 1;
+    for (uint64_t xt = A & ((1ull << u) - 1); xt; xt &= xt - 1) {
+      const int t = __ffsll((long long)xt) - 1;
+      const uint64_t B = A & ~(1ull << t) & ~(1ull << u);
+      const int64_t a02 = list_addr(L02, das, binom, B);
+      if (a02 < 0) continue;
+      const double2* Xr = X00 + (int64_t)pair_index(t, u) * ntp;
+      double2 s = make_double2(0.0, 0.0);
+      for (int w = 1; w < na; ++w) {
+        if ((B >> w) & 1) continue;
+        for (int v = 0; v < w; ++v) {
+          if ((B >> v) & 1) continue;
+          const int vw = pair_index(v, w);
+          s = cfma(Xr[vw], DTU[(int64_t)vw * L02.n + a02], s);
+        }
+      }
+      if ((popc_below(B, u) + popc_below(B, t)) & 1) s = make_double2(-s.x, -s.y);
+      V.x += s.x;
+      V.y += s.y;
+    }
+  }
+  return V;
+}
+
+// (0,0), DAS only: V[A] = <A|H - E_O|Psi> for A of a non-reference pattern
 __global__ void k_class00(DevList L00, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
                           const double2* __restrict__ DTDU /*[Kp][n11]*/, const double2* __restrict__ DTU /*[Kp][n02]*/,
                           const double2* __restrict__ X00, const double2* __restrict__ f, const double* __restrict__ E0p,
                           double b, double* __restrict__ partial) {
   __shared__ double sh[32];
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int na = sp.n_act, ntp = (int)pairs(na);
   double acc = 0.0;
   if (g < L00.n) {
-    const uint64_t A = L00.str[g];
-    double2 V = make_double2(0.0, 0.0);
-    int64_t a11 = list_addr(L11, das, binom, A);
-    if (a11 >= 0)
-      for (int t = 0; t < na; ++t)
-        for (int u = 0; u < na; ++u)
-          V = cfma(f[(int64_t)(sp.a0 + t) * sp.n_occ + sp.a0 + u], DTDU[(int64_t)(1 + t * na + u) * L11.n + a11], V);
-    for (uint64_t xu = A; xu; xu &= xu - 1) {
-      const int u = __ffsll((long long)xu) - 1;
-      for (uint64_t xt = A & ((1ull << u) - 1); xt; xt &= xt - 1) {
-        const int t = __ffsll((long long)xt) - 1;
-        const uint64_t B = A & ~(1ull << t) & ~(1ull << u);
-        const int64_t a02 = list_addr(L02, das, binom, B);
-        if (a02 < 0) continue;
-        const double2* Xr = X00 + (int64_t)pair_index(t, u) * ntp;
-        double2 s = make_double2(0.0, 0.0);
-        for (int w = 1; w < na; ++w) {
-          if ((B >> w) & 1) continue;
-          for (int v = 0; v < w; ++v) {
-            if ((B >> v) & 1) continue;
-            const int vw = pair_index(v, w);
-            s = cfma(Xr[vw], DTU[(int64_t)vw * L02.n + a02], s);
-          }
-        }
-        if ((popc_below(B, u) + popc_below(B, t)) & 1) s = make_double2(-s.x, -s.y);
-        V.x += s.x;
-        V.y += s.y;
-      }
-    }
+    const double2 V = active_sigma(L00.str[g], L11, L02, das, sp, binom, DTDU, DTU, X00, f);
     const double Dk = *E0p - L00.eA[g];
     acc = en_term(V.x * V.x + V.y * V.y, Dk, b);
   }
   double tot = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+}
+
+// ------------------------------------------------------------------ reference solver
+
+// sigma[g] = <A_g| H - E_O |c> for every reference string (P address order)
+__global__ void k_sigma(DevList LP, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
+                        const double2* __restrict__ DTDU, const double2* __restrict__ DTU, const double2* __restrict__ X00,
+                        const double2* __restrict__ f, double2* __restrict__ sigma) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= LP.n) return;
+  sigma[g] = active_sigma(LP.str[g], L11, L02, das, sp, binom, DTDU, DTU, X00, f);
+}
+
+// out[j][A] = (acc ? out[j][A] : 0) + sum_i Y[i*k + j] V[i][A]
+__global__ void k_lincomb(const double2* __restrict__ V, int m, int64_t n, const double2* __restrict__ Y, int k, int acc,
+                          double2* __restrict__ out) {
+  const int64_t A = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (A >= n) return;
+  double2 s = acc ? out[(int64_t)j * n + A] : make_double2(0.0, 0.0);
+  for (int i = 0; i < m; ++i) s = cfma(Y[i * k + j], V[(int64_t)i * n + A], s);
+  out[(int64_t)j * n + A] = s;
+}
+
+// r <- r - theta x ; then d = r / (theta - diag), |theta - diag| floored at 1e-4
+__global__ void k_residual(double2* __restrict__ r, const double2* __restrict__ x, const double* __restrict__ diag,
+                           int64_t n, double theta, double2* __restrict__ d) {
+  const int64_t A = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (A >= n) return;
+  double2 v = r[A], xv = x[A];
+  v.x -= theta * xv.x;
+  v.y -= theta * xv.y;
+  r[A] = v;
+  double den = theta - diag[A];
+  if (fabs(den) < 1e-4) den = den < 0 ? -1e-4 : 1e-4;
+  d[A] = make_double2(v.x / den, v.y / den);
+}
+
+__global__ void k_scale(double2* __restrict__ x, int64_t n, double s) {
+  const int64_t A = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (A < n) x[A] = make_double2(x[A].x * s, x[A].y * s);
+}
+
+// ------------------------------------------------------------------ FP64 peaks
+
+// Independent mma.sync m16n8k8 f64 chains (4 per warp), iters steps each.
+__global__ void k_peak_dmma(double* out, int iters) {
+  double a[4], bb[2], c[4][4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) a[j] = 1e-3 * (threadIdx.x + j);
+  bb[0] = 0.5;
+  bb[1] = 0.25;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) c[j][e] = 0.0;
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) mma_f64(c[j], a, bb);
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) s += c[j][0] + c[j][1] + c[j][2] + c[j][3];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+// Eight independent FP64 FMA chains per thread, iters steps each.
+__global__ void k_peak_dfma(double* out, int iters) {
+  double x[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) x[j] = 1e-3 * (threadIdx.x + j);
+  for (int i = 0; i < iters; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) x[j] = fma(x[j], 0.999, 1e-3);
+  double s = 0.0;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) s += x[j];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
 }
 
 // ------------------------------------------------------------------ reductions

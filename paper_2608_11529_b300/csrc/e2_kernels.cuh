@@ -36,6 +36,13 @@ __global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, Dev
 __global__ void k_class00(DevList L00, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* binom,
                           const double2* DTDU, const double2* DTU, const double2* X00, const double2* f,
                           const double* E0p, double b, double* partial);
+__global__ void k_sigma(DevList LP, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* binom,
+                        const double2* DTDU, const double2* DTU, const double2* X00, const double2* f, double2* sigma);
+__global__ void k_lincomb(const double2* V, int m, int64_t n, const double2* Y, int k, int acc, double2* out);
+__global__ void k_residual(double2* r, const double2* x, const double* diag, int64_t n, double theta, double2* d);
+__global__ void k_scale(double2* x, int64_t n, double s);
+__global__ void k_peak_dmma(double* out, int iters);
+__global__ void k_peak_dfma(double* out, int iters);
 __global__ void k_reduce(const double* partial, const int64_t* off, const int64_t* cnt, const double2* g1_all,
                          int g1_stride, int n_roots, double* e2c);
 __global__ void k_finalize(const double* e2c, int n_roots, double* E2, const double* E0in, double* E0out);

@@ -93,3 +93,24 @@ def test_breit_multiplier_lambda_zero_is_dirac_coulomb():
     e_dc = o.e2()[1]
     _, gc, _, _ = _gpu_e2(prob, c, lam=0.0)
     np.testing.assert_allclose(gc, e_dc, rtol=0, atol=TOL_E2)
+
+
+@pytest.mark.parametrize("case", [
+    dict(n_core=4, n_act=12, n_virt=12, n_elec=6, Lc=6, Lx=3, ham="DCG", x_scale=0.05, n_roots=2, seed=31),
+    dict(n_core=4, n_act=12, n_virt=10, n_elec=6, Lc=5, das_size=[4, 4, 4], das_min=[2, 0, 0], das_max=[4, 4, 2],
+         seed=32),
+])
+def test_reference_solver_matches_oracle(case):
+    """Device Davidson eigenpairs of P H P against the oracle's dense solve, and
+    E2 from each side's own reference state (phase-independent)."""
+    import paper_2608_11529_b300 as e2
+    prob = tiny_problem(**case)
+    c_o, E0_o, e2_o, ec_o = _oracle(prob)
+    plan = e2.E2Problem.from_problem(prob)
+    t = e2.device_inputs(prob, prob.X0)
+    c_g, E0_g, iters = plan.reference_solve(t["h"], t["B_c"], t["c"], t["B_x"], t["w_x"], lam=t["lam"], tol=1e-11)
+    np.testing.assert_allclose(E0_g, E0_o, rtol=0, atol=1e-9)
+    t["c"] = c_g
+    E2, E2c, E0 = plan.forward(**t)
+    np.testing.assert_allclose(E0.cpu().numpy(), E0_o, rtol=0, atol=1e-9)
+    np.testing.assert_allclose(E2c.cpu().numpy(), ec_o, rtol=0, atol=1e-8)
