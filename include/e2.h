@@ -173,6 +173,27 @@ E2_API e2_status e2_launch_count(const e2_problem* prob, int64_t* n);
 E2_API e2_status e2_fp64_peak(void* workspace, size_t workspace_bytes, void* stream, double* dmma_tflops,
                               double* dfma_tflops);
 
+/* Allocation-free variant of e2_forward (no counterpart in the paper).
+ * Some callers cannot call cudaMalloc: code that enqueues work while a CUDA
+ * graph is being captured, plugins living inside a host program that owns
+ * the device allocator, and embedded runtimes that forbid allocation after
+ * start-up.  This entry point runs exactly the computation of e2_forward, but
+ * in a scratch array compiled into the library, E2_STATIC_SCRATCH_BYTES per
+ * device, which every device that loads the library holds until the process
+ * exits.  It allocates nothing and takes no workspace argument; inputs and
+ * outputs are the caller's, as for e2_forward.
+ *   - A problem whose e2_workspace_size() exceeds E2_STATIC_SCRATCH_BYTES is
+ *     rejected with E2_ERR_WORKSPACE before any GPU work.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls, on every problem, share the one array and leave the last
+ *     call's contents in it: calls whose GPU work can overlap (other streams,
+ *     other host threads) overwrite each other's scratch and give wrong
+ *     results; serialise them on one stream. */
+#define E2_STATIC_SCRATCH_BYTES (32u << 20)
+E2_API e2_status e2_forward_noalloc(e2_problem* prob, const e2_inputs* in, void* stream, double* E2,
+                                    double* E2_class, double* E0);
+
 E2_API const char* e2_status_string(e2_status s);
 
 #ifdef __cplusplus

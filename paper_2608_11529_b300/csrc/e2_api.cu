@@ -7,6 +7,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -885,3 +886,38 @@ e2_status e2_reference_solve(e2_problem* P, const e2_inputs* in, double tol, int
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ fixed scratch variant
+
+// Scratch for e2_forward_noalloc, compiled into the library: every device
+// that loads it holds these bytes until the process exits.  Nothing in the
+// forward layout needs to start at zero (every buffer is fully written before
+// it is read), so calls do not clear it; consecutive calls simply overwrite it.
+static __device__ __align__(256) unsigned char e2_static_scratch[E2_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_scratch_mu;
+void* g_scratch_ptr[128] = {};  // device address of e2_static_scratch, per device ordinal
+}  // namespace
+
+extern "C" e2_status e2_forward_noalloc(e2_problem* P, const e2_inputs* in, void* stream, double* E2,
+                                        double* E2_class, double* E0) {
+  if (!P) return E2_ERR_INVALID_ARG;
+  if (P->ws_bytes > (size_t)E2_STATIC_SCRATCH_BYTES) return E2_ERR_WORKSPACE;  // before any GPU call
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return E2_ERR_CUDA;
+  void* ptr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_ptr[dev]) {
+      // once per device, with that device current: the host-side symbol is only
+      // a stand-in, the kernels need the array's device address
+      if (cudaGetSymbolAddress(&g_scratch_ptr[dev], e2_static_scratch) != cudaSuccess) {
+        g_scratch_ptr[dev] = nullptr;
+        return E2_ERR_CUDA;
+      }
+    }
+    ptr = g_scratch_ptr[dev];
+  }
+  return e2_forward(P, in, ptr, (size_t)E2_STATIC_SCRATCH_BYTES, stream, E2, E2_class, E0);
+}
