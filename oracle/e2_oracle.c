@@ -726,3 +726,243 @@ void oracle_eri(void* vp, int p, int q, int r, int s, double* out) {
   out[0] = creal(v);
   out[1] = cimag(v);
 }
+
+/* ---------------- gradient ----------------
+ *
+ * d(sum_m s_m E2_m) with respect to h, every factor B^L, the factor weights
+ * w_L and the reference coefficients c, by explicit accumulation over the
+ * same Q H P rows.  With v_K = |V_K|^2/n, D_K = E0 - H_KK, the term
+ * f(v, D) = v/D (or v D^3/(D^4+b^2) with the level shift), g_K = df/dv,
+ * h_K = df/dD, n = <c|c>:
+ *   dE2 = (2/n) Re sum_K g_K conj(V_K) <K|dH|c> + (sum_K h_K / n) <c|dH|c>
+ *         - sum_K h_K <K|dH|K>                                   (H part)
+ *   cbar = (2/n) H_PQ (g V) - (2/n^2)(sum_K g_K |V_K|^2) c
+ *          + (2/n)(sum_K h_K)(H_PP - E0) c                       (c part)
+ * Every matrix element <X|H|Y> met with coefficient k adds Re(k d<X|H|Y>):
+ * its h entries and chemists' integrals (pq|rs) = sum_L w_L B^L_pq B^L_rs
+ * receive k (times the Slater-Condon sign).  For a complex input z the
+ * returned gradient is dE/dRe z + i dE/dIm z, projected on Hermitian
+ * matrices for h and each B^L (dE = Re sum conj(grad) dz for Hermitian dz).
+ */
+typedef struct {
+  cplx* gh;  /* coefficient of dh_pq: dE = Re sum gh_pq dh_pq */
+  cplx* gB;  /* coefficient of dB^L_pq */
+  double* gw;
+} gacc_t;
+
+static void acc_eri(const oracle_t* P, gacc_t* G, int p, int q, int r, int s, cplx k) {
+  const size_t nn = (size_t)P->n * P->n;
+  for (int l = 0; l < P->L; ++l) {
+    cplx bpq = P->B[l * nn + (size_t)p * P->n + q], brs = P->B[l * nn + (size_t)r * P->n + s];
+    G->gB[l * nn + (size_t)p * P->n + q] += k * P->w[l] * brs;
+    G->gB[l * nn + (size_t)r * P->n + s] += k * P->w[l] * bpq;
+    G->gw[l] += creal(k * bpq * brs);
+  }
+}
+
+/* <pq||rs> = (pr|qs) - (ps|qr) */
+static void acc_asym(const oracle_t* P, gacc_t* G, int p, int q, int r, int s, cplx k) {
+  acc_eri(P, G, p, r, q, s, k);
+  acc_eri(P, G, p, s, q, r, -k);
+}
+
+/* Re(k d<X|H|Y>) into G, following hmat() term by term */
+static void acc_elem(const oracle_t* P, gacc_t* G, const det_t* X, const det_t* Y, cplx k) {
+  int pk[3], ql[3], np = 0, nq = 0;
+  for (int w = 0; w < MAXW; ++w) {
+    uint64_t a = X->w[w] & ~Y->w[w], b = Y->w[w] & ~X->w[w];
+    while (a) {
+      int bit = __builtin_ctzll(a);
+      a &= a - 1;
+      if (np < 3) pk[np] = 64 * w + bit;
+      ++np;
+    }
+    while (b) {
+      int bit = __builtin_ctzll(b);
+      b &= b - 1;
+      if (nq < 3) ql[nq] = 64 * w + bit;
+      ++nq;
+    }
+  }
+  if (np != nq || np > 2) return;
+  if (np == 0) {
+    int occ[1280], no = 0;
+    for (int p = 0; p < P->n; ++p)
+      if (det_get(X, p)) occ[no++] = p;
+    for (int i = 0; i < no; ++i) G->gh[(size_t)occ[i] * P->n + occ[i]] += k;
+    for (int i = 0; i < no; ++i)
+      for (int j = i + 1; j < no; ++j) acc_asym(P, G, occ[i], occ[j], occ[i], occ[j], k);
+    return;
+  }
+  if (np == 1) {
+    int p = pk[0], q = ql[0], sign = 1;
+    det_t t = *Y;
+    apply_ann(&t, q, &sign);
+    apply_cre(&t, p, &sign);
+    cplx ks = k * (double)sign;
+    G->gh[(size_t)p * P->n + q] += ks;
+    for (int r = 0; r < P->n; ++r)
+      if (det_get(&t, r) && r != p) acc_asym(P, G, p, r, q, r, ks);
+    return;
+  }
+  int sign = 1;
+  det_t t = *Y;
+  apply_ann(&t, ql[0], &sign);
+  apply_ann(&t, ql[1], &sign);
+  apply_cre(&t, pk[1], &sign);
+  apply_cre(&t, pk[0], &sign);
+  acc_asym(P, G, pk[0], pk[1], ql[0], ql[1], k * (double)sign);
+}
+
+/* df/dv and df/dD of the Epstein-Nesbet term */
+static void en_derivs(double v2, double D, double b, double* gv, double* hD) {
+  if (b == 0.0) {
+    *gv = 1.0 / D;
+    *hD = -v2 / (D * D);
+    return;
+  }
+  double D2 = D * D, den = D2 * D2 + b * b;
+  *gv = D * D2 / den;
+  *hD = v2 * D2 * (3.0 * b * b - D2 * D2) / (den * den);
+}
+
+typedef struct {
+  const oracle_t* P;
+  const det_t* K;
+  cplx coefK;      /* (2/n) s g conj(V) summed over roots is root dependent: kept per root below */
+  const cplx* kq;  /* [R] (2/n_m) s_m g_K conj(V_K,m) */
+  const cplx* kc;  /* [R] (2/n_m) s_m g_K V_K,m  (for cbar) */
+  gacc_t* G;
+  cplx* gc;        /* [R][np] */
+} gctx;
+
+static void grad_visit_q(void* vc, int64_t addr, cplx hkl) {
+  gctx* x = (gctx*)vc;
+  const oracle_t* P = x->P;
+  int64_t np = oracle_np((void*)P);
+  cplx k = 0;
+  for (int m = 0; m < P->n_roots; ++m) {
+    k += x->kq[m] * P->c[m * np + addr];
+    x->gc[m * np + addr] += x->kc[m] * conj(hkl);
+  }
+  det_t Ld;
+  make_det(P, &Ld, NULL, 0, P->pstr[addr], NULL, 0);
+  acc_elem(P, x->G, x->K, &Ld, k);
+}
+
+typedef struct {
+  const oracle_t* P;
+  const det_t* Lrow;
+  int64_t arow;
+  const double* kp;  /* [R] s_m sum_h_m / n_m */
+  gacc_t* G;
+  cplx* hc;          /* [R][np] (H_PP c) accumulation */
+} pctx;
+
+static void grad_visit_p(void* vc, int64_t addr, cplx hkl) {
+  pctx* x = (pctx*)vc;
+  const oracle_t* P = x->P;
+  int64_t np = oracle_np((void*)P);
+  cplx k = 0;
+  for (int m = 0; m < P->n_roots; ++m) {
+    k += x->kp[m] * conj(P->c[m * np + x->arow]) * P->c[m * np + addr];
+    x->hc[m * np + x->arow] += hkl * P->c[m * np + addr];
+  }
+  det_t Ld;
+  make_det(P, &Ld, NULL, 0, P->pstr[addr], NULL, 0);
+  acc_elem(P, x->G, x->Lrow, &Ld, k);
+}
+
+/* Gradient of sum_m seed[m] E2_m.  Outputs, complex interleaved unless noted:
+   gh [n][n], gB [L][n][n] (factor order of the descriptor), gw [L] (real),
+   gc [n_roots][np].  E0 must be the reference energies of c. */
+int oracle_grad(void* vp, const double* E0, const double* seed, double* gh_out, double* gB_out, double* gw_out,
+                double* gc_out) {
+  oracle_t* P = (oracle_t*)vp;
+  const int R = P->n_roots, n = P->n;
+  const int64_t np = oracle_np(P);
+  const size_t nn = (size_t)n * n;
+  double norm[64];
+  for (int m = 0; m < R; ++m) norm[m] = c_norm(P, m);
+  gacc_t G;
+  G.gh = (cplx*)calloc(nn, sizeof(cplx));
+  G.gB = (cplx*)calloc(nn * (P->L > 0 ? P->L : 1), sizeof(cplx));
+  G.gw = (double*)calloc(P->L > 0 ? P->L : 1, sizeof(double));
+  cplx* gc = (cplx*)calloc((size_t)R * np, sizeof(cplx));
+  cplx* hc = (cplx*)calloc((size_t)R * np, sizeof(cplx));
+  double sum_h[64] = {0}, sum_gv[64] = {0};
+  /* Q part (serial: the accumulation targets are shared) */
+  for (int h = 0; h <= 2; ++h)
+    for (int p = 0; p <= 2; ++p) {
+      int ne = P->n_elec + h - p;
+      if (ne < 0 || ne > P->n_act) continue;
+      int64_t nI = binom(P->ncc, h), nS = binom(P->nvc, p);
+      for (int64_t item = 0; item < nI * nS; ++item) {
+        int holes[2], parts[2];
+        subset_of(P->corr_core, P->ncc, h, item / nS, holes);
+        subset_of(P->corr_virt, P->nvc, p, item % nS, parts);
+        FOR_STRINGS(A, P->n_act, ne) {
+          det_t K;
+          make_det(P, &K, holes, h, A, parts, p);
+          if (h == 0 && p == 0 && p_address_active(P, A) >= 0) continue;
+          cplx V[64] = {0};
+          vctx x = {P, V, 0};
+          for_connected(P, &K, h, A, acc_v, &x);
+          if (!x.hit) continue;
+          double hkk = hdiag(P, &K);
+          cplx kq[64], kc[64];
+          double kdiag = 0.0;
+          for (int m = 0; m < R; ++m) {
+            double v2 = (creal(V[m]) * creal(V[m]) + cimag(V[m]) * cimag(V[m])) / norm[m];
+            double gv, hD;
+            en_derivs(v2, E0[m] - hkk, P->b, &gv, &hD);
+            sum_h[m] += hD;
+            sum_gv[m] += gv * v2 * norm[m];
+            kq[m] = (2.0 / norm[m]) * seed[m] * gv * conj(V[m]);
+            kc[m] = (2.0 / norm[m]) * seed[m] * gv * V[m];
+            kdiag += -seed[m] * hD;
+          }
+          gctx gx = {P, &K, 0, kq, kc, &G, gc};
+          for_connected(P, &K, h, A, grad_visit_q, &gx);
+          acc_elem(P, &G, &K, &K, kdiag);
+        }
+      }
+    }
+  /* P part: (sum_h / n) <c|dH|c>, and (H_PP c) for cbar */
+  double kp[64];
+  for (int m = 0; m < R; ++m) kp[m] = seed[m] * sum_h[m] / norm[m];
+  for (int64_t a = 0; a < np; ++a) {
+    det_t Ld;
+    make_det(P, &Ld, NULL, 0, P->pstr[a], NULL, 0);
+    pctx px = {P, &Ld, a, kp, &G, hc};
+    for_connected(P, &Ld, 0, P->pstr[a], grad_visit_p, &px);
+  }
+  for (int m = 0; m < R; ++m)
+    for (int64_t a = 0; a < np; ++a) {
+      cplx cv = P->c[m * np + a];
+      gc[m * np + a] += -(2.0 / (norm[m] * norm[m])) * seed[m] * sum_gv[m] * cv +
+                        (2.0 / norm[m]) * seed[m] * sum_h[m] * (hc[m * np + a] - E0[m] * cv);
+    }
+  /* gradient = conj(coefficient), Hermitian projection for h and each B^L */
+  for (int p = 0; p < n; ++p)
+    for (int q = 0; q < n; ++q) {
+      cplx v = 0.5 * (conj(G.gh[(size_t)p * n + q]) + G.gh[(size_t)q * n + p]);
+      gh_out[2 * ((size_t)p * n + q)] = creal(v);
+      gh_out[2 * ((size_t)p * n + q) + 1] = cimag(v);
+    }
+  for (int l = 0; l < P->L; ++l)
+    for (int p = 0; p < n; ++p)
+      for (int q = 0; q < n; ++q) {
+        cplx v = 0.5 * (conj(G.gB[l * nn + (size_t)p * n + q]) + G.gB[l * nn + (size_t)q * n + p]);
+        gB_out[2 * (l * nn + (size_t)p * n + q)] = creal(v);
+        gB_out[2 * (l * nn + (size_t)p * n + q) + 1] = cimag(v);
+      }
+  for (int l = 0; l < P->L; ++l) gw_out[l] = G.gw[l];
+  memcpy(gc_out, gc, sizeof(cplx) * R * np);
+  free(G.gh);
+  free(G.gB);
+  free(G.gw);
+  free(gc);
+  free(hc);
+  return 0;
+}

@@ -76,6 +76,7 @@ def _load():
         L.oracle_hmat.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.oracle_maxw.restype = C.c_int
         L.oracle_eri.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
+        L.oracle_grad.argtypes = [C.c_void_p] + [C.c_void_p] * 6
         _lib = L
     return _lib
 
@@ -193,6 +194,22 @@ class Oracle:
         self._L.oracle_couplings(self._h_ptr, _ptr(E0), nK, _ptr(nh), _ptr(holes), _ptr(npart), _ptr(parts),
                                  _ptr(act), _ptr(V), _ptr(D))
         return V, D
+
+    def grad(self, E0=None, seed=None):
+        """Gradient of sum_m seed[m] E2_m: returns (gh [n,n], gB [L,n,n] in the
+        factor order of Problem.factors(), gw [L], gc [roots, N_P]); complex
+        gradients are dE/dRe + i dE/dIm, Hermitian-projected for h and B."""
+        if E0 is None:
+            E0 = self.e0()
+        E0 = np.ascontiguousarray(E0, np.float64)
+        seed = np.ascontiguousarray(np.ones(self.n_roots) if seed is None else seed, np.float64)
+        n, L = self.prob.n, self._B.shape[0]
+        gh = np.zeros((n, n), np.complex128)
+        gB = np.zeros((L, n, n), np.complex128)
+        gw = np.zeros(L)
+        gc = np.zeros((self.n_roots, self.n_p), np.complex128)
+        self._L.oracle_grad(self._h_ptr, _ptr(E0), _ptr(seed), _ptr(gh), _ptr(gB), _ptr(gw), _ptr(gc))
+        return gh, gB, gw, gc
 
     def count_q(self):
         out = np.zeros(NCLASS)

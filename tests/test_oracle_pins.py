@@ -292,3 +292,67 @@ def test_e2_is_invariant_to_the_scale_of_c():
     e_ref = o.e2()[1]
     o.set_c(3.7 * c)
     np.testing.assert_allclose(o.e2()[1], e_ref, rtol=1e-12, atol=1e-18)
+
+
+# ---------------------------------------------------------------- gradient
+
+def _fd4(f, d):
+    return (-f(2 * d) + 8 * f(d) - 8 * f(-d) + f(-2 * d)) / (12 * d)
+
+
+def _herm(rng, n):
+    x = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    return (x + x.conj().T) / 2
+
+
+@pytest.mark.parametrize("b", [0.0, 0.05])
+def test_gradient_matches_central_differences(b):
+    """dE2 along random Hermitian directions of h and of a Coulomb and a Breit
+    factor, a complex direction of c (unnormalised, two roots with seeds),
+    and the Breit multiplier lambda: 4th-order central differences, relative
+    error <= 1e-7.  <c_m|cbar_m> = 0 (E2 is invariant to the scale and phase of c)."""
+    import copy
+    p = tiny_problem(4, 6, 6, 3, Lc=4, Lx=3, ham="DCB", x_scale=0.05, n_roots=2, seed=41, n_frozen_core=2,
+                     level_shift_b=b)
+    o, c, _ = _ground(p, 2)
+    c = c * np.array([[1.3], [0.8j]])
+    o.set_c(c)
+    seed = np.array([1.0, 0.7])
+    gh, gB, gw, gc = o.grad(seed=seed)
+    rng = np.random.default_rng(5)
+
+    def e2(q, cc):
+        oo = Oracle(q)
+        oo.set_c(cc)
+        return seed @ oo.e2()[0]
+
+    def check(fd, an):
+        assert abs(fd - an) <= 1e-7 * max(abs(an), 1e-3), (fd, an)
+
+    dh = _herm(rng, p.n)
+    def fh(t):
+        q = copy.deepcopy(p)
+        q.h = p.h + t * dh
+        return e2(q, c)
+    check(_fd4(fh, 1e-4), np.real(np.vdot(gh, dh)))
+    for which, idx in (("c", 1), ("x", p.Bc.shape[0])):
+        dB = _herm(rng, p.n)
+        def fB(t):
+            q = copy.deepcopy(p)
+            if which == "c":
+                q.Bc = p.Bc.copy()
+                q.Bc[1] = p.Bc[1] + t * dB
+            else:
+                q.Bx = p.Bx.copy()
+                q.Bx[0] = p.Bx[0] + t * dB
+            return e2(q, c)
+        check(_fd4(fB, 1e-4), np.real(np.vdot(gB[idx], dB)))
+    dc = rng.standard_normal(c.shape) + 1j * rng.standard_normal(c.shape)
+    check(_fd4(lambda t: e2(p, c + t * dc), 1e-4), np.real(np.vdot(gc, dc)))
+    for m in range(2):
+        assert abs(np.vdot(c[m], gc[m])) < 1e-13
+    def fl(t):
+        q = copy.deepcopy(p)
+        q.lam = p.lam + t
+        return e2(q, c)
+    check(_fd4(fl, 1e-3), np.dot(p.wx, gw[p.Bc.shape[0]:]))
