@@ -259,13 +259,16 @@ def run(args):
     ktime = {k: sum(evs[s][k][0].elapsed_time(evs[s][k][1]) for s in range(args.steps)) / args.steps for k in present}
     dom = max(ktime, key=ktime.get)
     if dom in GEMM_CLASSES:
-        flops = 8.0 * plan.q_per_class[dom] * _kdim(prob, dom)
+        # complex products by Gauss's three real products: 6 real flops per
+        # complex multiply-add, K of them per coupling
+        flops = 6.0 * plan.q_per_class[dom] * _kdim(prob, dom)
         achieved = flops / (ktime[dom] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_dmma, "unit": "TFLOP/s",
                 "frac": achieved / peak_dmma, "traffic": _traffic("k_class_gemm"),
                 "kernel": f"k_class_gemm class {CLASS_NAMES[dom]}", "peak_source":
                 "measured on this GPU: mma.sync m16n8k8 f64 burst (e2_fp64_peak)",
-                "algorithmic_flops_per_launch": flops, "ms_per_launch": ktime[dom]}
+                "algorithmic_flops_per_launch": flops, "ms_per_launch": ktime[dom],
+                "flops_per_coupling": "6 K (3 real products per complex product, K = contraction length)"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": peak_dfma, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "kernel": KERNEL_OF_CLASS[dom]}

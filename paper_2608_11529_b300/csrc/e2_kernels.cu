@@ -532,10 +532,13 @@ __global__ void k_e0(const double2* __restrict__ g1 /*[1+na*na] row 0 = <c|c>*/,
 
 // ------------------------------------------------------------------ dense classes
 
-// V[e,A] = sum_x W[e,x] D[x,A] on the FP64 tensor pipe (mma.sync m16n8k8 f64,
-// four real products per complex product), with the Epstein-Nesbet
-// denominator and |V|^2/D reduced in the epilogue; V is never stored.
-// CTA tile 64x64, 8 warps of 32x16, K steps of 8; one partial per CTA.
+// V[e,A] = sum_x W[e,x] D[x,A] on the FP64 tensor pipe (mma.sync m16n8k8
+// f64), with the Epstein-Nesbet denominator and |V|^2/D reduced in the
+// epilogue; V is never stored.  Complex products take three real products
+// (Gauss): T1 = Wr Dr, T2 = Wi Di, T3 = (Wr + Wi)(Dr + Di), Re V = T1 - T2,
+// Im V = T3 - T1 - T2; the sums are formed once per tile in shared memory.
+// CTA tile 64x64, 8 warps of 32x16, K steps of 8 with the next step's tile
+// prefetched into registers; one partial per CTA.
 constexpr int GBM = 64, GBN = 64, GBK = 8;
 
 __device__ __forceinline__ void mma_f64(double (&c)[4], const double (&a)[4], const double (&b)[2]) {
@@ -545,64 +548,74 @@ __device__ __forceinline__ void mma_f64(double (&c)[4], const double (&a)[4], co
       : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(b[0]), "d"(b[1]));
 }
 
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 1)
 k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M, int64_t N, int Kp,
              const RowInfo* __restrict__ rows, const double* __restrict__ U,
              const double* __restrict__ eA, const double* __restrict__ E0p, double b, double* __restrict__ partial) {
-  __shared__ double2 sW[GBM][GBK + 1];
-  __shared__ double2 sD[GBK][GBN + 1];
+  __shared__ double sWr[GBM][GBK + 1], sWi[GBM][GBK + 1], sWs[GBM][GBK + 1];
+  __shared__ double sDr[GBK][GBN + 1], sDi[GBK][GBN + 1], sDs[GBK][GBN + 1];
   __shared__ double sh[32];
   // grid: x = row tiles, y = column tiles
   const int64_t m0 = (int64_t)blockIdx.x * GBM, n0 = (int64_t)blockIdx.y * GBN;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tq = lane & 3;
   const int wm = warp >> 2, wn = warp & 3;  // warp tile: rows wm*32.., cols wn*16..
-  double cr[2][2][4], ci[2][2][4];
+  double t1[2][2][4], t2[2][2][4], t3[2][2][4];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
-      for (int e = 0; e < 4; ++e) cr[a][c][e] = ci[a][c][e] = 0.0;
+      for (int e = 0; e < 4; ++e) t1[a][c][e] = t2[a][c][e] = t3[a][c][e] = 0.0;
+
+  // per thread: two W elements (rows r, r+32 of the 64x8 tile) and two D
+  // elements (k rows kr, kr+4 of the 8x64 tile)
+  const int wr_ = tid >> 3, wk = tid & 7, dk = tid >> 6, dc = tid & 63;
+  const double2 zero = make_double2(0.0, 0.0);
+  auto ldW = [&](int k0, int q) {
+    const int64_t gr = m0 + wr_ + 32 * q;
+    return (gr < M) ? W[gr * Kp + k0 + wk] : zero;
+  };
+  auto ldD = [&](int k0, int q) {
+    const int64_t gc = n0 + dc;
+    return (gc < N) ? D[(int64_t)(k0 + dk + 4 * q) * N + gc] : zero;
+  };
+  double2 pw0 = ldW(0, 0), pw1 = ldW(0, 1), pd0 = ldD(0, 0), pd1 = ldD(0, 1);
 
   for (int k0 = 0; k0 < Kp; k0 += GBK) {
-    // W tile: 64 x 8, D tile: 8 x 64 complex; 256 threads x 2 each
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      int e = tid + q * 256;
-      int r = e >> 3, kk = e & 7;
-      int64_t gr = m0 + r;
-      sW[r][kk] = (gr < M) ? W[gr * Kp + k0 + kk] : make_double2(0.0, 0.0);
-      int kr = e >> 6, cc = e & 63;
-      int64_t gc = n0 + cc;
-      sD[kr][cc] = (gc < N) ? D[(int64_t)(k0 + kr) * N + gc] : make_double2(0.0, 0.0);
-    }
+    sWr[wr_][wk] = pw0.x; sWi[wr_][wk] = pw0.y; sWs[wr_][wk] = pw0.x + pw0.y;
+    sWr[wr_ + 32][wk] = pw1.x; sWi[wr_ + 32][wk] = pw1.y; sWs[wr_ + 32][wk] = pw1.x + pw1.y;
+    sDr[dk][dc] = pd0.x; sDi[dk][dc] = pd0.y; sDs[dk][dc] = pd0.x + pd0.y;
+    sDr[dk + 4][dc] = pd1.x; sDi[dk + 4][dc] = pd1.y; sDs[dk + 4][dc] = pd1.x + pd1.y;
     __syncthreads();
-    double ar[2][4], ai[2][4], br[2][2], bi[2][2], bn[2][2];
-#pragma unroll
-    for (int mi = 0; mi < 2; ++mi) {
-      const int rb = wm * 32 + mi * 16;
-      double2 x0 = sW[rb + g][tq], x1 = sW[rb + g + 8][tq], x2 = sW[rb + g][tq + 4], x3 = sW[rb + g + 8][tq + 4];
-      ar[mi][0] = x0.x; ar[mi][1] = x1.x; ar[mi][2] = x2.x; ar[mi][3] = x3.x;
-      ai[mi][0] = x0.y; ai[mi][1] = x1.y; ai[mi][2] = x2.y; ai[mi][3] = x3.y;
+    if (k0 + GBK < Kp) {  // prefetch the next K step while the tensor pipe works
+      pw0 = ldW(k0 + GBK, 0);
+      pw1 = ldW(k0 + GBK, 1);
+      pd0 = ldD(k0 + GBK, 0);
+      pd1 = ldD(k0 + GBK, 1);
     }
+    double br[2][2], bi[2][2], bs[2][2];
 #pragma unroll
     for (int ni = 0; ni < 2; ++ni) {
-      const int cb = wn * 16 + ni * 8;
-      double2 y0 = sD[tq][cb + g], y1 = sD[tq + 4][cb + g];
-      br[ni][0] = y0.x; br[ni][1] = y1.x;
-      bi[ni][0] = y0.y; bi[ni][1] = y1.y;
-      bn[ni][0] = -y0.y; bn[ni][1] = -y1.y;
+      const int cb = wn * 16 + ni * 8 + g;
+      br[ni][0] = sDr[tq][cb]; br[ni][1] = sDr[tq + 4][cb];
+      bi[ni][0] = sDi[tq][cb]; bi[ni][1] = sDi[tq + 4][cb];
+      bs[ni][0] = sDs[tq][cb]; bs[ni][1] = sDs[tq + 4][cb];
     }
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi)
+    for (int mi = 0; mi < 2; ++mi) {
+      const int r0 = wm * 32 + mi * 16 + g;
+      double a[4];
+      a[0] = sWr[r0][tq]; a[1] = sWr[r0 + 8][tq]; a[2] = sWr[r0][tq + 4]; a[3] = sWr[r0 + 8][tq + 4];
 #pragma unroll
-      for (int ni = 0; ni < 2; ++ni) {
-        mma_f64(cr[mi][ni], ar[mi], br[ni]);
-        mma_f64(cr[mi][ni], ai[mi], bn[ni]);
-        mma_f64(ci[mi][ni], ar[mi], bi[ni]);
-        mma_f64(ci[mi][ni], ai[mi], br[ni]);
-      }
+      for (int ni = 0; ni < 2; ++ni) mma_f64(t1[mi][ni], a, br[ni]);
+      a[0] = sWi[r0][tq]; a[1] = sWi[r0 + 8][tq]; a[2] = sWi[r0][tq + 4]; a[3] = sWi[r0 + 8][tq + 4];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) mma_f64(t2[mi][ni], a, bi[ni]);
+      a[0] = sWs[r0][tq]; a[1] = sWs[r0 + 8][tq]; a[2] = sWs[r0][tq + 4]; a[3] = sWs[r0 + 8][tq + 4];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) mma_f64(t3[mi][ni], a, bs[ni]);
+    }
     __syncthreads();
   }
 
@@ -628,7 +641,8 @@ k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64
           const int64_t col = n0 + wn * 16 + ni * 8 + 2 * tq + hc;
           if (col >= N) continue;
           const int e = hr * 2 + hc;
-          const double vr = cr[mi][ni][e], vi = ci[mi][ni][e];
+          const double vr = t1[mi][ni][e] - t2[mi][ni][e];
+          const double vi = t3[mi][ni][e] - t1[mi][ni][e] - t2[mi][ni][e];
           const double Dk = base - eA[col] - U1[col] - U2[col] + U3[col] + U4[col];
           acc += en_term(fma(vr, vr, vi * vi), Dk, b);
         }
