@@ -143,6 +143,22 @@ E2_API e2_status e2_workspace_size(const e2_problem* prob, size_t* bytes);
 E2_API e2_status e2_forward(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
                      void* stream, double* E2, double* E2_class, double* E0);
 
+/* Adjoint of e2_forward (gradients are not in the paper; they follow from
+ * differentiating Eq. pt2 with E0 = <Psi|H|Psi>/<Psi|Psi>).  For
+ * F = sum_m seed[m] E2_m it returns, for complex inputs z, dF/dRe z + i dF/dIm z:
+ *   g_h  device [n][n]          projected on Hermitian matrices (the unrelaxed
+ *                               response one-particle density), or NULL
+ *   g_c  device [n_roots][N_P]  gradient for each root's coefficients, or NULL
+ *                               (orthogonal to c: E2 does not depend on |c|)
+ *   seed host [n_roots]
+ * V is recomputed (never stored whole): the dense classes run in row chunks
+ * whose weighted amplitudes fit a 2 GiB buffer.  Enqueues on `stream`;
+ * workspace of at least e2_backward_workspace_size() bytes (it contains the
+ * e2_forward and reference-solver layouts). */
+E2_API e2_status e2_backward_workspace_size(const e2_problem* prob, size_t* bytes);
+E2_API e2_status e2_backward(e2_problem* prob, const e2_inputs* in, const double* seed, void* workspace,
+                             size_t workspace_bytes, void* stream, double* g_h, double* g_c);
+
 /* Reference states: the n_roots lowest eigenvectors of P H P (the CASCI /
  * DAS-CI reference of Sec. 2.2-2.3, Eq. zeroh first term), by block Davidson
  * iteration on the device (sigma = P H c built from the same coupling

@@ -57,6 +57,11 @@ def load():
         L.e2_reference_solve.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_double, C.c_int, C.c_void_p, C.c_size_t,
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
         L.e2_reference_solve.restype = C.c_int
+        L.e2_backward_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
+        L.e2_backward_workspace_size.restype = C.c_int
+        L.e2_backward.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
+                                  C.c_void_p, C.c_void_p]
+        L.e2_backward.restype = C.c_int
         L.e2_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
         L.e2_launch_count.restype = C.c_int
         L.e2_profile_events.argtypes = [C.c_void_p, C.c_void_p]
@@ -111,6 +116,8 @@ class E2Problem:
         self.workspace_bytes = int(ws.value)
         _check(L.e2_reference_workspace_size(self._h, C.byref(ws)))
         self.solve_workspace_bytes = int(ws.value)
+        _check(L.e2_backward_workspace_size(self._h, C.byref(ws)))
+        self.backward_workspace_bytes = int(ws.value)
         self._ws = None
         self._events = None
 
@@ -132,12 +139,13 @@ class E2Problem:
         except Exception:
             pass
 
-    def workspace(self, device, solver=False):
+    def workspace(self, device, solver=False, backward=False):
         """A 256-byte aligned uint8 CUDA tensor of the required size (cached);
-        the reference solver needs the larger layout, which contains the
-        forward one."""
+        the reference solver and the adjoint need larger layouts, which
+        contain the forward one."""
         import torch
-        need = self.solve_workspace_bytes if solver else self.workspace_bytes
+        need = (self.backward_workspace_bytes if backward else
+                self.solve_workspace_bytes if solver else self.workspace_bytes)
         if self._ws is None or self._ws.device != device or self._ws.numel() < need:
             self._ws = None
             raw = torch.empty(need + 256, dtype=torch.uint8, device=device)
@@ -145,6 +153,23 @@ class E2Problem:
             self._ws_raw = raw
             self._ws = raw[off:off + need]
         return self._ws
+
+    def backward(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, seed=None, want_h=True, want_c=True, stream=None):
+        """Gradient of sum_m seed[m] E2_m: returns (g_h [n, n] or None,
+        g_c [roots, N_P] or None) as complex128 CUDA tensors (dE/dRe + i dE/dIm;
+        g_h Hermitian-projected)."""
+        import torch
+        dev = c.device
+        ws = self.workspace(dev, backward=True)
+        seed = np.ascontiguousarray(np.ones(self.n_roots) if seed is None else seed, np.float64)
+        gh = torch.empty(self.n, self.n, dtype=torch.complex128, device=dev) if want_h else None
+        gc = torch.empty(self.n_roots, self.n_p, dtype=torch.complex128, device=dev) if want_c else None
+        inp = _Inputs(h.data_ptr(), B_c.data_ptr(), B_x.data_ptr() if self.L_extra else None,
+                      w_x.data_ptr() if self.L_extra else None, float(lam), c.data_ptr())
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        _check(load().e2_backward(self._h, C.byref(inp), seed.ctypes.data_as(C.c_void_p), ws.data_ptr(), ws.numel(),
+                                  C.c_void_p(s), gh.data_ptr() if want_h else None, gc.data_ptr() if want_c else None))
+        return gh, gc
 
     def reference_solve(self, h, B_c, X0, B_x=None, w_x=None, lam=1.0, tol=1e-10, max_iter=300, stream=None):
         """Lowest n_roots eigenvectors of P H P from start vectors X0 [roots, N_P]

@@ -1,0 +1,687 @@
+// sm_103a adjoint kernels of the Epstein-Nesbet second-order energy.
+//
+// With v_K = |V_K|^2/n (n = <c|c>), D_K = E0 - H_KK, E2 = sum_K f(v_K, D_K),
+// f = v/D or, with the level shift of Sec. 2.6, v D^3/(D^4 + b^2), and the
+// seed s of the root:
+//   t_K = s (2/n) (df/dv) V_K            weighted first-order amplitude
+//   eta_K = s df/dD                      denominator weight
+//   dE2 = Re sum_K conj(t_K) <K|dH|c> + (sum eta / n) <c|dH|c> - sum_K eta_K <K|dH|K>
+//   cbar = H_PQ t - (2/n) s (sum (df/dv) v) c + (2/n) (sum eta) (H_PP - E0) c
+// Coefficients Gamma_X below are "dE2 = Re sum Gamma_X dX"; a gradient with
+// respect to a complex input z is conj(Gamma_z) (dE2/dRe z + i dE2/dIm z).
+#include <cuda_runtime.h>
+
+#include "e2_common.cuh"
+#include "e2_device.cuh"
+#include "e2_kernels.cuh"
+
+namespace e2 {
+
+// ------------------------------------------------------------------ generic complex GEMM
+
+// C[m][n] = beta * C[m][n] + sum_k opA(m,k) opB(k,n) on the FP64 tensor pipe
+// (three real products per complex product), opA(m,k) = A[m*sam + k*sak]
+// (conjugated when conjA), opB(k,n) = B[k*sbk + n*sbn] (conjugated when
+// conjB); C row-major with leading dimension ldc; beta is 0 or 1.  Each C tile
+// is owned by one CTA over the full K: deterministic.
+__global__ void __launch_bounds__(256, 1)
+k_zgemm(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
+        const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t ldc,
+        int beta) {
+  constexpr int BM = 64, BN = 64, BK = 8;
+  __shared__ double sAr[BM][BK + 1], sAi[BM][BK + 1], sAs[BM][BK + 1];
+  __shared__ double sBr[BK][BN + 1], sBi[BK][BN + 1], sBs[BK][BN + 1];
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int wm = warp >> 2, wn = warp & 3;
+  double t1[2][2][4], t2[2][2][4], t3[2][2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) t1[a][c][e] = t2[a][c][e] = t3[a][c][e] = 0.0;
+  const int ar = tid >> 3, ak = tid & 7, bk = tid >> 6, bc = tid & 63;
+  const double2 zero = make_double2(0.0, 0.0);
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int64_t m = m0 + ar + 32 * q, k = k0 + ak;
+      double2 v = (m < M && k < K) ? A[m * sam + k * sak] : zero;
+      if (conjA) v.y = -v.y;
+      sAr[ar + 32 * q][ak] = v.x;
+      sAi[ar + 32 * q][ak] = v.y;
+      sAs[ar + 32 * q][ak] = v.x + v.y;
+      const int64_t kb = k0 + bk + 4 * q, nn = n0 + bc;
+      double2 u = (kb < K && nn < N) ? B[kb * sbk + nn * sbn] : zero;
+      if (conjB) u.y = -u.y;
+      sBr[bk + 4 * q][bc] = u.x;
+      sBi[bk + 4 * q][bc] = u.y;
+      sBs[bk + 4 * q][bc] = u.x + u.y;
+    }
+    __syncthreads();
+    double br[2][2], bi[2][2], bs[2][2];
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni) {
+      const int cb = wn * 16 + ni * 8 + g;
+      br[ni][0] = sBr[tq][cb]; br[ni][1] = sBr[tq + 4][cb];
+      bi[ni][0] = sBi[tq][cb]; bi[ni][1] = sBi[tq + 4][cb];
+      bs[ni][0] = sBs[tq][cb]; bs[ni][1] = sBs[tq + 4][cb];
+    }
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) {
+      const int r0 = wm * 32 + mi * 16 + g;
+      double a[4];
+      a[0] = sAr[r0][tq]; a[1] = sAr[r0 + 8][tq]; a[2] = sAr[r0][tq + 4]; a[3] = sAr[r0 + 8][tq + 4];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) mma_f64(t1[mi][ni], a, br[ni]);
+      a[0] = sAi[r0][tq]; a[1] = sAi[r0 + 8][tq]; a[2] = sAi[r0][tq + 4]; a[3] = sAi[r0 + 8][tq + 4];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) mma_f64(t2[mi][ni], a, bi[ni]);
+      a[0] = sAs[r0][tq]; a[1] = sAs[r0 + 8][tq]; a[2] = sAs[r0][tq + 4]; a[3] = sAs[r0 + 8][tq + 4];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) mma_f64(t3[mi][ni], a, bs[ni]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int64_t row = m0 + wm * 32 + mi * 16 + g + (e >> 1) * 8;
+        const int64_t col = n0 + wn * 16 + ni * 8 + 2 * tq + (e & 1);
+        if (row >= M || col >= N) continue;
+        double2 v = make_double2(t1[mi][ni][e] - t2[mi][ni][e], t3[mi][ni][e] - t1[mi][ni][e] - t2[mi][ni][e]);
+        double2* out = C + row * ldc + col;
+        if (beta) {
+          v.x += out->x;
+          v.y += out->y;
+        }
+        *out = v;
+      }
+}
+
+// ------------------------------------------------------------------ reductions of the adjoint sums
+
+// out[r] (+)= sum_c in[r*ncol + c] in index order
+__global__ void k_rowsum(const double* __restrict__ in, int64_t nrow, int64_t ncol, int acc, double* __restrict__ out) {
+  const int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (r >= nrow) return;
+  double s = 0.0;
+  for (int64_t c = 0; c < ncol; ++c) s += in[r * ncol + c];
+  out[r] = acc ? out[r] + s : s;
+}
+
+// out[c] (+)= sum_r in[r*ncol + c] in index order
+__global__ void k_colsum(const double* __restrict__ in, int64_t nrow, int64_t ncol, int acc, double* __restrict__ out) {
+  const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  double s = 0.0;
+  for (int64_t r = 0; r < nrow; ++r) s += in[r * ncol + c];
+  out[c] = acc ? out[c] + s : s;
+}
+
+// scal_out[k] += sum_i in[2*i + k], k = 0, 1 (one block, fixed order)
+__global__ void k_scalsum(const double* __restrict__ in, int64_t n, double* __restrict__ scal_out) {
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    a += in[2 * i];
+    b += in[2 * i + 1];
+  }
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    scal_out[0] += a;
+    scal_out[1] += b;
+  }
+}
+
+// Nx[x] += sum over rows e whose particles / holes include x of hsum[e]
+// (x indexes correlated core then correlated virtual spinors).
+__global__ void k_xmarg(const RowInfo* __restrict__ rows, const double* __restrict__ hsum, int64_t M, int nx,
+                        double* __restrict__ Nx) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= nx) return;
+  double s = 0.0;
+  for (int64_t e = 0; e < M; ++e) {
+    const RowInfo ri = rows[e];
+    if (ri.s1 == x || ri.s2 == x || ri.i1 == x || ri.i2 == x) s += hsum[e];
+  }
+  Nx[x] += s;
+}
+
+// Nt[t] += sum_A hA[A] [t in A] over one string list (one block per t)
+__global__ void k_amarg(DevList Ls, const double* __restrict__ hA, double* __restrict__ Nt) {
+  __shared__ double sh[32];
+  const int t = blockIdx.x;
+  double s = 0.0;
+  for (int64_t g = threadIdx.x; g < Ls.n; g += blockDim.x)
+    if ((Ls.str[g] >> t) & 1) s += hA[g];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) Nt[t] += s;
+}
+
+// out[e] = sum_A conj(T[e][A]) d[A]  (one block per row)
+__global__ void k_rowdot(const double2* __restrict__ T, const double2* __restrict__ d, int64_t N,
+                         double2* __restrict__ out) {
+  __shared__ double sh[32];
+  const int64_t e = blockIdx.x;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t A = threadIdx.x; A < N; A += blockDim.x) acc = cfma(cconj(T[e * N + A]), d[A], acc);
+  const double re = block_sum(acc.x, sh), im = block_sum(acc.y, sh);
+  if (threadIdx.x == 0) out[e] = make_double2(re, im);
+}
+
+// Gamma_f[a][i] += out[(i, a)] for the (1,1) rows e = i*nvc + a
+__global__ void k_fock11(const double2* __restrict__ rowdot, DevSpace sp, double2* __restrict__ Gf) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)sp.ncc * sp.nvc) return;
+  const int i = (int)(e / sp.nvc), a = (int)(e % sp.nvc);
+  double2* dst = Gf + (int64_t)sp.vc[a] * sp.n_occ + sp.cc[i];
+  dst->x += rowdot[e].x;
+  dst->y += rowdot[e].y;
+}
+
+// ------------------------------------------------------------------ class (2,2)
+
+// Per thread one string A; same tiling as the forward kernel.  Writes
+//   cpart[yz][A] = sum_{ab in block} s (df/dv) |<ab||ij>|^2      (cbar_A = (2/n) c_A sum)
+//   hpart[yz][A] = sum_{ab in block} s df/dD                     (string marginal)
+//   vpart[cta][0..15] = per-virtual sums of s df/dD (a block, then b block), vpart[cta][16] = ij sum,
+//   vpart[cta][17..18] = (sum s df/dD, sum s (df/dv) v)
+__global__ void __launch_bounds__(256)
+k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* __restrict__ g2,
+              const double* __restrict__ epsh, const double* __restrict__ G, const double* __restrict__ E0p, double b,
+              int nvb, double s, const double2* __restrict__ g1, double* __restrict__ cpart,
+              double* __restrict__ hpart, double* __restrict__ vpart) {
+  const double inv_n = 1.0 / g1[0].x;
+  __shared__ double sGab[8][8], sG2[8][8], sAl[2][8];
+  __shared__ double sh[32];
+  int ba = 0, bb = 0;
+  {
+    int yb = blockIdx.y, k = 0;
+    while (yb >= nvb - k) { yb -= nvb - k; ++k; }
+    ba = k;
+    bb = k + yb;
+  }
+  int iu, ju;
+  pair_decode(blockIdx.z, iu, ju);
+  const int gi = sp.cc[iu], gj = sp.cc[ju];
+  const int64_t nvp = pairs(sp.nvc);
+  const int tid = threadIdx.x;
+  if (tid < 64) {
+    int x = tid >> 3, y = tid & 7;
+    int a = ba * 8 + x, bq = bb * 8 + y;
+    bool ok = a < sp.nvc && bq < sp.nvc && a < bq;
+    sGab[x][y] = ok ? G[(int64_t)sp.vc[a] * sp.n + sp.vc[bq]] : 0.0;
+    sG2[x][y] = ok ? g2[(int64_t)blockIdx.z * nvp + pair_index(a, bq)] : 0.0;
+  } else if (tid < 80) {
+    int k = tid - 64, side = k >> 3, x = k & 7;
+    int a = (side ? bb : ba) * 8 + x;
+    double al = 0.0;
+    if (a < sp.nvc) {
+      int ga = sp.vc[a];
+      al = epsh[ga] - G[(int64_t)gi * sp.n + ga] - G[(int64_t)gj * sp.n + ga];
+    }
+    sAl[side][x] = al;
+  }
+  __syncthreads();
+  const int64_t A = blockIdx.x * (int64_t)blockDim.x + tid;
+  double ha[8], hb[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) ha[k] = hb[k] = 0.0;
+  double csum = 0.0, hsum = 0.0, gv = 0.0;
+  if (A < Ls.n) {
+    const double chi_ij = -epsh[gi] - epsh[gj] + G[(int64_t)gi * sp.n + gj];
+    const double ct = *E0p - Ls.eA[A] + Ls.U[(int64_t)iu * Ls.n + A] + Ls.U[(int64_t)ju * Ls.n + A] - chi_ij;
+    const double2 cv = c[A];
+    const double c2 = (cv.x * cv.x + cv.y * cv.y) * inv_n;
+    double pa[8], pb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      int a = ba * 8 + k, bq = bb * 8 + k;
+      pa[k] = (a < sp.nvc) ? sAl[0][k] + Ls.U[(int64_t)(sp.ncc + a) * Ls.n + A] : 0.0;
+      pb[k] = (bq < sp.nvc) ? sAl[1][k] + Ls.U[(int64_t)(sp.ncc + bq) * Ls.n + A] : 0.0;
+    }
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const double cx = ct - pa[x];
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        const double w = sG2[x][y];
+        if (w == 0.0) continue;
+        double gk, hk;
+        en_derivs(w * c2, cx - pb[y] - sGab[x][y], b, gk, hk);
+        hk *= s;
+        csum += s * gk * w;
+        gv += s * gk * w * c2;
+        hsum += hk;
+        ha[x] += hk;
+        hb[y] += hk;
+      }
+    }
+  }
+  const int64_t yz = (int64_t)blockIdx.z * gridDim.y + blockIdx.y;
+  if (A < Ls.n) {
+    cpart[yz * Ls.n + A] = csum;
+    hpart[yz * Ls.n + A] = hsum;
+  }
+  const int64_t cta = yz * gridDim.x + blockIdx.x;
+  for (int k = 0; k < 8; ++k) {
+    double v = block_sum(ha[k], sh);
+    if (tid == 0) vpart[cta * 19 + k] = v;
+    v = block_sum(hb[k], sh);
+    if (tid == 0) vpart[cta * 19 + 8 + k] = v;
+  }
+  double v = block_sum(hsum, sh);
+  double w2 = block_sum(gv, sh);
+  if (tid == 0) {
+    vpart[cta * 19 + 16] = v;
+    vpart[cta * 19 + 17] = v;
+    vpart[cta * 19 + 18] = w2;
+  }
+}
+
+// Reduce the (2,2) per-CTA partials: Nx (virtual and core marginals), scalars.
+__global__ void k_class22_marg(const double* __restrict__ vpart, int nx_blocks, int nvb, int64_t ncp, DevSpace sp,
+                               double* __restrict__ Nx, double* __restrict__ scal) {
+  // one thread per correlated virtual (index a) or per correlated core (index i)
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nyb = (int64_t)nvb * (nvb + 1) / 2;
+  if (x < sp.nvc) {
+    const int blk = x / 8, off = x % 8;
+    double s = 0.0;
+    for (int64_t z = 0; z < ncp; ++z)
+      for (int64_t y = 0; y < nyb; ++y) {
+        int yb = (int)y, k = 0;
+        while (yb >= nvb - k) { yb -= nvb - k; ++k; }
+        const int ba = k, bb = k + yb;
+        for (int64_t xb = 0; xb < nx_blocks; ++xb) {
+          const int64_t cta = (z * nyb + y) * nx_blocks + xb;
+          if (ba == blk) s += vpart[cta * 19 + off];
+          if (bb == blk) s += vpart[cta * 19 + 8 + off];
+        }
+      }
+    Nx[sp.ncc + x] += s;
+  } else if (x < sp.nvc + sp.ncc) {
+    const int i = x - sp.nvc;
+    double s = 0.0;
+    for (int64_t z = 0; z < ncp; ++z) {
+      int iu, ju;
+      pair_decode(z, iu, ju);
+      if (iu != i && ju != i) continue;
+      for (int64_t k = 0; k < nyb * nx_blocks; ++k) s += vpart[(z * nyb * nx_blocks + k) * 19 + 16];
+    }
+    Nx[i] += s;
+  } else if (x == sp.nvc + sp.ncc) {
+    double a = 0.0, bsum = 0.0;
+    for (int64_t k = 0; k < ncp * nyb * nx_blocks; ++k) {
+      a += vpart[k * 19 + 17];
+      bsum += vpart[k * 19 + 18];
+    }
+    scal[0] += a;
+    scal[1] += bsum;
+  }
+}
+
+// ------------------------------------------------------------------ gather classes, pass 1
+
+// Amplitudes and denominator weights of the gather classes, one thread per
+// (row, string): T[row][A] = t_K, H[row][A] = s df/dD.  cls 1: (0,1) rows a;
+// cls 3: (1,0) rows i; cls 0: (0,0) one row.
+__global__ void k_gather_t(int cls, DevList Lx, DevList L12, DevList L02, DevList L21, DevList L11, DevDas das,
+                           DevSpace sp, const int64_t* __restrict__ binom, const double2* __restrict__ DT,
+                           const double2* __restrict__ DTU, const double2* __restrict__ DTD,
+                           const double2* __restrict__ DTDU, const double2* __restrict__ X01,
+                           const double2* __restrict__ X10, const double2* __restrict__ X00,
+                           const double2* __restrict__ f, const double* __restrict__ epsh,
+                           const double* __restrict__ E0p, double b, double s, const double2* __restrict__ g1,
+                           double2* __restrict__ T, double* __restrict__ H, double* __restrict__ GV) {
+  const double inv_n = 1.0 / g1[0].x, s2n = 2.0 * s * inv_n;
+  const int row = blockIdx.y;
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= Lx.n) return;
+  const uint64_t A = Lx.str[g];
+  const int na = sp.n_act, ntp = (int)pairs(na);
+  double2 V = make_double2(0.0, 0.0);
+  double Dk = *E0p - Lx.eA[g];
+  if (cls == 1) {
+    const int ga = sp.vc[row];
+    int64_t a12 = list_addr(L12, das, binom, A);
+    if (a12 >= 0)
+      for (int t = 0; t < na; ++t) V = cfma(f[(int64_t)ga * sp.n_occ + sp.a0 + t], DT[(int64_t)t * L12.n + a12], V);
+    for (uint64_t x = A; x; x &= x - 1) {
+      const int u = __ffsll((long long)x) - 1;
+      const uint64_t B = A & ~(1ull << u);
+      const int64_t a02 = list_addr(L02, das, binom, B);
+      if (a02 < 0) continue;
+      double2 sacc = make_double2(0.0, 0.0);
+      const double2* Xr = X01 + ((int64_t)row * na + u) * ntp;
+      for (int w = 1; w < na; ++w) {
+        if ((B >> w) & 1) continue;
+        for (int v = 0; v < w; ++v) {
+          if ((B >> v) & 1) continue;
+          const int vw = pair_index(v, w);
+          sacc = cfma(Xr[vw], DTU[(int64_t)vw * L02.n + a02], sacc);
+        }
+      }
+      if (popc_below(A, u) & 1) sacc = make_double2(-sacc.x, -sacc.y);
+      V.x += sacc.x;
+      V.y += sacc.y;
+    }
+    Dk -= epsh[ga] + Lx.U[(int64_t)(sp.ncc + row) * Lx.n + g];
+  } else if (cls == 3) {
+    const int gi = sp.cc[row];
+    int64_t a21 = list_addr(L21, das, binom, A);
+    if (a21 >= 0)
+      for (int t = 0; t < na; ++t) V = cfma(f[(int64_t)(sp.a0 + t) * sp.n_occ + gi], DTD[(int64_t)t * L21.n + a21], V);
+    for (uint64_t xu = A; xu; xu &= xu - 1) {
+      const int u = __ffsll((long long)xu) - 1;
+      for (uint64_t xt = A & ((1ull << u) - 1); xt; xt &= xt - 1) {
+        const int t = __ffsll((long long)xt) - 1;
+        const uint64_t B = A & ~(1ull << t) & ~(1ull << u);
+        const int64_t a12 = list_addr(L12, das, binom, B);
+        if (a12 < 0) continue;
+        const double2* Xr = X10 + ((int64_t)row * pairs(na) + pair_index(t, u)) * na;
+        double2 sacc = make_double2(0.0, 0.0);
+        for (int v = 0; v < na; ++v) {
+          if ((B >> v) & 1) continue;
+          sacc = cfma(Xr[v], DT[(int64_t)v * L12.n + a12], sacc);
+        }
+        if ((popc_below(B, u) + popc_below(B, t)) & 1) sacc = make_double2(-sacc.x, -sacc.y);
+        V.x += sacc.x;
+        V.y += sacc.y;
+      }
+    }
+    Dk += epsh[gi] + Lx.U[(int64_t)row * Lx.n + g];
+  } else {
+    V = active_sigma(A, L11, L02, das, sp, binom, DTDU, DTU, X00, f);
+  }
+  const double v2 = V.x * V.x + V.y * V.y;
+  double gk, hk;
+  en_derivs(v2 * inv_n, Dk, b, gk, hk);
+  T[(int64_t)row * Lx.n + g] = make_double2(s2n * gk * V.x, s2n * gk * V.y);
+  H[(int64_t)row * Lx.n + g] = s * hk;
+  GV[(int64_t)row * Lx.n + g] = s * gk * v2 * inv_n;
+}
+
+
+// ------------------------------------------------------------------ gather classes, pass 2
+
+// Gamma_f rows: out[r][k] = sum_A conj(T[r][A]) Dsrc(k, A) for the one-body
+// part of a gather class (one block per (row, k)).
+//   cls 1: Gamma_f[a][t]  += sum_A conj(T01[a][A]) D^t_A          (A in L01 -> L12 address)
+//   cls 3: Gamma_f[t][i]  += sum_A conj(T10[i][A]) D^{t+}_A       (A in L10 -> L21 address)
+//   cls 0: Gamma_f[t][u]  += sum_A conj(T00[A]) D^{t+u}_A         (A in L00 -> L11 address)
+__global__ void k_gather_fock(int cls, DevList Lx, DevList Lsrc, DevDas das, DevSpace sp,
+                              const int64_t* __restrict__ binom, const double2* __restrict__ Dsrc,
+                              const double2* __restrict__ T, double2* __restrict__ Gf) {
+  __shared__ double sh[32];
+  const int na = sp.n_act;
+  const int row = blockIdx.y, k = blockIdx.x;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t g = threadIdx.x; g < Lx.n; g += blockDim.x) {
+    const int64_t as = list_addr(Lsrc, das, binom, Lx.str[g]);
+    if (as < 0) continue;
+    const int64_t drow = (cls == 0) ? (1 + k) : k;
+    acc = cfma(cconj(T[(int64_t)row * Lx.n + g]), Dsrc[drow * Lsrc.n + as], acc);
+  }
+  const double re = block_sum(acc.x, sh), im = block_sum(acc.y, sh);
+  if (threadIdx.x == 0) {
+    int64_t idx;
+    if (cls == 1) idx = (int64_t)sp.vc[row] * sp.n_occ + sp.a0 + k;
+    else if (cls == 3) idx = (int64_t)(sp.a0 + k) * sp.n_occ + sp.cc[row];
+    else idx = (int64_t)(sp.a0 + k / na) * sp.n_occ + sp.a0 + k % na;
+    Gf[idx].x += re;
+    Gf[idx].y += im;
+  }
+}
+
+// Gamma_D of the gather classes' one-body parts, one thread per string of the
+// coupling table's list (sum over the class rows in order):
+//   cls 1: Gamma_DT[t][A12]    += sum_a conj(T01[a][A]) f_at
+//   cls 3: Gamma_DTD[t][A21]   += sum_i conj(T10[i][A]) f_ti
+//   cls 0: Gamma_DTDU[1+tu][A11] += conj(T00[A]) f_tu
+__global__ void k_gather_d1(int cls, DevList Lx, DevList Ltab, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
+                            const double2* __restrict__ T, int nrow, const double2* __restrict__ f,
+                            double2* __restrict__ GD) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= Ltab.n) return;
+  const int64_t ax = list_addr(Lx, das, binom, Ltab.str[g]);
+  if (ax < 0) return;
+  const int na = sp.n_act;
+  if (cls == 0) {
+    const double2 tc = cconj(T[ax]);
+    for (int t = 0; t < na; ++t)
+      for (int u = 0; u < na; ++u) {
+        double2* dst = GD + (int64_t)(1 + t * na + u) * Ltab.n + g;
+        *dst = cfma(tc, f[(int64_t)(sp.a0 + t) * sp.n_occ + sp.a0 + u], *dst);
+      }
+    return;
+  }
+  for (int t = 0; t < na; ++t) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int r = 0; r < nrow; ++r) {
+      const double2 fv = (cls == 1) ? f[(int64_t)sp.vc[r] * sp.n_occ + sp.a0 + t]
+                                    : f[(int64_t)(sp.a0 + t) * sp.n_occ + sp.cc[r]];
+      acc = cfma(cconj(T[(int64_t)r * Lx.n + ax]), fv, acc);
+    }
+    double2* dst = GD + (int64_t)t * Ltab.n + g;
+    dst->x += acc.x;
+    dst->y += acc.y;
+  }
+}
+
+// Gamma_D of the gather classes' two-body parts, one thread per string B of
+// the table's list, summing every (A, row) that reads D[x][B]:
+//   cls 1: Gamma_DTU[vw][B]  += sum_{u not in B} sum_a conj(T01[a][B+u]) (-1)^{#(B+u)<u} <au||vw>
+//   cls 3: Gamma_DT[v][B]    += sum_{t<u not in B} sum_i conj(T10[i][B+t+u]) s(B;t,u) <tu||iv>
+//   cls 0: Gamma_DTU[vw][B]  += sum_{t<u not in B} conj(T00[B+t+u]) s(B;t,u) <tu||vw>
+__global__ void k_gather_d2(int cls, DevList Lx, DevList Ltab, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
+                            const double2* __restrict__ T, int nrow, const double2* __restrict__ X,
+                            double2* __restrict__ GD) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (g >= Ltab.n) return;
+  const uint64_t B = Ltab.str[g];
+  const int na = sp.n_act, ntp = (int)pairs(na);
+  if (cls == 1) {
+    for (int w = 1; w < na; ++w) {
+      if ((B >> w) & 1) continue;
+      for (int v = 0; v < w; ++v) {
+        if ((B >> v) & 1) continue;
+        const int vw = pair_index(v, w);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int u = 0; u < na; ++u) {
+          if ((B >> u) & 1) continue;
+          const uint64_t A = B | (1ull << u);
+          const int64_t ax = list_addr(Lx, das, binom, A);
+          if (ax < 0) continue;
+          double2 part = make_double2(0.0, 0.0);
+          for (int a = 0; a < nrow; ++a)
+            part = cfma(cconj(T[(int64_t)a * Lx.n + ax]), X[((int64_t)a * na + u) * ntp + vw], part);
+          if (popc_below(A, u) & 1) part = make_double2(-part.x, -part.y);
+          acc.x += part.x;
+          acc.y += part.y;
+        }
+        double2* dst = GD + (int64_t)vw * Ltab.n + g;
+        dst->x += acc.x;
+        dst->y += acc.y;
+      }
+    }
+    return;
+  }
+  const int nk = (cls == 3) ? na : ntp;
+  for (int k = 0; k < nk; ++k) {
+    if (cls == 3) {
+      if ((B >> k) & 1) continue;
+    } else {
+      int v, w;
+      pair_decode(k, v, w);
+      if (((B >> v) & 1) || ((B >> w) & 1)) continue;
+    }
+    double2 acc = make_double2(0.0, 0.0);
+    for (int u = 1; u < na; ++u) {
+      if ((B >> u) & 1) continue;
+      for (int t = 0; t < u; ++t) {
+        if ((B >> t) & 1) continue;
+        const uint64_t A = B | (1ull << t) | (1ull << u);
+        const int64_t ax = list_addr(Lx, das, binom, A);
+        if (ax < 0) continue;
+        const int tu = pair_index(t, u);
+        double2 part = make_double2(0.0, 0.0);
+        if (cls == 3) {
+          for (int i = 0; i < nrow; ++i)
+            part = cfma(cconj(T[(int64_t)i * Lx.n + ax]), X[((int64_t)i * ntp + tu) * na + k], part);
+        } else {
+          part = cmul(cconj(T[ax]), X[(int64_t)tu * ntp + k]);
+        }
+        if ((popc_below(B, u) + popc_below(B, t)) & 1) part = make_double2(-part.x, -part.y);
+        acc.x += part.x;
+        acc.y += part.y;
+      }
+    }
+    double2* dst = GD + (int64_t)k * Ltab.n + g;
+    dst->x += acc.x;
+    dst->y += acc.y;
+  }
+}
+
+// ------------------------------------------------------------------ coupling tensors -> reference coefficients
+
+// Gamma_c[L] = sum over every table entry D[x][A] = sign * c[L] of sign * Gamma_D[x][A],
+// one thread per reference string L (the transpose of k_dtable).
+__global__ void k_dscatter(int fam, DevList Ls, DevList Pl, DevDas das, const int64_t* __restrict__ binom,
+                           const double2* __restrict__ GD, double2* __restrict__ Gc) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= Pl.n) return;
+  const uint64_t L = Pl.str[l];
+  const int na = das.n_act;
+  double2 acc = make_double2(0.0, 0.0);
+  auto add = [&](int64_t x, uint64_t A, int par) {
+    const int64_t a = list_addr(Ls, das, binom, A);
+    if (a < 0) return;
+    double2 v = GD[x * Ls.n + a];
+    if (par & 1) v = make_double2(-v.x, -v.y);
+    acc.x += v.x;
+    acc.y += v.y;
+  };
+  switch (fam) {
+    case FAM_T:  // D^t_A = (-1)^{#A<t} c[A+t], t not in A: A = L - t
+      for (int t = 0; t < na; ++t)
+        if ((L >> t) & 1) add(t, L & ~(1ull << t), popc_below(L, t));
+      break;
+    case FAM_TD:  // D^{t+}_A = (-1)^{#A<t} c[A-t], t in A: A = L + t
+      for (int t = 0; t < na; ++t)
+        if (!((L >> t) & 1)) add(t, L | (1ull << t), popc_below(L, t));
+      break;
+    case FAM_TU:  // D^{tu}_A, A = L - t - u, parity #L<t + #(L-t)<u
+      for (int u = 1; u < na; ++u)
+        for (int t = 0; t < u; ++t)
+          if (((L >> t) & 1) && ((L >> u) & 1))
+            add(pair_index(t, u), L & ~(1ull << t) & ~(1ull << u),
+                popc_below(L, t) + popc_below(L & ~(1ull << t), u));
+      break;
+    case FAM_TDUD:  // D^{t+u+}_A, A = L + t + u, parity #L<u + #L<t
+      for (int u = 1; u < na; ++u)
+        for (int t = 0; t < u; ++t)
+          if (!((L >> t) & 1) && !((L >> u) & 1))
+            add(pair_index(t, u), L | (1ull << t) | (1ull << u), popc_below(L, u) + popc_below(L, t));
+      break;
+    case FAM_TDU:  // row 0: A = L ; row 1+t*na+u: A = L - u + t (u in L; t == u or t not in L)
+      add(0, L, 0);
+      for (int u = 0; u < na; ++u) {
+        if (!((L >> u) & 1)) continue;
+        for (int t = 0; t < na; ++t) {
+          if (t != u && ((L >> t) & 1)) continue;
+          const uint64_t A = (L & ~(1ull << u)) | (1ull << t);
+          add(1 + t * na + u, A, popc_below(L, u) + popc_below(A, t));
+        }
+      }
+      break;
+  }
+  Gc[l].x += acc.x;
+  Gc[l].y += acc.y;
+}
+
+// scal[0] += sum H, scal[1] += sum GV (one block, fixed order)
+__global__ void k_sum2(const double* __restrict__ H, const double* __restrict__ GV, int64_t n, double* __restrict__ scal) {
+  __shared__ double sh[32];
+  double x = 0.0, y = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    x += H[i];
+    y += GV[i];
+  }
+  x = block_sum(x, sh);
+  y = block_sum(y, sh);
+  if (threadIdx.x == 0) {
+    scal[0] += x;
+    scal[1] += y;
+  }
+}
+
+// E0 term of the h coefficient: Gamma_f[t][u] += (sum eta / n) gamma_tu
+__global__ void k_e0grad(const double2* __restrict__ g1, const double* __restrict__ scal, DevSpace sp,
+                         double2* __restrict__ Gf) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int na = sp.n_act;
+  if (k >= na * na) return;
+  const double w = scal[0] / g1[0].x;
+  const int t = k / na, u = k % na;
+  double2* dst = Gf + (int64_t)(sp.a0 + t) * sp.n_occ + sp.a0 + u;
+  dst->x += w * g1[1 + k].x;
+  dst->y += w * g1[1 + k].y;
+}
+
+// Diagonal coefficient of h: correlated core +Nx, active -Nt, correlated virtual -Nx
+__global__ void k_nd(DevSpace sp, const double* __restrict__ Nx, const double* __restrict__ Nt, double* __restrict__ Nd) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= sp.n) return;
+  double v = 0.0;
+  if (p >= sp.a0 && p < sp.v0) v = -Nt[p - sp.a0];
+  for (int i = 0; i < sp.ncc; ++i)
+    if (sp.cc[i] == p) v = Nx[i];
+  for (int a = 0; a < sp.nvc; ++a)
+    if (sp.vc[a] == p) v = -Nx[sp.ncc + a];
+  Nd[p] = v;
+}
+
+// cbar = conj(Gamma_c) + (2/n) c (s * sum22 [per string, (2,2)])
+//        + (2/n) eta (sigma' - E0' c) - (2/n) gv c
+// scal = (sum eta, sum s (df/dv) v) over every class.
+__global__ void k_cbar(int64_t np, const double2* __restrict__ Gc, const double* __restrict__ c22,
+                       const double2* __restrict__ c, const double2* __restrict__ sigma, const double* __restrict__ scal,
+                       const double* __restrict__ E0p, const double2* __restrict__ g1, double2* __restrict__ out) {
+  const int64_t l = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (l >= np) return;
+  const double n = g1[0].x, two_n = 2.0 / n;
+  const double eta = scal[0], gv = scal[1], e0p = *E0p;
+  const double2 cv = c[l], sg = sigma[l];
+  const double a = two_n * ((c22 ? c22[l] : 0.0) - gv);
+  double2 v = cconj(Gc[l]);
+  v.x += a * cv.x + two_n * eta * (sg.x - e0p * cv.x);
+  v.y += a * cv.y + two_n * eta * (sg.y - e0p * cv.y);
+  out[l] = v;
+}
+
+// hbar = Hermitian part of conj(Gamma_h), Gamma_h = Gamma_f (+ diagonal terms):
+//   Gamma_h[p][p] += Nd[p] (denominators and E0)
+__global__ void k_hbar(DevSpace sp, const double2* __restrict__ Gf, const double* __restrict__ Nd, double2* __restrict__ gh) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int n = sp.n;
+  if (idx >= (int64_t)n * n) return;
+  const int p = (int)(idx / n), q = (int)(idx % n);
+  auto coef = [&](int x, int y) {
+    double2 v = (y < sp.n_occ) ? Gf[(int64_t)x * sp.n_occ + y] : make_double2(0.0, 0.0);
+    if (x == y) v.x += Nd[x];
+    return v;
+  };
+  const double2 a = coef(p, q), bq = coef(q, p);
+  // Hermitian projection of conj(Gamma): (conj(G_pq) + G_qp) / 2
+  gh[idx] = make_double2(0.5 * (a.x + bq.x), 0.5 * (-a.y + bq.y));
+}
+
+}  // namespace e2

@@ -90,6 +90,12 @@ struct e2_problem {
   // reference solver region
   int sv_mmax;
   size_t o_sV, o_sS, o_sX, o_sR, o_sD, o_sT, o_sG, o_sY, solve_bytes;
+  // adjoint region
+  size_t o_dstart;                   // first D table of the root-0 slot
+  int64_t chunk_rows[E2_NCLASS];     // dense-class rows per adjoint chunk
+  size_t o_gD, o_bT, o_bHrow, o_bHcol, o_bScalT, o_bHsum, o_bHA, o_bRowdot;
+  size_t o_bGT, o_bGH, o_bGV, o_bC22p, o_bH22p, o_bV22, o_bC22, o_bGc, o_bSig, o_bGf, o_bNx, o_bNt, o_bNd, o_bScal;
+  size_t bwd_bytes;
 };
 
 namespace {
@@ -282,6 +288,7 @@ e2_status build_plan(e2_problem* P) {
   // D tables (per root)
   auto lsize = [&](int cls) -> int64_t { return P->list_of[cls] >= 0 ? P->lists[P->list_of[cls]].n : 0; };
   size_t dstart = ws.top;
+  P->o_dstart = dstart;
   P->o_DT = ws.take(16 * (size_t)P->KpT * std::max<int64_t>(lsize(5), 1));
   P->o_DTD = ws.take(16 * (size_t)P->KpT * std::max<int64_t>(lsize(7), 1));
   P->o_DTU = ws.take(16 * (size_t)P->KpTU * std::max<int64_t>(lsize(2), 1));
@@ -332,6 +339,55 @@ e2_status build_plan(e2_problem* P) {
   P->o_sG = ws.take(16 * (size_t)P->sv_mmax * P->sv_mmax);
   P->o_sY = ws.take(16 * (size_t)P->sv_mmax * std::max(R, 1));
   P->solve_bytes = ws.top;
+  // adjoint region on top of the solver layout (the forward one is its prefix)
+  {
+    const size_t tbudget = size_t(2) << 30;
+    size_t tmax = 16, hrow = 8, hcol = 8, scalt = 16, hsum = 8, hA = 8;
+    for (int c : {2, 5, 7, 4, 6}) {
+      const int64_t Mc = P->M[c], Nc = lsize(c);
+      P->chunk_rows[c] = 0;
+      if (Mc == 0 || Nc == 0) continue;
+      int64_t rows_fit = (int64_t)(tbudget / (16 * (size_t)Nc)) / 64 * 64;
+      rows_fit = std::max<int64_t>(64, rows_fit);
+      P->chunk_rows[c] = std::min<int64_t>(rows_fit, (Mc + 63) / 64 * 64);
+      const int64_t rt = (Mc + 63) / 64, ct = (Nc + 63) / 64;
+      tmax = std::max(tmax, (size_t)16 * P->chunk_rows[c] * Nc);
+      hrow = std::max(hrow, (size_t)8 * Mc * ct);
+      hcol = std::max(hcol, (size_t)8 * rt * Nc);
+      scalt = std::max(scalt, (size_t)16 * rt * ct);
+      hsum = std::max(hsum, (size_t)8 * Mc);
+    }
+    for (size_t li = 0; li < P->lists.size(); ++li) hA = std::max(hA, (size_t)8 * P->lists[li].n);
+    size_t gmax = 8;
+    for (int c : {1, 3, 0})
+      if (P->list_of[c] >= 0) gmax = std::max(gmax, (size_t)P->M[c] * P->lists[P->list_of[c]].n);
+    const int64_t nyb = (int64_t)P->nvb * (P->nvb + 1) / 2;
+    const int64_t np22 = lsize(8), xb22 = (np22 + 255) / 256;
+    const size_t yz = (size_t)std::max<int64_t>(1, nyb * P->ncp);
+    P->o_gD = ws.take(P->d_stride);
+    P->o_bT = ws.take(tmax);
+    P->o_bHrow = ws.take(hrow);
+    P->o_bHcol = ws.take(hcol);
+    P->o_bScalT = ws.take(scalt);
+    P->o_bHsum = ws.take(hsum);
+    P->o_bHA = ws.take(hA);
+    P->o_bRowdot = ws.take(16 * (size_t)std::max<int64_t>(P->M[4], 1));
+    P->o_bGT = ws.take(16 * gmax);
+    P->o_bGH = ws.take(8 * gmax);
+    P->o_bGV = ws.take(8 * gmax);
+    P->o_bC22p = ws.take(8 * yz * std::max<int64_t>(np22, 1));
+    P->o_bH22p = ws.take(8 * yz * std::max<int64_t>(np22, 1));
+    P->o_bV22 = ws.take(8 * 19 * yz * std::max<int64_t>(xb22, 1));
+    P->o_bC22 = ws.take(8 * (size_t)std::max<int64_t>(np_, 1));
+    P->o_bGc = ws.take(16 * (size_t)np_);
+    P->o_bSig = ws.take(16 * (size_t)np_);
+    P->o_bGf = ws.take(16 * (size_t)P->n * P->nocc);
+    P->o_bNx = ws.take(8 * (size_t)(P->nx + 1));
+    P->o_bNt = ws.take(8 * (size_t)std::max(P->na, 1));
+    P->o_bNd = ws.take(8 * (size_t)P->n);
+    P->o_bScal = ws.take(16);
+    P->bwd_bytes = ws.top;
+  }
 
   // ---- host image of the plan region
   P->plan_blob.assign(P->plan_bytes, 0);
@@ -548,6 +604,23 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
                                                                        P->ntp * na, P->ntp * na, ws + P->o_X10), ++g_launches);
 }
 
+// Coupling tensors of root r, the active one- and two-particle blocks of
+// its reference state, and E0 (Sec. 2.3).
+void prepare_root(e2_problem* P, unsigned char* ws, cudaStream_t st, const double2* c, int r) {
+  const int na = P->na;
+  Ctx X = ctx(P, ws);
+  Tabs T = tables(P, ws, r);
+  const DevList L02 = dev_list(P, P->list_of[2], ws), L11 = dev_list(P, P->list_of[4], ws);
+  build_tables(P, ws, st, c, T, true);
+  double2* g1 = (double2*)(ws + P->o_g1 + P->g_stride * r);
+  double2* g2 = (double2*)(ws + P->o_g2 + P->g_stride * r);
+  (k_gram<<<1 + na * na, 256, 0, st>>>(T.DTDU, T.DTDU, L11.n, 1 + na * na, g1), ++g_launches);
+  if (P->ntp > 0 && L02.n > 0) (k_gram<<<P->ntp * P->ntp, 256, 0, st>>>(T.DTU, T.DTU, L02.n, P->ntp, g2), ++g_launches);
+  else cudaMemsetAsync(g2, 0, 16 * (size_t)std::max(P->ntp * P->ntp, 1), st);
+  (k_e0<<<1, 256, 0, st>>>(g1, g2, X.f, (const double2*)(ws + P->o_X00), X.sp, P->ntp, X.EO, X.E0p + r, X.E0d + r),
+   ++g_launches);
+}
+
 }  // namespace
 
 extern "C" {
@@ -662,13 +735,7 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
   for (int r = 0; r < R; ++r) {
     const double2* c = (const double2*)in->c + (int64_t)r * LP.n;
     Tabs T = tables(P, ws, r);
-    build_tables(P, ws, st, c, T, true);
-    double2* g1 = (double2*)(ws + P->o_g1 + P->g_stride * r);
-    double2* g2 = (double2*)(ws + P->o_g2 + P->g_stride * r);
-    (k_gram<<<1 + na * na, 256, 0, st>>>(T.DTDU, T.DTDU, Lc[4].n, 1 + na * na, g1), ++g_launches);
-    if (P->ntp > 0 && Lc[2].n > 0) (k_gram<<<P->ntp * P->ntp, 256, 0, st>>>(T.DTU, T.DTU, Lc[2].n, P->ntp, g2), ++g_launches);
-    else cudaMemsetAsync(g2, 0, 16 * (size_t)std::max(P->ntp * P->ntp, 1), st);
-    (k_e0<<<1, 256, 0, st>>>(g1, g2, X.f, (const double2*)(ws + P->o_X00), X.sp, P->ntp, X.EO, X.E0p + r, X.E0d + r), ++g_launches);
+    prepare_root(P, ws, st, c, r);
 
     auto poff = [&](int cls) { return part + P->part_off[r * E2_NCLASS + cls]; };
     const double2* Dfor[E2_NCLASS] = {nullptr, nullptr, T.DTU, nullptr, T.DTDU, T.DT, T.DTDUD, T.DTD, nullptr};
@@ -681,7 +748,7 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
       dim3 grid((unsigned)((P->M[cls] + 63) / 64), (unsigned)((L.n + 63) / 64));
       mark(cls, 0);
       (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Dfor[cls], P->M[cls], L.n, P->Kp[cls],
-                                         (const RowInfo*)(ws + P->o_rows[cls]), L.U, L.eA, X.E0p + r, b, poff(cls)), ++g_launches);
+                                         (const RowInfo*)(ws + P->o_rows[cls]), L.U, L.eA, X.E0p + r, b, poff(cls), AdjOut{}), ++g_launches);
       mark(cls, 1);
     }
     if (P->part_cnt[8] > 0) {
@@ -767,6 +834,166 @@ e2_status e2_fp64_peak(void* workspace, size_t workspace_bytes, void* stream_, d
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
+}
+
+e2_status e2_backward_workspace_size(const e2_problem* P, size_t* bytes) {
+  if (!P || !bytes) return E2_ERR_INVALID_ARG;
+  *bytes = P->bwd_bytes;
+  return E2_OK;
+}
+
+e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, void* workspace, size_t workspace_bytes,
+                      void* stream_, double* g_h, double* g_c) {
+  if (!P || !in || !seed || !in->h || !in->B_c || !in->c) return E2_ERR_INVALID_ARG;
+  if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
+  if (!std::isfinite(in->lambda)) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < P->bwd_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  const e2_desc& d = P->d;
+  const int R = d.n_roots, na = P->na;
+  const double b = d.level_shift_b;
+  cudaGetLastError();
+  g_launches = 0;
+  if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
+  setup_classes(P, ws, st);
+  Ctx X = ctx(P, ws);
+  const DevList LP = dev_list(P, P->listP, ws);
+  DevList Lc[E2_NCLASS];
+  for (int c = 0; c < E2_NCLASS; ++c) Lc[c] = dev_list(P, P->list_of[c], ws);
+  auto B = [&](size_t o) { return (void*)(ws + o); };
+  double2* Gf = (double2*)B(P->o_bGf);
+  double* Nx = (double*)B(P->o_bNx);
+  double* Nt = (double*)B(P->o_bNt);
+  double* Nd = (double*)B(P->o_bNd);
+  double* scal = (double*)B(P->o_bScal);
+  double2* Gc = (double2*)B(P->o_bGc);
+  double2* sig = (double2*)B(P->o_bSig);
+  cudaMemsetAsync(Gf, 0, 16 * (size_t)P->n * P->nocc, st);
+  cudaMemsetAsync(Nx, 0, 8 * (size_t)(P->nx + 1), st);
+  cudaMemsetAsync(Nt, 0, 8 * (size_t)std::max(na, 1), st);
+  const bool on[E2_NCLASS] = {P->part_cnt[0] > 0, P->part_cnt[1] > 0, P->part_cnt[2] > 0, P->part_cnt[3] > 0,
+                              P->part_cnt[4] > 0, P->part_cnt[5] > 0, P->part_cnt[6] > 0, P->part_cnt[7] > 0,
+                              P->part_cnt[8] > 0};
+  for (int r = 0; r < R; ++r) {
+    const double2* c = (const double2*)in->c + (int64_t)r * LP.n;
+    prepare_root(P, ws, st, c, r);
+    const double s = seed[r];
+    if (s == 0.0) {
+      if (g_c) cudaMemsetAsync(g_c + 2 * (size_t)r * LP.n, 0, 16 * (size_t)LP.n, st);
+      continue;
+    }
+    Tabs T = tables(P, ws, r);
+    Tabs GT{(double2*)(ws + P->o_gD + (P->o_DT - P->o_dstart)), (double2*)(ws + P->o_gD + (P->o_DTD - P->o_dstart)),
+            (double2*)(ws + P->o_gD + (P->o_DTU - P->o_dstart)), (double2*)(ws + P->o_gD + (P->o_DTDUD - P->o_dstart)),
+            (double2*)(ws + P->o_gD + (P->o_DTDU - P->o_dstart))};
+    const double2* g1 = (const double2*)(ws + P->o_g1 + P->g_stride * r);
+    cudaMemsetAsync(ws + P->o_gD, 0, P->d_stride, st);
+    cudaMemsetAsync(Gc, 0, 16 * (size_t)LP.n, st);
+    cudaMemsetAsync(scal, 0, 16, st);
+    double* hsum = (double*)B(P->o_bHsum);
+    double* hA = (double*)B(P->o_bHA);
+    // dense classes: amplitudes in row chunks, Gamma_D += W^T conj(T)
+    const double2* Dfor[E2_NCLASS] = {nullptr, nullptr, T.DTU, nullptr, T.DTDU, T.DT, T.DTDUD, T.DTD, nullptr};
+    double2* GDfor[E2_NCLASS] = {nullptr, nullptr, GT.DTU, nullptr, GT.DTDU, GT.DT, GT.DTDUD, GT.DTD, nullptr};
+    for (int cls : {2, 5, 7, 4, 6}) {
+      if (!on[cls]) continue;
+      const DevList& L = Lc[cls];
+      const int64_t M = P->M[cls], N = L.n, Kp = P->Kp[cls];
+      const int64_t rt = (M + 63) / 64, ct = (N + 63) / 64;
+      const double2* W = (const double2*)(ws + P->o_W[cls]);
+      for (int64_t m0 = 0; m0 < M; m0 += P->chunk_rows[cls]) {
+        const int64_t Mc = std::min<int64_t>(P->chunk_rows[cls], M - m0);
+        AdjOut adj{(double2*)B(P->o_bT), (double*)B(P->o_bHrow), (double*)B(P->o_bHcol), (double*)B(P->o_bScalT),
+                   m0, Mc, s, g1};
+        dim3 grid((unsigned)((Mc + 63) / 64), (unsigned)ct);
+        (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
+                                            L.eA, X.E0p + r, b, nullptr, adj), ++g_launches);
+        dim3 gz((unsigned)((Kp + 63) / 64), (unsigned)ct);
+        (k_zgemm<<<gz, 256, 0, st>>>(Kp, N, Mc, W + m0 * Kp, 1, Kp, 0, adj.T, N, 1, 1, GDfor[cls], N, 1), ++g_launches);
+        if (cls == 4)
+          (k_rowdot<<<(unsigned)Mc, 256, 0, st>>>(adj.T, T.DTDU, N, (double2*)B(P->o_bRowdot) + m0), ++g_launches);
+      }
+      if (cls == 4) (k_fock11<<<blocks(M), 256, 0, st>>>((const double2*)B(P->o_bRowdot), X.sp, Gf), ++g_launches);
+      (k_rowsum<<<blocks(M), 256, 0, st>>>((const double*)B(P->o_bHrow), M, ct, 0, hsum), ++g_launches);
+      (k_xmarg<<<blocks(P->nx), 256, 0, st>>>((const RowInfo*)(ws + P->o_rows[cls]), hsum, M, P->nx, Nx), ++g_launches);
+      (k_colsum<<<blocks(N), 256, 0, st>>>((const double*)B(P->o_bHcol), rt, N, 0, hA), ++g_launches);
+      (k_amarg<<<na, 256, 0, st>>>(L, hA, Nt), ++g_launches);
+      (k_scalsum<<<1, 256, 0, st>>>((const double*)B(P->o_bScalT), rt * ct, scal), ++g_launches);
+    }
+    // class (2,2)
+    double* c22 = nullptr;
+    if (on[8]) {
+      const DevList& L = Lc[8];
+      const int64_t nyb = (int64_t)P->nvb * (P->nvb + 1) / 2, yz = nyb * P->ncp;
+      dim3 grid(blocks(L.n), (unsigned)nyb, (unsigned)P->ncp);
+      (k_class22_bwd<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b,
+                                           P->nvb, s, g1, (double*)B(P->o_bC22p), (double*)B(P->o_bH22p),
+                                           (double*)B(P->o_bV22)), ++g_launches);
+      c22 = (double*)B(P->o_bC22);
+      (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bC22p), yz, L.n, 0, c22), ++g_launches);
+      (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bH22p), yz, L.n, 0, hA), ++g_launches);
+      (k_amarg<<<na, 256, 0, st>>>(L, hA, Nt), ++g_launches);
+      (k_class22_marg<<<blocks(P->nvc + P->ncc + 1), 256, 0, st>>>((const double*)B(P->o_bV22), (int)blocks(L.n),
+                                                                   P->nvb, P->ncp, X.sp, Nx, scal), ++g_launches);
+    }
+    // gather classes
+    for (int cls : {1, 3, 0}) {
+      if (!on[cls]) continue;
+      const DevList& L = Lc[cls];
+      const int nrow = (int)P->M[cls];
+      double2* Tg = (double2*)B(P->o_bGT);
+      double* Hg = (double*)B(P->o_bGH);
+      double* GVg = (double*)B(P->o_bGV);
+      dim3 grid(blocks(L.n), (unsigned)nrow);
+      (k_gather_t<<<grid, 256, 0, st>>>(cls, L, Lc[5], Lc[2], Lc[7], Lc[4], P->das, X.sp, X.binom, T.DT, T.DTU, T.DTD,
+                                        T.DTDU, (const double2*)(ws + P->o_X01), (const double2*)(ws + P->o_X10),
+                                        (const double2*)(ws + P->o_X00), X.f, X.epsh, X.E0p + r, b, s, g1, Tg, Hg,
+                                        GVg), ++g_launches);
+      (k_sum2<<<1, 256, 0, st>>>(Hg, GVg, (int64_t)nrow * L.n, scal), ++g_launches);
+      if (cls == 1) (k_rowsum<<<blocks(nrow), 256, 0, st>>>(Hg, nrow, L.n, 1, Nx + P->ncc), ++g_launches);
+      if (cls == 3) (k_rowsum<<<blocks(nrow), 256, 0, st>>>(Hg, nrow, L.n, 1, Nx), ++g_launches);
+      (k_colsum<<<blocks(L.n), 256, 0, st>>>(Hg, nrow, L.n, 0, hA), ++g_launches);
+      (k_amarg<<<na, 256, 0, st>>>(L, hA, Nt), ++g_launches);
+      // one-body parts: Gamma_f and the D^t / D^{t+} / D^{t+u} coefficients
+      const int nk = (cls == 0) ? na * na : na;
+      const DevList& Lsrc = (cls == 1) ? Lc[5] : (cls == 3) ? Lc[7] : Lc[4];
+      const double2* Dsrc = (cls == 1) ? T.DT : (cls == 3) ? T.DTD : T.DTDU;
+      double2* GDsrc = (cls == 1) ? GT.DT : (cls == 3) ? GT.DTD : GT.DTDU;
+      if (Lsrc.n > 0) {
+        (k_gather_fock<<<dim3(nk, nrow), 256, 0, st>>>(cls, L, Lsrc, P->das, X.sp, X.binom, Dsrc, Tg, Gf), ++g_launches);
+        (k_gather_d1<<<blocks(Lsrc.n), 256, 0, st>>>(cls, L, Lsrc, P->das, X.sp, X.binom, Tg, nrow, X.f, GDsrc),
+         ++g_launches);
+      }
+      // two-body parts
+      const DevList& Ltab = (cls == 3) ? Lc[5] : Lc[2];
+      double2* GDtab = (cls == 3) ? GT.DT : GT.DTU;
+      const double2* Xb = (const double2*)(ws + ((cls == 1) ? P->o_X01 : (cls == 3) ? P->o_X10 : P->o_X00));
+      if (Ltab.n > 0)
+        (k_gather_d2<<<blocks(Ltab.n), 256, 0, st>>>(cls, L, Ltab, P->das, X.sp, X.binom, Tg, nrow, Xb, GDtab),
+         ++g_launches);
+    }
+    // E0 term of the one-body coefficient, then the reference-state gradient
+    (k_e0grad<<<blocks(na * na), 256, 0, st>>>(g1, scal, X.sp, Gf), ++g_launches);
+    if (g_c) {
+      const struct { int fam, cls; double2* g; } sc[5] = {{FAM_T, 5, GT.DT}, {FAM_TD, 7, GT.DTD}, {FAM_TU, 2, GT.DTU},
+                                                          {FAM_TDUD, 6, GT.DTDUD}, {FAM_TDU, 4, GT.DTDU}};
+      for (const auto& q : sc)
+        if (Lc[q.cls].n > 0)
+          (k_dscatter<<<blocks(LP.n), 256, 0, st>>>(q.fam, Lc[q.cls], LP, P->das, X.binom, q.g, Gc), ++g_launches);
+      (k_sigma<<<blocks(LP.n), 256, 0, st>>>(LP, Lc[4], Lc[2], P->das, X.sp, X.binom, T.DTDU, T.DTU,
+                                             (const double2*)(ws + P->o_X00), X.f, sig), ++g_launches);
+      (k_cbar<<<blocks(LP.n), 256, 0, st>>>(LP.n, Gc, c22, c, sig, scal, X.E0p + r, g1,
+                                            (double2*)g_c + (int64_t)r * LP.n), ++g_launches);
+    }
+  }
+  if (g_h) {
+    (k_nd<<<blocks(P->n), 256, 0, st>>>(X.sp, Nx, Nt, Nd), ++g_launches);
+    (k_hbar<<<blocks((int64_t)P->n * P->n), 256, 0, st>>>(X.sp, Gf, Nd, (double2*)g_h), ++g_launches);
+  }
+  P->launches = g_launches;
+  if (cudaGetLastError() != cudaSuccess) return E2_ERR_CUDA;
+  return E2_OK;
 }
 
 e2_status e2_reference_workspace_size(const e2_problem* P, size_t* bytes) {

@@ -40,6 +40,21 @@ struct RowInfo {
   double chi;
 };
 
+// Adjoint outputs of the dense-class kernel (T == nullptr: forward mode).
+// Rows [m_base, m_base + Mc) are processed; T holds t = s (2/n) (df/dv) V
+// for those rows, Hrow[row][column tile] and Hcol[row tile][column] the
+// per-tile sums of s df/dD, scal[2 * tile] = (sum s df/dD, sum s (df/dv) v);
+// n = <c|c> is read from g1[0].
+struct AdjOut {
+  double2* T;
+  double* Hrow;
+  double* Hcol;
+  double* scal;
+  int64_t m_base, Mc;
+  double s;
+  const double2* g1;
+};
+
 enum IntMode : int {
   INT_W02 = 0,  // <ab||tu>          rows (a<b), cols (t<u)
   INT_W12,      // <ab||it>          rows (i, a<b), cols t

@@ -1,0 +1,177 @@
+// Device helpers shared by the forward and adjoint kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "e2_common.cuh"
+
+namespace e2 {
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+  c.x = fma(a.x, b.x, c.x);
+  c.x = fma(-a.y, b.y, c.x);
+  c.y = fma(a.x, b.y, c.y);
+  c.y = fma(a.y, b.x, c.y);
+  return c;
+}
+__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
+
+__device__ __forceinline__ int popc_below(uint64_t A, int t) {
+  return __popcll(t ? (A & ((1ull << t) - 1)) : 0ull);
+}
+
+// 1/d: single-precision seed refined by two Newton-Raphson steps
+// (x <- x (2 - d x)); each step squares the relative error, 2^-23 -> 2^-46
+// -> below double rounding.  Valid for 1e-30 < |d| < 1e30.
+__device__ __forceinline__ double rcp_nr(double d) {
+  double r = (double)__frcp_rn(__double2float_rn(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
+// Epstein-Nesbet term |V|^2/D, or with the imaginary level shift the real
+// part of |V|^2/(D + i b/D) = |V|^2 D^3/(D^4 + b^2) (Sec. 2.6).
+__device__ __forceinline__ double en_term(double v2, double D, double b) {
+  if (b == 0.0) return v2 * rcp_nr(D);
+  double D2 = D * D;
+  return v2 * D * D2 * rcp_nr(fma(D2, D2, b * b));
+}
+
+// df/dv and df/dD of the Epstein-Nesbet term f(v, D) = v/D, or with the
+// level shift f = v D^3/(D^4 + b^2).
+__device__ __forceinline__ void en_derivs(double v, double D, double b, double& g, double& h) {
+  if (b == 0.0) {
+    const double r = rcp_nr(D);
+    g = r;
+    h = -v * r * r;
+    return;
+  }
+  const double D2 = D * D, r = rcp_nr(fma(D2, D2, b * b));
+  g = D * D2 * r;
+  h = v * D2 * fma(3.0 * b, b, -D2 * D2) * r * r;
+}
+
+__device__ __forceinline__ void pair_decode(int64_t e, int& x, int& y) {
+  int64_t yy = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)e)) * 0.5);
+  while (yy > 1 && yy * (yy - 1) / 2 > e) --yy;
+  while ((yy + 1) * yy / 2 <= e) ++yy;
+  y = (int)yy;
+  x = (int)(e - yy * (yy - 1) / 2);
+}
+
+__device__ __forceinline__ int pair_index(int x, int y) { return y * (y - 1) / 2 + x; }  // x < y
+
+// Colex rank of a substring with k set bits: sum_j C(t_j, j), j = 1..k.
+__device__ __forceinline__ int64_t colex_rank(uint64_t bits, const int64_t* __restrict__ binom) {
+  int64_t r = 0;
+  int j = 0;
+  while (bits) {
+    int t = __ffsll((long long)bits) - 1;
+    bits &= bits - 1;
+    ++j;
+    r += binom[t * kBinomN + j];
+  }
+  return r;
+}
+
+__device__ __forceinline__ uint64_t colex_unrank(int64_t rank, int k, int size, const int64_t* __restrict__ binom) {
+  uint64_t out = 0;
+  int t = size - 1;
+  for (int j = k; j >= 1; --j) {
+    while (binom[t * kBinomN + j] > rank) --t;
+    out |= 1ull << t;
+    rank -= binom[t * kBinomN + j];
+    --t;
+  }
+  return out;
+}
+
+// Position of string A in list Ls, or -1 when A's pattern is not in the list.
+__device__ __forceinline__ int64_t list_addr(const DevList& Ls, const DevDas& das, const int64_t* __restrict__ binom,
+                                             uint64_t A) {
+  if (Ls.key2off == nullptr) return -1;
+  int key = 0;
+  int occ[E2_MAX_DAS];
+  for (int s = 0; s < das.n_das; ++s) {
+    uint64_t m = ((das.size[s] == 64) ? ~0ull : ((1ull << das.size[s]) - 1)) << das.off[s];
+    occ[s] = __popcll(A & m);
+    key += occ[s] * das.keymul[s];
+  }
+  int64_t off = Ls.key2off[key];
+  if (off < 0) return -1;
+  int64_t stride = 1;
+  for (int s = 0; s < das.n_das; ++s) {
+    uint64_t sub = (A >> das.off[s]) & ((das.size[s] == 64) ? ~0ull : ((1ull << das.size[s]) - 1));
+    off += colex_rank(sub, binom) * stride;
+    stride *= binom[das.size[s] * kBinomN + occ[s]];
+  }
+  return off;
+}
+
+// Fixed-order block sum of a per-thread double; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < nw; ++k) t += sh[k];
+  return t;
+}
+
+// One m16n8k8 FP64 tensor-pipe product: c += a b (a: 16x8 row fragment,
+// b: 8x8 column fragment, c: 16x8 accumulator fragment).
+__device__ __forceinline__ void mma_f64(double (&c)[4], const double (&a)[4], const double (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
+      : "+d"(c[0]), "+d"(c[1]), "+d"(c[2]), "+d"(c[3])
+      : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(b[0]), "d"(b[1]));
+}
+
+// <A| H - E_O |Psi> for an n_elec-electron string A with no core hole or
+// virtual particle: sum_{tu} f_tu D^{t+u}_A + sum_{t<u in A} s(A;t,u)
+// sum_{v<w} <tu||vw> D^{vw}_{A-t-u}.  Class (0,0) evaluates it on strings of
+// non-reference patterns; the reference solver evaluates it on P (sigma = H c).
+__device__ inline double2 active_sigma(uint64_t A, const DevList& L11, const DevList& L02, const DevDas& das,
+                                const DevSpace& sp, const int64_t* __restrict__ binom, const double2* __restrict__ DTDU,
+                                const double2* __restrict__ DTU, const double2* __restrict__ X00,
+                                const double2* __restrict__ f) {
+  const int na = sp.n_act, ntp = (int)pairs(na);
+  double2 V = make_double2(0.0, 0.0);
+  int64_t a11 = list_addr(L11, das, binom, A);
+  if (a11 >= 0)
+    for (int t = 0; t < na; ++t)
+      for (int u = 0; u < na; ++u)
+        V = cfma(f[(int64_t)(sp.a0 + t) * sp.n_occ + sp.a0 + u], DTDU[(int64_t)(1 + t * na + u) * L11.n + a11], V);
+  for (uint64_t xu = A; xu; xu &= xu - 1) {
+    const int u = __ffsll((long long)xu) - 1;
+    for (uint64_t xt = A & ((1ull << u) - 1); xt; xt &= xt - 1) {
+      const int t = __ffsll((long long)xt) - 1;
+      const uint64_t B = A & ~(1ull << t) & ~(1ull << u);
+      const int64_t a02 = list_addr(L02, das, binom, B);
+      if (a02 < 0) continue;
+      const double2* Xr = X00 + (int64_t)pair_index(t, u) * ntp;
+      double2 s = make_double2(0.0, 0.0);
+      for (int w = 1; w < na; ++w) {
+        if ((B >> w) & 1) continue;
+        for (int v = 0; v < w; ++v) {
+          if ((B >> v) & 1) continue;
+          const int vw = pair_index(v, w);
+          s = cfma(Xr[vw], DTU[(int64_t)vw * L02.n + a02], s);
+        }
+      }
+      if ((popc_below(B, u) + popc_below(B, t)) & 1) s = make_double2(-s.x, -s.y);
+      V.x += s.x;
+      V.y += s.y;
+    }
+  }
+  return V;
+}
+
+}  // namespace e2

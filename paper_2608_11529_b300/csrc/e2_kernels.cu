@@ -13,102 +13,9 @@
 
 #include "e2_common.cuh"
 #include "e2_kernels.cuh"
+#include "e2_device.cuh"
 
 namespace e2 {
-
-// ------------------------------------------------------------------ helpers
-
-__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
-}
-__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
-  c.x = fma(a.x, b.x, c.x);
-  c.x = fma(-a.y, b.y, c.x);
-  c.y = fma(a.x, b.y, c.y);
-  c.y = fma(a.y, b.x, c.y);
-  return c;
-}
-__device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
-
-__device__ __forceinline__ int popc_below(uint64_t A, int t) {
-  return __popcll(t ? (A & ((1ull << t) - 1)) : 0ull);
-}
-
-// 1/d: single-precision seed refined by two Newton-Raphson steps
-// (x <- x (2 - d x)); each step squares the relative error, 2^-23 -> 2^-46
-// -> below double rounding.  Valid for 1e-30 < |d| < 1e30.
-__device__ __forceinline__ double rcp_nr(double d) {
-  double r = (double)__frcp_rn(__double2float_rn(d));
-  double e = fma(-d, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-d, r, 1.0);
-  return fma(r, e, r);
-}
-
-// Epstein-Nesbet term |V|^2/D, or with the imaginary level shift the real
-// part of |V|^2/(D + i b/D) = |V|^2 D^3/(D^4 + b^2) (Sec. 2.6).
-__device__ __forceinline__ double en_term(double v2, double D, double b) {
-  if (b == 0.0) return v2 * rcp_nr(D);
-  double D2 = D * D;
-  return v2 * D * D2 * rcp_nr(fma(D2, D2, b * b));
-}
-
-__device__ __forceinline__ void pair_decode(int64_t e, int& x, int& y) {
-  int64_t yy = (int64_t)((1.0 + sqrt(1.0 + 8.0 * (double)e)) * 0.5);
-  while (yy > 1 && yy * (yy - 1) / 2 > e) --yy;
-  while ((yy + 1) * yy / 2 <= e) ++yy;
-  y = (int)yy;
-  x = (int)(e - yy * (yy - 1) / 2);
-}
-
-__device__ __forceinline__ int pair_index(int x, int y) { return y * (y - 1) / 2 + x; }  // x < y
-
-// Colex rank of a substring with k set bits: sum_j C(t_j, j), j = 1..k.
-__device__ __forceinline__ int64_t colex_rank(uint64_t bits, const int64_t* __restrict__ binom) {
-  int64_t r = 0;
-  int j = 0;
-  while (bits) {
-    int t = __ffsll((long long)bits) - 1;
-    bits &= bits - 1;
-    ++j;
-    r += binom[t * kBinomN + j];
-  }
-  return r;
-}
-
-__device__ __forceinline__ uint64_t colex_unrank(int64_t rank, int k, int size, const int64_t* __restrict__ binom) {
-  uint64_t out = 0;
-  int t = size - 1;
-  for (int j = k; j >= 1; --j) {
-    while (binom[t * kBinomN + j] > rank) --t;
-    out |= 1ull << t;
-    rank -= binom[t * kBinomN + j];
-    --t;
-  }
-  return out;
-}
-
-// Position of string A in list Ls, or -1 when A's pattern is not in the list.
-__device__ __forceinline__ int64_t list_addr(const DevList& Ls, const DevDas& das, const int64_t* __restrict__ binom,
-                                             uint64_t A) {
-  if (Ls.key2off == nullptr) return -1;
-  int key = 0;
-  int occ[E2_MAX_DAS];
-  for (int s = 0; s < das.n_das; ++s) {
-    uint64_t m = ((das.size[s] == 64) ? ~0ull : ((1ull << das.size[s]) - 1)) << das.off[s];
-    occ[s] = __popcll(A & m);
-    key += occ[s] * das.keymul[s];
-  }
-  int64_t off = Ls.key2off[key];
-  if (off < 0) return -1;
-  int64_t stride = 1;
-  for (int s = 0; s < das.n_das; ++s) {
-    uint64_t sub = (A >> das.off[s]) & ((das.size[s] == 64) ? ~0ull : ((1ull << das.size[s]) - 1));
-    off += colex_rank(sub, binom) * stride;
-    stride *= binom[das.size[s] * kBinomN + occ[s]];
-  }
-  return off;
-}
 
 // ------------------------------------------------------------------ setup
 
@@ -479,19 +386,6 @@ __global__ void k_dtable(int fam, DevList Ls, DevList Pl, DevDas das, const int6
 
 // ------------------------------------------------------------------ E0
 
-// Fixed-order block sum of a per-thread double; result valid in thread 0.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) sh[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int k = 0; k < nw; ++k) t += sh[k];
-  return t;
-}
-
 // out[x][y] = sum_A conj(Da[x][A]) Db[y][A]  (one block per (x, y))
 __global__ void k_gram(const double2* __restrict__ Da, const double2* __restrict__ Db, int64_t n, int ny,
                        double2* __restrict__ out) {
@@ -541,22 +435,16 @@ __global__ void k_e0(const double2* __restrict__ g1 /*[1+na*na] row 0 = <c|c>*/,
 // prefetched into registers; one partial per CTA.
 constexpr int GBM = 64, GBN = 64, GBK = 8;
 
-__device__ __forceinline__ void mma_f64(double (&c)[4], const double (&a)[4], const double (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};"
-      : "+d"(c[0]), "+d"(c[1]), "+d"(c[2]), "+d"(c[3])
-      : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(b[0]), "d"(b[1]));
-}
-
 __global__ void __launch_bounds__(256, 1)
 k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M, int64_t N, int Kp,
              const RowInfo* __restrict__ rows, const double* __restrict__ U,
-             const double* __restrict__ eA, const double* __restrict__ E0p, double b, double* __restrict__ partial) {
+             const double* __restrict__ eA, const double* __restrict__ E0p, double b, double* __restrict__ partial,
+             AdjOut adj) {
   __shared__ double sWr[GBM][GBK + 1], sWi[GBM][GBK + 1], sWs[GBM][GBK + 1];
   __shared__ double sDr[GBK][GBN + 1], sDi[GBK][GBN + 1], sDs[GBK][GBN + 1];
   __shared__ double sh[32];
-  // grid: x = row tiles, y = column tiles
-  const int64_t m0 = (int64_t)blockIdx.x * GBM, n0 = (int64_t)blockIdx.y * GBN;
+  // grid: x = row tiles (from row m_base), y = column tiles
+  const int64_t m0 = adj.m_base + (int64_t)blockIdx.x * GBM, n0 = (int64_t)blockIdx.y * GBN;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tq = lane & 3;
   const int wm = warp >> 2, wn = warp & 3;  // warp tile: rows wm*32.., cols wn*16..
@@ -621,13 +509,16 @@ k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64
 
   // epilogue: D_K = E0' - chi(e) - e_A - U[s1,A] - U[s2,A] + U[i1,A] + U[i2,A]
   const double e0p = *E0p;
-  double acc = 0.0;
+  const int64_t mend = adj.T ? adj.m_base + adj.Mc : M;
+  double acc = 0.0, acc2 = 0.0;
+  double rowp[2][2] = {{0.0, 0.0}, {0.0, 0.0}};                 // adjoint: per-row sums of df/dD
+  double colp[2][2] = {{0.0, 0.0}, {0.0, 0.0}};                 // adjoint: per-column sums of df/dD
 #pragma unroll
   for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
     for (int hr = 0; hr < 2; ++hr) {
       const int64_t row = m0 + wm * 32 + mi * 16 + g + hr * 8;
-      if (row >= M) continue;
+      if (row >= mend) continue;
       const RowInfo ri = rows[row];
       const double* U1 = U + (int64_t)ri.s1 * N;
       const double* U2 = U + (int64_t)ri.s2 * N;
@@ -644,9 +535,56 @@ k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64
           const double vr = t1[mi][ni][e] - t2[mi][ni][e];
           const double vi = t3[mi][ni][e] - t1[mi][ni][e] - t2[mi][ni][e];
           const double Dk = base - eA[col] - U1[col] - U2[col] + U3[col] + U4[col];
-          acc += en_term(fma(vr, vr, vi * vi), Dk, b);
+          const double v2 = fma(vr, vr, vi * vi);
+          if (!adj.T) {
+            acc += en_term(v2, Dk, b);
+          } else {
+            const double inv_n = 1.0 / adj.g1[0].x;
+            double gk, hk;
+            en_derivs(v2 * inv_n, Dk, b, gk, hk);
+            const double w = 2.0 * adj.s * inv_n * gk;  // t = s (2/n) g V
+            adj.T[(row - adj.m_base) * N + col] = make_double2(w * vr, w * vi);
+            hk *= adj.s;
+            rowp[mi][hr] += hk;
+            colp[ni][hc] += hk;
+            acc += hk;
+            acc2 += adj.s * gk * v2 * inv_n;
+          }
         }
     }
+  if (adj.T) {
+    // fixed-order per-row / per-column sums over the tile (16 contributors each)
+    __shared__ double sRow[GBM][16], sCol[GBN][16];
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int hr = 0; hr < 2; ++hr) sRow[wm * 32 + mi * 16 + g + hr * 8][wn * 4 + tq] = rowp[mi][hr];
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int hc = 0; hc < 2; ++hc) sCol[wn * 16 + ni * 8 + 2 * tq + hc][wm * 8 + g] = colp[ni][hc];
+    __syncthreads();
+    if (tid < GBM) {
+      double s = 0.0;
+      for (int k = 0; k < 16; ++k) s += sRow[tid][k];
+      const int64_t row = m0 + tid;
+      if (row < mend) adj.Hrow[row * gridDim.y + blockIdx.y] = s;
+    } else if (tid < GBM + GBN) {
+      const int c = tid - GBM;
+      double s = 0.0;
+      for (int k = 0; k < 16; ++k) s += sCol[c][k];
+      const int64_t col = n0 + c;
+      if (col < N) adj.Hcol[((adj.m_base / GBM) + blockIdx.x) * N + col] = s;
+    }
+    double t2s = block_sum(acc2, sh);
+    double ts = block_sum(acc, sh);
+    if (tid == 0) {
+      const int64_t slot = ((adj.m_base / GBM) + blockIdx.x) * gridDim.y + blockIdx.y;
+      adj.scal[2 * slot] = ts;
+      adj.scal[2 * slot + 1] = t2s;
+    }
+    return;
+  }
   double tot = block_sum(acc, sh);
   if (tid == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
 }
@@ -807,46 +745,6 @@ __global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, Dev
   }
   double tot = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
-}
-
-// <A| H - E_O |Psi> for an n_elec-electron string A with no core hole or
-// virtual particle: sum_{tu} f_tu D^{t+u}_A + sum_{t<u in A} s(A;t,u)
-// sum_{v<w} <tu||vw> D^{vw}_{A-t-u}.  Class (0,0) evaluates it on strings of
-// non-reference patterns; the reference solver evaluates it on P (sigma = H c).
-__device__ double2 active_sigma(uint64_t A, const DevList& L11, const DevList& L02, const DevDas& das,
-                                const DevSpace& sp, const int64_t* __restrict__ binom, const double2* __restrict__ DTDU,
-                                const double2* __restrict__ DTU, const double2* __restrict__ X00,
-                                const double2* __restrict__ f) {
-  const int na = sp.n_act, ntp = (int)pairs(na);
-  double2 V = make_double2(0.0, 0.0);
-  int64_t a11 = list_addr(L11, das, binom, A);
-  if (a11 >= 0)
-    for (int t = 0; t < na; ++t)
-      for (int u = 0; u < na; ++u)
-        V = cfma(f[(int64_t)(sp.a0 + t) * sp.n_occ + sp.a0 + u], DTDU[(int64_t)(1 + t * na + u) * L11.n + a11], V);
-  for (uint64_t xu = A; xu; xu &= xu - 1) {
-    const int u = __ffsll((long long)xu) - 1;
-    for (uint64_t xt = A & ((1ull << u) - 1); xt; xt &= xt - 1) {
-      const int t = __ffsll((long long)xt) - 1;
-      const uint64_t B = A & ~(1ull << t) & ~(1ull << u);
-      const int64_t a02 = list_addr(L02, das, binom, B);
-      if (a02 < 0) continue;
-      const double2* Xr = X00 + (int64_t)pair_index(t, u) * ntp;
-      double2 s = make_double2(0.0, 0.0);
-      for (int w = 1; w < na; ++w) {
-        if ((B >> w) & 1) continue;
-        for (int v = 0; v < w; ++v) {
-          if ((B >> v) & 1) continue;
-          const int vw = pair_index(v, w);
-          s = cfma(Xr[vw], DTU[(int64_t)vw * L02.n + a02], s);
-        }
-      }
-      if ((popc_below(B, u) + popc_below(B, t)) & 1) s = make_double2(-s.x, -s.y);
-      V.x += s.x;
-      V.y += s.y;
-    }
-  }
-  return V;
 }
 
 // (0,0), DAS only: V[A] = <A|H - E_O|Psi> for A of a non-reference pattern

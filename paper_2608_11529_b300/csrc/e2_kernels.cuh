@@ -24,7 +24,7 @@ __global__ void k_gram(const double2* Da, const double2* Db, int64_t n, int ny, 
 __global__ void k_e0(const double2* g1, const double2* g2, const double2* f, const double2* X00, DevSpace sp, int ntp,
                      const double* EO, double* E0p, double* E0);
 __global__ void k_class_gemm(const double2* W, const double2* D, int64_t M, int64_t N, int Kp, const RowInfo* rows,
-                             const double* U, const double* eA, const double* E0p, double b, double* partial);
+                             const double* U, const double* eA, const double* E0p, double b, double* partial, AdjOut adj);
 __global__ void k_class22(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
                           const double* G, const double* E0p, double b, int nvb, double* partial);
 __global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, DevSpace sp, const int64_t* binom,
@@ -46,5 +46,40 @@ __global__ void k_peak_dfma(double* out, int iters);
 __global__ void k_reduce(const double* partial, const int64_t* off, const int64_t* cnt, const double2* g1_all,
                          int g1_stride, int n_roots, double* e2c);
 __global__ void k_finalize(const double* e2c, int n_roots, double* E2, const double* E0in, double* E0out);
+
+// adjoint (e2_adjoint.cu)
+__global__ void k_zgemm(int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
+                        const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t ldc, int beta);
+__global__ void k_rowsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);
+__global__ void k_colsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);
+__global__ void k_scalsum(const double* in, int64_t n, double* scal_out);
+__global__ void k_xmarg(const RowInfo* rows, const double* hsum, int64_t M, int nx, double* Nx);
+__global__ void k_amarg(DevList Ls, const double* hA, double* Nt);
+__global__ void k_rowdot(const double2* T, const double2* d, int64_t N, double2* out);
+__global__ void k_fock11(const double2* rowdot, DevSpace sp, double2* Gf);
+__global__ void k_class22_bwd(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
+                              const double* G, const double* E0p, double b, int nvb, double s, const double2* g1,
+                              double* cpart, double* hpart, double* vpart);
+__global__ void k_class22_marg(const double* vpart, int nx_blocks, int nvb, int64_t ncp, DevSpace sp, double* Nx,
+                               double* scal);
+__global__ void k_gather_t(int cls, DevList Lx, DevList L12, DevList L02, DevList L21, DevList L11, DevDas das,
+                           DevSpace sp, const int64_t* binom, const double2* DT, const double2* DTU, const double2* DTD,
+                           const double2* DTDU, const double2* X01, const double2* X10, const double2* X00,
+                           const double2* f, const double* epsh, const double* E0p, double b, double s,
+                           const double2* g1, double2* T, double* H, double* GV);
+__global__ void k_gather_fock(int cls, DevList Lx, DevList Lsrc, DevDas das, DevSpace sp, const int64_t* binom,
+                              const double2* Dsrc, const double2* T, double2* Gf);
+__global__ void k_gather_d1(int cls, DevList Lx, DevList Ltab, DevDas das, DevSpace sp, const int64_t* binom,
+                            const double2* T, int nrow, const double2* f, double2* GD);
+__global__ void k_gather_d2(int cls, DevList Lx, DevList Ltab, DevDas das, DevSpace sp, const int64_t* binom,
+                            const double2* T, int nrow, const double2* X, double2* GD);
+__global__ void k_dscatter(int fam, DevList Ls, DevList Pl, DevDas das, const int64_t* binom, const double2* GD,
+                           double2* Gc);
+__global__ void k_sum2(const double* H, const double* GV, int64_t n, double* scal);
+__global__ void k_e0grad(const double2* g1, const double* scal, DevSpace sp, double2* Gf);
+__global__ void k_nd(DevSpace sp, const double* Nx, const double* Nt, double* Nd);
+__global__ void k_cbar(int64_t np, const double2* Gc, const double* c22, const double2* c, const double2* sigma,
+                       const double* scal, const double* E0p, const double2* g1, double2* out);
+__global__ void k_hbar(DevSpace sp, const double2* Gf, const double* Nd, double2* gh);
 
 }  // namespace e2
