@@ -273,6 +273,22 @@ def run(args):
         roof = {"bound": "alu", "achieved": None, "peak": peak_dfma, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "kernel": KERNEL_OF_CLASS[dom]}
 
+    # forward + backward (dE2/dh, dE2/dc) against forward alone
+    fwdbwd = None
+    if not args.no_backward:
+        for _ in range(2):
+            plan.backward(want_B=True, want_lambda=True, **t)
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.steps):
+            plan.backward(want_B=True, want_lambda=True, **t)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1) / args.steps
+        fwdbwd = {"ms_fwd": ms, "ms_bwd": bms, "ratio_fwd_bwd_over_fwd": (ms + bms) / ms,
+                  "gradients": "dE2/dh, dE2/dB (all factors, Hermitian), dE2/dc, dE2/dlambda; V recomputed"}
+
     # end to end through the public API: pinned host inputs -> device, forward, E2 -> host
     e2e = None
     if not args.no_e2e:
@@ -317,7 +333,8 @@ def run(args):
                            "l2": "inputs larger than L2: the 456 MB factor set is re-read every step",
                            "E2": float(E2.cpu()[0]), "E0": float(E0.cpu()[0]),
                            "class_ms": {CLASS_NAMES[k]: ktime[k] for k in present}},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches * args.steps,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fwd_bwd": fwdbwd,
+                "gpu_launches": launches * args.steps,
                 "clocks": clk, "fp64_peaks_tflops": {"dmma": peak_dmma, "dfma": peak_dfma}}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -334,6 +351,7 @@ def main():
     ap.add_argument("--config", default="cfg2", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     ap.add_argument("--factors", type=int, default=0,
                     help="override the Coulomb factor count (extra set = half); a small-memory variant with the "

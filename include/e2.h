@@ -143,6 +143,31 @@ E2_API e2_status e2_workspace_size(const e2_problem* prob, size_t* bytes);
 E2_API e2_status e2_forward(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
                      void* stream, double* E2, double* E2_class, double* E0);
 
+/* Batches (no counterpart in the paper: a throughput device).  Several
+ * planned problems -- different Hamiltonians, root counts, frozen cutoffs --
+ * evaluated together: their dense-class tiles (all jobs, all roots) run in
+ * ONE persistent launch that takes tiles from an integer work counter,
+ * longest contraction first; the other classes and the reductions follow per
+ * job.  Results equal those of e2_forward job by job (same partial slots, same
+ * fixed reduction order).
+ *   e2_batch_create   host only; the problems must outlive the batch.
+ *   e2_batch_prepare  uploads plan tables and the work list into `workspace`
+ *                     and synchronises `stream`; call it once per workspace,
+ *                     outside stream capture.
+ *   e2_batch_forward  kernels and memsets only (no host synchronisation, no
+ *                     host-to-device copies): it can be captured in a CUDA
+ *                     graph and replayed.  `workspace` must be the prepared one.
+ *                     inputs [n_jobs]; E2 [n_jobs] device pointers ([n_roots_j]
+ *                     each); E2_class [n_jobs] or NULL. */
+typedef struct e2_batch e2_batch;
+E2_API e2_status e2_batch_create(e2_problem* const* jobs, int n_jobs, e2_batch** out);
+E2_API e2_status e2_batch_destroy(e2_batch* batch);
+E2_API e2_status e2_batch_workspace_size(const e2_batch* batch, size_t* bytes);
+E2_API e2_status e2_batch_prepare(e2_batch* batch, void* workspace, size_t workspace_bytes, void* stream);
+E2_API e2_status e2_batch_forward(e2_batch* batch, const e2_inputs* inputs, void* workspace, size_t workspace_bytes,
+                                  void* stream, double* const* E2, double* const* E2_class);
+E2_API e2_status e2_batch_launch_count(const e2_batch* batch, int64_t* n);
+
 /* Adjoint of e2_forward (gradients are not in the paper; they follow from
  * differentiating Eq. pt2 with E0 = <Psi|H|Psi>/<Psi|Psi>).  For
  * F = sum_m seed[m] E2_m it returns, for complex inputs z, dF/dRe z + i dF/dIm z:
@@ -150,6 +175,10 @@ E2_API e2_status e2_forward(e2_problem* prob, const e2_inputs* in, void* workspa
  *                               response one-particle density), or NULL
  *   g_c  device [n_roots][N_P]  gradient for each root's coefficients, or NULL
  *                               (orthogonal to c: E2 does not depend on |c|)
+ *   g_Bc device [L_coulomb][n][n], g_Bx device [L_extra][n][n]
+ *                               factor gradients, Hermitian-projected, or NULL
+ *   dE2_dlambda device [1]      dF/dlambda: the Gaunt / Breit share of the
+ *                               correlation energy to first order, or NULL
  *   seed host [n_roots]
  * V is recomputed (never stored whole): the dense classes run in row chunks
  * whose weighted amplitudes fit a 2 GiB buffer.  Enqueues on `stream`;
@@ -157,7 +186,8 @@ E2_API e2_status e2_forward(e2_problem* prob, const e2_inputs* in, void* workspa
  * e2_forward and reference-solver layouts). */
 E2_API e2_status e2_backward_workspace_size(const e2_problem* prob, size_t* bytes);
 E2_API e2_status e2_backward(e2_problem* prob, const e2_inputs* in, const double* seed, void* workspace,
-                             size_t workspace_bytes, void* stream, double* g_h, double* g_c);
+                             size_t workspace_bytes, void* stream, double* g_h, double* g_c, double* g_Bc,
+                             double* g_Bx, double* dE2_dlambda);
 
 /* Reference states: the n_roots lowest eigenvectors of P H P (the CASCI /
  * DAS-CI reference of Sec. 2.2-2.3, Eq. zeroh first term), by block Davidson

@@ -60,8 +60,21 @@ def load():
         L.e2_backward_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
         L.e2_backward_workspace_size.restype = C.c_int
         L.e2_backward.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
-                                  C.c_void_p, C.c_void_p]
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.e2_backward.restype = C.c_int
+        L.e2_batch_create.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]
+        L.e2_batch_create.restype = C.c_int
+        L.e2_batch_destroy.argtypes = [C.c_void_p]
+        L.e2_batch_destroy.restype = C.c_int
+        L.e2_batch_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
+        L.e2_batch_workspace_size.restype = C.c_int
+        L.e2_batch_prepare.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.e2_batch_prepare.restype = C.c_int
+        L.e2_batch_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p,
+                                       C.c_void_p]
+        L.e2_batch_forward.restype = C.c_int
+        L.e2_batch_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
+        L.e2_batch_launch_count.restype = C.c_int
         L.e2_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
         L.e2_launch_count.restype = C.c_int
         L.e2_profile_events.argtypes = [C.c_void_p, C.c_void_p]
@@ -154,21 +167,29 @@ class E2Problem:
             self._ws = raw[off:off + need]
         return self._ws
 
-    def backward(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, seed=None, want_h=True, want_c=True, stream=None):
-        """Gradient of sum_m seed[m] E2_m: returns (g_h [n, n] or None,
-        g_c [roots, N_P] or None) as complex128 CUDA tensors (dE/dRe + i dE/dIm;
-        g_h Hermitian-projected)."""
+    def backward(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, seed=None, want_h=True, want_c=True, want_B=False,
+                 want_lambda=False, stream=None):
+        """Gradient of sum_m seed[m] E2_m: returns (g_h [n, n], g_c [roots, N_P],
+        g_Bc [Lc, n, n], g_Bx [Lx, n, n], dE2/dlambda [1]) as CUDA tensors (None
+        where not requested); complex gradients are dE/dRe + i dE/dIm, h and B
+        Hermitian-projected."""
         import torch
         dev = c.device
         ws = self.workspace(dev, backward=True)
         seed = np.ascontiguousarray(np.ones(self.n_roots) if seed is None else seed, np.float64)
         gh = torch.empty(self.n, self.n, dtype=torch.complex128, device=dev) if want_h else None
         gc = torch.empty(self.n_roots, self.n_p, dtype=torch.complex128, device=dev) if want_c else None
+        gbc = torch.empty(B_c.shape, dtype=torch.complex128, device=dev) if want_B else None
+        gbx = torch.empty(B_x.shape, dtype=torch.complex128, device=dev) if (want_B and self.L_extra) else None
+        dl = torch.zeros(1, dtype=torch.float64, device=dev) if want_lambda else None
         inp = _Inputs(h.data_ptr(), B_c.data_ptr(), B_x.data_ptr() if self.L_extra else None,
                       w_x.data_ptr() if self.L_extra else None, float(lam), c.data_ptr())
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        ptr = lambda x: x.data_ptr() if x is not None else None
         _check(load().e2_backward(self._h, C.byref(inp), seed.ctypes.data_as(C.c_void_p), ws.data_ptr(), ws.numel(),
-                                  C.c_void_p(s), gh.data_ptr() if want_h else None, gc.data_ptr() if want_c else None))
+                                  C.c_void_p(s), ptr(gh), ptr(gc), ptr(gbc), ptr(gbx), ptr(dl)))
+        if want_B or want_lambda:
+            return gh, gc, gbc, gbx, dl
         return gh, gc
 
     def reference_solve(self, h, B_c, X0, B_x=None, w_x=None, lam=1.0, tol=1e-10, max_iter=300, stream=None):
@@ -248,6 +269,66 @@ class E2Problem:
         _check(load().e2_forward(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s), E2.data_ptr(),
                                  E2c.data_ptr(), E0.data_ptr()))
         return E2, E2c, E0
+
+
+class E2Batch:
+    """Several planned problems evaluated with one persistent launch for their
+    dense classes (e2_batch_*).  forward() enqueues kernels only, so it can be
+    captured in a CUDA graph after prepare()."""
+
+    def __init__(self, plans):
+        L = load()
+        self.plans = list(plans)
+        arr = (C.c_void_p * len(self.plans))(*[p._h for p in self.plans])
+        h = C.c_void_p()
+        _check(L.e2_batch_create(arr, len(self.plans), C.byref(h)))
+        self._h = h
+        ws = C.c_size_t()
+        _check(L.e2_batch_workspace_size(self._h, C.byref(ws)))
+        self.workspace_bytes = int(ws.value)
+        self._ws = None
+
+    def __del__(self):
+        try:
+            if self._h:
+                load().e2_batch_destroy(self._h)
+                self._h = None
+        except Exception:
+            pass
+
+    def prepare(self, device, stream=None):
+        import torch
+        raw = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=device)
+        off = (-raw.data_ptr()) % 256
+        self._ws_raw = raw
+        self._ws = raw[off:off + self.workspace_bytes]
+        s = torch.cuda.current_stream(device).cuda_stream if stream is None else stream
+        _check(load().e2_batch_prepare(self._h, self._ws.data_ptr(), self._ws.numel(), C.c_void_p(s)))
+        self.outputs = [(torch.empty(p.n_roots, dtype=torch.float64, device=device),
+                         torch.empty(p.n_roots, NCLASS, dtype=torch.float64, device=device)) for p in self.plans]
+
+    def forward(self, inputs, stream=None):
+        """inputs: one dict per job (as from device_inputs).  Returns the
+        per-job (E2, E2_class) tensors (reused between calls)."""
+        import torch
+        dev = self._ws.device
+        self._keep = []
+        arr = (_Inputs * len(self.plans))()
+        for k, (p, t) in enumerate(zip(self.plans, inputs)):
+            arr[k] = _Inputs(t["h"].data_ptr(), t["B_c"].data_ptr(), t["B_x"].data_ptr() if p.L_extra else None,
+                             t["w_x"].data_ptr() if p.L_extra else None, float(t["lam"]), t["c"].data_ptr())
+        e2p = (C.c_void_p * len(self.plans))(*[o[0].data_ptr() for o in self.outputs])
+        e2c = (C.c_void_p * len(self.plans))(*[o[1].data_ptr() for o in self.outputs])
+        self._keep = [arr, e2p, e2c]
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        _check(load().e2_batch_forward(self._h, C.cast(arr, C.c_void_p), self._ws.data_ptr(), self._ws.numel(),
+                                       C.c_void_p(s), C.cast(e2p, C.c_void_p), C.cast(e2c, C.c_void_p)))
+        return self.outputs
+
+    def launch_count(self):
+        n = C.c_int64()
+        _check(load().e2_batch_launch_count(self._h, C.byref(n)))
+        return int(n.value)
 
 
 def fp64_peak(device="cuda"):

@@ -49,6 +49,8 @@ struct Layout {
 
 }  // namespace
 
+struct e2_batch;
+
 struct e2_problem {
   e2_desc d;
   std::vector<uint8_t> frozen;
@@ -95,6 +97,10 @@ struct e2_problem {
   int64_t chunk_rows[E2_NCLASS];     // dense-class rows per adjoint chunk
   size_t o_gD, o_bT, o_bHrow, o_bHcol, o_bScalT, o_bHsum, o_bHA, o_bRowdot;
   size_t o_bGT, o_bGH, o_bGV, o_bC22p, o_bH22p, o_bV22, o_bC22, o_bGc, o_bSig, o_bGf, o_bNx, o_bNt, o_bNd, o_bScal;
+  // factor gradient
+  int64_t npair;
+  size_t o_bGW[E2_NCLASS], o_bHm, o_bHocc, o_bZ, o_bZs, o_bGe, o_bGea, o_bNtt, o_bGG, o_bGt, o_bGh, o_bTsh;
+  size_t o_bGX01, o_bGX10, o_bGX00, o_bR22, o_bHs22, o_bP22, o_bG22c, o_bGg22, o_bCs, o_bGB, o_bFtr, o_bGw, o_bRg;
   size_t bwd_bytes;
 };
 
@@ -386,6 +392,53 @@ e2_status build_plan(e2_problem* P) {
     P->o_bNt = ws.take(8 * (size_t)std::max(P->na, 1));
     P->o_bNd = ws.take(8 * (size_t)P->n);
     P->o_bScal = ws.take(16);
+    // factor gradient
+    const int64_t npair = (int64_t)P->n * P->nocc;
+    P->npair = npair;
+    size_t hm = 8, hocc = 8, zz = 8, tsh = 16;
+    for (int c = 0; c < E2_NCLASS; ++c) P->o_bGW[c] = 0;
+    for (int c : {2, 5, 7, 4, 6}) {
+      const int64_t Mc = P->M[c], Nc = lsize(c);
+      if (Mc == 0 || Nc == 0) continue;
+      P->o_bGW[c] = ws.take(16 * (size_t)Mc * P->Kp[c]);
+      hm = std::max(hm, (size_t)8 * P->chunk_rows[c] * Nc);
+      hocc = std::max(hocc, (size_t)8 * Mc * P->na);
+      zz = std::max(zz, (size_t)8 * Mc * P->nx);
+    }
+    const int64_t M22 = P->ncp * P->nvp;
+    hocc = std::max(hocc, (size_t)8 * std::max<int64_t>(M22, 1) * P->na);
+    zz = std::max(zz, (size_t)8 * std::max<int64_t>(M22, 1) * P->nx);
+    for (int c : {1, 3, 0})
+      if (P->list_of[c] >= 0) {
+        hocc = std::max(hocc, (size_t)8 * P->M[c] * P->na);
+        zz = std::max(zz, (size_t)8 * P->M[c] * P->nx);
+      }
+    tsh = std::max<size_t>(tsh, 16 * (size_t)std::max<int64_t>(P->nvc, 1) * std::max<int64_t>(lsize(2), 1));
+    tsh = std::max<size_t>(tsh, 16 * (size_t)std::max<int64_t>(P->ncc, 1) * std::max<int64_t>(lsize(5), 1));
+    P->o_bHm = ws.take(hm);
+    P->o_bHocc = ws.take(hocc);
+    P->o_bZ = ws.take(zz);
+    P->o_bZs = ws.take(zz);
+    P->o_bRg = ws.take(sizeof(RowInfo) * (size_t)std::max<int64_t>(std::max(P->nvc, P->ncc), 1));
+    P->o_bGe = ws.take(8 * (size_t)std::max(P->nx, 1) * std::max(P->nx, 1));
+    P->o_bGea = ws.take(8 * (size_t)std::max(P->nx, 1) * std::max(P->na, 1));
+    P->o_bNtt = ws.take(8 * (size_t)P->na * P->na);
+    P->o_bGG = ws.take(8 * (size_t)P->n * P->n);
+    P->o_bGt = ws.take(16 * (size_t)npair * npair);
+    P->o_bGh = ws.take(16 * (size_t)npair * npair);
+    P->o_bTsh = ws.take(tsh);
+    P->o_bGX01 = ws.take(16 * (size_t)std::max<int64_t>((int64_t)P->nvc * P->na * P->ntp, 1));
+    P->o_bGX10 = ws.take(16 * (size_t)std::max<int64_t>((int64_t)P->ncc * P->ntp * P->na, 1));
+    P->o_bGX00 = ws.take(16 * (size_t)std::max<int64_t>((int64_t)P->ntp * P->ntp, 1));
+    P->o_bR22 = ws.take(sizeof(RowInfo) * (size_t)std::max<int64_t>(M22, 1));
+    P->o_bHs22 = ws.take(8 * (size_t)std::max<int64_t>(M22, 1));
+    P->o_bP22 = ws.take(8 * (size_t)std::max<int64_t>(M22, 1));
+    P->o_bG22c = ws.take(16 * (size_t)std::max<int64_t>(M22, 1));
+    P->o_bGg22 = ws.take(16 * (size_t)std::max<int64_t>(M22, 1));
+    P->o_bCs = ws.take(16 * (size_t)Lt * npair);
+    P->o_bGB = ws.take(16 * (size_t)Lt * P->n * P->n);
+    P->o_bFtr = ws.take(16 * (size_t)std::max(Lt, 1));
+    P->o_bGw = ws.take(8 * (size_t)std::max(Lt, 1));
     P->bwd_bytes = ws.top;
   }
 
@@ -550,11 +603,12 @@ void build_tables(const e2_problem* P, unsigned char* ws, cudaStream_t st, const
 // Everything that depends only on the Hamiltonian and the partition:
 // binomials, compact factors, G, eps^, f, E_O, string lists with e_A and U,
 // and the active two-electron block <tu||vw>.
-e2_status setup_common(e2_problem* P, const e2_inputs* in, unsigned char* ws, cudaStream_t st) {
+e2_status setup_common(e2_problem* P, const e2_inputs* in, unsigned char* ws, cudaStream_t st, bool upload = true) {
   const e2_desc& d = P->d;
   const int n = P->n, nocc = P->nocc, Lt = d.L_coulomb + d.L_extra;
   Ctx X = ctx(P, ws);
-  if (cudaMemcpyAsync(ws + P->o_plan, P->plan_blob.data(), P->plan_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+  if (upload &&
+      cudaMemcpyAsync(ws + P->o_plan, P->plan_blob.data(), P->plan_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return E2_ERR_CUDA;
   (k_binom<<<1, 256, 0, st>>>((int64_t*)(ws + P->o_binom)), ++g_launches);
   {
@@ -619,6 +673,56 @@ void prepare_root(e2_problem* P, unsigned char* ws, cudaStream_t st, const doubl
   else cudaMemsetAsync(g2, 0, 16 * (size_t)std::max(P->ntp * P->ntp, 1), st);
   (k_e0<<<1, 256, 0, st>>>(g1, g2, X.f, (const double2*)(ws + P->o_X00), X.sp, P->ntp, X.EO, X.E0p + r, X.E0d + r),
    ++g_launches);
+}
+
+// Classes (2,2), (0,1), (1,0), (0,0) of root r (their partial slots).
+template <class Mark>
+void launch_sparse_classes(e2_problem* P, unsigned char* ws, cudaStream_t st, int r, const double2* c, Mark mark) {
+  Ctx X = ctx(P, ws);
+  Tabs T = tables(P, ws, r);
+  DevList Lc[E2_NCLASS];
+  for (int k = 0; k < E2_NCLASS; ++k) Lc[k] = dev_list(P, P->list_of[k], ws);
+  const double b = P->d.level_shift_b;
+  double* part = (double*)(ws + P->o_part);
+  auto poff = [&](int cls) { return part + P->part_off[r * E2_NCLASS + cls]; };
+  if (P->part_cnt[8] > 0) {
+    const DevList& L = Lc[8];
+    dim3 grid(blocks(L.n), (unsigned)(P->nvb * (P->nvb + 1) / 2), (unsigned)P->ncp);
+    mark(8, 0);
+    (k_class22<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb,
+                                    poff(8)), ++g_launches);
+    mark(8, 1);
+  }
+  if (P->part_cnt[1] > 0) {
+    dim3 grid(blocks(Lc[1].n), (unsigned)P->nvc);
+    mark(1, 0);
+    (k_class01<<<grid, 256, 0, st>>>(Lc[1], Lc[5], Lc[2], P->das, X.sp, X.binom, T.DT, T.DTU,
+                                    (const double2*)(ws + P->o_X01), X.f, X.epsh, X.E0p + r, b, poff(1)), ++g_launches);
+    mark(1, 1);
+  }
+  if (P->part_cnt[3] > 0) {
+    dim3 grid(blocks(Lc[3].n), (unsigned)P->ncc);
+    mark(3, 0);
+    (k_class10<<<grid, 256, 0, st>>>(Lc[3], Lc[7], Lc[5], P->das, X.sp, X.binom, T.DTD, T.DT,
+                                    (const double2*)(ws + P->o_X10), X.f, X.epsh, X.E0p + r, b, poff(3)), ++g_launches);
+    mark(3, 1);
+  }
+  if (P->part_cnt[0] > 0) {
+    mark(0, 0);
+    (k_class00<<<blocks(Lc[0].n), 256, 0, st>>>(Lc[0], Lc[4], Lc[2], P->das, X.sp, X.binom, T.DTDU, T.DTU,
+                                               (const double2*)(ws + P->o_X00), X.f, X.E0p + r, b, poff(0)), ++g_launches);
+    mark(0, 1);
+  }
+}
+
+// E2_class and E2 of every root from the partial slots (fixed order).
+void launch_reduce(e2_problem* P, unsigned char* ws, cudaStream_t st, double* E2, double* E2_class, double* E0) {
+  const int R = P->d.n_roots;
+  double* e2c = E2_class ? E2_class : (double*)(ws + P->o_e2c);
+  (k_reduce<<<R * E2_NCLASS, 256, 0, st>>>((const double*)(ws + P->o_part), (const int64_t*)(ws + P->o_partoff),
+                                           (const int64_t*)(ws + P->o_partcnt), (const double2*)(ws + P->o_g1),
+                                           (int)(P->g_stride / 16), R, e2c), ++g_launches);
+  (k_finalize<<<1, 32, 0, st>>>(e2c, R, E2, (const double*)(ws + P->o_E0), E0), ++g_launches);
 }
 
 }  // namespace
@@ -751,34 +855,7 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
                                          (const RowInfo*)(ws + P->o_rows[cls]), L.U, L.eA, X.E0p + r, b, poff(cls), AdjOut{}), ++g_launches);
       mark(cls, 1);
     }
-    if (P->part_cnt[8] > 0) {
-      const DevList& L = Lc[8];
-      dim3 grid(blocks(L.n), (unsigned)(P->nvb * (P->nvb + 1) / 2), (unsigned)P->ncp);
-      mark(8, 0);
-      (k_class22<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb,
-                                      poff(8)), ++g_launches);
-      mark(8, 1);
-    }
-    if (P->part_cnt[1] > 0) {
-      dim3 grid(blocks(Lc[1].n), (unsigned)P->nvc);
-      mark(1, 0);
-      (k_class01<<<grid, 256, 0, st>>>(Lc[1], Lc[5], Lc[2], P->das, X.sp, X.binom, T.DT, T.DTU,
-                                      (const double2*)(ws + P->o_X01), X.f, X.epsh, X.E0p + r, b, poff(1)), ++g_launches);
-      mark(1, 1);
-    }
-    if (P->part_cnt[3] > 0) {
-      dim3 grid(blocks(Lc[3].n), (unsigned)P->ncc);
-      mark(3, 0);
-      (k_class10<<<grid, 256, 0, st>>>(Lc[3], Lc[7], Lc[5], P->das, X.sp, X.binom, T.DTD, T.DT,
-                                      (const double2*)(ws + P->o_X10), X.f, X.epsh, X.E0p + r, b, poff(3)), ++g_launches);
-      mark(3, 1);
-    }
-    if (P->part_cnt[0] > 0) {
-      mark(0, 0);
-      (k_class00<<<blocks(Lc[0].n), 256, 0, st>>>(Lc[0], Lc[4], Lc[2], P->das, X.sp, X.binom, T.DTDU, T.DTU,
-                                                 (const double2*)(ws + P->o_X00), X.f, X.E0p + r, b, poff(0)), ++g_launches);
-      mark(0, 1);
-    }
+    launch_sparse_classes(P, ws, st, r, c, mark);
   }
   double* e2c = E2_class ? E2_class : (double*)(ws + P->o_e2c);
   (k_reduce<<<R * E2_NCLASS, 256, 0, st>>>(part, (const int64_t*)(ws + P->o_partoff), (const int64_t*)(ws + P->o_partcnt),
@@ -836,6 +913,170 @@ e2_status e2_fp64_peak(void* workspace, size_t workspace_bytes, void* stream_, d
   return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
 }
 
+
+// ------------------------------------------------------------------ batches
+
+struct e2_batch {
+  std::vector<e2_problem*> jobs;
+  std::vector<size_t> off;          // workspace offset of each job's forward layout
+  size_t o_jobs = 0, o_items = 0, o_counter = 0, bytes = 0;
+  std::vector<GemmJob> gj;          // absolute pointers, built by e2_batch_prepare
+  std::vector<WorkItem> items;
+  int64_t n_items = 0;
+  const void* prepared = nullptr;
+  int64_t launches = 0;
+};
+
+e2_status e2_batch_create(e2_problem* const* jobs, int n_jobs, e2_batch** out) {
+  if (!out) return E2_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!jobs || n_jobs < 1) return E2_ERR_INVALID_ARG;
+  e2_batch* B = new (std::nothrow) e2_batch();
+  if (!B) return E2_ERR_INVALID_ARG;
+  Layout ws;
+  int64_t njc = 0;
+  for (int j = 0; j < n_jobs; ++j) {
+    if (!jobs[j]) {
+      delete B;
+      return E2_ERR_INVALID_ARG;
+    }
+    B->jobs.push_back(jobs[j]);
+    B->off.push_back(ws.take(jobs[j]->ws_bytes));
+    for (int c : {2, 5, 7, 4, 6})
+      if (jobs[j]->part_cnt[c] > 0) {
+        njc += jobs[j]->d.n_roots;
+        B->n_items += jobs[j]->part_cnt[c] * jobs[j]->d.n_roots;
+      }
+  }
+  if (B->n_items >= (int64_t)1 << 31) {
+    delete B;
+    return E2_ERR_UNSUPPORTED;
+  }
+  B->o_jobs = ws.take(sizeof(GemmJob) * std::max<int64_t>(njc, 1));
+  B->o_items = ws.take(sizeof(WorkItem) * std::max<int64_t>(B->n_items, 1));
+  B->o_counter = ws.take(sizeof(int));
+  B->bytes = ws.top;
+  *out = B;
+  return E2_OK;
+}
+
+e2_status e2_batch_destroy(e2_batch* B) {
+  delete B;
+  return E2_OK;
+}
+
+e2_status e2_batch_workspace_size(const e2_batch* B, size_t* bytes) {
+  if (!B || !bytes) return E2_ERR_INVALID_ARG;
+  *bytes = B->bytes;
+  return E2_OK;
+}
+
+e2_status e2_batch_prepare(e2_batch* B, void* workspace, size_t workspace_bytes, void* stream_) {
+  if (!B) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < B->bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  B->gj.clear();
+  B->items.clear();
+  struct Key {
+    int kp;
+    int job;
+  };
+  std::vector<Key> order;
+  for (size_t j = 0; j < B->jobs.size(); ++j) {
+    e2_problem* P = B->jobs[j];
+    unsigned char* w = ws + B->off[j];
+    for (int c : {2, 5, 7, 4, 6}) {
+      if (P->part_cnt[c] == 0) continue;
+      const DevList L = dev_list(P, P->list_of[c], w);
+      for (int r = 0; r < P->d.n_roots; ++r) {
+        Tabs T = tables(P, w, r);
+        const double2* Dfor[E2_NCLASS] = {nullptr, nullptr, T.DTU, nullptr, T.DTDU, T.DT, T.DTDUD, T.DTD, nullptr};
+        GemmJob g;
+        g.W = (const double2*)(w + P->o_W[c]);
+        g.D = Dfor[c];
+        g.M = P->M[c];
+        g.N = L.n;
+        g.Kp = P->Kp[c];
+        g.rows = (const RowInfo*)(w + P->o_rows[c]);
+        g.U = L.U;
+        g.eA = L.eA;
+        g.E0p = (const double*)(w + P->o_E0p) + r;
+        g.b = P->d.level_shift_b;
+        g.partial = (double*)(w + P->o_part) + P->part_off[r * E2_NCLASS + c];
+        order.push_back({g.Kp, (int)B->gj.size()});
+        B->gj.push_back(g);
+      }
+    }
+    if (cudaMemcpyAsync(w + P->o_plan, P->plan_blob.data(), P->plan_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+      return E2_ERR_CUDA;
+  }
+  // longest first: contraction length, then job order
+  std::stable_sort(order.begin(), order.end(), [](const Key& x, const Key& y) { return x.kp > y.kp; });
+  for (const Key& k : order) {
+    const GemmJob& g = B->gj[k.job];
+    const int ntm = (int)((g.M + 63) / 64), ntn = (int)((g.N + 63) / 64);
+    for (int tm = 0; tm < ntm; ++tm)
+      for (int tn = 0; tn < ntn; ++tn) B->items.push_back({k.job, tm, tn});
+  }
+  if ((int64_t)B->items.size() != B->n_items) return E2_ERR_SHAPE;
+  if (cudaMemcpyAsync(ws + B->o_jobs, B->gj.data(), sizeof(GemmJob) * B->gj.size(), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(ws + B->o_items, B->items.data(), sizeof(WorkItem) * B->items.size(), cudaMemcpyHostToDevice,
+                      st) != cudaSuccess)
+    return E2_ERR_CUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return E2_ERR_CUDA;
+  B->prepared = workspace;
+  return E2_OK;
+}
+
+e2_status e2_batch_forward(e2_batch* B, const e2_inputs* inputs, void* workspace, size_t workspace_bytes,
+                           void* stream_, double* const* E2, double* const* E2_class) {
+  if (!B || !inputs || !E2) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < B->bytes || workspace != B->prepared) return E2_ERR_WORKSPACE;
+  for (size_t j = 0; j < B->jobs.size(); ++j) {
+    const e2_inputs* in = inputs + j;
+    if (!E2[j] || !in->h || !in->B_c || !in->c || !std::isfinite(in->lambda)) return E2_ERR_INVALID_ARG;
+    if (B->jobs[j]->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  cudaGetLastError();
+  g_launches = 0;
+  for (size_t j = 0; j < B->jobs.size(); ++j) {
+    e2_problem* P = B->jobs[j];
+    unsigned char* w = ws + B->off[j];
+    setup_common(P, inputs + j, w, st, false);
+    setup_classes(P, w, st);
+    for (int r = 0; r < P->d.n_roots; ++r)
+      prepare_root(P, w, st, (const double2*)inputs[j].c + (int64_t)r * P->lists[P->listP].n, r);
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaMemsetAsync(ws + B->o_counter, 0, sizeof(int), st);
+  if (B->n_items > 0)
+    (k_batch_gemm<<<std::max(sms, 1), 256, 0, st>>>((const GemmJob*)(ws + B->o_jobs), (const WorkItem*)(ws + B->o_items),
+                                                     (int)B->n_items, (int*)(ws + B->o_counter)), ++g_launches);
+  auto nomark = [](int, int) {};
+  for (size_t j = 0; j < B->jobs.size(); ++j) {
+    e2_problem* P = B->jobs[j];
+    unsigned char* w = ws + B->off[j];
+    for (int r = 0; r < P->d.n_roots; ++r)
+      launch_sparse_classes(P, w, st, r, (const double2*)inputs[j].c + (int64_t)r * P->lists[P->listP].n, nomark);
+    launch_reduce(P, w, st, E2[j], E2_class ? E2_class[j] : nullptr, nullptr);
+  }
+  B->launches = g_launches;
+  if (cudaGetLastError() != cudaSuccess) return E2_ERR_CUDA;
+  return E2_OK;
+}
+
+e2_status e2_batch_launch_count(const e2_batch* B, int64_t* n) {
+  if (!B || !n) return E2_ERR_INVALID_ARG;
+  *n = B->launches;
+  return E2_OK;
+}
+
 e2_status e2_backward_workspace_size(const e2_problem* P, size_t* bytes) {
   if (!P || !bytes) return E2_ERR_INVALID_ARG;
   *bytes = P->bwd_bytes;
@@ -843,7 +1084,7 @@ e2_status e2_backward_workspace_size(const e2_problem* P, size_t* bytes) {
 }
 
 e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, void* workspace, size_t workspace_bytes,
-                      void* stream_, double* g_h, double* g_c) {
+                      void* stream_, double* g_h, double* g_c, double* g_Bc, double* g_Bx, double* dE2_dlambda) {
   if (!P || !in || !seed || !in->h || !in->B_c || !in->c) return E2_ERR_INVALID_ARG;
   if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
   if (!std::isfinite(in->lambda)) return E2_ERR_INVALID_ARG;
@@ -872,6 +1113,31 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
   cudaMemsetAsync(Gf, 0, 16 * (size_t)P->n * P->nocc, st);
   cudaMemsetAsync(Nx, 0, 8 * (size_t)(P->nx + 1), st);
   cudaMemsetAsync(Nt, 0, 8 * (size_t)std::max(na, 1), st);
+  const bool want_B = g_Bc || g_Bx || dE2_dlambda;
+  const int nx = P->nx;
+  const int64_t npair = P->npair;
+  double* Ge = (double*)B(P->o_bGe);
+  double* Gea = (double*)B(P->o_bGea);
+  double* Ntt = (double*)B(P->o_bNtt);
+  double2* Gt = (double2*)B(P->o_bGt);
+  double* Hocc = (double*)B(P->o_bHocc);
+  double* Zm = (double*)B(P->o_bZ);
+  double* Zs = (double*)B(P->o_bZs);
+  if (want_B) {
+    cudaMemsetAsync(Ge, 0, 8 * (size_t)std::max(nx, 1) * std::max(nx, 1), st);
+    cudaMemsetAsync(Gea, 0, 8 * (size_t)std::max(nx, 1) * std::max(na, 1), st);
+    cudaMemsetAsync(Ntt, 0, 8 * (size_t)na * na, st);
+    cudaMemsetAsync(Gt, 0, 16 * (size_t)npair * npair, st);
+  }
+  // denominators of rows with external indices: Ge += Z^T diag(hsum) Z, Gea += Z^T Hocc
+  auto zpair = [&](const RowInfo* rows, int64_t M, const double* hs, const double* hocc) {
+    (k_zmat<<<blocks(M * nx), 256, 0, st>>>(rows, M, nx, Zm), ++g_launches);
+    (k_zscale<<<blocks(M * nx), 256, 0, st>>>(Zm, hs, M, nx, Zs), ++g_launches);
+    dim3 g1((unsigned)((nx + 63) / 64), (unsigned)((nx + 63) / 64));
+    (k_dgemm<<<g1, 256, 0, st>>>(nx, nx, M, Zm, 1, nx, Zs, nx, 1, Ge, nx, 1), ++g_launches);
+    dim3 g2((unsigned)((nx + 63) / 64), (unsigned)((na + 63) / 64));
+    (k_dgemm<<<g2, 256, 0, st>>>(nx, na, M, Zm, 1, nx, hocc, na, 1, Gea, na, 1), ++g_launches);
+  };
   const bool on[E2_NCLASS] = {P->part_cnt[0] > 0, P->part_cnt[1] > 0, P->part_cnt[2] > 0, P->part_cnt[3] > 0,
                               P->part_cnt[4] > 0, P->part_cnt[5] > 0, P->part_cnt[6] > 0, P->part_cnt[7] > 0,
                               P->part_cnt[8] > 0};
@@ -891,6 +1157,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
     cudaMemsetAsync(ws + P->o_gD, 0, P->d_stride, st);
     cudaMemsetAsync(Gc, 0, 16 * (size_t)LP.n, st);
     cudaMemsetAsync(scal, 0, 16, st);
+    if (want_B) cudaMemsetAsync(B(P->o_bGX00), 0, 16 * (size_t)std::max(P->ntp * P->ntp, 1), st);
     double* hsum = (double*)B(P->o_bHsum);
     double* hA = (double*)B(P->o_bHA);
     // dense classes: amplitudes in row chunks, Gamma_D += W^T conj(T)
@@ -904,8 +1171,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       const double2* W = (const double2*)(ws + P->o_W[cls]);
       for (int64_t m0 = 0; m0 < M; m0 += P->chunk_rows[cls]) {
         const int64_t Mc = std::min<int64_t>(P->chunk_rows[cls], M - m0);
-        AdjOut adj{(double2*)B(P->o_bT), (double*)B(P->o_bHrow), (double*)B(P->o_bHcol), (double*)B(P->o_bScalT),
-                   m0, Mc, s, g1};
+        AdjOut adj{(double2*)B(P->o_bT), want_B ? (double*)B(P->o_bHm) : nullptr, (double*)B(P->o_bHrow),
+                   (double*)B(P->o_bHcol), (double*)B(P->o_bScalT), m0, Mc, s, g1};
         dim3 grid((unsigned)((Mc + 63) / 64), (unsigned)ct);
         (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
                                             L.eA, X.E0p + r, b, nullptr, adj), ++g_launches);
@@ -913,6 +1180,12 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         (k_zgemm<<<gz, 256, 0, st>>>(Kp, N, Mc, W + m0 * Kp, 1, Kp, 0, adj.T, N, 1, 1, GDfor[cls], N, 1), ++g_launches);
         if (cls == 4)
           (k_rowdot<<<(unsigned)Mc, 256, 0, st>>>(adj.T, T.DTDU, N, (double2*)B(P->o_bRowdot) + m0), ++g_launches);
+        if (want_B) {  // Gamma_W = conj(T) D^T and the per-row occupation sums of eta
+          dim3 gw_((unsigned)((Mc + 63) / 64), (unsigned)((Kp + 63) / 64));
+          (k_zgemm<<<gw_, 256, 0, st>>>(Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0,
+                                        (double2*)B(P->o_bGW[cls]) + m0 * Kp, Kp, 0), ++g_launches);
+          (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na), ++g_launches);
+        }
       }
       if (cls == 4) (k_fock11<<<blocks(M), 256, 0, st>>>((const double2*)B(P->o_bRowdot), X.sp, Gf), ++g_launches);
       (k_rowsum<<<blocks(M), 256, 0, st>>>((const double*)B(P->o_bHrow), M, ct, 0, hsum), ++g_launches);
@@ -920,6 +1193,14 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       (k_colsum<<<blocks(N), 256, 0, st>>>((const double*)B(P->o_bHcol), rt, N, 0, hA), ++g_launches);
       (k_amarg<<<na, 256, 0, st>>>(L, hA, Nt), ++g_launches);
       (k_scalsum<<<1, 256, 0, st>>>((const double*)B(P->o_bScalT), rt * ct, scal), ++g_launches);
+      if (want_B) {
+        zpair((const RowInfo*)(ws + P->o_rows[cls]), M, hsum, Hocc);
+        (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
+        const int modes[E2_NCLASS] = {-1, -1, INT_W02, -1, INT_W11, INT_W12, INT_W20, INT_W21, -1};
+        const int cols[E2_NCLASS] = {0, 0, P->ntp, 0, 1 + na * na, na, P->ntp, na, 0};
+        (k_gint<<<blocks(M * cols[cls]), 256, 0, st>>>(modes[cls], X.sp, (const double2*)B(P->o_bGW[cls]), M, cols[cls],
+                                                       (int)Kp, Gt, npair), ++g_launches);
+      }
     }
     // class (2,2)
     double* c22 = nullptr;
@@ -936,6 +1217,23 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       (k_amarg<<<na, 256, 0, st>>>(L, hA, Nt), ++g_launches);
       (k_class22_marg<<<blocks(P->nvc + P->ncc + 1), 256, 0, st>>>((const double*)B(P->o_bV22), (int)blocks(L.n),
                                                                    P->nvb, P->ncp, X.sp, Nx, scal), ++g_launches);
+      if (want_B) {
+        const int64_t M22 = P->ncp * P->nvp;
+        double* hs22 = (double*)B(P->o_bHs22);
+        double* P22 = (double*)B(P->o_bP22);
+        (k_class22_rows<<<(unsigned)M22, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G,
+                                                       X.E0p + r, b, s, g1, hs22, Hocc, P22), ++g_launches);
+        (k_rows<<<blocks(M22), 256, 0, st>>>(8, X.sp, X.epsh, X.G, M22, (RowInfo*)B(P->o_bR22)), ++g_launches);
+        zpair((const RowInfo*)B(P->o_bR22), M22, hs22, Hocc);
+        (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
+        const int Lt = d.L_coulomb + d.L_extra;
+        (k_integrals<<<blocks(M22), 256, 0, st>>>(INT_G22C, X.sp, X.Bo, X.wt, Lt, X.f, P->ncp, (int)P->nvp,
+                                                  (int)P->nvp, B(P->o_bG22c)), ++g_launches);
+        (k_g22coef<<<blocks(M22), 256, 0, st>>>((const double2*)B(P->o_bG22c), P22, M22, (double2*)B(P->o_bGg22)),
+         ++g_launches);
+        (k_gint<<<blocks(M22), 256, 0, st>>>(INT_G22C, X.sp, (const double2*)B(P->o_bGg22), P->ncp, (int)P->nvp,
+                                             (int)P->nvp, Gt, npair), ++g_launches);
+      }
     }
     // gather classes
     for (int cls : {1, 3, 0}) {
@@ -972,9 +1270,66 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       if (Ltab.n > 0)
         (k_gather_d2<<<blocks(Ltab.n), 256, 0, st>>>(cls, L, Ltab, P->das, X.sp, X.binom, Tg, nrow, Xb, GDtab),
          ++g_launches);
+      if (want_B) {
+        (k_rowsum<<<blocks(nrow), 256, 0, st>>>(Hg, nrow, L.n, 0, hsum), ++g_launches);
+        (k_hocc<<<(unsigned)nrow, 256, 0, st>>>(Hg, L, na, Hocc), ++g_launches);
+        if (cls != 0) {
+          (k_rows<<<blocks(nrow), 256, 0, st>>>(cls, X.sp, X.epsh, X.G, nrow, (RowInfo*)B(P->o_bRg)), ++g_launches);
+          zpair((const RowInfo*)B(P->o_bRg), nrow, hsum, Hocc);
+        }
+        (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
+        // integral coefficients: shifted amplitudes times the coupling table they read
+        double2* Tsh = (double2*)B(P->o_bTsh);
+        const int ntp = P->ntp;
+        if (cls == 1 && Lc[2].n > 0) {
+          double2* GX = (double2*)B(P->o_bGX01);
+          for (int u = 0; u < na; ++u) {
+            (k_tshift<<<dim3(blocks(Lc[2].n), nrow), 256, 0, st>>>(L, Lc[2], P->das, X.binom, Tg, nrow, u, -1, Tsh),
+             ++g_launches);
+            dim3 gz((unsigned)((nrow + 63) / 64), (unsigned)((ntp + 63) / 64));
+            (k_zgemm<<<gz, 256, 0, st>>>(nrow, ntp, Lc[2].n, Tsh, Lc[2].n, 1, 0, T.DTU, 1, Lc[2].n, 0, GX + (int64_t)u * ntp,
+                                         (int64_t)na * ntp, 0), ++g_launches);
+          }
+          (k_gint<<<blocks((int64_t)nrow * na * ntp), 256, 0, st>>>(INT_X01, X.sp, GX, nrow, na * ntp, na * ntp, Gt,
+                                                                   npair), ++g_launches);
+        }
+        if (cls == 3 && Lc[5].n > 0) {
+          double2* GX = (double2*)B(P->o_bGX10);
+          for (int u = 1; u < na; ++u)
+            for (int t = 0; t < u; ++t) {
+              const int tu = u * (u - 1) / 2 + t;
+              (k_tshift<<<dim3(blocks(Lc[5].n), nrow), 256, 0, st>>>(L, Lc[5], P->das, X.binom, Tg, nrow, t, u, Tsh),
+               ++g_launches);
+              dim3 gz((unsigned)((nrow + 63) / 64), (unsigned)((na + 63) / 64));
+              (k_zgemm<<<gz, 256, 0, st>>>(nrow, na, Lc[5].n, Tsh, Lc[5].n, 1, 0, T.DT, 1, Lc[5].n, 0,
+                                           GX + (int64_t)tu * na, (int64_t)ntp * na, 0), ++g_launches);
+            }
+          (k_gint<<<blocks((int64_t)nrow * ntp * na), 256, 0, st>>>(INT_X10, X.sp, GX, nrow, ntp * na, ntp * na, Gt,
+                                                                   npair), ++g_launches);
+        }
+        if (cls == 0 && Lc[2].n > 0) {
+          double2* GX = (double2*)B(P->o_bGX00);
+          for (int u = 1; u < na; ++u)
+            for (int t = 0; t < u; ++t) {
+              const int tu = u * (u - 1) / 2 + t;
+              (k_tshift<<<dim3(blocks(Lc[2].n), 1), 256, 0, st>>>(L, Lc[2], P->das, X.binom, Tg, 1, t, u, Tsh),
+               ++g_launches);
+              dim3 gz(1u, (unsigned)((ntp + 63) / 64));
+              (k_zgemm<<<gz, 256, 0, st>>>(1, ntp, Lc[2].n, Tsh, Lc[2].n, 1, 0, T.DTU, 1, Lc[2].n, 0,
+                                           GX + (int64_t)tu * ntp, ntp, 1), ++g_launches);
+            }
+        }
+      }
     }
     // E0 term of the one-body coefficient, then the reference-state gradient
     (k_e0grad<<<blocks(na * na), 256, 0, st>>>(g1, scal, X.sp, Gf), ++g_launches);
+    if (want_B && P->ntp > 0) {  // E0 term of <tu||vw>, then its pair-space coefficients
+      const double2* g2 = (const double2*)(ws + P->o_g2 + P->g_stride * r);
+      (k_x00e0<<<blocks((int64_t)P->ntp * P->ntp), 256, 0, st>>>(g1, g2, scal, P->ntp, (double2*)B(P->o_bGX00)),
+       ++g_launches);
+      (k_gint<<<blocks((int64_t)P->ntp * P->ntp), 256, 0, st>>>(INT_X00, X.sp, (const double2*)B(P->o_bGX00), P->ntp,
+                                                                P->ntp, P->ntp, Gt, npair), ++g_launches);
+    }
     if (g_c) {
       const struct { int fam, cls; double2* g; } sc[5] = {{FAM_T, 5, GT.DT}, {FAM_TD, 7, GT.DTD}, {FAM_TU, 2, GT.DTU},
                                                           {FAM_TDUD, 6, GT.DTDUD}, {FAM_TDU, 4, GT.DTDU}};
@@ -987,9 +1342,32 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
                                             (double2*)g_c + (int64_t)r * LP.n), ++g_launches);
     }
   }
-  if (g_h) {
-    (k_nd<<<blocks(P->n), 256, 0, st>>>(X.sp, Nx, Nt, Nd), ++g_launches);
-    (k_hbar<<<blocks((int64_t)P->n * P->n), 256, 0, st>>>(X.sp, Gf, Nd, (double2*)g_h), ++g_launches);
+  (k_nd<<<blocks(P->n), 256, 0, st>>>(X.sp, Nx, Nt, Nd), ++g_launches);
+  if (g_h) (k_hbar<<<blocks((int64_t)P->n * P->n), 256, 0, st>>>(X.sp, Gf, Nd, (double2*)g_h), ++g_launches);
+  if (want_B) {
+    const int Lc_ = d.L_coulomb, Lx_ = d.L_extra, Lt = Lc_ + Lx_, n = P->n;
+    double* GG = (double*)B(P->o_bGG);
+    double2* Gh = (double2*)B(P->o_bGh);
+    double2* Cs = (double2*)B(P->o_bCs);
+    double2* GBc = (double2*)B(P->o_bGB);
+    double2* ftr = (double2*)B(P->o_bFtr);
+    double* gw = (double*)B(P->o_bGw);
+    (k_gg<<<blocks((int64_t)n * n), 256, 0, st>>>(X.sp, Nd, Ntt, Ge, Gea, GG), ++g_launches);
+    (k_symm<<<blocks(npair * npair), 256, 0, st>>>(Gt, npair, Gh), ++g_launches);
+    dim3 gc_((unsigned)((Lt + 63) / 64), (unsigned)((npair + 63) / 64));
+    (k_zgemm<<<gc_, 256, 0, st>>>(Lt, npair, npair, X.Bo, npair, 1, 0, Gh, 1, npair, 0, Cs, npair, 0), ++g_launches);
+    (k_ftr<<<Lt, 256, 0, st>>>(X.sp, (const double2*)in->B_c, (const double2*)in->B_x, Lc_, Gf, ftr), ++g_launches);
+    (k_bcoef<<<blocks((int64_t)Lt * n * n), 256, 0, st>>>(X.sp, (const double2*)in->B_c, (const double2*)in->B_x, Lc_,
+                                                          Lx_, X.wt, X.dg, Cs, GG, Gf, ftr, GBc), ++g_launches);
+    if (g_Bc || g_Bx)
+      (k_bproj<<<blocks((int64_t)Lt * n * n), 256, 0, st>>>(n, Lc_, Lx_, GBc, (double2*)g_Bc, (double2*)g_Bx),
+       ++g_launches);
+    if (dE2_dlambda) {
+      (k_gw<<<Lt, 256, 0, st>>>(X.sp, (const double2*)in->B_c, (const double2*)in->B_x, Lc_, X.Bo, Cs, GG, Gf, X.dg,
+                                gw), ++g_launches);
+      if (Lx_ > 0) (k_dlambda<<<1, 256, 0, st>>>(gw, in->w_x, Lc_, Lx_, dE2_dlambda), ++g_launches);
+      else cudaMemsetAsync(dE2_dlambda, 0, sizeof(double), st);
+    }
   }
   P->launches = g_launches;
   if (cudaGetLastError() != cudaSuccess) return E2_ERR_CUDA;

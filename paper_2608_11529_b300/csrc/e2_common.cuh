@@ -47,12 +47,32 @@ struct RowInfo {
 // n = <c|c> is read from g1[0].
 struct AdjOut {
   double2* T;
+  double* Hm;      // optional: s df/dD per element of the chunk (same layout as T)
   double* Hrow;
   double* Hcol;
   double* scal;
   int64_t m_base, Mc;
   double s;
   const double2* g1;
+};
+
+// One dense-class contraction of a batch (absolute device pointers).
+struct GemmJob {
+  const double2* W;
+  const double2* D;
+  int64_t M, N;
+  int Kp;
+  const RowInfo* rows;
+  const double* U;
+  const double* eA;
+  const double* E0p;
+  double b;
+  double* partial;
+};
+
+struct WorkItem {
+  int job;
+  int tile_m, tile_n;
 };
 
 enum IntMode : int {
@@ -64,7 +84,8 @@ enum IntMode : int {
   INT_G22,      // |<ab||ij>|^2      rows (i<j), cols (a<b), real
   INT_X01,      // <au||vw>          rows a, cols u*ntp + (v<w)
   INT_X10,      // <tu||iv>          rows i, cols (t<u)*na + v
-  INT_X00       // <tu||vw>          rows (t<u), cols (v<w)
+  INT_X00,      // <tu||vw>          rows (t<u), cols (v<w)
+  INT_G22C      // <ab||ij>          rows (i<j), cols (a<b), complex
 };
 
 enum DFamily : int {

@@ -65,6 +65,73 @@ __device__ __forceinline__ void pair_decode(int64_t e, int& x, int& y) {
 
 __device__ __forceinline__ int pair_index(int x, int y) { return y * (y - 1) / 2 + x; }  // x < y
 
+
+// Global spinor indices (p, q, r, s) of entry (row, col) of an integral block
+// <pq||rs> (see IntMode); returns true for the one-body column of INT_W11
+// (f_pq, with q in place of the occupied index).
+__device__ inline bool int_indices(int mode, const DevSpace& sp, int64_t row, int col, int& p, int& q, int& r, int& s) {
+  const int na = sp.n_act, a0 = sp.a0, nvp = (int)pairs(sp.nvc), ntp = (int)pairs(na);
+  int x, y;
+  p = q = r = s = 0;
+  switch (mode) {
+    case INT_W02:
+      pair_decode(row, x, y);
+      p = sp.vc[x]; q = sp.vc[y];
+      pair_decode(col, x, y);
+      r = a0 + x; s = a0 + y;
+      break;
+    case INT_W12: {
+      const int i = (int)(row / nvp);
+      pair_decode(row % nvp, x, y);
+      p = sp.vc[x]; q = sp.vc[y]; r = sp.cc[i]; s = a0 + col;
+    } break;
+    case INT_W21: {
+      const int a = (int)(row % sp.nvc);
+      pair_decode(row / sp.nvc, x, y);
+      p = sp.vc[a]; q = a0 + col; r = sp.cc[x]; s = sp.cc[y];
+    } break;
+    case INT_W11: {
+      const int i = (int)(row / sp.nvc), a = (int)(row % sp.nvc);
+      if (col == 0) {
+        p = sp.vc[a]; q = sp.cc[i];
+        return true;
+      }
+      const int t = (col - 1) / na, u = (col - 1) % na;
+      p = sp.vc[a]; q = a0 + t; r = sp.cc[i]; s = a0 + u;
+    } break;
+    case INT_W20:
+      pair_decode(row, x, y);
+      r = sp.cc[x]; s = sp.cc[y];
+      pair_decode(col, x, y);
+      p = a0 + x; q = a0 + y;
+      break;
+    case INT_G22:
+    case INT_G22C:
+      pair_decode(row, x, y);
+      r = sp.cc[x]; s = sp.cc[y];
+      pair_decode(col, x, y);
+      p = sp.vc[x]; q = sp.vc[y];
+      break;
+    case INT_X01: {
+      const int u = col / ntp;
+      pair_decode(col % ntp, x, y);
+      p = sp.vc[row]; q = a0 + u; r = a0 + x; s = a0 + y;
+    } break;
+    case INT_X10: {
+      const int vv = col % na;
+      pair_decode(col / na, x, y);
+      p = a0 + x; q = a0 + y; r = sp.cc[row]; s = a0 + vv;
+    } break;
+    case INT_X00:
+      pair_decode(row, x, y);
+      p = a0 + x; q = a0 + y;
+      pair_decode(col, x, y);
+      r = a0 + x; s = a0 + y;
+      break;
+  }
+  return false;
+}
+
 // Colex rank of a substring with k set bits: sum_j C(t_j, j), j = 1..k.
 __device__ __forceinline__ int64_t colex_rank(uint64_t bits, const int64_t* __restrict__ binom) {
   int64_t r = 0;

@@ -201,68 +201,10 @@ __global__ void k_integrals(int mode, DevSpace sp, const double2* __restrict__ B
   if (idx >= rows * (int64_t)ld) return;
   int64_t row = idx / ld;
   int col = (int)(idx % ld);
-  const int na = sp.n_act, a0 = sp.a0, nvp = (int)pairs(sp.nvc), ntp = (int)pairs(na);
   double2 v = make_double2(0.0, 0.0);
   if (col < cols) {
-    int p = 0, q = 0, r = 0, s = 0, x, y;
-    bool fock = false;
-    switch (mode) {
-      case INT_W02: {
-        pair_decode(row, x, y);
-        p = sp.vc[x]; q = sp.vc[y];
-        pair_decode(col, x, y);
-        r = a0 + x; s = a0 + y;
-      } break;
-      case INT_W12: {
-        int i = (int)(row / nvp);
-        pair_decode(row % nvp, x, y);
-        p = sp.vc[x]; q = sp.vc[y]; r = sp.cc[i]; s = a0 + col;
-      } break;
-      case INT_W21: {
-        int a = (int)(row % sp.nvc);
-        pair_decode(row / sp.nvc, x, y);
-        p = sp.vc[a]; q = a0 + col; r = sp.cc[x]; s = sp.cc[y];
-      } break;
-      case INT_W11: {
-        int i = (int)(row / sp.nvc), a = (int)(row % sp.nvc);
-        if (col == 0) {
-          fock = true;
-          p = sp.vc[a]; q = sp.cc[i];
-        } else {
-          int t = (col - 1) / na, u = (col - 1) % na;
-          p = sp.vc[a]; q = a0 + t; r = sp.cc[i]; s = a0 + u;
-        }
-      } break;
-      case INT_W20: {
-        pair_decode(row, x, y);
-        r = sp.cc[x]; s = sp.cc[y];
-        pair_decode(col, x, y);
-        p = a0 + x; q = a0 + y;
-      } break;
-      case INT_G22: {
-        pair_decode(row, x, y);
-        r = sp.cc[x]; s = sp.cc[y];
-        pair_decode(col, x, y);
-        p = sp.vc[x]; q = sp.vc[y];
-      } break;
-      case INT_X01: {
-        int u = col / ntp;
-        pair_decode(col % ntp, x, y);
-        p = sp.vc[row]; q = a0 + u; r = a0 + x; s = a0 + y;
-      } break;
-      case INT_X10: {
-        int vv = col % na;
-        pair_decode(col / na, x, y);
-        p = a0 + x; q = a0 + y; r = sp.cc[row]; s = a0 + vv;
-      } break;
-      case INT_X00: {
-        pair_decode(row, x, y);
-        p = a0 + x; q = a0 + y;
-        pair_decode(col, x, y);
-        r = a0 + x; s = a0 + y;
-      } break;
-    }
-    if (fock) v = f[(int64_t)p * sp.n_occ + q];
+    int p, q, r, s;
+    if (int_indices(mode, sp, row, col, p, q, r, s)) v = f[(int64_t)p * sp.n_occ + q];
     else v = asym(Bo, wt, L, sp.n, sp.n_occ, p, q, r, s);
   }
   if (mode == INT_G22) ((double*)out)[idx] = v.x * v.x + v.y * v.y;
@@ -285,6 +227,11 @@ __global__ void k_rows(int cls, DevSpace sp, const double* __restrict__ epsh, co
     case 6: pair_decode(row, x, y); I[0] = x; I[1] = y; break;                                     // (2,0)
     case 1: S[0] = (int)row; break;                                                                 // (0,1)
     case 3: I[0] = (int)row; break;                                                                 // (1,0)
+    case 8: {                                                                                       // (2,2)
+      const int64_t nv2 = nvp;
+      pair_decode(row / nv2, x, y); I[0] = x; I[1] = y;
+      pair_decode(row % nv2, x, y); S[0] = x; S[1] = y;
+    } break;
     default: break;                                                                                 // (0,0)
   }
   double chi = 0.0;
@@ -435,16 +382,16 @@ __global__ void k_e0(const double2* __restrict__ g1 /*[1+na*na] row 0 = <c|c>*/,
 // prefetched into registers; one partial per CTA.
 constexpr int GBM = 64, GBN = 64, GBK = 8;
 
-__global__ void __launch_bounds__(256, 1)
-k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M, int64_t N, int Kp,
-             const RowInfo* __restrict__ rows, const double* __restrict__ U,
-             const double* __restrict__ eA, const double* __restrict__ E0p, double b, double* __restrict__ partial,
-             AdjOut adj) {
+__device__ __forceinline__ void class_tile(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M,
+                                           int64_t N, int Kp, const RowInfo* __restrict__ rows,
+                                           const double* __restrict__ U, const double* __restrict__ eA,
+                                           const double* __restrict__ E0p, double b, double* __restrict__ partial_slot,
+                                           const AdjOut& adj, int64_t tile_m, int64_t tile_n, int64_t n_tile_n) {
   __shared__ double sWr[GBM][GBK + 1], sWi[GBM][GBK + 1], sWs[GBM][GBK + 1];
   __shared__ double sDr[GBK][GBN + 1], sDi[GBK][GBN + 1], sDs[GBK][GBN + 1];
   __shared__ double sh[32];
-  // grid: x = row tiles (from row m_base), y = column tiles
-  const int64_t m0 = adj.m_base + (int64_t)blockIdx.x * GBM, n0 = (int64_t)blockIdx.y * GBN;
+  // tile (tile_m, tile_n): rows from m_base + 64 tile_m, columns from 64 tile_n
+  const int64_t m0 = adj.m_base + tile_m * GBM, n0 = tile_n * GBN;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tq = lane & 3;
   const int wm = warp >> 2, wn = warp & 3;  // warp tile: rows wm*32.., cols wn*16..
@@ -545,6 +492,7 @@ k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64
             const double w = 2.0 * adj.s * inv_n * gk;  // t = s (2/n) g V
             adj.T[(row - adj.m_base) * N + col] = make_double2(w * vr, w * vi);
             hk *= adj.s;
+            if (adj.Hm) adj.Hm[(row - adj.m_base) * N + col] = hk;
             rowp[mi][hr] += hk;
             colp[ni][hc] += hk;
             acc += hk;
@@ -568,25 +516,58 @@ k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64
       double s = 0.0;
       for (int k = 0; k < 16; ++k) s += sRow[tid][k];
       const int64_t row = m0 + tid;
-      if (row < mend) adj.Hrow[row * gridDim.y + blockIdx.y] = s;
+      if (row < mend) adj.Hrow[row * n_tile_n + tile_n] = s;
     } else if (tid < GBM + GBN) {
       const int c = tid - GBM;
       double s = 0.0;
       for (int k = 0; k < 16; ++k) s += sCol[c][k];
       const int64_t col = n0 + c;
-      if (col < N) adj.Hcol[((adj.m_base / GBM) + blockIdx.x) * N + col] = s;
+      if (col < N) adj.Hcol[((adj.m_base / GBM) + tile_m) * N + col] = s;
     }
     double t2s = block_sum(acc2, sh);
     double ts = block_sum(acc, sh);
     if (tid == 0) {
-      const int64_t slot = ((adj.m_base / GBM) + blockIdx.x) * gridDim.y + blockIdx.y;
+      const int64_t slot = ((adj.m_base / GBM) + tile_m) * n_tile_n + tile_n;
       adj.scal[2 * slot] = ts;
       adj.scal[2 * slot + 1] = t2s;
     }
     return;
   }
   double tot = block_sum(acc, sh);
-  if (tid == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  if (tid == 0) *partial_slot = tot;
+}
+
+// One CTA per 64x64 tile; grid x = row tiles (of the chunk from adj.m_base),
+// y = column tiles.  Forward: one partial per tile in partial[y * gridDim.x + x].
+__global__ void __launch_bounds__(256, 1)
+k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M, int64_t N, int Kp,
+             const RowInfo* __restrict__ rows, const double* __restrict__ U, const double* __restrict__ eA,
+             const double* __restrict__ E0p, double b, double* __restrict__ partial, AdjOut adj) {
+  double* slot = partial ? partial + (int64_t)blockIdx.y * gridDim.x + blockIdx.x : nullptr;
+  class_tile(W, D, M, N, Kp, rows, U, eA, E0p, b, slot, adj, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
+// Persistent form: one CTA per SM takes tiles of every (job, class, root) of a
+// batch from an integer work counter; items are ordered longest first
+// (contraction length times tile area).  Each tile writes the same partial
+// slot as the one-launch-per-class form, so the reduction order is unchanged.
+__global__ void __launch_bounds__(256, 1)
+k_batch_gemm(const GemmJob* __restrict__ jobs, const WorkItem* __restrict__ items, int n_items,
+             int* __restrict__ counter) {
+  __shared__ int s_item;
+  const AdjOut none{};
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;
+    const WorkItem w = items[it];
+    const GemmJob j = jobs[w.job];
+    const int64_t ntm = (j.M + GBM - 1) / GBM;
+    class_tile(j.W, j.D, j.M, j.N, j.Kp, j.rows, j.U, j.eA, j.E0p, j.b,
+               j.partial + (int64_t)w.tile_n * ntm + w.tile_m, none, w.tile_m, w.tile_n, (j.N + GBN - 1) / GBN);
+  }
 }
 
 // ------------------------------------------------------------------ class (2,2)

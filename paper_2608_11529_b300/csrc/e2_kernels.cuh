@@ -25,6 +25,7 @@ __global__ void k_e0(const double2* g1, const double2* g2, const double2* f, con
                      const double* EO, double* E0p, double* E0);
 __global__ void k_class_gemm(const double2* W, const double2* D, int64_t M, int64_t N, int Kp, const RowInfo* rows,
                              const double* U, const double* eA, const double* E0p, double b, double* partial, AdjOut adj);
+__global__ void k_batch_gemm(const GemmJob* jobs, const WorkItem* items, int n_items, int* counter);
 __global__ void k_class22(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
                           const double* G, const double* E0p, double b, int nvb, double* partial);
 __global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, DevSpace sp, const int64_t* binom,
@@ -81,5 +82,31 @@ __global__ void k_nd(DevSpace sp, const double* Nx, const double* Nt, double* Nd
 __global__ void k_cbar(int64_t np, const double2* Gc, const double* c22, const double2* c, const double2* sigma,
                        const double* scal, const double* E0p, const double2* g1, double2* out);
 __global__ void k_hbar(DevSpace sp, const double2* Gf, const double* Nd, double2* gh);
+
+__global__ void k_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t sam, int64_t sak, const double* B,
+                        int64_t sbk, int64_t sbn, double* C, int64_t ldc, int beta);
+__global__ void k_hocc(const double* H, DevList Ls, int na, double* Hocc);
+__global__ void k_zmat(const RowInfo* rows, int64_t M, int nx, double* Z);
+__global__ void k_zscale(const double* Z, const double* hsum, int64_t M, int nx, double* out);
+__global__ void k_gint(int mode, DevSpace sp, const double2* Gam, int64_t rows, int cols, int ld, double2* Gt,
+                       int64_t npair);
+__global__ void k_tshift(DevList Lx, DevList Ltab, DevDas das, const int64_t* binom, const double2* T, int nrow, int t,
+                         int u, double2* Tsh);
+__global__ void k_class22_rows(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
+                               const double* G, const double* E0p, double b, double s, const double2* g1, double* hsum,
+                               double* Hocc, double* P22);
+__global__ void k_g22coef(const double2* g, const double* P22, int64_t n, double2* out);
+__global__ void k_ntt(DevList Ls, const double* hA, int na, double* Ntt);
+__global__ void k_gg(DevSpace sp, const double* Nd, const double* Ntt, const double* Ge, const double* Gea, double* GG);
+__global__ void k_symm(const double2* Gt, int64_t npair, double2* Gh);
+__global__ void k_bcoef(DevSpace sp, const double2* Bc, const double2* Bx, int Lc, int Lx, const double* wt,
+                        const double* dg, const double2* Cs, const double* GG, const double2* Gf, const double2* ftr,
+                        double2* GB);
+__global__ void k_ftr(DevSpace sp, const double2* Bc, const double2* Bx, int Lc, const double2* Gf, double2* ftr);
+__global__ void k_gw(DevSpace sp, const double2* Bc, const double2* Bx, int Lc, const double2* Bo, const double2* Cs,
+                     const double* GG, const double2* Gf, const double* dg, double* gw);
+__global__ void k_bproj(int n, int Lc, int Lx, const double2* GB, double2* gBc, double2* gBx);
+__global__ void k_x00e0(const double2* g1, const double2* g2, const double* scal, int ntp, double2* GX00);
+__global__ void k_dlambda(const double* gw, const double* wx, int Lc, int Lx, double* out);
 
 }  // namespace e2

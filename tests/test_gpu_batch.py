@@ -1,0 +1,67 @@
+"""Batched evaluation: one persistent launch for the dense classes of several
+jobs (different Hamiltonians, root counts and frozen cutoffs), plain and
+captured in a CUDA graph, against e2_forward job by job (bitwise: same
+partial slots, same reduction order) and the oracle."""
+import numpy as np
+import pytest
+
+from e2_inputs.synth import tiny_problem
+from oracle import Oracle
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _jobs():
+    base = dict(n_core=6, n_act=10, n_virt=16, n_elec=5, Lc=6, Lx=3, x_scale=0.05, seed=61)
+    specs = [dict(ham="DC", n_roots=1), dict(ham="DCG", n_roots=2, n_frozen_core=2),
+             dict(ham="DCB", n_roots=2, n_frozen_core=2, n_frozen_virt=4)]
+    out = []
+    for sp in specs:
+        kw = dict(base)
+        kw.update(sp)
+        p = tiny_problem(**kw)
+        o = Oracle(p)
+        c, _ = o.ground_state(p.n_roots)
+        out.append((p, o, c))
+    return out
+
+
+def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph():
+    import paper_2608_11529_b300 as e2
+    from paper_2608_11529_b300 import build as e2build
+    e2build.build()
+    jobs = _jobs()
+    plans = [e2.E2Problem.from_problem(p) for p, _, _ in jobs]
+    inputs = [e2.device_inputs(p, c) for p, _, c in jobs]
+    single = []
+    for plan, t in zip(plans, inputs):
+        E2, E2c, _ = plan.forward(**t)
+        single.append((E2.clone(), E2c.clone()))
+    batch = e2.E2Batch(plans)
+    batch.prepare(torch.device("cuda"))
+    out = batch.forward(inputs)
+    torch.cuda.synchronize()
+    for (E2, E2c), (B2, B2c), (p, o, c) in zip(single, out, jobs):
+        assert torch.equal(E2, B2) and torch.equal(E2c, B2c)
+        _, ec, _ = o.e2()
+        np.testing.assert_allclose(B2c.cpu().numpy(), ec, rtol=0, atol=1e-9)
+    # capture once, replay twice
+    for o2 in out:
+        o2[0].zero_()
+        o2[1].zero_()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            batch.forward(inputs)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(2):
+        for o2 in out:
+            o2[0].zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        for (E2, E2c), (B2, B2c) in zip(single, out):
+            assert torch.equal(E2, B2) and torch.equal(E2c, B2c)
+    assert batch.launch_count() > 0
