@@ -104,6 +104,99 @@ k_zgemm(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t 
       }
 }
 
+// C[m][n] = beta * C[m][n] + sum_k A[m*sam + k*sak] B[k*sbk + n*sbn], real,
+// on the FP64 tensor pipe; one CTA per 64x64 tile of C over the full K.
+__global__ void __launch_bounds__(256, 2)
+k_dgemm(int64_t M, int64_t N, int64_t K, const double* __restrict__ A, int64_t sam, int64_t sak,
+        const double* __restrict__ B, int64_t sbk, int64_t sbn, double* __restrict__ C, int64_t ldc, int beta) {
+  constexpr int BM = 64, BN = 64, BK = 8;
+  __shared__ double sA[BM][BK + 1], sB[BK][BN + 1];
+  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+  const int wm = warp >> 2, wn = warp & 3;
+  double acc[2][2][4];
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[a][c][e] = 0.0;
+  const int ar = tid >> 3, ak = tid & 7, bk = tid >> 6, bc = tid & 63;
+  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int64_t m = m0 + ar + 32 * q, k = k0 + ak;
+      sA[ar + 32 * q][ak] = (m < M && k < K) ? A[m * sam + k * sak] : 0.0;
+      const int64_t kb = k0 + bk + 4 * q, nn = n0 + bc;
+      sB[bk + 4 * q][bc] = (kb < K && nn < N) ? B[kb * sbk + nn * sbn] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi) {
+      const int r0 = wm * 32 + mi * 16 + g;
+      double a[4] = {sA[r0][tq], sA[r0 + 8][tq], sA[r0][tq + 4], sA[r0 + 8][tq + 4]};
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) {
+        const int cb = wn * 16 + ni * 8 + g;
+        double b2[2] = {sB[tq][cb], sB[tq + 4][cb]};
+        mma_f64(acc[mi][ni], a, b2);
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int64_t row = m0 + wm * 32 + mi * 16 + g + (e >> 1) * 8;
+        const int64_t col = n0 + wn * 16 + ni * 8 + 2 * tq + (e & 1);
+        if (row >= M || col >= N) continue;
+        double* out = C + row * ldc + col;
+        *out = beta ? *out + acc[mi][ni][e] : acc[mi][ni][e];
+      }
+}
+
+// Hocc[r][t] = sum_A H[r][A] [t in A]  (one block per row of the chunk)
+__global__ void k_hocc(const double* __restrict__ H, DevList Ls, int na, double* __restrict__ Hocc) {
+  __shared__ double sh[32];
+  const int64_t r = blockIdx.x;
+  double acc[64];
+  for (int t = 0; t < na; ++t) acc[t] = 0.0;
+  for (int64_t g = threadIdx.x; g < Ls.n; g += blockDim.x) {
+    const double h = H[r * Ls.n + g];
+    for (uint64_t x = Ls.str[g]; x; x &= x - 1) acc[__ffsll((long long)x) - 1] += h;
+  }
+  for (int t = 0; t < na; ++t) {
+    const double v = block_sum(acc[t], sh);
+    if (threadIdx.x == 0) Hocc[r * na + t] = v;
+  }
+}
+
+// Signed incidence of the external indices of each row: Z[e][x] = +1 for a
+// particle x, -1 for a hole x (x: correlated core, then correlated virtual).
+__global__ void k_zmat(const RowInfo* __restrict__ rows, int64_t M, int nx, double* __restrict__ Z) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= M * nx) return;
+  const int64_t e = idx / nx;
+  const int x = (int)(idx % nx);
+  const RowInfo ri = rows[e];
+  double v = 0.0;
+  if (ri.s1 == x || ri.s2 == x) v = 1.0;
+  if (ri.i1 == x || ri.i2 == x) v = -1.0;
+  Z[idx] = v;
+}
+
+// out[e][x] = hsum[e] * Z[e][x]
+__global__ void k_zscale(const double* __restrict__ Z, const double* __restrict__ hsum, int64_t M, int nx,
+                         double* __restrict__ out) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= M * nx) return;
+  out[idx] = Z[idx] * hsum[idx / nx];
+}
+
 // ------------------------------------------------------------------ reductions of the adjoint sums
 
 // out[r] (+)= sum_c in[r*ncol + c] in index order
@@ -682,6 +775,305 @@ __global__ void k_hbar(DevSpace sp, const double2* __restrict__ Gf, const double
   const double2 a = coef(p, q), bq = coef(q, p);
   // Hermitian projection of conj(Gamma): (conj(G_pq) + G_qp) / 2
   gh[idx] = make_double2(0.5 * (a.x + bq.x), 0.5 * (-a.y + bq.y));
+}
+
+
+// ------------------------------------------------------------------ factor gradient
+
+// Pair-space coefficients of the chemists' integrals: pi = p * n_occ + y.
+// Entry (row, col) of block `mode` with coefficient G (dE2 = Re G d<pq||rs>)
+// adds G to (pr|qs) and -G to (ps|qr).  Within one launch every slot is
+// written by one entry at most.
+__global__ void k_gint(int mode, DevSpace sp, const double2* __restrict__ Gam, int64_t rows, int cols, int ld,
+                       double2* __restrict__ Gt, int64_t npair) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= rows * (int64_t)cols) return;
+  const int64_t row = idx / cols;
+  const int col = (int)(idx % cols);
+  int p, q, r, s;
+  if (int_indices(mode, sp, row, col, p, q, r, s)) return;  // one-body column: handled by Gamma_f
+  const double2 v = Gam[row * ld + col];
+  const int no = sp.n_occ;
+  double2* a = Gt + ((int64_t)p * no + r) * npair + (int64_t)q * no + s;
+  double2* b = Gt + ((int64_t)p * no + s) * npair + (int64_t)q * no + r;
+  a->x += v.x;
+  a->y += v.y;
+  b->x -= v.x;
+  b->y -= v.y;
+}
+
+// Tsh[row][B] = conj(T[row][A]) * sign for A = B + t (u < 0) or A = B + t + u
+// (t < u), sign of the coupling-table entry D_B the class reads for A; zero
+// when t or u is in B or A is not in the class list.
+__global__ void k_tshift(DevList Lx, DevList Ltab, DevDas das, const int64_t* __restrict__ binom,
+                         const double2* __restrict__ T, int nrow, int t, int u, double2* __restrict__ Tsh) {
+  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int row = blockIdx.y;
+  if (g >= Ltab.n) return;
+  const uint64_t B = Ltab.str[g];
+  double2 v = make_double2(0.0, 0.0);
+  const bool clash = ((B >> t) & 1) || (u >= 0 && ((B >> u) & 1));
+  if (!clash) {
+    const uint64_t A = B | (1ull << t) | (u >= 0 ? (1ull << u) : 0ull);
+    const int64_t ax = list_addr(Lx, das, binom, A);
+    if (ax >= 0) {
+      v = cconj(T[(int64_t)row * Lx.n + ax]);
+      const int par = (u < 0) ? popc_below(A, t) : popc_below(B, u) + popc_below(B, t);
+      if (par & 1) v = make_double2(-v.x, -v.y);
+    }
+  }
+  Tsh[(int64_t)row * Ltab.n + g] = v;
+}
+
+// Row-owner pass of class (2,2): one block per row (i<j, a<b).  For every A:
+// eta = s df/dD and s (df/dv) |c_A|^2 / n; writes hsum[row], Hocc[row][t],
+// P22[row] = sum_A s (df/dv) |c_A|^2 / n.
+__global__ void __launch_bounds__(256)
+k_class22_rows(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* __restrict__ g2,
+               const double* __restrict__ epsh, const double* __restrict__ G, const double* __restrict__ E0p, double b,
+               double s, const double2* __restrict__ g1, double* __restrict__ hsum, double* __restrict__ Hocc,
+               double* __restrict__ P22) {
+  __shared__ double sh[32];
+  const int64_t nvp = pairs(sp.nvc);
+  const int64_t row = blockIdx.x;
+  int iu, ju, au, bu;
+  pair_decode(row / nvp, iu, ju);
+  pair_decode(row % nvp, au, bu);
+  const int gi = sp.cc[iu], gj = sp.cc[ju], ga = sp.vc[au], gb = sp.vc[bu];
+  const double w = g2[row];
+  const double inv_n = 1.0 / g1[0].x;
+  const double chi = -epsh[gi] - epsh[gj] + G[(int64_t)gi * sp.n + gj] + epsh[ga] + epsh[gb] + G[(int64_t)ga * sp.n + gb] -
+                     G[(int64_t)gi * sp.n + ga] - G[(int64_t)gi * sp.n + gb] - G[(int64_t)gj * sp.n + ga] -
+                     G[(int64_t)gj * sp.n + gb];
+  const double e0p = *E0p;
+  const int na = sp.n_act;
+  double hs = 0.0, p22 = 0.0, ho[64];
+  for (int t = 0; t < na; ++t) ho[t] = 0.0;
+  for (int64_t A = threadIdx.x; A < Ls.n; A += blockDim.x) {
+    const double D = e0p - Ls.eA[A] - chi - Ls.U[(int64_t)(sp.ncc + au) * Ls.n + A] -
+                     Ls.U[(int64_t)(sp.ncc + bu) * Ls.n + A] + Ls.U[(int64_t)iu * Ls.n + A] + Ls.U[(int64_t)ju * Ls.n + A];
+    const double2 cv = c[A];
+    const double c2 = (cv.x * cv.x + cv.y * cv.y) * inv_n;
+    double gk, hk;
+    en_derivs(w * c2, D, b, gk, hk);
+    hk *= s;
+    hs += hk;
+    p22 += s * gk * c2;
+    for (uint64_t x = Ls.str[A]; x; x &= x - 1) ho[__ffsll((long long)x) - 1] += hk;
+  }
+  double v = block_sum(hs, sh);
+  if (threadIdx.x == 0) hsum[row] = v;
+  v = block_sum(p22, sh);
+  if (threadIdx.x == 0) P22[row] = v;
+  for (int t = 0; t < na; ++t) {
+    v = block_sum(ho[t], sh);
+    if (threadIdx.x == 0) Hocc[row * na + t] = v;
+  }
+}
+
+// Gamma of <ab||ij>: 2 conj(g) P22
+__global__ void k_g22coef(const double2* __restrict__ g, const double* __restrict__ P22, int64_t n,
+                          double2* __restrict__ out) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  out[k] = make_double2(2.0 * P22[k] * g[k].x, -2.0 * P22[k] * g[k].y);
+}
+
+// Ntt[t][u] += sum_A hA[A] [t, u in A] (one block per ordered pair, t != u)
+__global__ void k_ntt(DevList Ls, const double* __restrict__ hA, int na, double* __restrict__ Ntt) {
+  __shared__ double sh[32];
+  const int t = blockIdx.x / na, u = blockIdx.x % na;
+  if (t == u) return;
+  const uint64_t m = (1ull << t) | (1ull << u);
+  double acc = 0.0;
+  for (int64_t g = threadIdx.x; g < Ls.n; g += blockDim.x)
+    if ((Ls.str[g] & m) == m) acc += hA[g];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) Ntt[t * na + u] += acc;
+}
+
+// Coefficient of G_pq (real, ordered entries):
+//   eps^_p = h_pp + sum_{k in core} G_pk            -> Nd[p] on (p, k)
+//   e_A    = ... + 1/2 sum_{t != u in A} G_tu         -> -1/2 Ntt[t][u]
+//   chi_e  = ... + G of hole / particle pairs        -> -1/2 Ge[x][y]
+//   U[x][A] = sum_{t in A} G_{X(x), t}              -> -Gea[x][t]
+__global__ void k_gg(DevSpace sp, const double* __restrict__ Nd, const double* __restrict__ Ntt,
+                     const double* __restrict__ Ge, const double* __restrict__ Gea, double* __restrict__ GG) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int n = sp.n, na = sp.n_act, nx = sp.nx;
+  if (idx >= (int64_t)n * n) return;
+  const int p = (int)(idx / n), q = (int)(idx % n);
+  double v = 0.0;
+  if (p != q) {
+    if (q < sp.n_core) v += Nd[p];
+    const bool pa = p >= sp.a0 && p < sp.v0, qa = q >= sp.a0 && q < sp.v0;
+    if (pa && qa) v -= 0.5 * Ntt[(p - sp.a0) * na + (q - sp.a0)];
+    int xp = -1, xq = -1;
+    for (int i = 0; i < sp.ncc; ++i) {
+      if (sp.cc[i] == p) xp = i;
+      if (sp.cc[i] == q) xq = i;
+    }
+    for (int a = 0; a < sp.nvc; ++a) {
+      if (sp.vc[a] == p) xp = sp.ncc + a;
+      if (sp.vc[a] == q) xq = sp.ncc + a;
+    }
+    if (xp >= 0 && xq >= 0) v -= 0.5 * Ge[xp * nx + xq];
+    if (xp >= 0 && qa) v -= Gea[xp * na + (q - sp.a0)];
+  }
+  GG[idx] = v;
+}
+
+// Gh = Gt + Gt^T (pair space)
+__global__ void k_symm(const double2* __restrict__ Gt, int64_t npair, double2* __restrict__ Gh) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= npair * npair) return;
+  const int64_t a = idx / npair, b = idx % npair;
+  const double2 x = Gt[idx], y = Gt[b * npair + a];
+  Gh[idx] = make_double2(x.x + y.x, x.y + y.y);
+}
+
+// Coefficient of dB^L_pq for every factor (complex, n x n per L):
+//   integrals: w_L Cs[L][p*no + q] (q < n_occ), Cs = Bo Gh^T
+//   G:         -w_L (GG_pq + GG_qp) B_qp (p != q); diagonal: w_L sum_r (GG_pr + GG_rp) B_rr
+//   f:         w_L tr_L Gf[p][q] (q < n_occ); core k: diagonal w_L sum Gf B, and the
+//              -w_L sum_y Gf[p][y] B_ky (q = k core) / -w_L sum_p' Gf[p'][q] B_p'p (p core) terms
+__global__ void k_bcoef(DevSpace sp, const double2* __restrict__ Bc, const double2* __restrict__ Bx, int Lc, int Lx,
+                        const double* __restrict__ wt, const double* __restrict__ dg, const double2* __restrict__ Cs,
+                        const double* __restrict__ GG, const double2* __restrict__ Gf, const double2* __restrict__ ftr,
+                        double2* __restrict__ GB) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int n = sp.n, no = sp.n_occ;
+  if (idx >= (int64_t)(Lc + Lx) * n * n) return;
+  const int L = (int)(idx / ((int64_t)n * n));
+  const int64_t pq = idx % ((int64_t)n * n);
+  const int p = (int)(pq / n), q = (int)(pq % n);
+  const double2* B = (L < Lc) ? Bc + (int64_t)L * n * n : Bx + (int64_t)(L - Lc) * n * n;
+  const double w = wt[L];
+  double trc = 0.0;
+  for (int k = 0; k < sp.n_core; ++k) trc += dg[(int64_t)L * n + k];
+  double2 v = make_double2(0.0, 0.0);
+  if (q < no) {
+    const double2 cs = Cs[(int64_t)L * n * no + (int64_t)p * no + q];
+    const double2 gf = Gf[(int64_t)p * no + q];
+    v.x += w * (cs.x + trc * gf.x);
+    v.y += w * (cs.y + trc * gf.y);
+  }
+  if (p != q) {
+    const double gs = GG[(int64_t)p * n + q] + GG[(int64_t)q * n + p];
+    const double2 bqp = B[(int64_t)q * n + p];
+    v.x -= w * gs * bqp.x;
+    v.y -= w * gs * bqp.y;
+  } else {
+    double acc = 0.0;
+    for (int r = 0; r < n; ++r) acc += (GG[(int64_t)p * n + r] + GG[(int64_t)r * n + p]) * B[(int64_t)r * n + r].x;
+    v.x += w * acc;
+    if (p < sp.n_core) {
+      v.x += w * ftr[L].x;
+      v.y += w * ftr[L].y;
+    }
+  }
+  if (q < sp.n_core) {  // -w sum_y Gf[p][y] B_qy
+    double2 acc = make_double2(0.0, 0.0);
+    for (int y = 0; y < no; ++y) acc = cfma(Gf[(int64_t)p * no + y], B[(int64_t)q * n + y], acc);
+    v.x -= w * acc.x;
+    v.y -= w * acc.y;
+  }
+  if (p < sp.n_core && q < no) {  // -w sum_p' Gf[p'][q] B_p'p
+    double2 acc = make_double2(0.0, 0.0);
+    for (int r = 0; r < n; ++r) acc = cfma(Gf[(int64_t)r * no + q], B[(int64_t)r * n + p], acc);
+    v.x -= w * acc.x;
+    v.y -= w * acc.y;
+  }
+  GB[idx] = v;
+}
+
+// ftr[L] = sum_{p, y < n_occ} Gf[p][y] B^L_py  (one block per factor)
+__global__ void k_ftr(DevSpace sp, const double2* __restrict__ Bc, const double2* __restrict__ Bx, int Lc,
+                      const double2* __restrict__ Gf, double2* __restrict__ ftr) {
+  __shared__ double sh[32];
+  const int L = blockIdx.x, n = sp.n, no = sp.n_occ;
+  const double2* B = (L < Lc) ? Bc + (int64_t)L * n * n : Bx + (int64_t)(L - Lc) * n * n;
+  double2 acc = make_double2(0.0, 0.0);
+  for (int64_t k = threadIdx.x; k < (int64_t)n * no; k += blockDim.x) {
+    const int p = (int)(k / no), y = (int)(k % no);
+    acc = cfma(Gf[k], B[(int64_t)p * n + y], acc);
+  }
+  const double re = block_sum(acc.x, sh), im = block_sum(acc.y, sh);
+  if (threadIdx.x == 0) ftr[L] = make_double2(re, im);
+}
+
+// Weight gradient per factor: dE2/dw_L = 1/2 Re sum Bo Cs / w (integral part)
+//   + sum GG (B_pp B_qq - |B_pq|^2) + Re sum_{p,y<no} Gf[p][y] (B_py tr - sum_k B_pk B_ky)
+__global__ void k_gw(DevSpace sp, const double2* __restrict__ Bc, const double2* __restrict__ Bx, int Lc,
+                     const double2* __restrict__ Bo, const double2* __restrict__ Cs, const double* __restrict__ GG,
+                     const double2* __restrict__ Gf, const double* __restrict__ dg, double* __restrict__ gw) {
+  __shared__ double sh[32];
+  const int L = blockIdx.x, n = sp.n, no = sp.n_occ;
+  const double2* B = (L < Lc) ? Bc + (int64_t)L * n * n : Bx + (int64_t)(L - Lc) * n * n;
+  const int64_t np_ = (int64_t)n * no;
+  double acc = 0.0;
+  for (int64_t k = threadIdx.x; k < np_; k += blockDim.x) {
+    const double2 a = Bo[(int64_t)L * np_ + k], c = Cs[(int64_t)L * np_ + k];
+    acc += 0.5 * (a.x * c.x - a.y * c.y);
+  }
+  double trc = 0.0;
+  for (int k = 0; k < sp.n_core; ++k) trc += dg[(int64_t)L * n + k];
+  for (int64_t k = threadIdx.x; k < (int64_t)n * n; k += blockDim.x) {
+    const int p = (int)(k / n), q = (int)(k % n);
+    if (p != q) {
+      const double2 bpq = B[k];
+      acc += GG[k] * (dg[(int64_t)L * n + p] * dg[(int64_t)L * n + q] - (bpq.x * bpq.x + bpq.y * bpq.y));
+    }
+    if (q < no) {
+      double2 t = make_double2(B[k].x * trc, B[k].y * trc);
+      for (int kk = 0; kk < sp.n_core; ++kk) {
+        const double2 m = cmul(B[(int64_t)p * n + kk], B[(int64_t)kk * n + q]);
+        t.x -= m.x;
+        t.y -= m.y;
+      }
+      const double2 gf = Gf[(int64_t)p * no + q];
+      acc += gf.x * t.x - gf.y * t.y;
+    }
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) gw[L] = acc;
+}
+
+// g_B = Hermitian projection of conj(coefficient), written per factor set
+__global__ void k_bproj(int n, int Lc, int Lx, const double2* __restrict__ GB, double2* __restrict__ gBc,
+                        double2* __restrict__ gBx) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)(Lc + Lx) * n * n) return;
+  const int L = (int)(idx / ((int64_t)n * n));
+  const int64_t pq = idx % ((int64_t)n * n);
+  const int p = (int)(pq / n), q = (int)(pq % n);
+  const double2 a = GB[idx], b = GB[(int64_t)L * n * n + (int64_t)q * n + p];
+  const double2 v = make_double2(0.5 * (a.x + b.x), 0.5 * (-a.y + b.y));
+  if (L < Lc) {
+    if (gBc) gBc[idx] = v;
+  } else if (gBx) {
+    gBx[idx - (int64_t)Lc * n * n] = v;
+  }
+}
+
+// E0 term of the <tu||vw> coefficient: GX00 += (sum eta / n) Gamma2
+__global__ void k_x00e0(const double2* __restrict__ g1, const double2* __restrict__ g2, const double* __restrict__ scal,
+                        int ntp, double2* __restrict__ GX00) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= (int64_t)ntp * ntp) return;
+  const double w = scal[0] / g1[0].x;
+  GX00[k].x += w * g2[k].x;
+  GX00[k].y += w * g2[k].y;
+}
+
+// dE2/dlambda = sum over the extra set of w_x[L] dE2/dw_L
+__global__ void k_dlambda(const double* __restrict__ gw, const double* __restrict__ wx, int Lc, int Lx,
+                          double* __restrict__ out) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (int k = threadIdx.x; k < Lx; k += blockDim.x) acc += wx[k] * gw[Lc + k];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) *out = acc;
 }
 
 }  // namespace e2
