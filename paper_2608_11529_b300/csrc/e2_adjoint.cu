@@ -19,89 +19,129 @@ namespace e2 {
 
 // ------------------------------------------------------------------ generic complex GEMM
 
-// C[m][n] = beta * C[m][n] + sum_k opA(m,k) opB(k,n) on the FP64 tensor pipe
+// C(m,n) = beta * C(m,n) + sum_k opA(m,k) opB(k,n) on the FP64 tensor pipe
 // (three real products per complex product), opA(m,k) = A[m*sam + k*sak]
 // (conjugated when conjA), opB(k,n) = B[k*sbk + n*sbn] (conjugated when
-// conjB); C row-major with leading dimension ldc; beta is 0 or 1.  Each C tile
-// is owned by one CTA over the full K: deterministic.
-__global__ void __launch_bounds__(256, 1)
-k_zgemm(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
-        const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t ldc,
-        int beta) {
-  constexpr int BM = 64, BN = 64, BK = 8;
+// conjB), C(m,n) = C[m*csm + n*csn].  Tile BM = 64 by BN = 64 or 16.  Split K:
+// grid.z segments of kseg, segment z writing C + z*czs (beta applies to each
+// segment's own output); a fixed-order sum of the segments (k_zacc) keeps the
+// result deterministic.  Each output element is owned by one CTA per segment.
+template <int BN>
+__device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam,
+                                           int64_t sak, int conjA, const double2* __restrict__ B, int64_t sbk,
+                                           int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm, int64_t csn,
+                                           int beta, int64_t kseg, int64_t czs) {
+  constexpr int BM = 64, BK = 8;
+  constexpr int NI = BN / 32 > 0 ? BN / 32 : 1;       // n8 tiles per warp (64: 2, 16: 1)
+  constexpr int WN = BN == 64 ? 4 : 2;                  // warps across N
+  constexpr int WM = 8 / WN;                            // warps across M (64: 2, 16: 4)
+  constexpr int MI = BM / (WM * 16);                    // m16 tiles per warp (64: 2, 16: 1)
   __shared__ double sAr[BM][BK + 1], sAi[BM][BK + 1], sAs[BM][BK + 1];
   __shared__ double sBr[BK][BN + 1], sBi[BK][BN + 1], sBs[BK][BN + 1];
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t kb0 = (int64_t)blockIdx.z * kseg, kb1 = kb0 + kseg < K ? kb0 + kseg : K;
+  C += (int64_t)blockIdx.z * czs;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tq = lane & 3;
-  const int wm = warp >> 2, wn = warp & 3;
-  double t1[2][2][4], t2[2][2][4], t3[2][2][4];
+  const int wm = warp / WN, wn = warp % WN;
+  double t1[MI][NI][4], t2[MI][NI][4], t3[MI][NI][4];
 #pragma unroll
-  for (int a = 0; a < 2; ++a)
+  for (int a = 0; a < MI; ++a)
 #pragma unroll
-    for (int c = 0; c < 2; ++c)
+    for (int c = 0; c < NI; ++c)
 #pragma unroll
       for (int e = 0; e < 4; ++e) t1[a][c][e] = t2[a][c][e] = t3[a][c][e] = 0.0;
-  const int ar = tid >> 3, ak = tid & 7, bk = tid >> 6, bc = tid & 63;
+  const int ar = tid >> 3, ak = tid & 7;
   const double2 zero = make_double2(0.0, 0.0);
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  for (int64_t k0 = kb0; k0 < kb1; k0 += BK) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int64_t m = m0 + ar + 32 * q, k = k0 + ak;
-      double2 v = (m < M && k < K) ? A[m * sam + k * sak] : zero;
+      double2 v = (m < M && k < kb1) ? A[m * sam + k * sak] : zero;
       if (conjA) v.y = -v.y;
       sAr[ar + 32 * q][ak] = v.x;
       sAi[ar + 32 * q][ak] = v.y;
       sAs[ar + 32 * q][ak] = v.x + v.y;
-      const int64_t kb = k0 + bk + 4 * q, nn = n0 + bc;
-      double2 u = (kb < K && nn < N) ? B[kb * sbk + nn * sbn] : zero;
+    }
+    for (int e = tid; e < BK * BN; e += 256) {
+      const int bk = e / BN, bc = e % BN;
+      const int64_t kb = k0 + bk, nn = n0 + bc;
+      double2 u = (kb < kb1 && nn < N) ? B[kb * sbk + nn * sbn] : zero;
       if (conjB) u.y = -u.y;
-      sBr[bk + 4 * q][bc] = u.x;
-      sBi[bk + 4 * q][bc] = u.y;
-      sBs[bk + 4 * q][bc] = u.x + u.y;
+      sBr[bk][bc] = u.x;
+      sBi[bk][bc] = u.y;
+      sBs[bk][bc] = u.x + u.y;
     }
     __syncthreads();
-    double br[2][2], bi[2][2], bs[2][2];
+    double br[NI][2], bi[NI][2], bs[NI][2];
 #pragma unroll
-    for (int ni = 0; ni < 2; ++ni) {
-      const int cb = wn * 16 + ni * 8 + g;
+    for (int ni = 0; ni < NI; ++ni) {
+      const int cb = wn * (8 * NI) + ni * 8 + g;
       br[ni][0] = sBr[tq][cb]; br[ni][1] = sBr[tq + 4][cb];
       bi[ni][0] = sBi[tq][cb]; bi[ni][1] = sBi[tq + 4][cb];
       bs[ni][0] = sBs[tq][cb]; bs[ni][1] = sBs[tq + 4][cb];
     }
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi) {
-      const int r0 = wm * 32 + mi * 16 + g;
+    for (int mi = 0; mi < MI; ++mi) {
+      const int r0 = wm * (16 * MI) + mi * 16 + g;
       double a[4];
       a[0] = sAr[r0][tq]; a[1] = sAr[r0 + 8][tq]; a[2] = sAr[r0][tq + 4]; a[3] = sAr[r0 + 8][tq + 4];
 #pragma unroll
-      for (int ni = 0; ni < 2; ++ni) mma_f64(t1[mi][ni], a, br[ni]);
+      for (int ni = 0; ni < NI; ++ni) mma_f64(t1[mi][ni], a, br[ni]);
       a[0] = sAi[r0][tq]; a[1] = sAi[r0 + 8][tq]; a[2] = sAi[r0][tq + 4]; a[3] = sAi[r0 + 8][tq + 4];
 #pragma unroll
-      for (int ni = 0; ni < 2; ++ni) mma_f64(t2[mi][ni], a, bi[ni]);
+      for (int ni = 0; ni < NI; ++ni) mma_f64(t2[mi][ni], a, bi[ni]);
       a[0] = sAs[r0][tq]; a[1] = sAs[r0 + 8][tq]; a[2] = sAs[r0][tq + 4]; a[3] = sAs[r0 + 8][tq + 4];
 #pragma unroll
-      for (int ni = 0; ni < 2; ++ni) mma_f64(t3[mi][ni], a, bs[ni]);
+      for (int ni = 0; ni < NI; ++ni) mma_f64(t3[mi][ni], a, bs[ni]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+  for (int mi = 0; mi < MI; ++mi)
 #pragma unroll
-    for (int ni = 0; ni < 2; ++ni)
+    for (int ni = 0; ni < NI; ++ni)
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        const int64_t row = m0 + wm * 32 + mi * 16 + g + (e >> 1) * 8;
-        const int64_t col = n0 + wn * 16 + ni * 8 + 2 * tq + (e & 1);
+        const int64_t row = m0 + wm * (16 * MI) + mi * 16 + g + (e >> 1) * 8;
+        const int64_t col = n0 + wn * (8 * NI) + ni * 8 + 2 * tq + (e & 1);
         if (row >= M || col >= N) continue;
         double2 v = make_double2(t1[mi][ni][e] - t2[mi][ni][e], t3[mi][ni][e] - t1[mi][ni][e] - t2[mi][ni][e]);
-        double2* out = C + row * ldc + col;
+        double2* out = C + row * csm + col * csn;
         if (beta) {
           v.x += out->x;
           v.y += out->y;
         }
         *out = v;
       }
+}
+
+__global__ void __launch_bounds__(256, 1)
+k_zgemm64(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
+          const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm,
+          int64_t csn, int beta, int64_t kseg, int64_t czs) {
+  zgemm_body<64>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs);
+}
+
+__global__ void __launch_bounds__(256, 1)
+k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
+          const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm,
+          int64_t csn, int beta, int64_t kseg, int64_t czs) {
+  zgemm_body<16>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs);
+}
+
+// out[i] += sum_z part[z*ps + i] in z order, i < count (segments of a split-K
+// product, written in the output's own layout)
+__global__ void k_zacc(const double2* __restrict__ part, int nseg, int64_t ps, int64_t count, double2* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double2 v = out[i];
+  for (int z = 0; z < nseg; ++z) {
+    const double2 p = part[z * ps + i];
+    v.x += p.x;
+    v.y += p.y;
+  }
+  out[i] = v;
 }
 
 // C[m][n] = beta * C[m][n] + sum_k A[m*sam + k*sak] B[k*sbk + n*sbn], real,

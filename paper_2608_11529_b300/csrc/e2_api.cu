@@ -101,6 +101,7 @@ struct e2_problem {
   int64_t npair;
   size_t o_bGW[E2_NCLASS], o_bHm, o_bHocc, o_bZ, o_bZs, o_bGe, o_bGea, o_bNtt, o_bGG, o_bGt, o_bGh, o_bTsh;
   size_t o_bGX01, o_bGX10, o_bGX00, o_bR22, o_bHs22, o_bP22, o_bG22c, o_bGg22, o_bCs, o_bGB, o_bFtr, o_bGw, o_bRg;
+  size_t o_bPart;  // split-K segments
   size_t bwd_bytes;
 };
 
@@ -439,6 +440,7 @@ e2_status build_plan(e2_problem* P) {
     P->o_bGB = ws.take(16 * (size_t)Lt * P->n * P->n);
     P->o_bFtr = ws.take(16 * (size_t)std::max(Lt, 1));
     P->o_bGw = ws.take(8 * (size_t)std::max(Lt, 1));
+    P->o_bPart = ws.take(size_t(512) << 20);
     P->bwd_bytes = ws.top;
   }
 
@@ -656,6 +658,39 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
   if (P->part_cnt[3] > 0)
     (k_integrals<<<blocks((int64_t)P->ncc * P->ntp * na), 256, 0, st>>>(INT_X10, X.sp, X.Bo, X.wt, Lt, X.f, P->ncc,
                                                                        P->ntp * na, P->ntp * na, ws + P->o_X10), ++g_launches);
+}
+
+
+// C(m,n) = beta C(m,n) + sum_k opA(m,k) opB(k,n) (complex, tensor pipe), C(m,n)
+// at C[m*csm + n*csn].  Tile width bn = 64 or 16.  With `part` given and few
+// output tiles, K is split into segments summed in a fixed order (the output
+// region C[0 .. M*N) must then be dense in C's layout).
+void zgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
+           const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn, int beta,
+           int bn = 64, double2* part = nullptr, size_t part_bytes = 0) {
+  if (M <= 0 || N <= 0) return;
+  const int64_t tiles = ((M + 63) / 64) * ((N + bn - 1) / bn);
+  int nseg = 1;
+  if (part && K >= 256) {
+    nseg = (int)std::min<int64_t>(32, std::max<int64_t>(1, (4 * 148 + tiles - 1) / tiles));
+    nseg = (int)std::min<int64_t>(nseg, (int64_t)(part_bytes / (16 * (size_t)M * N)));
+    nseg = std::max(nseg, 1);
+  }
+  const int64_t kseg = (K + nseg - 1) / nseg;
+  dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + bn - 1) / bn), (unsigned)nseg);
+  double2* out = nseg > 1 ? part : C;
+  const int b = nseg > 1 ? 0 : beta;
+  const int64_t czs = M * N;
+  if (bn == 16)
+    (k_zgemm16<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, csm, csn, b, kseg, czs),
+     ++g_launches);
+  else
+    (k_zgemm64<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, csm, csn, b, kseg, czs),
+     ++g_launches);
+  if (nseg > 1) {
+    if (!beta) cudaMemsetAsync(C, 0, 16 * (size_t)M * N, st);
+    (k_zacc<<<blocks(M * N), 256, 0, st>>>(part, nseg, czs, M * N, C), ++g_launches);
+  }
 }
 
 // Coupling tensors of root r, the active one- and two-particle blocks of
@@ -1176,14 +1211,18 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         dim3 grid((unsigned)((Mc + 63) / 64), (unsigned)ct);
         (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
                                             L.eA, X.E0p + r, b, nullptr, adj), ++g_launches);
-        dim3 gz((unsigned)((Kp + 63) / 64), (unsigned)ct);
-        (k_zgemm<<<gz, 256, 0, st>>>(Kp, N, Mc, W + m0 * Kp, 1, Kp, 0, adj.T, N, 1, 1, GDfor[cls], N, 1), ++g_launches);
+        // Gamma_D[x][A] += sum_e W[e][x] conj(T[e][A]) (split over the rows of the chunk)
+        if (Kp >= 64)
+          zgemm(st, Kp, N, Mc, W + m0 * Kp, 1, Kp, 0, adj.T, N, 1, 1, GDfor[cls], N, 1, 1, 64,
+                (double2*)B(P->o_bPart), size_t(512) << 20);
+        else
+          zgemm(st, N, Kp, Mc, adj.T, 1, N, 1, W + m0 * Kp, Kp, 1, 0, GDfor[cls], 1, N, 1, 16,
+                (double2*)B(P->o_bPart), size_t(512) << 20);
         if (cls == 4)
           (k_rowdot<<<(unsigned)Mc, 256, 0, st>>>(adj.T, T.DTDU, N, (double2*)B(P->o_bRowdot) + m0), ++g_launches);
         if (want_B) {  // Gamma_W = conj(T) D^T and the per-row occupation sums of eta
-          dim3 gw_((unsigned)((Mc + 63) / 64), (unsigned)((Kp + 63) / 64));
-          (k_zgemm<<<gw_, 256, 0, st>>>(Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0,
-                                        (double2*)B(P->o_bGW[cls]) + m0 * Kp, Kp, 0), ++g_launches);
+          zgemm(st, Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0, (double2*)B(P->o_bGW[cls]) + m0 * Kp, Kp, 1, 0,
+                Kp >= 64 ? 64 : 16);
           (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na), ++g_launches);
         }
       }
@@ -1263,13 +1302,10 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         (k_gather_d1<<<blocks(Lsrc.n), 256, 0, st>>>(cls, L, Lsrc, P->das, X.sp, X.binom, Tg, nrow, X.f, GDsrc),
          ++g_launches);
       }
-      // two-body parts
-      const DevList& Ltab = (cls == 3) ? Lc[5] : Lc[2];
-      double2* GDtab = (cls == 3) ? GT.DT : GT.DTU;
-      const double2* Xb = (const double2*)(ws + ((cls == 1) ? P->o_X01 : (cls == 3) ? P->o_X10 : P->o_X00));
-      if (Ltab.n > 0)
-        (k_gather_d2<<<blocks(Ltab.n), 256, 0, st>>>(cls, L, Ltab, P->das, X.sp, X.binom, Tg, nrow, Xb, GDtab),
-         ++g_launches);
+      // two-body parts: per removed spinor u (or pair t<u) the shifted
+      // amplitudes Tsh[row][B] = conj(t[row][B + ...]) * sign give
+      //   Gamma_D[x][B] += sum_row X[row][...][x] Tsh[row][B]        (reference gradient)
+      //   Gamma_X[row][...][x] = sum_B Tsh[row][B] D[x][B]            (integral coefficients)
       if (want_B) {
         (k_rowsum<<<blocks(nrow), 256, 0, st>>>(Hg, nrow, L.n, 0, hsum), ++g_launches);
         (k_hocc<<<(unsigned)nrow, 256, 0, st>>>(Hg, L, na, Hocc), ++g_launches);
@@ -1278,47 +1314,51 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           zpair((const RowInfo*)B(P->o_bRg), nrow, hsum, Hocc);
         }
         (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
-        // integral coefficients: shifted amplitudes times the coupling table they read
-        double2* Tsh = (double2*)B(P->o_bTsh);
-        const int ntp = P->ntp;
-        if (cls == 1 && Lc[2].n > 0) {
-          double2* GX = (double2*)B(P->o_bGX01);
-          for (int u = 0; u < na; ++u) {
-            (k_tshift<<<dim3(blocks(Lc[2].n), nrow), 256, 0, st>>>(L, Lc[2], P->das, X.binom, Tg, nrow, u, -1, Tsh),
-             ++g_launches);
-            dim3 gz((unsigned)((nrow + 63) / 64), (unsigned)((ntp + 63) / 64));
-            (k_zgemm<<<gz, 256, 0, st>>>(nrow, ntp, Lc[2].n, Tsh, Lc[2].n, 1, 0, T.DTU, 1, Lc[2].n, 0, GX + (int64_t)u * ntp,
-                                         (int64_t)na * ntp, 0), ++g_launches);
-          }
+      }
+      double2* Tsh = (double2*)B(P->o_bTsh);
+      const int ntp = P->ntp;
+      if (cls == 1 && Lc[2].n > 0) {
+        const int64_t nb = Lc[2].n;
+        double2* GX = (double2*)B(P->o_bGX01);
+        const double2* X01 = (const double2*)(ws + P->o_X01);
+        for (int u = 0; u < na; ++u) {
+          (k_tshift<<<dim3(blocks(nb), nrow), 256, 0, st>>>(L, Lc[2], P->das, X.binom, Tg, nrow, u, -1, Tsh), ++g_launches);
+          zgemm(st, ntp, nb, nrow, X01 + (int64_t)u * ntp, 1, (int64_t)na * ntp, 0, Tsh, nb, 1, 0, GT.DTU, nb, 1, 1);
+          if (want_B)
+            zgemm(st, nrow, ntp, nb, Tsh, nb, 1, 0, T.DTU, 1, nb, 0, GX + (int64_t)u * ntp, (int64_t)na * ntp, 1, 0);
+        }
+        if (want_B)
           (k_gint<<<blocks((int64_t)nrow * na * ntp), 256, 0, st>>>(INT_X01, X.sp, GX, nrow, na * ntp, na * ntp, Gt,
                                                                    npair), ++g_launches);
-        }
-        if (cls == 3 && Lc[5].n > 0) {
-          double2* GX = (double2*)B(P->o_bGX10);
-          for (int u = 1; u < na; ++u)
-            for (int t = 0; t < u; ++t) {
-              const int tu = u * (u - 1) / 2 + t;
-              (k_tshift<<<dim3(blocks(Lc[5].n), nrow), 256, 0, st>>>(L, Lc[5], P->das, X.binom, Tg, nrow, t, u, Tsh),
-               ++g_launches);
-              dim3 gz((unsigned)((nrow + 63) / 64), (unsigned)((na + 63) / 64));
-              (k_zgemm<<<gz, 256, 0, st>>>(nrow, na, Lc[5].n, Tsh, Lc[5].n, 1, 0, T.DT, 1, Lc[5].n, 0,
-                                           GX + (int64_t)tu * na, (int64_t)ntp * na, 0), ++g_launches);
-            }
+      }
+      if (cls == 3 && Lc[5].n > 0) {
+        const int64_t nb = Lc[5].n;
+        double2* GX = (double2*)B(P->o_bGX10);
+        const double2* X10 = (const double2*)(ws + P->o_X10);
+        for (int u = 1; u < na; ++u)
+          for (int t = 0; t < u; ++t) {
+            const int tu = u * (u - 1) / 2 + t;
+            (k_tshift<<<dim3(blocks(nb), nrow), 256, 0, st>>>(L, Lc[5], P->das, X.binom, Tg, nrow, t, u, Tsh),
+             ++g_launches);
+            zgemm(st, na, nb, nrow, X10 + (int64_t)tu * na, 1, (int64_t)ntp * na, 0, Tsh, nb, 1, 0, GT.DT, nb, 1, 1, 16);
+            if (want_B)
+              zgemm(st, nrow, na, nb, Tsh, nb, 1, 0, T.DT, 1, nb, 0, GX + (int64_t)tu * na, (int64_t)ntp * na, 1, 0, 16);
+          }
+        if (want_B)
           (k_gint<<<blocks((int64_t)nrow * ntp * na), 256, 0, st>>>(INT_X10, X.sp, GX, nrow, ntp * na, ntp * na, Gt,
                                                                    npair), ++g_launches);
-        }
-        if (cls == 0 && Lc[2].n > 0) {
-          double2* GX = (double2*)B(P->o_bGX00);
-          for (int u = 1; u < na; ++u)
-            for (int t = 0; t < u; ++t) {
-              const int tu = u * (u - 1) / 2 + t;
-              (k_tshift<<<dim3(blocks(Lc[2].n), 1), 256, 0, st>>>(L, Lc[2], P->das, X.binom, Tg, 1, t, u, Tsh),
-               ++g_launches);
-              dim3 gz(1u, (unsigned)((ntp + 63) / 64));
-              (k_zgemm<<<gz, 256, 0, st>>>(1, ntp, Lc[2].n, Tsh, Lc[2].n, 1, 0, T.DTU, 1, Lc[2].n, 0,
-                                           GX + (int64_t)tu * ntp, ntp, 1), ++g_launches);
-            }
-        }
+      }
+      if (cls == 0 && Lc[2].n > 0) {
+        const int64_t nb = Lc[2].n;
+        double2* GX = (double2*)B(P->o_bGX00);
+        const double2* X00 = (const double2*)(ws + P->o_X00);
+        for (int u = 1; u < na; ++u)
+          for (int t = 0; t < u; ++t) {
+            const int tu = u * (u - 1) / 2 + t;
+            (k_tshift<<<dim3(blocks(nb), 1), 256, 0, st>>>(L, Lc[2], P->das, X.binom, Tg, 1, t, u, Tsh), ++g_launches);
+            zgemm(st, ntp, nb, 1, X00 + (int64_t)tu * ntp, 1, 1, 0, Tsh, nb, 1, 0, GT.DTU, nb, 1, 1);
+            if (want_B) zgemm(st, 1, ntp, nb, Tsh, nb, 1, 0, T.DTU, 1, nb, 0, GX + (int64_t)tu * ntp, ntp, 1, 1);
+          }
       }
     }
     // E0 term of the one-body coefficient, then the reference-state gradient
@@ -1354,8 +1394,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
     double* gw = (double*)B(P->o_bGw);
     (k_gg<<<blocks((int64_t)n * n), 256, 0, st>>>(X.sp, Nd, Ntt, Ge, Gea, GG), ++g_launches);
     (k_symm<<<blocks(npair * npair), 256, 0, st>>>(Gt, npair, Gh), ++g_launches);
-    dim3 gc_((unsigned)((Lt + 63) / 64), (unsigned)((npair + 63) / 64));
-    (k_zgemm<<<gc_, 256, 0, st>>>(Lt, npair, npair, X.Bo, npair, 1, 0, Gh, 1, npair, 0, Cs, npair, 0), ++g_launches);
+    zgemm(st, Lt, npair, npair, X.Bo, npair, 1, 0, Gh, 1, npair, 0, Cs, npair, 1, 0);
     (k_ftr<<<Lt, 256, 0, st>>>(X.sp, (const double2*)in->B_c, (const double2*)in->B_x, Lc_, Gf, ftr), ++g_launches);
     (k_bcoef<<<blocks((int64_t)Lt * n * n), 256, 0, st>>>(X.sp, (const double2*)in->B_c, (const double2*)in->B_x, Lc_,
                                                           Lx_, X.wt, X.dg, Cs, GG, Gf, ftr, GBc), ++g_launches);

@@ -49,8 +49,13 @@ __global__ void k_reduce(const double* partial, const int64_t* off, const int64_
 __global__ void k_finalize(const double* e2c, int n_roots, double* E2, const double* E0in, double* E0out);
 
 // adjoint (e2_adjoint.cu)
-__global__ void k_zgemm(int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
-                        const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t ldc, int beta);
+__global__ void k_zgemm64(int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
+                          const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn,
+                          int beta, int64_t kseg, int64_t czs);
+__global__ void k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
+                          const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn,
+                          int beta, int64_t kseg, int64_t czs);
+__global__ void k_zacc(const double2* part, int nseg, int64_t ps, int64_t count, double2* out);
 __global__ void k_rowsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);
 __global__ void k_colsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);
 __global__ void k_scalsum(const double* in, int64_t n, double* scal_out);
