@@ -26,11 +26,12 @@ namespace e2 {
 // grid.z segments of kseg, segment z writing C + z*czs (beta applies to each
 // segment's own output); a fixed-order sum of the segments (k_zacc) keeps the
 // result deterministic.  Each output element is owned by one CTA per segment.
+// With lower >= 0 only tiles holding some n <= lower + m are computed.
 template <int BN>
 __device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam,
                                            int64_t sak, int conjA, const double2* __restrict__ B, int64_t sbk,
                                            int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm, int64_t csn,
-                                           int beta, int64_t kseg, int64_t czs) {
+                                           int beta, int64_t kseg, int64_t czs, int64_t lower) {
   constexpr int BM = 64, BK = 8;
   constexpr int NI = BN / 32 > 0 ? BN / 32 : 1;       // n8 tiles per warp (64: 2, 16: 1)
   constexpr int WN = BN == 64 ? 4 : 2;                  // warps across N
@@ -39,6 +40,7 @@ __device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, cons
   __shared__ double sAr[BM][BK + 1], sAi[BM][BK + 1], sAs[BM][BK + 1];
   __shared__ double sBr[BK][BN + 1], sBi[BK][BN + 1], sBs[BK][BN + 1];
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  if (lower >= 0 && n0 > lower + m0 + BM - 1) return;  // tile above the diagonal n = lower + m
   const int64_t kb0 = (int64_t)blockIdx.z * kseg, kb1 = kb0 + kseg < K ? kb0 + kseg : K;
   C += (int64_t)blockIdx.z * czs;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -119,15 +121,15 @@ __device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, cons
 __global__ void __launch_bounds__(256, 1)
 k_zgemm64(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
           const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm,
-          int64_t csn, int beta, int64_t kseg, int64_t czs) {
-  zgemm_body<64>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs);
+          int64_t csn, int beta, int64_t kseg, int64_t czs, int64_t lower) {
+  zgemm_body<64>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower);
 }
 
 __global__ void __launch_bounds__(256, 1)
 k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
           const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm,
-          int64_t csn, int beta, int64_t kseg, int64_t czs) {
-  zgemm_body<16>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs);
+          int64_t csn, int beta, int64_t kseg, int64_t czs, int64_t lower) {
+  zgemm_body<16>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower);
 }
 
 // out[i] += sum_z part[z*ps + i] in z order, i < count (segments of a split-K

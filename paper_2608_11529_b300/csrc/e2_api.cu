@@ -76,6 +76,7 @@ struct e2_problem {
   size_t o_binom, o_EO, o_E0p, o_E0, o_G, o_epsh, o_dg, o_wt, o_Bo, o_f, o_cc, o_vc;
   size_t o_rows[E2_NCLASS], o_W[E2_NCLASS];
   size_t o_G22, o_X01, o_X10, o_X00;
+  size_t o_vaY, o_vaZ, o_vaX, va_cap;
   size_t o_DT, o_DTD, o_DTU, o_DTDUD, o_DTDU;  // per-root stride below
   size_t d_stride;                              // bytes per root of all D tables
   size_t o_g1, o_g2, g_stride;                  // gram outputs per root
@@ -333,6 +334,23 @@ e2_status build_plan(e2_problem* P) {
     }
   P->o_part = ws.take(sizeof(double) * std::max<int64_t>(tot, 1));
   P->o_e2c = ws.take(sizeof(double) * R * E2_NCLASS);
+  // Scratch of the (0,2) integrals: weighted and plain (virtual, active)
+  // factor columns and a stripe of (at|bu).  It lies over the D tables and
+  // partials, which are written only after the integrals are formed; the
+  // stripe takes what is left there (at least 8 virtuals of rows, at most
+  // the whole lower triangle) and extends the workspace only when needed.
+  {
+    const int64_t nva = (int64_t)P->nvc * P->na;
+    const size_t yb = 16 * (size_t)std::max<int64_t>(nva * Lt, 1);
+    P->o_vaY = P->o_dstart;
+    P->o_vaZ = P->o_vaY + yb;
+    P->o_vaX = P->o_vaZ + yb;
+    const size_t full = 16 * (size_t)std::max<int64_t>(nva * nva, 1);
+    const size_t least = 16 * (size_t)std::max<int64_t>((int64_t)std::min(8, P->nvc) * P->na * nva, 1);
+    const size_t room = ws.top > P->o_vaX ? ws.top - P->o_vaX : 0;
+    P->va_cap = std::min(full, std::max(least, room));
+    ws.top = std::max(ws.top, P->o_vaX + P->va_cap);
+  }
   P->ws_bytes = ws.top;
   // reference solver (block Davidson) on top of the forward layout
   const int64_t np_ = P->lists[P->listP].n;
@@ -602,6 +620,38 @@ void build_tables(const e2_problem* P, unsigned char* ws, cudaStream_t st, const
   }
 }
 
+// C(m,n) = beta C(m,n) + sum_k opA(m,k) opB(k,n) (complex, tensor pipe), C(m,n)
+// at C[m*csm + n*csn].  Tile width bn = 64 or 16.  With `part` given and few
+// output tiles, K is split into segments summed in a fixed order (the output
+// region C[0 .. M*N) must then be dense in C's layout).
+void zgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
+           const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn, int beta,
+           int bn = 64, double2* part = nullptr, size_t part_bytes = 0) {
+  if (M <= 0 || N <= 0) return;
+  const int64_t tiles = ((M + 63) / 64) * ((N + bn - 1) / bn);
+  int nseg = 1;
+  if (part && K >= 256) {
+    nseg = (int)std::min<int64_t>(32, std::max<int64_t>(1, (4 * 148 + tiles - 1) / tiles));
+    nseg = (int)std::min<int64_t>(nseg, (int64_t)(part_bytes / (16 * (size_t)M * N)));
+    nseg = std::max(nseg, 1);
+  }
+  const int64_t kseg = (K + nseg - 1) / nseg;
+  dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + bn - 1) / bn), (unsigned)nseg);
+  double2* out = nseg > 1 ? part : C;
+  const int b = nseg > 1 ? 0 : beta;
+  const int64_t czs = M * N;
+  if (bn == 16)
+    (k_zgemm16<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, csm, csn, b, kseg, czs, -1),
+     ++g_launches);
+  else
+    (k_zgemm64<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, csm, csn, b, kseg, czs, -1),
+     ++g_launches);
+  if (nseg > 1) {
+    if (!beta) cudaMemsetAsync(C, 0, 16 * (size_t)M * N, st);
+    (k_zacc<<<blocks(M * N), 256, 0, st>>>(part, nseg, czs, M * N, C), ++g_launches);
+  }
+}
+
 // Everything that depends only on the Hamiltonian and the partition:
 // binomials, compact factors, G, eps^, f, E_O, string lists with e_A and U,
 // and the active two-electron block <tu||vw>.
@@ -646,6 +696,27 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
   for (int c = 0; c < E2_NCLASS; ++c) {
     if (modes[c] < 0 || P->M[c] == 0 || P->part_cnt[c] == 0) continue;
     (k_rows<<<blocks(P->M[c]), 256, 0, st>>>(c, X.sp, X.epsh, X.G, P->M[c], (RowInfo*)(ws + P->o_rows[c])), ++g_launches);
+    if (c == 2) {
+      // (at|bu) = sum_L wt_L B_at B_bu on the tensor pipe, lower triangle
+      // (a < b) in stripes of whole virtuals b, then <ab||tu> = (at|bu) - (au|bt)
+      const int64_t nva = (int64_t)P->nvc * na;
+      double2* Yw = (double2*)(ws + P->o_vaY);
+      double2* Zf = (double2*)(ws + P->o_vaZ);
+      double2* Xv = (double2*)(ws + P->o_vaX);
+      (k_vafactors<<<blocks(nva * Lt), 256, 0, st>>>(X.sp, X.Bo, X.wt, Lt, Yw, Zf), ++g_launches);
+      for (int b0 = 0, b1; b0 < P->nvc; b0 = b1) {
+        b1 = b0 + 1;
+        while (b1 < P->nvc && 16 * (size_t)(b1 + 1 - b0) * na * (size_t)(b1 + 1) * na <= P->va_cap) ++b1;
+        const int64_t r0 = (int64_t)b0 * na, rows = (int64_t)(b1 - b0) * na, ldx = (int64_t)b1 * na;
+        dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((ldx + 63) / 64), 1);
+        (k_zgemm64<<<grid, 256, 0, st>>>(rows, ldx, Lt, Yw + r0 * Lt, Lt, 1, 0, Zf, nva, 1, 0, Xv, ldx, 1, 0, Lt, 0,
+                                          r0), ++g_launches);
+        if (pairs(b1) > pairs(b0))
+          (k_w02<<<blocks((pairs(b1) - pairs(b0)) * P->Kp[c]), 256, 0, st>>>(X.sp, Xv, ldx, b0, b1, P->Kp[c],
+                                                                             (double2*)(ws + P->o_W[c])), ++g_launches);
+      }
+      continue;
+    }
     (k_integrals<<<blocks(P->M[c] * P->Kp[c]), 256, 0, st>>>(modes[c], X.sp, X.Bo, X.wt, Lt, X.f, P->M[c], cols[c],
                                                              P->Kp[c], ws + P->o_W[c]), ++g_launches);
   }
@@ -660,38 +731,6 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
                                                                        P->ntp * na, P->ntp * na, ws + P->o_X10), ++g_launches);
 }
 
-
-// C(m,n) = beta C(m,n) + sum_k opA(m,k) opB(k,n) (complex, tensor pipe), C(m,n)
-// at C[m*csm + n*csn].  Tile width bn = 64 or 16.  With `part` given and few
-// output tiles, K is split into segments summed in a fixed order (the output
-// region C[0 .. M*N) must then be dense in C's layout).
-void zgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
-           const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn, int beta,
-           int bn = 64, double2* part = nullptr, size_t part_bytes = 0) {
-  if (M <= 0 || N <= 0) return;
-  const int64_t tiles = ((M + 63) / 64) * ((N + bn - 1) / bn);
-  int nseg = 1;
-  if (part && K >= 256) {
-    nseg = (int)std::min<int64_t>(32, std::max<int64_t>(1, (4 * 148 + tiles - 1) / tiles));
-    nseg = (int)std::min<int64_t>(nseg, (int64_t)(part_bytes / (16 * (size_t)M * N)));
-    nseg = std::max(nseg, 1);
-  }
-  const int64_t kseg = (K + nseg - 1) / nseg;
-  dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + bn - 1) / bn), (unsigned)nseg);
-  double2* out = nseg > 1 ? part : C;
-  const int b = nseg > 1 ? 0 : beta;
-  const int64_t czs = M * N;
-  if (bn == 16)
-    (k_zgemm16<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, csm, csn, b, kseg, czs),
-     ++g_launches);
-  else
-    (k_zgemm64<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, csm, csn, b, kseg, czs),
-     ++g_launches);
-  if (nseg > 1) {
-    if (!beta) cudaMemsetAsync(C, 0, 16 * (size_t)M * N, st);
-    (k_zacc<<<blocks(M * N), 256, 0, st>>>(part, nseg, czs, M * N, C), ++g_launches);
-  }
-}
 
 // Coupling tensors of root r, the active one- and two-particle blocks of
 // its reference state, and E0 (Sec. 2.3).
@@ -864,7 +903,7 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
   if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
   setup_classes(P, ws, st);
   const e2_desc& d = P->d;
-  const int na = P->na, R = d.n_roots;
+  const int R = d.n_roots;
   const double b = d.level_shift_b;
   Ctx X = ctx(P, ws);
   const DevList LP = dev_list(P, P->listP, ws);

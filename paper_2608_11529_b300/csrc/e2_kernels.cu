@@ -211,6 +211,47 @@ __global__ void k_integrals(int mode, DevSpace sp, const double2* __restrict__ B
   else ((double2*)out)[idx] = v;
 }
 
+// Factor columns of the (virtual, active) pairs, nva = nvc * na:
+//   Yw[(a*na + t)*Lt + L] = wt_L B^L_{a t}   (row-major in the pair)
+//   Zt[L*nva + a*na + t] = B^L_{a t}         (row-major in L)
+__global__ void k_vafactors(DevSpace sp, const double2* __restrict__ Bo, const double* __restrict__ wt, int Lt,
+                            double2* __restrict__ Yw, double2* __restrict__ Zt) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int na = sp.n_act;
+  const int64_t nva = (int64_t)sp.nvc * na;
+  if (idx >= nva * Lt) return;
+  const int L = (int)(idx / nva);
+  const int64_t at = idx % nva;
+  const int a = (int)(at / na), t = (int)(at % na);
+  const double2 b = Bo[((int64_t)L * sp.n + sp.vc[a]) * sp.n_occ + sp.a0 + t];
+  Zt[idx] = b;
+  Yw[at * Lt + L] = make_double2(wt[L] * b.x, wt[L] * b.y);
+}
+
+// <ab||tu> = (at|bu) - (au|bt) for the rows (a<b) with b0 <= b < b1 (a
+// contiguous run of rows in pair order), columns (t<u) padded to Kp with zeros,
+// from a stripe X[(b*na + u - b0*na)*ldx + a*na + t] = (at|bu), a < b.
+__global__ void k_w02(DevSpace sp, const double2* __restrict__ X, int64_t ldx, int b0, int b1, int Kp,
+                      double2* __restrict__ W) {
+  const int64_t r0 = pairs(b0), nrow = pairs(b1) - r0;
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= nrow * Kp) return;
+  const int64_t row = r0 + idx / Kp;
+  const int col = (int)(idx % Kp);
+  const int na = sp.n_act;
+  double2 v = make_double2(0.0, 0.0);
+  if (col < (int)pairs(na)) {
+    int a, b, t, u;
+    pair_decode(row, a, b);
+    pair_decode(col, t, u);
+    const double2* Xb = X + (int64_t)(b - b0) * na * ldx;
+    const double2 x1 = Xb[(int64_t)u * ldx + (int64_t)a * na + t];
+    const double2 x2 = Xb[(int64_t)t * ldx + (int64_t)a * na + u];
+    v = make_double2(x1.x - x2.x, x1.y - x2.y);
+  }
+  W[row * Kp + col] = v;
+}
+
 // Row descriptors of the dense classes: U rows of particles / holes and
 // chi(e) = -sum_I eps^_i + [h=2] G_ij + sum_S eps^_s + [p=2] G_ab - sum_{IxS} G.
 __global__ void k_rows(int cls, DevSpace sp, const double* __restrict__ epsh, const double* __restrict__ G, int64_t M,

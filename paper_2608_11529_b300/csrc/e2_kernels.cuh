@@ -17,6 +17,8 @@ __global__ void k_eA(DevList Ls, const double* epsh, const double* G, int n, int
 __global__ void k_U(DevList Ls, DevSpace sp, const double* G);
 __global__ void k_integrals(int mode, DevSpace sp, const double2* Bo, const double* wt, int L, const double2* f,
                             int64_t rows, int cols, int ld, void* out);
+__global__ void k_vafactors(DevSpace sp, const double2* Bo, const double* wt, int Lt, double2* Yw, double2* Z);
+__global__ void k_w02(DevSpace sp, const double2* X, int64_t ldx, int b0, int b1, int Kp, double2* W);
 __global__ void k_rows(int cls, DevSpace sp, const double* epsh, const double* G, int64_t M, RowInfo* out);
 __global__ void k_dtable(int fam, DevList Ls, DevList Pl, DevDas das, const int64_t* binom, const double2* c, int Kp,
                          double2* D);
@@ -51,10 +53,10 @@ __global__ void k_finalize(const double* e2c, int n_roots, double* E2, const dou
 // adjoint (e2_adjoint.cu)
 __global__ void k_zgemm64(int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
                           const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn,
-                          int beta, int64_t kseg, int64_t czs);
+                          int beta, int64_t kseg, int64_t czs, int64_t lower);
 __global__ void k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
                           const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn,
-                          int beta, int64_t kseg, int64_t czs);
+                          int beta, int64_t kseg, int64_t czs, int64_t lower);
 __global__ void k_zacc(const double2* part, int nseg, int64_t ps, int64_t count, double2* out);
 __global__ void k_rowsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);
 __global__ void k_colsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);
