@@ -180,6 +180,9 @@ E2_API e2_status e2_batch_launch_count(const e2_batch* batch, int64_t* n);
  *   dE2_dlambda device [1]      dF/dlambda: the Gaunt / Breit share of the
  *                               correlation energy to first order, or NULL
  *   seed host [n_roots]
+ *   E2   device [n_roots], or NULL: the energies themselves, bitwise equal to
+ *        e2_forward's (the pass forms every V anyway), so that one call gives
+ *        the value and its gradient
  * V is recomputed (never stored whole): the dense classes run in row chunks
  * whose weighted amplitudes fit a 2 GiB buffer.  Enqueues on `stream`;
  * workspace of at least e2_backward_workspace_size() bytes (it contains the
@@ -187,7 +190,7 @@ E2_API e2_status e2_batch_launch_count(const e2_batch* batch, int64_t* n);
 E2_API e2_status e2_backward_workspace_size(const e2_problem* prob, size_t* bytes);
 E2_API e2_status e2_backward(e2_problem* prob, const e2_inputs* in, const double* seed, void* workspace,
                              size_t workspace_bytes, void* stream, double* g_h, double* g_c, double* g_Bc,
-                             double* g_Bx, double* dE2_dlambda);
+                             double* g_Bx, double* dE2_dlambda, double* E2);
 
 /* Reference states: the n_roots lowest eigenvectors of P H P (the CASCI /
  * DAS-CI reference of Sec. 2.2-2.3, Eq. zeroh first term), by block Davidson

@@ -60,7 +60,7 @@ def load():
         L.e2_backward_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
         L.e2_backward_workspace_size.restype = C.c_int
         L.e2_backward.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
-                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.e2_backward.restype = C.c_int
         L.e2_batch_create.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]
         L.e2_batch_create.restype = C.c_int
@@ -168,11 +168,12 @@ class E2Problem:
         return self._ws
 
     def backward(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, seed=None, want_h=True, want_c=True, want_B=False,
-                 want_lambda=False, stream=None):
+                 want_lambda=False, stream=None, E2_out=None):
         """Gradient of sum_m seed[m] E2_m: returns (g_h [n, n], g_c [roots, N_P],
         g_Bc [Lc, n, n], g_Bx [Lx, n, n], dE2/dlambda [1]) as CUDA tensors (None
         where not requested); complex gradients are dE/dRe + i dE/dIm, h and B
-        Hermitian-projected."""
+        Hermitian-projected.  E2_out (float64 CUDA [roots]), if given, receives
+        the energies of the same pass."""
         import torch
         dev = c.device
         ws = self.workspace(dev, backward=True)
@@ -187,10 +188,21 @@ class E2Problem:
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
         ptr = lambda x: x.data_ptr() if x is not None else None
         _check(load().e2_backward(self._h, C.byref(inp), seed.ctypes.data_as(C.c_void_p), ws.data_ptr(), ws.numel(),
-                                  C.c_void_p(s), ptr(gh), ptr(gc), ptr(gbc), ptr(gbx), ptr(dl)))
+                                  C.c_void_p(s), ptr(gh), ptr(gc), ptr(gbc), ptr(gbx), ptr(dl), ptr(E2_out)))
         if want_B or want_lambda:
             return gh, gc, gbc, gbx, dl
         return gh, gc
+
+    def value_and_grad(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, seed=None, want_B=True, want_lambda=True,
+                       stream=None):
+        """E2 [roots] and the gradient of sum_m seed[m] E2_m from one pass
+        (V formed once): returns (E2, g_h, g_c, g_Bc, g_Bx, dE2/dlambda)."""
+        import torch
+        E2 = torch.empty(self.n_roots, dtype=torch.float64, device=c.device)
+        g = self.backward(h, B_c, c, B_x=B_x, w_x=w_x, lam=lam, seed=seed, want_B=want_B, want_lambda=want_lambda,
+                          stream=stream, E2_out=E2)
+        g = tuple(g) + (None,) * (5 - len(g))
+        return (E2,) + g
 
     def reference_solve(self, h, B_c, X0, B_x=None, w_x=None, lam=1.0, tol=1e-10, max_iter=300, stream=None):
         """Lowest n_roots eigenvectors of P H P from start vectors X0 [roots, N_P]

@@ -53,28 +53,62 @@ __device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, cons
     for (int c = 0; c < NI; ++c)
 #pragma unroll
       for (int e = 0; e < 4; ++e) t1[a][c][e] = t2[a][c][e] = t3[a][c][e] = 0.0;
-  const int ar = tid >> 3, ak = tid & 7;
+  // load maps follow the contiguous operand dimension: A rows fastest when
+  // sam == 1 (else k fastest), B columns fastest unless sbk == 1
+  constexpr int NB = (BK * BN + 255) / 256;  // B elements per thread (64: 2, 16: 1 on half the threads)
+  const bool a_mfast = (sam == 1 && sak != 1), b_kfast = (sbk == 1 && sbn != 1);
+  int ra[2], ka[2], rb[NB], kb_[NB];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    ra[q] = a_mfast ? (tid & 63) : (tid >> 3) + 32 * q;
+    ka[q] = a_mfast ? (tid >> 6) + 4 * q : (tid & 7);
+  }
+#pragma unroll
+  for (int q = 0; q < NB; ++q) {
+    const int e = tid + 256 * q;
+    rb[q] = b_kfast ? e / BK : e % BN;
+    kb_[q] = b_kfast ? e % BK : e / BN;
+  }
   const double2 zero = make_double2(0.0, 0.0);
+  auto ldA = [&](int64_t k0, int q) {
+    const int64_t m = m0 + ra[q], k = k0 + ka[q];
+    double2 v = (m < M && k < kb1) ? A[m * sam + k * sak] : zero;
+    if (conjA) v.y = -v.y;
+    return v;
+  };
+  auto ldB = [&](int64_t k0, int q) {
+    const int64_t kb = k0 + kb_[q], nn = n0 + rb[q];
+    double2 u = (tid + 256 * q < BK * BN && kb < kb1 && nn < N) ? B[kb * sbk + nn * sbn] : zero;
+    if (conjB) u.y = -u.y;
+    return u;
+  };
+  // register prefetch of the next K step while the tensor pipe works on this one
+  double2 pa[2], pb[NB];
+  pa[0] = ldA(kb0, 0);
+  pa[1] = ldA(kb0, 1);
+#pragma unroll
+  for (int q = 0; q < NB; ++q) pb[q] = ldB(kb0, q);
   for (int64_t k0 = kb0; k0 < kb1; k0 += BK) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
-      const int64_t m = m0 + ar + 32 * q, k = k0 + ak;
-      double2 v = (m < M && k < kb1) ? A[m * sam + k * sak] : zero;
-      if (conjA) v.y = -v.y;
-      sAr[ar + 32 * q][ak] = v.x;
-      sAi[ar + 32 * q][ak] = v.y;
-      sAs[ar + 32 * q][ak] = v.x + v.y;
+      sAr[ra[q]][ka[q]] = pa[q].x;
+      sAi[ra[q]][ka[q]] = pa[q].y;
+      sAs[ra[q]][ka[q]] = pa[q].x + pa[q].y;
     }
-    for (int e = tid; e < BK * BN; e += 256) {
-      const int bk = e / BN, bc = e % BN;
-      const int64_t kb = k0 + bk, nn = n0 + bc;
-      double2 u = (kb < kb1 && nn < N) ? B[kb * sbk + nn * sbn] : zero;
-      if (conjB) u.y = -u.y;
-      sBr[bk][bc] = u.x;
-      sBi[bk][bc] = u.y;
-      sBs[bk][bc] = u.x + u.y;
-    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q)
+      if (tid + 256 * q < BK * BN) {
+        sBr[kb_[q]][rb[q]] = pb[q].x;
+        sBi[kb_[q]][rb[q]] = pb[q].y;
+        sBs[kb_[q]][rb[q]] = pb[q].x + pb[q].y;
+      }
     __syncthreads();
+    if (k0 + BK < kb1) {
+      pa[0] = ldA(k0 + BK, 0);
+      pa[1] = ldA(k0 + BK, 1);
+#pragma unroll
+      for (int q = 0; q < NB; ++q) pb[q] = ldB(k0 + BK, q);
+    }
     double br[NI][2], bi[NI][2], bs[NI][2];
 #pragma unroll
     for (int ni = 0; ni < NI; ++ni) {
@@ -132,28 +166,43 @@ k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_
   zgemm_body<16>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower);
 }
 
-// out[i] += sum_z part[z*ps + i] in z order, i < count (segments of a split-K
-// product, written in the output's own layout)
-__global__ void k_zacc(const double2* __restrict__ part, int nseg, int64_t ps, int64_t count, double2* __restrict__ out) {
+// C(m,n) = beta C(m,n) + sum_z part[z*ps + m*N + n] in z order (segments of a
+// split-K product, each dense row-major), C(m,n) at C[m*csm + n*csn]
+__global__ void k_zacc(const double2* __restrict__ part, int nseg, int64_t ps, int64_t M, int64_t N,
+                       double2* __restrict__ C, int64_t csm, int64_t csn, int beta) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= count) return;
-  double2 v = out[i];
+  if (i >= M * N) return;
+  double2* out = C + (i / N) * csm + (i % N) * csn;
+  double2 v = beta ? *out : make_double2(0.0, 0.0);
   for (int z = 0; z < nseg; ++z) {
     const double2 p = part[z * ps + i];
     v.x += p.x;
     v.y += p.y;
   }
+  *out = v;
+}
+
+// out[i] += sum_z part[z*ps + i] in z order (real split-K segments)
+__global__ void k_dacc(const double* __restrict__ part, int nseg, int64_t ps, int64_t count, double* __restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  double v = out[i];
+  for (int z = 0; z < nseg; ++z) v += part[z * ps + i];
   out[i] = v;
 }
 
 // C[m][n] = beta * C[m][n] + sum_k A[m*sam + k*sak] B[k*sbk + n*sbn], real,
-// on the FP64 tensor pipe; one CTA per 64x64 tile of C over the full K.
+// on the FP64 tensor pipe; one CTA per 64x64 tile of C and K segment
+// (grid.z segments of kseg, segment z writing C + z*czs).
 __global__ void __launch_bounds__(256, 2)
 k_dgemm(int64_t M, int64_t N, int64_t K, const double* __restrict__ A, int64_t sam, int64_t sak,
-        const double* __restrict__ B, int64_t sbk, int64_t sbn, double* __restrict__ C, int64_t ldc, int beta) {
+        const double* __restrict__ B, int64_t sbk, int64_t sbn, double* __restrict__ C, int64_t ldc, int beta,
+        int64_t kseg, int64_t czs) {
   constexpr int BM = 64, BN = 64, BK = 8;
   __shared__ double sA[BM][BK + 1], sB[BK][BN + 1];
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t kb0 = (int64_t)blockIdx.z * kseg, K1 = kb0 + kseg < K ? kb0 + kseg : K;
+  C += (int64_t)blockIdx.z * czs;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tq = lane & 3;
   const int wm = warp >> 2, wn = warp & 3;
@@ -165,13 +214,13 @@ k_dgemm(int64_t M, int64_t N, int64_t K, const double* __restrict__ A, int64_t s
 #pragma unroll
       for (int e = 0; e < 4; ++e) acc[a][c][e] = 0.0;
   const int ar = tid >> 3, ak = tid & 7, bk = tid >> 6, bc = tid & 63;
-  for (int64_t k0 = 0; k0 < K; k0 += BK) {
+  for (int64_t k0 = kb0; k0 < K1; k0 += BK) {
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const int64_t m = m0 + ar + 32 * q, k = k0 + ak;
-      sA[ar + 32 * q][ak] = (m < M && k < K) ? A[m * sam + k * sak] : 0.0;
+      sA[ar + 32 * q][ak] = (m < M && k < K1) ? A[m * sam + k * sak] : 0.0;
       const int64_t kb = k0 + bk + 4 * q, nn = n0 + bc;
-      sB[bk + 4 * q][bc] = (kb < K && nn < N) ? B[kb * sbk + nn * sbn] : 0.0;
+      sB[bk + 4 * q][bc] = (kb < K1 && nn < N) ? B[kb * sbk + nn * sbn] : 0.0;
     }
     __syncthreads();
 #pragma unroll
@@ -844,14 +893,18 @@ __global__ void k_gint(int mode, DevSpace sp, const double2* __restrict__ Gam, i
   b->y -= v.y;
 }
 
-// Tsh[row][B] = conj(T[row][A]) * sign for A = B + t (u < 0) or A = B + t + u
-// (t < u), sign of the coupling-table entry D_B the class reads for A; zero
-// when t or u is in B or A is not in the class list.
+// Shifted amplitudes of a gather class for rows [row0, row0 + gridDim.y) and
+// every shift z = blockIdx.z: one removed spinor t = z (pairs == 0) or a pair
+// t < u with z = u(u-1)/2 + t.  Tsh[(y*S + z)*nB + g] = conj(T[row][A]) * sign
+// for A = B_g + t (+ u), the sign of the coupling-table entry D_B the class
+// reads for A; zero when t or u is in B or A is not in the class list.
 __global__ void k_tshift(DevList Lx, DevList Ltab, DevDas das, const int64_t* __restrict__ binom,
-                         const double2* __restrict__ T, int nrow, int t, int u, double2* __restrict__ Tsh) {
+                         const double2* __restrict__ T, int row0, int pairs_mode, double2* __restrict__ Tsh) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int row = blockIdx.y;
   if (g >= Ltab.n) return;
+  const int y = blockIdx.y, z = blockIdx.z, S = gridDim.z;
+  int t = z, u = -1;
+  if (pairs_mode) pair_decode(z, t, u);
   const uint64_t B = Ltab.str[g];
   double2 v = make_double2(0.0, 0.0);
   const bool clash = ((B >> t) & 1) || (u >= 0 && ((B >> u) & 1));
@@ -859,12 +912,12 @@ __global__ void k_tshift(DevList Lx, DevList Ltab, DevDas das, const int64_t* __
     const uint64_t A = B | (1ull << t) | (u >= 0 ? (1ull << u) : 0ull);
     const int64_t ax = list_addr(Lx, das, binom, A);
     if (ax >= 0) {
-      v = cconj(T[(int64_t)row * Lx.n + ax]);
+      v = cconj(T[(int64_t)(row0 + y) * Lx.n + ax]);
       const int par = (u < 0) ? popc_below(A, t) : popc_below(B, u) + popc_below(B, t);
       if (par & 1) v = make_double2(-v.x, -v.y);
     }
   }
-  Tsh[(int64_t)row * Ltab.n + g] = v;
+  Tsh[((int64_t)y * S + z) * Ltab.n + g] = v;
 }
 
 // Row-owner pass of class (2,2): one block per row (i<j, a<b).  For every A:

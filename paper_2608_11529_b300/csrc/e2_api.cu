@@ -102,7 +102,8 @@ struct e2_problem {
   int64_t npair;
   size_t o_bGW[E2_NCLASS], o_bHm, o_bHocc, o_bZ, o_bZs, o_bGe, o_bGea, o_bNtt, o_bGG, o_bGt, o_bGh, o_bTsh;
   size_t o_bGX01, o_bGX10, o_bGX00, o_bR22, o_bHs22, o_bP22, o_bG22c, o_bGg22, o_bCs, o_bGB, o_bFtr, o_bGw, o_bRg;
-  size_t o_bPart;  // split-K segments
+  size_t o_bPart, bpart_bytes;  // split-K segments
+  size_t tsh_bytes;
   size_t bwd_bytes;
 };
 
@@ -432,8 +433,15 @@ e2_status build_plan(e2_problem* P) {
         hocc = std::max(hocc, (size_t)8 * P->M[c] * P->na);
         zz = std::max(zz, (size_t)8 * P->M[c] * P->nx);
       }
-    tsh = std::max<size_t>(tsh, 16 * (size_t)std::max<int64_t>(P->nvc, 1) * std::max<int64_t>(lsize(2), 1));
-    tsh = std::max<size_t>(tsh, 16 * (size_t)std::max<int64_t>(P->ncc, 1) * std::max<int64_t>(lsize(5), 1));
+    {  // shifted amplitudes of the gather classes: all shifts of a row chunk
+      const size_t n01 = 16 * (size_t)P->na * std::max<int64_t>(lsize(2), 1);
+      const size_t n10 = 16 * (size_t)std::max(P->ntp, 1) * std::max<int64_t>(lsize(5), 1);
+      const size_t n00 = 16 * (size_t)std::max(P->ntp, 1) * std::max<int64_t>(lsize(2), 1);
+      const size_t one = std::max(n01, std::max(n10, n00));
+      const size_t all = std::max(n01 * std::max(P->nvc, 1), std::max(n10 * std::max(P->ncc, 1), n00));
+      tsh = std::max(one, std::min(all, size_t(1) << 30));
+      P->tsh_bytes = tsh;
+    }
     P->o_bHm = ws.take(hm);
     P->o_bHocc = ws.take(hocc);
     P->o_bZ = ws.take(zz);
@@ -458,7 +466,8 @@ e2_status build_plan(e2_problem* P) {
     P->o_bGB = ws.take(16 * (size_t)Lt * P->n * P->n);
     P->o_bFtr = ws.take(16 * (size_t)std::max(Lt, 1));
     P->o_bGw = ws.take(8 * (size_t)std::max(Lt, 1));
-    P->o_bPart = ws.take(size_t(512) << 20);
+    P->bpart_bytes = size_t(512) << 20;
+    P->o_bPart = ws.take(P->bpart_bytes);
     P->bwd_bytes = ws.top;
   }
 
@@ -620,36 +629,65 @@ void build_tables(const e2_problem* P, unsigned char* ws, cudaStream_t st, const
   }
 }
 
+// Scratch for split-K segments of the GEMM helpers (set while a pass that
+// owns such a region runs; null: no split).
+thread_local void* g_splitk = nullptr;
+thread_local size_t g_splitk_bytes = 0;
+
+// Segments for a product with `tiles` output tiles and contraction K: enough
+// CTAs for two per SM over the B300's 148 SMs, at least 256 of K each.
+int splitk_segments(int64_t tiles, int64_t K, size_t seg_bytes) {
+  if (!g_splitk || K < 512) return 1;
+  int64_t n = (2 * 2 * 148 + tiles - 1) / tiles;
+  n = std::min<int64_t>(n, K / 256);
+  n = std::min<int64_t>(n, 64);
+  n = std::min<int64_t>(n, (int64_t)(g_splitk_bytes / std::max<size_t>(seg_bytes, 1)));
+  return (int)std::max<int64_t>(n, 1);
+}
+
+// C(m,n) = beta C(m,n) + sum_k opA(m,k) opB(k,n) (real, tensor pipe), C row-major
+// with leading dimension ldc = N when split.
+void dgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double* A, int64_t sam, int64_t sak,
+           const double* B, int64_t sbk, int64_t sbn, double* C, int64_t ldc, int beta) {
+  if (M <= 0 || N <= 0) return;
+  const int64_t tiles = ((M + 63) / 64) * ((N + 63) / 64);
+  const int nseg = ldc == N ? splitk_segments(tiles, K, 8 * (size_t)M * N) : 1;  // segments dense in C's layout
+  const int64_t kseg = (K + nseg - 1) / nseg;
+  dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + 63) / 64), (unsigned)nseg);
+  if (nseg == 1) {
+    (k_dgemm<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, beta, kseg, 0), ++g_launches);
+    return;
+  }
+  double* part = (double*)g_splitk;
+  (k_dgemm<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, B, sbk, sbn, part, ldc, 0, kseg, M * N), ++g_launches);
+  if (!beta) cudaMemsetAsync(C, 0, 8 * (size_t)M * N, st);
+  (k_dacc<<<blocks(M * N), 256, 0, st>>>(part, nseg, M * N, M * N, C), ++g_launches);
+}
+
 // C(m,n) = beta C(m,n) + sum_k opA(m,k) opB(k,n) (complex, tensor pipe), C(m,n)
 // at C[m*csm + n*csn].  Tile width bn = 64 or 16.  With `part` given and few
 // output tiles, K is split into segments summed in a fixed order (the output
 // region C[0 .. M*N) must then be dense in C's layout).
 void zgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
            const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn, int beta,
-           int bn = 64, double2* part = nullptr, size_t part_bytes = 0) {
+           int bn = 64) {
   if (M <= 0 || N <= 0) return;
   const int64_t tiles = ((M + 63) / 64) * ((N + bn - 1) / bn);
-  int nseg = 1;
-  if (part && K >= 256) {
-    nseg = (int)std::min<int64_t>(32, std::max<int64_t>(1, (4 * 148 + tiles - 1) / tiles));
-    nseg = (int)std::min<int64_t>(nseg, (int64_t)(part_bytes / (16 * (size_t)M * N)));
-    nseg = std::max(nseg, 1);
-  }
+  const int nseg = splitk_segments(tiles, K, 16 * (size_t)M * N);
   const int64_t kseg = (K + nseg - 1) / nseg;
   dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + bn - 1) / bn), (unsigned)nseg);
-  double2* out = nseg > 1 ? part : C;
+  // split: segment z is written dense row-major at scratch + z*M*N, then summed into C
+  double2* out = nseg > 1 ? (double2*)g_splitk : C;
+  const int64_t om = nseg > 1 ? N : csm, on = nseg > 1 ? 1 : csn;
   const int b = nseg > 1 ? 0 : beta;
   const int64_t czs = M * N;
   if (bn == 16)
-    (k_zgemm16<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, csm, csn, b, kseg, czs, -1),
+    (k_zgemm16<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, om, on, b, kseg, czs, -1),
      ++g_launches);
   else
-    (k_zgemm64<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, csm, csn, b, kseg, czs, -1),
+    (k_zgemm64<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, om, on, b, kseg, czs, -1),
      ++g_launches);
-  if (nseg > 1) {
-    if (!beta) cudaMemsetAsync(C, 0, 16 * (size_t)M * N, st);
-    (k_zacc<<<blocks(M * N), 256, 0, st>>>(part, nseg, czs, M * N, C), ++g_launches);
-  }
+  if (nseg > 1) (k_zacc<<<blocks(M * N), 256, 0, st>>>(out, nseg, czs, M, N, C, csm, csn, beta), ++g_launches);
 }
 
 // Everything that depends only on the Hamiltonian and the partition:
@@ -1158,7 +1196,8 @@ e2_status e2_backward_workspace_size(const e2_problem* P, size_t* bytes) {
 }
 
 e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, void* workspace, size_t workspace_bytes,
-                      void* stream_, double* g_h, double* g_c, double* g_Bc, double* g_Bx, double* dE2_dlambda) {
+                      void* stream_, double* g_h, double* g_c, double* g_Bc, double* g_Bx, double* dE2_dlambda,
+                      double* E2) {
   if (!P || !in || !seed || !in->h || !in->B_c || !in->c) return E2_ERR_INVALID_ARG;
   if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
   if (!std::isfinite(in->lambda)) return E2_ERR_INVALID_ARG;
@@ -1172,6 +1211,10 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
   g_launches = 0;
   if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
   setup_classes(P, ws, st);
+  struct SplitScope {  // split-K scratch of this pass's GEMM helpers
+    SplitScope(void* p, size_t n) { g_splitk = p; g_splitk_bytes = n; }
+    ~SplitScope() { g_splitk = nullptr; g_splitk_bytes = 0; }
+  } split_scope(ws + P->o_bPart, P->bpart_bytes);
   Ctx X = ctx(P, ws);
   const DevList LP = dev_list(P, P->listP, ws);
   DevList Lc[E2_NCLASS];
@@ -1207,10 +1250,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
   auto zpair = [&](const RowInfo* rows, int64_t M, const double* hs, const double* hocc) {
     (k_zmat<<<blocks(M * nx), 256, 0, st>>>(rows, M, nx, Zm), ++g_launches);
     (k_zscale<<<blocks(M * nx), 256, 0, st>>>(Zm, hs, M, nx, Zs), ++g_launches);
-    dim3 g1((unsigned)((nx + 63) / 64), (unsigned)((nx + 63) / 64));
-    (k_dgemm<<<g1, 256, 0, st>>>(nx, nx, M, Zm, 1, nx, Zs, nx, 1, Ge, nx, 1), ++g_launches);
-    dim3 g2((unsigned)((nx + 63) / 64), (unsigned)((na + 63) / 64));
-    (k_dgemm<<<g2, 256, 0, st>>>(nx, na, M, Zm, 1, nx, hocc, na, 1, Gea, na, 1), ++g_launches);
+    dgemm(st, nx, nx, M, Zm, 1, nx, Zs, nx, 1, Ge, nx, 1);
+    dgemm(st, nx, na, M, Zm, 1, nx, hocc, na, 1, Gea, na, 1);
   };
   const bool on[E2_NCLASS] = {P->part_cnt[0] > 0, P->part_cnt[1] > 0, P->part_cnt[2] > 0, P->part_cnt[3] > 0,
                               P->part_cnt[4] > 0, P->part_cnt[5] > 0, P->part_cnt[6] > 0, P->part_cnt[7] > 0,
@@ -1219,8 +1260,23 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
     const double2* c = (const double2*)in->c + (int64_t)r * LP.n;
     prepare_root(P, ws, st, c, r);
     const double s = seed[r];
+    double* part_r = (double*)(ws + P->o_part);
+    auto poff = [&](int cls) { return E2 ? part_r + P->part_off[r * E2_NCLASS + cls] : nullptr; };
+    auto nomark = [](int, int) {};
+    if (E2) launch_sparse_classes(P, ws, st, r, c, nomark);
     if (s == 0.0) {
       if (g_c) cudaMemsetAsync(g_c + 2 * (size_t)r * LP.n, 0, 16 * (size_t)LP.n, st);
+      if (E2) {  // no amplitudes for this root: the forward's dense classes alone
+        Tabs T0 = tables(P, ws, r);
+        const double2* Df[E2_NCLASS] = {nullptr, nullptr, T0.DTU, nullptr, T0.DTDU, T0.DT, T0.DTDUD, T0.DTD, nullptr};
+        for (int cls : {2, 5, 7, 4, 6}) {
+          if (!on[cls]) continue;
+          dim3 grid((unsigned)((P->M[cls] + 63) / 64), (unsigned)((Lc[cls].n + 63) / 64));
+          (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Df[cls], P->M[cls], Lc[cls].n,
+                                              P->Kp[cls], (const RowInfo*)(ws + P->o_rows[cls]), Lc[cls].U, Lc[cls].eA,
+                                              X.E0p + r, b, poff(cls), AdjOut{}), ++g_launches);
+        }
+      }
       continue;
     }
     Tabs T = tables(P, ws, r);
@@ -1246,17 +1302,15 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       for (int64_t m0 = 0; m0 < M; m0 += P->chunk_rows[cls]) {
         const int64_t Mc = std::min<int64_t>(P->chunk_rows[cls], M - m0);
         AdjOut adj{(double2*)B(P->o_bT), want_B ? (double*)B(P->o_bHm) : nullptr, (double*)B(P->o_bHrow),
-                   (double*)B(P->o_bHcol), (double*)B(P->o_bScalT), m0, Mc, s, g1};
+                   (double*)B(P->o_bHcol), (double*)B(P->o_bScalT), m0, Mc, s, g1, poff(cls), rt};
         dim3 grid((unsigned)((Mc + 63) / 64), (unsigned)ct);
         (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
                                             L.eA, X.E0p + r, b, nullptr, adj), ++g_launches);
         // Gamma_D[x][A] += sum_e W[e][x] conj(T[e][A]) (split over the rows of the chunk)
         if (Kp >= 64)
-          zgemm(st, Kp, N, Mc, W + m0 * Kp, 1, Kp, 0, adj.T, N, 1, 1, GDfor[cls], N, 1, 1, 64,
-                (double2*)B(P->o_bPart), size_t(512) << 20);
+          zgemm(st, Kp, N, Mc, W + m0 * Kp, 1, Kp, 0, adj.T, N, 1, 1, GDfor[cls], N, 1, 1, 64);
         else
-          zgemm(st, N, Kp, Mc, adj.T, 1, N, 1, W + m0 * Kp, Kp, 1, 0, GDfor[cls], 1, N, 1, 16,
-                (double2*)B(P->o_bPart), size_t(512) << 20);
+          zgemm(st, N, Kp, Mc, adj.T, 1, N, 1, W + m0 * Kp, Kp, 1, 0, GDfor[cls], 1, N, 1, 16);
         if (cls == 4)
           (k_rowdot<<<(unsigned)Mc, 256, 0, st>>>(adj.T, T.DTDU, N, (double2*)B(P->o_bRowdot) + m0), ++g_launches);
         if (want_B) {  // Gamma_W = conj(T) D^T and the per-row occupation sums of eta
@@ -1356,49 +1410,35 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       }
       double2* Tsh = (double2*)B(P->o_bTsh);
       const int ntp = P->ntp;
-      if (cls == 1 && Lc[2].n > 0) {
-        const int64_t nb = Lc[2].n;
-        double2* GX = (double2*)B(P->o_bGX01);
-        const double2* X01 = (const double2*)(ws + P->o_X01);
-        for (int u = 0; u < na; ++u) {
-          (k_tshift<<<dim3(blocks(nb), nrow), 256, 0, st>>>(L, Lc[2], P->das, X.binom, Tg, nrow, u, -1, Tsh), ++g_launches);
-          zgemm(st, ntp, nb, nrow, X01 + (int64_t)u * ntp, 1, (int64_t)na * ntp, 0, Tsh, nb, 1, 0, GT.DTU, nb, 1, 1);
+      // Gamma_D[x][B] += sum_(row,s) X[row][s][x] Tsh[(row,s)][B] and
+      // Gamma_X[row][s][x] = sum_B Tsh[(row,s)][B] D[x][B], rows in chunks that fit Tsh
+      auto shifted = [&](const DevList& Ltab, int S, int pairs_mode, int nx_, const double2* Xint, const double2* D,
+                         double2* GD, double2* GX, int gx_beta, int bn) {
+        const int64_t nb = Ltab.n;
+        if (nb == 0 || S == 0) return;
+        const int rc = (int)std::max<int64_t>(1, std::min<int64_t>(nrow, (int64_t)(P->tsh_bytes / (16 * (size_t)S * nb))));
+        for (int r0 = 0; r0 < nrow; r0 += rc) {
+          const int nr = std::min(rc, nrow - r0);
+          (k_tshift<<<dim3(blocks(nb), nr, S), 256, 0, st>>>(L, Ltab, P->das, X.binom, Tg, r0, pairs_mode, Tsh),
+           ++g_launches);
+          const int64_t k = (int64_t)nr * S;
+          zgemm(st, nx_, nb, k, Xint + (int64_t)r0 * S * nx_, 1, nx_, 0, Tsh, nb, 1, 0, GD, nb, 1, 1);
           if (want_B)
-            zgemm(st, nrow, ntp, nb, Tsh, nb, 1, 0, T.DTU, 1, nb, 0, GX + (int64_t)u * ntp, (int64_t)na * ntp, 1, 0);
+            zgemm(st, k, nx_, nb, Tsh, nb, 1, 0, D, 1, nb, 0, GX + (int64_t)r0 * S * nx_, nx_, 1, gx_beta, bn);
         }
-        if (want_B)
-          (k_gint<<<blocks((int64_t)nrow * na * ntp), 256, 0, st>>>(INT_X01, X.sp, GX, nrow, na * ntp, na * ntp, Gt,
-                                                                   npair), ++g_launches);
-      }
-      if (cls == 3 && Lc[5].n > 0) {
-        const int64_t nb = Lc[5].n;
-        double2* GX = (double2*)B(P->o_bGX10);
-        const double2* X10 = (const double2*)(ws + P->o_X10);
-        for (int u = 1; u < na; ++u)
-          for (int t = 0; t < u; ++t) {
-            const int tu = u * (u - 1) / 2 + t;
-            (k_tshift<<<dim3(blocks(nb), nrow), 256, 0, st>>>(L, Lc[5], P->das, X.binom, Tg, nrow, t, u, Tsh),
-             ++g_launches);
-            zgemm(st, na, nb, nrow, X10 + (int64_t)tu * na, 1, (int64_t)ntp * na, 0, Tsh, nb, 1, 0, GT.DT, nb, 1, 1, 16);
-            if (want_B)
-              zgemm(st, nrow, na, nb, Tsh, nb, 1, 0, T.DT, 1, nb, 0, GX + (int64_t)tu * na, (int64_t)ntp * na, 1, 0, 16);
-          }
-        if (want_B)
-          (k_gint<<<blocks((int64_t)nrow * ntp * na), 256, 0, st>>>(INT_X10, X.sp, GX, nrow, ntp * na, ntp * na, Gt,
-                                                                   npair), ++g_launches);
-      }
-      if (cls == 0 && Lc[2].n > 0) {
-        const int64_t nb = Lc[2].n;
-        double2* GX = (double2*)B(P->o_bGX00);
-        const double2* X00 = (const double2*)(ws + P->o_X00);
-        for (int u = 1; u < na; ++u)
-          for (int t = 0; t < u; ++t) {
-            const int tu = u * (u - 1) / 2 + t;
-            (k_tshift<<<dim3(blocks(nb), 1), 256, 0, st>>>(L, Lc[2], P->das, X.binom, Tg, 1, t, u, Tsh), ++g_launches);
-            zgemm(st, ntp, nb, 1, X00 + (int64_t)tu * ntp, 1, 1, 0, Tsh, nb, 1, 0, GT.DTU, nb, 1, 1);
-            if (want_B) zgemm(st, 1, ntp, nb, Tsh, nb, 1, 0, T.DTU, 1, nb, 0, GX + (int64_t)tu * ntp, ntp, 1, 1);
-          }
-      }
+      };
+      if (cls == 1)
+        shifted(Lc[2], na, 0, ntp, (const double2*)(ws + P->o_X01), T.DTU, GT.DTU, (double2*)B(P->o_bGX01), 0, 64);
+      if (cls == 3)
+        shifted(Lc[5], ntp, 1, na, (const double2*)(ws + P->o_X10), T.DT, GT.DT, (double2*)B(P->o_bGX10), 0, 16);
+      if (cls == 0)
+        shifted(Lc[2], ntp, 1, ntp, (const double2*)(ws + P->o_X00), T.DTU, GT.DTU, (double2*)B(P->o_bGX00), 1, 64);
+      if (want_B && cls == 1 && Lc[2].n > 0)
+        (k_gint<<<blocks((int64_t)nrow * na * ntp), 256, 0, st>>>(INT_X01, X.sp, (const double2*)B(P->o_bGX01), nrow,
+                                                                 na * ntp, na * ntp, Gt, npair), ++g_launches);
+      if (want_B && cls == 3 && Lc[5].n > 0)
+        (k_gint<<<blocks((int64_t)nrow * ntp * na), 256, 0, st>>>(INT_X10, X.sp, (const double2*)B(P->o_bGX10), nrow,
+                                                                 ntp * na, ntp * na, Gt, npair), ++g_launches);
     }
     // E0 term of the one-body coefficient, then the reference-state gradient
     (k_e0grad<<<blocks(na * na), 256, 0, st>>>(g1, scal, X.sp, Gf), ++g_launches);
@@ -1421,6 +1461,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
                                             (double2*)g_c + (int64_t)r * LP.n), ++g_launches);
     }
   }
+  if (E2) launch_reduce(P, ws, st, E2, nullptr, nullptr);
   (k_nd<<<blocks(P->n), 256, 0, st>>>(X.sp, Nx, Nt, Nd), ++g_launches);
   if (g_h) (k_hbar<<<blocks((int64_t)P->n * P->n), 256, 0, st>>>(X.sp, Gf, Nd, (double2*)g_h), ++g_launches);
   if (want_B) {

@@ -44,7 +44,9 @@ struct RowInfo {
 // Rows [m_base, m_base + Mc) are processed; T holds t = s (2/n) (df/dv) V
 // for those rows, Hrow[row][column tile] and Hcol[row tile][column] the
 // per-tile sums of s df/dD, scal[2 * tile] = (sum s df/dD, sum s (df/dv) v);
-// n = <c|c> is read from g1[0].
+// n = <c|c> is read from g1[0].  With part set, each tile also writes the
+// forward's partial of sum f (slot tile_n * rt + global row tile), so that the
+// backward pass returns E2 as well.
 struct AdjOut {
   double2* T;
   double* Hm;      // optional: s df/dD per element of the chunk (same layout as T)
@@ -54,6 +56,8 @@ struct AdjOut {
   int64_t m_base, Mc;
   double s;
   const double2* g1;
+  double* part;
+  int64_t rt;
 };
 
 // One dense-class contraction of a batch (absolute device pointers).

@@ -498,7 +498,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
   // epilogue: D_K = E0' - chi(e) - e_A - U[s1,A] - U[s2,A] + U[i1,A] + U[i2,A]
   const double e0p = *E0p;
   const int64_t mend = adj.T ? adj.m_base + adj.Mc : M;
-  double acc = 0.0, acc2 = 0.0;
+  double acc = 0.0, acc2 = 0.0, acc3 = 0.0;
   double rowp[2][2] = {{0.0, 0.0}, {0.0, 0.0}};                 // adjoint: per-row sums of df/dD
   double colp[2][2] = {{0.0, 0.0}, {0.0, 0.0}};                 // adjoint: per-column sums of df/dD
 #pragma unroll
@@ -538,6 +538,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
             colp[ni][hc] += hk;
             acc += hk;
             acc2 += adj.s * gk * v2 * inv_n;
+            if (adj.part) acc3 += en_term(v2, Dk, b);
           }
         }
     }
@@ -571,6 +572,10 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
       const int64_t slot = ((adj.m_base / GBM) + tile_m) * n_tile_n + tile_n;
       adj.scal[2 * slot] = ts;
       adj.scal[2 * slot + 1] = t2s;
+    }
+    if (adj.part) {  // the forward's partial of this tile, same terms in the same order
+      const double t3s = block_sum(acc3, sh);
+      if (tid == 0) adj.part[tile_n * adj.rt + (adj.m_base / GBM) + tile_m] = t3s;
     }
     return;
   }

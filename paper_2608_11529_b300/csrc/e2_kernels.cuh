@@ -57,7 +57,8 @@ __global__ void k_zgemm64(int64_t M, int64_t N, int64_t K, const double2* A, int
 __global__ void k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
                           const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn,
                           int beta, int64_t kseg, int64_t czs, int64_t lower);
-__global__ void k_zacc(const double2* part, int nseg, int64_t ps, int64_t count, double2* out);
+__global__ void k_zacc(const double2* part, int nseg, int64_t ps, int64_t M, int64_t N, double2* C, int64_t csm,
+                       int64_t csn, int beta);
 __global__ void k_rowsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);
 __global__ void k_colsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);
 __global__ void k_scalsum(const double* in, int64_t n, double* scal_out);
@@ -91,14 +92,15 @@ __global__ void k_cbar(int64_t np, const double2* Gc, const double* c22, const d
 __global__ void k_hbar(DevSpace sp, const double2* Gf, const double* Nd, double2* gh);
 
 __global__ void k_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t sam, int64_t sak, const double* B,
-                        int64_t sbk, int64_t sbn, double* C, int64_t ldc, int beta);
+                        int64_t sbk, int64_t sbn, double* C, int64_t ldc, int beta, int64_t kseg, int64_t czs);
+__global__ void k_dacc(const double* part, int nseg, int64_t ps, int64_t count, double* out);
 __global__ void k_hocc(const double* H, DevList Ls, int na, double* Hocc);
 __global__ void k_zmat(const RowInfo* rows, int64_t M, int nx, double* Z);
 __global__ void k_zscale(const double* Z, const double* hsum, int64_t M, int nx, double* out);
 __global__ void k_gint(int mode, DevSpace sp, const double2* Gam, int64_t rows, int cols, int ld, double2* Gt,
                        int64_t npair);
-__global__ void k_tshift(DevList Lx, DevList Ltab, DevDas das, const int64_t* binom, const double2* T, int nrow, int t,
-                         int u, double2* Tsh);
+__global__ void k_tshift(DevList Lx, DevList Ltab, DevDas das, const int64_t* binom, const double2* T, int row0,
+                         int pairs_mode, double2* Tsh);
 __global__ void k_class22_rows(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
                                const double* G, const double* E0p, double b, double s, const double2* g1, double* hsum,
                                double* Hocc, double* P22);
