@@ -222,6 +222,28 @@ E2_API e2_status e2_launch_count(const e2_problem* prob, int64_t* n);
 E2_API e2_status e2_fp64_peak(void* workspace, size_t workspace_bytes, void* stream, double* dmma_tflops,
                               double* dfma_tflops);
 
+/* Per-CTA partial sums of the last e2_forward (or e2_backward with E2) that
+ * used `workspace` (no counterpart in the paper; it lets a caller check any
+ * block of couplings of a full-size run against an independent evaluation).
+ * Sets *partials to a device pointer into the workspace (valid until the
+ * workspace is reused) and *count to the number of partials of (root, cls),
+ * cls = 3 h + p.  Each partial is sum |V_K|^2 g(D_K) over its couplings, with
+ * V from the unnormalised c (E2 divides the total by <c|c>), g = 1/D or the
+ * level-shifted weight.  Layout:
+ *   dense classes (0,2) (1,2) (1,1) (2,0) (2,1): 64 x 64 tiles of (external
+ *     row, class string), partial[tile_n * row_tiles + tile_m]; rows in the
+ *     class's row order (pairs a<b of correlated virtuals have index
+ *     b(b-1)/2 + a; (i, a<b) is i * npair_v + pair(a,b); (i<j, a) is
+ *     pair(i,j) * n_vc + a; (i, a) is i * n_vc + a; (i<j) is pair(i,j)),
+ *     strings of the class's list in address order (the convention at the
+ *     top of this file, over the occupation patterns the class reaches);
+ *   gather classes (0,1) (1,0) (0,0): per row (virtual a, core i, or the
+ *     single row) blocks of 256 strings, partial[row * ceil(n_A/256) + block];
+ *   class (2,2): kernel order; *row_tiles = 0 for every non-dense class.
+ * Errors: E2_ERR_INVALID_ARG for a NULL argument or root / cls out of range. */
+E2_API e2_status e2_partials(const e2_problem* prob, const void* workspace, int root, int cls,
+                             const double** partials, int64_t* count, int64_t* row_tiles);
+
 /* Allocation-free variant of e2_forward (no counterpart in the paper).
  * Some callers cannot call cudaMalloc: code that enqueues work while a CUDA
  * graph is being captured, plugins living inside a host program that owns

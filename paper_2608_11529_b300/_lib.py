@@ -57,6 +57,9 @@ def load():
         L.e2_reference_solve.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_double, C.c_int, C.c_void_p, C.c_size_t,
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
         L.e2_reference_solve.restype = C.c_int
+        L.e2_partials.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_void_p),
+                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+        L.e2_partials.restype = C.c_int
         L.e2_backward_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
         L.e2_backward_workspace_size.restype = C.c_int
         L.e2_backward.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
@@ -219,6 +222,19 @@ class E2Problem:
         _check(load().e2_reference_solve(self._h, C.byref(inp), tol, max_iter, ws.data_ptr(), ws.numel(),
                                          C.c_void_p(s), c.data_ptr(), E0.ctypes.data_as(C.c_void_p), C.byref(it)))
         return c, E0, int(it.value)
+
+    def partials(self, root, cls):
+        """Per-CTA partial sums of class cls (3h+p) for `root` from the last
+        forward() (or value_and_grad()) as a float64 CUDA tensor view of the
+        workspace, and the row-tile count of a dense class (0 otherwise)."""
+        import torch
+        ptr, cnt, rt = C.c_void_p(), C.c_int64(), C.c_int64()
+        _check(load().e2_partials(self._h, C.c_void_p(self._ws.data_ptr()), root, cls, C.byref(ptr), C.byref(cnt),
+                                  C.byref(rt)))
+        if cnt.value == 0:
+            return torch.empty(0, dtype=torch.float64, device=self._ws.device), int(rt.value)
+        off = ptr.value - self._ws.data_ptr()
+        return self._ws[off:off + 8 * cnt.value].view(torch.float64), int(rt.value)
 
     def launch_count(self):
         """Kernels enqueued by the last forward()."""

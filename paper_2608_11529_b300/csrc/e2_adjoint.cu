@@ -22,21 +22,24 @@ namespace e2 {
 // C(m,n) = beta * C(m,n) + sum_k opA(m,k) opB(k,n) on the FP64 tensor pipe
 // (three real products per complex product), opA(m,k) = A[m*sam + k*sak]
 // (conjugated when conjA), opB(k,n) = B[k*sbk + n*sbn] (conjugated when
-// conjB), C(m,n) = C[m*csm + n*csn].  Tile BM = 64 by BN = 64 or 16.  Split K:
+// conjB), C(m,n) = C[m*csm + n*csn].  Tile BM x BN = 64 x 64 (warp tiles
+// 32 x 16) or 128 x 16 (warp tiles 16 x 16, for the 16-wide outputs of the
+// classes whose contraction is one active index).  Split K:
 // grid.z segments of kseg, segment z writing C + z*czs (beta applies to each
 // segment's own output); a fixed-order sum of the segments (k_zacc) keeps the
 // result deterministic.  Each output element is owned by one CTA per segment.
 // With lower >= 0 only tiles holding some n <= lower + m are computed.
-template <int BN>
+template <int BM, int BN>
 __device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam,
                                            int64_t sak, int conjA, const double2* __restrict__ B, int64_t sbk,
                                            int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm, int64_t csn,
                                            int beta, int64_t kseg, int64_t czs, int64_t lower) {
-  constexpr int BM = 64, BK = 8;
-  constexpr int NI = BN / 32 > 0 ? BN / 32 : 1;       // n8 tiles per warp (64: 2, 16: 1)
-  constexpr int WN = BN == 64 ? 4 : 2;                  // warps across N
-  constexpr int WM = 8 / WN;                            // warps across M (64: 2, 16: 4)
-  constexpr int MI = BM / (WM * 16);                    // m16 tiles per warp (64: 2, 16: 1)
+  constexpr int BK = 8;
+  constexpr int WN = BN == 64 ? 4 : 1;                  // warps across N
+  constexpr int WM = 8 / WN;                            // warps across M
+  constexpr int MI = BM / (WM * 16);                    // m16 tiles per warp
+  constexpr int NI = BN / (WN * 8);                     // n8 tiles per warp
+  static_assert(MI >= 1 && NI >= 1 && WM * 16 * MI == BM && WN * 8 * NI == BN, "tile shape");
   __shared__ double sAr[BM][BK + 1], sAi[BM][BK + 1], sAs[BM][BK + 1];
   __shared__ double sBr[BK][BN + 1], sBi[BK][BN + 1], sBs[BK][BN + 1];
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
@@ -55,13 +58,15 @@ __device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, cons
       for (int e = 0; e < 4; ++e) t1[a][c][e] = t2[a][c][e] = t3[a][c][e] = 0.0;
   // load maps follow the contiguous operand dimension: A rows fastest when
   // sam == 1 (else k fastest), B columns fastest unless sbk == 1
-  constexpr int NB = (BK * BN + 255) / 256;  // B elements per thread (64: 2, 16: 1 on half the threads)
+  constexpr int NA = BM * BK / 256;          // A elements per thread
+  constexpr int NB = (BK * BN + 255) / 256;  // B elements per thread (16 wide: on half the threads)
   const bool a_mfast = (sam == 1 && sak != 1), b_kfast = (sbk == 1 && sbn != 1);
-  int ra[2], ka[2], rb[NB], kb_[NB];
+  int ra[NA], ka[NA], rb[NB], kb_[NB];
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    ra[q] = a_mfast ? (tid & 63) : (tid >> 3) + 32 * q;
-    ka[q] = a_mfast ? (tid >> 6) + 4 * q : (tid & 7);
+  for (int q = 0; q < NA; ++q) {
+    const int e = tid + 256 * q;
+    ra[q] = a_mfast ? e % BM : e / BK;
+    ka[q] = a_mfast ? e / BM : e % BK;
   }
 #pragma unroll
   for (int q = 0; q < NB; ++q) {
@@ -83,14 +88,14 @@ __device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, cons
     return u;
   };
   // register prefetch of the next K step while the tensor pipe works on this one
-  double2 pa[2], pb[NB];
-  pa[0] = ldA(kb0, 0);
-  pa[1] = ldA(kb0, 1);
+  double2 pa[NA], pb[NB];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) pa[q] = ldA(kb0, q);
 #pragma unroll
   for (int q = 0; q < NB; ++q) pb[q] = ldB(kb0, q);
   for (int64_t k0 = kb0; k0 < kb1; k0 += BK) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
+    for (int q = 0; q < NA; ++q) {
       sAr[ra[q]][ka[q]] = pa[q].x;
       sAi[ra[q]][ka[q]] = pa[q].y;
       sAs[ra[q]][ka[q]] = pa[q].x + pa[q].y;
@@ -104,8 +109,8 @@ __device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, cons
       }
     __syncthreads();
     if (k0 + BK < kb1) {
-      pa[0] = ldA(k0 + BK, 0);
-      pa[1] = ldA(k0 + BK, 1);
+#pragma unroll
+      for (int q = 0; q < NA; ++q) pa[q] = ldA(k0 + BK, q);
 #pragma unroll
       for (int q = 0; q < NB; ++q) pb[q] = ldB(k0 + BK, q);
     }
@@ -156,14 +161,14 @@ __global__ void __launch_bounds__(256, 1)
 k_zgemm64(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
           const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm,
           int64_t csn, int beta, int64_t kseg, int64_t czs, int64_t lower) {
-  zgemm_body<64>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower);
+  zgemm_body<64, 64>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower);
 }
 
 __global__ void __launch_bounds__(256, 1)
 k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
           const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm,
           int64_t csn, int beta, int64_t kseg, int64_t czs, int64_t lower) {
-  zgemm_body<16>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower);
+  zgemm_body<128, 16>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower);
 }
 
 // C(m,n) = beta C(m,n) + sum_z part[z*ps + m*N + n] in z order (segments of a
@@ -328,14 +333,15 @@ __global__ void k_scalsum(const double* __restrict__ in, int64_t n, double* __re
 // (x indexes correlated core then correlated virtual spinors).
 __global__ void k_xmarg(const RowInfo* __restrict__ rows, const double* __restrict__ hsum, int64_t M, int nx,
                         double* __restrict__ Nx) {
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= nx) return;
+  __shared__ double sh[32];
+  const int x = blockIdx.x;  // one block per external index
   double s = 0.0;
-  for (int64_t e = 0; e < M; ++e) {
+  for (int64_t e = threadIdx.x; e < M; e += blockDim.x) {
     const RowInfo ri = rows[e];
     if (ri.s1 == x || ri.s2 == x || ri.i1 == x || ri.i2 == x) s += hsum[e];
   }
-  Nx[x] += s;
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) Nx[x] += s;
 }
 
 // Nt[t] += sum_A hA[A] [t in A] over one string list (one block per t)

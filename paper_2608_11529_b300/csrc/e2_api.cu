@@ -367,7 +367,7 @@ e2_status build_plan(e2_problem* P) {
   P->solve_bytes = ws.top;
   // adjoint region on top of the solver layout (the forward one is its prefix)
   {
-    const size_t tbudget = size_t(2) << 30;
+    const size_t tbudget = size_t(4) << 30;
     size_t tmax = 16, hrow = 8, hcol = 8, scalt = 16, hsum = 8, hA = 8;
     for (int c : {2, 5, 7, 4, 6}) {
       const int64_t Mc = P->M[c], Nc = lsize(c);
@@ -634,15 +634,25 @@ void build_tables(const e2_problem* P, unsigned char* ws, cudaStream_t st, const
 thread_local void* g_splitk = nullptr;
 thread_local size_t g_splitk_bytes = 0;
 
-// Segments for a product with `tiles` output tiles and contraction K: enough
-// CTAs for two per SM over the B300's 148 SMs, at least 256 of K each.
+// Segments for a product with `tiles` output tiles (one CTA per SM, 148 SMs)
+// and contraction K: the count (at most 16, at least 256 of K each) that
+// minimises waves / segments, i.e. the time of a wave-quantised launch whose
+// CTAs each take K / segments; ties go to fewer segments.
 int splitk_segments(int64_t tiles, int64_t K, size_t seg_bytes) {
   if (!g_splitk || K < 512) return 1;
-  int64_t n = (2 * 2 * 148 + tiles - 1) / tiles;
-  n = std::min<int64_t>(n, K / 256);
-  n = std::min<int64_t>(n, 64);
-  n = std::min<int64_t>(n, (int64_t)(g_splitk_bytes / std::max<size_t>(seg_bytes, 1)));
-  return (int)std::max<int64_t>(n, 1);
+  const int64_t slots = 148;
+  int64_t nmax = std::min<int64_t>(16, K / 256);
+  nmax = std::min<int64_t>(nmax, (int64_t)(g_splitk_bytes / std::max<size_t>(seg_bytes, 1)));
+  int best = 1;
+  double tbest = (double)((tiles + slots - 1) / slots);
+  for (int64_t n = 2; n <= nmax; ++n) {
+    const double t = (double)((tiles * n + slots - 1) / slots) / (double)n;
+    if (t < 0.97 * tbest) {
+      tbest = t;
+      best = (int)n;
+    }
+  }
+  return best;
 }
 
 // C(m,n) = beta C(m,n) + sum_k opA(m,k) opB(k,n) (real, tensor pipe), C row-major
@@ -672,10 +682,11 @@ void zgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, i
            const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn, int beta,
            int bn = 64) {
   if (M <= 0 || N <= 0) return;
-  const int64_t tiles = ((M + 63) / 64) * ((N + bn - 1) / bn);
+  const int bm = bn == 16 ? 128 : 64;  // tiles 64 x 64 or 128 x 16
+  const int64_t tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
   const int nseg = splitk_segments(tiles, K, 16 * (size_t)M * N);
   const int64_t kseg = (K + nseg - 1) / nseg;
-  dim3 grid((unsigned)((M + 63) / 64), (unsigned)((N + bn - 1) / bn), (unsigned)nseg);
+  dim3 grid((unsigned)((M + bm - 1) / bm), (unsigned)((N + bn - 1) / bn), (unsigned)nseg);
   // split: segment z is written dense row-major at scratch + z*M*N, then summed into C
   double2* out = nseg > 1 ? (double2*)g_splitk : C;
   const int64_t om = nseg > 1 ? N : csm, on = nseg > 1 ? 1 : csn;
@@ -975,6 +986,17 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
   (k_finalize<<<1, 32, 0, st>>>(e2c, R, E2, X.E0d, E0), ++g_launches);
   P->launches = g_launches;
   if (cudaGetLastError() != cudaSuccess) return E2_ERR_CUDA;
+  return E2_OK;
+}
+
+e2_status e2_partials(const e2_problem* P, const void* workspace, int root, int cls, const double** partials,
+                      int64_t* count, int64_t* row_tiles) {
+  if (!P || !workspace || !partials || !count) return E2_ERR_INVALID_ARG;
+  if (root < 0 || root >= P->d.n_roots || cls < 0 || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
+  *partials = (const double*)((const unsigned char*)workspace + P->o_part) + P->part_off[root * E2_NCLASS + cls];
+  *count = P->part_cnt[cls];
+  const bool dense = cls == 2 || cls == 5 || cls == 7 || cls == 4 || cls == 6;
+  if (row_tiles) *row_tiles = dense ? (P->M[cls] + 63) / 64 : 0;
   return E2_OK;
 }
 
@@ -1321,7 +1343,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       }
       if (cls == 4) (k_fock11<<<blocks(M), 256, 0, st>>>((const double2*)B(P->o_bRowdot), X.sp, Gf), ++g_launches);
       (k_rowsum<<<blocks(M), 256, 0, st>>>((const double*)B(P->o_bHrow), M, ct, 0, hsum), ++g_launches);
-      (k_xmarg<<<blocks(P->nx), 256, 0, st>>>((const RowInfo*)(ws + P->o_rows[cls]), hsum, M, P->nx, Nx), ++g_launches);
+      (k_xmarg<<<P->nx, 256, 0, st>>>((const RowInfo*)(ws + P->o_rows[cls]), hsum, M, P->nx, Nx), ++g_launches);
       (k_colsum<<<blocks(N), 256, 0, st>>>((const double*)B(P->o_bHcol), rt, N, 0, hA), ++g_launches);
       (k_amarg<<<na, 256, 0, st>>>(L, hA, Nt), ++g_launches);
       (k_scalsum<<<1, 256, 0, st>>>((const double*)B(P->o_bScalT), rt * ct, scal), ++g_launches);

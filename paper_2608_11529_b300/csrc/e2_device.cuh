@@ -33,16 +33,18 @@ __device__ __forceinline__ double rcp_nr(double d) {
   return fma(r, e, r);
 }
 
-// Epstein-Nesbet term |V|^2/D, or with the imaginary level shift the real
-// part of |V|^2/(D + i b/D) = |V|^2 D^3/(D^4 + b^2) (Sec. 2.6).
-__device__ __forceinline__ double en_term(double v2, double D, double b) {
-  if (b == 0.0) return v2 * rcp_nr(D);
-  double D2 = D * D;
-  return v2 * D * D2 * rcp_nr(fma(D2, D2, b * b));
+// Weight g(D) of the Epstein-Nesbet term f = v g(D): g = 1/D, or with the
+// imaginary level shift the real part of 1/(D + i b/D) = D^3/(D^4 + b^2)
+// (Sec. 2.6).  g is also df/dv.
+__device__ __forceinline__ double en_g(double D, double b) {
+  if (b == 0.0) return rcp_nr(D);
+  const double D2 = D * D;
+  return D * D2 * rcp_nr(fma(D2, D2, b * b));
 }
 
-// df/dv and df/dD of the Epstein-Nesbet term f(v, D) = v/D, or with the
-// level shift f = v D^3/(D^4 + b^2).
+__device__ __forceinline__ double en_term(double v2, double D, double b) { return v2 * en_g(D, b); }
+
+// df/dv and df/dD of f(v, D) = v g(D); g bitwise equal to en_g.
 __device__ __forceinline__ void en_derivs(double v, double D, double b, double& g, double& h) {
   if (b == 0.0) {
     const double r = rcp_nr(D);

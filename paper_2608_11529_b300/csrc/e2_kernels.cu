@@ -498,7 +498,8 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
   // epilogue: D_K = E0' - chi(e) - e_A - U[s1,A] - U[s2,A] + U[i1,A] + U[i2,A]
   const double e0p = *E0p;
   const int64_t mend = adj.T ? adj.m_base + adj.Mc : M;
-  double acc = 0.0, acc2 = 0.0, acc3 = 0.0;
+  double acc = 0.0, acc2 = 0.0;
+  const double inv_n = adj.T ? 1.0 / adj.g1[0].x : 0.0, s2n = 2.0 * adj.s * inv_n;
   double rowp[2][2] = {{0.0, 0.0}, {0.0, 0.0}};                 // adjoint: per-row sums of df/dD
   double colp[2][2] = {{0.0, 0.0}, {0.0, 0.0}};                 // adjoint: per-column sums of df/dD
 #pragma unroll
@@ -527,18 +528,16 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
           if (!adj.T) {
             acc += en_term(v2, Dk, b);
           } else {
-            const double inv_n = 1.0 / adj.g1[0].x;
             double gk, hk;
             en_derivs(v2 * inv_n, Dk, b, gk, hk);
-            const double w = 2.0 * adj.s * inv_n * gk;  // t = s (2/n) g V
+            const double w = s2n * gk;  // t = s (2/n) g V
             adj.T[(row - adj.m_base) * N + col] = make_double2(w * vr, w * vi);
             hk *= adj.s;
             if (adj.Hm) adj.Hm[(row - adj.m_base) * N + col] = hk;
             rowp[mi][hr] += hk;
             colp[ni][hc] += hk;
             acc += hk;
-            acc2 += adj.s * gk * v2 * inv_n;
-            if (adj.part) acc3 += en_term(v2, Dk, b);
+            acc2 += v2 * gk;  // = en_term(v2, Dk, b), the forward's term
           }
         }
     }
@@ -566,17 +565,16 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
       const int64_t col = n0 + c;
       if (col < N) adj.Hcol[((adj.m_base / GBM) + tile_m) * N + col] = s;
     }
-    double t2s = block_sum(acc2, sh);
+    const double fs = block_sum(acc2, sh);  // sum f over the tile, as the forward sums it
+    const double t2s = adj.s * inv_n * fs;  // sum s (df/dv) v
     double ts = block_sum(acc, sh);
     if (tid == 0) {
       const int64_t slot = ((adj.m_base / GBM) + tile_m) * n_tile_n + tile_n;
       adj.scal[2 * slot] = ts;
       adj.scal[2 * slot + 1] = t2s;
     }
-    if (adj.part) {  // the forward's partial of this tile, same terms in the same order
-      const double t3s = block_sum(acc3, sh);
-      if (tid == 0) adj.part[tile_n * adj.rt + (adj.m_base / GBM) + tile_m] = t3s;
-    }
+    if (adj.part && tid == 0)  // the forward's partial of this tile, same terms in the same order
+      adj.part[tile_n * adj.rt + (adj.m_base / GBM) + tile_m] = fs;
     return;
   }
   double tot = block_sum(acc, sh);
