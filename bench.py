@@ -238,11 +238,13 @@ def run(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    torch.cuda.nvtx.range_push("forward")   # ncu --nvtx --nvtx-include "forward/" selects these launches
     start.record(stream)
     for s in range(args.steps):
         plan.set_events(evs[s])
         E2, E2c, E0 = plan.forward(**t)
     end.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     if ws > 1:
@@ -282,10 +284,12 @@ def run(args):
             plan.value_and_grad(**t)
         torch.cuda.synchronize()
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("fwd_bwd")   # ncu --nvtx --nvtx-include "fwd_bwd/" selects these launches
         b0.record(stream)
         for _ in range(args.steps):
             vg = plan.value_and_grad(**t)
         b1.record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         bms = b0.elapsed_time(b1) / args.steps
         same = bool(torch.equal(vg[0], E2dev)) if E2dev is not None else None
