@@ -51,6 +51,17 @@ def _dist():
     return ws, rank, local
 
 
+def _ncols(prob, cls):
+    """Strings of a dense class of a CAS workload (its coupling-table columns)."""
+    from math import comb
+    h, p = divmod(cls, 3)
+    return comb(prob.n_act, prob.n_elec + h - p)
+
+
+def _kpad(prob, cls):
+    return (_kdim(prob, cls) + 7) // 8 * 8
+
+
 def _kdim(prob, cls):
     na = prob.n_act
     return {"ntp": na * (na - 1) // 2, "na": na, "na2p1": 1 + na * na}[GEMM_CLASSES[cls]]
@@ -214,6 +225,14 @@ def run(args):
     t["c"] = c
     torch.cuda.synchronize()
     peak_dmma, peak_dfma = e2.fp64_peak(dev)
+    # column tiles: time plain against compacted per class once, keep the faster
+    tune = plan.autotune(**t) if not args.no_autotune else {}
+    col_tiles = {}
+    for k in (2, 4, 6):
+        tiles, krows, used = plan.class_tiles(k)
+        if tiles:
+            col_tiles[CLASS_NAMES[k]] = {"used": used, "compacted_share": krows / (tiles * _kpad(prob, k)),
+                                         "autotune_ms": list(tune.get(k, ()))}
 
     # warm-up
     for _ in range(args.warmup):
@@ -263,15 +282,20 @@ def run(args):
     dom = max(ktime, key=ktime.get)
     if dom in GEMM_CLASSES:
         # complex products by Gauss's three real products: 6 real flops per
-        # complex multiply-add, K of them per coupling
+        # complex multiply-add, K of them per coupling; with column tiles K is
+        # each tile's compacted length (the products the kernel executes)
         flops = 6.0 * plan.q_per_class[dom] * _kdim(prob, dom)
+        tiles, krows, used = plan.class_tiles(dom)
+        if used:
+            flops = 6.0 * (plan.q_per_class[dom] / _ncols(prob, dom)) * krows * 64
         achieved = flops / (ktime[dom] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_dmma, "unit": "TFLOP/s",
                 "frac": achieved / peak_dmma, "traffic": _traffic("k_class_gemm"),
                 "kernel": f"k_class_gemm class {CLASS_NAMES[dom]}", "peak_source":
                 "measured on this GPU: mma.sync m16n8k8 f64 burst (e2_fp64_peak)",
                 "algorithmic_flops_per_launch": flops, "ms_per_launch": ktime[dom],
-                "flops_per_coupling": "6 K (3 real products per complex product, K = contraction length)"}
+                "flops_per_coupling": "6 K (3 real products per complex product, K = contraction length; "
+                                      "with column tiles, each tile's compacted K)"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": peak_dfma, "unit": "TFLOP/s", "frac": None,
                 "traffic": None, "kernel": KERNEL_OF_CLASS[dom]}
@@ -340,6 +364,7 @@ def run(args):
                 "config": {"workload": WORKLOADS[args.config], "couplings_per_step": int(couplings),
                            "roots": plan.n_roots, "reference": f"device Davidson, {iters} iterations",
                            "l2": "inputs larger than L2: the 456 MB factor set is re-read every step",
+                           "column_tiles": col_tiles,
                            "E2": float(E2.cpu()[0]), "E0": float(E0.cpu()[0]),
                            "class_ms": {CLASS_NAMES[k]: ktime[k] for k in present}},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fwd_bwd": fwdbwd,
@@ -361,6 +386,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default column tiles")
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     ap.add_argument("--factors", type=int, default=0,
                     help="override the Coulomb factor count (extra set = half); a small-memory variant with the "

@@ -240,9 +240,39 @@ E2_API e2_status e2_fp64_peak(void* workspace, size_t workspace_bytes, void* str
  *   gather classes (0,1) (1,0) (0,0): per row (virtual a, core i, or the
  *     single row) blocks of 256 strings, partial[row * ceil(n_A/256) + block];
  *   class (2,2): kernel order; *row_tiles = 0 for every non-dense class.
+ * columns: see the column tiles below (NULL output allowed).
  * Errors: E2_ERR_INVALID_ARG for a NULL argument or root / cls out of range. */
 E2_API e2_status e2_partials(const e2_problem* prob, const void* workspace, int root, int cls,
-                             const double** partials, int64_t* count, int64_t* row_tiles);
+                             const double** partials, int64_t* count, int64_t* row_tiles,
+                             const int32_t** columns);
+
+/* Column tiles of the dense classes (no counterpart in the paper; a layout
+ * choice).  The coupling tables D^{tu} (class (0,2)), D^{t+u+} (class (2,0))
+ * and D^{t+u} (class (1,1)) are mostly structural zeros: D^{tu}_A = 0
+ * whenever t or u is occupied in A.  The plan groups the class's strings
+ * into 64-column tiles whose strings share three occupied (or empty)
+ * spinors, and each tile contracts only over the table rows that are
+ * non-zero for one of its strings.  The result is the same sum in a
+ * different order.
+ *   e2_class_tiles     tiles, compacted rows (sum over tiles of the padded
+ *                      contraction length) and whether class cls uses them; 0
+ *                      tiles when the class has no such plan.
+ *   e2_set_class_tiles switch a class to compacted (on = 1) or plain
+ *                      columns; E2_ERR_UNSUPPORTED when it has no plan.  The
+ *                      plan's default: on when the compacted work is below
+ *                      85% of the plain work.
+ *   e2_autotune        times the class kernel of root 0 both ways for every
+ *                      class that has a plan and keeps the faster.  ms_out
+ *                      [2 * E2_NCLASS] (host, or NULL) receives the plain and
+ *                      compacted times.  It synchronises `stream`; workspace
+ *                      as for e2_forward, inputs as for e2_forward.
+ * When a class uses column tiles, e2_partials' tile_n indexes the column
+ * tiles and *columns (device, [tiles * 64]) gives each tile column's string
+ * (list index, -1 for padding); otherwise *columns is NULL. */
+E2_API e2_status e2_class_tiles(const e2_problem* prob, int cls, int64_t* tiles, int64_t* krows, int* in_use);
+E2_API e2_status e2_set_class_tiles(e2_problem* prob, int cls, int on);
+E2_API e2_status e2_autotune(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                             void* stream, float* ms_out);
 
 /* Allocation-free variant of e2_forward (no counterpart in the paper).
  * Some callers cannot call cudaMalloc: code that enqueues work while a CUDA

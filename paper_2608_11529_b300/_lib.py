@@ -58,8 +58,15 @@ def load():
                                          C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_int)]
         L.e2_reference_solve.restype = C.c_int
         L.e2_partials.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_void_p),
-                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_void_p)]
         L.e2_partials.restype = C.c_int
+        L.e2_class_tiles.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int)]
+        L.e2_class_tiles.restype = C.c_int
+        L.e2_set_class_tiles.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.e2_set_class_tiles.restype = C.c_int
+        L.e2_autotune.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
+        L.e2_autotune.restype = C.c_int
         L.e2_backward_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
         L.e2_backward_workspace_size.restype = C.c_int
         L.e2_backward.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
@@ -226,15 +233,44 @@ class E2Problem:
     def partials(self, root, cls):
         """Per-CTA partial sums of class cls (3h+p) for `root` from the last
         forward() (or value_and_grad()) as a float64 CUDA tensor view of the
-        workspace, and the row-tile count of a dense class (0 otherwise)."""
+        workspace, the row-tile count of a dense class (0 otherwise), and the
+        column map of a class that uses column tiles (int32 CUDA view, list
+        index per tile column, -1 = padding) or None."""
         import torch
-        ptr, cnt, rt = C.c_void_p(), C.c_int64(), C.c_int64()
+        ptr, cnt, rt, cols = C.c_void_p(), C.c_int64(), C.c_int64(), C.c_void_p()
         _check(load().e2_partials(self._h, C.c_void_p(self._ws.data_ptr()), root, cls, C.byref(ptr), C.byref(cnt),
-                                  C.byref(rt)))
+                                  C.byref(rt), C.byref(cols)))
         if cnt.value == 0:
-            return torch.empty(0, dtype=torch.float64, device=self._ws.device), int(rt.value)
+            return torch.empty(0, dtype=torch.float64, device=self._ws.device), int(rt.value), None
         off = ptr.value - self._ws.data_ptr()
-        return self._ws[off:off + 8 * cnt.value].view(torch.float64), int(rt.value)
+        part = self._ws[off:off + 8 * cnt.value].view(torch.float64)
+        perm = None
+        if cols.value:
+            tiles, _, _ = self.class_tiles(cls)
+            co = cols.value - self._ws.data_ptr()
+            perm = self._ws[co:co + 4 * 64 * tiles].view(torch.int32)
+        return part, int(rt.value), perm
+
+    def class_tiles(self, cls):
+        """(tiles, compacted rows, in use) of class cls's column tiles."""
+        t, k, u = C.c_int64(), C.c_int64(), C.c_int()
+        _check(load().e2_class_tiles(self._h, cls, C.byref(t), C.byref(k), C.byref(u)))
+        return int(t.value), int(k.value), bool(u.value)
+
+    def set_class_tiles(self, cls, on):
+        _check(load().e2_set_class_tiles(self._h, cls, int(bool(on))))
+
+    def autotune(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, stream=None):
+        """Time plain against compacted columns per class and keep the faster;
+        returns {class: (ms plain, ms compacted)} for the classes tried."""
+        import torch
+        ws = self.workspace(c.device)
+        inp = _Inputs(h.data_ptr(), B_c.data_ptr(), B_x.data_ptr() if self.L_extra else None,
+                      w_x.data_ptr() if self.L_extra else None, float(lam), c.data_ptr())
+        s = torch.cuda.current_stream(c.device).cuda_stream if stream is None else stream
+        ms = (C.c_float * (2 * NCLASS))()
+        _check(load().e2_autotune(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s), ms))
+        return {k: (ms[2 * k], ms[2 * k + 1]) for k in range(NCLASS) if ms[2 * k] > 0}
 
     def launch_count(self):
         """Kernels enqueued by the last forward()."""

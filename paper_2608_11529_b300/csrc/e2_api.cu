@@ -9,6 +9,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <queue>
 #include <vector>
 
 #include "e2_common.cuh"
@@ -35,6 +36,17 @@ struct HostList {
   int64_t n = 0;
   std::vector<int64_t> key2off;
   size_t o_str = 0, o_key = 0, o_patoff = 0, o_patocc = 0, o_eA = 0, o_U = 0;
+};
+
+// Column tiles of a dense class with a compacted contraction (see ColTiles).
+struct ColPlan {
+  bool built = false;
+  std::vector<int32_t> perm;   // [tiles * 64] list index, -1 = padding
+  std::vector<int32_t> tdesc;  // [tiles][4] {koff, klen, ktrue, 0}
+  std::vector<int32_t> klist;  // [krows]
+  int64_t tiles = 0, krows = 0;
+  double ratio = 1.0;          // krows / (tiles * Kp): share of the dense contraction
+  size_t o_perm = 0, o_tdesc = 0, o_klist = 0, o_Dc = 0;  // o_Dc: per-root D region
 };
 
 // Bump allocator over the workspace (256-byte aligned segments).
@@ -105,6 +117,9 @@ struct e2_problem {
   size_t o_bPart, bpart_bytes;  // split-K segments
   size_t tsh_bytes;
   size_t bwd_bytes;
+  // compacted column tiles of the dense classes and whether each class uses them
+  ColPlan cplan[E2_NCLASS];
+  bool use_cols[E2_NCLASS] = {};
 };
 
 namespace {
@@ -174,6 +189,169 @@ int add_list(e2_problem* P, int count, const std::vector<Pat>& pats) {
   L.n = off;
   P->lists.push_back(L);
   return (int)P->lists.size() - 1;
+}
+
+// Active-local bitset of the k-subset of colex rank r (r = sum_j C(t_j, j)).
+uint64_t colex_unrank_h(int64_t r, int k) {
+  uint64_t bits = 0;
+  for (int j = k; j >= 1; --j) {
+    int t = j - 1;
+    while (binom_h(t + 1, j) <= r) ++t;
+    r -= binom_h(t, j);
+    bits |= 1ull << t;
+  }
+  return bits;
+}
+
+// The strings of a list in address order (pattern blocks, subspace 1 fastest,
+// colex inside each subspace): the order the device unranks them in.
+std::vector<uint64_t> host_strings(const e2_problem* P, const HostList& L) {
+  std::vector<uint64_t> out;
+  out.reserve((size_t)L.n);
+  for (const Pat& pt : L.pats) {
+    const int64_t cnt = pattern_size(P, pt);
+    for (int64_t g = 0; g < cnt; ++g) {
+      int64_t r = g;
+      uint64_t A = 0;
+      for (int s = 0; s < P->d.n_das; ++s) {
+        const int64_t cs = binom_h(P->das_size[s], pt[s]);
+        A |= colex_unrank_h(r % cs, pt[s]) << P->das.off[s];
+        r /= cs;
+      }
+      out.push_back(A);
+    }
+  }
+  return out;
+}
+
+// Structural non-zero of coupling-table row x at string A (a necessary
+// condition: the table entry is exactly zero when it fails).
+bool table_nonzero(int fam, int na, uint64_t A, int x) {
+  auto in = [&](int t) { return (A >> t) & 1ull; };
+  switch (fam) {
+    case FAM_T: return !in(x);
+    case FAM_TD: return in(x);
+    case FAM_TU:
+    case FAM_TDUD: {
+      int u = 1;
+      while ((u + 1) * u / 2 <= x) ++u;
+      const int t = x - u * (u - 1) / 2;
+      return fam == FAM_TU ? (!in(t) && !in(u)) : (in(t) && in(u));
+    }
+    default: {  // FAM_TDU: row 0 is c_A, row 1 + t*na + u is a+_t a_u
+      if (x == 0) return true;
+      const int t = (x - 1) / na, u = (x - 1) % na;
+      return t == u ? in(t) : (in(t) && !in(u));
+    }
+  }
+}
+
+// Column tiles of one dense class: strings grouped greedily by a shared
+// 3-spinor set (occupied spinors for tables that need empty ones, empty
+// spinors for those that need occupied ones), 64 to a tile, each tile keeping
+// the table rows that are non-zero for some of its strings.
+void build_colplan(e2_problem* P, int cls, int fam, int kvalid) {
+  ColPlan& cp = P->cplan[cls];
+  cp = ColPlan{};
+  const int li = P->list_of[cls];
+  if (li < 0 || P->M[cls] == 0) return;
+  const HostList& L = P->lists[li];
+  const int na = P->na, Kp = P->Kp[cls];
+  const std::vector<uint64_t> S = host_strings(P, L);
+  const int64_t nS = (int64_t)S.size();
+  const uint64_t full = na >= 64 ? ~0ull : ((1ull << na) - 1);
+  const bool by_occ = (fam == FAM_T || fam == FAM_TU || fam == FAM_TDU);
+  const int nkey = by_occ ? L.count : na - L.count;
+  std::vector<int32_t> order;
+  order.reserve((size_t)nS);
+  if (nkey < 3 || na < 3) {
+    for (int64_t s = 0; s < nS; ++s) order.push_back((int32_t)s);
+  } else {
+    const int nsub = (int)binom_h(nkey, 3);
+    const int64_t nF = binom_h(na, 3);
+    std::vector<int32_t> fid((size_t)nS * nsub);
+    std::vector<int64_t> fcnt((size_t)nF, 0);
+    for (int64_t s = 0; s < nS; ++s) {
+      const uint64_t key = by_occ ? S[s] : (~S[s] & full);
+      int bits[64], nb = 0;
+      for (uint64_t x = key; x; x &= x - 1) bits[nb++] = __builtin_ctzll(x);
+      int q = 0;
+      for (int i = 0; i < nb; ++i)
+        for (int j = i + 1; j < nb; ++j)
+          for (int k = j + 1; k < nb; ++k) {
+            const int f = (int)(binom_h(bits[i], 1) + binom_h(bits[j], 2) + binom_h(bits[k], 3));
+            fid[(size_t)s * nsub + q++] = f;
+            ++fcnt[f];
+          }
+    }
+    std::vector<int64_t> boff((size_t)nF + 1, 0);
+    for (int64_t f = 0; f < nF; ++f) boff[f + 1] = boff[f] + fcnt[f];
+    std::vector<int32_t> bucket((size_t)boff[nF]);
+    std::vector<int64_t> fill(boff.begin(), boff.end() - 1);
+    for (int64_t s = 0; s < nS; ++s)
+      for (int q = 0; q < nsub; ++q) bucket[fill[fid[(size_t)s * nsub + q]]++] = (int32_t)s;
+    std::vector<int64_t> ptr(boff.begin(), boff.end() - 1);
+    std::vector<char> alive((size_t)nS, 1);
+    std::priority_queue<std::pair<int64_t, int64_t>> heap;  // (count, -F): largest, then smallest F
+    for (int64_t f = 0; f < nF; ++f)
+      if (fcnt[f] > 0) heap.push({fcnt[f], -f});
+    int64_t left = nS;
+    std::vector<int32_t> cur;
+    while (left > 0 && !heap.empty()) {
+      const auto top = heap.top();
+      heap.pop();
+      const int64_t f = -top.second;
+      if (top.first != fcnt[f]) {
+        if (fcnt[f] > 0) heap.push({fcnt[f], -f});
+        continue;
+      }
+      while (ptr[f] < boff[f + 1] && (int)cur.size() < 64) {
+        const int32_t s = bucket[ptr[f]++];
+        if (!alive[s]) continue;
+        alive[s] = 0;
+        cur.push_back(s);
+        --left;
+        for (int q = 0; q < nsub; ++q) --fcnt[fid[(size_t)s * nsub + q]];
+      }
+      if ((int)cur.size() == 64 || left == 0) {
+        std::sort(cur.begin(), cur.end());
+        order.insert(order.end(), cur.begin(), cur.end());
+        cur.clear();
+      }
+      if (fcnt[f] > 0) heap.push({fcnt[f], -f});
+    }
+    if (!cur.empty()) {
+      std::sort(cur.begin(), cur.end());
+      order.insert(order.end(), cur.begin(), cur.end());
+    }
+  }
+  cp.tiles = (nS + 63) / 64;
+  cp.perm.assign((size_t)cp.tiles * 64, -1);
+  std::copy(order.begin(), order.end(), cp.perm.begin());
+  const int words = (kvalid + 63) / 64;
+  std::vector<uint64_t> mask((size_t)words);
+  for (int64_t j = 0; j < cp.tiles; ++j) {
+    std::fill(mask.begin(), mask.end(), 0ull);
+    for (int c = 0; c < 64; ++c) {
+      const int32_t s = cp.perm[j * 64 + c];
+      if (s < 0) continue;
+      for (int x = 0; x < kvalid; ++x)
+        if (!((mask[x >> 6] >> (x & 63)) & 1ull) && table_nonzero(fam, na, S[s], x)) mask[x >> 6] |= 1ull << (x & 63);
+    }
+    const int koff = (int)cp.klist.size();
+    int ktrue = 0;
+    for (int x = 0; x < kvalid; ++x)
+      if ((mask[x >> 6] >> (x & 63)) & 1ull) {
+        cp.klist.push_back(x);
+        ++ktrue;
+      }
+    const int klen = std::max(8, (ktrue + 7) / 8 * 8);
+    for (int x = ktrue; x < klen; ++x) cp.klist.push_back(0);
+    cp.tdesc.insert(cp.tdesc.end(), {koff, klen, ktrue, 0});
+  }
+  cp.krows = (int64_t)cp.klist.size();
+  cp.ratio = (double)cp.krows / ((double)cp.tiles * Kp);
+  cp.built = true;
 }
 
 template <class T>
@@ -250,6 +428,12 @@ e2_status build_plan(e2_problem* P) {
   P->Kp[7] = P->KpT;
   P->Kp[4] = P->Kp11;
   P->Kp[6] = P->KpTU;
+  // compacted column tiles where the coupling tables are mostly structural
+  // zeros: D^{tu} (class (0,2)), D^{t+u+} (class (2,0)), D^{t+u} (class (1,1))
+  build_colplan(P, 2, FAM_TU, P->ntp);
+  build_colplan(P, 6, FAM_TDUD, P->ntp);
+  build_colplan(P, 4, FAM_TDU, 1 + P->na * P->na);
+  for (int c = 0; c < E2_NCLASS; ++c) P->use_cols[c] = P->cplan[c].built && P->cplan[c].ratio < 0.85;
 
   // ---- workspace layout
   Layout ws;
@@ -266,6 +450,12 @@ e2_status build_plan(e2_problem* P) {
   }
   P->o_partoff = ws.take(sizeof(int64_t) * R * E2_NCLASS);
   P->o_partcnt = ws.take(sizeof(int64_t) * E2_NCLASS);
+  for (ColPlan& cp : P->cplan) {
+    if (!cp.built) continue;
+    cp.o_perm = ws.take(sizeof(int32_t) * cp.perm.size());
+    cp.o_tdesc = ws.take(sizeof(int32_t) * cp.tdesc.size());
+    cp.o_klist = ws.take(sizeof(int32_t) * cp.klist.size());
+  }
   P->plan_bytes = ws.top - P->o_plan;
   // device-computed data
   P->o_binom = ws.take(sizeof(int64_t) * kBinomN * kBinomN);
@@ -303,6 +493,8 @@ e2_status build_plan(e2_problem* P) {
   P->o_DTU = ws.take(16 * (size_t)P->KpTU * std::max<int64_t>(lsize(2), 1));
   P->o_DTDUD = ws.take(16 * (size_t)P->KpTU * std::max<int64_t>(lsize(6), 1));
   P->o_DTDU = ws.take(16 * (size_t)P->Kp11 * std::max<int64_t>(lsize(4), 1));
+  for (ColPlan& cp : P->cplan)
+    if (cp.built) cp.o_Dc = ws.take(16 * (size_t)cp.krows * 64);
   P->d_stride = ws.top - dstart;
   ws.top = dstart + P->d_stride * R;
   size_t gstart = ws.top;
@@ -486,6 +678,12 @@ e2_status build_plan(e2_problem* P) {
   }
   put(P->plan_blob, rel(P->o_partoff), P->part_off.data(), P->part_off.size());
   put(P->plan_blob, rel(P->o_partcnt), P->part_cnt, E2_NCLASS);
+  for (const ColPlan& cp : P->cplan) {
+    if (!cp.built) continue;
+    put(P->plan_blob, rel(cp.o_perm), cp.perm.data(), cp.perm.size());
+    put(P->plan_blob, rel(cp.o_tdesc), cp.tdesc.data(), cp.tdesc.size());
+    put(P->plan_blob, rel(cp.o_klist), cp.klist.data(), cp.klist.size());
+  }
   return E2_OK;
 }
 
@@ -609,6 +807,14 @@ Tabs tables(const e2_problem* P, unsigned char* ws, int r) {
   unsigned char* dr = ws + P->d_stride * r;
   return Tabs{(double2*)(dr + P->o_DT), (double2*)(dr + P->o_DTD), (double2*)(dr + P->o_DTU),
               (double2*)(dr + P->o_DTDUD), (double2*)(dr + P->o_DTDU)};
+}
+
+// Column tiles of class cls for root r (plain columns unless the class uses them).
+ColTiles col_tiles(const e2_problem* P, unsigned char* ws, int r, int cls) {
+  if (!P->use_cols[cls]) return ColTiles{nullptr, nullptr, nullptr, nullptr};
+  const ColPlan& cp = P->cplan[cls];
+  return ColTiles{(const int32_t*)(ws + cp.o_perm), (const int4*)(ws + cp.o_tdesc), (const int32_t*)(ws + cp.o_klist),
+                  (const double2*)(ws + P->d_stride * r + cp.o_Dc)};
 }
 
 // Coupling tensors D^x_A = <A|x|c> of one reference vector c; `all` = false
@@ -789,6 +995,13 @@ void prepare_root(e2_problem* P, unsigned char* ws, cudaStream_t st, const doubl
   Tabs T = tables(P, ws, r);
   const DevList L02 = dev_list(P, P->list_of[2], ws), L11 = dev_list(P, P->list_of[4], ws);
   build_tables(P, ws, st, c, T, true);
+  const double2* Dcls[E2_NCLASS] = {nullptr, nullptr, T.DTU, nullptr, T.DTDU, T.DT, T.DTDUD, T.DTD, nullptr};
+  for (int cls = 0; cls < E2_NCLASS; ++cls)
+    if (P->use_cols[cls]) {
+      const ColTiles ct = col_tiles(P, ws, r, cls);
+      (k_dcompact<<<(unsigned)P->cplan[cls].tiles, 256, 0, st>>>(Dcls[cls], P->lists[P->list_of[cls]].n, ct,
+                                                                 (double2*)ct.Dc), ++g_launches);
+    }
   double2* g1 = (double2*)(ws + P->o_g1 + P->g_stride * r);
   double2* g2 = (double2*)(ws + P->o_g2 + P->g_stride * r);
   (k_gram<<<1 + na * na, 256, 0, st>>>(T.DTDU, T.DTDU, L11.n, 1 + na * na, g1), ++g_launches);
@@ -975,7 +1188,8 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
       dim3 grid((unsigned)((P->M[cls] + 63) / 64), (unsigned)((L.n + 63) / 64));
       mark(cls, 0);
       (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Dfor[cls], P->M[cls], L.n, P->Kp[cls],
-                                         (const RowInfo*)(ws + P->o_rows[cls]), L.U, L.eA, X.E0p + r, b, poff(cls), AdjOut{}), ++g_launches);
+                                         (const RowInfo*)(ws + P->o_rows[cls]), L.U, L.eA, X.E0p + r, b, poff(cls), AdjOut{},
+                                         col_tiles(P, ws, r, cls)), ++g_launches);
       mark(cls, 1);
     }
     launch_sparse_classes(P, ws, st, r, c, mark);
@@ -990,14 +1204,86 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
 }
 
 e2_status e2_partials(const e2_problem* P, const void* workspace, int root, int cls, const double** partials,
-                      int64_t* count, int64_t* row_tiles) {
+                      int64_t* count, int64_t* row_tiles, const int32_t** columns) {
   if (!P || !workspace || !partials || !count) return E2_ERR_INVALID_ARG;
   if (root < 0 || root >= P->d.n_roots || cls < 0 || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
   *partials = (const double*)((const unsigned char*)workspace + P->o_part) + P->part_off[root * E2_NCLASS + cls];
   *count = P->part_cnt[cls];
   const bool dense = cls == 2 || cls == 5 || cls == 7 || cls == 4 || cls == 6;
   if (row_tiles) *row_tiles = dense ? (P->M[cls] + 63) / 64 : 0;
+  if (columns)
+    *columns = P->use_cols[cls] ? (const int32_t*)((const unsigned char*)workspace + P->cplan[cls].o_perm) : nullptr;
   return E2_OK;
+}
+
+e2_status e2_class_tiles(const e2_problem* P, int cls, int64_t* tiles, int64_t* krows, int* in_use) {
+  if (!P || cls < 0 || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
+  const ColPlan& cp = P->cplan[cls];
+  if (tiles) *tiles = cp.built ? cp.tiles : 0;
+  if (krows) *krows = cp.built ? cp.krows : 0;
+  if (in_use) *in_use = P->use_cols[cls] ? 1 : 0;
+  return E2_OK;
+}
+
+e2_status e2_set_class_tiles(e2_problem* P, int cls, int on) {
+  if (!P || cls < 0 || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
+  if (on && !P->cplan[cls].built) return E2_ERR_UNSUPPORTED;
+  P->use_cols[cls] = on != 0;
+  return E2_OK;
+}
+
+e2_status e2_autotune(e2_problem* P, const e2_inputs* in, void* workspace, size_t workspace_bytes, void* stream_,
+                      float* ms_out) {
+  if (!P || !in || !in->h || !in->B_c || !in->c) return E2_ERR_INVALID_ARG;
+  if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
+  if (!std::isfinite(in->lambda)) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < P->ws_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  cudaGetLastError();
+  if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
+  setup_classes(P, ws, st);
+  bool cand[E2_NCLASS];
+  for (int c = 0; c < E2_NCLASS; ++c) {
+    cand[c] = P->cplan[c].built && P->part_cnt[c] > 0;
+    if (cand[c]) P->use_cols[c] = true;  // so that root 0's compacted tables are built
+  }
+  prepare_root(P, ws, st, (const double2*)in->c, 0);
+  Ctx X = ctx(P, ws);
+  Tabs T = tables(P, ws, 0);
+  const double2* Dfor[E2_NCLASS] = {nullptr, nullptr, T.DTU, nullptr, T.DTDU, T.DT, T.DTDUD, T.DTD, nullptr};
+  double* part = (double*)(ws + P->o_part);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return E2_ERR_CUDA;
+  for (int c = 0; c < E2_NCLASS; ++c) {
+    if (ms_out) ms_out[2 * c] = ms_out[2 * c + 1] = 0.f;
+    if (!cand[c]) continue;
+    const DevList L = dev_list(P, P->list_of[c], ws);
+    dim3 grid((unsigned)((P->M[c] + 63) / 64), (unsigned)((L.n + 63) / 64));
+    float t[2] = {0.f, 0.f};
+    for (int v = 0; v < 2; ++v) {  // v = 0: plain columns, 1: compacted column tiles
+      P->use_cols[c] = v == 1;
+      auto launch = [&] {
+        k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[c]), Dfor[c], P->M[c], L.n, P->Kp[c],
+                                           (const RowInfo*)(ws + P->o_rows[c]), L.U, L.eA, X.E0p, P->d.level_shift_b,
+                                           part + P->part_off[c], AdjOut{}, col_tiles(P, ws, 0, c));
+      };
+      launch();
+      cudaEventRecord(e0, st);
+      for (int k = 0; k < 2; ++k) launch();
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      cudaEventElapsedTime(&t[v], e0, e1);
+    }
+    P->use_cols[c] = t[1] < t[0];
+    if (ms_out) {
+      ms_out[2 * c] = 0.5f * t[0];
+      ms_out[2 * c + 1] = 0.5f * t[1];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
 }
 
 e2_status e2_launch_count(const e2_problem* P, int64_t* n) {
@@ -1138,7 +1424,10 @@ e2_status e2_batch_prepare(e2_batch* B, void* workspace, size_t workspace_bytes,
         g.E0p = (const double*)(w + P->o_E0p) + r;
         g.b = P->d.level_shift_b;
         g.partial = (double*)(w + P->o_part) + P->part_off[r * E2_NCLASS + c];
-        order.push_back({g.Kp, (int)B->gj.size()});
+        g.ct = col_tiles(P, w, r, c);
+        // longest contraction first: the mean compacted length for a column-tiled class
+        const int keff = P->use_cols[c] ? (int)(P->cplan[c].ratio * g.Kp + 0.5) : g.Kp;
+        order.push_back({keff, (int)B->gj.size()});
         B->gj.push_back(g);
       }
     }
@@ -1296,7 +1585,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           dim3 grid((unsigned)((P->M[cls] + 63) / 64), (unsigned)((Lc[cls].n + 63) / 64));
           (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Df[cls], P->M[cls], Lc[cls].n,
                                               P->Kp[cls], (const RowInfo*)(ws + P->o_rows[cls]), Lc[cls].U, Lc[cls].eA,
-                                              X.E0p + r, b, poff(cls), AdjOut{}), ++g_launches);
+                                              X.E0p + r, b, poff(cls), AdjOut{}, col_tiles(P, ws, r, cls)), ++g_launches);
         }
       }
       continue;
@@ -1327,7 +1616,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
                    (double*)B(P->o_bHcol), (double*)B(P->o_bScalT), m0, Mc, s, g1, poff(cls), rt};
         dim3 grid((unsigned)((Mc + 63) / 64), (unsigned)ct);
         (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
-                                            L.eA, X.E0p + r, b, nullptr, adj), ++g_launches);
+                                            L.eA, X.E0p + r, b, nullptr, adj, col_tiles(P, ws, r, cls)), ++g_launches);
         // Gamma_D[x][A] += sum_e W[e][x] conj(T[e][A]) (split over the rows of the chunk)
         if (Kp >= 64)
           zgemm(st, Kp, N, Mc, W + m0 * Kp, 1, Kp, 0, adj.T, N, 1, 1, GDfor[cls], N, 1, 1, 64);

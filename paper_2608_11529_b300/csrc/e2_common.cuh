@@ -60,6 +60,23 @@ struct AdjOut {
   int64_t rt;
 };
 
+// Column tiles of a dense class with a compacted contraction.  The coupling
+// table D [Kp][N] has structural zeros (D^{tu}_A = 0 when t or u is in A,
+// and so on); the class's strings are grouped into 64-column tiles whose
+// strings share occupied (or empty) spinors, and each tile contracts only
+// over the rows of D that are non-zero somewhere in it:
+//   perm[64 j + c]   list index of column c of tile j, -1 for padding
+//   tdesc[j]         {koff, klen (multiple of 8), ktrue, 0}
+//   klist[koff + k]  D row of compacted row k (0 beyond ktrue)
+//   Dc[(koff + k) * 64 + c] = D[klist[koff + k]][perm[64 j + c]] (0 beyond ktrue)
+// perm == nullptr: plain consecutive columns over the full Kp.
+struct ColTiles {
+  const int32_t* perm;
+  const int4* tdesc;
+  const int32_t* klist;
+  const double2* Dc;
+};
+
 // One dense-class contraction of a batch (absolute device pointers).
 struct GemmJob {
   const double2* W;
@@ -72,6 +89,7 @@ struct GemmJob {
   const double* E0p;
   double b;
   double* partial;
+  ColTiles ct;
 };
 
 struct WorkItem {

@@ -427,13 +427,28 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
                                            int64_t N, int Kp, const RowInfo* __restrict__ rows,
                                            const double* __restrict__ U, const double* __restrict__ eA,
                                            const double* __restrict__ E0p, double b, double* __restrict__ partial_slot,
-                                           const AdjOut& adj, int64_t tile_m, int64_t tile_n, int64_t n_tile_n) {
+                                           const AdjOut& adj, int64_t tile_m, int64_t tile_n, int64_t n_tile_n,
+                                           const ColTiles& ctl) {
   __shared__ double sWr[GBM][GBK + 1], sWi[GBM][GBK + 1], sWs[GBM][GBK + 1];
   __shared__ double sDr[GBK][GBN + 1], sDi[GBK][GBN + 1], sDs[GBK][GBN + 1];
   __shared__ double sh[32];
+  __shared__ int32_t sCol[GBN];   // list index of each tile column (-1: none)
+  __shared__ int32_t sK[512];     // compacted D rows of this tile (staged in 512-row windows)
   // tile (tile_m, tile_n): rows from m_base + 64 tile_m, columns from 64 tile_n
+  // (through perm for a compacted class)
   const int64_t m0 = adj.m_base + tile_m * GBM, n0 = tile_n * GBN;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool sparse = ctl.perm != nullptr;
+  int koff = 0, klen = Kp;
+  if (sparse) {
+    const int4 td = ctl.tdesc[tile_n];
+    koff = td.x;
+    klen = td.y;
+    D = ctl.Dc + (int64_t)koff * GBN;  // compacted rows of this tile, 64 wide
+  }
+  if (tid < GBN) sCol[tid] = sparse ? ctl.perm[n0 + tid] : (n0 + tid < N ? (int32_t)(n0 + tid) : -1);
+  const int64_t ldd = sparse ? GBN : N;    // row stride of the B operand
+  const int64_t dcol0 = sparse ? 0 : n0;   // its first column
   const int g = lane >> 2, tq = lane & 3;
   const int wm = warp >> 2, wn = warp & 3;  // warp tile: rows wm*32.., cols wn*16..
   double t1[2][2][4], t2[2][2][4], t3[2][2][4];
@@ -448,23 +463,37 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
   // elements (k rows kr, kr+4 of the 8x64 tile)
   const int wr_ = tid >> 3, wk = tid & 7, dk = tid >> 6, dc = tid & 63;
   const double2 zero = make_double2(0.0, 0.0);
+  // W column of compacted row k: staged window [kw0, kw0 + 512) of klist
+  int kw0 = 0;
+  auto stage = [&](int k0) {
+    kw0 = k0;
+    for (int i = tid; i < 512 && k0 + i < klen; i += blockDim.x) sK[i] = ctl.klist[koff + k0 + i];
+  };
+  if (sparse) stage(0);
+  __syncthreads();
+  auto wcol = [&](int k) { return sparse ? sK[k - kw0] : k; };
+  const bool colok = dcol0 + dc < N || sparse;
   auto ldW = [&](int k0, int q) {
     const int64_t gr = m0 + wr_ + 32 * q;
-    return (gr < M) ? W[gr * Kp + k0 + wk] : zero;
+    return (gr < M) ? W[gr * Kp + wcol(k0 + wk)] : zero;
   };
   auto ldD = [&](int k0, int q) {
-    const int64_t gc = n0 + dc;
-    return (gc < N) ? D[(int64_t)(k0 + dk + 4 * q) * N + gc] : zero;
+    return colok ? D[(int64_t)(k0 + dk + 4 * q) * ldd + dcol0 + dc] : zero;
   };
   double2 pw0 = ldW(0, 0), pw1 = ldW(0, 1), pd0 = ldD(0, 0), pd1 = ldD(0, 1);
 
-  for (int k0 = 0; k0 < Kp; k0 += GBK) {
+  for (int k0 = 0; k0 < klen; k0 += GBK) {
     sWr[wr_][wk] = pw0.x; sWi[wr_][wk] = pw0.y; sWs[wr_][wk] = pw0.x + pw0.y;
     sWr[wr_ + 32][wk] = pw1.x; sWi[wr_ + 32][wk] = pw1.y; sWs[wr_ + 32][wk] = pw1.x + pw1.y;
     sDr[dk][dc] = pd0.x; sDi[dk][dc] = pd0.y; sDs[dk][dc] = pd0.x + pd0.y;
     sDr[dk + 4][dc] = pd1.x; sDi[dk + 4][dc] = pd1.y; sDs[dk + 4][dc] = pd1.x + pd1.y;
     __syncthreads();
-    if (k0 + GBK < Kp) {  // prefetch the next K step while the tensor pipe works
+    if (k0 + GBK < klen) {  // prefetch the next K step while the tensor pipe works
+      if (sparse && k0 + GBK - kw0 >= 512) {  // next klist window (all threads are past their reads)
+        __syncthreads();
+        stage(k0 + GBK);
+        __syncthreads();
+      }
       pw0 = ldW(k0 + GBK, 0);
       pw1 = ldW(k0 + GBK, 1);
       pd0 = ldD(k0 + GBK, 0);
@@ -518,8 +547,8 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
       for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
         for (int hc = 0; hc < 2; ++hc) {
-          const int64_t col = n0 + wn * 16 + ni * 8 + 2 * tq + hc;
-          if (col >= N) continue;
+          const int64_t col = sCol[wn * 16 + ni * 8 + 2 * tq + hc];
+          if (col < 0) continue;
           const int e = hr * 2 + hc;
           const double vr = t1[mi][ni][e] - t2[mi][ni][e];
           const double vi = t3[mi][ni][e] - t1[mi][ni][e] - t2[mi][ni][e];
@@ -543,7 +572,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
     }
   if (adj.T) {
     // fixed-order per-row / per-column sums over the tile (16 contributors each)
-    __shared__ double sRow[GBM][16], sCol[GBN][16];
+    __shared__ double sRow[GBM][16], sColP[GBN][16];
 #pragma unroll
     for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
@@ -551,7 +580,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
 #pragma unroll
     for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
-      for (int hc = 0; hc < 2; ++hc) sCol[wn * 16 + ni * 8 + 2 * tq + hc][wm * 8 + g] = colp[ni][hc];
+      for (int hc = 0; hc < 2; ++hc) sColP[wn * 16 + ni * 8 + 2 * tq + hc][wm * 8 + g] = colp[ni][hc];
     __syncthreads();
     if (tid < GBM) {
       double s = 0.0;
@@ -561,9 +590,9 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
     } else if (tid < GBM + GBN) {
       const int c = tid - GBM;
       double s = 0.0;
-      for (int k = 0; k < 16; ++k) s += sCol[c][k];
-      const int64_t col = n0 + c;
-      if (col < N) adj.Hcol[((adj.m_base / GBM) + tile_m) * N + col] = s;
+      for (int k = 0; k < 16; ++k) s += sColP[c][k];
+      const int64_t col = sCol[c];
+      if (col >= 0) adj.Hcol[((adj.m_base / GBM) + tile_m) * N + col] = s;
     }
     const double fs = block_sum(acc2, sh);  // sum f over the tile, as the forward sums it
     const double t2s = adj.s * inv_n * fs;  // sum s (df/dv) v
@@ -581,14 +610,28 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
   if (tid == 0) *partial_slot = tot;
 }
 
+// Compacted coupling table of a column-tiled class (one block per tile):
+//   Dc[(koff + k) * 64 + c] = D[klist[koff + k]][perm[64 j + c]], 0 beyond ktrue or for padding
+__global__ void k_dcompact(const double2* __restrict__ D, int64_t N, ColTiles ctl, double2* __restrict__ Dc) {
+  const int j = blockIdx.x;
+  const int4 td = ctl.tdesc[j];
+  for (int i = threadIdx.x; i < td.y * GBN; i += blockDim.x) {
+    const int kk = i / GBN, c = i % GBN;
+    const int32_t p = ctl.perm[(int64_t)j * GBN + c];
+    double2 v = make_double2(0.0, 0.0);
+    if (kk < td.z && p >= 0) v = D[(int64_t)ctl.klist[td.x + kk] * N + p];
+    Dc[((int64_t)td.x + kk) * GBN + c] = v;
+  }
+}
+
 // One CTA per 64x64 tile; grid x = row tiles (of the chunk from adj.m_base),
 // y = column tiles.  Forward: one partial per tile in partial[y * gridDim.x + x].
 __global__ void __launch_bounds__(256, 1)
 k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M, int64_t N, int Kp,
              const RowInfo* __restrict__ rows, const double* __restrict__ U, const double* __restrict__ eA,
-             const double* __restrict__ E0p, double b, double* __restrict__ partial, AdjOut adj) {
+             const double* __restrict__ E0p, double b, double* __restrict__ partial, AdjOut adj, ColTiles ctl) {
   double* slot = partial ? partial + (int64_t)blockIdx.y * gridDim.x + blockIdx.x : nullptr;
-  class_tile(W, D, M, N, Kp, rows, U, eA, E0p, b, slot, adj, blockIdx.x, blockIdx.y, gridDim.y);
+  class_tile(W, D, M, N, Kp, rows, U, eA, E0p, b, slot, adj, blockIdx.x, blockIdx.y, gridDim.y, ctl);
 }
 
 // Persistent form: one CTA per SM takes tiles of every (job, class, root) of a
@@ -610,7 +653,7 @@ k_batch_gemm(const GemmJob* __restrict__ jobs, const WorkItem* __restrict__ item
     const GemmJob j = jobs[w.job];
     const int64_t ntm = (j.M + GBM - 1) / GBM;
     class_tile(j.W, j.D, j.M, j.N, j.Kp, j.rows, j.U, j.eA, j.E0p, j.b,
-               j.partial + (int64_t)w.tile_n * ntm + w.tile_m, none, w.tile_m, w.tile_n, (j.N + GBN - 1) / GBN);
+               j.partial + (int64_t)w.tile_n * ntm + w.tile_m, none, w.tile_m, w.tile_n, (j.N + GBN - 1) / GBN, j.ct);
   }
 }
 

@@ -26,7 +26,8 @@ __global__ void k_gram(const double2* Da, const double2* Db, int64_t n, int ny, 
 __global__ void k_e0(const double2* g1, const double2* g2, const double2* f, const double2* X00, DevSpace sp, int ntp,
                      const double* EO, double* E0p, double* E0);
 __global__ void k_class_gemm(const double2* W, const double2* D, int64_t M, int64_t N, int Kp, const RowInfo* rows,
-                             const double* U, const double* eA, const double* E0p, double b, double* partial, AdjOut adj);
+                             const double* U, const double* eA, const double* E0p, double b, double* partial, AdjOut adj, ColTiles ctl);
+__global__ void k_dcompact(const double2* D, int64_t N, ColTiles ctl, double2* Dc);
 __global__ void k_batch_gemm(const GemmJob* jobs, const WorkItem* items, int n_items, int* counter);
 __global__ void k_class22(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
                           const double* G, const double* E0p, double b, int nvb, double* partial);

@@ -71,3 +71,32 @@ def test_factor_gradient_and_breit_derivative_match_oracle(name):
     assert _rel(gB, gB_o) < 1e-7, _rel(gB, gB_o)
     dlam_o = float(np.dot(prob.wx, gw_o[Lc:])) if prob.ham != "DC" else 0.0
     assert abs(float(dl.cpu()[0]) - dlam_o) <= 1e-7 * max(abs(dlam_o), 1e-12) + 1e-15
+
+
+@pytest.mark.parametrize("name", ["mid_dcb", "das"])
+def test_adjoint_with_column_tiles_matches_oracle(name):
+    """The adjoint class kernel over compacted column tiles (amplitudes and
+    denominator weights scattered back to their strings) gives the oracle's
+    dE2/dh, dE2/dc and dE2/dB."""
+    import paper_2608_11529_b300 as e2
+    from paper_2608_11529_b300 import build as e2build
+    e2build.build()
+    prob = CASES[name]()
+    o = Oracle(prob)
+    c, _ = o.ground_state(prob.n_roots)
+    o.set_c(c)
+    seed = np.array([1.0, -0.6][:prob.n_roots])
+    gh_o, gB_o, _, gc_o = o.grad(seed=seed)
+    plan = e2.E2Problem.from_problem(prob)
+    on = [cls for cls in (2, 4, 6) if plan.class_tiles(cls)[0]]
+    assert on
+    for cls in on:
+        plan.set_class_tiles(cls, True)
+    t = e2.device_inputs(prob, c)
+    E2, gh, gc, gbc, gbx, _ = plan.value_and_grad(seed=seed, **t)
+    torch.cuda.synchronize()
+    assert torch.equal(E2, plan.forward(**t)[0])
+    gB = gbc.cpu().numpy() if gbx is None else np.concatenate([gbc.cpu().numpy(), gbx.cpu().numpy()])
+    assert _rel(gh.cpu().numpy(), gh_o) < 1e-7
+    assert _rel(gc.cpu().numpy(), gc_o) < 1e-7
+    assert _rel(gB, gB_o) < 1e-7

@@ -27,12 +27,17 @@ def _jobs():
     return out
 
 
-def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph():
+@pytest.mark.parametrize("col_tiles", [False, True])
+def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph(col_tiles):
     import paper_2608_11529_b300 as e2
     from paper_2608_11529_b300 import build as e2build
     e2build.build()
     jobs = _jobs()
     plans = [e2.E2Problem.from_problem(p) for p, _, _ in jobs]
+    for plan in plans:                             # plain columns, or compacted tiles where a plan exists
+        for cls in (2, 4, 6):
+            if plan.class_tiles(cls)[0]:
+                plan.set_class_tiles(cls, col_tiles)
     inputs = [e2.device_inputs(p, c) for p, _, c in jobs]
     single = []
     for plan, t in zip(plans, inputs):

@@ -9,7 +9,8 @@ explicit Q H P rows and H_KK.  The result is compared with that block's
 per-CTA partial of the GPU forward (e2_partials).  Blocks are taken at both
 ragged edges and at seeded interior positions of every class that has rows.
 Row and string orders are the ones that e2.h documents, rebuilt here from
-that documentation."""
+that documentation; the strings of a column tile come from e2_partials'
+column map."""
 from math import comb
 
 import numpy as np
@@ -112,8 +113,9 @@ def test_sampled_blocks_match_the_oracle_at_full_size(run):
     ne_of = lambda cls: prob.n_elec + CLASSES[cls][0] - CLASSES[cls][1]
     checked = 0
     for cls in CLASSES:
-        part, rt = plan.partials(0, cls)
+        part, rt, perm = plan.partials(0, cls)
         part = part.cpu().numpy()
+        perm = None if perm is None else perm.cpu().numpy()
         if part.size == 0:
             continue
         nA = comb(prob.n_act, ne_of(cls))                 # CAS: every string of ne electrons
@@ -125,7 +127,10 @@ def test_sampled_blocks_match_the_oracle_at_full_size(run):
             picks |= {(int(rng.integers(rt)), int(rng.integers(ct))) for _ in range(2)}
             for tm, tn in sorted(picks):
                 rows = range(64 * tm, min(64 * tm + 64, M))
-                ranks = range(64 * tn, min(64 * tn + 64, nA))
+                if perm is None:                          # consecutive strings
+                    ranks = range(64 * tn, min(64 * tn + 64, nA))
+                else:                                     # column tiles: the tile's strings
+                    ranks = [int(x) for x in perm[64 * tn:64 * tn + 64] if x >= 0]
                 want, scale = _oracle_block(o, E0, prob, cls, rows, ranks)
                 got = part[tn * rt + tm]
                 assert abs(got - want) <= 1e-10 * scale + 1e-14, (cls, tm, tn, got, want)

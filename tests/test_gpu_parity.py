@@ -18,11 +18,15 @@ TOL_E2 = 1e-9
 TOL_E0 = 1e-10
 
 
-def _gpu_e2(prob, c, class_mask=0x1FF, lam=None):
+def _gpu_e2(prob, c, class_mask=0x1FF, lam=None, col_tiles=None):
     import paper_2608_11529_b300 as e2
     from paper_2608_11529_b300 import build as e2build
     e2build.build()
     plan = e2.E2Problem.from_problem(prob, class_mask=class_mask, n_roots=c.shape[0])
+    if col_tiles is not None:                      # force compacted (True) or plain (False) columns
+        for cls in (2, 4, 6):
+            if plan.class_tiles(cls)[0]:
+                plan.set_class_tiles(cls, col_tiles)
     t = e2.device_inputs(prob, c)
     if lam is not None:
         t["lam"] = lam
@@ -61,6 +65,22 @@ def test_e2_matches_oracle(name):
     c, E0, e2, ec = _oracle(prob)
     g2, gc, g0, _ = _gpu_e2(prob, c)
     np.testing.assert_allclose(g0, E0, rtol=0, atol=TOL_E0)
+    np.testing.assert_allclose(gc, ec, rtol=0, atol=TOL_E2)
+    np.testing.assert_allclose(g2, e2, rtol=0, atol=TOL_E2)
+
+
+@pytest.mark.parametrize("name", ["cfg1", "dcb_two_roots_frozen", "das_three_subspaces", "level_shift",
+                                  "full_active"])
+@pytest.mark.parametrize("col_tiles", [True, False])
+def test_column_tiles_match_oracle(name, col_tiles):
+    """Compacted column tiles (the structural zeros of D^{tu}, D^{t+u+} and
+    D^{t+u} skipped per tile) and plain columns both meet the bar."""
+    prob = CASES[name]()
+    c, E0, e2, ec = _oracle(prob)
+    g2, gc, g0, plan = _gpu_e2(prob, c, col_tiles=col_tiles)
+    for cls in (2, 4, 6):
+        tiles, _, used = plan.class_tiles(cls)
+        assert used == (col_tiles and tiles > 0)
     np.testing.assert_allclose(gc, ec, rtol=0, atol=TOL_E2)
     np.testing.assert_allclose(g2, e2, rtol=0, atol=TOL_E2)
 
