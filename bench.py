@@ -217,6 +217,8 @@ def run(args):
     import paper_2608_11529_b300 as e2
     from e2_inputs import make_problem
     over = dict(Lc=args.factors, Lx=args.factors // 2) if args.factors else {}
+    if args.virt:
+        over["n_virt"] = args.virt
     prob = make_problem(args.config, **over)
     plan = e2.E2Problem.from_problem(prob)
     couplings = float(plan.q_per_class.sum()) * plan.n_roots
@@ -361,7 +363,8 @@ def run(args):
         line = {"metric": METRIC, "value": ws * couplings / (ms * 1e-3), "unit": "couplings/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOADS[args.config], "couplings_per_step": int(couplings),
+                "config": {"workload": WORKLOADS[args.config] + (f" [profiling variant {over}]" if over else ""),
+                           "couplings_per_step": int(couplings),
                            "roots": plan.n_roots, "reference": f"device Davidson, {iters} iterations",
                            "l2": "inputs larger than L2: the 456 MB factor set is re-read every step",
                            "column_tiles": col_tiles,
@@ -388,6 +391,9 @@ def main():
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default column tiles")
     ap.add_argument("--ref-seconds", type=float, default=6.0)
+    ap.add_argument("--virt", type=int, default=0,
+                    help="override the virtual spinor count: a smaller variant with the same tile shapes, for "
+                         "profiler captures of the backward (its workspace scales with the virtual pairs)")
     ap.add_argument("--factors", type=int, default=0,
                     help="override the Coulomb factor count (extra set = half); a small-memory variant with the "
                          "same class shapes, for profiler captures")

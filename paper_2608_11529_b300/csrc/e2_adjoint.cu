@@ -22,30 +22,37 @@ namespace e2 {
 // C(m,n) = beta * C(m,n) + sum_k opA(m,k) opB(k,n) on the FP64 tensor pipe
 // (three real products per complex product), opA(m,k) = A[m*sam + k*sak]
 // (conjugated when conjA), opB(k,n) = B[k*sbk + n*sbn] (conjugated when
-// conjB), C(m,n) = C[m*csm + n*csn].  Tile BM x BN = 64 x 64 (warp tiles
-// 32 x 16) or 128 x 16 (warp tiles 16 x 16, for the 16-wide outputs of the
-// classes whose contraction is one active index).  Split K:
+// conjB), C(m,n) = C[m*csm + n*csn].  Tile BM x BN with WM x (8 / WM) warps:
+// 64 x 64 (warp tiles 32 x 16), 128 x 16 (warp tiles 16 x 16, for the
+// 16-wide outputs of the classes whose contraction is one active index) or
+// 64 x 80 (warp tiles 16 x 40, for the compacted rows of a column tile,
+// mostly 78 of them for D^{tu} at 16 active spinors).  Split K:
 // grid.z segments of kseg, segment z writing C + z*czs (beta applies to each
 // segment's own output); a fixed-order sum of the segments (k_zacc) keeps the
 // result deterministic.  Each output element is owned by one CTA per segment.
 // With lower >= 0 only tiles holding some n <= lower + m are computed.
-template <int BM, int BN>
+// Optional index maps gather operand rows / columns: A(m,k) reads row
+// amap[m] and column akmap[k] of A, B(k,n) reads column bmap[n] of B; a
+// negative map entry reads zero.  (bx, by, bz) = (M tile, N tile, K segment).
+template <int BM, int BN, int WM>
 __device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam,
                                            int64_t sak, int conjA, const double2* __restrict__ B, int64_t sbk,
                                            int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm, int64_t csn,
-                                           int beta, int64_t kseg, int64_t czs, int64_t lower) {
+                                           int beta, int64_t kseg, int64_t czs, int64_t lower, int64_t bx, int64_t by,
+                                           int64_t bz, const int32_t* __restrict__ amap = nullptr,
+                                           const int32_t* __restrict__ akmap = nullptr,
+                                           const int32_t* __restrict__ bmap = nullptr) {
   constexpr int BK = 8;
-  constexpr int WN = BN == 64 ? 4 : 1;                  // warps across N
-  constexpr int WM = 8 / WN;                            // warps across M
+  constexpr int WN = 8 / WM;                            // warps across N (WM across M)
   constexpr int MI = BM / (WM * 16);                    // m16 tiles per warp
   constexpr int NI = BN / (WN * 8);                     // n8 tiles per warp
   static_assert(MI >= 1 && NI >= 1 && WM * 16 * MI == BM && WN * 8 * NI == BN, "tile shape");
   __shared__ double sAr[BM][BK + 1], sAi[BM][BK + 1], sAs[BM][BK + 1];
   __shared__ double sBr[BK][BN + 1], sBi[BK][BN + 1], sBs[BK][BN + 1];
-  const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  const int64_t m0 = bx * BM, n0 = by * BN;
   if (lower >= 0 && n0 > lower + m0 + BM - 1) return;  // tile above the diagonal n = lower + m
-  const int64_t kb0 = (int64_t)blockIdx.z * kseg, kb1 = kb0 + kseg < K ? kb0 + kseg : K;
-  C += (int64_t)blockIdx.z * czs;
+  const int64_t kb0 = bz * kseg, kb1 = kb0 + kseg < K ? kb0 + kseg : K;
+  C += bz * czs;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tq = lane & 3;
   const int wm = warp / WN, wn = warp % WN;
@@ -77,13 +84,21 @@ __device__ __forceinline__ void zgemm_body(int64_t M, int64_t N, int64_t K, cons
   const double2 zero = make_double2(0.0, 0.0);
   auto ldA = [&](int64_t k0, int q) {
     const int64_t m = m0 + ra[q], k = k0 + ka[q];
-    double2 v = (m < M && k < kb1) ? A[m * sam + k * sak] : zero;
+    double2 v = zero;
+    if (m < M && k < kb1) {
+      const int64_t mi = amap ? (int64_t)amap[m] : m, ki = akmap ? (int64_t)akmap[k] : k;
+      if (mi >= 0 && ki >= 0) v = A[mi * sam + ki * sak];
+    }
     if (conjA) v.y = -v.y;
     return v;
   };
   auto ldB = [&](int64_t k0, int q) {
     const int64_t kb = k0 + kb_[q], nn = n0 + rb[q];
-    double2 u = (tid + 256 * q < BK * BN && kb < kb1 && nn < N) ? B[kb * sbk + nn * sbn] : zero;
+    double2 u = zero;
+    if (tid + 256 * q < BK * BN && kb < kb1 && nn < N) {
+      const int64_t ni = bmap ? (int64_t)bmap[nn] : nn;
+      if (ni >= 0) u = B[kb * sbk + ni * sbn];
+    }
     if (conjB) u.y = -u.y;
     return u;
   };
@@ -161,14 +176,79 @@ __global__ void __launch_bounds__(256, 1)
 k_zgemm64(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
           const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm,
           int64_t csn, int beta, int64_t kseg, int64_t czs, int64_t lower) {
-  zgemm_body<64, 64>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower);
+  zgemm_body<64, 64, 2>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower,
+                        blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 __global__ void __launch_bounds__(256, 1)
 k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
           const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm,
           int64_t csn, int beta, int64_t kseg, int64_t czs, int64_t lower) {
-  zgemm_body<128, 16>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower);
+  zgemm_body<128, 16, 8>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower,
+                         blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Gamma_D of a column-tiled class in compacted form (tile j = blockIdx.y,
+// 80 compacted rows per blockIdx.x, K segment blockIdx.z):
+//   GDc[(koff + k) * 64 + c] (+)= sum_e conj(T[e][perm[64 j + c]]) W[e][klist[koff + k]]
+// over the chunk's rows e, as the 64 x klen product of the tile's strings
+// with its compacted rows; same split-K segments as the plain product.
+constexpr int kTileRows = 80;
+__global__ void __launch_bounds__(256, 1)
+k_zgemm_gd_tiles(ColTiles ctl, const double2* __restrict__ W, int Kp, const double2* __restrict__ T, int64_t N,
+                 int64_t Mc, double2* __restrict__ GDc, int beta, int64_t kseg, int64_t czs) {
+  const int j = blockIdx.y;
+  const int4 td = ctl.tdesc[j];
+  if ((int64_t)blockIdx.x * kTileRows >= td.y) return;
+  zgemm_body<64, kTileRows, 4>(64, td.y, Mc, T, 1, N, 1, W, Kp, 1, 0, GDc + (int64_t)td.x * 64, 1, 64, beta, kseg, czs,
+                               -1, 0, blockIdx.x, blockIdx.z, ctl.perm + (int64_t)j * 64, nullptr, ctl.klist + td.x);
+}
+
+// Gamma_W of a column-tiled class in compacted form (tile j = blockIdx.z):
+//   GWc[e * krows + koff + k] = sum_c conj(T[e][perm[64 j + c]]) Dc[(koff + k) * 64 + c]
+__global__ void __launch_bounds__(256, 1)
+k_zgemm_gw_tiles(ColTiles ctl, const double2* __restrict__ T, int64_t N, int64_t Mc, int64_t krows,
+                 double2* __restrict__ GWc) {
+  const int j = blockIdx.z;
+  const int4 td = ctl.tdesc[j];
+  if ((int64_t)blockIdx.y * kTileRows >= td.y) return;
+  zgemm_body<64, kTileRows, 4>(Mc, td.y, 64, T, N, 1, 1, ctl.Dc + (int64_t)td.x * 64, 1, 64, 0, GWc + td.x, krows, 1,
+                               0, 64, 0, -1, blockIdx.x, blockIdx.y, 0, nullptr, ctl.perm + (int64_t)j * 64, nullptr);
+}
+
+// GD[klist[koff + k]][perm[64 j + c]] += GDc[(koff + k) * 64 + c], k < ktrue (one block per tile)
+__global__ void k_gd_scatter(ColTiles ctl, const double2* __restrict__ GDc, int64_t N, double2* __restrict__ GD) {
+  const int j = blockIdx.x;
+  const int4 td = ctl.tdesc[j];
+  for (int i = threadIdx.x; i < td.z * 64; i += blockDim.x) {
+    const int k = i / 64, c = i % 64;
+    const int32_t p = ctl.perm[(int64_t)j * 64 + c];
+    if (p < 0) continue;
+    double2* o = GD + (int64_t)ctl.klist[td.x + k] * N + p;
+    const double2 v = GDc[((int64_t)td.x + k) * 64 + c];
+    o->x += v.x;
+    o->y += v.y;
+  }
+}
+
+// GW[e][x] = sum_j GWc[e * krows + koff_j + pos[j][x]] over the tiles j whose
+// compacted rows include x (pos[j][x] >= 0), in tile order
+__global__ void k_gw_reduce(const int4* __restrict__ tdesc, const int32_t* __restrict__ pos, int64_t tiles, int Kp,
+                            const double2* __restrict__ GWc, int64_t krows, int64_t Mc, double2* __restrict__ GW) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= Mc * Kp) return;
+  const int64_t e = idx / Kp;
+  const int x = (int)(idx % Kp);
+  double2 s = make_double2(0.0, 0.0);
+  const double2* row = GWc + e * krows;
+  for (int64_t j = 0; j < tiles; ++j) {
+    const int32_t p = pos[j * Kp + x];
+    if (p < 0) continue;
+    const double2 v = row[tdesc[j].x + p];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  GW[idx] = s;
 }
 
 // C(m,n) = beta C(m,n) + sum_z part[z*ps + m*N + n] in z order (segments of a

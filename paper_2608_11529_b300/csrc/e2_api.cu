@@ -44,9 +44,12 @@ struct ColPlan {
   std::vector<int32_t> perm;   // [tiles * 64] list index, -1 = padding
   std::vector<int32_t> tdesc;  // [tiles][4] {koff, klen, ktrue, 0}
   std::vector<int32_t> klist;  // [krows]
+  std::vector<int32_t> pos;    // [tiles][Kp] compacted row of table row x in tile j, -1 if absent
   int64_t tiles = 0, krows = 0;
+  int maxklen = 0;             // longest compacted contraction of a tile
+  int64_t gd_ctas = 0;         // sum over tiles of ceil(klen / 64)
   double ratio = 1.0;          // krows / (tiles * Kp): share of the dense contraction
-  size_t o_perm = 0, o_tdesc = 0, o_klist = 0, o_Dc = 0;  // o_Dc: per-root D region
+  size_t o_perm = 0, o_tdesc = 0, o_klist = 0, o_pos = 0, o_Dc = 0;  // o_Dc: per-root D region
 };
 
 // Bump allocator over the workspace (256-byte aligned segments).
@@ -116,6 +119,7 @@ struct e2_problem {
   size_t o_bGX01, o_bGX10, o_bGX00, o_bR22, o_bHs22, o_bP22, o_bG22c, o_bGg22, o_bCs, o_bGB, o_bFtr, o_bGw, o_bRg;
   size_t o_bPart, bpart_bytes;  // split-K segments
   size_t tsh_bytes;
+  size_t o_bGDc, o_bGWc;
   size_t bwd_bytes;
   // compacted column tiles of the dense classes and whether each class uses them
   ColPlan cplan[E2_NCLASS];
@@ -348,7 +352,12 @@ void build_colplan(e2_problem* P, int cls, int fam, int kvalid) {
     const int klen = std::max(8, (ktrue + 7) / 8 * 8);
     for (int x = ktrue; x < klen; ++x) cp.klist.push_back(0);
     cp.tdesc.insert(cp.tdesc.end(), {koff, klen, ktrue, 0});
+    cp.maxklen = std::max(cp.maxklen, klen);
+    cp.gd_ctas += (klen + 79) / 80;  // 64 x 80 product tiles of the compacted backward products
   }
+  cp.pos.assign((size_t)cp.tiles * Kp, -1);
+  for (int64_t j = 0; j < cp.tiles; ++j)
+    for (int k = 0; k < cp.tdesc[4 * j + 2]; ++k) cp.pos[(size_t)j * Kp + cp.klist[cp.tdesc[4 * j] + k]] = k;
   cp.krows = (int64_t)cp.klist.size();
   cp.ratio = (double)cp.krows / ((double)cp.tiles * Kp);
   cp.built = true;
@@ -455,6 +464,7 @@ e2_status build_plan(e2_problem* P) {
     cp.o_perm = ws.take(sizeof(int32_t) * cp.perm.size());
     cp.o_tdesc = ws.take(sizeof(int32_t) * cp.tdesc.size());
     cp.o_klist = ws.take(sizeof(int32_t) * cp.klist.size());
+    cp.o_pos = ws.take(sizeof(int32_t) * cp.pos.size());
   }
   P->plan_bytes = ws.top - P->o_plan;
   // device-computed data
@@ -559,17 +569,23 @@ e2_status build_plan(e2_problem* P) {
   P->solve_bytes = ws.top;
   // adjoint region on top of the solver layout (the forward one is its prefix)
   {
-    const size_t tbudget = size_t(4) << 30;
-    size_t tmax = 16, hrow = 8, hcol = 8, scalt = 16, hsum = 8, hA = 8;
+    const size_t tbudget = size_t(4) << 30, gwbudget = size_t(8) << 30;
+    size_t tmax = 16, hrow = 8, hcol = 8, scalt = 16, hsum = 8, hA = 8, gdc = 16, gwc = 16;
     for (int c : {2, 5, 7, 4, 6}) {
       const int64_t Mc = P->M[c], Nc = lsize(c);
       P->chunk_rows[c] = 0;
       if (Mc == 0 || Nc == 0) continue;
       int64_t rows_fit = (int64_t)(tbudget / (16 * (size_t)Nc)) / 64 * 64;
+      if (P->cplan[c].built)  // compacted Gamma_W of a chunk: rows x compacted columns
+        rows_fit = std::min<int64_t>(rows_fit, (int64_t)(gwbudget / (16 * (size_t)P->cplan[c].krows)) / 64 * 64);
       rows_fit = std::max<int64_t>(64, rows_fit);
       P->chunk_rows[c] = std::min<int64_t>(rows_fit, (Mc + 63) / 64 * 64);
       const int64_t rt = (Mc + 63) / 64, ct = (Nc + 63) / 64;
       tmax = std::max(tmax, (size_t)16 * P->chunk_rows[c] * Nc);
+      if (P->cplan[c].built) {
+        gdc = std::max(gdc, (size_t)16 * P->cplan[c].krows * 64);
+        gwc = std::max(gwc, (size_t)16 * P->chunk_rows[c] * P->cplan[c].krows);
+      }
       hrow = std::max(hrow, (size_t)8 * Mc * ct);
       hcol = std::max(hcol, (size_t)8 * rt * Nc);
       scalt = std::max(scalt, (size_t)16 * rt * ct);
@@ -584,6 +600,8 @@ e2_status build_plan(e2_problem* P) {
     const size_t yz = (size_t)std::max<int64_t>(1, nyb * P->ncp);
     P->o_gD = ws.take(P->d_stride);
     P->o_bT = ws.take(tmax);
+    P->o_bGDc = ws.take(gdc);  // compacted Gamma_D / Gamma_W of a column-tiled class
+    P->o_bGWc = ws.take(gwc);
     P->o_bHrow = ws.take(hrow);
     P->o_bHcol = ws.take(hcol);
     P->o_bScalT = ws.take(scalt);
@@ -683,6 +701,7 @@ e2_status build_plan(e2_problem* P) {
     put(P->plan_blob, rel(cp.o_perm), cp.perm.data(), cp.perm.size());
     put(P->plan_blob, rel(cp.o_tdesc), cp.tdesc.data(), cp.tdesc.size());
     put(P->plan_blob, rel(cp.o_klist), cp.klist.data(), cp.klist.size());
+    put(P->plan_blob, rel(cp.o_pos), cp.pos.data(), cp.pos.size());
   }
   return E2_OK;
 }
@@ -986,6 +1005,23 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
                                                                        P->ntp * na, P->ntp * na, ws + P->o_X10), ++g_launches);
 }
 
+
+// Gamma_D of a column-tiled class in compacted form, GDc (+)= per tile
+// W[:, klist]^T conj(T[:, perm]) over the chunk's Mc rows, split-K as zgemm.
+void zgemm_gd_tiles(cudaStream_t st, const ColPlan& cp, const ColTiles& ctl, const double2* W, int Kp,
+                    const double2* T, int64_t N, int64_t Mc, double2* GDc, int beta) {
+  const int64_t czs = cp.krows * 64;
+  const int nseg = splitk_segments(cp.gd_ctas, Mc, 16 * (size_t)czs);
+  const int64_t kseg = (Mc + nseg - 1) / nseg;
+  dim3 grid((unsigned)((cp.maxklen + 79) / 80), (unsigned)cp.tiles, (unsigned)nseg);
+  if (nseg == 1) {
+    (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, GDc, beta, kseg, 0), ++g_launches);
+    return;
+  }
+  double2* part = (double2*)g_splitk;
+  (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, part, 0, kseg, czs), ++g_launches);
+  (k_zacc<<<blocks(czs), 256, 0, st>>>(part, nseg, czs, cp.krows, 64, GDc, 64, 1, beta), ++g_launches);
+}
 
 // Coupling tensors of root r, the active one- and two-particle blocks of
 // its reference state, and E0 (Sec. 2.3).
@@ -1610,6 +1646,9 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       const int64_t M = P->M[cls], N = L.n, Kp = P->Kp[cls];
       const int64_t rt = (M + 63) / 64, ct = (N + 63) / 64;
       const double2* W = (const double2*)(ws + P->o_W[cls]);
+      const bool tiled = P->use_cols[cls];
+      const ColPlan& cp = P->cplan[cls];
+      const ColTiles ctl = col_tiles(P, ws, r, cls);
       for (int64_t m0 = 0; m0 < M; m0 += P->chunk_rows[cls]) {
         const int64_t Mc = std::min<int64_t>(P->chunk_rows[cls], M - m0);
         AdjOut adj{(double2*)B(P->o_bT), want_B ? (double*)B(P->o_bHm) : nullptr, (double*)B(P->o_bHrow),
@@ -1618,18 +1657,31 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
                                             L.eA, X.E0p + r, b, nullptr, adj, col_tiles(P, ws, r, cls)), ++g_launches);
         // Gamma_D[x][A] += sum_e W[e][x] conj(T[e][A]) (split over the rows of the chunk)
-        if (Kp >= 64)
+        if (tiled)
+          zgemm_gd_tiles(st, cp, ctl, W + m0 * Kp, (int)Kp, adj.T, N, Mc, (double2*)B(P->o_bGDc), m0 > 0);
+        else if (Kp >= 64)
           zgemm(st, Kp, N, Mc, W + m0 * Kp, 1, Kp, 0, adj.T, N, 1, 1, GDfor[cls], N, 1, 1, 64);
         else
           zgemm(st, N, Kp, Mc, adj.T, 1, N, 1, W + m0 * Kp, Kp, 1, 0, GDfor[cls], 1, N, 1, 16);
         if (cls == 4)
           (k_rowdot<<<(unsigned)Mc, 256, 0, st>>>(adj.T, T.DTDU, N, (double2*)B(P->o_bRowdot) + m0), ++g_launches);
         if (want_B) {  // Gamma_W = conj(T) D^T and the per-row occupation sums of eta
-          zgemm(st, Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0, (double2*)B(P->o_bGW[cls]) + m0 * Kp, Kp, 1, 0,
-                Kp >= 64 ? 64 : 16);
+          double2* GW = (double2*)B(P->o_bGW[cls]) + m0 * Kp;
+          if (tiled) {  // per tile over its compacted rows, then summed per table row in tile order
+            dim3 g((unsigned)((Mc + 63) / 64), (unsigned)((cp.maxklen + 79) / 80), (unsigned)cp.tiles);
+            (k_zgemm_gw_tiles<<<g, 256, 0, st>>>(ctl, adj.T, N, Mc, cp.krows, (double2*)B(P->o_bGWc)), ++g_launches);
+            (k_gw_reduce<<<blocks(Mc * Kp), 256, 0, st>>>(ctl.tdesc, (const int32_t*)(ws + cp.o_pos), cp.tiles,
+                                                         (int)Kp, (const double2*)B(P->o_bGWc), cp.krows, Mc, GW),
+             ++g_launches);
+          } else {
+            zgemm(st, Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0, GW, Kp, 1, 0, Kp >= 64 ? 64 : 16);
+          }
           (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na), ++g_launches);
         }
       }
+      if (tiled)
+        (k_gd_scatter<<<(unsigned)cp.tiles, 256, 0, st>>>(ctl, (const double2*)B(P->o_bGDc), N, GDfor[cls]),
+         ++g_launches);
       if (cls == 4) (k_fock11<<<blocks(M), 256, 0, st>>>((const double2*)B(P->o_bRowdot), X.sp, Gf), ++g_launches);
       (k_rowsum<<<blocks(M), 256, 0, st>>>((const double*)B(P->o_bHrow), M, ct, 0, hsum), ++g_launches);
       (k_xmarg<<<P->nx, 256, 0, st>>>((const RowInfo*)(ws + P->o_rows[cls]), hsum, M, P->nx, Nx), ++g_launches);
