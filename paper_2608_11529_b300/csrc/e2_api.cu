@@ -92,6 +92,7 @@ struct e2_problem {
   size_t o_rows[E2_NCLASS], o_W[E2_NCLASS];
   size_t o_G22, o_X01, o_X10, o_X00;
   size_t o_vaY, o_vaZ, o_vaX, va_cap;
+  size_t o_xYc, o_xZaa, o_x12, o_x01;
   size_t o_DT, o_DTD, o_DTU, o_DTDUD, o_DTDU;  // per-root stride below
   size_t d_stride;                              // bytes per root of all D tables
   size_t o_g1, o_g2, g_stride;                  // gram outputs per root
@@ -545,9 +546,15 @@ e2_status build_plan(e2_problem* P) {
   {
     const int64_t nva = (int64_t)P->nvc * P->na;
     const size_t yb = 16 * (size_t)std::max<int64_t>(nva * Lt, 1);
+    auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
     P->o_vaY = P->o_dstart;
-    P->o_vaZ = P->o_vaY + yb;
-    P->o_vaX = P->o_vaZ + yb;
+    P->o_vaZ = P->o_vaY + al(yb);
+    // (virtual, core) and active-pair factor columns, (ai|bt) and (av|uw)
+    P->o_xYc = P->o_vaZ + al(yb);
+    P->o_xZaa = P->o_xYc + al(16 * (size_t)std::max<int64_t>((int64_t)P->nvc * P->ncc * Lt, 1));
+    P->o_x12 = P->o_xZaa + al(16 * (size_t)std::max<int64_t>((int64_t)P->na * P->na * Lt, 1));
+    P->o_x01 = P->o_x12 + al(16 * (size_t)std::max<int64_t>((int64_t)P->nvc * P->ncc * nva, 1));
+    P->o_vaX = P->o_x01 + al(16 * (size_t)std::max<int64_t>(nva * P->na * P->na, 1));
     const size_t full = 16 * (size_t)std::max<int64_t>(nva * nva, 1);
     const size_t least = 16 * (size_t)std::max<int64_t>((int64_t)std::min(8, P->nvc) * P->na * nva, 1);
     const size_t room = ws.top > P->o_vaX ? ws.top - P->o_vaX : 0;
@@ -967,17 +974,34 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
   Ctx X = ctx(P, ws);
   const int modes[E2_NCLASS] = {-1, -1, INT_W02, -1, INT_W11, INT_W12, INT_W20, INT_W21, -1};
   const int cols[E2_NCLASS] = {0, 0, P->ntp, 0, 1 + na * na, na, P->ntp, na, 0};
+  // factor columns for the blocks formed on the tensor pipe: <ab||tu>,
+  // <ab||it> and <au||vw> as products over the factor index L
+  const int64_t nva = (int64_t)P->nvc * na;
+  double2* Yw = (double2*)(ws + P->o_vaY);
+  double2* Zf = (double2*)(ws + P->o_vaZ);
+  const bool on2 = P->M[2] > 0 && P->part_cnt[2] > 0, on5 = P->M[5] > 0 && P->part_cnt[5] > 0;
+  const bool on1 = P->part_cnt[1] > 0;
+  if ((on2 || on5 || on1) && nva > 0) {
+    (k_vafactors<<<blocks(nva * Lt), 256, 0, st>>>(X.sp, X.Bo, X.wt, Lt, Yw, Zf), ++g_launches);
+    (k_xfactors<<<blocks(((int64_t)P->nvc * P->ncc + (int64_t)na * na) * Lt), 256, 0, st>>>(
+         X.sp, X.Bo, X.wt, Lt, (double2*)(ws + P->o_xYc), (double2*)(ws + P->o_xZaa)), ++g_launches);
+  }
   for (int c = 0; c < E2_NCLASS; ++c) {
     if (modes[c] < 0 || P->M[c] == 0 || P->part_cnt[c] == 0) continue;
     (k_rows<<<blocks(P->M[c]), 256, 0, st>>>(c, X.sp, X.epsh, X.G, P->M[c], (RowInfo*)(ws + P->o_rows[c])), ++g_launches);
+    if (c == 5) {
+      // (ai|bt) = sum_L wt_L B_ai B_bt for all (a,i), (b,t), then <ab||it> = (ai|bt) - (at|bi)
+      double2* X12 = (double2*)(ws + P->o_x12);
+      zgemm(st, (int64_t)P->nvc * P->ncc, nva, Lt, (const double2*)(ws + P->o_xYc), Lt, 1, 0, Zf, nva, 1, 0, X12, nva, 1,
+            0);
+      (k_w12<<<blocks(P->M[c] * P->Kp[c]), 256, 0, st>>>(X.sp, X12, nva, P->M[c], P->Kp[c], (double2*)(ws + P->o_W[c])),
+       ++g_launches);
+      continue;
+    }
     if (c == 2) {
       // (at|bu) = sum_L wt_L B_at B_bu on the tensor pipe, lower triangle
       // (a < b) in stripes of whole virtuals b, then <ab||tu> = (at|bu) - (au|bt)
-      const int64_t nva = (int64_t)P->nvc * na;
-      double2* Yw = (double2*)(ws + P->o_vaY);
-      double2* Zf = (double2*)(ws + P->o_vaZ);
       double2* Xv = (double2*)(ws + P->o_vaX);
-      (k_vafactors<<<blocks(nva * Lt), 256, 0, st>>>(X.sp, X.Bo, X.wt, Lt, Yw, Zf), ++g_launches);
       for (int b0 = 0, b1; b0 < P->nvc; b0 = b1) {
         b1 = b0 + 1;
         while (b1 < P->nvc && 16 * (size_t)(b1 + 1 - b0) * na * (size_t)(b1 + 1) * na <= P->va_cap) ++b1;
@@ -997,9 +1021,12 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
   if (P->part_cnt[8] > 0)
     (k_integrals<<<blocks(P->ncp * P->nvp), 256, 0, st>>>(INT_G22, X.sp, X.Bo, X.wt, Lt, X.f, P->ncp, (int)P->nvp,
                                                          (int)P->nvp, ws + P->o_G22), ++g_launches);
-  if (P->part_cnt[1] > 0)
-    (k_integrals<<<blocks((int64_t)P->nvc * na * P->ntp), 256, 0, st>>>(INT_X01, X.sp, X.Bo, X.wt, Lt, X.f, P->nvc,
-                                                                       na * P->ntp, na * P->ntp, ws + P->o_X01), ++g_launches);
+  if (on1 && nva > 0) {  // (av|uw) for all (a,v), (u,w), then <au||vw> = (av|uw) - (aw|uv)
+    double2* X01g = (double2*)(ws + P->o_x01);
+    zgemm(st, nva, (int64_t)na * na, Lt, Yw, Lt, 1, 0, (const double2*)(ws + P->o_xZaa), (int64_t)na * na, 1, 0, X01g,
+          (int64_t)na * na, 1, 0);
+    (k_x01<<<blocks((int64_t)P->nvc * na * P->ntp), 256, 0, st>>>(X.sp, X01g, (double2*)(ws + P->o_X01)), ++g_launches);
+  }
   if (P->part_cnt[3] > 0)
     (k_integrals<<<blocks((int64_t)P->ncc * P->ntp * na), 256, 0, st>>>(INT_X10, X.sp, X.Bo, X.wt, Lt, X.f, P->ncc,
                                                                        P->ntp * na, P->ntp * na, ws + P->o_X10), ++g_launches);

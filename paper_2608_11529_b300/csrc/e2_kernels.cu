@@ -228,6 +228,65 @@ __global__ void k_vafactors(DevSpace sp, const double2* __restrict__ Bo, const d
   Yw[at * Lt + L] = make_double2(wt[L] * b.x, wt[L] * b.y);
 }
 
+// Factor columns of (virtual, core) pairs and of active pairs:
+//   Ywc[(a*ncc + i)*Lt + L] = wt_L B^L_{a i},  Zaa[L*na*na + u*na + w] = B^L_{u w}
+__global__ void k_xfactors(DevSpace sp, const double2* __restrict__ Bo, const double* __restrict__ wt, int Lt,
+                           double2* __restrict__ Ywc, double2* __restrict__ Zaa) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int na = sp.n_act;
+  const int64_t nvc = (int64_t)sp.nvc * sp.ncc * Lt, naa = (int64_t)na * na * Lt;
+  if (idx < nvc) {
+    const int L = (int)(idx % Lt);
+    const int64_t ai = idx / Lt;
+    const int a = (int)(ai / sp.ncc), i = (int)(ai % sp.ncc);
+    const double2 b = Bo[((int64_t)L * sp.n + sp.vc[a]) * sp.n_occ + sp.cc[i]];
+    Ywc[idx] = make_double2(wt[L] * b.x, wt[L] * b.y);
+  } else if (idx < nvc + naa) {
+    const int64_t r = idx - nvc;
+    const int L = (int)(r / (na * na));
+    const int uw = (int)(r % (na * na));
+    Zaa[r] = Bo[((int64_t)L * sp.n + sp.a0 + uw / na) * sp.n_occ + sp.a0 + uw % na];
+  }
+}
+
+// <ab||it> = (ai|bt) - (at|bi) from X[(a*ncc + i)*ldx + b*na + t] = (ai|bt):
+// rows (i, a<b) = i * npair_v + pair(a,b), columns t padded to Kp with zeros
+__global__ void k_w12(DevSpace sp, const double2* __restrict__ X, int64_t ldx, int64_t M, int Kp,
+                      double2* __restrict__ W) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= M * Kp) return;
+  const int64_t row = idx / Kp;
+  const int t = (int)(idx % Kp), na = sp.n_act;
+  double2 v = make_double2(0.0, 0.0);
+  if (t < na) {
+    const int64_t nvp = pairs(sp.nvc);
+    const int i = (int)(row / nvp);
+    int a, b;
+    pair_decode(row % nvp, a, b);
+    const double2 x1 = X[((int64_t)a * sp.ncc + i) * ldx + (int64_t)b * na + t];
+    const double2 x2 = X[((int64_t)b * sp.ncc + i) * ldx + (int64_t)a * na + t];
+    v = make_double2(x1.x - x2.x, x1.y - x2.y);
+  }
+  W[idx] = v;
+}
+
+// <au||vw> = (av|uw) - (aw|uv) from X[(a*na + v)*na*na + u*na + w] = (av|uw):
+// rows a, columns u * ntp + pair(v,w)
+__global__ void k_x01(DevSpace sp, const double2* __restrict__ X, double2* __restrict__ X01) {
+  const int na = sp.n_act, ntp = (int)pairs(na);
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= (int64_t)sp.nvc * na * ntp) return;
+  const int a = (int)(idx / ((int64_t)na * ntp));
+  const int col = (int)(idx % ((int64_t)na * ntp));
+  const int u = col / ntp;
+  int v, w;
+  pair_decode(col % ntp, v, w);
+  const int64_t n2 = (int64_t)na * na;
+  const double2 x1 = X[((int64_t)a * na + v) * n2 + u * na + w];
+  const double2 x2 = X[((int64_t)a * na + w) * n2 + u * na + v];
+  X01[idx] = make_double2(x1.x - x2.x, x1.y - x2.y);
+}
+
 // <ab||tu> = (at|bu) - (au|bt) for the rows (a<b) with b0 <= b < b1 (a
 // contiguous run of rows in pair order), columns (t<u) padded to Kp with zeros,
 // from a stripe X[(b*na + u - b0*na)*ldx + a*na + t] = (at|bu), a < b.

@@ -18,6 +18,9 @@ __global__ void k_U(DevList Ls, DevSpace sp, const double* G);
 __global__ void k_integrals(int mode, DevSpace sp, const double2* Bo, const double* wt, int L, const double2* f,
                             int64_t rows, int cols, int ld, void* out);
 __global__ void k_vafactors(DevSpace sp, const double2* Bo, const double* wt, int Lt, double2* Yw, double2* Z);
+__global__ void k_xfactors(DevSpace sp, const double2* Bo, const double* wt, int Lt, double2* Ywc, double2* Zaa);
+__global__ void k_w12(DevSpace sp, const double2* X, int64_t ldx, int64_t M, int Kp, double2* W);
+__global__ void k_x01(DevSpace sp, const double2* X, double2* X01);
 __global__ void k_w02(DevSpace sp, const double2* X, int64_t ldx, int b0, int b1, int Kp, double2* W);
 __global__ void k_rows(int cls, DevSpace sp, const double* epsh, const double* G, int64_t M, RowInfo* out);
 __global__ void k_dtable(int fam, DevList Ls, DevList Pl, DevDas das, const int64_t* binom, const double2* c, int Kp,
