@@ -37,6 +37,10 @@ METRIC = "E2 perturber couplings/s (FP64, |ΔE2|≤1e-9 Eh); fwd+bwd vs fwd time
 WORKLOADS = {
     "cfg2": "Ne-shaped DCG: 2 core + CAS(8e,16) + 200 virtual spinors, 400 Coulomb + 200 Gaunt factors, 1 root",
     "cfg1": "DC: 4 core + CAS(6e,12) + 40 virtual spinors, 60 Coulomb factors, 1 root",
+    "cfg3": "Ar-shaped DCB: 8 core + DAS 3x8 spinors (10e, N_P = 40,608) + 400 virtual spinors, 600 Coulomb + "
+            "300 Breit factors, 1 root",
+    "cfg4": "Kr-shaped DCB: 16 core + CAS(8e,24) + 600 virtual spinors, 900 Coulomb + 450 Breit factors, 4 roots",
+    "cfg5": "Xe-shaped DCB: 46 core + CAS(8e,24) + 1000 virtual spinors, 1400 Coulomb + 700 Breit factors, 1 root",
 }
 GEMM_CLASSES = {2: "ntp", 5: "na", 7: "na", 4: "na2p1", 6: "ntp"}
 CLASS_NAMES = ["(0,0)", "(0,1)", "(0,2)", "(1,0)", "(1,1)", "(1,2)", "(2,0)", "(2,1)", "(2,2)"]
@@ -51,11 +55,18 @@ def _dist():
     return ws, rank, local
 
 
-def _ncols(prob, cls):
-    """Strings of a dense class of a CAS workload (its coupling-table columns)."""
-    from math import comb
-    h, p = divmod(cls, 3)
-    return comb(prob.n_act, prob.n_elec + h - p)
+def _rows(prob, cls):
+    """External rows of class cls (correlated core / virtual indices)."""
+    nc = sum(1 for k in range(prob.n_core) if not prob.frozen[k])
+    nv = sum(1 for v in range(prob.n_core + prob.n_act, prob.n) if not prob.frozen[v])
+    pair = lambda n: n * (n - 1) // 2
+    return {0: 1, 1: nv, 2: pair(nv), 3: nc, 4: nc * nv, 5: nc * pair(nv), 6: pair(nc), 7: pair(nc) * nv,
+            8: pair(nc) * pair(nv)}[cls]
+
+
+def _ncols(prob, plan, cls):
+    """Strings of a class (its coupling-table columns)."""
+    return plan.q_per_class[cls] / max(_rows(prob, cls), 1)
 
 
 def _kpad(prob, cls):
@@ -165,8 +176,9 @@ def oracle_rate(prob, seconds=15.0, seed=0):
     E0 = np.zeros(1)
     n = 256
     while True:   # calibrate the sample size to about `seconds` of work
+        ks = _sample_ks(prob, n, rng)
         t0 = time.perf_counter()
-        o.couplings(E0, *_sample_ks(prob, n, rng))
+        o.couplings(E0, *ks)
         dt = time.perf_counter() - t0
         if dt >= 0.2 * seconds or n >= 2_000_000:
             break
@@ -222,6 +234,7 @@ def run(args):
     prob = make_problem(args.config, **over)
     plan = e2.E2Problem.from_problem(prob)
     couplings = float(plan.q_per_class.sum()) * plan.n_roots
+    fbytes = 16.0 * (prob.Bc.shape[0] + (prob.Bx.shape[0] if prob.ham != "DC" else 0)) * prob.n * prob.n
     t = e2.device_inputs(prob, prob.X0, device=dev)
     c, E0_ref, iters = plan.reference_solve(t["h"], t["B_c"], t["c"], t["B_x"], t["w_x"], lam=t["lam"], tol=1e-10)
     t["c"] = c
@@ -289,7 +302,7 @@ def run(args):
         flops = 6.0 * plan.q_per_class[dom] * _kdim(prob, dom)
         tiles, krows, used = plan.class_tiles(dom)
         if used:
-            flops = 6.0 * (plan.q_per_class[dom] / _ncols(prob, dom)) * krows * 64
+            flops = 6.0 * (plan.q_per_class[dom] / _ncols(prob, plan, dom)) * krows * 64
         achieved = flops / (ktime[dom] * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_dmma, "unit": "TFLOP/s",
                 "frac": achieved / peak_dmma, "traffic": _traffic("k_class_gemm"),
@@ -354,7 +367,7 @@ def run(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        r, n, dt = oracle_rate(prob, seconds=args.ref_seconds)
+        r, n, dt = oracle_rate(prob, seconds=args.cpu_seconds)
         cpu = {"value": r, "unit": "couplings/s", "cores": os.cpu_count(), "kind": "oracle",
                "sample": f"{n} random external determinants of this workload (class-size weighted), "
                          f"V_K from the explicit Q H P row and H_KK each, {dt:.1f} s"}
@@ -366,7 +379,7 @@ def run(args):
                 "config": {"workload": WORKLOADS[args.config] + (f" [profiling variant {over}]" if over else ""),
                            "couplings_per_step": int(couplings),
                            "roots": plan.n_roots, "reference": f"device Davidson, {iters} iterations",
-                           "l2": "inputs larger than L2: the 456 MB factor set is re-read every step",
+                           "l2": f"inputs larger than L2: the {fbytes / 1e6:.0f} MB factor set is re-read every step",
                            "column_tiles": col_tiles,
                            "E2": float(E2.cpu()[0]), "E0": float(E0.cpu()[0]),
                            "class_ms": {CLASS_NAMES[k]: ktime[k] for k in present}},
@@ -385,11 +398,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--config", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--config", default="cfg2", choices=sorted(WORKLOADS),
+                    help="cfg2 is the benchmark workload; the others run as evidence / profiling variants")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default column tiles")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0,
+                    help="oracle work per cpu_baseline sample (the sample is sized to about this long)")
     ap.add_argument("--ref-seconds", type=float, default=6.0)
     ap.add_argument("--virt", type=int, default=0,
                     help="override the virtual spinor count: a smaller variant with the same tile shapes, for "

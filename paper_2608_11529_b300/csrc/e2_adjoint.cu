@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(256)
 k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* __restrict__ g2,
               const double* __restrict__ epsh, const double* __restrict__ G, const double* __restrict__ E0p, double b,
               int nvb, double s, const double2* __restrict__ g1, double* __restrict__ cpart,
-              double* __restrict__ hpart, double* __restrict__ vpart) {
+              double* __restrict__ hpart, double* __restrict__ vpart, double* __restrict__ part) {
   const double inv_n = 1.0 / g1[0].x;
   __shared__ double sGab[8][8], sG2[8][8], sAl[2][8];
   __shared__ double sh[32];
@@ -504,12 +504,13 @@ k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const doub
   double ha[8], hb[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) ha[k] = hb[k] = 0.0;
-  double csum = 0.0, hsum = 0.0, gv = 0.0;
+  double csum = 0.0, hsum = 0.0, gv = 0.0, acc = 0.0;
   if (A < Ls.n) {
     const double chi_ij = -epsh[gi] - epsh[gj] + G[(int64_t)gi * sp.n + gj];
     const double ct = *E0p - Ls.eA[A] + Ls.U[(int64_t)iu * Ls.n + A] + Ls.U[(int64_t)ju * Ls.n + A] - chi_ij;
     const double2 cv = c[A];
     const double c2 = (cv.x * cv.x + cv.y * cv.y) * inv_n;
+    double inner = 0.0;  // sum w g(D): the forward's per-string sum, same order
     double pa[8], pb[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
@@ -532,8 +533,10 @@ k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const doub
         hsum += hk;
         ha[x] += hk;
         hb[y] += hk;
+        inner = fma(w, gk, inner);
       }
     }
+    acc = fma(cv.x, cv.x, cv.y * cv.y) * inner;
   }
   const int64_t yz = (int64_t)blockIdx.z * gridDim.y + blockIdx.y;
   if (A < Ls.n) {
@@ -553,6 +556,10 @@ k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const doub
     vpart[cta * 19 + 16] = v;
     vpart[cta * 19 + 17] = v;
     vpart[cta * 19 + 18] = w2;
+  }
+  if (part) {  // the forward's E2 partial of this block
+    const double tot = block_sum(acc, sh);
+    if (tid == 0) part[cta] = tot;
   }
 }
 
@@ -610,15 +617,18 @@ __global__ void k_gather_t(int cls, DevList Lx, DevList L12, DevList L02, DevLis
                            const double2* __restrict__ X10, const double2* __restrict__ X00,
                            const double2* __restrict__ f, const double* __restrict__ epsh,
                            const double* __restrict__ E0p, double b, double s, const double2* __restrict__ g1,
-                           double2* __restrict__ T, double* __restrict__ H, double* __restrict__ GV) {
+                           double2* __restrict__ T, double* __restrict__ H, double* __restrict__ GV,
+                           double* __restrict__ part) {
+  __shared__ double sh[32];
   const double inv_n = 1.0 / g1[0].x, s2n = 2.0 * s * inv_n;
   const int row = blockIdx.y;
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (g >= Lx.n) return;
+  double acc = 0.0;
+  if (g < Lx.n) {
   const uint64_t A = Lx.str[g];
   const int na = sp.n_act, ntp = (int)pairs(na);
   double2 V = make_double2(0.0, 0.0);
-  double Dk = *E0p - Lx.eA[g];
+  double Dk = 0.0;  // denominators in the forward's operation order
   if (cls == 1) {
     const int ga = sp.vc[row];
     int64_t a12 = list_addr(L12, das, binom, A);
@@ -643,7 +653,7 @@ __global__ void k_gather_t(int cls, DevList Lx, DevList L12, DevList L02, DevLis
       V.x += sacc.x;
       V.y += sacc.y;
     }
-    Dk -= epsh[ga] + Lx.U[(int64_t)(sp.ncc + row) * Lx.n + g];
+    Dk = *E0p - Lx.eA[g] - epsh[ga] - Lx.U[(int64_t)(sp.ncc + row) * Lx.n + g];
   } else if (cls == 3) {
     const int gi = sp.cc[row];
     int64_t a21 = list_addr(L21, das, binom, A);
@@ -667,16 +677,23 @@ __global__ void k_gather_t(int cls, DevList Lx, DevList L12, DevList L02, DevLis
         V.y += sacc.y;
       }
     }
-    Dk += epsh[gi] + Lx.U[(int64_t)row * Lx.n + g];
+    Dk = *E0p - Lx.eA[g] + epsh[gi] + Lx.U[(int64_t)row * Lx.n + g];
   } else {
     V = active_sigma(A, L11, L02, das, sp, binom, DTDU, DTU, X00, f);
+    Dk = *E0p - Lx.eA[g];
   }
-  const double v2 = V.x * V.x + V.y * V.y;
+  const double v2 = fma(V.x, V.x, V.y * V.y);
   double gk, hk;
   en_derivs(v2 * inv_n, Dk, b, gk, hk);
   T[(int64_t)row * Lx.n + g] = make_double2(s2n * gk * V.x, s2n * gk * V.y);
   H[(int64_t)row * Lx.n + g] = s * hk;
   GV[(int64_t)row * Lx.n + g] = s * gk * v2 * inv_n;
+  acc = v2 * gk;  // the forward's E2 term (gk = en_g(Dk, b))
+  }
+  if (part) {  // the forward's E2 partial of this block
+    const double tot = block_sum(acc, sh);
+    if (threadIdx.x == 0) part[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  }
 }
 
 

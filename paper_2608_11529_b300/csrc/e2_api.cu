@@ -538,11 +538,13 @@ e2_status build_plan(e2_problem* P) {
     }
   P->o_part = ws.take(sizeof(double) * std::max<int64_t>(tot, 1));
   P->o_e2c = ws.take(sizeof(double) * R * E2_NCLASS);
-  // Scratch of the (0,2) integrals: weighted and plain (virtual, active)
-  // factor columns and a stripe of (at|bu).  It lies over the D tables and
-  // partials, which are written only after the integrals are formed; the
-  // stripe takes what is left there (at least 8 virtuals of rows, at most
-  // the whole lower triangle) and extends the workspace only when needed.
+  // Scratch of the integrals formed as products over the factor index:
+  // weighted and plain (virtual, active) factor columns, (virtual, core) and
+  // active-pair columns, (ai|bt), (av|uw) and a stripe of (at|bu).  It lies
+  // over the D tables and partials, which are written only after the
+  // integrals are formed; the stripe holds the whole lower triangle when that
+  // takes at most 1 GiB (else what is left there, at least 8 virtuals of
+  // rows), extending the workspace as needed.
   {
     const int64_t nva = (int64_t)P->nvc * P->na;
     const size_t yb = 16 * (size_t)std::max<int64_t>(nva * Lt, 1);
@@ -558,7 +560,8 @@ e2_status build_plan(e2_problem* P) {
     const size_t full = 16 * (size_t)std::max<int64_t>(nva * nva, 1);
     const size_t least = 16 * (size_t)std::max<int64_t>((int64_t)std::min(8, P->nvc) * P->na * nva, 1);
     const size_t room = ws.top > P->o_vaX ? ws.top - P->o_vaX : 0;
-    P->va_cap = std::min(full, std::max(least, room));
+    // the whole lower triangle in one product when it takes at most 1 GiB
+    P->va_cap = std::min(full, std::max(std::max(least, room), std::min(full, size_t(1) << 30)));
     ws.top = std::max(ws.top, P->o_vaX + P->va_cap);
   }
   P->ws_bytes = ws.top;
@@ -1637,8 +1640,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
     double* part_r = (double*)(ws + P->o_part);
     auto poff = [&](int cls) { return E2 ? part_r + P->part_off[r * E2_NCLASS + cls] : nullptr; };
     auto nomark = [](int, int) {};
-    if (E2) launch_sparse_classes(P, ws, st, r, c, nomark);
     if (s == 0.0) {
+      if (E2) launch_sparse_classes(P, ws, st, r, c, nomark);
       if (g_c) cudaMemsetAsync(g_c + 2 * (size_t)r * LP.n, 0, 16 * (size_t)LP.n, st);
       if (E2) {  // no amplitudes for this root: the forward's dense classes alone
         Tabs T0 = tables(P, ws, r);
@@ -1732,7 +1735,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       dim3 grid(blocks(L.n), (unsigned)nyb, (unsigned)P->ncp);
       (k_class22_bwd<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b,
                                            P->nvb, s, g1, (double*)B(P->o_bC22p), (double*)B(P->o_bH22p),
-                                           (double*)B(P->o_bV22)), ++g_launches);
+                                           (double*)B(P->o_bV22), poff(8)), ++g_launches);
       c22 = (double*)B(P->o_bC22);
       (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bC22p), yz, L.n, 0, c22), ++g_launches);
       (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bH22p), yz, L.n, 0, hA), ++g_launches);
@@ -1769,7 +1772,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       (k_gather_t<<<grid, 256, 0, st>>>(cls, L, Lc[5], Lc[2], Lc[7], Lc[4], P->das, X.sp, X.binom, T.DT, T.DTU, T.DTD,
                                         T.DTDU, (const double2*)(ws + P->o_X01), (const double2*)(ws + P->o_X10),
                                         (const double2*)(ws + P->o_X00), X.f, X.epsh, X.E0p + r, b, s, g1, Tg, Hg,
-                                        GVg), ++g_launches);
+                                        GVg, poff(cls)), ++g_launches);
       (k_sum2<<<1, 256, 0, st>>>(Hg, GVg, (int64_t)nrow * L.n, scal), ++g_launches);
       if (cls == 1) (k_rowsum<<<blocks(nrow), 256, 0, st>>>(Hg, nrow, L.n, 1, Nx + P->ncc), ++g_launches);
       if (cls == 3) (k_rowsum<<<blocks(nrow), 256, 0, st>>>(Hg, nrow, L.n, 1, Nx), ++g_launches);

@@ -42,8 +42,6 @@ __device__ __forceinline__ double en_g(double D, double b) {
   return D * D2 * rcp_nr(fma(D2, D2, b * b));
 }
 
-__device__ __forceinline__ double en_term(double v2, double D, double b) { return v2 * en_g(D, b); }
-
 // df/dv and df/dD of f(v, D) = v g(D); g bitwise equal to en_g.
 __device__ __forceinline__ void en_derivs(double v, double D, double b, double& g, double& h) {
   if (b == 0.0) {

@@ -614,7 +614,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
           const double Dk = base - eA[col] - U1[col] - U2[col] + U3[col] + U4[col];
           const double v2 = fma(vr, vr, vi * vi);
           if (!adj.T) {
-            acc += en_term(v2, Dk, b);
+            acc = fma(v2, en_g(Dk, b), acc);  // the E2 term, same rounding in both passes
           } else {
             double gk, hk;
             en_derivs(v2 * inv_n, Dk, b, gk, hk);
@@ -625,7 +625,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
             rowp[mi][hr] += hk;
             colp[ni][hc] += hk;
             acc += hk;
-            acc2 += v2 * gk;  // = en_term(v2, Dk, b), the forward's term
+            acc2 = fma(v2, gk, acc2);  // the forward's E2 term (gk = en_g(Dk, b))
           }
         }
     }
@@ -777,11 +777,11 @@ k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* 
 #pragma unroll
       for (int y = 0; y < 8; ++y) {
         const double w = sG2[x][y];
-        if (w != 0.0) inner += en_term(w, cx - pb[y] - sGab[x][y], b);
+        if (w != 0.0) inner = fma(w, en_g(cx - pb[y] - sGab[x][y], b), inner);
       }
     }
     double2 cv = c[A];
-    acc = (cv.x * cv.x + cv.y * cv.y) * inner;
+    acc = fma(cv.x, cv.x, cv.y * cv.y) * inner;
   }
   double tot = block_sum(acc, sh);
   if (tid == 0) partial[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tot;
@@ -826,7 +826,7 @@ __global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, Dev
       V.y += s.y;
     }
     const double Dk = *E0p - L01.eA[g] - epsh[ga] - L01.U[(int64_t)(sp.ncc + a) * L01.n + g];
-    acc = en_term(V.x * V.x + V.y * V.y, Dk, b);
+    acc = fma(V.x, V.x, V.y * V.y) * en_g(Dk, b);
   }
   double tot = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
@@ -868,7 +868,7 @@ __global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, Dev
       }
     }
     const double Dk = *E0p - L10.eA[g] + epsh[gi] + L10.U[(int64_t)i * L10.n + g];
-    acc = en_term(V.x * V.x + V.y * V.y, Dk, b);
+    acc = fma(V.x, V.x, V.y * V.y) * en_g(Dk, b);
   }
   double tot = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
@@ -885,7 +885,7 @@ __global__ void k_class00(DevList L00, DevList L11, DevList L02, DevDas das, Dev
   if (g < L00.n) {
     const double2 V = active_sigma(L00.str[g], L11, L02, das, sp, binom, DTDU, DTU, X00, f);
     const double Dk = *E0p - L00.eA[g];
-    acc = en_term(V.x * V.x + V.y * V.y, Dk, b);
+    acc = fma(V.x, V.x, V.y * V.y) * en_g(Dk, b);
   }
   double tot = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[blockIdx.x] = tot;

@@ -78,14 +78,14 @@ __global__ void k_rowdot(const double2* T, const double2* d, int64_t N, double2*
 __global__ void k_fock11(const double2* rowdot, DevSpace sp, double2* Gf);
 __global__ void k_class22_bwd(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
                               const double* G, const double* E0p, double b, int nvb, double s, const double2* g1,
-                              double* cpart, double* hpart, double* vpart);
+                              double* cpart, double* hpart, double* vpart, double* part);
 __global__ void k_class22_marg(const double* vpart, int nx_blocks, int nvb, int64_t ncp, DevSpace sp, double* Nx,
                                double* scal);
 __global__ void k_gather_t(int cls, DevList Lx, DevList L12, DevList L02, DevList L21, DevList L11, DevDas das,
                            DevSpace sp, const int64_t* binom, const double2* DT, const double2* DTU, const double2* DTD,
                            const double2* DTDU, const double2* X01, const double2* X10, const double2* X00,
                            const double2* f, const double* epsh, const double* E0p, double b, double s,
-                           const double2* g1, double2* T, double* H, double* GV);
+                           const double2* g1, double2* T, double* H, double* GV, double* part);
 __global__ void k_gather_fock(int cls, DevList Lx, DevList Lsrc, DevDas das, DevSpace sp, const int64_t* binom,
                               const double2* Dsrc, const double2* T, double2* Gf);
 __global__ void k_gather_d1(int cls, DevList Lx, DevList Ltab, DevDas das, DevSpace sp, const int64_t* binom,

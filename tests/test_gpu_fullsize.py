@@ -11,6 +11,7 @@ ragged edges and at seeded interior positions of every class that has rows.
 Row and string orders are the ones that e2.h documents, rebuilt here from
 that documentation; the strings of a column tile come from e2_partials'
 column map."""
+import os
 from math import comb
 
 import numpy as np
@@ -32,6 +33,52 @@ def _pair(e):
     return e - y * (y - 1) // 2, y
 
 
+def _patterns(sizes, count):
+    """Occupation patterns (n_1..n_k), sum = count, n_s <= sizes[s], in
+    lexicographic order with n_1 most significant."""
+    if len(sizes) == 1:
+        return [(count,)] if 0 <= count <= sizes[0] else []
+    out = []
+    for k in range(0, min(sizes[0], count) + 1):
+        out += [(k,) + rest for rest in _patterns(sizes[1:], count - k)]
+    return out
+
+
+class ClassStrings:
+    """Address order of a class's strings, rebuilt from the documented
+    convention: the patterns of N+h-p electrons within two substitutions of a
+    P pattern (h + min deficit <= 2; class (0,0) without the P patterns), in
+    lexicographic order; inside a pattern a mixed radix over the subspaces,
+    subspace 1 fastest, of colex ranks."""
+
+    def __init__(self, prob, h, p):
+        sizes, lo, hi = list(prob.das_size), list(prob.das_min), list(prob.das_max)
+        ok = lambda pt: all(lo[s] <= pt[s] <= hi[s] for s in range(len(sizes)))
+        P = [q for q in _patterns(sizes, prob.n_elec) if ok(q)]
+        deficit = lambda pt: min(sum(max(0, q[s] - pt[s]) for s in range(len(sizes))) for q in P)
+        self.sizes = sizes
+        self.off = [sum(sizes[:s]) for s in range(len(sizes))]
+        self.pats, self.start = [], []
+        n = 0
+        for pt in _patterns(sizes, prob.n_elec + h - p):
+            if h + deficit(pt) > 2 or (h == 0 and p == 0 and ok(pt)):
+                continue
+            self.pats.append(pt)
+            self.start.append(n)
+            n += int(np.prod([comb(sizes[s], pt[s]) for s in range(len(sizes))]))
+        self.n = n
+
+    def __call__(self, r):
+        k = max(i for i, s in enumerate(self.start) if s <= r)
+        r -= self.start[k]
+        bits = 0
+        for s, occ in enumerate(self.pats[k]):
+            cs = comb(self.sizes[s], occ)
+            bits |= _colex_unrank(r % cs, occ) << self.off[s]
+            r //= cs
+        return bits
+
+
 def _colex_unrank(r, k):
     """Active-local bitset of the k-subset with colex rank r (sum_j C(t_j, j))."""
     bits = 0
@@ -44,13 +91,19 @@ def _colex_unrank(r, k):
     return bits
 
 
-@pytest.fixture(scope="module")
-def run():
+FULLSIZE = {"cfg2": True, "cfg3": os.environ.get("E2_FULLSIZE_DAS") == "1"}
+
+
+@pytest.fixture(scope="module", params=list(FULLSIZE))
+def run(request):
+    if not FULLSIZE[request.param]:
+        pytest.skip("the Ar-shaped DAS run (oracle reference solve of 40,608 determinants) is opt-in: "
+                    "E2_FULLSIZE_DAS=1")
     import paper_2608_11529_b300 as e2
     from paper_2608_11529_b300 import build as e2build
     from oracle import Oracle
     e2build.build()
-    prob = make_problem("cfg2")
+    prob = make_problem(request.param)
     o = Oracle(prob, use_eri_cache=False)
     c, _ = o.ground_state(1)
     E0 = o.e0()
@@ -58,11 +111,11 @@ def run():
     t = e2.device_inputs(prob, c)
     plan.forward(**t)
     torch.cuda.synchronize()
-    return prob, o, E0, plan
+    return prob, o, E0, plan, t
 
 
 # class id -> (h, p); rows decoded per e2.h's documented order
-CLASSES = {2: (0, 2), 5: (1, 2), 7: (2, 1), 4: (1, 1), 6: (2, 0), 1: (0, 1), 3: (1, 0)}
+CLASSES = {2: (0, 2), 5: (1, 2), 7: (2, 1), 4: (1, 1), 6: (2, 0), 1: (0, 1), 3: (1, 0), 0: (0, 0)}
 
 
 def _row(cls, row, cc, vc):
@@ -86,16 +139,16 @@ def _row(cls, row, cc, vc):
         return [], [vc[row]]
     if cls == 3:
         return [cc[row]], []
+    if cls == 0:
+        return [], []
     raise ValueError(cls)
 
 
-def _oracle_block(o, E0, prob, cls, rows, ranks):
-    h, p = CLASSES[cls]
-    ne = prob.n_elec + h - p
+def _oracle_block(o, E0, prob, cls, rows, ranks, lists):
     cc = [k for k in range(prob.n_core) if not prob.frozen[k]]
     vc = [v for v in range(prob.n_core + prob.n_act, prob.n) if not prob.frozen[v]]
     nh, hs, npp, ps, acts = [], [], [], [], []
-    strings = [_colex_unrank(r, ne) for r in ranks]
+    strings = [lists[cls](r) for r in ranks]
     for row in rows:
         H, Pp = _row(cls, row, cc, vc)
         for s in strings:
@@ -108,9 +161,9 @@ def _oracle_block(o, E0, prob, cls, rows, ranks):
 
 
 def test_sampled_blocks_match_the_oracle_at_full_size(run):
-    prob, o, E0, plan = run
+    prob, o, E0, plan, _ = run
     rng = np.random.default_rng(7)
-    ne_of = lambda cls: prob.n_elec + CLASSES[cls][0] - CLASSES[cls][1]
+    lists = {cls: ClassStrings(prob, *CLASSES[cls]) for cls in CLASSES}
     checked = 0
     for cls in CLASSES:
         part, rt, perm = plan.partials(0, cls)
@@ -118,9 +171,9 @@ def test_sampled_blocks_match_the_oracle_at_full_size(run):
         perm = None if perm is None else perm.cpu().numpy()
         if part.size == 0:
             continue
-        nA = comb(prob.n_act, ne_of(cls))                 # CAS: every string of ne electrons
+        nA = lists[cls].n
         if rt:                                            # dense class: 64 x 64 tiles
-            M = int(plan.q_per_class[cls] // nA)
+            M = int(round(plan.q_per_class[cls] / nA))
             ct = (nA + 63) // 64
             assert rt == (M + 63) // 64 and part.size == rt * ct
             picks = {(0, 0), (rt - 1, ct - 1), (rt - 1, 0), (0, ct - 1)}
@@ -131,7 +184,7 @@ def test_sampled_blocks_match_the_oracle_at_full_size(run):
                     ranks = range(64 * tn, min(64 * tn + 64, nA))
                 else:                                     # column tiles: the tile's strings
                     ranks = [int(x) for x in perm[64 * tn:64 * tn + 64] if x >= 0]
-                want, scale = _oracle_block(o, E0, prob, cls, rows, ranks)
+                want, scale = _oracle_block(o, E0, prob, cls, rows, ranks, lists)
                 got = part[tn * rt + tm]
                 assert abs(got - want) <= 1e-10 * scale + 1e-14, (cls, tm, tn, got, want)
                 checked += 1
@@ -141,7 +194,7 @@ def test_sampled_blocks_match_the_oracle_at_full_size(run):
             picks = {(0, 0), (nrow - 1, nb - 1), (int(rng.integers(nrow)), int(rng.integers(nb)))}
             for row, blk in sorted(picks):
                 ranks = range(256 * blk, min(256 * blk + 256, nA))
-                want, scale = _oracle_block(o, E0, prob, cls, [row], ranks)
+                want, scale = _oracle_block(o, E0, prob, cls, [row], ranks, lists)
                 got = part[row * nb + blk]
                 assert abs(got - want) <= 1e-10 * scale + 1e-14, (cls, row, blk, got, want)
                 checked += 1
