@@ -199,3 +199,39 @@ def test_sampled_blocks_match_the_oracle_at_full_size(run):
                 assert abs(got - want) <= 1e-10 * scale + 1e-14, (cls, row, blk, got, want)
                 checked += 1
     assert checked >= 20
+
+
+def _herm(rng, shape):
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    return 0.5 * (x + np.conj(np.swapaxes(x, -1, -2)))
+
+
+def test_fullsize_gradient_matches_central_differences(run):
+    """dE2/dlambda and the h-gradient of the full-size run against
+    Richardson-extrapolated central differences of the forward, and the
+    value-and-gradient pass's E2 against the forward's, bitwise."""
+    prob, _, _, plan, t = run
+    E2f = plan.forward(**t)[0].clone()
+    out = plan.value_and_grad(**t)
+    torch.cuda.synchronize()
+    assert torch.equal(out[0], E2f)
+    gh, dl = out[1].cpu().numpy(), float(out[5].cpu().numpy()[0])
+
+    def f(**kw):
+        tt = dict(t)
+        tt.update(kw)
+        return float(plan.forward(**tt)[0].cpu().numpy()[0])
+
+    def richardson(g, eps):
+        d1 = (g(eps) - g(-eps)) / (2 * eps)
+        d2 = (g(eps / 2) - g(-eps / 2)) / eps
+        return (4 * d2 - d1) / 3
+
+    num_l = richardson(lambda e: f(lam=t["lam"] + e), 1e-2)
+    assert abs(dl - num_l) <= 1e-6 * abs(num_l) + 1e-12, (dl, num_l)
+    d = _herm(np.random.default_rng(11), tuple(t["h"].shape))
+    d /= np.linalg.norm(d)
+    dd = torch.from_numpy(d).to(t["h"].device)
+    num_h = richardson(lambda e: f(h=t["h"] + e * dd), 1e-3)
+    ana_h = float(np.real(np.vdot(gh, d)))
+    assert abs(ana_h - num_h) <= 1e-6 * max(abs(num_h), 1e-3 * np.abs(gh).max()), (ana_h, num_h)
