@@ -35,12 +35,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "E2 perturber couplings/s (FP64, |ΔE2|≤1e-9 Eh); fwd+bwd vs fwd time"
 WORKLOADS = {
-    "cfg2": "Ne-shaped DCG: 2 core + CAS(8e,16) + 200 virtual spinors, 400 Coulomb + 200 Gaunt factors, 1 root",
-    "cfg1": "DC: 4 core + CAS(6e,12) + 40 virtual spinors, 60 Coulomb factors, 1 root",
-    "cfg3": "Ar-shaped DCB: 8 core + DAS 3x8 spinors (10e, N_P = 40,608) + 400 virtual spinors, 600 Coulomb + "
+    "ne_dcg": "Ne-shaped DCG: 2 core + CAS(8e,16) + 200 virtual spinors, 400 Coulomb + 200 Gaunt factors, 1 root",
+    "dc_small": "DC: 4 core + CAS(6e,12) + 40 virtual spinors, 60 Coulomb factors, 1 root",
+    "ar_dcb_das": "Ar-shaped DCB: 8 core + DAS 3x8 spinors (10e, N_P = 40,608) + 400 virtual spinors, 600 Coulomb + "
             "300 Breit factors, 1 root",
-    "cfg4": "Kr-shaped DCB: 16 core + CAS(8e,24) + 600 virtual spinors, 900 Coulomb + 450 Breit factors, 4 roots",
-    "cfg5": "Xe-shaped DCB: 46 core + CAS(8e,24) + 1000 virtual spinors, 1400 Coulomb + 700 Breit factors, 1 root",
+    "kr_dcb": "Kr-shaped DCB: 16 core + CAS(8e,24) + 600 virtual spinors, 900 Coulomb + 450 Breit factors, 4 roots",
+    "xe_dcb": "Xe-shaped DCB: 46 core + CAS(8e,24) + 1000 virtual spinors, 1400 Coulomb + 700 Breit factors, 1 root",
 }
 GEMM_CLASSES = {2: "ntp", 5: "na", 7: "na", 4: "na2p1", 6: "ntp"}
 CLASS_NAMES = ["(0,0)", "(0,1)", "(0,2)", "(1,0)", "(1,1)", "(1,2)", "(2,0)", "(2,1)", "(2,2)"]
@@ -218,6 +218,89 @@ def run_reference(args):
     return 0
 
 
+def run_batch(args):
+    """Batched evidence run: the 3 Hamiltonians x 3 frozen cutoffs of a workload
+    shape (all roots of each) in one e2_batch_forward, captured in a CUDA
+    graph and replayed, against the same jobs' e2_forward calls one after
+    another.  Prints one JSON line with "mode": "batch"."""
+    import torch
+    import paper_2608_11529_b300 as e2
+    from e2_inputs import make_problem
+    from e2_inputs.synth import CONFIGS
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    over = dict(Lc=args.factors, Lx=args.factors // 2) if args.factors else {}
+    if args.virt:
+        over["n_virt"] = args.virt
+    if args.core:
+        over["n_core"] = args.core
+    nv = over.get("n_virt", CONFIGS[args.config]["n_virt"])
+    cutoffs = [(0, 0), (2, nv // 5), (6, 2 * nv // 5)]   # none, 1s pair + 20%, more core + 40% of the virtuals
+    jobs = []
+    for ham in ("DC", "DCG", "DCB"):
+        for fc, fv in cutoffs:
+            prob = make_problem(args.config, ham=ham, n_frozen_core=fc, n_frozen_virt=fv, **over)
+            plan = e2.E2Problem.from_problem(prob)
+            t = e2.device_inputs(prob, prob.X0, device=dev)
+            c, _, _ = plan.reference_solve(t["h"], t["B_c"], t["c"], t["B_x"], t["w_x"], lam=t["lam"], tol=1e-10)
+            t["c"] = c
+            if not args.no_autotune:
+                plan.autotune(**t)
+            jobs.append((ham, fc, fv, plan, t))
+    couplings = sum(float(p.q_per_class.sum()) * p.n_roots for *_, p, _ in jobs)
+    stream = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def seq():
+        return [p.forward(**t) for *_, p, t in jobs]
+
+    for _ in range(args.warmup):
+        seq()
+    torch.cuda.synchronize()
+    a, z = ev(), ev()
+    a.record(stream)
+    for _ in range(args.steps):
+        ref = seq()
+    z.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = a.elapsed_time(z) / args.steps
+    ref = [(E2.clone(), E2c.clone()) for E2, E2c, _ in ref]
+    batch = e2.E2Batch([p for *_, p, _ in jobs])
+    batch.prepare(dev)
+    inputs = [t for *_, t in jobs]
+    for _ in range(args.warmup):
+        batch.forward(inputs)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(stream)
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            out = batch.forward(inputs)
+    stream.wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(args.steps):
+        g.replay()
+    z.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = a.elapsed_time(z) / args.steps
+    same = all(torch.equal(x[0], y[0]) and torch.equal(x[1], y[1]) for x, y in zip(ref, out))
+    line = {"mode": "batch", "metric": METRIC, "value": couplings / (ms_batch * 1e-3), "unit": "couplings/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOADS[args.config] + (f" [variant {over}]" if over else ""),
+                       "jobs": [{"ham": h, "frozen_core": fc, "frozen_virt": fv, "roots": p.n_roots,
+                                 "couplings": float(p.q_per_class.sum()) * p.n_roots} for h, fc, fv, p, _ in jobs],
+                       "couplings_per_step": couplings},
+            "sequential_ms": ms_seq, "sequential_couplings_per_s": couplings / (ms_seq * 1e-3),
+            "graph_replay": True, "bitwise_equal_to_sequential": same,
+            "gpu_launches": sum(p.launch_count() for *_, p, _ in jobs)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run(args):
     import torch
     import torch.distributed as dist
@@ -231,6 +314,8 @@ def run(args):
     over = dict(Lc=args.factors, Lx=args.factors // 2) if args.factors else {}
     if args.virt:
         over["n_virt"] = args.virt
+    if args.core:
+        over["n_core"] = args.core
     prob = make_problem(args.config, **over)
     plan = e2.E2Problem.from_problem(prob)
     couplings = float(plan.q_per_class.sum()) * plan.n_roots
@@ -243,7 +328,7 @@ def run(args):
     # column tiles: time plain against compacted per class once, keep the faster
     tune = plan.autotune(**t) if not args.no_autotune else {}
     col_tiles = {}
-    for k in (2, 4, 6):
+    for k in (2, 4, 5, 6):
         tiles, krows, used = plan.class_tiles(k)
         if tiles:
             col_tiles[CLASS_NAMES[k]] = {"used": used, "compacted_share": krows / (tiles * _kpad(prob, k)),
@@ -398,15 +483,19 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--config", default="cfg2", choices=sorted(WORKLOADS),
-                    help="cfg2 is the benchmark workload; the others run as evidence / profiling variants")
+    ap.add_argument("--config", default="ne_dcg", choices=sorted(WORKLOADS),
+                    help="ne_dcg is the benchmark workload; the others run as evidence / profiling variants")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default column tiles")
+    ap.add_argument("--batch", action="store_true",
+                    help="evidence run: the 3 Hamiltonians x 3 frozen cutoffs of --config batched in one "
+                         "graph-captured launch against sequential forwards")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="oracle work per cpu_baseline sample (the sample is sized to about this long)")
     ap.add_argument("--ref-seconds", type=float, default=6.0)
+    ap.add_argument("--core", type=int, default=0, help="override the core spinor count (slices)")
     ap.add_argument("--virt", type=int, default=0,
                     help="override the virtual spinor count: a smaller variant with the same tile shapes, for "
                          "profiler captures of the backward (its workspace scales with the virtual pairs)")
@@ -418,6 +507,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        return run_batch(args)
     return run(args)
 
 

@@ -192,20 +192,20 @@ def tiny_problem(n_core, n_act, n_virt, n_elec, *, Lc=6, Lx=0, ham="DC", x_scale
 # The five workload shapes (Ne- to Xe-shaped).  Sizes are spinors.
 CONFIGS = {
     # plain DC, CAS(6e,12), 924 reference determinants
-    "cfg1": dict(n_core=4, n_act=12, n_virt=40, n_elec=6, Lc=60, Lx=0, ham="DC",
+    "dc_small": dict(n_core=4, n_act=12, n_virt=40, n_elec=6, Lc=60, Lx=0, ham="DC",
                  core_ends=(-20.0, -2.0), virt_ends=(0.1, 50.0), seed=1),
     # Ne-shaped DCG, CAS(8e,16), 12870 reference determinants
-    "cfg2": dict(n_core=2, n_act=16, n_virt=200, n_elec=8, Lc=400, Lx=200, ham="DCG", x_scale=1e-3,
+    "ne_dcg": dict(n_core=2, n_act=16, n_virt=200, n_elec=8, Lc=400, Lx=200, ham="DCG", x_scale=1e-3,
                  core_ends=(-33.0, -33.0), virt_ends=(0.2, 200.0), seed=2),
     # Ar-shaped DCB with three active subspaces of 8 (RAS-like 8/2/0 nominal)
-    "cfg3": dict(n_core=8, n_act=24, n_virt=400, n_elec=10, Lc=600, Lx=300, ham="DCB", x_scale=2e-3,
+    "ar_dcb_das": dict(n_core=8, n_act=24, n_virt=400, n_elec=10, Lc=600, Lx=300, ham="DCB", x_scale=2e-3,
                  das_size=[8, 8, 8], das_min=[6, 0, 0], das_max=[8, 8, 2],
                  core_ends=(-119.0, -9.5), virt_ends=(0.1, 200.0), seed=3),
     # Kr-shaped, CAS(8e,24), 4 roots; the batch varies Hamiltonian and frozen cutoffs
-    "cfg4": dict(n_core=16, n_act=24, n_virt=600, n_elec=8, Lc=900, Lx=450, ham="DCB", x_scale=3e-3,
+    "kr_dcb": dict(n_core=16, n_act=24, n_virt=600, n_elec=8, Lc=900, Lx=450, ham="DCB", x_scale=3e-3,
                  core_ends=(-520.0, -3.0), virt_ends=(0.1, 400.0), n_roots=4, seed=4),
     # Xe-shaped, CAS(8e,24), DCB
-    "cfg5": dict(n_core=46, n_act=24, n_virt=1000, n_elec=8, Lc=1400, Lx=700, ham="DCB", x_scale=4e-3,
+    "xe_dcb": dict(n_core=46, n_act=24, n_virt=1000, n_elec=8, Lc=1400, Lx=700, ham="DCB", x_scale=4e-3,
                  core_ends=(-1280.0, -2.5), virt_ends=(0.1, 800.0), seed=5),
 }
 

@@ -191,28 +191,30 @@ k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_
 // Gamma_D of a column-tiled class in compacted form (tile j = blockIdx.y,
 // 80 compacted rows per blockIdx.x, K segment blockIdx.z):
 //   GDc[(koff + k) * 64 + c] (+)= sum_e conj(T[e][perm[64 j + c]]) W[e][klist[koff + k]]
+// (T itself instead of conj(T) when conjT == 0: shifted amplitudes arrive conjugated)
 // over the chunk's rows e, as the 64 x klen product of the tile's strings
 // with its compacted rows; same split-K segments as the plain product.
 constexpr int kTileRows = 80;
 __global__ void __launch_bounds__(256, 1)
 k_zgemm_gd_tiles(ColTiles ctl, const double2* __restrict__ W, int Kp, const double2* __restrict__ T, int64_t N,
-                 int64_t Mc, double2* __restrict__ GDc, int beta, int64_t kseg, int64_t czs) {
+                 int64_t Mc, double2* __restrict__ GDc, int beta, int64_t kseg, int64_t czs, int conjT) {
   const int j = blockIdx.y;
   const int4 td = ctl.tdesc[j];
   if ((int64_t)blockIdx.x * kTileRows >= td.y) return;
-  zgemm_body<64, kTileRows, 4>(64, td.y, Mc, T, 1, N, 1, W, Kp, 1, 0, GDc + (int64_t)td.x * 64, 1, 64, beta, kseg, czs,
+  zgemm_body<64, kTileRows, 4>(64, td.y, Mc, T, 1, N, conjT, W, Kp, 1, 0, GDc + (int64_t)td.x * 64, 1, 64, beta, kseg, czs,
                                -1, 0, blockIdx.x, blockIdx.z, ctl.perm + (int64_t)j * 64, nullptr, ctl.klist + td.x);
 }
 
 // Gamma_W of a column-tiled class in compacted form (tile j = blockIdx.z):
 //   GWc[e * krows + koff + k] = sum_c conj(T[e][perm[64 j + c]]) Dc[(koff + k) * 64 + c]
+// (T itself when conjT == 0)
 __global__ void __launch_bounds__(256, 1)
 k_zgemm_gw_tiles(ColTiles ctl, const double2* __restrict__ T, int64_t N, int64_t Mc, int64_t krows,
-                 double2* __restrict__ GWc) {
+                 double2* __restrict__ GWc, int conjT) {
   const int j = blockIdx.z;
   const int4 td = ctl.tdesc[j];
   if ((int64_t)blockIdx.y * kTileRows >= td.y) return;
-  zgemm_body<64, kTileRows, 4>(Mc, td.y, 64, T, N, 1, 1, ctl.Dc + (int64_t)td.x * 64, 1, 64, 0, GWc + td.x, krows, 1,
+  zgemm_body<64, kTileRows, 4>(Mc, td.y, 64, T, N, 1, conjT, ctl.Dc + (int64_t)td.x * 64, 1, 64, 0, GWc + td.x, krows, 1,
                                0, 64, 0, -1, blockIdx.x, blockIdx.y, 0, nullptr, ctl.perm + (int64_t)j * 64, nullptr);
 }
 
@@ -231,14 +233,16 @@ __global__ void k_gd_scatter(ColTiles ctl, const double2* __restrict__ GDc, int6
   }
 }
 
-// GW[e][x] = sum_j GWc[e * krows + koff_j + pos[j][x]] over the tiles j whose
-// compacted rows include x (pos[j][x] >= 0), in tile order
+// GW[e * ldo + x] = sum_j GWc[e * krows + koff_j + pos[j][x]], x < nxo, over
+// the tiles j whose compacted rows include x (pos[j][x] >= 0, pos rows Kp
+// wide), in tile order
 __global__ void k_gw_reduce(const int4* __restrict__ tdesc, const int32_t* __restrict__ pos, int64_t tiles, int Kp,
-                            const double2* __restrict__ GWc, int64_t krows, int64_t Mc, double2* __restrict__ GW) {
+                            const double2* __restrict__ GWc, int64_t krows, int64_t Mc, double2* __restrict__ GW,
+                            int nxo, int64_t ldo) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= Mc * Kp) return;
-  const int64_t e = idx / Kp;
-  const int x = (int)(idx % Kp);
+  if (idx >= Mc * nxo) return;
+  const int64_t e = idx / nxo;
+  const int x = (int)(idx % nxo);
   double2 s = make_double2(0.0, 0.0);
   const double2* row = GWc + e * krows;
   for (int64_t j = 0; j < tiles; ++j) {
@@ -248,7 +252,7 @@ __global__ void k_gw_reduce(const int4* __restrict__ tdesc, const int32_t* __res
     s.x += v.x;
     s.y += v.y;
   }
-  GW[idx] = s;
+  GW[e * ldo + x] = s;
 }
 
 // C(m,n) = beta C(m,n) + sum_z part[z*ps + m*N + n] in z order (segments of a

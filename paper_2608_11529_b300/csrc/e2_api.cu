@@ -47,6 +47,7 @@ struct ColPlan {
   std::vector<int32_t> pos;    // [tiles][Kp] compacted row of table row x in tile j, -1 if absent
   int64_t tiles = 0, krows = 0;
   int maxklen = 0;             // longest compacted contraction of a tile
+  int gran = 8;                // contraction granularity of the tiles (4: a k = 4 tail step)
   int64_t gd_ctas = 0;         // sum over tiles of ceil(klen / 64)
   double ratio = 1.0;          // krows / (tiles * Kp): share of the dense contraction
   size_t o_perm = 0, o_tdesc = 0, o_klist = 0, o_pos = 0, o_Dc = 0;  // o_Dc: per-root D region
@@ -120,7 +121,7 @@ struct e2_problem {
   size_t o_bGX01, o_bGX10, o_bGX00, o_bR22, o_bHs22, o_bP22, o_bG22c, o_bGg22, o_bCs, o_bGB, o_bFtr, o_bGw, o_bRg;
   size_t o_bPart, bpart_bytes;  // split-K segments
   size_t tsh_bytes;
-  size_t o_bGDc, o_bGWc;
+  size_t o_bGDc, o_bGWc, gwc_bytes;
   size_t bwd_bytes;
   // compacted column tiles of the dense classes and whether each class uses them
   ColPlan cplan[E2_NCLASS];
@@ -255,9 +256,10 @@ bool table_nonzero(int fam, int na, uint64_t A, int x) {
 // 3-spinor set (occupied spinors for tables that need empty ones, empty
 // spinors for those that need occupied ones), 64 to a tile, each tile keeping
 // the table rows that are non-zero for some of its strings.
-void build_colplan(e2_problem* P, int cls, int fam, int kvalid) {
+void build_colplan(e2_problem* P, int cls, int fam, int kvalid, int fs = 3, int gran = 8) {
   ColPlan& cp = P->cplan[cls];
   cp = ColPlan{};
+  cp.gran = gran;
   const int li = P->list_of[cls];
   if (li < 0 || P->M[cls] == 0) return;
   const HostList& L = P->lists[li];
@@ -269,25 +271,31 @@ void build_colplan(e2_problem* P, int cls, int fam, int kvalid) {
   const int nkey = by_occ ? L.count : na - L.count;
   std::vector<int32_t> order;
   order.reserve((size_t)nS);
-  if (nkey < 3 || na < 3) {
+  if (nkey < fs || na < fs) {
     for (int64_t s = 0; s < nS; ++s) order.push_back((int32_t)s);
   } else {
-    const int nsub = (int)binom_h(nkey, 3);
-    const int64_t nF = binom_h(na, 3);
+    const int nsub = (int)binom_h(nkey, fs);
+    const int64_t nF = binom_h(na, fs);
     std::vector<int32_t> fid((size_t)nS * nsub);
     std::vector<int64_t> fcnt((size_t)nF, 0);
     for (int64_t s = 0; s < nS; ++s) {
       const uint64_t key = by_occ ? S[s] : (~S[s] & full);
       int bits[64], nb = 0;
       for (uint64_t x = key; x; x &= x - 1) bits[nb++] = __builtin_ctzll(x);
-      int q = 0;
-      for (int i = 0; i < nb; ++i)
-        for (int j = i + 1; j < nb; ++j)
-          for (int k = j + 1; k < nb; ++k) {
-            const int f = (int)(binom_h(bits[i], 1) + binom_h(bits[j], 2) + binom_h(bits[k], 3));
-            fid[(size_t)s * nsub + q++] = f;
-            ++fcnt[f];
-          }
+      // every fs-subset of the key spinors, by colex rank
+      int q = 0, idx[8];
+      for (int i = 0; i < fs; ++i) idx[i] = i;
+      for (;;) {
+        int64_t f = 0;
+        for (int i = 0; i < fs; ++i) f += binom_h(bits[idx[i]], i + 1);
+        fid[(size_t)s * nsub + q++] = (int32_t)f;
+        ++fcnt[f];
+        int i = fs - 1;
+        while (i >= 0 && idx[i] == nb - fs + i) --i;
+        if (i < 0) break;
+        ++idx[i];
+        for (int j = i + 1; j < fs; ++j) idx[j] = idx[j - 1] + 1;
+      }
     }
     std::vector<int64_t> boff((size_t)nF + 1, 0);
     for (int64_t f = 0; f < nF; ++f) boff[f + 1] = boff[f] + fcnt[f];
@@ -350,7 +358,7 @@ void build_colplan(e2_problem* P, int cls, int fam, int kvalid) {
         cp.klist.push_back(x);
         ++ktrue;
       }
-    const int klen = std::max(8, (ktrue + 7) / 8 * 8);
+    const int klen = std::max(gran, (ktrue + gran - 1) / gran * gran);
     for (int x = ktrue; x < klen; ++x) cp.klist.push_back(0);
     cp.tdesc.insert(cp.tdesc.end(), {koff, klen, ktrue, 0});
     cp.maxklen = std::max(cp.maxklen, klen);
@@ -443,6 +451,9 @@ e2_status build_plan(e2_problem* P) {
   build_colplan(P, 2, FAM_TU, P->ntp);
   build_colplan(P, 6, FAM_TDUD, P->ntp);
   build_colplan(P, 4, FAM_TDU, 1 + P->na * P->na);
+  // D^t (class (1,2)): strings sharing four occupied spinors leave at most
+  // n_act - 4 non-zero rows; a k = 4 tail step turns that into work saved
+  build_colplan(P, 5, FAM_T, P->na, 4, 4);
   for (int c = 0; c < E2_NCLASS; ++c) P->use_cols[c] = P->cplan[c].built && P->cplan[c].ratio < 0.85;
 
   // ---- workspace layout
@@ -612,6 +623,7 @@ e2_status build_plan(e2_problem* P) {
     P->o_bT = ws.take(tmax);
     P->o_bGDc = ws.take(gdc);  // compacted Gamma_D / Gamma_W of a column-tiled class
     P->o_bGWc = ws.take(gwc);
+    P->gwc_bytes = gwc;
     P->o_bHrow = ws.take(hrow);
     P->o_bHcol = ws.take(hcol);
     P->o_bScalT = ws.take(scalt);
@@ -1039,17 +1051,17 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
 // Gamma_D of a column-tiled class in compacted form, GDc (+)= per tile
 // W[:, klist]^T conj(T[:, perm]) over the chunk's Mc rows, split-K as zgemm.
 void zgemm_gd_tiles(cudaStream_t st, const ColPlan& cp, const ColTiles& ctl, const double2* W, int Kp,
-                    const double2* T, int64_t N, int64_t Mc, double2* GDc, int beta) {
+                    const double2* T, int64_t N, int64_t Mc, double2* GDc, int beta, int conjT = 1) {
   const int64_t czs = cp.krows * 64;
   const int nseg = splitk_segments(cp.gd_ctas, Mc, 16 * (size_t)czs);
   const int64_t kseg = (Mc + nseg - 1) / nseg;
   dim3 grid((unsigned)((cp.maxklen + 79) / 80), (unsigned)cp.tiles, (unsigned)nseg);
   if (nseg == 1) {
-    (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, GDc, beta, kseg, 0), ++g_launches);
+    (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, GDc, beta, kseg, 0, conjT), ++g_launches);
     return;
   }
   double2* part = (double2*)g_splitk;
-  (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, part, 0, kseg, czs), ++g_launches);
+  (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, part, 0, kseg, czs, conjT), ++g_launches);
   (k_zacc<<<blocks(czs), 256, 0, st>>>(part, nseg, czs, cp.krows, 64, GDc, 64, 1, beta), ++g_launches);
 }
 
@@ -1676,7 +1688,10 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       const int64_t M = P->M[cls], N = L.n, Kp = P->Kp[cls];
       const int64_t rt = (M + 63) / 64, ct = (N + 63) / 64;
       const double2* W = (const double2*)(ws + P->o_W[cls]);
-      const bool tiled = P->use_cols[cls];
+      // the class kernel reads the column tiles whenever the class uses them;
+      // the Gamma products do so for the 8-granular plans (a 16-row table
+      // gains nothing at the products' 8-wide output granularity)
+      const bool tiled = P->use_cols[cls] && P->cplan[cls].gran == 8;
       const ColPlan& cp = P->cplan[cls];
       const ColTiles ctl = col_tiles(P, ws, r, cls);
       for (int64_t m0 = 0; m0 < M; m0 += P->chunk_rows[cls]) {
@@ -1699,10 +1714,11 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           double2* GW = (double2*)B(P->o_bGW[cls]) + m0 * Kp;
           if (tiled) {  // per tile over its compacted rows, then summed per table row in tile order
             dim3 g((unsigned)((Mc + 63) / 64), (unsigned)((cp.maxklen + 79) / 80), (unsigned)cp.tiles);
-            (k_zgemm_gw_tiles<<<g, 256, 0, st>>>(ctl, adj.T, N, Mc, cp.krows, (double2*)B(P->o_bGWc)), ++g_launches);
-            (k_gw_reduce<<<blocks(Mc * Kp), 256, 0, st>>>(ctl.tdesc, (const int32_t*)(ws + cp.o_pos), cp.tiles,
-                                                         (int)Kp, (const double2*)B(P->o_bGWc), cp.krows, Mc, GW),
+            (k_zgemm_gw_tiles<<<g, 256, 0, st>>>(ctl, adj.T, N, Mc, cp.krows, (double2*)B(P->o_bGWc), 1),
              ++g_launches);
+            (k_gw_reduce<<<blocks(Mc * Kp), 256, 0, st>>>(ctl.tdesc, (const int32_t*)(ws + cp.o_pos), cp.tiles,
+                                                         (int)Kp, (const double2*)B(P->o_bGWc), cp.krows, Mc, GW,
+                                                         (int)Kp, Kp), ++g_launches);
           } else {
             zgemm(st, Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0, GW, Kp, 1, 0, Kp >= 64 ? 64 : 16);
           }
@@ -1805,27 +1821,53 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       const int ntp = P->ntp;
       // Gamma_D[x][B] += sum_(row,s) X[row][s][x] Tsh[(row,s)][B] and
       // Gamma_X[row][s][x] = sum_B Tsh[(row,s)][B] D[x][B], rows in chunks that fit Tsh
+      // With the (0,2) list's column tiles in use, the products that meet
+      // D^{tu} run over the tiles' compacted rows (tcls = 2).
       auto shifted = [&](const DevList& Ltab, int S, int pairs_mode, int nx_, const double2* Xint, const double2* D,
-                         double2* GD, double2* GX, int gx_beta, int bn) {
+                         double2* GD, double2* GX, int gx_beta, int bn, int tcls) {
         const int64_t nb = Ltab.n;
         if (nb == 0 || S == 0) return;
-        const int rc = (int)std::max<int64_t>(1, std::min<int64_t>(nrow, (int64_t)(P->tsh_bytes / (16 * (size_t)S * nb))));
+        const bool tl = tcls >= 0 && P->use_cols[tcls];
+        const ColPlan& cpt = P->cplan[tcls >= 0 ? tcls : 0];
+        const ColTiles ctt = tl ? col_tiles(P, ws, r, tcls) : ColTiles{nullptr, nullptr, nullptr, nullptr};
+        int64_t rcap = (int64_t)(P->tsh_bytes / (16 * (size_t)S * nb));
+        if (tl && want_B) rcap = std::min<int64_t>(rcap, (int64_t)(P->gwc_bytes / (16 * (size_t)S * cpt.krows)));
+        const int rc = (int)std::max<int64_t>(1, std::min<int64_t>(nrow, rcap));
         for (int r0 = 0; r0 < nrow; r0 += rc) {
           const int nr = std::min(rc, nrow - r0);
           (k_tshift<<<dim3(blocks(nb), nr, S), 256, 0, st>>>(L, Ltab, P->das, X.binom, Tg, r0, pairs_mode, Tsh),
            ++g_launches);
           const int64_t k = (int64_t)nr * S;
-          zgemm(st, nx_, nb, k, Xint + (int64_t)r0 * S * nx_, 1, nx_, 0, Tsh, nb, 1, 0, GD, nb, 1, 1);
-          if (want_B)
-            zgemm(st, k, nx_, nb, Tsh, nb, 1, 0, D, 1, nb, 0, GX + (int64_t)r0 * S * nx_, nx_, 1, gx_beta, bn);
+          const double2* Xr = Xint + (int64_t)r0 * S * nx_;
+          if (tl)
+            zgemm_gd_tiles(st, cpt, ctt, Xr, nx_, Tsh, nb, k, (double2*)B(P->o_bGDc), r0 > 0, 0);
+          else
+            zgemm(st, nx_, nb, k, Xr, 1, nx_, 0, Tsh, nb, 1, 0, GD, nb, 1, 1);
+          if (want_B) {
+            double2* GXr = GX + (int64_t)r0 * S * nx_;
+            if (tl) {
+              dim3 g((unsigned)((k + 63) / 64), (unsigned)((cpt.maxklen + 79) / 80), (unsigned)cpt.tiles);
+              (k_zgemm_gw_tiles<<<g, 256, 0, st>>>(ctt, Tsh, nb, k, cpt.krows, (double2*)B(P->o_bGWc), 0),
+               ++g_launches);
+              // written, not accumulated: gx_beta is set only for class (0,0),
+              // one row, whose target is still zero here
+              (k_gw_reduce<<<blocks(k * nx_), 256, 0, st>>>(ctt.tdesc, (const int32_t*)(ws + cpt.o_pos), cpt.tiles,
+                                                           P->Kp[tcls], (const double2*)B(P->o_bGWc), cpt.krows, k,
+                                                           GXr, nx_, nx_), ++g_launches);
+            } else {
+              zgemm(st, k, nx_, nb, Tsh, nb, 1, 0, D, 1, nb, 0, GXr, nx_, 1, gx_beta, bn);
+            }
+          }
         }
+        if (tl)
+          (k_gd_scatter<<<(unsigned)cpt.tiles, 256, 0, st>>>(ctt, (const double2*)B(P->o_bGDc), nb, GD), ++g_launches);
       };
       if (cls == 1)
-        shifted(Lc[2], na, 0, ntp, (const double2*)(ws + P->o_X01), T.DTU, GT.DTU, (double2*)B(P->o_bGX01), 0, 64);
+        shifted(Lc[2], na, 0, ntp, (const double2*)(ws + P->o_X01), T.DTU, GT.DTU, (double2*)B(P->o_bGX01), 0, 64, 2);
       if (cls == 3)
-        shifted(Lc[5], ntp, 1, na, (const double2*)(ws + P->o_X10), T.DT, GT.DT, (double2*)B(P->o_bGX10), 0, 16);
+        shifted(Lc[5], ntp, 1, na, (const double2*)(ws + P->o_X10), T.DT, GT.DT, (double2*)B(P->o_bGX10), 0, 16, -1);
       if (cls == 0)
-        shifted(Lc[2], ntp, 1, ntp, (const double2*)(ws + P->o_X00), T.DTU, GT.DTU, (double2*)B(P->o_bGX00), 1, 64);
+        shifted(Lc[2], ntp, 1, ntp, (const double2*)(ws + P->o_X00), T.DTU, GT.DTU, (double2*)B(P->o_bGX00), 1, 64, 2);
       if (want_B && cls == 1 && Lc[2].n > 0)
         (k_gint<<<blocks((int64_t)nrow * na * ntp), 256, 0, st>>>(INT_X01, X.sp, (const double2*)B(P->o_bGX01), nrow,
                                                                  na * ntp, na * ntp, Gt, npair), ++g_launches);

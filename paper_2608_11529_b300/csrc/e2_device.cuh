@@ -201,6 +201,14 @@ __device__ __forceinline__ void mma_f64(double (&c)[4], const double (&a)[4], co
       : "d"(a[0]), "d"(a[1]), "d"(a[2]), "d"(a[3]), "d"(b[0]), "d"(b[1]));
 }
 
+// D (16x8) += A (16x4, row) * B (4x8, col) in FP64: a[0] = A[g][tq],
+// a[1] = A[g+8][tq], b = B[tq][g] (g = lane / 4, tq = lane % 4); C as for k = 8.
+__device__ __forceinline__ void mma_f64_k4(double (&c)[4], const double (&a)[2], double b) {
+  asm volatile("mma.sync.aligned.m16n8k4.row.col.f64.f64.f64.f64 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+               : "+d"(c[0]), "+d"(c[1]), "+d"(c[2]), "+d"(c[3])
+               : "d"(a[0]), "d"(a[1]), "d"(b));
+}
+
 // <A| H - E_O |Psi> for an n_elec-electron string A with no core hole or
 // virtual particle: sum_{tu} f_tu D^{t+u}_A + sum_{t<u in A} s(A;t,u)
 // sum_{v<w} <tu||vw> D^{vw}_{A-t-u}.  Class (0,0) evaluates it on strings of

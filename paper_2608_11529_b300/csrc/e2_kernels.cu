@@ -532,12 +532,13 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
   __syncthreads();
   auto wcol = [&](int k) { return sparse ? sK[k - kw0] : k; };
   const bool colok = dcol0 + dc < N || sparse;
+  // rows past klen (a k = 4 tail of a compacted tile) read zero
   auto ldW = [&](int k0, int q) {
     const int64_t gr = m0 + wr_ + 32 * q;
-    return (gr < M) ? W[gr * Kp + wcol(k0 + wk)] : zero;
+    return (gr < M && k0 + wk < klen) ? W[gr * Kp + wcol(k0 + wk)] : zero;
   };
   auto ldD = [&](int k0, int q) {
-    return colok ? D[(int64_t)(k0 + dk + 4 * q) * ldd + dcol0 + dc] : zero;
+    return (colok && k0 + dk + 4 * q < klen) ? D[(int64_t)(k0 + dk + 4 * q) * ldd + dcol0 + dc] : zero;
   };
   double2 pw0 = ldW(0, 0), pw1 = ldW(0, 1), pd0 = ldD(0, 0), pd1 = ldD(0, 1);
 
@@ -566,19 +567,36 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
       bi[ni][0] = sDi[tq][cb]; bi[ni][1] = sDi[tq + 4][cb];
       bs[ni][0] = sDs[tq][cb]; bs[ni][1] = sDs[tq + 4][cb];
     }
+    if (k0 + GBK <= klen) {
 #pragma unroll
-    for (int mi = 0; mi < 2; ++mi) {
-      const int r0 = wm * 32 + mi * 16 + g;
-      double a[4];
-      a[0] = sWr[r0][tq]; a[1] = sWr[r0 + 8][tq]; a[2] = sWr[r0][tq + 4]; a[3] = sWr[r0 + 8][tq + 4];
+      for (int mi = 0; mi < 2; ++mi) {
+        const int r0 = wm * 32 + mi * 16 + g;
+        double a[4];
+        a[0] = sWr[r0][tq]; a[1] = sWr[r0 + 8][tq]; a[2] = sWr[r0][tq + 4]; a[3] = sWr[r0 + 8][tq + 4];
 #pragma unroll
-      for (int ni = 0; ni < 2; ++ni) mma_f64(t1[mi][ni], a, br[ni]);
-      a[0] = sWi[r0][tq]; a[1] = sWi[r0 + 8][tq]; a[2] = sWi[r0][tq + 4]; a[3] = sWi[r0 + 8][tq + 4];
+        for (int ni = 0; ni < 2; ++ni) mma_f64(t1[mi][ni], a, br[ni]);
+        a[0] = sWi[r0][tq]; a[1] = sWi[r0 + 8][tq]; a[2] = sWi[r0][tq + 4]; a[3] = sWi[r0 + 8][tq + 4];
 #pragma unroll
-      for (int ni = 0; ni < 2; ++ni) mma_f64(t2[mi][ni], a, bi[ni]);
-      a[0] = sWs[r0][tq]; a[1] = sWs[r0 + 8][tq]; a[2] = sWs[r0][tq + 4]; a[3] = sWs[r0 + 8][tq + 4];
+        for (int ni = 0; ni < 2; ++ni) mma_f64(t2[mi][ni], a, bi[ni]);
+        a[0] = sWs[r0][tq]; a[1] = sWs[r0 + 8][tq]; a[2] = sWs[r0][tq + 4]; a[3] = sWs[r0 + 8][tq + 4];
 #pragma unroll
-      for (int ni = 0; ni < 2; ++ni) mma_f64(t3[mi][ni], a, bs[ni]);
+        for (int ni = 0; ni < 2; ++ni) mma_f64(t3[mi][ni], a, bs[ni]);
+      }
+    } else {  // k = 4 tail: the first four staged rows (m16n8k4 fragments)
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int r0 = wm * 32 + mi * 16 + g;
+        double a[2];
+        a[0] = sWr[r0][tq]; a[1] = sWr[r0 + 8][tq];
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) mma_f64_k4(t1[mi][ni], a, br[ni][0]);
+        a[0] = sWi[r0][tq]; a[1] = sWi[r0 + 8][tq];
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) mma_f64_k4(t2[mi][ni], a, bi[ni][0]);
+        a[0] = sWs[r0][tq]; a[1] = sWs[r0 + 8][tq];
+#pragma unroll
+        for (int ni = 0; ni < 2; ++ni) mma_f64_k4(t3[mi][ni], a, bs[ni][0]);
+      }
     }
     __syncthreads();
   }

@@ -62,11 +62,12 @@ __global__ void k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* A, int
                           const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn,
                           int beta, int64_t kseg, int64_t czs, int64_t lower);
 __global__ void k_zgemm_gd_tiles(ColTiles ctl, const double2* W, int Kp, const double2* T, int64_t N, int64_t Mc,
-                                 double2* GDc, int beta, int64_t kseg, int64_t czs);
-__global__ void k_zgemm_gw_tiles(ColTiles ctl, const double2* T, int64_t N, int64_t Mc, int64_t krows, double2* GWc);
+                                 double2* GDc, int beta, int64_t kseg, int64_t czs, int conjT);
+__global__ void k_zgemm_gw_tiles(ColTiles ctl, const double2* T, int64_t N, int64_t Mc, int64_t krows, double2* GWc,
+                                 int conjT);
 __global__ void k_gd_scatter(ColTiles ctl, const double2* GDc, int64_t N, double2* GD);
 __global__ void k_gw_reduce(const int4* tdesc, const int32_t* pos, int64_t tiles, int Kp, const double2* GWc,
-                            int64_t krows, int64_t Mc, double2* GW);
+                            int64_t krows, int64_t Mc, double2* GW, int nxo, int64_t ldo);
 __global__ void k_zacc(const double2* part, int nseg, int64_t ps, int64_t M, int64_t N, double2* C, int64_t csm,
                        int64_t csn, int beta);
 __global__ void k_rowsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);

@@ -75,7 +75,7 @@ def test_plan_sizes_match_oracle_counts(case):
 
 def test_plan_sizes_of_the_workload_shapes():
     """|Q| per root of the Ne- and Ar-shaped workloads (no arrays needed)."""
-    for name, q in [("cfg1", 7557198), ("cfg2", 880539088)]:
+    for name, q in [("dc_small", 7557198), ("ne_dcg", 880539088)]:
         kw = dict(make_problem.__globals__["CONFIGS"][name])
         p = e2.E2Problem(kw["n_core"], kw["n_act"], kw["n_virt"], kw["n_elec"], ham=kw["ham"],
                          L_coulomb=kw["Lc"], L_extra=kw["Lx"] if kw["ham"] != "DC" else 0)

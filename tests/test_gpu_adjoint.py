@@ -88,7 +88,7 @@ def test_adjoint_with_column_tiles_matches_oracle(name):
     seed = np.array([1.0, -0.6][:prob.n_roots])
     gh_o, gB_o, _, gc_o = o.grad(seed=seed)
     plan = e2.E2Problem.from_problem(prob)
-    on = [cls for cls in (2, 4, 6) if plan.class_tiles(cls)[0]]
+    on = [cls for cls in (2, 4, 5, 6) if plan.class_tiles(cls)[0]]
     assert on
     for cls in on:
         plan.set_class_tiles(cls, True)

@@ -35,7 +35,7 @@ def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph(col_tile
     jobs = _jobs()
     plans = [e2.E2Problem.from_problem(p) for p, _, _ in jobs]
     for plan in plans:                             # plain columns, or compacted tiles where a plan exists
-        for cls in (2, 4, 6):
+        for cls in (2, 4, 5, 6):
             if plan.class_tiles(cls)[0]:
                 plan.set_class_tiles(cls, col_tiles)
     inputs = [e2.device_inputs(p, c) for p, _, c in jobs]

@@ -91,7 +91,7 @@ def _colex_unrank(r, k):
     return bits
 
 
-FULLSIZE = {"cfg2": True, "cfg3": os.environ.get("E2_FULLSIZE_DAS") == "1"}
+FULLSIZE = {"ne_dcg": True, "ar_dcb_das": os.environ.get("E2_FULLSIZE_DAS") == "1"}
 
 
 @pytest.fixture(scope="module", params=list(FULLSIZE))

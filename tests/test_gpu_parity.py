@@ -24,7 +24,7 @@ def _gpu_e2(prob, c, class_mask=0x1FF, lam=None, col_tiles=None):
     e2build.build()
     plan = e2.E2Problem.from_problem(prob, class_mask=class_mask, n_roots=c.shape[0])
     if col_tiles is not None:                      # force compacted (True) or plain (False) columns
-        for cls in (2, 4, 6):
+        for cls in (2, 4, 5, 6):
             if plan.class_tiles(cls)[0]:
                 plan.set_class_tiles(cls, col_tiles)
     t = e2.device_inputs(prob, c)
@@ -45,7 +45,7 @@ def _oracle(prob, n_roots=None):
 
 CASES = {
     # Ne-shaped small workload: every dense class spans several 64-wide tiles with ragged tails
-    "cfg1": lambda: make_problem("cfg1"),
+    "dc_small": lambda: make_problem("dc_small"),
     "dcb_two_roots_frozen": lambda: tiny_problem(6, 8, 14, 4, Lc=6, Lx=4, ham="DCB", x_scale=0.05, n_roots=2,
                                                  n_frozen_core=2, n_frozen_virt=3, seed=21),
     "dcg_odd_electrons": lambda: tiny_problem(4, 10, 12, 5, Lc=5, Lx=3, ham="DCG", x_scale=0.05, seed=22),
@@ -69,7 +69,7 @@ def test_e2_matches_oracle(name):
     np.testing.assert_allclose(g2, e2, rtol=0, atol=TOL_E2)
 
 
-@pytest.mark.parametrize("name", ["cfg1", "dcb_two_roots_frozen", "das_three_subspaces", "level_shift",
+@pytest.mark.parametrize("name", ["dc_small", "dcb_two_roots_frozen", "das_three_subspaces", "level_shift",
                                   "full_active"])
 @pytest.mark.parametrize("col_tiles", [True, False])
 def test_column_tiles_match_oracle(name, col_tiles):
@@ -78,7 +78,7 @@ def test_column_tiles_match_oracle(name, col_tiles):
     prob = CASES[name]()
     c, E0, e2, ec = _oracle(prob)
     g2, gc, g0, plan = _gpu_e2(prob, c, col_tiles=col_tiles)
-    for cls in (2, 4, 6):
+    for cls in (2, 4, 5, 6):
         tiles, _, used = plan.class_tiles(cls)
         assert used == (col_tiles and tiles > 0)
     np.testing.assert_allclose(gc, ec, rtol=0, atol=TOL_E2)

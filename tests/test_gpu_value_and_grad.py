@@ -25,7 +25,7 @@ def setup():
     import paper_2608_11529_b300 as e2
     from paper_2608_11529_b300 import build as e2build
     e2build.build()
-    prob = make_problem("cfg1", ham="DCB", Lx=30, x_scale=2e-3, n_roots=2)
+    prob = make_problem("dc_small", ham="DCB", Lx=30, x_scale=2e-3, n_roots=2)
     c, _ = Oracle(prob).ground_state(2)
     plan = e2.E2Problem.from_problem(prob)
     t = e2.device_inputs(prob, c)

@@ -38,7 +38,7 @@ def _inputs(binding, plan, t):
 def test_noalloc_forward_matches_workspace_forward_on_consecutive_calls():
     from oracle import Oracle
     e2, binding, lib = _lib()
-    prob = make_problem("cfg1")
+    prob = make_problem("dc_small")
     c, _ = Oracle(prob).ground_state(1)
     plan = e2.E2Problem.from_problem(prob)
     t = e2.device_inputs(prob, c)
