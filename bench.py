@@ -234,8 +234,12 @@ def run_batch(args):
         over["n_virt"] = args.virt
     if args.core:
         over["n_core"] = args.core
+    if args.roots:
+        over["n_roots"] = args.roots
     nv = over.get("n_virt", CONFIGS[args.config]["n_virt"])
-    cutoffs = [(0, 0), (2, nv // 5), (6, 2 * nv // 5)]   # none, 1s pair + 20%, more core + 40% of the virtuals
+    nc = over.get("n_core", CONFIGS[args.config]["n_core"])
+    # frozen (core, virtual) cutoffs: none, a core pair + 20%, more core + 40% of the virtuals
+    cutoffs = [(0, 0), (min(2, nc), nv // 5), (min(6, nc), 2 * nv // 5)]
     jobs = []
     for ham in ("DC", "DCG", "DCB"):
         for fc, fv in cutoffs:
@@ -265,6 +269,9 @@ def run_batch(args):
     torch.cuda.synchronize()
     ms_seq = a.elapsed_time(z) / args.steps
     ref = [(E2.clone(), E2c.clone()) for E2, E2c, _ in ref]
+    for *_, p, _ in jobs:   # the batch holds all jobs' layouts in one workspace
+        p.release()
+    torch.cuda.empty_cache()
     batch = e2.E2Batch([p for *_, p, _ in jobs])
     batch.prepare(dev)
     inputs = [t for *_, t in jobs]
@@ -489,6 +496,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default column tiles")
+    ap.add_argument("--roots", type=int, default=0, help="override the root count (batch evidence runs)")
     ap.add_argument("--batch", action="store_true",
                     help="evidence run: the 3 Hamiltonians x 3 frozen cutoffs of --config batched in one "
                          "graph-captured launch against sequential forwards")

@@ -170,12 +170,16 @@ class E2Problem:
         need = (self.backward_workspace_bytes if backward else
                 self.solve_workspace_bytes if solver else self.workspace_bytes)
         if self._ws is None or self._ws.device != device or self._ws.numel() < need:
-            self._ws = None
+            self._ws = self._ws_raw = None   # free the smaller layout before taking the larger one
             raw = torch.empty(need + 256, dtype=torch.uint8, device=device)
             off = (-raw.data_ptr()) % 256
             self._ws_raw = raw
             self._ws = raw[off:off + need]
         return self._ws
+
+    def release(self):
+        """Drop the cached device workspace (the next call allocates again)."""
+        self._ws = self._ws_raw = None
 
     def backward(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, seed=None, want_h=True, want_c=True, want_B=False,
                  want_lambda=False, stream=None, E2_out=None):

@@ -526,21 +526,40 @@ k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const doub
     for (int x = 0; x < 8; ++x) {
       const double cx = ct - pa[x];
 #pragma unroll
-      for (int y = 0; y < 8; ++y) {
-        const double w = sG2[x][y];
-        if (w == 0.0) continue;
-        double gk, hk;
-        en_derivs(w * c2, cx - pb[y] - sGab[x][y], b, gk, hk);
-        hk *= s;
-        csum += s * gk * w;
-        gv += s * gk * w * c2;
-        hsum += hk;
-        ha[x] += hk;
-        hb[y] += hk;
-        inner = fma(w, gk, inner);
+      for (int y0 = 0; y0 < 8; y0 += 4) {  // the forward's groups of four denominators
+        double Dv[4], q[4], rq[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          Dv[k] = cx - pb[y0 + k] - sGab[x][y0 + k];
+          q[k] = sG2[x][y0 + k] != 0.0 ? en_q(Dv[k], b) : 1.0;
+        }
+        rcp4(q, rq);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int y = y0 + k;
+          const double w = sG2[x][y];
+          if (w == 0.0) continue;
+          // df/dD is linear in v = w c2: accumulate it for v = w and scale
+          // the sums by s c2 once per string
+          double gk, hw;
+          en_derivs_r(w, Dv[k], b, rq[k], gk, hw);
+          hsum += hw;
+          ha[x] += hw;
+          hb[y] += hw;
+          inner = fma(w, gk, inner);
+        }
       }
     }
     acc = fma(cv.x, cv.x, cv.y * cv.y) * inner;
+    const double sc2 = s * c2;
+    csum = s * inner;   // sum s (df/dv) w
+    gv = sc2 * inner;   // sum s (df/dv) v
+    hsum *= sc2;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      ha[k] *= sc2;
+      hb[k] *= sc2;
+    }
   }
   const int64_t yz = (int64_t)blockIdx.z * gridDim.y + blockIdx.y;
   if (A < Ls.n) {
@@ -1051,18 +1070,39 @@ k_class22_rows(DevList Ls, DevSpace sp, const double2* __restrict__ c, const dou
   const int na = sp.n_act;
   double hs = 0.0, p22 = 0.0, ho[64];
   for (int t = 0; t < na; ++t) ho[t] = 0.0;
-  for (int64_t A = threadIdx.x; A < Ls.n; A += blockDim.x) {
-    const double D = e0p - Ls.eA[A] - chi - Ls.U[(int64_t)(sp.ncc + au) * Ls.n + A] -
-                     Ls.U[(int64_t)(sp.ncc + bu) * Ls.n + A] + Ls.U[(int64_t)iu * Ls.n + A] + Ls.U[(int64_t)ju * Ls.n + A];
-    const double2 cv = c[A];
-    const double c2 = (cv.x * cv.x + cv.y * cv.y) * inv_n;
-    double gk, hk;
-    en_derivs(w * c2, D, b, gk, hk);
-    hk *= s;
-    hs += hk;
-    p22 += s * gk * c2;
-    for (uint64_t x = Ls.str[A]; x; x &= x - 1) ho[__ffsll((long long)x) - 1] += hk;
+  const double* Ua = Ls.U + (int64_t)(sp.ncc + au) * Ls.n;
+  const double* Ub = Ls.U + (int64_t)(sp.ncc + bu) * Ls.n;
+  const double* Ui = Ls.U + (int64_t)iu * Ls.n;
+  const double* Uj = Ls.U + (int64_t)ju * Ls.n;
+  // four strings per step (stride blockDim), their denominators inverted
+  // together; df/dD is linear in v = w c2, so it is taken for v = w and scaled
+  for (int64_t A0 = threadIdx.x; A0 < Ls.n; A0 += 4 * (int64_t)blockDim.x) {
+    double Dv[4], q[4], rq[4], c2[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t A = A0 + k * (int64_t)blockDim.x;
+      const bool ok = A < Ls.n;
+      Dv[k] = ok ? e0p - Ls.eA[A] - chi - Ua[A] - Ub[A] + Ui[A] + Uj[A] : 1.0;
+      q[k] = ok ? en_q(Dv[k], b) : 1.0;
+      const double2 cv = ok ? c[A] : make_double2(0.0, 0.0);
+      c2[k] = (cv.x * cv.x + cv.y * cv.y) * inv_n;
+    }
+    rcp4(q, rq);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int64_t A = A0 + k * (int64_t)blockDim.x;
+      if (A >= Ls.n) break;
+      double gk, hw;
+      en_derivs_r(w, Dv[k], b, rq[k], gk, hw);
+      const double hk = c2[k] * hw;
+      hs += hk;
+      p22 = fma(gk, c2[k], p22);
+      for (uint64_t x = Ls.str[A]; x; x &= x - 1) ho[__ffsll((long long)x) - 1] += hk;
+    }
   }
+  hs *= s;
+  p22 *= s;
+  for (int t = 0; t < na; ++t) ho[t] *= s;
   double v = block_sum(hs, sh);
   if (threadIdx.x == 0) hsum[row] = v;
   v = block_sum(p22, sh);

@@ -620,22 +620,34 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
       const double* U3 = U + (int64_t)ri.i1 * N;
       const double* U4 = U + (int64_t)ri.i2 * N;
       const double base = e0p - ri.chi;
+      // the thread's four denominators of this row, inverted together
+      double Dv[4], q[4], rq[4];
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int hc = 0; hc < 2; ++hc) {
+          const int64_t col = sCol[wn * 16 + ni * 8 + 2 * tq + hc];
+          const int kk = ni * 2 + hc;
+          Dv[kk] = col >= 0 ? base - eA[col] - U1[col] - U2[col] + U3[col] + U4[col] : 1.0;
+          q[kk] = col >= 0 ? en_q(Dv[kk], b) : 1.0;
+        }
+      rcp4(q, rq);
 #pragma unroll
       for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
         for (int hc = 0; hc < 2; ++hc) {
           const int64_t col = sCol[wn * 16 + ni * 8 + 2 * tq + hc];
           if (col < 0) continue;
-          const int e = hr * 2 + hc;
+          const int e = hr * 2 + hc, kk = ni * 2 + hc;
           const double vr = t1[mi][ni][e] - t2[mi][ni][e];
           const double vi = t3[mi][ni][e] - t1[mi][ni][e] - t2[mi][ni][e];
-          const double Dk = base - eA[col] - U1[col] - U2[col] + U3[col] + U4[col];
+          const double Dk = Dv[kk];
           const double v2 = fma(vr, vr, vi * vi);
           if (!adj.T) {
-            acc = fma(v2, en_g(Dk, b), acc);  // the E2 term, same rounding in both passes
+            acc = fma(v2, en_g_r(Dk, b, rq[kk]), acc);  // the E2 term, same rounding in both passes
           } else {
             double gk, hk;
-            en_derivs(v2 * inv_n, Dk, b, gk, hk);
+            en_derivs_r(v2 * inv_n, Dk, b, rq[kk], gk, hk);
             const double w = s2n * gk;  // t = s (2/n) g V
             adj.T[(row - adj.m_base) * N + col] = make_double2(w * vr, w * vi);
             hk *= adj.s;
@@ -643,7 +655,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
             rowp[mi][hr] += hk;
             colp[ni][hc] += hk;
             acc += hk;
-            acc2 = fma(v2, gk, acc2);  // the forward's E2 term (gk = en_g(Dk, b))
+            acc2 = fma(v2, gk, acc2);  // the forward's E2 term (gk = en_g_r(Dk, b, r))
           }
         }
     }
@@ -793,9 +805,19 @@ k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* 
     for (int x = 0; x < 8; ++x) {
       const double cx = ct - pa[x];
 #pragma unroll
-      for (int y = 0; y < 8; ++y) {
-        const double w = sG2[x][y];
-        if (w != 0.0) inner = fma(w, en_g(cx - pb[y] - sGab[x][y], b), inner);
+      for (int y0 = 0; y0 < 8; y0 += 4) {  // four denominators inverted together
+        double Dv[4], q[4], rq[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          Dv[k] = cx - pb[y0 + k] - sGab[x][y0 + k];
+          q[k] = sG2[x][y0 + k] != 0.0 ? en_q(Dv[k], b) : 1.0;
+        }
+        rcp4(q, rq);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const double w = sG2[x][y0 + k];
+          if (w != 0.0) inner = fma(w, en_g_r(Dv[k], b, rq[k]), inner);
+        }
       }
     }
     double2 cv = c[A];
