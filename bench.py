@@ -255,8 +255,13 @@ def run_batch(args):
     stream = torch.cuda.current_stream(dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
-    def seq():
-        return [p.forward(**t) for *_, p, t in jobs]
+    def seq():   # one job at a time, each job's workspace released after its forward
+        out = []
+        for *_, p, t in jobs:
+            E2, E2c, _ = p.forward(**t)
+            out.append((E2.clone(), E2c.clone(), None))
+            p.release()
+        return out
 
     for _ in range(args.warmup):
         seq()
@@ -268,10 +273,8 @@ def run_batch(args):
     z.record(stream)
     torch.cuda.synchronize()
     ms_seq = a.elapsed_time(z) / args.steps
-    ref = [(E2.clone(), E2c.clone()) for E2, E2c, _ in ref]
-    for *_, p, _ in jobs:   # the batch holds all jobs' layouts in one workspace
-        p.release()
-    torch.cuda.empty_cache()
+    ref = [(E2, E2c) for E2, E2c, _ in ref]
+    torch.cuda.empty_cache()   # the batch holds all jobs' layouts in one workspace
     batch = e2.E2Batch([p for *_, p, _ in jobs])
     batch.prepare(dev)
     inputs = [t for *_, t in jobs]

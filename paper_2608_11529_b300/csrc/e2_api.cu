@@ -95,7 +95,8 @@ struct e2_problem {
   size_t o_vaY, o_vaZ, o_vaX, va_cap;
   size_t o_xYc, o_xZaa, o_x12, o_x01;
   size_t o_DT, o_DTD, o_DTU, o_DTDUD, o_DTDU;  // per-root stride below
-  size_t d_stride;                              // bytes per root of all D tables
+  size_t d_stride;                              // bytes of one root's D tables
+  bool multi_slot = false;                      // set while a batch uses the job: one slot per root
   size_t o_g1, o_g2, g_stride;                  // gram outputs per root
   size_t o_part, o_partoff, o_partcnt, o_e2c;
   int64_t part_cnt[E2_NCLASS];
@@ -518,7 +519,10 @@ e2_status build_plan(e2_problem* P) {
   for (ColPlan& cp : P->cplan)
     if (cp.built) cp.o_Dc = ws.take(16 * (size_t)cp.krows * 64);
   P->d_stride = ws.top - dstart;
-  ws.top = dstart + P->d_stride * R;
+  // one slot: the forward and backward build and consume each root's tables
+  // in turn on one stream; a batch, which holds every root's tables until its
+  // single launch, appends R - 1 more slots to each job's region
+  ws.top = dstart + P->d_stride;
   size_t gstart = ws.top;
   P->o_g1 = ws.take(16 * (size_t)(1 + P->na * P->na));
   P->o_g2 = ws.take(16 * (size_t)std::max(P->ntp * P->ntp, 1));
@@ -844,8 +848,15 @@ struct Tabs {
   double2 *DT, *DTD, *DTU, *DTDUD, *DTDU;
 };
 
+// Base of root r's D-table slot (offsets o_DT... apply to it): slot 0 inside
+// the layout, or for a batch slot r >= 1 after the job's forward layout.
+unsigned char* slot_base(const e2_problem* P, unsigned char* ws, int r) {
+  if (!P->multi_slot || r == 0) return ws;
+  return ws + P->ws_bytes + (size_t)(r - 1) * P->d_stride - P->o_dstart;
+}
+
 Tabs tables(const e2_problem* P, unsigned char* ws, int r) {
-  unsigned char* dr = ws + P->d_stride * r;
+  unsigned char* dr = slot_base(P, ws, r);
   return Tabs{(double2*)(dr + P->o_DT), (double2*)(dr + P->o_DTD), (double2*)(dr + P->o_DTU),
               (double2*)(dr + P->o_DTDUD), (double2*)(dr + P->o_DTDU)};
 }
@@ -855,7 +866,7 @@ ColTiles col_tiles(const e2_problem* P, unsigned char* ws, int r, int cls) {
   if (!P->use_cols[cls]) return ColTiles{nullptr, nullptr, nullptr, nullptr};
   const ColPlan& cp = P->cplan[cls];
   return ColTiles{(const int32_t*)(ws + cp.o_perm), (const int4*)(ws + cp.o_tdesc), (const int32_t*)(ws + cp.o_klist),
-                  (const double2*)(ws + P->d_stride * r + cp.o_Dc)};
+                  (const double2*)(slot_base(P, ws, r) + cp.o_Dc)};
 }
 
 // Coupling tensors D^x_A = <A|x|c> of one reference vector c; `all` = false
@@ -1439,7 +1450,7 @@ e2_status e2_batch_create(e2_problem* const* jobs, int n_jobs, e2_batch** out) {
       return E2_ERR_INVALID_ARG;
     }
     B->jobs.push_back(jobs[j]);
-    B->off.push_back(ws.take(jobs[j]->ws_bytes));
+    B->off.push_back(ws.take(jobs[j]->ws_bytes + (size_t)(jobs[j]->d.n_roots - 1) * jobs[j]->d_stride));
     for (int c : {2, 5, 7, 4, 6})
       if (jobs[j]->part_cnt[c] > 0) {
         njc += jobs[j]->d.n_roots;
@@ -1476,6 +1487,11 @@ e2_status e2_batch_prepare(e2_batch* B, void* workspace, size_t workspace_bytes,
   unsigned char* ws = (unsigned char*)workspace;
   B->gj.clear();
   B->items.clear();
+  struct Slots {  // every root of every job keeps its own tables for the batch's one launch
+    e2_batch* b;
+    explicit Slots(e2_batch* b_) : b(b_) { for (e2_problem* P : b->jobs) P->multi_slot = true; }
+    ~Slots() { for (e2_problem* P : b->jobs) P->multi_slot = false; }
+  } slots(B);
   struct Key {
     int kp;
     int job;
@@ -1544,6 +1560,11 @@ e2_status e2_batch_forward(e2_batch* B, const e2_inputs* inputs, void* workspace
   unsigned char* ws = (unsigned char*)workspace;
   cudaGetLastError();
   g_launches = 0;
+  struct Slots {
+    e2_batch* b;
+    explicit Slots(e2_batch* b_) : b(b_) { for (e2_problem* P : b->jobs) P->multi_slot = true; }
+    ~Slots() { for (e2_problem* P : b->jobs) P->multi_slot = false; }
+  } slots(B);
   for (size_t j = 0; j < B->jobs.size(); ++j) {
     e2_problem* P = B->jobs[j];
     unsigned char* w = ws + B->off[j];
