@@ -270,6 +270,12 @@ E2_API e2_status e2_partials(const e2_problem* prob, const void* workspace, int 
  * tiles and *columns (device, [tiles * 64]) gives each tile column's string
  * (list index, -1 for padding); otherwise *columns is NULL. */
 E2_API e2_status e2_class_tiles(const e2_problem* prob, int cls, int64_t* tiles, int64_t* krows, int* in_use);
+/* The plan's column tiles of class cls as host copies, for inspection: perm
+ * [tiles * 64] (list index per tile column, -1 padding), tdesc [tiles * 4]
+ * ({koff, klen, ktrue, 0} per tile) and klist [krows] (table row of each
+ * compacted row); sizes from e2_class_tiles.  E2_ERR_UNSUPPORTED when the
+ * class has no plan. */
+E2_API e2_status e2_class_tiles_copy(const e2_problem* prob, int cls, int32_t* perm, int32_t* tdesc, int32_t* klist);
 E2_API e2_status e2_set_class_tiles(e2_problem* prob, int cls, int on);
 E2_API e2_status e2_autotune(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
                              void* stream, float* ms_out);

@@ -63,6 +63,8 @@ def load():
         L.e2_class_tiles.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                      C.POINTER(C.c_int)]
         L.e2_class_tiles.restype = C.c_int
+        L.e2_class_tiles_copy.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.e2_class_tiles_copy.restype = C.c_int
         L.e2_set_class_tiles.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.e2_set_class_tiles.restype = C.c_int
         L.e2_autotune.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
@@ -260,6 +262,17 @@ class E2Problem:
         t, k, u = C.c_int64(), C.c_int64(), C.c_int()
         _check(load().e2_class_tiles(self._h, cls, C.byref(t), C.byref(k), C.byref(u)))
         return int(t.value), int(k.value), bool(u.value)
+
+    def class_tiles_plan(self, cls):
+        """Host copies (perm [tiles*64], tdesc [tiles, 4], klist [krows]) of
+        class cls's column tiles."""
+        tiles, krows, _ = self.class_tiles(cls)
+        perm = np.zeros(tiles * 64, np.int32)
+        tdesc = np.zeros((tiles, 4), np.int32)
+        klist = np.zeros(max(krows, 1), np.int32)
+        _check(load().e2_class_tiles_copy(self._h, cls, perm.ctypes.data_as(C.c_void_p),
+                                          tdesc.ctypes.data_as(C.c_void_p), klist.ctypes.data_as(C.c_void_p)))
+        return perm, tdesc, klist[:krows]
 
     def set_class_tiles(self, cls, on):
         _check(load().e2_set_class_tiles(self._h, cls, int(bool(on))))

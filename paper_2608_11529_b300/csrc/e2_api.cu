@@ -1314,6 +1314,16 @@ e2_status e2_class_tiles(const e2_problem* P, int cls, int64_t* tiles, int64_t* 
   return E2_OK;
 }
 
+e2_status e2_class_tiles_copy(const e2_problem* P, int cls, int32_t* perm, int32_t* tdesc, int32_t* klist) {
+  if (!P || cls < 0 || cls >= E2_NCLASS || !perm || !tdesc || !klist) return E2_ERR_INVALID_ARG;
+  const ColPlan& cp = P->cplan[cls];
+  if (!cp.built) return E2_ERR_UNSUPPORTED;
+  std::copy(cp.perm.begin(), cp.perm.end(), perm);
+  std::copy(cp.tdesc.begin(), cp.tdesc.end(), tdesc);
+  std::copy(cp.klist.begin(), cp.klist.end(), klist);
+  return E2_OK;
+}
+
 e2_status e2_set_class_tiles(e2_problem* P, int cls, int on) {
   if (!P || cls < 0 || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
   if (on && !P->cplan[cls].built) return E2_ERR_UNSUPPORTED;
