@@ -388,6 +388,17 @@ __global__ void k_rowsum(const double* __restrict__ in, int64_t nrow, int64_t nc
   out[r] = acc ? out[r] + s : s;
 }
 
+// out[r] (+)= sum_c in[r*ncol + c] for long rows: one block per row, strided
+// per-thread sums and a fixed-order block reduction
+__global__ void k_rowsum_wide(const double* __restrict__ in, int64_t ncol, int acc, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const int64_t r = blockIdx.x;
+  double s = 0.0;
+  for (int64_t c = threadIdx.x; c < ncol; c += blockDim.x) s += in[r * ncol + c];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) out[r] = acc ? out[r] + s : s;
+}
+
 // out[c] (+)= sum_r in[r*ncol + c] in index order
 __global__ void k_colsum(const double* __restrict__ in, int64_t nrow, int64_t ncol, int acc, double* __restrict__ out) {
   const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -589,42 +600,46 @@ k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const doub
 // Reduce the (2,2) per-CTA partials: Nx (virtual and core marginals), scalars.
 __global__ void k_class22_marg(const double* __restrict__ vpart, int nx_blocks, int nvb, int64_t ncp, DevSpace sp,
                                double* __restrict__ Nx, double* __restrict__ scal) {
-  // one thread per correlated virtual (index a) or per correlated core (index i)
-  const int x = blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nyb = (int64_t)nvb * (nvb + 1) / 2;
+  // one block per correlated virtual a, per correlated core i, and one for
+  // the two scalars; block-strided fixed-order sums
+  __shared__ double sh[32];
+  const int64_t nyb = (int64_t)nvb * (nvb + 1) / 2, nxb = nx_blocks;
+  auto yidx = [&](int ba, int bb) { return (int64_t)ba * nvb - (int64_t)ba * (ba - 1) / 2 + (bb - ba); };
+  const int x = blockIdx.x;
+  double s = 0.0, s2 = 0.0;
   if (x < sp.nvc) {
     const int blk = x / 8, off = x % 8;
-    double s = 0.0;
-    for (int64_t z = 0; z < ncp; ++z)
-      for (int64_t y = 0; y < nyb; ++y) {
-        int yb = (int)y, k = 0;
-        while (yb >= nvb - k) { yb -= nvb - k; ++k; }
-        const int ba = k, bb = k + yb;
-        for (int64_t xb = 0; xb < nx_blocks; ++xb) {
-          const int64_t cta = (z * nyb + y) * nx_blocks + xb;
-          if (ba == blk) s += vpart[cta * 19 + off];
-          if (bb == blk) s += vpart[cta * 19 + 8 + off];
-        }
-      }
-    Nx[sp.ncc + x] += s;
+    const int64_t n = ncp * nvb * nxb;
+    for (int64_t idx = threadIdx.x; idx < n; idx += blockDim.x) {
+      const int64_t z = idx / ((int64_t)nvb * nxb), xb = idx % nxb;
+      const int m = (int)((idx / nxb) % nvb);   // the other virtual block of the pair
+      if (m >= blk) s += vpart[((z * nyb + yidx(blk, m)) * nxb + xb) * 19 + off];
+      if (m <= blk) s += vpart[((z * nyb + yidx(m, blk)) * nxb + xb) * 19 + 8 + off];
+    }
   } else if (x < sp.nvc + sp.ncc) {
     const int i = x - sp.nvc;
-    double s = 0.0;
-    for (int64_t z = 0; z < ncp; ++z) {
+    const int64_t per = nyb * nxb;
+    for (int64_t idx = threadIdx.x; idx < ncp * per; idx += blockDim.x) {
+      const int64_t z = idx / per;
       int iu, ju;
       pair_decode(z, iu, ju);
-      if (iu != i && ju != i) continue;
-      for (int64_t k = 0; k < nyb * nx_blocks; ++k) s += vpart[(z * nyb * nx_blocks + k) * 19 + 16];
+      if (iu == i || ju == i) s += vpart[idx * 19 + 16];
     }
-    Nx[i] += s;
-  } else if (x == sp.nvc + sp.ncc) {
-    double a = 0.0, bsum = 0.0;
-    for (int64_t k = 0; k < ncp * nyb * nx_blocks; ++k) {
-      a += vpart[k * 19 + 17];
-      bsum += vpart[k * 19 + 18];
+  } else {
+    for (int64_t k = threadIdx.x; k < ncp * nyb * nxb; k += blockDim.x) {
+      s += vpart[k * 19 + 17];
+      s2 += vpart[k * 19 + 18];
     }
-    scal[0] += a;
-    scal[1] += bsum;
+  }
+  s = block_sum(s, sh);
+  s2 = block_sum(s2, sh);
+  if (threadIdx.x == 0) {
+    if (x < sp.nvc) Nx[sp.ncc + x] += s;
+    else if (x < sp.nvc + sp.ncc) Nx[x - sp.nvc] += s;
+    else {
+      scal[0] += s;
+      scal[1] += s2;
+    }
   }
 }
 

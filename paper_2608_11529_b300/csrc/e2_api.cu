@@ -893,13 +893,13 @@ thread_local void* g_splitk = nullptr;
 thread_local size_t g_splitk_bytes = 0;
 
 // Segments for a product with `tiles` output tiles (one CTA per SM, 148 SMs)
-// and contraction K: the count (at most 16, at least 256 of K each) that
+// and contraction K: the count (at most 64, at least 256 of K each) that
 // minimises waves / segments, i.e. the time of a wave-quantised launch whose
 // CTAs each take K / segments; ties go to fewer segments.
 int splitk_segments(int64_t tiles, int64_t K, size_t seg_bytes) {
   if (!g_splitk || K < 512) return 1;
   const int64_t slots = 148;
-  int64_t nmax = std::min<int64_t>(16, K / 256);
+  int64_t nmax = std::min<int64_t>(64, K / 256);
   nmax = std::min<int64_t>(nmax, (int64_t)(g_splitk_bytes / std::max<size_t>(seg_bytes, 1)));
   int best = 1;
   double tbest = (double)((tiles + slots - 1) / slots);
@@ -1787,7 +1787,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bC22p), yz, L.n, 0, c22), ++g_launches);
       (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bH22p), yz, L.n, 0, hA), ++g_launches);
       (k_amarg<<<na, 256, 0, st>>>(L, hA, Nt), ++g_launches);
-      (k_class22_marg<<<blocks(P->nvc + P->ncc + 1), 256, 0, st>>>((const double*)B(P->o_bV22), (int)blocks(L.n),
+      (k_class22_marg<<<(unsigned)(P->nvc + P->ncc + 1), 256, 0, st>>>((const double*)B(P->o_bV22), (int)blocks(L.n),
                                                                    P->nvb, P->ncp, X.sp, Nx, scal), ++g_launches);
       if (want_B) {
         const int64_t M22 = P->ncp * P->nvp;
@@ -1821,8 +1821,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
                                         (const double2*)(ws + P->o_X00), X.f, X.epsh, X.E0p + r, b, s, g1, Tg, Hg,
                                         GVg, poff(cls)), ++g_launches);
       (k_sum2<<<1, 256, 0, st>>>(Hg, GVg, (int64_t)nrow * L.n, scal), ++g_launches);
-      if (cls == 1) (k_rowsum<<<blocks(nrow), 256, 0, st>>>(Hg, nrow, L.n, 1, Nx + P->ncc), ++g_launches);
-      if (cls == 3) (k_rowsum<<<blocks(nrow), 256, 0, st>>>(Hg, nrow, L.n, 1, Nx), ++g_launches);
+      if (cls == 1) (k_rowsum_wide<<<(unsigned)nrow, 256, 0, st>>>(Hg, L.n, 1, Nx + P->ncc), ++g_launches);
+      if (cls == 3) (k_rowsum_wide<<<(unsigned)nrow, 256, 0, st>>>(Hg, L.n, 1, Nx), ++g_launches);
       (k_colsum<<<blocks(L.n), 256, 0, st>>>(Hg, nrow, L.n, 0, hA), ++g_launches);
       (k_amarg<<<na, 256, 0, st>>>(L, hA, Nt), ++g_launches);
       // one-body parts: Gamma_f and the D^t / D^{t+} / D^{t+u} coefficients
@@ -1840,7 +1840,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       //   Gamma_D[x][B] += sum_row X[row][...][x] Tsh[row][B]        (reference gradient)
       //   Gamma_X[row][...][x] = sum_B Tsh[row][B] D[x][B]            (integral coefficients)
       if (want_B) {
-        (k_rowsum<<<blocks(nrow), 256, 0, st>>>(Hg, nrow, L.n, 0, hsum), ++g_launches);
+        (k_rowsum_wide<<<(unsigned)nrow, 256, 0, st>>>(Hg, L.n, 0, hsum), ++g_launches);
         (k_hocc<<<(unsigned)nrow, 256, 0, st>>>(Hg, L, na, Hocc), ++g_launches);
         if (cls != 0) {
           (k_rows<<<blocks(nrow), 256, 0, st>>>(cls, X.sp, X.epsh, X.G, nrow, (RowInfo*)B(P->o_bRg)), ++g_launches);

@@ -70,6 +70,7 @@ __global__ void k_gw_reduce(const int4* tdesc, const int32_t* pos, int64_t tiles
                             int64_t krows, int64_t Mc, double2* GW, int nxo, int64_t ldo);
 __global__ void k_zacc(const double2* part, int nseg, int64_t ps, int64_t M, int64_t N, double2* C, int64_t csm,
                        int64_t csn, int beta);
+__global__ void k_rowsum_wide(const double* in, int64_t ncol, int acc, double* out);
 __global__ void k_rowsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);
 __global__ void k_colsum(const double* in, int64_t nrow, int64_t ncol, int acc, double* out);
 __global__ void k_scalsum(const double* in, int64_t n, double* scal_out);
