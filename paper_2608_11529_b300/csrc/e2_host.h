@@ -1,0 +1,217 @@
+// Host-side internals shared by the C-ABI translation units (plan,
+// execution, batches, gradient, reference solver): the plan structures, the
+// workspace layout and the stream-ordered launch helpers.  Not installed.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <vector>
+
+#include "e2_common.cuh"
+#include "e2_kernels.cuh"
+
+namespace e2 {
+
+using Pat = std::array<int, E2_MAX_DAS>;
+
+int64_t binom_h(int n, int k);
+
+struct HostList {
+  int count = 0;
+  std::vector<Pat> pats;
+  std::vector<int64_t> patoff;
+  int64_t n = 0;
+  std::vector<int64_t> key2off;
+  size_t o_str = 0, o_key = 0, o_patoff = 0, o_patocc = 0, o_eA = 0, o_U = 0;
+};
+
+// Column tiles of a dense class with a compacted contraction (see ColTiles).
+struct ColPlan {
+  bool built = false;
+  std::vector<int32_t> perm;   // [tiles * 64] list index, -1 = padding
+  std::vector<int32_t> tdesc;  // [tiles][4] {koff, klen, ktrue, 0}
+  std::vector<int32_t> klist;  // [krows]
+  std::vector<int32_t> pos;    // [tiles][Kp] compacted row of table row x in tile j, -1 if absent
+  int64_t tiles = 0, krows = 0;
+  int maxklen = 0;             // longest compacted contraction of a tile
+  int gran = 8;                // contraction granularity of the tiles (4: a k = 4 tail step)
+  int64_t gd_ctas = 0;         // sum over tiles of ceil(klen / 64)
+  double ratio = 1.0;          // krows / (tiles * Kp): share of the dense contraction
+  size_t o_perm = 0, o_tdesc = 0, o_klist = 0, o_pos = 0, o_Dc = 0;  // o_Dc: per-root D region
+};
+
+// Bump allocator over the workspace (256-byte aligned segments).
+struct Layout {
+  size_t top = 0;
+  size_t take(size_t bytes) {
+    size_t o = top;
+    top += (bytes + 255) & ~size_t(255);
+    return o;
+  }
+};
+
+}  // namespace e2
+
+struct e2_problem {
+  e2_desc d;
+  std::vector<uint8_t> frozen;
+  int das_size[E2_MAX_DAS], das_min[E2_MAX_DAS], das_max[E2_MAX_DAS];
+  int n, nocc, ncc, nvc, nx, na, N;
+  std::vector<int32_t> cc, vc;
+  e2::DevDas das;
+  int nkeys;
+  std::vector<e2::Pat> ppats;          // P patterns (address order)
+  std::vector<e2::HostList> lists;     // unique string lists
+  int list_of[E2_NCLASS];          // class -> list (-1: no strings)
+  int listP;
+  // integral / table shapes
+  int ntp;
+  int64_t nvp, ncp;
+  int64_t M[E2_NCLASS];            // rows of each class
+  int Kp[E2_NCLASS];               // padded contraction length of the dense classes
+  int KpT, KpTU, Kp11;             // rows of the D^t / D^tu / D^{t+u} tables
+  double q_per_class[E2_NCLASS];
+  // workspace layout
+  size_t ws_bytes;
+  size_t o_plan, plan_bytes;
+  size_t o_binom, o_EO, o_E0p, o_E0, o_G, o_epsh, o_dg, o_wt, o_Bo, o_f, o_cc, o_vc;
+  size_t o_rows[E2_NCLASS], o_W[E2_NCLASS];
+  size_t o_G22, o_X01, o_X10, o_X00;
+  size_t o_vaY, o_vaZ, o_vaX, va_cap;
+  size_t o_xYc, o_xZaa, o_x12, o_x01;
+  size_t o_DT, o_DTD, o_DTU, o_DTDUD, o_DTDU;  // per-root stride below
+  size_t d_stride;                              // bytes of one root's D tables
+  bool multi_slot = false;                      // set while a batch uses the job: one slot per root
+  size_t o_g1, o_g2, g_stride;                  // gram outputs per root
+  size_t o_part, o_partoff, o_partcnt, o_e2c;
+  int64_t part_cnt[E2_NCLASS];
+  std::vector<int64_t> part_off;                // [n_roots][E2_NCLASS]
+  std::vector<unsigned char> plan_blob;         // host image of the plan region
+  // launch shapes of the sparse / elementwise classes
+  int nvb;
+  // optional CUDA events around each class kernel of root 0 (bench hooks)
+  cudaEvent_t prof[2 * E2_NCLASS];
+  bool prof_on = false;
+  int64_t launches = 0;  // kernels enqueued by the last e2_forward
+  // reference solver region
+  int sv_mmax;
+  size_t o_sV, o_sS, o_sX, o_sR, o_sD, o_sT, o_sG, o_sY, solve_bytes;
+  // adjoint region
+  size_t o_dstart;                   // first D table of the root-0 slot
+  int64_t chunk_rows[E2_NCLASS];     // dense-class rows per adjoint chunk
+  size_t o_gD, o_bT, o_bHrow, o_bHcol, o_bScalT, o_bHsum, o_bHA, o_bRowdot;
+  size_t o_bGT, o_bGH, o_bGV, o_bC22p, o_bH22p, o_bV22, o_bC22, o_bGc, o_bSig, o_bGf, o_bNx, o_bNt, o_bNd, o_bScal;
+  // factor gradient
+  int64_t npair;
+  size_t o_bGW[E2_NCLASS], o_bHm, o_bHocc, o_bZ, o_bZs, o_bGe, o_bGea, o_bNtt, o_bGG, o_bGt, o_bGh, o_bTsh;
+  size_t o_bGX01, o_bGX10, o_bGX00, o_bR22, o_bHs22, o_bP22, o_bG22c, o_bGg22, o_bCs, o_bGB, o_bFtr, o_bGw, o_bRg;
+  size_t o_bPart, bpart_bytes;  // split-K segments
+  size_t tsh_bytes;
+  size_t o_bGDc, o_bGWc, gwc_bytes;
+  size_t bwd_bytes;
+  // compacted column tiles of the dense classes and whether each class uses them
+  e2::ColPlan cplan[E2_NCLASS];
+  bool use_cols[E2_NCLASS] = {};
+};
+
+struct e2_batch {
+  std::vector<e2_problem*> jobs;
+  std::vector<size_t> off;          // workspace offset of each job's forward layout
+  size_t o_jobs = 0, o_items = 0, o_counter = 0, bytes = 0;
+  std::vector<e2::GemmJob> gj;          // absolute pointers, built by e2_batch_prepare
+  std::vector<e2::WorkItem> items;
+  int64_t n_items = 0;
+  const void* prepared = nullptr;
+  int64_t launches = 0;
+};
+
+namespace e2 {
+
+// ---- planning (e2_plan.cu)
+e2_status build_plan(e2_problem* P);
+
+// ---- launch helpers (e2_api.cu)
+inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// kernels enqueued by the current host thread (read back as the count of one call)
+extern thread_local int64_t g_launches;
+// scratch for split-K segments of the GEMM helpers (set while a pass that
+// owns such a region runs; null: no split)
+extern thread_local void* g_splitk;
+extern thread_local size_t g_splitk_bytes;
+
+struct Ctx {
+  const int64_t* binom;
+  double *G, *epsh, *EO, *E0p, *E0d, *dg, *wt;
+  double2 *Bo, *f;
+  DevSpace sp;
+};
+
+struct Tabs {
+  double2 *DT, *DTD, *DTU, *DTDUD, *DTDU;
+};
+
+DevList dev_list(const e2_problem* P, int li, unsigned char* ws);
+Ctx ctx(const e2_problem* P, unsigned char* ws);
+unsigned char* slot_base(const e2_problem* P, unsigned char* ws, int r);
+Tabs tables(const e2_problem* P, unsigned char* ws, int r);
+ColTiles col_tiles(const e2_problem* P, unsigned char* ws, int r, int cls);
+void build_tables(const e2_problem* P, unsigned char* ws, cudaStream_t st, const double2* c, const Tabs& T, bool all);
+int splitk_segments(int64_t tiles, int64_t K, size_t seg_bytes);
+void dgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double* A, int64_t sam, int64_t sak,
+           const double* B, int64_t sbk, int64_t sbn, double* C, int64_t ldc, int beta);
+void zgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
+           const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn, int beta,
+           int bn = 64);
+e2_status setup_common(e2_problem* P, const e2_inputs* in, unsigned char* ws, cudaStream_t st, bool upload = true);
+void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st);
+void zgemm_gd_tiles(cudaStream_t st, const ColPlan& cp, const ColTiles& ctl, const double2* W, int Kp,
+                    const double2* T, int64_t N, int64_t Mc, double2* GDc, int beta, int conjT = 1);
+void prepare_root(e2_problem* P, unsigned char* ws, cudaStream_t st, const double2* c, int r);
+void launch_reduce(e2_problem* P, unsigned char* ws, cudaStream_t st, double* E2, double* E2_class, double* E0);
+
+// Classes (2,2), (0,1), (1,0), (0,0) of root r (their partial slots).
+template <class Mark>
+void launch_sparse_classes(e2_problem* P, unsigned char* ws, cudaStream_t st, int r, const double2* c, Mark mark) {
+  Ctx X = ctx(P, ws);
+  Tabs T = tables(P, ws, r);
+  DevList Lc[E2_NCLASS];
+  for (int k = 0; k < E2_NCLASS; ++k) Lc[k] = dev_list(P, P->list_of[k], ws);
+  const double b = P->d.level_shift_b;
+  double* part = (double*)(ws + P->o_part);
+  auto poff = [&](int cls) { return part + P->part_off[r * E2_NCLASS + cls]; };
+  if (P->part_cnt[8] > 0) {
+    const DevList& L = Lc[8];
+    dim3 grid(blocks(L.n), (unsigned)(P->nvb * (P->nvb + 1) / 2), (unsigned)P->ncp);
+    mark(8, 0);
+    (k_class22<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb,
+                                    poff(8)), ++g_launches);
+    mark(8, 1);
+  }
+  if (P->part_cnt[1] > 0) {
+    dim3 grid(blocks(Lc[1].n), (unsigned)P->nvc);
+    mark(1, 0);
+    (k_class01<<<grid, 256, 0, st>>>(Lc[1], Lc[5], Lc[2], P->das, X.sp, X.binom, T.DT, T.DTU,
+                                    (const double2*)(ws + P->o_X01), X.f, X.epsh, X.E0p + r, b, poff(1)), ++g_launches);
+    mark(1, 1);
+  }
+  if (P->part_cnt[3] > 0) {
+    dim3 grid(blocks(Lc[3].n), (unsigned)P->ncc);
+    mark(3, 0);
+    (k_class10<<<grid, 256, 0, st>>>(Lc[3], Lc[7], Lc[5], P->das, X.sp, X.binom, T.DTD, T.DT,
+                                    (const double2*)(ws + P->o_X10), X.f, X.epsh, X.E0p + r, b, poff(3)), ++g_launches);
+    mark(3, 1);
+  }
+  if (P->part_cnt[0] > 0) {
+    mark(0, 0);
+    (k_class00<<<blocks(Lc[0].n), 256, 0, st>>>(Lc[0], Lc[4], Lc[2], P->das, X.sp, X.binom, T.DTDU, T.DTU,
+                                               (const double2*)(ws + P->o_X00), X.f, X.E0p + r, b, poff(0)), ++g_launches);
+    mark(0, 1);
+  }
+}
+
+}  // namespace e2

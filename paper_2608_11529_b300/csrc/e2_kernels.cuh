@@ -1,4 +1,4 @@
-// Kernel entry points (defined in e2_kernels.cu), launched by e2_api.cu.
+// Kernel entry points (defined in e2_kernels.cu and e2_adjoint.cu), launched by the host units.
 #pragma once
 #include "e2_common.cuh"
 
