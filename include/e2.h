@@ -184,13 +184,21 @@ E2_API e2_status e2_batch_launch_count(const e2_batch* batch, int64_t* n);
  *        e2_forward's (the pass forms every V anyway), so that one call gives
  *        the value and its gradient
  * V is recomputed (never stored whole): the dense classes run in row chunks
- * whose weighted amplitudes fit a 2 GiB buffer.  Enqueues on `stream`;
- * workspace of at least e2_backward_workspace_size() bytes (it contains the
- * e2_forward and reference-solver layouts). */
+ * whose weighted amplitudes fit 4 GiB (and whose compacted Gamma_W, for a
+ * column-tiled class, fits 8 GiB); class (2,2) runs in chunks of core pairs
+ * whose partial sums fit 2 GiB.  Enqueues on `stream`; workspace of at least
+ * e2_backward_workspace_size() bytes (it contains the e2_forward and
+ * reference-solver layouts). */
 E2_API e2_status e2_backward_workspace_size(const e2_problem* prob, size_t* bytes);
 E2_API e2_status e2_backward(e2_problem* prob, const e2_inputs* in, const double* seed, void* workspace,
                              size_t workspace_bytes, void* stream, double* g_h, double* g_c, double* g_Bc,
                              double* g_Bx, double* dE2_dlambda, double* E2);
+/* Smaller adjoint chunks than the plan's (the workspace layout is unchanged):
+ * rows per dense-class chunk (rounded down to a multiple of 64, at least 64)
+ * and core pairs per class-(2,2) chunk, each capped at the plan's value; 0
+ * (or less) restores the plan's value.  The results change only by the order
+ * of the sums across chunks.  E2_ERR_INVALID_ARG for a NULL problem. */
+E2_API e2_status e2_set_adjoint_chunks(e2_problem* prob, int64_t rows, int core_pairs);
 
 /* Reference states: the n_roots lowest eigenvectors of P H P (the CASCI /
  * DAS-CI reference of Sec. 2.2-2.3, Eq. zeroh first term), by block Davidson

@@ -67,6 +67,8 @@ def load():
         L.e2_class_tiles_copy.restype = C.c_int
         L.e2_set_class_tiles.argtypes = [C.c_void_p, C.c_int, C.c_int]
         L.e2_set_class_tiles.restype = C.c_int
+        L.e2_set_adjoint_chunks.argtypes = [C.c_void_p, C.c_int64, C.c_int]
+        L.e2_set_adjoint_chunks.restype = C.c_int
         L.e2_autotune.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
         L.e2_autotune.restype = C.c_int
         L.e2_backward_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
@@ -276,6 +278,10 @@ class E2Problem:
 
     def set_class_tiles(self, cls, on):
         _check(load().e2_set_class_tiles(self._h, cls, int(bool(on))))
+
+    def set_adjoint_chunks(self, rows=0, core_pairs=0):
+        """Run the adjoint in smaller chunks than planned (0 restores the plan)."""
+        _check(load().e2_set_adjoint_chunks(self._h, int(rows), int(core_pairs)))
 
     def autotune(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, stream=None):
         """Time plain against compacted columns per class and keep the faster;

@@ -355,26 +355,64 @@ __global__ void k_hocc(const double* __restrict__ H, DevList Ls, int na, double*
   }
 }
 
-// Signed incidence of the external indices of each row: Z[e][x] = +1 for a
-// particle x, -1 for a hole x (x: correlated core, then correlated virtual).
-__global__ void k_zmat(const RowInfo* __restrict__ rows, int64_t M, int nx, double* __restrict__ Z) {
+// Rows of every class with external spinors are tuples (h, p): a hole tuple h
+// (none, one correlated core spinor, or a pair i<j) and a particle tuple p
+// (likewise over correlated virtuals), row = h * n_p + p, pairs indexed
+// b(b-1)/2 + a.  The marginals of per-row sums over the spinors a row
+// contains are sums over tuples: for s a spinor of the tuple's set,
+// out[b*ob + s*os + c*oc] (+)= sign * sum_{t contains s} in[(b*nt + t)*w + c]
+// (arity 1: t = s; arity 2: t = pair(s,u) over u != s, in u order).
+__global__ void k_tmarg(const double* __restrict__ in, int64_t nb, int64_t nt, int w, int arity, int ns, double sign,
+                        int acc, double* __restrict__ out, int64_t ob, int64_t os, int64_t oc) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= M * nx) return;
-  const int64_t e = idx / nx;
-  const int x = (int)(idx % nx);
-  const RowInfo ri = rows[e];
+  if (idx >= nb * ns * w) return;
+  const int c = (int)(idx % w);
+  const int64_t bs = idx / w;
+  const int sp = (int)(bs % ns);
+  const int64_t bb = bs / ns;
+  const double* src = in + bb * nt * w + c;
   double v = 0.0;
-  if (ri.s1 == x || ri.s2 == x) v = 1.0;
-  if (ri.i1 == x || ri.i2 == x) v = -1.0;
-  Z[idx] = v;
+  if (arity == 1) {
+    v = src[(int64_t)sp * w];
+  } else {
+    for (int u = 0; u < ns; ++u) {
+      if (u == sp) continue;
+      const int64_t hi = max(sp, u), lo = min(sp, u);
+      v += src[(hi * (hi - 1) / 2 + lo) * w];
+    }
+  }
+  double* o = out + bb * ob + sp * os + c * oc;
+  *o = acc ? *o + sign * v : sign * v;
 }
 
-// out[e][x] = hsum[e] * Z[e][x]
-__global__ void k_zscale(const double* __restrict__ Z, const double* __restrict__ hsum, int64_t M, int nx,
-                         double* __restrict__ out) {
+// out[a*ldo + b] += in[pair(a,b)] for a != b (the pair entries of a tuple-set Gram matrix)
+__global__ void k_pairplace(const double* __restrict__ in, int ns, double* __restrict__ out, int64_t ldo) {
   const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (idx >= M * nx) return;
-  out[idx] = Z[idx] * hsum[idx / nx];
+  if (idx >= (int64_t)ns * ns) return;
+  const int a = (int)(idx / ns), b = (int)(idx % ns);
+  if (a == b) return;
+  const int64_t hi = max(a, b), lo = min(a, b);
+  out[a * ldo + b] += in[hi * (hi - 1) / 2 + lo];
+}
+
+// out[h][c] = sum_p in[(h*np + p)*w + c]: one block per h, w <= 256; thread
+// (q, c) sums p = q, q + nq, ... (coalesced over the flattened (p, c) index),
+// then the nq partials of each c are added in q order
+__global__ void k_midsum(const double* __restrict__ in, int64_t np, int w, double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int nq = 256 / w, tid = threadIdx.x;
+  const int c = tid % w, q = tid / w;
+  const double* src = in + blockIdx.x * np * w;
+  double v = 0.0;
+  if (q < nq)
+    for (int64_t p = q; p < np; p += nq) v += src[p * w + c];
+  sh[tid] = v;
+  __syncthreads();
+  if (tid < w) {
+    double t = 0.0;
+    for (int k = 0; k < nq; ++k) t += sh[k * w + tid];
+    out[blockIdx.x * (int64_t)w + tid] = t;
+  }
 }
 
 // ------------------------------------------------------------------ reductions of the adjoint sums
@@ -482,7 +520,9 @@ __global__ void __launch_bounds__(256)
 k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* __restrict__ g2,
               const double* __restrict__ epsh, const double* __restrict__ G, const double* __restrict__ E0p, double b,
               int nvb, double s, const double2* __restrict__ g1, double* __restrict__ cpart,
-              double* __restrict__ hpart, double* __restrict__ vpart, double* __restrict__ part) {
+              double* __restrict__ hpart, double* __restrict__ vpart, double* __restrict__ part, int z0) {
+  // core pair z0 + blockIdx.z; the chunk's partials are indexed by blockIdx.z
+  const int zg = z0 + blockIdx.z;
   const double inv_n = 1.0 / g1[0].x;
   __shared__ double sGab[8][8], sG2[8][8], sAl[2][8];
   __shared__ double sh[32];
@@ -494,7 +534,7 @@ k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const doub
     bb = k + yb;
   }
   int iu, ju;
-  pair_decode(blockIdx.z, iu, ju);
+  pair_decode(zg, iu, ju);
   const int gi = sp.cc[iu], gj = sp.cc[ju];
   const int64_t nvp = pairs(sp.nvc);
   const int tid = threadIdx.x;
@@ -503,7 +543,7 @@ k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const doub
     int a = ba * 8 + x, bq = bb * 8 + y;
     bool ok = a < sp.nvc && bq < sp.nvc && a < bq;
     sGab[x][y] = ok ? G[(int64_t)sp.vc[a] * sp.n + sp.vc[bq]] : 0.0;
-    sG2[x][y] = ok ? g2[(int64_t)blockIdx.z * nvp + pair_index(a, bq)] : 0.0;
+    sG2[x][y] = ok ? g2[(int64_t)zg * nvp + pair_index(a, bq)] : 0.0;
   } else if (tid < 80) {
     int k = tid - 64, side = k >> 3, x = k & 7;
     int a = (side ? bb : ba) * 8 + x;
@@ -591,15 +631,16 @@ k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const doub
     vpart[cta * 19 + 17] = v;
     vpart[cta * 19 + 18] = w2;
   }
-  if (part) {  // the forward's E2 partial of this block
+  if (part) {  // the forward's E2 partial of this block (global core-pair index)
     const double tot = block_sum(acc, sh);
-    if (tid == 0) part[cta] = tot;
+    if (tid == 0) part[((int64_t)zg * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tot;
   }
 }
 
 // Reduce the (2,2) per-CTA partials: Nx (virtual and core marginals), scalars.
-__global__ void k_class22_marg(const double* __restrict__ vpart, int nx_blocks, int nvb, int64_t ncp, DevSpace sp,
-                               double* __restrict__ Nx, double* __restrict__ scal) {
+__global__ void k_class22_marg(const double* __restrict__ vpart, int nx_blocks, int nvb, int64_t ncp, int z0,
+                               DevSpace sp, double* __restrict__ Nx, double* __restrict__ scal) {
+  // vpart holds core pairs z0 .. z0 + ncp - 1 (a chunk)
   // one block per correlated virtual a, per correlated core i, and one for
   // the two scalars; block-strided fixed-order sums
   __shared__ double sh[32];
@@ -622,7 +663,7 @@ __global__ void k_class22_marg(const double* __restrict__ vpart, int nx_blocks, 
     for (int64_t idx = threadIdx.x; idx < ncp * per; idx += blockDim.x) {
       const int64_t z = idx / per;
       int iu, ju;
-      pair_decode(z, iu, ju);
+      pair_decode(z0 + z, iu, ju);
       if (iu == i || ju == i) s += vpart[idx * 19 + 16];
     }
   } else {

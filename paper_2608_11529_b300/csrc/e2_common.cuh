@@ -50,9 +50,9 @@ struct RowInfo {
 struct AdjOut {
   double2* T;
   double* Hm;      // optional: s df/dD per element of the chunk (same layout as T)
-  double* Hrow;
-  double* Hcol;
-  double* scal;
+  double* Hrow;    // [Mc][column tiles]: per-tile row sums of eta, rows local to the chunk
+  double* Hcol;    // [row tiles of the chunk][N]: per-tile column sums of eta
+  double* scal;    // [row tiles of the chunk][column tiles][2]: the two per-tile scalars
   int64_t m_base, Mc;
   double s;
   const double2* g1;

@@ -57,19 +57,68 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
   double2* Gt = (double2*)B(P->o_bGt);
   double* Hocc = (double*)B(P->o_bHocc);
   double* Zm = (double*)B(P->o_bZ);
-  double* Zs = (double*)B(P->o_bZs);
   if (want_B) {
     cudaMemsetAsync(Ge, 0, 8 * (size_t)std::max(nx, 1) * std::max(nx, 1), st);
     cudaMemsetAsync(Gea, 0, 8 * (size_t)std::max(nx, 1) * std::max(na, 1), st);
     cudaMemsetAsync(Ntt, 0, 8 * (size_t)na * na, st);
     cudaMemsetAsync(Gt, 0, 16 * (size_t)npair * npair, st);
   }
-  // denominators of rows with external indices: Ge += Z^T diag(hsum) Z, Gea += Z^T Hocc
-  auto zpair = [&](const RowInfo* rows, int64_t M, const double* hs, const double* hocc) {
-    (k_zmat<<<blocks(M * nx), 256, 0, st>>>(rows, M, nx, Zm), ++g_launches);
-    (k_zscale<<<blocks(M * nx), 256, 0, st>>>(Zm, hs, M, nx, Zs), ++g_launches);
-    dgemm(st, nx, nx, M, Zm, 1, nx, Zs, nx, 1, Ge, nx, 1);
-    dgemm(st, nx, na, M, Zm, 1, nx, hocc, na, 1, Gea, na, 1);
+  // denominators of rows with external spinors: with z_e the signed incidence
+  // of row e (+1 on its particles, -1 on its holes),
+  //   Ge[x][y] += sum_e hs[e] z_e[x] z_e[y],  Gea[x][t] += sum_e z_e[x] hocc[e][t],
+  // formed from marginals of hs and hocc over the (hole tuple, particle tuple)
+  // structure of the class's rows.
+  auto zpair = [&](int cls, const double* hs, const double* hocc) {
+    const int ncc = P->ncc, nvc = P->nvc;
+    const int64_t ncp = pairs(ncc), nvp = pairs(nvc);
+    int kh = 0, kp = 0;
+    switch (cls) {
+      case 2: kp = 2; break;
+      case 5: kh = 1; kp = 2; break;
+      case 7: kh = 2; kp = 1; break;
+      case 4: kh = 1; kp = 1; break;
+      case 6: kh = 2; break;
+      case 1: kp = 1; break;
+      case 3: kh = 1; break;
+      case 8: kh = 2; kp = 2; break;
+      default: return;
+    }
+    const int64_t nh = kh == 0 ? 1 : kh == 1 ? ncc : ncp, np_ = kp == 0 ? 1 : kp == 1 ? nvc : nvp;
+    if (nh == 0 || np_ == 0) return;
+    double* Sp = Zm;              // [np]      sum over holes
+    double* Sh = Sp + np_;        // [nh]      sum over particles
+    double* Spo = Sh + nh;        // [np][na]  hocc summed over holes
+    double* Sho = Spo + np_ * na; // [nh][na]  hocc summed over particles
+    double* Cr = Sho + nh * na;   // [nh][nvc] per hole tuple, summed over the particle tuples holding a
+    const int64_t dg = nx + 1;    // stride of Ge's diagonal
+    (k_colsum<<<blocks(np_), 256, 0, st>>>(hs, nh, np_, 0, Sp), ++g_launches);
+    if (np_ >= 256)
+      (k_rowsum_wide<<<(unsigned)nh, 256, 0, st>>>(hs, np_, 0, Sh), ++g_launches);
+    else
+      (k_rowsum<<<blocks(nh), 256, 0, st>>>(hs, nh, np_, 0, Sh), ++g_launches);
+    if (kp) {
+      (k_tmarg<<<blocks(nvc), 256, 0, st>>>(Sp, 1, np_, 1, kp, nvc, 1.0, 1, Ge + ncc * dg, 0, dg, 0), ++g_launches);
+      if (kp == 2)
+        (k_pairplace<<<blocks((int64_t)nvc * nvc), 256, 0, st>>>(Sp, nvc, Ge + (int64_t)ncc * nx + ncc, nx),
+         ++g_launches);
+      (k_colsum<<<blocks(np_ * na), 256, 0, st>>>(hocc, nh, np_ * na, 0, Spo), ++g_launches);
+      (k_tmarg<<<blocks((int64_t)nvc * na), 256, 0, st>>>(Spo, 1, np_, na, kp, nvc, 1.0, 1, Gea + (int64_t)ncc * na,
+                                                         0, na, 1), ++g_launches);
+    }
+    if (kh) {
+      (k_tmarg<<<blocks(ncc), 256, 0, st>>>(Sh, 1, nh, 1, kh, ncc, 1.0, 1, Ge, 0, dg, 0), ++g_launches);
+      if (kh == 2) (k_pairplace<<<blocks((int64_t)ncc * ncc), 256, 0, st>>>(Sh, ncc, Ge, nx), ++g_launches);
+      (k_midsum<<<(unsigned)nh, 256, 0, st>>>(hocc, np_, na, Sho), ++g_launches);
+      (k_tmarg<<<blocks((int64_t)ncc * na), 256, 0, st>>>(Sho, 1, nh, na, kh, ncc, -1.0, 1, Gea, 0, na, 1),
+       ++g_launches);
+    }
+    if (kh && kp) {  // hole-particle entries, both orders
+      (k_tmarg<<<blocks(nh * nvc), 256, 0, st>>>(hs, nh, np_, 1, kp, nvc, 1.0, 0, Cr, nvc, 1, 0), ++g_launches);
+      (k_tmarg<<<blocks((int64_t)ncc * nvc), 256, 0, st>>>(Cr, 1, nh, nvc, kh, ncc, -1.0, 1, Ge + ncc, 0, nx, 1),
+       ++g_launches);
+      (k_tmarg<<<blocks((int64_t)ncc * nvc), 256, 0, st>>>(Cr, 1, nh, nvc, kh, ncc, -1.0, 1, Ge + (int64_t)ncc * nx,
+                                                          0, 1, nx), ++g_launches);
+    }
   };
   const bool on[E2_NCLASS] = {P->part_cnt[0] > 0, P->part_cnt[1] > 0, P->part_cnt[2] > 0, P->part_cnt[3] > 0,
                               P->part_cnt[4] > 0, P->part_cnt[5] > 0, P->part_cnt[6] > 0, P->part_cnt[7] > 0,
@@ -130,6 +179,13 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         dim3 grid((unsigned)((Mc + 63) / 64), (unsigned)ct);
         (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
                                             L.eA, X.E0p + r, b, nullptr, adj, col_tiles(P, ws, r, cls)), ++g_launches);
+        // per-tile sums of this chunk: row sums of eta, column sums per row tile, the scalars
+        {
+          const int64_t rtc = (Mc + 63) / 64;
+          (k_rowsum<<<blocks(Mc), 256, 0, st>>>(adj.Hrow, Mc, ct, 0, hsum + m0), ++g_launches);
+          (k_colsum<<<blocks(N), 256, 0, st>>>(adj.Hcol, rtc, N, m0 > 0, hA), ++g_launches);
+          (k_scalsum<<<1, 256, 0, st>>>(adj.scal, rtc * ct, scal), ++g_launches);
+        }
         // Gamma_D[x][A] += sum_e W[e][x] conj(T[e][A]) (split over the rows of the chunk)
         if (tiled)
           zgemm_gd_tiles(st, cp, ctl, W + m0 * Kp, (int)Kp, adj.T, N, Mc, (double2*)B(P->o_bGDc), m0 > 0);
@@ -158,13 +214,10 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         (k_gd_scatter<<<(unsigned)cp.tiles, 256, 0, st>>>(ctl, (const double2*)B(P->o_bGDc), N, GDfor[cls]),
          ++g_launches);
       if (cls == 4) (k_fock11<<<blocks(M), 256, 0, st>>>((const double2*)B(P->o_bRowdot), X.sp, Gf), ++g_launches);
-      (k_rowsum<<<blocks(M), 256, 0, st>>>((const double*)B(P->o_bHrow), M, ct, 0, hsum), ++g_launches);
       (k_xmarg<<<P->nx, 256, 0, st>>>((const RowInfo*)(ws + P->o_rows[cls]), hsum, M, P->nx, Nx), ++g_launches);
-      (k_colsum<<<blocks(N), 256, 0, st>>>((const double*)B(P->o_bHcol), rt, N, 0, hA), ++g_launches);
       (k_amarg<<<na, 256, 0, st>>>(L, hA, Nt), ++g_launches);
-      (k_scalsum<<<1, 256, 0, st>>>((const double*)B(P->o_bScalT), rt * ct, scal), ++g_launches);
       if (want_B) {
-        zpair((const RowInfo*)(ws + P->o_rows[cls]), M, hsum, Hocc);
+        zpair(cls, hsum, Hocc);
         (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
         const int modes[E2_NCLASS] = {-1, -1, INT_W02, -1, INT_W11, INT_W12, INT_W20, INT_W21, -1};
         const int cols[E2_NCLASS] = {0, 0, P->ntp, 0, 1 + na * na, na, P->ntp, na, 0};
@@ -176,25 +229,30 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
     double* c22 = nullptr;
     if (on[8]) {
       const DevList& L = Lc[8];
-      const int64_t nyb = (int64_t)P->nvb * (P->nvb + 1) / 2, yz = nyb * P->ncp;
-      dim3 grid(blocks(L.n), (unsigned)nyb, (unsigned)P->ncp);
-      (k_class22_bwd<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b,
-                                           P->nvb, s, g1, (double*)B(P->o_bC22p), (double*)B(P->o_bH22p),
-                                           (double*)B(P->o_bV22), poff(8)), ++g_launches);
+      const int64_t nyb = (int64_t)P->nvb * (P->nvb + 1) / 2;
       c22 = (double*)B(P->o_bC22);
-      (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bC22p), yz, L.n, 0, c22), ++g_launches);
-      (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bH22p), yz, L.n, 0, hA), ++g_launches);
+      // chunks of core pairs: partials of one chunk, reduced before the next
+      for (int z0 = 0; z0 < (int)P->ncp; z0 += P->z22_chunk) {
+        const int zc = (int)std::min<int64_t>(P->z22_chunk, P->ncp - z0);
+        const int64_t yz = nyb * zc;
+        dim3 grid(blocks(L.n), (unsigned)nyb, (unsigned)zc);
+        (k_class22_bwd<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b,
+                                             P->nvb, s, g1, (double*)B(P->o_bC22p), (double*)B(P->o_bH22p),
+                                             (double*)B(P->o_bV22), poff(8), z0), ++g_launches);
+        (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bC22p), yz, L.n, z0 > 0, c22), ++g_launches);
+        (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bH22p), yz, L.n, z0 > 0, hA), ++g_launches);
+        (k_class22_marg<<<(unsigned)(P->nvc + P->ncc + 1), 256, 0, st>>>((const double*)B(P->o_bV22),
+                                                                     (int)blocks(L.n), P->nvb, zc, z0, X.sp, Nx,
+                                                                     scal), ++g_launches);
+      }
       (k_amarg<<<na, 256, 0, st>>>(L, hA, Nt), ++g_launches);
-      (k_class22_marg<<<(unsigned)(P->nvc + P->ncc + 1), 256, 0, st>>>((const double*)B(P->o_bV22), (int)blocks(L.n),
-                                                                   P->nvb, P->ncp, X.sp, Nx, scal), ++g_launches);
       if (want_B) {
         const int64_t M22 = P->ncp * P->nvp;
         double* hs22 = (double*)B(P->o_bHs22);
         double* P22 = (double*)B(P->o_bP22);
         (k_class22_rows<<<(unsigned)M22, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G,
                                                        X.E0p + r, b, s, g1, hs22, Hocc, P22), ++g_launches);
-        (k_rows<<<blocks(M22), 256, 0, st>>>(8, X.sp, X.epsh, X.G, M22, (RowInfo*)B(P->o_bR22)), ++g_launches);
-        zpair((const RowInfo*)B(P->o_bR22), M22, hs22, Hocc);
+        zpair(8, hs22, Hocc);
         (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
         const int Lt = d.L_coulomb + d.L_extra;
         (k_integrals<<<blocks(M22), 256, 0, st>>>(INT_G22C, X.sp, X.Bo, X.wt, Lt, X.f, P->ncp, (int)P->nvp,
@@ -240,10 +298,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       if (want_B) {
         (k_rowsum_wide<<<(unsigned)nrow, 256, 0, st>>>(Hg, L.n, 0, hsum), ++g_launches);
         (k_hocc<<<(unsigned)nrow, 256, 0, st>>>(Hg, L, na, Hocc), ++g_launches);
-        if (cls != 0) {
-          (k_rows<<<blocks(nrow), 256, 0, st>>>(cls, X.sp, X.epsh, X.G, nrow, (RowInfo*)B(P->o_bRg)), ++g_launches);
-          zpair((const RowInfo*)B(P->o_bRg), nrow, hsum, Hocc);
-        }
+        zpair(cls, hsum, Hocc);
         (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
       }
       double2* Tsh = (double2*)B(P->o_bTsh);

@@ -102,13 +102,15 @@ struct e2_problem {
   size_t o_sV, o_sS, o_sX, o_sR, o_sD, o_sT, o_sG, o_sY, solve_bytes;
   // adjoint region
   size_t o_dstart;                   // first D table of the root-0 slot
-  int64_t chunk_rows[E2_NCLASS];     // dense-class rows per adjoint chunk
+  int64_t chunk_rows[E2_NCLASS] = {};  // dense-class rows per adjoint chunk
+  int64_t chunk_rows_plan[E2_NCLASS] = {};  // the planned (largest) values of the two chunk sizes
+  int z22_chunk = 1, z22_plan = 1;   // core pairs per chunk of the (2,2) adjoint
   size_t o_gD, o_bT, o_bHrow, o_bHcol, o_bScalT, o_bHsum, o_bHA, o_bRowdot;
   size_t o_bGT, o_bGH, o_bGV, o_bC22p, o_bH22p, o_bV22, o_bC22, o_bGc, o_bSig, o_bGf, o_bNx, o_bNt, o_bNd, o_bScal;
   // factor gradient
   int64_t npair;
-  size_t o_bGW[E2_NCLASS], o_bHm, o_bHocc, o_bZ, o_bZs, o_bGe, o_bGea, o_bNtt, o_bGG, o_bGt, o_bGh, o_bTsh;
-  size_t o_bGX01, o_bGX10, o_bGX00, o_bR22, o_bHs22, o_bP22, o_bG22c, o_bGg22, o_bCs, o_bGB, o_bFtr, o_bGw, o_bRg;
+  size_t o_bGW[E2_NCLASS], o_bHm, o_bHocc, o_bZ, o_bGe, o_bGea, o_bNtt, o_bGG, o_bGt, o_bGh, o_bTsh;
+  size_t o_bGX01, o_bGX10, o_bGX00, o_bHs22, o_bP22, o_bG22c, o_bGg22, o_bCs, o_bGB, o_bFtr, o_bGw;
   size_t o_bPart, bpart_bytes;  // split-K segments
   size_t tsh_bytes;
   size_t o_bGDc, o_bGWc, gwc_bytes;

@@ -675,19 +675,19 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
       double s = 0.0;
       for (int k = 0; k < 16; ++k) s += sRow[tid][k];
       const int64_t row = m0 + tid;
-      if (row < mend) adj.Hrow[row * n_tile_n + tile_n] = s;
+      if (row < mend) adj.Hrow[(row - adj.m_base) * n_tile_n + tile_n] = s;  // chunk-local rows
     } else if (tid < GBM + GBN) {
       const int c = tid - GBM;
       double s = 0.0;
       for (int k = 0; k < 16; ++k) s += sColP[c][k];
       const int64_t col = sCol[c];
-      if (col >= 0) adj.Hcol[((adj.m_base / GBM) + tile_m) * N + col] = s;
+      if (col >= 0) adj.Hcol[tile_m * N + col] = s;  // chunk-local row tiles
     }
     const double fs = block_sum(acc2, sh);  // sum f over the tile, as the forward sums it
     const double t2s = adj.s * inv_n * fs;  // sum s (df/dv) v
     double ts = block_sum(acc, sh);
     if (tid == 0) {
-      const int64_t slot = ((adj.m_base / GBM) + tile_m) * n_tile_n + tile_n;
+      const int64_t slot = tile_m * n_tile_n + tile_n;  // chunk-local
       adj.scal[2 * slot] = ts;
       adj.scal[2 * slot + 1] = t2s;
     }

@@ -80,9 +80,9 @@ __global__ void k_rowdot(const double2* T, const double2* d, int64_t N, double2*
 __global__ void k_fock11(const double2* rowdot, DevSpace sp, double2* Gf);
 __global__ void k_class22_bwd(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
                               const double* G, const double* E0p, double b, int nvb, double s, const double2* g1,
-                              double* cpart, double* hpart, double* vpart, double* part);
-__global__ void k_class22_marg(const double* vpart, int nx_blocks, int nvb, int64_t ncp, DevSpace sp, double* Nx,
-                               double* scal);
+                              double* cpart, double* hpart, double* vpart, double* part, int z0);
+__global__ void k_class22_marg(const double* vpart, int nx_blocks, int nvb, int64_t ncp, int z0, DevSpace sp,
+                               double* Nx, double* scal);
 __global__ void k_gather_t(int cls, DevList Lx, DevList L12, DevList L02, DevList L21, DevList L11, DevDas das,
                            DevSpace sp, const int64_t* binom, const double2* DT, const double2* DTU, const double2* DTD,
                            const double2* DTDU, const double2* X01, const double2* X10, const double2* X00,
@@ -107,8 +107,10 @@ __global__ void k_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_
                         int64_t sbk, int64_t sbn, double* C, int64_t ldc, int beta, int64_t kseg, int64_t czs);
 __global__ void k_dacc(const double* part, int nseg, int64_t ps, int64_t count, double* out);
 __global__ void k_hocc(const double* H, DevList Ls, int na, double* Hocc);
-__global__ void k_zmat(const RowInfo* rows, int64_t M, int nx, double* Z);
-__global__ void k_zscale(const double* Z, const double* hsum, int64_t M, int nx, double* out);
+__global__ void k_tmarg(const double* in, int64_t nb, int64_t nt, int w, int arity, int ns, double sign, int acc,
+                        double* out, int64_t ob, int64_t os, int64_t oc);
+__global__ void k_pairplace(const double* in, int ns, double* out, int64_t ldo);
+__global__ void k_midsum(const double* in, int64_t np, int w, double* out);
 __global__ void k_gint(int mode, DevSpace sp, const double2* Gam, int64_t rows, int cols, int ld, double2* Gt,
                        int64_t npair);
 __global__ void k_tshift(DevList Lx, DevList Ltab, DevDas das, const int64_t* binom, const double2* T, int row0,

@@ -489,15 +489,17 @@ e2_status build_plan(e2_problem* P) {
         rows_fit = std::min<int64_t>(rows_fit, (int64_t)(gwbudget / (16 * (size_t)P->cplan[c].krows)) / 64 * 64);
       rows_fit = std::max<int64_t>(64, rows_fit);
       P->chunk_rows[c] = std::min<int64_t>(rows_fit, (Mc + 63) / 64 * 64);
-      const int64_t rt = (Mc + 63) / 64, ct = (Nc + 63) / 64;
+      const int64_t ct = (Nc + 63) / 64;
       tmax = std::max(tmax, (size_t)16 * P->chunk_rows[c] * Nc);
       if (P->cplan[c].built) {
         gdc = std::max(gdc, (size_t)16 * P->cplan[c].krows * 64);
         gwc = std::max(gwc, (size_t)16 * P->chunk_rows[c] * P->cplan[c].krows);
       }
-      hrow = std::max(hrow, (size_t)8 * Mc * ct);
-      hcol = std::max(hcol, (size_t)8 * rt * Nc);
-      scalt = std::max(scalt, (size_t)16 * rt * ct);
+      // per-tile sums of one row chunk, reduced before the next chunk
+      const int64_t rtc = P->chunk_rows[c] / 64;
+      hrow = std::max(hrow, (size_t)8 * P->chunk_rows[c] * ct);
+      hcol = std::max(hcol, (size_t)8 * rtc * Nc);
+      scalt = std::max(scalt, (size_t)16 * rtc * ct);
       hsum = std::max(hsum, (size_t)8 * Mc);
     }
     for (size_t li = 0; li < P->lists.size(); ++li) hA = std::max(hA, (size_t)8 * P->lists[li].n);
@@ -506,7 +508,13 @@ e2_status build_plan(e2_problem* P) {
       if (P->list_of[c] >= 0) gmax = std::max(gmax, (size_t)P->M[c] * P->lists[P->list_of[c]].n);
     const int64_t nyb = (int64_t)P->nvb * (P->nvb + 1) / 2;
     const int64_t np22 = lsize(8), xb22 = (np22 + 255) / 256;
-    const size_t yz = (size_t)std::max<int64_t>(1, nyb * P->ncp);
+    // class (2,2) adjoint in chunks of core pairs whose partials fit 2 GiB
+    const size_t per_z = 8 * (size_t)nyb * (2 * (size_t)std::max<int64_t>(np22, 1) + 19 * (size_t)std::max<int64_t>(xb22, 1));
+    P->z22_chunk = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(P->ncp, 1),
+                                                             (int64_t)((size_t(2) << 30) / std::max<size_t>(per_z, 1))));
+    const size_t yz = (size_t)std::max<int64_t>(1, nyb * P->z22_chunk);
+    P->z22_plan = P->z22_chunk;
+    for (int c = 0; c < E2_NCLASS; ++c) P->chunk_rows_plan[c] = P->chunk_rows[c];
     P->o_gD = ws.take(P->d_stride);
     P->o_bT = ws.take(tmax);
     P->o_bGDc = ws.take(gdc);  // compacted Gamma_D / Gamma_W of a column-tiled class
@@ -535,7 +543,7 @@ e2_status build_plan(e2_problem* P) {
     // factor gradient
     const int64_t npair = (int64_t)P->n * P->nocc;
     P->npair = npair;
-    size_t hm = 8, hocc = 8, zz = 8, tsh = 16;
+    size_t hm = 8, hocc = 8, tsh = 16;
     for (int c = 0; c < E2_NCLASS; ++c) P->o_bGW[c] = 0;
     for (int c : {2, 5, 7, 4, 6}) {
       const int64_t Mc = P->M[c], Nc = lsize(c);
@@ -543,16 +551,16 @@ e2_status build_plan(e2_problem* P) {
       P->o_bGW[c] = ws.take(16 * (size_t)Mc * P->Kp[c]);
       hm = std::max(hm, (size_t)8 * P->chunk_rows[c] * Nc);
       hocc = std::max(hocc, (size_t)8 * Mc * P->na);
-      zz = std::max(zz, (size_t)8 * Mc * P->nx);
     }
     const int64_t M22 = P->ncp * P->nvp;
     hocc = std::max(hocc, (size_t)8 * std::max<int64_t>(M22, 1) * P->na);
-    zz = std::max(zz, (size_t)8 * std::max<int64_t>(M22, 1) * P->nx);
     for (int c : {1, 3, 0})
-      if (P->list_of[c] >= 0) {
-        hocc = std::max(hocc, (size_t)8 * P->M[c] * P->na);
-        zz = std::max(zz, (size_t)8 * P->M[c] * P->nx);
-      }
+      if (P->list_of[c] >= 0) hocc = std::max(hocc, (size_t)8 * P->M[c] * P->na);
+    // marginals of the per-row sums over hole / particle tuples (at most
+    // C(n_vc,2) particle and C(n_cc,2) hole tuples)
+    const size_t tp = (size_t)std::max<int64_t>(std::max<int64_t>(pairs(P->nvc), P->nvc), 1);
+    const size_t th = (size_t)std::max<int64_t>(std::max<int64_t>(pairs(P->ncc), P->ncc), 1);
+    const size_t zz = 8 * (tp * (1 + (size_t)P->na) + th * (1 + (size_t)P->na + (size_t)std::max(P->nvc, 1)));
     {  // shifted amplitudes of the gather classes: all shifts of a row chunk
       const size_t n01 = 16 * (size_t)P->na * std::max<int64_t>(lsize(2), 1);
       const size_t n10 = 16 * (size_t)std::max(P->ntp, 1) * std::max<int64_t>(lsize(5), 1);
@@ -565,8 +573,6 @@ e2_status build_plan(e2_problem* P) {
     P->o_bHm = ws.take(hm);
     P->o_bHocc = ws.take(hocc);
     P->o_bZ = ws.take(zz);
-    P->o_bZs = ws.take(zz);
-    P->o_bRg = ws.take(sizeof(RowInfo) * (size_t)std::max<int64_t>(std::max(P->nvc, P->ncc), 1));
     P->o_bGe = ws.take(8 * (size_t)std::max(P->nx, 1) * std::max(P->nx, 1));
     P->o_bGea = ws.take(8 * (size_t)std::max(P->nx, 1) * std::max(P->na, 1));
     P->o_bNtt = ws.take(8 * (size_t)P->na * P->na);
@@ -577,7 +583,6 @@ e2_status build_plan(e2_problem* P) {
     P->o_bGX01 = ws.take(16 * (size_t)std::max<int64_t>((int64_t)P->nvc * P->na * P->ntp, 1));
     P->o_bGX10 = ws.take(16 * (size_t)std::max<int64_t>((int64_t)P->ncc * P->ntp * P->na, 1));
     P->o_bGX00 = ws.take(16 * (size_t)std::max<int64_t>((int64_t)P->ntp * P->ntp, 1));
-    P->o_bR22 = ws.take(sizeof(RowInfo) * (size_t)std::max<int64_t>(M22, 1));
     P->o_bHs22 = ws.take(8 * (size_t)std::max<int64_t>(M22, 1));
     P->o_bP22 = ws.take(8 * (size_t)std::max<int64_t>(M22, 1));
     P->o_bG22c = ws.take(16 * (size_t)std::max<int64_t>(M22, 1));
@@ -712,6 +717,16 @@ e2_status e2_class_tiles_copy(const e2_problem* P, int cls, int32_t* perm, int32
   std::copy(cp.perm.begin(), cp.perm.end(), perm);
   std::copy(cp.tdesc.begin(), cp.tdesc.end(), tdesc);
   std::copy(cp.klist.begin(), cp.klist.end(), klist);
+  return E2_OK;
+}
+
+e2_status e2_set_adjoint_chunks(e2_problem* P, int64_t rows, int core_pairs) {
+  if (!P) return E2_ERR_INVALID_ARG;
+  for (int c = 0; c < E2_NCLASS; ++c) {
+    const int64_t plan = P->chunk_rows_plan[c];
+    P->chunk_rows[c] = (rows <= 0 || plan == 0) ? plan : std::min<int64_t>(plan, std::max<int64_t>(64, rows / 64 * 64));
+  }
+  P->z22_chunk = core_pairs <= 0 ? P->z22_plan : std::min(P->z22_plan, core_pairs);
   return E2_OK;
 }
 
