@@ -285,6 +285,29 @@ E2_API e2_status e2_class_tiles(const e2_problem* prob, int cls, int64_t* tiles,
  * class has no plan. */
 E2_API e2_status e2_class_tiles_copy(const e2_problem* prob, int cls, int32_t* perm, int32_t* tdesc, int32_t* klist);
 E2_API e2_status e2_set_class_tiles(e2_problem* prob, int cls, int on);
+
+/* Arithmetic of the dense-class contraction (step a7; no counterpart in the
+ * paper, which fixes only the FP64 accuracy of the result).
+ *   E2_CONTRACT_FP64   complex FP64 products on the FP64 tensor pipe
+ *                      (mma.sync f64), plain or column-tiled;
+ *   E2_CONTRACT_SLICED the error-free slicing of Ozaki et al.: five 8-bit
+ *                      slices of each operand on the bf16 tensor pipe with
+ *                      exact FP32 accumulation of the leading levels, and the
+ *                      Epstein-Nesbet epilogue in float-float arithmetic
+ *                      (each V to about 2^-40 of its row and string scale;
+ *                      about 48 significant bits in the epilogue).  Available
+ *                      for (0,2), (1,2), (2,1), (2,0) when the real
+ *                      contraction length 2 K is at most 256 and the slices
+ *                      fit 16 GiB; the default there.
+ * e2_set_contraction returns E2_ERR_UNSUPPORTED for a class without the
+ * sliced plan; e2_contraction reports the mode in use and whether the sliced
+ * plan exists (either output may be NULL).  The backward pass forms its
+ * amplitudes in FP64 either way; its E2 output comes from the forward's
+ * kernel, so it stays bitwise equal to e2_forward's. */
+#define E2_CONTRACT_FP64 0
+#define E2_CONTRACT_SLICED 1
+E2_API e2_status e2_set_contraction(e2_problem* prob, int cls, int mode);
+E2_API e2_status e2_contraction(const e2_problem* prob, int cls, int* mode, int* sliced_available);
 E2_API e2_status e2_autotune(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
                              void* stream, float* ms_out);
 

@@ -69,6 +69,10 @@ def load():
         L.e2_set_class_tiles.restype = C.c_int
         L.e2_set_adjoint_chunks.argtypes = [C.c_void_p, C.c_int64, C.c_int]
         L.e2_set_adjoint_chunks.restype = C.c_int
+        L.e2_set_contraction.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.e2_set_contraction.restype = C.c_int
+        L.e2_contraction.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.e2_contraction.restype = C.c_int
         L.e2_autotune.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p]
         L.e2_autotune.restype = C.c_int
         L.e2_backward_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
@@ -278,6 +282,16 @@ class E2Problem:
 
     def set_class_tiles(self, cls, on):
         _check(load().e2_set_class_tiles(self._h, cls, int(bool(on))))
+
+    def set_contraction(self, cls, sliced):
+        """Dense class cls on the sliced bf16 contraction (True) or FP64 (False)."""
+        _check(load().e2_set_contraction(self._h, cls, 1 if sliced else 0))
+
+    def contraction(self, cls):
+        """(sliced in use, sliced available) for class cls."""
+        m, a = C.c_int(), C.c_int()
+        _check(load().e2_contraction(self._h, cls, C.byref(m), C.byref(a)))
+        return bool(m.value), bool(a.value)
 
     def set_adjoint_chunks(self, rows=0, core_pairs=0):
         """Run the adjoint in smaller chunks than planned (0 restores the plan)."""

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libe2.so")
-SOURCES = ["e2_kernels.cu", "e2_adjoint.cu", "e2_plan.cu", "e2_api.cu", "e2_batch.cu", "e2_grad.cu", "e2_solver.cu"]
+SOURCES = ["e2_kernels.cu", "e2_adjoint.cu", "e2_ozaki.cu", "e2_plan.cu", "e2_api.cu", "e2_batch.cu", "e2_grad.cu", "e2_solver.cu"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
          "-shared", "-cudart", "static", "-Xcompiler", "-fvisibility=hidden"]

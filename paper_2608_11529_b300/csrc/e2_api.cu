@@ -75,6 +75,14 @@ ColTiles col_tiles(const e2_problem* P, unsigned char* ws, int r, int cls) {
                   (const double2*)(slot_base(P, ws, r) + cp.o_Dc)};
 }
 
+OzOperands oz_operands(const e2_problem* P, unsigned char* ws, int r, int cls) {
+  const HostList& L = P->lists[P->list_of[cls]];
+  unsigned char* sb = slot_base(P, ws, r);
+  return OzOperands{(const __nv_bfloat16*)(ws + P->o_ozA[cls]), P->oz_mpad[cls], (const int*)(ws + P->o_ozRx[cls]),
+                    (const __nv_bfloat16*)(sb + P->o_ozB[cls]), P->oz_npad[cls], (const int*)(sb + P->o_ozCx[cls]),
+                    P->oz_kq[cls], (const float2*)(ws + L.o_Udf), (const float2*)(ws + L.o_eAdf)};
+}
+
 // Coupling tensors D^x_A = <A|x|c> of one reference vector c; `all` = false
 // builds only the two that the active sigma needs.
 void build_tables(const e2_problem* P, unsigned char* ws, cudaStream_t st, const double2* c, const Tabs& T, bool all) {
@@ -192,6 +200,11 @@ e2_status setup_common(e2_problem* P, const e2_inputs* in, unsigned char* ws, cu
     (k_unrank<<<blocks(L.n), 256, 0, st>>>(L, P->das, X.binom), ++g_launches);
     (k_eA<<<blocks(L.n), 256, 0, st>>>(L, X.epsh, X.G, n, X.sp.a0), ++g_launches);
     (k_U<<<blocks((int64_t)(P->nx + 1) * L.n), 256, 0, st>>>(L, X.sp, X.G), ++g_launches);
+    const HostList& H = P->lists[li];
+    if (H.df)
+      (k_oz_tables<<<blocks((int64_t)(P->nx + 1) * L.n), 256, 0, st>>>(L.eA, L.U, L.n, P->nx + 1,
+                                                                      (float2*)(ws + H.o_eAdf),
+                                                                      (float2*)(ws + H.o_Udf)), ++g_launches);
   }
   if (P->ntp > 0)
     (k_integrals<<<blocks((int64_t)P->ntp * P->ntp), 256, 0, st>>>(INT_X00, X.sp, X.Bo, X.wt, Lt, X.f, P->ntp, P->ntp,
@@ -262,6 +275,12 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
   if (P->part_cnt[3] > 0)
     (k_integrals<<<blocks((int64_t)P->ncc * P->ntp * na), 256, 0, st>>>(INT_X10, X.sp, X.Bo, X.wt, Lt, X.f, P->ncc,
                                                                        P->ntp * na, P->ntp * na, ws + P->o_X10), ++g_launches);
+  // row slices of W for the classes on the sliced contraction
+  for (int c : {2, 5, 7, 6})
+    if (P->use_oz[c] && P->part_cnt[c] > 0)
+      (k_oz_split_rows<<<(unsigned)(P->oz_mpad[c] / 8), 256, 0, st>>>(
+           (const double2*)(ws + P->o_W[c]), P->M[c], P->Kp[c], P->Kp[c], P->oz_kq[c], P->oz_mpad[c],
+           (__nv_bfloat16*)(ws + P->o_ozA[c]), (int*)(ws + P->o_ozRx[c])), ++g_launches);
 }
 
 
@@ -296,6 +315,14 @@ void prepare_root(e2_problem* P, unsigned char* ws, cudaStream_t st, const doubl
       const ColTiles ct = col_tiles(P, ws, r, cls);
       (k_dcompact<<<(unsigned)P->cplan[cls].tiles, 256, 0, st>>>(Dcls[cls], P->lists[P->list_of[cls]].n, ct,
                                                                  (double2*)ct.Dc), ++g_launches);
+    }
+  for (int cls : {2, 5, 7, 6})
+    if (P->use_oz[cls] && P->part_cnt[cls] > 0) {
+      const int64_t N = P->lists[P->list_of[cls]].n;
+      unsigned char* sb = slot_base(P, ws, r);
+      (k_oz_split_cols<<<(unsigned)(P->oz_npad[cls] / 32), 256, 0, st>>>(
+           Dcls[cls], P->Kp[cls], N, P->oz_kq[cls], P->oz_npad[cls], (__nv_bfloat16*)(sb + P->o_ozB[cls]),
+           (int*)(sb + P->o_ozCx[cls])), ++g_launches);
     }
   double2* g1 = (double2*)(ws + P->o_g1 + P->g_stride * r);
   double2* g2 = (double2*)(ws + P->o_g2 + P->g_stride * r);
@@ -370,9 +397,13 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
       const DevList& L = Lc[cls];
       dim3 grid((unsigned)((P->M[cls] + 63) / 64), (unsigned)((L.n + 63) / 64));
       mark(cls, 0);
-      (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Dfor[cls], P->M[cls], L.n, P->Kp[cls],
-                                         (const RowInfo*)(ws + P->o_rows[cls]), L.U, L.eA, X.E0p + r, b, poff(cls), AdjOut{},
-                                         col_tiles(P, ws, r, cls)), ++g_launches);
+      if (P->use_oz[cls])
+        launch_class_oz(st, oz_operands(P, ws, r, cls), P->M[cls], L.n, (const RowInfo*)(ws + P->o_rows[cls]),
+                        X.E0p + r, b, poff(cls));
+      else
+        (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Dfor[cls], P->M[cls], L.n, P->Kp[cls],
+                                           (const RowInfo*)(ws + P->o_rows[cls]), L.U, L.eA, X.E0p + r, b, poff(cls),
+                                           AdjOut{}, col_tiles(P, ws, r, cls)), ++g_launches);
       mark(cls, 1);
     }
     launch_sparse_classes(P, ws, st, r, c, mark);
@@ -395,7 +426,9 @@ e2_status e2_partials(const e2_problem* P, const void* workspace, int root, int 
   const bool dense = cls == 2 || cls == 5 || cls == 7 || cls == 4 || cls == 6;
   if (row_tiles) *row_tiles = dense ? (P->M[cls] + 63) / 64 : 0;
   if (columns)
-    *columns = P->use_cols[cls] ? (const int32_t*)((const unsigned char*)workspace + P->cplan[cls].o_perm) : nullptr;
+    *columns = (P->use_cols[cls] && !P->use_oz[cls])
+                   ? (const int32_t*)((const unsigned char*)workspace + P->cplan[cls].o_perm)
+                   : nullptr;
   return E2_OK;
 }
 

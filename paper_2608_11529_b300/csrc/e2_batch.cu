@@ -24,7 +24,7 @@ e2_status e2_batch_create(e2_problem* const* jobs, int n_jobs, e2_batch** out) {
     B->jobs.push_back(jobs[j]);
     B->off.push_back(ws.take(jobs[j]->ws_bytes + (size_t)(jobs[j]->d.n_roots - 1) * jobs[j]->d_stride));
     for (int c : {2, 5, 7, 4, 6})
-      if (jobs[j]->part_cnt[c] > 0) {
+      if (jobs[j]->part_cnt[c] > 0 && !jobs[j]->use_oz[c]) {  // sliced classes launch on their own
         njc += jobs[j]->d.n_roots;
         B->n_items += jobs[j]->part_cnt[c] * jobs[j]->d.n_roots;
       }
@@ -73,7 +73,7 @@ e2_status e2_batch_prepare(e2_batch* B, void* workspace, size_t workspace_bytes,
     e2_problem* P = B->jobs[j];
     unsigned char* w = ws + B->off[j];
     for (int c : {2, 5, 7, 4, 6}) {
-      if (P->part_cnt[c] == 0) continue;
+      if (P->part_cnt[c] == 0 || P->use_oz[c]) continue;
       const DevList L = dev_list(P, P->list_of[c], w);
       for (int r = 0; r < P->d.n_roots; ++r) {
         Tabs T = tables(P, w, r);
@@ -156,6 +156,12 @@ e2_status e2_batch_forward(e2_batch* B, const e2_inputs* inputs, void* workspace
   for (size_t j = 0; j < B->jobs.size(); ++j) {
     e2_problem* P = B->jobs[j];
     unsigned char* w = ws + B->off[j];
+    for (int c : {2, 5, 7, 6})
+      if (P->use_oz[c] && P->part_cnt[c] > 0)
+        for (int r = 0; r < P->d.n_roots; ++r)
+          launch_class_oz(st, oz_operands(P, w, r, c), P->M[c], P->lists[P->list_of[c]].n,
+                          (const RowInfo*)(w + P->o_rows[c]), (const double*)(w + P->o_E0p) + r,
+                          P->d.level_shift_b, (double*)(w + P->o_part) + P->part_off[r * E2_NCLASS + c]);
     for (int r = 0; r < P->d.n_roots; ++r)
       launch_sparse_classes(P, w, st, r, (const double2*)inputs[j].c + (int64_t)r * P->lists[P->listP].n, nomark);
     launch_reduce(P, w, st, E2[j], E2_class ? E2_class[j] : nullptr, nullptr);

@@ -1,6 +1,7 @@
 // Internal declarations shared by the host plan and the sm_103a kernels.
 #pragma once
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "e2.h"
@@ -10,6 +11,24 @@ namespace e2 {
 constexpr int kMaxPat = 1024;      // occupation patterns per string list
 constexpr int kMaxKeys = 1 << 20;  // size of the pattern-key table
 constexpr int kBinomN = 65;        // binomial table is [65][65]
+constexpr int OZ_S = 5;            // slices per operand of the sliced bf16 contraction
+
+// Operands of the sliced (bf16) dense-class contraction: row slices of W
+// [OZ_S][Mpad][Kq] with one exponent per row, string slices of D
+// [OZ_S][2 Npad][Kq] with one exponent per string (Kq: the real contraction
+// length 2K padded to a multiple of 32), and float-float copies (hi, lo) of
+// the class list's e_A [n] and U [nx + 1][n].
+struct OzOperands {
+  const __nv_bfloat16* A;
+  int64_t Mpad;
+  const int* rexp;
+  const __nv_bfloat16* B;
+  int64_t Npad;
+  const int* cexp;
+  int Kq;
+  const float2* Udf;
+  const float2* eAdf;
+};
 
 // Active-space partition as the kernels see it.
 struct DevDas {

@@ -138,6 +138,11 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         const double2* Df[E2_NCLASS] = {nullptr, nullptr, T0.DTU, nullptr, T0.DTDU, T0.DT, T0.DTDUD, T0.DTD, nullptr};
         for (int cls : {2, 5, 7, 4, 6}) {
           if (!on[cls]) continue;
+          if (P->use_oz[cls]) {
+            launch_class_oz(st, oz_operands(P, ws, r, cls), P->M[cls], Lc[cls].n,
+                            (const RowInfo*)(ws + P->o_rows[cls]), X.E0p + r, b, poff(cls));
+            continue;
+          }
           dim3 grid((unsigned)((P->M[cls] + 63) / 64), (unsigned)((Lc[cls].n + 63) / 64));
           (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Df[cls], P->M[cls], Lc[cls].n,
                                               P->Kp[cls], (const RowInfo*)(ws + P->o_rows[cls]), Lc[cls].U, Lc[cls].eA,
@@ -172,10 +177,16 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       const bool tiled = P->use_cols[cls] && P->cplan[cls].gran == 8;
       const ColPlan& cp = P->cplan[cls];
       const ColTiles ctl = col_tiles(P, ws, r, cls);
+      // E2 of a class on the sliced contraction: the forward's own kernel, so
+      // that the energies equal e2_forward's bit for bit
+      if (E2 && P->use_oz[cls])
+        launch_class_oz(st, oz_operands(P, ws, r, cls), M, N, (const RowInfo*)(ws + P->o_rows[cls]), X.E0p + r, b,
+                        poff(cls));
+      double* part_adj = P->use_oz[cls] ? nullptr : poff(cls);
       for (int64_t m0 = 0; m0 < M; m0 += P->chunk_rows[cls]) {
         const int64_t Mc = std::min<int64_t>(P->chunk_rows[cls], M - m0);
         AdjOut adj{(double2*)B(P->o_bT), want_B ? (double*)B(P->o_bHm) : nullptr, (double*)B(P->o_bHrow),
-                   (double*)B(P->o_bHcol), (double*)B(P->o_bScalT), m0, Mc, s, g1, poff(cls), rt};
+                   (double*)B(P->o_bHcol), (double*)B(P->o_bScalT), m0, Mc, s, g1, part_adj, rt};
         dim3 grid((unsigned)((Mc + 63) / 64), (unsigned)ct);
         (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
                                             L.eA, X.E0p + r, b, nullptr, adj, col_tiles(P, ws, r, cls)), ++g_launches);

@@ -27,6 +27,8 @@ struct HostList {
   int64_t n = 0;
   std::vector<int64_t> key2off;
   size_t o_str = 0, o_key = 0, o_patoff = 0, o_patocc = 0, o_eA = 0, o_U = 0;
+  bool df = false;               // float-float copies of e_A and U (a class on the sliced path uses the list)
+  size_t o_eAdf = 0, o_Udf = 0;
 };
 
 // Column tiles of a dense class with a compacted contraction (see ColTiles).
@@ -118,6 +120,14 @@ struct e2_problem {
   // compacted column tiles of the dense classes and whether each class uses them
   e2::ColPlan cplan[E2_NCLASS];
   bool use_cols[E2_NCLASS] = {};
+  // sliced bf16 contraction of the dense classes (real length 2 Kp <= 256):
+  // W slices and row exponents beside W, D slices and string exponents in
+  // each root's table slot
+  bool oz_ok[E2_NCLASS] = {};        // planned (buffers laid out)
+  bool use_oz[E2_NCLASS] = {};       // in use
+  int oz_kq[E2_NCLASS] = {};
+  int64_t oz_mpad[E2_NCLASS] = {}, oz_npad[E2_NCLASS] = {};
+  size_t o_ozA[E2_NCLASS] = {}, o_ozRx[E2_NCLASS] = {}, o_ozB[E2_NCLASS] = {}, o_ozCx[E2_NCLASS] = {};
 };
 
 struct e2_batch {
@@ -162,6 +172,12 @@ Ctx ctx(const e2_problem* P, unsigned char* ws);
 unsigned char* slot_base(const e2_problem* P, unsigned char* ws, int r);
 Tabs tables(const e2_problem* P, unsigned char* ws, int r);
 ColTiles col_tiles(const e2_problem* P, unsigned char* ws, int r, int cls);
+// operands of the sliced contraction of class cls for root r
+OzOperands oz_operands(const e2_problem* P, unsigned char* ws, int r, int cls);
+// the sliced contraction with its Epstein-Nesbet epilogue; partial: one slot
+// per 64 x 64 tile, [column tile][row tile] (e2_ozaki.cu)
+void launch_class_oz(cudaStream_t st, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
+                     const double* E0p, double b, double* partial);
 void build_tables(const e2_problem* P, unsigned char* ws, cudaStream_t st, const double2* c, const Tabs& T, bool all);
 int splitk_segments(int64_t tiles, int64_t K, size_t seg_bytes);
 void dgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double* A, int64_t sam, int64_t sak,

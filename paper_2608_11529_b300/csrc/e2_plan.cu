@@ -375,10 +375,38 @@ e2_status build_plan(e2_problem* P) {
   P->o_wt = ws.take(sizeof(double) * Lt);
   P->o_Bo = ws.take(16 * (size_t)Lt * P->n * P->nocc);
   P->o_f = ws.take(16 * (size_t)P->n * P->nocc);
+  // Sliced bf16 contraction: classes whose real contraction length 2 Kp is at
+  // most 256 (the exactness bound of the level sums), when the slices and the
+  // float-float tables take at most 16 GiB in all.
+  {
+    size_t extra = 0;
+    std::vector<bool> ldf(P->lists.size(), false);
+    for (int c : {2, 5, 7, 6}) {
+      const int li = P->list_of[c];
+      P->oz_ok[c] = ((d.class_mask >> c) & 1u) && P->M[c] > 0 && li >= 0 && P->lists[li].n > 0 && 2 * P->Kp[c] <= 256;
+      if (!P->oz_ok[c]) continue;
+      P->oz_kq[c] = (2 * P->Kp[c] + 31) / 32 * 32;
+      P->oz_mpad[c] = (P->M[c] + 63) / 64 * 64;
+      P->oz_npad[c] = (P->lists[li].n + 63) / 64 * 64;
+      extra += (size_t)2 * OZ_S * P->oz_kq[c] * (P->oz_mpad[c] + 2 * P->oz_npad[c]);
+      if (!ldf[li]) extra += 8 * (size_t)(P->nx + 2) * P->lists[li].n;
+      ldf[li] = true;
+    }
+    const bool fits = extra <= (size_t(16) << 30);
+    for (int c : {2, 5, 7, 6}) {
+      P->oz_ok[c] = P->oz_ok[c] && fits;
+      P->use_oz[c] = P->oz_ok[c];
+      if (P->oz_ok[c]) P->lists[P->list_of[c]].df = true;
+    }
+  }
   for (HostList& L : P->lists) {
     L.o_str = ws.take(sizeof(uint64_t) * std::max<int64_t>(L.n, 1));
     L.o_eA = ws.take(sizeof(double) * std::max<int64_t>(L.n, 1));
     L.o_U = ws.take(sizeof(double) * (size_t)(P->nx + 1) * std::max<int64_t>(L.n, 1));
+    if (L.df) {
+      L.o_eAdf = ws.take(8 * (size_t)L.n);
+      L.o_Udf = ws.take(8 * (size_t)(P->nx + 1) * L.n);
+    }
   }
   const int dense[5] = {2, 5, 7, 4, 6};
   for (int c = 0; c < E2_NCLASS; ++c) P->o_rows[c] = P->o_W[c] = 0;
@@ -386,6 +414,10 @@ e2_status build_plan(e2_problem* P) {
     if (P->M[c] == 0) continue;
     P->o_rows[c] = ws.take(sizeof(RowInfo) * P->M[c]);
     P->o_W[c] = ws.take(16 * (size_t)P->M[c] * P->Kp[c]);
+    if (P->oz_ok[c]) {
+      P->o_ozA[c] = ws.take((size_t)2 * OZ_S * P->oz_mpad[c] * P->oz_kq[c]);
+      P->o_ozRx[c] = ws.take(4 * (size_t)P->oz_mpad[c]);
+    }
   }
   P->o_G22 = ws.take(sizeof(double) * std::max<int64_t>(P->ncp * P->nvp, 1));
   P->o_X01 = ws.take(16 * (size_t)std::max<int64_t>((int64_t)P->nvc * P->na * P->ntp, 1));
@@ -402,6 +434,11 @@ e2_status build_plan(e2_problem* P) {
   P->o_DTDU = ws.take(16 * (size_t)P->Kp11 * std::max<int64_t>(lsize(4), 1));
   for (ColPlan& cp : P->cplan)
     if (cp.built) cp.o_Dc = ws.take(16 * (size_t)cp.krows * 64);
+  for (int c : {2, 5, 7, 6})
+    if (P->oz_ok[c]) {
+      P->o_ozB[c] = ws.take((size_t)2 * OZ_S * 2 * P->oz_npad[c] * P->oz_kq[c]);
+      P->o_ozCx[c] = ws.take(4 * (size_t)P->oz_npad[c]);
+    }
   P->d_stride = ws.top - dstart;
   // one slot: the forward and backward build and consume each root's tables
   // in turn on one stream; a batch, which holds every root's tables until its
@@ -717,6 +754,21 @@ e2_status e2_class_tiles_copy(const e2_problem* P, int cls, int32_t* perm, int32
   std::copy(cp.perm.begin(), cp.perm.end(), perm);
   std::copy(cp.tdesc.begin(), cp.tdesc.end(), tdesc);
   std::copy(cp.klist.begin(), cp.klist.end(), klist);
+  return E2_OK;
+}
+
+e2_status e2_set_contraction(e2_problem* P, int cls, int mode) {
+  if (!P || cls < 0 || cls >= E2_NCLASS || (mode != E2_CONTRACT_FP64 && mode != E2_CONTRACT_SLICED))
+    return E2_ERR_INVALID_ARG;
+  if (mode == E2_CONTRACT_SLICED && !P->oz_ok[cls]) return E2_ERR_UNSUPPORTED;
+  P->use_oz[cls] = mode == E2_CONTRACT_SLICED;
+  return E2_OK;
+}
+
+e2_status e2_contraction(const e2_problem* P, int cls, int* mode, int* sliced_available) {
+  if (!P || cls < 0 || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
+  if (mode) *mode = P->use_oz[cls] ? E2_CONTRACT_SLICED : E2_CONTRACT_FP64;
+  if (sliced_available) *sliced_available = P->oz_ok[cls] ? 1 : 0;
   return E2_OK;
 }
 

@@ -4,6 +4,7 @@ e2_backward with seed w, and dE2/dlambda must match central differences."""
 import numpy as np
 import pytest
 
+from fp64_mode import fp64_contraction
 from e2_inputs.synth import tiny_problem
 from oracle import Oracle
 
@@ -38,7 +39,8 @@ def test_autograd_function_gives_the_adjoint_gradients():
     def f(x):
         return float((plan.forward(**dict(t, lam=x))[0].cpu().numpy() * w).sum())
     eps = 1e-2
-    d1 = (f(1 + eps) - f(1 - eps)) / (2 * eps)
-    d2 = (f(1 + eps / 2) - f(1 - eps / 2)) / eps
+    with fp64_contraction(plan):
+        d1 = (f(1 + eps) - f(1 - eps)) / (2 * eps)
+        d2 = (f(1 + eps / 2) - f(1 - eps / 2)) / eps
     num = (4 * d2 - d1) / 3
     assert abs(float(gl) - num) <= 1e-6 * abs(num) + 1e-12, (float(gl), num)

@@ -28,7 +28,8 @@ def _jobs():
 
 
 @pytest.mark.parametrize("col_tiles", [False, True])
-def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph(col_tiles):
+@pytest.mark.parametrize("sliced", [True, False])
+def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph(col_tiles, sliced):
     import paper_2608_11529_b300 as e2
     from paper_2608_11529_b300 import build as e2build
     e2build.build()
@@ -38,6 +39,9 @@ def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph(col_tile
         for cls in (2, 4, 5, 6):
             if plan.class_tiles(cls)[0]:
                 plan.set_class_tiles(cls, col_tiles)
+        for cls in (2, 5, 6, 7):                   # sliced classes run beside the persistent FP64 kernel
+            if plan.contraction(cls)[1]:
+                plan.set_contraction(cls, sliced)
     inputs = [e2.device_inputs(p, c) for p, _, c in jobs]
     single = []
     for plan, t in zip(plans, inputs):

@@ -16,6 +16,7 @@ import os
 import numpy as np
 import pytest
 
+from fp64_mode import fp64_contraction
 from e2_inputs import make_problem
 from strings_ref import ClassStrings
 
@@ -165,8 +166,9 @@ def test_fullsize_gradient_matches_central_differences(run):
         return float(plan.forward(**tt)[0].cpu().numpy()[0])
 
     def richardson(g, eps):
-        d1 = (g(eps) - g(-eps)) / (2 * eps)
-        d2 = (g(eps / 2) - g(-eps / 2)) / eps
+        with fp64_contraction(plan):
+            d1 = (g(eps) - g(-eps)) / (2 * eps)
+            d2 = (g(eps / 2) - g(-eps / 2)) / eps
         return (4 * d2 - d1) / 3
 
     num_l = richardson(lambda e: f(lam=t["lam"] + e), 1e-2)

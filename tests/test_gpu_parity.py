@@ -18,7 +18,7 @@ TOL_E2 = 1e-9
 TOL_E0 = 1e-10
 
 
-def _gpu_e2(prob, c, class_mask=0x1FF, lam=None, col_tiles=None):
+def _gpu_e2(prob, c, class_mask=0x1FF, lam=None, col_tiles=None, sliced=None):
     import paper_2608_11529_b300 as e2
     from paper_2608_11529_b300 import build as e2build
     e2build.build()
@@ -27,6 +27,10 @@ def _gpu_e2(prob, c, class_mask=0x1FF, lam=None, col_tiles=None):
         for cls in (2, 4, 5, 6):
             if plan.class_tiles(cls)[0]:
                 plan.set_class_tiles(cls, col_tiles)
+    if sliced is not None:                         # force the sliced bf16 (True) or FP64 (False) contraction
+        for cls in (2, 5, 6, 7):
+            if plan.contraction(cls)[1]:
+                plan.set_contraction(cls, sliced)
     t = e2.device_inputs(prob, c)
     if lam is not None:
         t["lam"] = lam
@@ -77,12 +81,42 @@ def test_column_tiles_match_oracle(name, col_tiles):
     D^{t+u} skipped per tile) and plain columns both meet the bar."""
     prob = CASES[name]()
     c, E0, e2, ec = _oracle(prob)
-    g2, gc, g0, plan = _gpu_e2(prob, c, col_tiles=col_tiles)
+    g2, gc, g0, plan = _gpu_e2(prob, c, col_tiles=col_tiles, sliced=False)
     for cls in (2, 4, 5, 6):
         tiles, _, used = plan.class_tiles(cls)
         assert used == (col_tiles and tiles > 0)
     np.testing.assert_allclose(gc, ec, rtol=0, atol=TOL_E2)
     np.testing.assert_allclose(g2, e2, rtol=0, atol=TOL_E2)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("sliced", [True, False])
+def test_contraction_modes_match_oracle(name, sliced):
+    """Both contractions of the dense classes meet the bar: FP64 on the FP64
+    tensor pipe, and the exact bf16 slices with the float-float epilogue."""
+    prob = CASES[name]()
+    c, E0, e2, ec = _oracle(prob)
+    g2, gc, g0, plan = _gpu_e2(prob, c, sliced=sliced)
+    for cls in (2, 5, 6, 7):
+        used, avail = plan.contraction(cls)
+        assert used == (sliced and avail)
+    np.testing.assert_allclose(gc, ec, rtol=0, atol=TOL_E2)
+    np.testing.assert_allclose(g2, e2, rtol=0, atol=TOL_E2)
+
+
+@pytest.mark.parametrize("name", ["dc_small", "dcb_two_roots_frozen", "level_shift", "das_three_subspaces"])
+def test_sliced_contraction_against_fp64(name):
+    """Per class, the sliced contraction agrees with the FP64 one to 1e-11 of
+    the class energy: the slices lose about 2^-40 of each V."""
+    prob = CASES[name]()
+    c, *_ = _oracle(prob)
+    _, fp, _, plan = _gpu_e2(prob, c, sliced=False)
+    _, sl, _, _ = _gpu_e2(prob, c, sliced=True)
+    on = [cls for cls in (2, 5, 6, 7) if plan.contraction(cls)[1]]
+    assert on
+    for r in range(fp.shape[0]):
+        for cls in on:
+            assert abs(sl[r, cls] - fp[r, cls]) <= 1e-11 * abs(fp[r, cls]) + 1e-15, (r, cls, sl[r, cls], fp[r, cls])
 
 
 def test_repeated_calls_are_bitwise_equal():

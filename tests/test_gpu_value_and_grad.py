@@ -8,6 +8,7 @@ differences are Richardson-extrapolated, so the step error is O(eps^4)."""
 import numpy as np
 import pytest
 
+from fp64_mode import fp64_contraction
 from e2_inputs import make_problem
 from oracle import Oracle
 
@@ -51,8 +52,9 @@ def _fd(plan, t, seed, key, direction, eps):
         else:
             tt[key] = t[key] + h * direction
         return float((plan.forward(**tt)[0].cpu().numpy() * seed).sum())
-    d1 = (f(eps) - f(-eps)) / (2 * eps)
-    d2 = (f(eps / 2) - f(-eps / 2)) / eps
+    with fp64_contraction(plan):
+        d1 = (f(eps) - f(-eps)) / (2 * eps)
+        d2 = (f(eps / 2) - f(-eps / 2)) / eps
     return (4 * d2 - d1) / 3
 
 
