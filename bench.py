@@ -123,17 +123,27 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+KERNEL_SOURCE = {"k_class_gemm": "e2_kernels.cu", "k_class_oz": "e2_ozaki.cu"}
+
+
 def _traffic(kernel):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    the current source of that kernel; else None."""
     path = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-    if not os.path.exists(path):
+    if not os.path.exists(path) or kernel not in KERNEL_SOURCE:
         return None
-    rec = json.load(open(path))
-    src = open(os.path.join(ROOT, "paper_2608_11529_b300", "csrc", "e2_kernels.cu"), "rb").read()
-    if rec.get("kernels_sha256") != hashlib.sha256(src).hexdigest():
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
         return None
-    return rec.get("bytes_per_launch", {}).get(kernel)
+    src = open(os.path.join(ROOT, "paper_2608_11529_b300", "csrc", KERNEL_SOURCE[kernel]), "rb").read()
+    if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def _measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    return json.load(open(path)) if os.path.exists(path) else {}
 
 
 def _sample_ks(prob, n, rng):
@@ -386,29 +396,60 @@ def run(args):
     ms = float(ms_all.item())
     E2dev = E2.clone()
 
-    # per-class kernel times (root 0) over the timed region
+    # per-class kernel times (root 0) over the timed region, summed per kernel
     present = [k for k in range(9) if plan.q_per_class[k] > 0]
     ktime = {k: sum(evs[s][k][0].elapsed_time(evs[s][k][1]) for s in range(args.steps)) / args.steps for k in present}
-    dom = max(ktime, key=ktime.get)
-    if dom in GEMM_CLASSES:
+    sliced = {k for k in GEMM_CLASSES if k in present and plan.contraction(k)[0]}
+    kern = {k: ("k_class_oz" if k in sliced else KERNEL_OF_CLASS[k]) for k in present}
+    ksum = {}
+    for k in present:
+        ksum[kern[k]] = ksum.get(kern[k], 0.0) + ktime[k]
+    dom_kernel = max(ksum, key=ksum.get)
+    classes = [k for k in present if kern[k] == dom_kernel]
+    if dom_kernel == "k_class_oz":
+        # the sliced method's tensor work: 15 slice pairs (levels 2..6 of five
+        # slices per operand), each a real product of length 2K into the two
+        # real outputs (Re V, Im V) of a coupling: 15 * 2 * 2K * 2 = 120 K bf16
+        # flops per coupling; peak: the measured bf16 rate, sustained (the
+        # kernel runs inside a long step)
+        mp = _measured_peaks()
+        peak_bf16 = mp.get("bf16_tflops_sustained") or 1400.0
+        flops = sum(120.0 * plan.q_per_class[k] * _kdim(prob, k) for k in classes)
+        t_ms = sum(ktime[k] for k in classes)
+        achieved = flops / (t_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_bf16, "unit": "TFLOP/s",
+                "frac": achieved / peak_bf16, "traffic": _traffic("k_class_oz"),
+                "kernel": "k_class_oz classes " + " ".join(CLASS_NAMES[k] for k in classes),
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"
+                                if mp.get("bf16_tflops_sustained") else "fallback 1.4 PFLOP/s sustained bf16"),
+                "algorithmic_flops_per_step": flops, "ms_per_step": t_ms,
+                "launches_per_step": len(classes),
+                "couplings_per_s": sum(plan.q_per_class[k] for k in classes) / (t_ms * 1e-3),
+                "flops_per_coupling": "120 K bf16 (15 slice pairs x 2 real outputs x real length 2K x 2)"}
+    elif dom_kernel == "k_class_gemm":
         # complex products by Gauss's three real products: 6 real flops per
         # complex multiply-add, K of them per coupling; with column tiles K is
         # each tile's compacted length (the products the kernel executes)
-        flops = 6.0 * plan.q_per_class[dom] * _kdim(prob, dom)
-        tiles, krows, used = plan.class_tiles(dom)
-        if used:
-            flops = 6.0 * (plan.q_per_class[dom] / _ncols(prob, plan, dom)) * krows * 64
-        achieved = flops / (ktime[dom] * 1e-3) / 1e12
+        flops = 0.0
+        for k in classes:
+            f = 6.0 * plan.q_per_class[k] * _kdim(prob, k)
+            tiles, krows, used = plan.class_tiles(k)
+            if used:
+                f = 6.0 * (plan.q_per_class[k] / _ncols(prob, plan, k)) * krows * 64
+            flops += f
+        t_ms = sum(ktime[k] for k in classes)
+        achieved = flops / (t_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_dmma, "unit": "TFLOP/s",
                 "frac": achieved / peak_dmma, "traffic": _traffic("k_class_gemm"),
-                "kernel": f"k_class_gemm class {CLASS_NAMES[dom]}", "peak_source":
+                "kernel": "k_class_gemm classes " + " ".join(CLASS_NAMES[k] for k in classes), "peak_source":
                 "measured on this GPU: mma.sync m16n8k8 f64 burst (e2_fp64_peak)",
-                "algorithmic_flops_per_launch": flops, "ms_per_launch": ktime[dom],
+                "algorithmic_flops_per_step": flops, "ms_per_step": t_ms, "launches_per_step": len(classes),
                 "flops_per_coupling": "6 K (3 real products per complex product, K = contraction length; "
                                       "with column tiles, each tile's compacted K)"}
     else:
         roof = {"bound": "alu", "achieved": None, "peak": peak_dfma, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "kernel": KERNEL_OF_CLASS[dom]}
+                "traffic": None, "kernel": dom_kernel}
+    roof["kernel_ms_per_step"] = ksum
 
     # forward + backward in one pass (E2 and dE2/d(h, c, B, lambda), V formed
     # once) against forward alone

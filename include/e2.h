@@ -299,6 +299,10 @@ E2_API e2_status e2_set_class_tiles(e2_problem* prob, int cls, int on);
  *                      for (0,2), (1,2), (2,1), (2,0) when the real
  *                      contraction length 2 K is at most 256 and the slices
  *                      fit 16 GiB; the default there.
+ * cls = E2_CONTRACT_SETUP selects the same choice for the products over the
+ * factor index that form the integral blocks (step a5: (ai|bt), (at|bu),
+ * (av|uw)); there the slices are exact per 256 real terms and the sums over
+ * the factor index accumulate in float-float; the default is sliced.
  * e2_set_contraction returns E2_ERR_UNSUPPORTED for a class without the
  * sliced plan; e2_contraction reports the mode in use and whether the sliced
  * plan exists (either output may be NULL).  The backward pass forms its
@@ -306,6 +310,7 @@ E2_API e2_status e2_set_class_tiles(e2_problem* prob, int cls, int on);
  * kernel, so it stays bitwise equal to e2_forward's. */
 #define E2_CONTRACT_FP64 0
 #define E2_CONTRACT_SLICED 1
+#define E2_CONTRACT_SETUP (-1)
 E2_API e2_status e2_set_contraction(e2_problem* prob, int cls, int mode);
 E2_API e2_status e2_contraction(const e2_problem* prob, int cls, int* mode, int* sliced_available);
 E2_API e2_status e2_autotune(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,

@@ -80,7 +80,7 @@ OzOperands oz_operands(const e2_problem* P, unsigned char* ws, int r, int cls) {
   unsigned char* sb = slot_base(P, ws, r);
   return OzOperands{(const __nv_bfloat16*)(ws + P->o_ozA[cls]), P->oz_mpad[cls], (const int*)(ws + P->o_ozRx[cls]),
                     (const __nv_bfloat16*)(sb + P->o_ozB[cls]), P->oz_npad[cls], (const int*)(sb + P->o_ozCx[cls]),
-                    P->oz_kq[cls], (const float2*)(ws + L.o_Udf), (const float2*)(ws + L.o_eAdf)};
+                    P->oz_kq[cls], (const float2*)(ws + L.o_Udf), (const float2*)(ws + L.o_eAdf), P->nx};
 }
 
 // Coupling tensors D^x_A = <A|x|c> of one reference vector c; `all` = false
@@ -237,8 +237,10 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
     if (c == 5) {
       // (ai|bt) = sum_L wt_L B_ai B_bt for all (a,i), (b,t), then <ab||it> = (ai|bt) - (at|bi)
       double2* X12 = (double2*)(ws + P->o_x12);
-      zgemm(st, (int64_t)P->nvc * P->ncc, nva, Lt, (const double2*)(ws + P->o_xYc), Lt, 1, 0, Zf, nva, 1, 0, X12, nva, 1,
-            0);
+      if (!(P->use_oz_setup && zgemm_sliced(st, (int64_t)P->nvc * P->ncc, nva, Lt, (const double2*)(ws + P->o_xYc), Lt,
+                                            1, 0, Zf, nva, 1, 0, X12, nva, 1, 0, -1, ws + P->o_ozS, P->ozS_bytes)))
+        zgemm(st, (int64_t)P->nvc * P->ncc, nva, Lt, (const double2*)(ws + P->o_xYc), Lt, 1, 0, Zf, nva, 1, 0, X12, nva,
+              1, 0);
       (k_w12<<<blocks(P->M[c] * P->Kp[c]), 256, 0, st>>>(X.sp, X12, nva, P->M[c], P->Kp[c], (double2*)(ws + P->o_W[c])),
        ++g_launches);
       continue;
@@ -252,8 +254,12 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
         while (b1 < P->nvc && 16 * (size_t)(b1 + 1 - b0) * na * (size_t)(b1 + 1) * na <= P->va_cap) ++b1;
         const int64_t r0 = (int64_t)b0 * na, rows = (int64_t)(b1 - b0) * na, ldx = (int64_t)b1 * na;
         dim3 grid((unsigned)((rows + 63) / 64), (unsigned)((ldx + 63) / 64), 1);
-        (k_zgemm64<<<grid, 256, 0, st>>>(rows, ldx, Lt, Yw + r0 * Lt, Lt, 1, 0, Zf, nva, 1, 0, Xv, ldx, 1, 0, Lt, 0,
-                                          r0), ++g_launches);
+        // sliced: the factor columns of all n_v n_a pairs are cut once and
+        // kept for the following stripes
+        if (!(P->use_oz_setup && zgemm_sliced(st, rows, ldx, Lt, Yw + r0 * Lt, Lt, 1, 0, Zf, nva, 1, 0, Xv, ldx, 1, 0,
+                                              r0, ws + P->o_ozS, P->ozS_bytes, nva, b0 > 0)))
+          (k_zgemm64<<<grid, 256, 0, st>>>(rows, ldx, Lt, Yw + r0 * Lt, Lt, 1, 0, Zf, nva, 1, 0, Xv, ldx, 1, 0, Lt, 0,
+                                            r0), ++g_launches);
         if (pairs(b1) > pairs(b0))
           (k_w02<<<blocks((pairs(b1) - pairs(b0)) * P->Kp[c]), 256, 0, st>>>(X.sp, Xv, ldx, b0, b1, P->Kp[c],
                                                                              (double2*)(ws + P->o_W[c])), ++g_launches);
@@ -268,8 +274,11 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
                                                          (int)P->nvp, ws + P->o_G22), ++g_launches);
   if (on1 && nva > 0) {  // (av|uw) for all (a,v), (u,w), then <au||vw> = (av|uw) - (aw|uv)
     double2* X01g = (double2*)(ws + P->o_x01);
-    zgemm(st, nva, (int64_t)na * na, Lt, Yw, Lt, 1, 0, (const double2*)(ws + P->o_xZaa), (int64_t)na * na, 1, 0, X01g,
-          (int64_t)na * na, 1, 0);
+    if (!(P->use_oz_setup && zgemm_sliced(st, nva, (int64_t)na * na, Lt, Yw, Lt, 1, 0, (const double2*)(ws + P->o_xZaa),
+                                          (int64_t)na * na, 1, 0, X01g, (int64_t)na * na, 1, 0, -1, ws + P->o_ozS,
+                                          P->ozS_bytes)))
+      zgemm(st, nva, (int64_t)na * na, Lt, Yw, Lt, 1, 0, (const double2*)(ws + P->o_xZaa), (int64_t)na * na, 1, 0,
+            X01g, (int64_t)na * na, 1, 0);
     (k_x01<<<blocks((int64_t)P->nvc * na * P->ntp), 256, 0, st>>>(X.sp, X01g, (double2*)(ws + P->o_X01)), ++g_launches);
   }
   if (P->part_cnt[3] > 0)
@@ -278,8 +287,8 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
   // row slices of W for the classes on the sliced contraction
   for (int c : {2, 5, 7, 6})
     if (P->use_oz[c] && P->part_cnt[c] > 0)
-      (k_oz_split_rows<<<(unsigned)(P->oz_mpad[c] / 8), 256, 0, st>>>(
-           (const double2*)(ws + P->o_W[c]), P->M[c], P->Kp[c], P->Kp[c], P->oz_kq[c], P->oz_mpad[c],
+      (k_oz_slice_a<<<(unsigned)(P->oz_mpad[c] / 8), 256, 0, st>>>(
+           (const double2*)(ws + P->o_W[c]), P->Kp[c], 1, 0, P->M[c], P->Kp[c], P->oz_kq[c], P->oz_mpad[c],
            (__nv_bfloat16*)(ws + P->o_ozA[c]), (int*)(ws + P->o_ozRx[c])), ++g_launches);
 }
 
@@ -320,8 +329,8 @@ void prepare_root(e2_problem* P, unsigned char* ws, cudaStream_t st, const doubl
     if (P->use_oz[cls] && P->part_cnt[cls] > 0) {
       const int64_t N = P->lists[P->list_of[cls]].n;
       unsigned char* sb = slot_base(P, ws, r);
-      (k_oz_split_cols<<<(unsigned)(P->oz_npad[cls] / 32), 256, 0, st>>>(
-           Dcls[cls], P->Kp[cls], N, P->oz_kq[cls], P->oz_npad[cls], (__nv_bfloat16*)(sb + P->o_ozB[cls]),
+      (k_oz_slice_b<<<(unsigned)(P->oz_npad[cls] / 32), 256, 0, st>>>(
+           Dcls[cls], N, 1, 0, P->Kp[cls], N, P->oz_kq[cls], P->oz_npad[cls], (__nv_bfloat16*)(sb + P->o_ozB[cls]),
            (int*)(sb + P->o_ozCx[cls])), ++g_launches);
     }
   double2* g1 = (double2*)(ws + P->o_g1 + P->g_stride * r);
@@ -398,7 +407,7 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
       dim3 grid((unsigned)((P->M[cls] + 63) / 64), (unsigned)((L.n + 63) / 64));
       mark(cls, 0);
       if (P->use_oz[cls])
-        launch_class_oz(st, oz_operands(P, ws, r, cls), P->M[cls], L.n, (const RowInfo*)(ws + P->o_rows[cls]),
+        launch_class_oz(st, cls, oz_operands(P, ws, r, cls), P->M[cls], L.n, (const RowInfo*)(ws + P->o_rows[cls]),
                         X.E0p + r, b, poff(cls));
       else
         (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Dfor[cls], P->M[cls], L.n, P->Kp[cls],

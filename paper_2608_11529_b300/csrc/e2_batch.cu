@@ -159,7 +159,7 @@ e2_status e2_batch_forward(e2_batch* B, const e2_inputs* inputs, void* workspace
     for (int c : {2, 5, 7, 6})
       if (P->use_oz[c] && P->part_cnt[c] > 0)
         for (int r = 0; r < P->d.n_roots; ++r)
-          launch_class_oz(st, oz_operands(P, w, r, c), P->M[c], P->lists[P->list_of[c]].n,
+          launch_class_oz(st, c, oz_operands(P, w, r, c), P->M[c], P->lists[P->list_of[c]].n,
                           (const RowInfo*)(w + P->o_rows[c]), (const double*)(w + P->o_E0p) + r,
                           P->d.level_shift_b, (double*)(w + P->o_part) + P->part_off[r * E2_NCLASS + c]);
     for (int r = 0; r < P->d.n_roots; ++r)

@@ -28,6 +28,7 @@ struct OzOperands {
   int Kq;
   const float2* Udf;
   const float2* eAdf;
+  int nx;  // U row index of an absent spinor (a zero row)
 };
 
 // Active-space partition as the kernels see it.

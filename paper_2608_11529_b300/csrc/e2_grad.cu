@@ -139,7 +139,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         for (int cls : {2, 5, 7, 4, 6}) {
           if (!on[cls]) continue;
           if (P->use_oz[cls]) {
-            launch_class_oz(st, oz_operands(P, ws, r, cls), P->M[cls], Lc[cls].n,
+            launch_class_oz(st, cls, oz_operands(P, ws, r, cls), P->M[cls], Lc[cls].n,
                             (const RowInfo*)(ws + P->o_rows[cls]), X.E0p + r, b, poff(cls));
             continue;
           }
@@ -180,7 +180,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       // E2 of a class on the sliced contraction: the forward's own kernel, so
       // that the energies equal e2_forward's bit for bit
       if (E2 && P->use_oz[cls])
-        launch_class_oz(st, oz_operands(P, ws, r, cls), M, N, (const RowInfo*)(ws + P->o_rows[cls]), X.E0p + r, b,
+        launch_class_oz(st, cls, oz_operands(P, ws, r, cls), M, N, (const RowInfo*)(ws + P->o_rows[cls]), X.E0p + r, b,
                         poff(cls));
       double* part_adj = P->use_oz[cls] ? nullptr : poff(cls);
       for (int64_t m0 = 0; m0 < M; m0 += P->chunk_rows[cls]) {

@@ -127,6 +127,8 @@ struct e2_problem {
   bool use_oz[E2_NCLASS] = {};       // in use
   int oz_kq[E2_NCLASS] = {};
   int64_t oz_mpad[E2_NCLASS] = {}, oz_npad[E2_NCLASS] = {};
+  bool use_oz_setup = false;         // the setup's integral products on the sliced GEMM
+  size_t o_ozS = 0, ozS_bytes = 0;   // their scratch (over the region the D tables take later)
   size_t o_ozA[E2_NCLASS] = {}, o_ozRx[E2_NCLASS] = {}, o_ozB[E2_NCLASS] = {}, o_ozCx[E2_NCLASS] = {};
 };
 
@@ -176,8 +178,19 @@ ColTiles col_tiles(const e2_problem* P, unsigned char* ws, int r, int cls);
 OzOperands oz_operands(const e2_problem* P, unsigned char* ws, int r, int cls);
 // the sliced contraction with its Epstein-Nesbet epilogue; partial: one slot
 // per 64 x 64 tile, [column tile][row tile] (e2_ozaki.cu)
-void launch_class_oz(cudaStream_t st, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
+void launch_class_oz(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
                      const double* E0p, double b, double* partial);
+// C (+)= A B (complex, strided as zgemm) through exact bf16 slices with
+// float-float accumulation (e2_ozaki.cu); lower >= 0: only tiles reaching
+// n <= lower + m.  Needs zgemm_sliced_bytes(M, max(N, Nslice), K) of scratch
+// (returns false, launching nothing, when it is short).  B is sliced over
+// Nslice >= N columns when given, so that reuse_b can keep those slices for
+// a following call on the same scratch and B with a narrower N.
+size_t zgemm_sliced_bytes(int64_t M, int64_t N, int64_t K);
+bool zgemm_sliced(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak,
+                  int conjA, const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm,
+                  int64_t csn, int beta, int64_t lower, unsigned char* scratch, size_t scratch_bytes,
+                  int64_t Nslice = 0, bool reuse_b = false);
 void build_tables(const e2_problem* P, unsigned char* ws, cudaStream_t st, const double2* c, const Tabs& T, bool all);
 int splitk_segments(int64_t tiles, int64_t K, size_t seg_bytes);
 void dgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double* A, int64_t sam, int64_t sak,

@@ -55,13 +55,11 @@ __global__ void k_reduce(const double* partial, const int64_t* off, const int64_
 __global__ void k_finalize(const double* e2c, int n_roots, double* E2, const double* E0in, double* E0out);
 
 // sliced bf16 contraction (e2_ozaki.cu)
-__global__ void k_oz_split_rows(const double2* W, int64_t M, int K, int64_t ldw, int Kq, int64_t Mpad,
-                                __nv_bfloat16* A, int* rexp);
-__global__ void k_oz_split_cols(const double2* D, int K, int64_t N, int Kq, int64_t Npad, __nv_bfloat16* B,
-                                int* cexp);
+__global__ void k_oz_slice_a(const double2* A, int64_t sam, int64_t sak, int conj, int64_t M, int K, int Kq,
+                             int64_t Mpad, __nv_bfloat16* out, int* rexp);
+__global__ void k_oz_slice_b(const double2* B, int64_t sbk, int64_t sbn, int conj, int K, int64_t N, int Kq,
+                             int64_t Npad, __nv_bfloat16* out, int* cexp);
 __global__ void k_oz_tables(const double* eA, const double* U, int64_t n, int64_t rows, float2* eAdf, float2* Udf);
-__global__ void k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* rows, const double* E0p, double b,
-                           double* partial);
 
 // adjoint (e2_adjoint.cu)
 __global__ void k_zgemm64(int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,

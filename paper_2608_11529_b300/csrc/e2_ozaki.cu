@@ -37,18 +37,6 @@ namespace e2 {
 
 namespace {
 
-__device__ __forceinline__ double oz_block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double t = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < nw; ++i) t += sh[i];
-  return t;
-}
-
 // the slices of x (|x| < 1): w_i 2^(-8 (i - 1)), i = 1..OZ_S (each exact in bf16)
 __device__ __forceinline__ void oz_cut(double x, float (&s)[OZ_S]) {
   double v = x;
@@ -96,39 +84,44 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
 
 // ------------------------------------------------------------------ slicing
 
-// Row slices of W (M x K complex, row stride ldw): A[s][row][k'] over the real
-// length 2K ([Re | Im], zero to Kq), one exponent per row.  One warp per row;
-// rows M..Mpad-1 are zero.
-__global__ void k_oz_split_rows(const double2* __restrict__ W, int64_t M, int K, int64_t ldw, int Kq, int64_t Mpad,
-                                __nv_bfloat16* __restrict__ A, int* __restrict__ rexp) {
+// Row slices of a complex M x K operand A (element (m, k) at A[m sam + k sak],
+// conjugated if conj): out[s][m][k'] over the real length 2K ([Re | Im],
+// zero to Kq), one exponent per row.  One warp per row; rows M..Mpad-1 are
+// zero.
+__global__ void k_oz_slice_a(const double2* __restrict__ A, int64_t sam, int64_t sak, int conj, int64_t M, int K,
+                             int Kq, int64_t Mpad, __nv_bfloat16* __restrict__ out, int* __restrict__ rexp) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= Mpad) return;
-  const double2* w = W + row * ldw;
+  const double2* a = A + row * sam;
   double m = 0.0;
   if (row < M)
-    for (int k = lane; k < K; k += 32) m = fmax(m, fmax(fabs(w[k].x), fabs(w[k].y)));
+    for (int k = lane; k < K; k += 32) {
+      const double2 v = a[k * sak];
+      m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+    }
   for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   int e = 0;
   if (m > 0.0) frexp(m, &e);  // m < 2^e
-  const double sc = ldexp(1.0, -e);
+  const double sc = ldexp(1.0, -e), si = conj ? -sc : sc;
   for (int k = lane; k < Kq; k += 32) {
     double x = 0.0;
-    if (row < M && k < 2 * K) x = (k < K ? w[k].x : w[k - K].y) * sc;
-    float s[OZ_S];
-    oz_cut(x, s);
+    if (row < M && k < 2 * K) x = k < K ? a[k * sak].x * sc : a[(k - K) * sak].y * si;
+    float sl[OZ_S];
+    oz_cut(x, sl);
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i) A[((int64_t)i * Mpad + row) * Kq + k] = __float2bfloat16_rn(s[i]);
+    for (int i = 0; i < OZ_S; ++i) out[((int64_t)i * Mpad + row) * Kq + k] = __float2bfloat16_rn(sl[i]);
   }
   if (lane == 0) rexp[row] = e;
 }
 
-// Column slices of D (K x N complex, row-major): B[s][2A + h][k'] with
-//   h = 0: (Dr[k], -Di[k]) over k' = k, K + k;  h = 1: (Di[k], Dr[k]),
-// zero to Kq and for the padding strings N..Npad-1; one exponent per string.
-// Block: 32 strings, 8 warps over k.
-__global__ void k_oz_split_cols(const double2* __restrict__ D, int K, int64_t N, int Kq, int64_t Npad,
-                                __nv_bfloat16* __restrict__ B, int* __restrict__ cexp) {
+// Column slices of a complex K x N operand B (element (k, n) at B[k sbk +
+// n sbn], conjugated if conj): out[s][2n + h][k'] with
+//   h = 0: (Re B[k], -Im B[k]) over k' = k, K + k;  h = 1: (Im B[k], Re B[k]),
+// zero to Kq and for the padding columns N..Npad-1; one exponent per column.
+// Block: 32 columns, 8 warps over k.
+__global__ void k_oz_slice_b(const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conj, int K, int64_t N,
+                             int Kq, int64_t Npad, __nv_bfloat16* __restrict__ out, int* __restrict__ cexp) {
   __shared__ double sm[8][32];
   __shared__ int se[32];
   const int c = threadIdx.x & 31, kk = threadIdx.x >> 5;
@@ -137,7 +130,7 @@ __global__ void k_oz_split_cols(const double2* __restrict__ D, int K, int64_t N,
   double m = 0.0;
   if (ok)
     for (int k = kk; k < K; k += 8) {
-      const double2 d = D[(int64_t)k * N + col];
+      const double2 d = B[(int64_t)k * sbk + col * sbn];
       m = fmax(m, fmax(fabs(d.x), fabs(d.y)));
     }
   sm[kk][c] = m;
@@ -152,20 +145,20 @@ __global__ void k_oz_split_cols(const double2* __restrict__ D, int K, int64_t N,
   }
   __syncthreads();
   if (col >= Npad) return;
-  const double sc = ldexp(1.0, -se[c]);
+  const double sc = ldexp(1.0, -se[c]), si = conj ? -sc : sc;
   const int64_t ps = 2 * Npad * (int64_t)Kq;  // one slice
-  __nv_bfloat16* b0 = B + (2 * col) * (int64_t)Kq;
+  __nv_bfloat16* b0 = out + (2 * col) * (int64_t)Kq;
   __nv_bfloat16* b1 = b0 + Kq;
   for (int k = kk; k < K; k += 8) {
-    const double2 d = ok ? D[(int64_t)k * N + col] : make_double2(0.0, 0.0);
-    float sr[OZ_S], si[OZ_S];
+    const double2 d = ok ? B[(int64_t)k * sbk + col * sbn] : make_double2(0.0, 0.0);
+    float sr[OZ_S], sim[OZ_S];
     oz_cut(d.x * sc, sr);
-    oz_cut(d.y * sc, si);
+    oz_cut(d.y * si, sim);
 #pragma unroll
     for (int i = 0; i < OZ_S; ++i) {
       b0[i * ps + k] = __float2bfloat16_rn(sr[i]);
-      b0[i * ps + K + k] = __float2bfloat16_rn(-si[i]);
-      b1[i * ps + k] = __float2bfloat16_rn(si[i]);
+      b0[i * ps + K + k] = __float2bfloat16_rn(-sim[i]);
+      b1[i * ps + k] = __float2bfloat16_rn(sim[i]);
       b1[i * ps + K + k] = __float2bfloat16_rn(sr[i]);
     }
   }
@@ -202,12 +195,16 @@ __global__ void k_oz_tables(const double* __restrict__ eA, const double* __restr
 constexpr int OZ_BM = 64, OZ_BNR = 128, OZ_BK = 32, OZ_LD = OZ_BK + 8;
 constexpr size_t OZ_STAGE = (size_t)OZ_S * (OZ_BM + OZ_BNR) * OZ_LD * 2;
 constexpr size_t OZ_SMEM = 2 * OZ_STAGE;
+constexpr int OZ_VROW = 65;  // float4 stride of a staged row of V (65: no bank conflicts on the writes)
+static_assert((size_t)OZ_VROW * 64 * 16 + 64 * 8 + 64 * 16 <= OZ_SMEM, "staged epilogue fits the stage buffers");
 
+// NS, NH: the particles and holes of each row of the class (which U terms
+// enter D), so that the epilogue is straight-line code.
+template <int NS, int NH>
 __global__ void __launch_bounds__(256, 1)
 k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows, const double* __restrict__ E0p,
            double b, double* __restrict__ partial) {
   extern __shared__ __align__(16) unsigned char oz_smem[];
-  __shared__ double sh[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 2, wn = warp & 3, g = lane >> 2, t = lane & 3;
   const int64_t m0 = (int64_t)blockIdx.x * OZ_BM, n0 = (int64_t)blockIdx.y * 64;
@@ -284,67 +281,339 @@ k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows
     __syncthreads();
   }
 
-  // epilogue, float-float: D_K = E0' - chi_e - e_A - U[s1,A] - U[s2,A] + U[i1,A] + U[i2,A]
-  const double e0p = *E0p;
-  const dfl bb = df_from_double(b * b);
-  dfl sum{0.0f, 0.0f};
+  // Epilogue, phase 1: the four levels of each coupling combined into
+  // float-float Re V, Im V (scaled by 2^(sigma_e + tau_A)) and staged in the
+  // free stage buffers, [64 rows][65] float4; the rows' E0' - chi_e and
+  // spinor indices beside them (the only FP64 work of the kernel: 64 rows).
+  float4* sV = (float4*)oz_smem;
+  float2* sBase = (float2*)(oz_smem + OZ_VROW * 64 * 16);
+  int4* sRI = (int4*)(oz_smem + OZ_VROW * 64 * 16 + 64 * 8);
+  if (tid < 64) {
+    const int64_t row = m0 + tid;
+    float2 bs = make_float2(0.f, 0.f);
+    int4 r4 = make_int4(0, 0, 0, 0);
+    if (row < M) {
+      const RowInfo ri = rows[row];
+      const dfl d = df_from_double(*E0p - ri.chi);
+      bs = make_float2(d.hi, d.lo);
+      r4 = make_int4(ri.s1, ri.s2, ri.i1, ri.i2);
+    }
+    sBase[tid] = bs;
+    sRI[tid] = r4;
+  }
 #pragma unroll
   for (int mi = 0; mi < 2; ++mi)
 #pragma unroll
     for (int hr = 0; hr < 2; ++hr) {
-      const int64_t row = m0 + wm * 32 + mi * 16 + g + hr * 8;
-      if (row >= M) continue;
-      const RowInfo ri = rows[row];
-      const dfl base = df_from_double(e0p - ri.chi);
-      const float2* U1 = op.Udf + (int64_t)ri.s1 * N;
-      const float2* U2 = op.Udf + (int64_t)ri.s2 * N;
-      const float2* U3 = op.Udf + (int64_t)ri.i1 * N;
-      const float2* U4 = op.Udf + (int64_t)ri.i2 * N;
-      const int er = op.rexp[row] - 16;
+      const int rl = wm * 32 + mi * 16 + g + hr * 8;
+      const int er = op.rexp[m0 + rl] - 16;  // rows to Mpad carry exponents
 #pragma unroll
       for (int ni = 0; ni < 4; ++ni) {
-        const int64_t col = n0 + wn * 16 + ni * 4 + t;
-        if (col >= N) continue;
-        const float sc = oz_pow2(er + op.cexp[col]);
-        // levels 2 and 3 exactly (two_sum), then the small remainder
+        const int cl = wn * 16 + ni * 4 + t;
+        const float sc = oz_pow2(er + op.cexp[n0 + cl]);
         const int cr = 2 * hr, ci = 2 * hr + 1;
-        dfl vr = df_add_f(two_sum(acc[0][mi][ni][cr], acc[1][mi][ni][cr]),
-                          __fadd_rn(acc[2][mi][ni][cr], acc[3][mi][ni][cr]));
-        dfl vi = df_add_f(two_sum(acc[0][mi][ni][ci], acc[1][mi][ni][ci]),
-                          __fadd_rn(acc[2][mi][ni][ci], acc[3][mi][ni][ci]));
-        vr = df_scale(vr, sc);
-        vi = df_scale(vi, sc);
-        const dfl v2 = df_add(df_sqr(vr), df_sqr(vi));
-        const float2 a = op.eAdf[col], u1 = U1[col], u2 = U2[col], u3 = U3[col], u4 = U4[col];
-        dfl Dk = df_sub(base, dfl{a.x, a.y});
-        Dk = df_sub(Dk, dfl{u1.x, u1.y});
-        Dk = df_sub(Dk, dfl{u2.x, u2.y});
-        Dk = df_add(Dk, dfl{u3.x, u3.y});
-        Dk = df_add(Dk, dfl{u4.x, u4.y});
+        // levels 2 and 3 exactly (two_sum), the small remainder into the low part
+        dfl vr = two_sum(acc[0][mi][ni][cr], acc[1][mi][ni][cr]);
+        vr = fast_two_sum(vr.hi, __fadd_rn(vr.lo, __fadd_rn(acc[2][mi][ni][cr], acc[3][mi][ni][cr])));
+        dfl vi = two_sum(acc[0][mi][ni][ci], acc[1][mi][ni][ci]);
+        vi = fast_two_sum(vi.hi, __fadd_rn(vi.lo, __fadd_rn(acc[2][mi][ni][ci], acc[3][mi][ni][ci])));
+        sV[rl * OZ_VROW + cl] = make_float4(__fmul_rn(vr.hi, sc), __fmul_rn(vr.lo, sc), __fmul_rn(vi.hi, sc),
+                                            __fmul_rn(vi.lo, sc));
+      }
+    }
+  __syncthreads();
+
+  // Phase 2: one warp per row, lanes over the tile's strings (coalesced reads
+  // of the float-float tables), four rows at a time so that each thread has
+  // eight independent couplings in flight; eight partial sums, added in a
+  // fixed order at the end.
+  //   D_K = E0' - chi_e - e_A - U[s1,A] - U[s2,A] + U[i1,A] + U[i2,A]
+  const bool shifted = b != 0.0;
+  const dfl bb = df_from_double(b * b);  // once per thread
+  float shi[8], serr[8];  // per slot: hi parts by two_sum, their errors beside
+#pragma unroll
+  for (int k = 0; k < 8; ++k) shi[k] = serr[k] = 0.0f;
+#pragma unroll
+  for (int rb = 0; rb < 8; rb += 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int rr = warp + 8 * (rb + q);
+      const bool rok = m0 + rr < M;
+      const int4 ri = sRI[rr];
+      const float2 bs = sBase[rr];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int slot = q * 2 + h;
+        const int cl = lane + 32 * h;
+        const int64_t col = n0 + cl;
+        if (!rok || col >= N) continue;
+        const float4 v = sV[rr * OZ_VROW + cl];
+        // |V|^2 = vr^2 + vi^2 from the exact squares of the high parts
+        const dfl p = two_prod(v.x, v.x), qq = two_prod(v.z, v.z);
+        const dfl s2 = two_sum(p.hi, qq.hi);
+        float e = __fadd_rn(__fadd_rn(p.lo, qq.lo), s2.lo);
+        e = __fmaf_rn(__fadd_rn(v.x, v.x), v.y, e);
+        e = __fmaf_rn(__fadd_rn(v.z, v.z), v.w, e);
+        const dfl v2 = fast_two_sum(s2.hi, e);
+        const float2 a = op.eAdf[col];
+        dfl Dk = df_sub(dfl{bs.x, bs.y}, dfl{a.x, a.y});
+        if (NS >= 1) {
+          const float2 u = op.Udf[(int64_t)ri.x * N + col];
+          Dk = df_sub(Dk, dfl{u.x, u.y});
+        }
+        if (NS >= 2) {
+          const float2 u = op.Udf[(int64_t)ri.y * N + col];
+          Dk = df_sub(Dk, dfl{u.x, u.y});
+        }
+        if (NH >= 1) {
+          const float2 u = op.Udf[(int64_t)ri.z * N + col];
+          Dk = df_add(Dk, dfl{u.x, u.y});
+        }
+        if (NH >= 2) {
+          const float2 u = op.Udf[(int64_t)ri.w * N + col];
+          Dk = df_add(Dk, dfl{u.x, u.y});
+        }
         dfl gk;
-        if (b == 0.0) {
+        if (!shifted) {
           gk = df_rcp(Dk);
         } else {  // level shift: g = D^3 / (D^4 + b^2)
           const dfl D2 = df_sqr(Dk);
           gk = df_mul(df_mul(Dk, D2), df_rcp(df_add(df_sqr(D2), bb)));
         }
-        sum = df_add(sum, df_mul(v2, gk));
+        const dfl term = df_mul(v2, gk);
+        const dfl u = two_sum(shi[slot], term.hi);
+        shi[slot] = u.hi;
+        serr[slot] = __fadd_rn(serr[slot], __fadd_rn(u.lo, term.lo));
       }
     }
-  const double tot = oz_block_sum(df_to_double(sum), sh);
-  if (tid == 0 && partial) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  }
+  dfl tsum = fast_two_sum(shi[0], serr[0]);
+#pragma unroll
+  for (int k = 1; k < 8; ++k) tsum = df_add(tsum, fast_two_sum(shi[k], serr[k]));
+  // block sum in float-float (fixed order: warp tree, then warps 0..7), one
+  // conversion to double per CTA
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const dfl other{__shfl_xor_sync(0xffffffffu, tsum.hi, o), __shfl_xor_sync(0xffffffffu, tsum.lo, o)};
+    tsum = df_add(tsum, other);
+  }
+  __shared__ float2 sW[8];
+  if (lane == 0) sW[warp] = make_float2(tsum.hi, tsum.lo);
+  __syncthreads();
+  if (tid == 0 && partial) {
+    dfl tot{sW[0].x, sW[0].y};
+    for (int w = 1; w < 8; ++w) tot = df_add(tot, dfl{sW[w].x, sW[w].y});
+    partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = df_to_double(tot);
+  }
 }
 
 // grid (Mpad / 64, Npad / 64); the shared-memory opt-in is set once per process
-void launch_class_oz(cudaStream_t st, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
+void launch_class_oz(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
                      const double* E0p, double b, double* partial) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_class_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    cudaFuncSetAttribute(k_class_oz<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    cudaFuncSetAttribute(k_class_oz<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    cudaFuncSetAttribute(k_class_oz<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    cudaFuncSetAttribute(k_class_oz<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
     attr = true;
   }
   dim3 grid((unsigned)(op.Mpad / OZ_BM), (unsigned)(op.Npad / 64));
-  (k_class_oz<<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial), ++g_launches);
+  switch (cls) {  // particles and holes of the rows
+    case 2: (k_class_oz<2, 0><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial), ++g_launches); break;
+    case 5: (k_class_oz<2, 1><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial), ++g_launches); break;
+    case 7: (k_class_oz<1, 2><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial), ++g_launches); break;
+    case 6: (k_class_oz<0, 2><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial), ++g_launches); break;
+    default: break;
+  }
+}
+
+// ------------------------------------------------------------------ general product
+
+// C (+)= A B for complex FP64 operands through their slices (k_oz_slice_a/b):
+// CTA tile 64 rows x 32 complex columns (64 real), 8 warps of 32 x 16 real;
+// the four level accumulators of each output are exact over 256 real k and
+// are flushed after every 256 into a float-float accumulator (so any
+// contraction length keeps the per-256 exactness), which is scaled by
+// 2^(rexp + cexp - 16) and written in FP64 at the end.  With lower >= 0 only
+// tiles holding some column n <= lower + m are computed (a triangle).
+struct OzGemm {
+  const __nv_bfloat16* A;
+  int64_t Mpad;
+  const int* rexp;
+  const __nv_bfloat16* B;
+  int64_t Npad;
+  const int* cexp;
+  int Kq;
+  int64_t M, N;
+  double2* C;
+  int64_t csm, csn;
+  int beta;
+  int64_t lower;
+};
+
+constexpr int OG_BM = 64, OG_BNR = 64, OG_BK = 32, OG_LD = OG_BK + 8;
+constexpr size_t OG_STAGE = (size_t)OZ_S * (OG_BM + OG_BNR) * OG_LD * 2;
+constexpr size_t OG_SMEM = 2 * OG_STAGE;
+
+__global__ void __launch_bounds__(256, 1) k_zgemm_sl(OzGemm q) {
+  extern __shared__ __align__(16) unsigned char og_smem[];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp >> 2, wn = warp & 3, g = lane >> 2, t = lane & 3;
+  const int64_t m0 = (int64_t)blockIdx.x * OG_BM, n0 = (int64_t)blockIdx.y * (OG_BNR / 2);
+  if (q.lower >= 0 && n0 > q.lower + m0 + OG_BM - 1) return;
+  const int Kq = q.Kq;
+  auto sA = [&](int st, int s, int r, int k) {
+    return (__nv_bfloat16*)(og_smem + st * OG_STAGE) + ((s * OG_BM + r) * OG_LD + k);
+  };
+  auto sB = [&](int st, int s, int r, int k) {
+    return (__nv_bfloat16*)(og_smem + st * OG_STAGE) + (OZ_S * OG_BM * OG_LD + (s * OG_BNR + r) * OG_LD + k);
+  };
+  auto load = [&](int st, int kc) {
+    const int k0 = kc * OG_BK;
+    for (int i = tid; i < OZ_S * OG_BM * 4; i += 256) {
+      const int s = i / (OG_BM * 4), r = (i / 4) % OG_BM, c = i & 3;
+      cp_async16(sA(st, s, r, c * 8), q.A + ((int64_t)s * q.Mpad + m0 + r) * Kq + k0 + c * 8);
+    }
+    for (int i = tid; i < OZ_S * OG_BNR * 4; i += 256) {
+      const int s = i / (OG_BNR * 4), r = (i / 4) % OG_BNR, c = i & 3;
+      cp_async16(sB(st, s, r, c * 8), q.B + ((int64_t)s * 2 * q.Npad + 2 * n0 + r) * Kq + k0 + c * 8);
+    }
+    cp_async_commit();
+  };
+  float acc[4][2][2][4];
+  float dh[2][2][4], dl[2][2][4];  // float-float sums of the flushed 256-chunks
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        dh[mi][ni][e] = dl[mi][ni][e] = 0.0f;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) acc[l][mi][ni][e] = 0.0f;
+      }
+  auto flush = [&]() {
+#pragma unroll
+    for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          dfl v = two_sum(acc[0][mi][ni][e], acc[1][mi][ni][e]);
+          v = fast_two_sum(v.hi, __fadd_rn(v.lo, __fadd_rn(acc[2][mi][ni][e], acc[3][mi][ni][e])));
+          const dfl d = df_add(dfl{dh[mi][ni][e], dl[mi][ni][e]}, v);
+          dh[mi][ni][e] = d.hi;
+          dl[mi][ni][e] = d.lo;
+#pragma unroll
+          for (int l = 0; l < 4; ++l) acc[l][mi][ni][e] = 0.0f;
+        }
+  };
+
+  const int nk = Kq / OG_BK;
+  load(0, 0);
+  for (int kc = 0; kc < nk; ++kc) {
+    const int st = kc & 1;
+    if (kc + 1 < nk) {
+      load(st ^ 1, kc + 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+#pragma unroll
+    for (int ks = 0; ks < OG_BK; ks += 16) {
+      uint32_t bf[OZ_S][2][2];
+#pragma unroll
+      for (int s = 0; s < OZ_S; ++s) {
+        uint32_t r[4];
+        ldsm_x4(r, sB(st, s, wn * 16 + (lane & 7) + (lane >> 4) * 8, ks + ((lane >> 3) & 1) * 8));
+        bf[s][0][0] = r[0];
+        bf[s][0][1] = r[1];
+        bf[s][1][0] = r[2];
+        bf[s][1][1] = r[3];
+      }
+#pragma unroll
+      for (int sa = 0; sa < OZ_S; ++sa) {
+        uint32_t af[2][4];
+#pragma unroll
+        for (int mi = 0; mi < 2; ++mi) ldsm_x4(af[mi], sA(st, sa, wm * 32 + mi * 16 + (lane & 15), ks + (lane >> 4) * 8));
+#pragma unroll
+        for (int sb = 0; sb < OZ_S - sa; ++sb) {
+          const int l = sa + sb < 3 ? sa + sb : 3;
+#pragma unroll
+          for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+            for (int ni = 0; ni < 2; ++ni) mma_bf16_16816(acc[l][mi][ni], af[mi], bf[sb][ni][0], bf[sb][ni][1]);
+        }
+      }
+    }
+    __syncthreads();
+    if ((kc & 7) == 7 || kc + 1 == nk) flush();  // every 256 real k
+  }
+  // C[m][n] (+)= 2^(rexp + cexp - 16) (re, im)
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int hr = 0; hr < 2; ++hr) {
+      const int64_t row = m0 + wm * 32 + mi * 16 + g + hr * 8;
+      if (row >= q.M) continue;
+      const int er = q.rexp[row] - 16;
+#pragma unroll
+      for (int ni = 0; ni < 2; ++ni) {
+        const int64_t col = n0 + wn * 8 + ni * 4 + t;
+        if (col >= q.N) continue;
+        const double sc = ldexp(1.0, er + q.cexp[col]);
+        const double re = df_to_double(dfl{dh[mi][ni][2 * hr], dl[mi][ni][2 * hr]}) * sc;
+        const double im = df_to_double(dfl{dh[mi][ni][2 * hr + 1], dl[mi][ni][2 * hr + 1]}) * sc;
+        double2* c = q.C + row * q.csm + col * q.csn;
+        if (q.beta) {
+          const double2 o = *c;
+          *c = make_double2(o.x + re, o.y + im);
+        } else {
+          *c = make_double2(re, im);
+        }
+      }
+    }
+}
+
+size_t zgemm_sliced_bytes(int64_t M, int64_t N, int64_t K) {
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const int64_t Mpad = (M + OG_BM - 1) / OG_BM * OG_BM, Npad = (N + 31) / 32 * 32;
+  const int64_t Kq = (2 * K + 31) / 32 * 32;
+  return al((size_t)2 * OZ_S * Mpad * Kq) + al(4 * (size_t)Mpad) + al((size_t)2 * OZ_S * 2 * Npad * Kq) +
+         al(4 * (size_t)Npad);
+}
+
+bool zgemm_sliced(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak,
+                  int conjA, const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm,
+                  int64_t csn, int beta, int64_t lower, unsigned char* scratch, size_t scratch_bytes, int64_t Nslice,
+                  bool reuse_b) {
+  if (M <= 0 || N <= 0) return true;
+  const int64_t Nb = Nslice > N ? Nslice : N;  // columns of B that are sliced
+  if (K <= 0 || zgemm_sliced_bytes(M, Nb, K) > scratch_bytes) return false;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_zgemm_sl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OG_SMEM);
+    attr = true;
+  }
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const int64_t Mpad = (M + OG_BM - 1) / OG_BM * OG_BM, Npad = (Nb + 31) / 32 * 32;
+  const int Kq = (int)((2 * K + 31) / 32 * 32);
+  // B's slices first, so that a caller reusing them (reuse_b) keeps them in place
+  __nv_bfloat16* Bs = (__nv_bfloat16*)scratch;
+  int* cx = (int*)(scratch + al((size_t)2 * OZ_S * 2 * Npad * Kq));
+  __nv_bfloat16* As = (__nv_bfloat16*)((unsigned char*)cx + al(4 * (size_t)Npad));
+  int* rx = (int*)((unsigned char*)As + al((size_t)2 * OZ_S * Mpad * Kq));
+  if (!reuse_b)
+    (k_oz_slice_b<<<(unsigned)(Npad / 32), 256, 0, st>>>(B, sbk, sbn, conjB, (int)K, Nb, Kq, Npad, Bs, cx),
+     ++g_launches);
+  (k_oz_slice_a<<<(unsigned)(Mpad / 8), 256, 0, st>>>(A, sam, sak, conjA, M, (int)K, Kq, Mpad, As, rx),
+   ++g_launches);
+  OzGemm q{As, Mpad, rx, Bs, Npad, cx, Kq, M, N, C, csm, csn, beta, lower};
+  dim3 grid((unsigned)(Mpad / OG_BM), (unsigned)((N + 31) / 32));
+  (k_zgemm_sl<<<grid, 256, OG_SMEM, st>>>(q), ++g_launches);
+  return true;
 }
 
 }  // namespace e2

@@ -499,6 +499,17 @@ e2_status build_plan(e2_problem* P) {
     // the whole lower triangle in one product when it takes at most 1 GiB
     P->va_cap = std::min(full, std::max(std::max(least, room), std::min(full, size_t(1) << 30)));
     ws.top = std::max(ws.top, P->o_vaX + P->va_cap);
+    // slices of the factor-index products on the sliced GEMM: the largest of
+    // (ai|bt), (at|bu) (B sliced over all n_v n_a columns) and (av|uw)
+    if (Lt > 0 && nva > 0) {
+      size_t b = zgemm_sliced_bytes(nva, nva, Lt);
+      b = std::max(b, zgemm_sliced_bytes((int64_t)P->nvc * P->ncc, nva, Lt));
+      b = std::max(b, zgemm_sliced_bytes(nva, (int64_t)P->na * P->na, Lt));
+      P->o_ozS = P->o_vaX + al(P->va_cap);
+      P->ozS_bytes = b;
+      P->use_oz_setup = true;
+      ws.top = std::max(ws.top, P->o_ozS + al(b));
+    }
   }
   P->ws_bytes = ws.top;
   // reference solver (block Davidson) on top of the forward layout
@@ -758,17 +769,24 @@ e2_status e2_class_tiles_copy(const e2_problem* P, int cls, int32_t* perm, int32
 }
 
 e2_status e2_set_contraction(e2_problem* P, int cls, int mode) {
-  if (!P || cls < 0 || cls >= E2_NCLASS || (mode != E2_CONTRACT_FP64 && mode != E2_CONTRACT_SLICED))
+  if (!P || cls < E2_CONTRACT_SETUP || cls >= E2_NCLASS || (mode != E2_CONTRACT_FP64 && mode != E2_CONTRACT_SLICED))
     return E2_ERR_INVALID_ARG;
+  if (cls == E2_CONTRACT_SETUP) {
+    if (mode == E2_CONTRACT_SLICED && P->ozS_bytes == 0) return E2_ERR_UNSUPPORTED;
+    P->use_oz_setup = mode == E2_CONTRACT_SLICED;
+    return E2_OK;
+  }
   if (mode == E2_CONTRACT_SLICED && !P->oz_ok[cls]) return E2_ERR_UNSUPPORTED;
   P->use_oz[cls] = mode == E2_CONTRACT_SLICED;
   return E2_OK;
 }
 
 e2_status e2_contraction(const e2_problem* P, int cls, int* mode, int* sliced_available) {
-  if (!P || cls < 0 || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
-  if (mode) *mode = P->use_oz[cls] ? E2_CONTRACT_SLICED : E2_CONTRACT_FP64;
-  if (sliced_available) *sliced_available = P->oz_ok[cls] ? 1 : 0;
+  if (!P || cls < E2_CONTRACT_SETUP || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
+  const bool on = cls == E2_CONTRACT_SETUP ? P->use_oz_setup : P->use_oz[cls];
+  const bool ok = cls == E2_CONTRACT_SETUP ? P->ozS_bytes > 0 : P->oz_ok[cls];
+  if (mode) *mode = on ? E2_CONTRACT_SLICED : E2_CONTRACT_FP64;
+  if (sliced_available) *sliced_available = ok ? 1 : 0;
   return E2_OK;
 }
 

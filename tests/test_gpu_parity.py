@@ -27,8 +27,8 @@ def _gpu_e2(prob, c, class_mask=0x1FF, lam=None, col_tiles=None, sliced=None):
         for cls in (2, 4, 5, 6):
             if plan.class_tiles(cls)[0]:
                 plan.set_class_tiles(cls, col_tiles)
-    if sliced is not None:                         # force the sliced bf16 (True) or FP64 (False) contraction
-        for cls in (2, 5, 6, 7):
+    if sliced is not None:                         # force the sliced bf16 (True) or FP64 (False) products
+        for cls in (-1, 2, 5, 6, 7):               # -1: the integral products of the setup
             if plan.contraction(cls)[1]:
                 plan.set_contraction(cls, sliced)
     t = e2.device_inputs(prob, c)
