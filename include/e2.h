@@ -303,6 +303,9 @@ E2_API e2_status e2_set_class_tiles(e2_problem* prob, int cls, int on);
  * factor index that form the integral blocks (step a5: (ai|bt), (at|bu),
  * (av|uw)); there the slices are exact per 256 real terms and the sums over
  * the factor index accumulate in float-float; the default is sliced.
+ * cls = E2_CONTRACT_ADJOINT selects it for the products of e2_backward
+ * (Gamma_D = W^T conj(T), Gamma_W = conj(T) D^T per row chunk, and
+ * Cs = B Gamma^ when its slices fit 4 GiB); the default is sliced.
  * e2_set_contraction returns E2_ERR_UNSUPPORTED for a class without the
  * sliced plan; e2_contraction reports the mode in use and whether the sliced
  * plan exists (either output may be NULL).  The backward pass forms its
@@ -311,6 +314,7 @@ E2_API e2_status e2_set_class_tiles(e2_problem* prob, int cls, int on);
 #define E2_CONTRACT_FP64 0
 #define E2_CONTRACT_SLICED 1
 #define E2_CONTRACT_SETUP (-1)
+#define E2_CONTRACT_ADJOINT (-2)
 E2_API e2_status e2_set_contraction(e2_problem* prob, int cls, int mode);
 E2_API e2_status e2_contraction(const e2_problem* prob, int cls, int* mode, int* sliced_available);
 E2_API e2_status e2_autotune(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,

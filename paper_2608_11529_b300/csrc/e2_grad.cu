@@ -174,7 +174,10 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       // the class kernel reads the column tiles whenever the class uses them;
       // the Gamma products do so for the 8-granular plans (a 16-row table
       // gains nothing at the products' 8-wide output granularity)
-      const bool tiled = P->use_cols[cls] && P->cplan[cls].gran == 8;
+      // (on the sliced GEMM the products take plain columns: their tensor work
+      // no longer dominates)
+      const bool slg = P->use_oz_adj;
+      const bool tiled = !slg && P->use_cols[cls] && P->cplan[cls].gran == 8;
       const ColPlan& cp = P->cplan[cls];
       const ColTiles ctl = col_tiles(P, ws, r, cls);
       // E2 of a class on the sliced contraction: the forward's own kernel, so
@@ -188,8 +191,13 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         AdjOut adj{(double2*)B(P->o_bT), want_B ? (double*)B(P->o_bHm) : nullptr, (double*)B(P->o_bHrow),
                    (double*)B(P->o_bHcol), (double*)B(P->o_bScalT), m0, Mc, s, g1, part_adj, rt};
         dim3 grid((unsigned)((Mc + 63) / 64), (unsigned)ct);
-        (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
-                                            L.eA, X.E0p + r, b, nullptr, adj, col_tiles(P, ws, r, cls)), ++g_launches);
+        if (P->use_oz[cls])  // the sliced contraction in its adjoint mode (plain columns)
+          launch_class_oz_adj(st, cls, oz_operands(P, ws, r, cls), M, N, (const RowInfo*)(ws + P->o_rows[cls]),
+                              X.E0p + r, b, adj);
+        else
+          (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
+                                              L.eA, X.E0p + r, b, nullptr, adj, col_tiles(P, ws, r, cls)),
+           ++g_launches);
         // per-tile sums of this chunk: row sums of eta, column sums per row tile, the scalars
         {
           const int64_t rtc = (Mc + 63) / 64;
@@ -200,6 +208,9 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         // Gamma_D[x][A] += sum_e W[e][x] conj(T[e][A]) (split over the rows of the chunk)
         if (tiled)
           zgemm_gd_tiles(st, cp, ctl, W + m0 * Kp, (int)Kp, adj.T, N, Mc, (double2*)B(P->o_bGDc), m0 > 0);
+        else if (slg && zgemm_sliced(st, N, Kp, Mc, adj.T, 1, N, 1, W + m0 * Kp, Kp, 1, 0, GDfor[cls], 1, N, 1, -1,
+                                     (unsigned char*)B(P->o_bOz), P->bOz_bytes))
+          ;  // Gamma_D^T = conj(T)^T W: T is the row operand (sliced without duplication)
         else if (Kp >= 64)
           zgemm(st, Kp, N, Mc, W + m0 * Kp, 1, Kp, 0, adj.T, N, 1, 1, GDfor[cls], N, 1, 1, 64);
         else
@@ -215,7 +226,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
             (k_gw_reduce<<<blocks(Mc * Kp), 256, 0, st>>>(ctl.tdesc, (const int32_t*)(ws + cp.o_pos), cp.tiles,
                                                          (int)Kp, (const double2*)B(P->o_bGWc), cp.krows, Mc, GW,
                                                          (int)Kp, Kp), ++g_launches);
-          } else {
+          } else if (!(slg && zgemm_sliced(st, Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0, GW, Kp, 1, 0, -1,
+                                           (unsigned char*)B(P->o_bOz), P->bOz_bytes))) {
             zgemm(st, Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0, GW, Kp, 1, 0, Kp >= 64 ? 64 : 16);
           }
           (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na), ++g_launches);
@@ -404,7 +416,9 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
     double* gw = (double*)B(P->o_bGw);
     (k_gg<<<blocks((int64_t)n * n), 256, 0, st>>>(X.sp, Nd, Ntt, Ge, Gea, GG), ++g_launches);
     (k_symm<<<blocks(npair * npair), 256, 0, st>>>(Gt, npair, Gh), ++g_launches);
-    zgemm(st, Lt, npair, npair, X.Bo, npair, 1, 0, Gh, 1, npair, 0, Cs, npair, 1, 0);
+    if (!(P->use_oz_adj && zgemm_sliced(st, Lt, npair, npair, X.Bo, npair, 1, 0, Gh, 1, npair, 0, Cs, npair, 1, 0, -1,
+                                        (unsigned char*)B(P->o_bOz), P->bOz_bytes)))
+      zgemm(st, Lt, npair, npair, X.Bo, npair, 1, 0, Gh, 1, npair, 0, Cs, npair, 1, 0);
     (k_ftr<<<Lt, 256, 0, st>>>(X.sp, (const double2*)in->B_c, (const double2*)in->B_x, Lc_, Gf, ftr), ++g_launches);
     (k_bcoef<<<blocks((int64_t)Lt * n * n), 256, 0, st>>>(X.sp, (const double2*)in->B_c, (const double2*)in->B_x, Lc_,
                                                           Lx_, X.wt, X.dg, Cs, GG, Gf, ftr, GBc), ++g_launches);

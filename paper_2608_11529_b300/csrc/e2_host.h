@@ -129,6 +129,8 @@ struct e2_problem {
   int64_t oz_mpad[E2_NCLASS] = {}, oz_npad[E2_NCLASS] = {};
   bool use_oz_setup = false;         // the setup's integral products on the sliced GEMM
   size_t o_ozS = 0, ozS_bytes = 0;   // their scratch (over the region the D tables take later)
+  bool use_oz_adj = false;           // the adjoint's Gamma products and Cs on the sliced GEMM
+  size_t o_bOz = 0, bOz_bytes = 0;   // their scratch (backward region)
   size_t o_ozA[E2_NCLASS] = {}, o_ozRx[E2_NCLASS] = {}, o_ozB[E2_NCLASS] = {}, o_ozCx[E2_NCLASS] = {};
 };
 
@@ -180,6 +182,9 @@ OzOperands oz_operands(const e2_problem* P, unsigned char* ws, int r, int cls);
 // per 64 x 64 tile, [column tile][row tile] (e2_ozaki.cu)
 void launch_class_oz(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
                      const double* E0p, double b, double* partial);
+// its adjoint mode over one row chunk of the backward pass (see AdjOut)
+void launch_class_oz_adj(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
+                         const double* E0p, double b, const AdjOut& adj);
 // C (+)= A B (complex, strided as zgemm) through exact bf16 slices with
 // float-float accumulation (e2_ozaki.cu); lower >= 0: only tiles reaching
 // n <= lower + m.  Needs zgemm_sliced_bytes(M, max(N, Nslice), K) of scratch

@@ -5,9 +5,9 @@
 // (Ozaki, Ogita, Oishi, Rump, Numer. Algorithms 59, 2012): every row of W is
 // scaled by a power of two 2^-sigma_e to magnitudes below 1 and cut into
 // OZ_S slices of 8 significant bits, x = sum_i w_i 2^(-8 i), each w_i an
-// integer of magnitude at most 256 (the first) or 128 (the others), chosen by
-// rounding to nearest, so that the remainder after the last slice is below
-// 2^(-8 OZ_S - 1).  Columns of D are cut the same way with 2^-tau_A.  The
+// integer of magnitude at most 256 (the first) or 128 (the others): x
+// 2^(8 OZ_S) rounded to an integer, in balanced base-256 digits, so that the
+// remainder after the last slice is at most 2^(-8 OZ_S - 1).  Columns of D are cut the same way with 2^-tau_A.  The
 // slices are exact in bf16, their products exact in FP32, and the sums of
 // level 2 (i + j = 2) and level 3 (i + j = 3) are integers (after a fixed
 // power-of-two scaling) below 2^24 as long as the real contraction length is
@@ -37,16 +37,38 @@ namespace e2 {
 
 namespace {
 
-// the slices of x (|x| < 1): w_i 2^(-8 (i - 1)), i = 1..OZ_S (each exact in bf16)
-__device__ __forceinline__ void oz_cut(double x, float (&s)[OZ_S]) {
-  double v = x;
-#pragma unroll
-  for (int i = 0; i < OZ_S; ++i) {
-    const double t = v * 256.0;
-    const double w = rint(t);
-    s[i] = (float)w * __int_as_float((127 - 8 * i) << 23);  // w 2^(-8 i), exact
-    v = t - w;                                               // exact
+// The slices of x relative to 2^e (|x| < 2^e), from the bit pattern of x in
+// integer arithmetic (the FP64 pipe of this part is slow): N = x 2^(8 OZ_S - e)
+// rounded to an integer (|N| <= 2^(8 OZ_S)), then balanced base-256 digits
+// from the low end, d_i in [-128, 127] for i > 1 and d_1 in [-256, 256];
+// slice i holds d_i 2^(-8 (i - 1)) (exact in bf16).  neg: slices of -x.
+__device__ __forceinline__ void oz_digits(double x, int e, bool neg, float (&s)[OZ_S]) {
+  long long bits = __double_as_longlong(x);
+  if (neg) bits ^= (long long)0x8000000000000000ULL;
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  long long N = 0;
+  if (ex != 0) {
+    const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
+    const int sh = 1075 + e - 8 * OZ_S - ex;  // at least 13 when |x| < 2^e
+    if (sh < 63) N = (mant + (1LL << (sh - 1))) >> sh;
+    if (bits < 0) N = -N;
   }
+#pragma unroll
+  for (int i = OZ_S - 1; i >= 1; --i) {
+    const long long d = ((N + 128) & 255) - 128;
+    s[i] = (float)(int)d * __int_as_float((127 - 8 * i) << 23);
+    N = (N - d) >> 8;
+  }
+  s[0] = (float)(int)N;
+}
+
+// exponent e with |x| < 2^e from the largest magnitude's bit pattern (0 for 0)
+__device__ __forceinline__ int oz_exp(unsigned long long maxbits) {
+  const int ex = (int)(maxbits >> 52);
+  return ex ? ex - 1022 : 0;
+}
+__device__ __forceinline__ unsigned long long oz_mag(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
 }
 
 // 2^k as a float, k clamped to the normal range
@@ -94,21 +116,23 @@ __global__ void k_oz_slice_a(const double2* __restrict__ A, int64_t sam, int64_t
   const int lane = threadIdx.x & 31;
   if (row >= Mpad) return;
   const double2* a = A + row * sam;
-  double m = 0.0;
+  unsigned long long m = 0;
   if (row < M)
     for (int k = lane; k < K; k += 32) {
       const double2 v = a[k * sak];
-      m = fmax(m, fmax(fabs(v.x), fabs(v.y)));
+      m = max(m, max(oz_mag(v.x), oz_mag(v.y)));
     }
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);  // m < 2^e
-  const double sc = ldexp(1.0, -e), si = conj ? -sc : sc;
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const int e = oz_exp(m);
   for (int k = lane; k < Kq; k += 32) {
-    double x = 0.0;
-    if (row < M && k < 2 * K) x = k < K ? a[k * sak].x * sc : a[(k - K) * sak].y * si;
     float sl[OZ_S];
-    oz_cut(x, sl);
+    if (row < M && k < 2 * K) {
+      if (k < K) oz_digits(a[k * sak].x, e, false, sl);
+      else oz_digits(a[(k - K) * sak].y, e, conj != 0, sl);
+    } else {
+#pragma unroll
+      for (int i = 0; i < OZ_S; ++i) sl[i] = 0.0f;
+    }
 #pragma unroll
     for (int i = 0; i < OZ_S; ++i) out[((int64_t)i * Mpad + row) * Kq + k] = __float2bfloat16_rn(sl[i]);
   }
@@ -122,38 +146,37 @@ __global__ void k_oz_slice_a(const double2* __restrict__ A, int64_t sam, int64_t
 // Block: 32 columns, 8 warps over k.
 __global__ void k_oz_slice_b(const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conj, int K, int64_t N,
                              int Kq, int64_t Npad, __nv_bfloat16* __restrict__ out, int* __restrict__ cexp) {
-  __shared__ double sm[8][32];
+  __shared__ unsigned long long sm[8][32];
   __shared__ int se[32];
   const int c = threadIdx.x & 31, kk = threadIdx.x >> 5;
   const int64_t col = (int64_t)blockIdx.x * 32 + c;
   const bool ok = col < N;
-  double m = 0.0;
+  unsigned long long m = 0;
   if (ok)
     for (int k = kk; k < K; k += 8) {
       const double2 d = B[(int64_t)k * sbk + col * sbn];
-      m = fmax(m, fmax(fabs(d.x), fabs(d.y)));
+      m = max(m, max(oz_mag(d.x), oz_mag(d.y)));
     }
   sm[kk][c] = m;
   __syncthreads();
   if (kk == 0) {
-    double t = 0.0;
-    for (int i = 0; i < 8; ++i) t = fmax(t, sm[i][c]);
-    int e = 0;
-    if (t > 0.0) frexp(t, &e);
+    unsigned long long t = 0;
+    for (int i = 0; i < 8; ++i) t = max(t, sm[i][c]);
+    const int e = oz_exp(t);
     se[c] = e;
     if (col < Npad) cexp[col] = e;
   }
   __syncthreads();
   if (col >= Npad) return;
-  const double sc = ldexp(1.0, -se[c]), si = conj ? -sc : sc;
+  const int e = se[c];
   const int64_t ps = 2 * Npad * (int64_t)Kq;  // one slice
   __nv_bfloat16* b0 = out + (2 * col) * (int64_t)Kq;
   __nv_bfloat16* b1 = b0 + Kq;
   for (int k = kk; k < K; k += 8) {
     const double2 d = ok ? B[(int64_t)k * sbk + col * sbn] : make_double2(0.0, 0.0);
     float sr[OZ_S], sim[OZ_S];
-    oz_cut(d.x * sc, sr);
-    oz_cut(d.y * si, sim);
+    oz_digits(d.x, e, false, sr);
+    oz_digits(d.y, e, conj != 0, sim);
 #pragma unroll
     for (int i = 0; i < OZ_S; ++i) {
       b0[i * ps + k] = __float2bfloat16_rn(sr[i]);
@@ -198,16 +221,155 @@ constexpr size_t OZ_SMEM = 2 * OZ_STAGE;
 constexpr int OZ_VROW = 65;  // float4 stride of a staged row of V (65: no bank conflicts on the writes)
 static_assert((size_t)OZ_VROW * 64 * 16 + 64 * 8 + 64 * 16 <= OZ_SMEM, "staged epilogue fits the stage buffers");
 
+// Adjoint epilogue of one staged tile (rows m0.., strings n0..): per coupling
+// f = |V|^2 g(D) / n (n = <c|c>) and, with s the seed,
+//   t = s (2/n) g V                   -> adj.T (FP64, chunk-local rows)
+//   eta = s df/dD = s (|V|^2/n) g'(D)  -> adj.Hm (if set)
+// and the sums of eta over the tile's strings per row (adj.Hrow), over its
+// rows per string (adj.Hcol), over the tile (scal[2 slot]), and of s f
+// (scal[2 slot + 1]); all sums float-float in a fixed order.
+struct OzSums {
+  float hi, err;
+  __device__ __forceinline__ void add(dfl x) {  // cascaded: hi parts by two_sum, the rest beside
+    const dfl u = two_sum(hi, x.hi);
+    hi = u.hi;
+    err = __fadd_rn(err, __fadd_rn(u.lo, x.lo));
+  }
+  __device__ __forceinline__ dfl value() const { return fast_two_sum(hi, err); }
+};
+
+__device__ __forceinline__ dfl warp_df_sum(dfl v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, dfl{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)});
+  return v;
+}
+
+template <int NS, int NH>
+__device__ __forceinline__ void oz_adjoint_phase2(const OzOperands& op, int64_t M, int64_t N, int64_t m0, int64_t n0,
+                                                  double b, const AdjOut& adj, const float4* sV, const float2* sBase,
+                                                  const int4* sRI) {
+  __shared__ float2 sCol[8][64];
+  __shared__ float2 sTot[8][2];
+  __shared__ float2 sC[3];  // 1/n, s, s 2/n (float-float)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    const double inv_n = 1.0 / adj.g1[0].x;
+    const dfl a = df_from_double(inv_n), c = df_from_double(adj.s), d = df_from_double(2.0 * adj.s * inv_n);
+    sC[0] = make_float2(a.hi, a.lo);
+    sC[1] = make_float2(c.hi, c.lo);
+    sC[2] = make_float2(d.hi, d.lo);
+  }
+  __syncthreads();
+  const dfl inv_n{sC[0].x, sC[0].y}, sd{sC[1].x, sC[1].y}, s2n{sC[2].x, sC[2].y};
+  const bool shifted = b != 0.0;
+  const dfl bb = df_from_double(b * b), b3 = df_from_double(3.0 * b * b);
+  const int64_t ct = gridDim.y;
+  OzSums col[2] = {{0.f, 0.f}, {0.f, 0.f}}, ts{0.f, 0.f}, fs{0.f, 0.f};
+  for (int rr = warp; rr < OZ_BM; rr += 8) {
+    const int64_t row = m0 + rr;
+    if (row >= M) break;
+    const int4 ri = sRI[rr];
+    const float2 bs = sBase[rr];
+    OzSums rs{0.f, 0.f};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int cl = lane + 32 * h;
+      const int64_t colg = n0 + cl;
+      if (colg >= N) continue;
+      const float4 v = sV[rr * OZ_VROW + cl];
+      const dfl vr{v.x, v.y}, vi{v.z, v.w};
+      const dfl p = two_prod(v.x, v.x), qq = two_prod(v.z, v.z);
+      const dfl s2 = two_sum(p.hi, qq.hi);
+      float e = __fadd_rn(__fadd_rn(p.lo, qq.lo), s2.lo);
+      e = __fmaf_rn(__fadd_rn(v.x, v.x), v.y, e);
+      e = __fmaf_rn(__fadd_rn(v.z, v.z), v.w, e);
+      const dfl v2 = fast_two_sum(s2.hi, e);
+      const float2 a = op.eAdf[colg];
+      dfl Dk = df_sub(dfl{bs.x, bs.y}, dfl{a.x, a.y});
+      if (NS >= 1) {
+        const float2 u = op.Udf[(int64_t)ri.x * N + colg];
+        Dk = df_sub(Dk, dfl{u.x, u.y});
+      }
+      if (NS >= 2) {
+        const float2 u = op.Udf[(int64_t)ri.y * N + colg];
+        Dk = df_sub(Dk, dfl{u.x, u.y});
+      }
+      if (NH >= 1) {
+        const float2 u = op.Udf[(int64_t)ri.z * N + colg];
+        Dk = df_add(Dk, dfl{u.x, u.y});
+      }
+      if (NH >= 2) {
+        const float2 u = op.Udf[(int64_t)ri.w * N + colg];
+        Dk = df_add(Dk, dfl{u.x, u.y});
+      }
+      const dfl vn = df_mul(v2, inv_n);  // |V|^2 / n
+      dfl gk, hk;
+      if (!shifted) {  // g = 1/D, dg/dD = -1/D^2
+        gk = df_rcp(Dk);
+        hk = df_mul(df_mul(vn, gk), gk);
+        hk = dfl{-hk.hi, -hk.lo};
+      } else {  // g = D^3 r, dg/dD = D^2 (3 b^2 - D^4) r^2, r = 1/(D^4 + b^2)
+        const dfl D2 = df_sqr(Dk), D4 = df_sqr(D2);
+        const dfl rq = df_rcp(df_add(D4, bb));
+        gk = df_mul(df_mul(Dk, D2), rq);
+        hk = df_mul(df_mul(df_mul(vn, D2), df_sub(b3, D4)), df_sqr(rq));
+      }
+      hk = df_mul(hk, sd);
+      const dfl w = df_mul(s2n, gk);
+      const int64_t o = (row - adj.m_base) * N + colg;
+      adj.T[o] = make_double2(df_to_double(df_mul(w, vr)), df_to_double(df_mul(w, vi)));
+      if (adj.Hm) adj.Hm[o] = df_to_double(hk);
+      rs.add(hk);
+      col[h].add(hk);
+      ts.add(hk);
+      fs.add(df_mul(v2, gk));
+    }
+    const dfl rsum = warp_df_sum(rs.value());  // the row's sum over the tile's strings
+    if (lane == 0) adj.Hrow[(row - adj.m_base) * ct + blockIdx.y] = df_to_double(rsum);
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const dfl c = col[h].value();
+    sCol[warp][lane + 32 * h] = make_float2(c.hi, c.lo);
+  }
+  const dfl t1 = warp_df_sum(ts.value()), t2 = warp_df_sum(fs.value());
+  if (lane == 0) {
+    sTot[warp][0] = make_float2(t1.hi, t1.lo);
+    sTot[warp][1] = make_float2(t2.hi, t2.lo);
+  }
+  __syncthreads();
+  if (tid < 64 && n0 + tid < N) {  // per string, over the 8 warps' rows in warp order
+    dfl c{sCol[0][tid].x, sCol[0][tid].y};
+    for (int w = 1; w < 8; ++w) c = df_add(c, dfl{sCol[w][tid].x, sCol[w][tid].y});
+    adj.Hcol[(int64_t)blockIdx.x * N + n0 + tid] = df_to_double(c);
+  }
+  if (tid == 0) {
+    dfl a{sTot[0][0].x, sTot[0][0].y}, f{sTot[0][1].x, sTot[0][1].y};
+    for (int w = 1; w < 8; ++w) {
+      a = df_add(a, dfl{sTot[w][0].x, sTot[w][0].y});
+      f = df_add(f, dfl{sTot[w][1].x, sTot[w][1].y});
+    }
+    const int64_t slot = (int64_t)blockIdx.x * ct + blockIdx.y;
+    adj.scal[2 * slot] = df_to_double(a);
+    adj.scal[2 * slot + 1] = df_to_double(df_mul(df_mul(f, inv_n), sd));  // s f over the tile
+  }
+}
+
 // NS, NH: the particles and holes of each row of the class (which U terms
 // enter D), so that the epilogue is straight-line code.
-template <int NS, int NH>
+// ADJ: the adjoint pass over the rows [adj.m_base, adj.m_base + adj.Mc) of a
+// row chunk (grid x over the chunk's row tiles): amplitudes and sums of the
+// FP64 kernel's adjoint mode (AdjOut), and no partial.
+template <int NS, int NH, bool ADJ>
 __global__ void __launch_bounds__(256, 1)
 k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows, const double* __restrict__ E0p,
-           double b, double* __restrict__ partial) {
+           double b, double* __restrict__ partial, AdjOut adj) {
   extern __shared__ __align__(16) unsigned char oz_smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 2, wn = warp & 3, g = lane >> 2, t = lane & 3;
-  const int64_t m0 = (int64_t)blockIdx.x * OZ_BM, n0 = (int64_t)blockIdx.y * 64;
+  const int64_t m0 = (ADJ ? adj.m_base : 0) + (int64_t)blockIdx.x * OZ_BM, n0 = (int64_t)blockIdx.y * 64;
+  if (ADJ) M = min(M, adj.m_base + adj.Mc);  // the chunk's last row
   const int Kq = op.Kq;
   auto sA = [&](int st, int s, int r, int k) {
     return (__nv_bfloat16*)(oz_smem + st * OZ_STAGE) + ((s * OZ_BM + r) * OZ_LD + k);
@@ -323,6 +485,10 @@ k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows
     }
   __syncthreads();
 
+  if constexpr (ADJ) {
+    oz_adjoint_phase2<NS, NH>(op, M, N, m0, n0, b, adj, sV, sBase, sRI);
+    return;
+  }
   // Phase 2: one warp per row, lanes over the tile's strings (coalesced reads
   // of the float-float tables), four rows at a time so that each thread has
   // eight independent couplings in flight; eight partial sums, added in a
@@ -407,25 +573,50 @@ k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows
   }
 }
 
-// grid (Mpad / 64, Npad / 64); the shared-memory opt-in is set once per process
-void launch_class_oz(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
-                     const double* E0p, double b, double* partial) {
+// Forward: grid (Mpad / 64, Npad / 64).  Adjoint: grid (row tiles of the
+// chunk, Npad / 64).  The shared-memory opt-in is set once per process.
+template <bool ADJ>
+static void set_oz_attr() {
+  cudaFuncSetAttribute(k_class_oz<2, 0, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+  cudaFuncSetAttribute(k_class_oz<2, 1, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+  cudaFuncSetAttribute(k_class_oz<1, 2, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+  cudaFuncSetAttribute(k_class_oz<0, 2, ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+}
+
+static void launch_class_oz_mode(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N,
+                                 const RowInfo* rows, const double* E0p, double b, double* partial,
+                                 const AdjOut* adj) {
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_class_oz<2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
-    cudaFuncSetAttribute(k_class_oz<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
-    cudaFuncSetAttribute(k_class_oz<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
-    cudaFuncSetAttribute(k_class_oz<0, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM);
+    set_oz_attr<false>();
+    set_oz_attr<true>();
     attr = true;
   }
-  dim3 grid((unsigned)(op.Mpad / OZ_BM), (unsigned)(op.Npad / 64));
+  const AdjOut a = adj ? *adj : AdjOut{};
+  dim3 grid((unsigned)(adj ? (adj->Mc + OZ_BM - 1) / OZ_BM : op.Mpad / OZ_BM), (unsigned)(op.Npad / 64));
+#define E2_OZ_LAUNCH(NS_, NH_)                                                                                   \
+  if (adj)                                                                                                     \
+    (k_class_oz<NS_, NH_, true><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, nullptr, a), ++g_launches);  \
+  else                                                                                                         \
+    (k_class_oz<NS_, NH_, false><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial, a), ++g_launches);
   switch (cls) {  // particles and holes of the rows
-    case 2: (k_class_oz<2, 0><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial), ++g_launches); break;
-    case 5: (k_class_oz<2, 1><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial), ++g_launches); break;
-    case 7: (k_class_oz<1, 2><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial), ++g_launches); break;
-    case 6: (k_class_oz<0, 2><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial), ++g_launches); break;
+    case 2: E2_OZ_LAUNCH(2, 0) break;
+    case 5: E2_OZ_LAUNCH(2, 1) break;
+    case 7: E2_OZ_LAUNCH(1, 2) break;
+    case 6: E2_OZ_LAUNCH(0, 2) break;
     default: break;
   }
+#undef E2_OZ_LAUNCH
+}
+
+void launch_class_oz(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
+                     const double* E0p, double b, double* partial) {
+  launch_class_oz_mode(st, cls, op, M, N, rows, E0p, b, partial, nullptr);
+}
+
+void launch_class_oz_adj(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
+                         const double* E0p, double b, const AdjOut& adj) {
+  launch_class_oz_mode(st, cls, op, M, N, rows, E0p, b, nullptr, &adj);
 }
 
 // ------------------------------------------------------------------ general product

@@ -641,6 +641,23 @@ e2_status build_plan(e2_problem* P) {
     P->o_bGw = ws.take(8 * (size_t)std::max(Lt, 1));
     P->bpart_bytes = size_t(512) << 20;
     P->o_bPart = ws.take(P->bpart_bytes);
+    // slices of the adjoint's products on the sliced GEMM: Gamma_D and
+    // Gamma_W of a row chunk of each dense class, and Cs = B Gamma^ when its
+    // slices take at most 4 GiB (else Cs stays on the FP64 pipe)
+    {
+      size_t oz = 0;
+      for (int c : {2, 5, 7, 4, 6}) {
+        const int64_t Nc = lsize(c), Mc = P->chunk_rows[c];
+        if (P->M[c] == 0 || Nc == 0 || Mc == 0) continue;
+        oz = std::max(oz, zgemm_sliced_bytes(Nc, P->Kp[c], Mc));
+        oz = std::max(oz, zgemm_sliced_bytes(Mc, P->Kp[c], Nc));
+      }
+      const size_t cs = Lt > 0 ? zgemm_sliced_bytes(Lt, npair, npair) : 0;
+      if (cs <= (size_t(4) << 30)) oz = std::max(oz, cs);
+      P->bOz_bytes = oz;
+      P->use_oz_adj = oz > 0;
+      P->o_bOz = ws.take(std::max<size_t>(oz, 256));
+    }
     P->bwd_bytes = ws.top;
   }
 
@@ -769,8 +786,13 @@ e2_status e2_class_tiles_copy(const e2_problem* P, int cls, int32_t* perm, int32
 }
 
 e2_status e2_set_contraction(e2_problem* P, int cls, int mode) {
-  if (!P || cls < E2_CONTRACT_SETUP || cls >= E2_NCLASS || (mode != E2_CONTRACT_FP64 && mode != E2_CONTRACT_SLICED))
+  if (!P || cls < E2_CONTRACT_ADJOINT || cls >= E2_NCLASS || (mode != E2_CONTRACT_FP64 && mode != E2_CONTRACT_SLICED))
     return E2_ERR_INVALID_ARG;
+  if (cls == E2_CONTRACT_ADJOINT) {
+    if (mode == E2_CONTRACT_SLICED && P->bOz_bytes == 0) return E2_ERR_UNSUPPORTED;
+    P->use_oz_adj = mode == E2_CONTRACT_SLICED;
+    return E2_OK;
+  }
   if (cls == E2_CONTRACT_SETUP) {
     if (mode == E2_CONTRACT_SLICED && P->ozS_bytes == 0) return E2_ERR_UNSUPPORTED;
     P->use_oz_setup = mode == E2_CONTRACT_SLICED;
@@ -782,9 +804,13 @@ e2_status e2_set_contraction(e2_problem* P, int cls, int mode) {
 }
 
 e2_status e2_contraction(const e2_problem* P, int cls, int* mode, int* sliced_available) {
-  if (!P || cls < E2_CONTRACT_SETUP || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
-  const bool on = cls == E2_CONTRACT_SETUP ? P->use_oz_setup : P->use_oz[cls];
-  const bool ok = cls == E2_CONTRACT_SETUP ? P->ozS_bytes > 0 : P->oz_ok[cls];
+  if (!P || cls < E2_CONTRACT_ADJOINT || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
+  const bool on = cls == E2_CONTRACT_ADJOINT ? P->use_oz_adj
+                  : cls == E2_CONTRACT_SETUP ? P->use_oz_setup
+                                             : P->use_oz[cls];
+  const bool ok = cls == E2_CONTRACT_ADJOINT ? P->bOz_bytes > 0
+                  : cls == E2_CONTRACT_SETUP ? P->ozS_bytes > 0
+                                             : P->oz_ok[cls];
   if (mode) *mode = on ? E2_CONTRACT_SLICED : E2_CONTRACT_FP64;
   if (sliced_available) *sliced_available = ok ? 1 : 0;
   return E2_OK;
