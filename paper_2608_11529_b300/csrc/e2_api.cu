@@ -331,7 +331,7 @@ void prepare_root(e2_problem* P, unsigned char* ws, cudaStream_t st, const doubl
       unsigned char* sb = slot_base(P, ws, r);
       (k_oz_slice_b<<<(unsigned)(P->oz_npad[cls] / 32), 256, 0, st>>>(
            Dcls[cls], N, 1, 0, P->Kp[cls], N, P->oz_kq[cls], P->oz_npad[cls], (__nv_bfloat16*)(sb + P->o_ozB[cls]),
-           (int*)(sb + P->o_ozCx[cls])), ++g_launches);
+           (int*)(sb + P->o_ozCx[cls]), nullptr, P->Kp[cls]), ++g_launches);
     }
   double2* g1 = (double2*)(ws + P->o_g1 + P->g_stride * r);
   double2* g2 = (double2*)(ws + P->o_g2 + P->g_stride * r);

@@ -334,7 +334,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
                          double2* GD, double2* GX, int gx_beta, int bn, int tcls) {
         const int64_t nb = Ltab.n;
         if (nb == 0 || S == 0) return;
-        const bool tl = tcls >= 0 && P->use_cols[tcls];
+        const bool tl = !P->use_oz_adj && tcls >= 0 && P->use_cols[tcls];
+        unsigned char* oz = (unsigned char*)B(P->o_bOz);
         const ColPlan& cpt = P->cplan[tcls >= 0 ? tcls : 0];
         const ColTiles ctt = tl ? col_tiles(P, ws, r, tcls) : ColTiles{nullptr, nullptr, nullptr, nullptr};
         int64_t rcap = (int64_t)(P->tsh_bytes / (16 * (size_t)S * nb));
@@ -348,7 +349,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           const double2* Xr = Xint + (int64_t)r0 * S * nx_;
           if (tl)
             zgemm_gd_tiles(st, cpt, ctt, Xr, nx_, Tsh, nb, k, (double2*)B(P->o_bGDc), r0 > 0, 0);
-          else
+          else if (!(P->use_oz_adj &&  // Gamma_D^T = Tsh^T X: Tsh is the row operand
+                     zgemm_sliced(st, nb, nx_, k, Tsh, 1, nb, 0, Xr, nx_, 1, 0, GD, 1, nb, 1, -1, oz, P->bOz_bytes)))
             zgemm(st, nx_, nb, k, Xr, 1, nx_, 0, Tsh, nb, 1, 0, GD, nb, 1, 1);
           if (want_B) {
             double2* GXr = GX + (int64_t)r0 * S * nx_;
@@ -361,7 +363,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
               (k_gw_reduce<<<blocks(k * nx_), 256, 0, st>>>(ctt.tdesc, (const int32_t*)(ws + cpt.o_pos), cpt.tiles,
                                                            P->Kp[tcls], (const double2*)B(P->o_bGWc), cpt.krows, k,
                                                            GXr, nx_, nx_), ++g_launches);
-            } else {
+            } else if (!(P->use_oz_adj && zgemm_sliced(st, k, nx_, nb, Tsh, nb, 1, 0, D, 1, nb, 0, GXr, nx_, 1,
+                                                       gx_beta, -1, oz, P->bOz_bytes))) {
               zgemm(st, k, nx_, nb, Tsh, nb, 1, 0, D, 1, nb, 0, GXr, nx_, 1, gx_beta, bn);
             }
           }

@@ -139,40 +139,71 @@ __global__ void k_oz_slice_a(const double2* __restrict__ A, int64_t sam, int64_t
   if (lane == 0) rexp[row] = e;
 }
 
-// Column slices of a complex K x N operand B (element (k, n) at B[k sbk +
-// n sbn], conjugated if conj): out[s][2n + h][k'] with
-//   h = 0: (Re B[k], -Im B[k]) over k' = k, K + k;  h = 1: (Im B[k], Re B[k]),
-// zero to Kq and for the padding columns N..Npad-1; one exponent per column.
-// Block: 32 columns, 8 warps over k.
-__global__ void k_oz_slice_b(const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conj, int K, int64_t N,
-                             int Kq, int64_t Npad, __nv_bfloat16* __restrict__ out, int* __restrict__ cexp) {
+// Largest magnitude (bit pattern) per column of a complex K x N operand B,
+// over chunks of kchunk rows: grid (ceil(N / 32), ceil(K / kchunk)), atomicMax
+// into cmax (zeroed by the caller; a maximum does not depend on the order).
+__global__ void k_oz_colmax(const double2* __restrict__ B, int64_t sbk, int64_t sbn, int K, int64_t N, int kchunk,
+                            unsigned long long* __restrict__ cmax) {
   __shared__ unsigned long long sm[8][32];
-  __shared__ int se[32];
   const int c = threadIdx.x & 31, kk = threadIdx.x >> 5;
   const int64_t col = (int64_t)blockIdx.x * 32 + c;
-  const bool ok = col < N;
+  const int k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
   unsigned long long m = 0;
-  if (ok)
-    for (int k = kk; k < K; k += 8) {
+  if (col < N)
+    for (int k = k0 + kk; k < k1; k += 8) {
       const double2 d = B[(int64_t)k * sbk + col * sbn];
       m = max(m, max(oz_mag(d.x), oz_mag(d.y)));
     }
   sm[kk][c] = m;
   __syncthreads();
-  if (kk == 0) {
+  if (kk == 0 && col < N) {
     unsigned long long t = 0;
     for (int i = 0; i < 8; ++i) t = max(t, sm[i][c]);
-    const int e = oz_exp(t);
-    se[c] = e;
-    if (col < Npad) cexp[col] = e;
+    atomicMax(cmax + col, t);
+  }
+}
+
+// Column slices of a complex K x N operand B (element (k, n) at B[k sbk +
+// n sbn], conjugated if conj): out[s][2n + h][k'] with
+//   h = 0: (Re B[k], -Im B[k]) over k' = k, K + k;  h = 1: (Im B[k], Re B[k]),
+// zero to Kq and for the padding columns N..Npad-1; one exponent per column,
+// from cmax (k_oz_colmax) or, when cmax is null, found by the block itself
+// (then grid y must be 1).  Block: 32 columns x 8 warps over the rows
+// [blockIdx.y kchunk, +kchunk).
+__global__ void k_oz_slice_b(const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conj, int K, int64_t N,
+                             int Kq, int64_t Npad, __nv_bfloat16* __restrict__ out, int* __restrict__ cexp,
+                             const unsigned long long* __restrict__ cmax, int kchunk) {
+  __shared__ unsigned long long sm[8][32];
+  __shared__ int se[32];
+  const int c = threadIdx.x & 31, kk = threadIdx.x >> 5;
+  const int64_t col = (int64_t)blockIdx.x * 32 + c;
+  const bool ok = col < N;
+  if (cmax) {
+    if (kk == 0) se[c] = ok ? oz_exp(cmax[col]) : 0;
+  } else {
+    unsigned long long m = 0;
+    if (ok)
+      for (int k = kk; k < K; k += 8) {
+        const double2 d = B[(int64_t)k * sbk + col * sbn];
+        m = max(m, max(oz_mag(d.x), oz_mag(d.y)));
+      }
+    sm[kk][c] = m;
+    __syncthreads();
+    if (kk == 0) {
+      unsigned long long t = 0;
+      for (int i = 0; i < 8; ++i) t = max(t, sm[i][c]);
+      se[c] = oz_exp(t);
+    }
   }
   __syncthreads();
   if (col >= Npad) return;
   const int e = se[c];
+  if (blockIdx.y == 0 && kk == 0) cexp[col] = e;
   const int64_t ps = 2 * Npad * (int64_t)Kq;  // one slice
   __nv_bfloat16* b0 = out + (2 * col) * (int64_t)Kq;
   __nv_bfloat16* b1 = b0 + Kq;
-  for (int k = kk; k < K; k += 8) {
+  const int k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
+  for (int k = k0 + kk; k < k1; k += 8) {
     const double2 d = ok ? B[(int64_t)k * sbk + col * sbn] : make_double2(0.0, 0.0);
     float sr[OZ_S], sim[OZ_S];
     oz_digits(d.x, e, false, sr);
@@ -185,13 +216,15 @@ __global__ void k_oz_slice_b(const double2* __restrict__ B, int64_t sbk, int64_t
       b1[i * ps + K + k] = __float2bfloat16_rn(sr[i]);
     }
   }
-  const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
-  for (int k = 2 * K + kk; k < Kq; k += 8)
+  if (blockIdx.y == 0) {
+    const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
+    for (int k = 2 * K + kk; k < Kq; k += 8)
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i) {
-      b0[i * ps + k] = z;
-      b1[i * ps + k] = z;
-    }
+      for (int i = 0; i < OZ_S; ++i) {
+        b0[i * ps + k] = z;
+        b1[i * ps + k] = z;
+      }
+  }
 }
 
 // Float-float copies of e_A [n] and U [rows][n].
@@ -773,8 +806,12 @@ size_t zgemm_sliced_bytes(int64_t M, int64_t N, int64_t K) {
   const int64_t Mpad = (M + OG_BM - 1) / OG_BM * OG_BM, Npad = (N + 31) / 32 * 32;
   const int64_t Kq = (2 * K + 31) / 32 * 32;
   return al((size_t)2 * OZ_S * Mpad * Kq) + al(4 * (size_t)Mpad) + al((size_t)2 * OZ_S * 2 * Npad * Kq) +
-         al(4 * (size_t)Npad);
+         al(4 * (size_t)Npad) + al(8 * (size_t)Npad);
 }
+
+// the column slicer's rows per block: all of them for a short contraction,
+// chunks of 256 (after a column-maximum pass) for a long one
+static constexpr int OZ_KCHUNK = 256;
 
 bool zgemm_sliced(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak,
                   int conjA, const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm,
@@ -794,11 +831,22 @@ bool zgemm_sliced(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double
   // B's slices first, so that a caller reusing them (reuse_b) keeps them in place
   __nv_bfloat16* Bs = (__nv_bfloat16*)scratch;
   int* cx = (int*)(scratch + al((size_t)2 * OZ_S * 2 * Npad * Kq));
-  __nv_bfloat16* As = (__nv_bfloat16*)((unsigned char*)cx + al(4 * (size_t)Npad));
+  unsigned long long* cm = (unsigned long long*)((unsigned char*)cx + al(4 * (size_t)Npad));
+  __nv_bfloat16* As = (__nv_bfloat16*)((unsigned char*)cm + al(8 * (size_t)Npad));
   int* rx = (int*)((unsigned char*)As + al((size_t)2 * OZ_S * Mpad * Kq));
-  if (!reuse_b)
-    (k_oz_slice_b<<<(unsigned)(Npad / 32), 256, 0, st>>>(B, sbk, sbn, conjB, (int)K, Nb, Kq, Npad, Bs, cx),
-     ++g_launches);
+  if (!reuse_b) {
+    if (K <= 4 * OZ_KCHUNK) {
+      (k_oz_slice_b<<<(unsigned)(Npad / 32), 256, 0, st>>>(B, sbk, sbn, conjB, (int)K, Nb, Kq, Npad, Bs, cx, nullptr,
+                                                          (int)K), ++g_launches);
+    } else {  // many rows: the column maxima first, then the slices of each chunk in parallel
+      const unsigned kb = (unsigned)((K + OZ_KCHUNK - 1) / OZ_KCHUNK);
+      cudaMemsetAsync(cm, 0, 8 * (size_t)Npad, st);
+      (k_oz_colmax<<<dim3((unsigned)((Nb + 31) / 32), kb), 256, 0, st>>>(B, sbk, sbn, (int)K, Nb, OZ_KCHUNK, cm),
+       ++g_launches);
+      (k_oz_slice_b<<<dim3((unsigned)(Npad / 32), kb), 256, 0, st>>>(B, sbk, sbn, conjB, (int)K, Nb, Kq, Npad, Bs, cx,
+                                                                     cm, OZ_KCHUNK), ++g_launches);
+    }
+  }
   (k_oz_slice_a<<<(unsigned)(Mpad / 8), 256, 0, st>>>(A, sam, sak, conjA, M, (int)K, Kq, Mpad, As, rx),
    ++g_launches);
   OzGemm q{As, Mpad, rx, Bs, Npad, cx, Kq, M, N, C, csm, csn, beta, lower};

@@ -652,6 +652,19 @@ e2_status build_plan(e2_problem* P) {
         oz = std::max(oz, zgemm_sliced_bytes(Nc, P->Kp[c], Mc));
         oz = std::max(oz, zgemm_sliced_bytes(Mc, P->Kp[c], Nc));
       }
+      // shifted amplitudes of the gather classes: (table list, shifts S, width nx, rows)
+      struct Sh { int lcls; int64_t S, nx, rows; };
+      const Sh shs[3] = {{2, P->na, P->ntp, P->nvc}, {5, P->ntp, P->na, P->ncc}, {2, P->ntp, P->ntp, 1}};
+      const int gcls[3] = {1, 3, 0};
+      for (int q = 0; q < 3; ++q) {
+        const int64_t nb = lsize(shs[q].lcls);
+        if (P->list_of[gcls[q]] < 0 || nb == 0 || shs[q].S == 0 || shs[q].nx == 0) continue;
+        const int64_t k = std::max<int64_t>(
+            1, std::min<int64_t>(shs[q].rows * shs[q].S, (int64_t)(P->tsh_bytes / (16 * (size_t)nb))) / shs[q].S *
+                   shs[q].S);
+        oz = std::max(oz, zgemm_sliced_bytes(nb, shs[q].nx, k));
+        oz = std::max(oz, zgemm_sliced_bytes(k, shs[q].nx, nb));
+      }
       const size_t cs = Lt > 0 ? zgemm_sliced_bytes(Lt, npair, npair) : 0;
       if (cs <= (size_t(4) << 30)) oz = std::max(oz, cs);
       P->bOz_bytes = oz;
