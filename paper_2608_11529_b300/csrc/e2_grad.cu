@@ -230,7 +230,11 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
                                            (unsigned char*)B(P->o_bOz), P->bOz_bytes))) {
             zgemm(st, Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0, GW, Kp, 1, 0, Kp >= 64 ? 64 : 16);
           }
-          (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na), ++g_launches);
+          if (P->use_oz[cls])  // eta came as float-float pairs from the sliced adjoint
+            (k_hocc_df<<<blocks(Mc, 8), 256, 0, st>>>((const float2*)adj.Hm, L, na, Mc, Hocc + m0 * na),
+             ++g_launches);
+          else
+            (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na), ++g_launches);
         }
       }
       if (tiled)

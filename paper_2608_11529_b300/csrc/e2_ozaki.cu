@@ -124,8 +124,7 @@ __global__ void k_oz_slice_a(const double2* __restrict__ A, int64_t sam, int64_t
     }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   const int e = oz_exp(m);
-  for (int k = lane; k < Kq; k += 32) {
-    float sl[OZ_S];
+  auto cut = [&](int k, float (&sl)[OZ_S]) {
     if (row < M && k < 2 * K) {
       if (k < K) oz_digits(a[k * sak].x, e, false, sl);
       else oz_digits(a[(k - K) * sak].y, e, conj != 0, sl);
@@ -133,8 +132,14 @@ __global__ void k_oz_slice_a(const double2* __restrict__ A, int64_t sam, int64_t
 #pragma unroll
       for (int i = 0; i < OZ_S; ++i) sl[i] = 0.0f;
     }
+  };
+  for (int k = 2 * lane; k < Kq; k += 64) {  // two real k per lane: one 4-byte store per slice (Kq is even)
+    float s0[OZ_S], s1[OZ_S];
+    cut(k, s0);
+    cut(k + 1, s1);
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i) out[((int64_t)i * Mpad + row) * Kq + k] = __float2bfloat16_rn(sl[i]);
+    for (int i = 0; i < OZ_S; ++i)
+      *(__nv_bfloat162*)(out + ((int64_t)i * Mpad + row) * Kq + k) = __floats2bfloat162_rn(s0[i], s1[i]);
   }
   if (lane == 0) rexp[row] = e;
 }
@@ -257,7 +262,7 @@ static_assert((size_t)OZ_VROW * 64 * 16 + 64 * 8 + 64 * 16 <= OZ_SMEM, "staged e
 // Adjoint epilogue of one staged tile (rows m0.., strings n0..): per coupling
 // f = |V|^2 g(D) / n (n = <c|c>) and, with s the seed,
 //   t = s (2/n) g V                   -> adj.T (FP64, chunk-local rows)
-//   eta = s df/dD = s (|V|^2/n) g'(D)  -> adj.Hm (if set)
+//   eta = s df/dD = s (|V|^2/n) g'(D)  -> adj.Hm (if set; float-float pairs)
 // and the sums of eta over the tile's strings per row (adj.Hrow), over its
 // rows per string (adj.Hcol), over the tile (scal[2 slot]), and of s f
 // (scal[2 slot + 1]); all sums float-float in a fixed order.
@@ -352,7 +357,7 @@ __device__ __forceinline__ void oz_adjoint_phase2(const OzOperands& op, int64_t 
       const dfl w = df_mul(s2n, gk);
       const int64_t o = (row - adj.m_base) * N + colg;
       adj.T[o] = make_double2(df_to_double(df_mul(w, vr)), df_to_double(df_mul(w, vi)));
-      if (adj.Hm) adj.Hm[o] = df_to_double(hk);
+      if (adj.Hm) ((float2*)adj.Hm)[o] = make_float2(hk.hi, hk.lo);  // float-float, for k_hocc_df
       rs.add(hk);
       col[h].add(hk);
       ts.add(hk);
@@ -680,7 +685,7 @@ constexpr int OG_BM = 64, OG_BNR = 64, OG_BK = 32, OG_LD = OG_BK + 8;
 constexpr size_t OG_STAGE = (size_t)OZ_S * (OG_BM + OG_BNR) * OG_LD * 2;
 constexpr size_t OG_SMEM = 2 * OG_STAGE;
 
-__global__ void __launch_bounds__(256, 1) k_zgemm_sl(OzGemm q) {
+__global__ void __launch_bounds__(256, 2) k_zgemm_sl(OzGemm q) {
   extern __shared__ __align__(16) unsigned char og_smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 2, wn = warp & 3, g = lane >> 2, t = lane & 3;
@@ -853,6 +858,26 @@ bool zgemm_sliced(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double
   dim3 grid((unsigned)(Mpad / OG_BM), (unsigned)((N + 31) / 32));
   (k_zgemm_sl<<<grid, 256, OG_SMEM, st>>>(q), ++g_launches);
   return true;
+}
+
+// Per-row occupation sums of eta stored as float-float pairs (the sliced
+// adjoint's adj.Hm): Hocc[r][t] = sum_A eta[r][A] [t occupied in A].  One warp
+// per row, lane t < na sums its spinor over the row's strings in string order
+// (reads are broadcast across the warp); cascaded float-float sums.
+__global__ void k_hocc_df(const float2* __restrict__ H, DevList Ls, int na, int64_t rows, double* __restrict__ Hocc) {
+  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int t = threadIdx.x & 31;
+  if (r >= rows) return;
+  const float2* h = H + r * Ls.n;
+  OzSums acc[2] = {{0.f, 0.f}, {0.f, 0.f}};  // spinors t and t + 32
+  for (int64_t g = 0; g < Ls.n; ++g) {
+    const float2 v = h[g];
+    const uint64_t A = Ls.str[g];
+    if ((A >> t) & 1) acc[0].add(dfl{v.x, v.y});
+    if (t + 32 < na && ((A >> (t + 32)) & 1)) acc[1].add(dfl{v.x, v.y});
+  }
+  if (t < na) Hocc[r * na + t] = df_to_double(acc[0].value());
+  if (t + 32 < na) Hocc[r * na + t + 32] = df_to_double(acc[1].value());
 }
 
 }  // namespace e2
