@@ -231,8 +231,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
             zgemm(st, Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0, GW, Kp, 1, 0, Kp >= 64 ? 64 : 16);
           }
           if (P->use_oz[cls])  // eta came as float-float pairs from the sliced adjoint
-            (k_hocc_df<<<blocks(Mc, 8), 256, 0, st>>>((const float2*)adj.Hm, L, na, Mc, Hocc + m0 * na),
-             ++g_launches);
+            launch_hocc_df(st, (const float2*)adj.Hm, L, na, Mc, Hocc + m0 * na);
           else
             (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na), ++g_launches);
         }
@@ -277,8 +276,16 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         const int64_t M22 = P->ncp * P->nvp;
         double* hs22 = (double*)B(P->o_bHs22);
         double* P22 = (double*)B(P->o_bP22);
-        (k_class22_rows<<<(unsigned)M22, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G,
-                                                       X.E0p + r, b, s, g1, hs22, Hocc, P22), ++g_launches);
+        const HostList& H8 = P->lists[P->list_of[8]];
+        if (P->use_oz_adj && H8.df) {  // float-float per-row sums
+          float2* c2 = (float2*)B(P->o_bC2);
+          (k_c2df<<<blocks(L.n), 256, 0, st>>>(c, L.n, g1, c2), ++g_launches);
+          launch_class22_rows_df(st, L, X.sp, (const float2*)(ws + H8.o_eAdf), (const float2*)(ws + H8.o_Udf), c2,
+                                 (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, s, M22, hs22, Hocc, P22);
+        } else {
+          (k_class22_rows<<<(unsigned)M22, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G,
+                                                         X.E0p + r, b, s, g1, hs22, Hocc, P22), ++g_launches);
+        }
         zpair(8, hs22, Hocc);
         (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
         const int Lt = d.L_coulomb + d.L_extra;

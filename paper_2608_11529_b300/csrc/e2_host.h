@@ -131,6 +131,7 @@ struct e2_problem {
   size_t o_ozS = 0, ozS_bytes = 0;   // their scratch (over the region the D tables take later)
   bool use_oz_adj = false;           // the adjoint's Gamma products and Cs on the sliced GEMM
   size_t o_bOz = 0, bOz_bytes = 0;   // their scratch (backward region)
+  size_t o_bC2 = 0;                  // |c_A|^2 / n of the class-(2,2) strings, float-float (backward)
   size_t o_ozA[E2_NCLASS] = {}, o_ozRx[E2_NCLASS] = {}, o_ozB[E2_NCLASS] = {}, o_ozCx[E2_NCLASS] = {};
 };
 
@@ -182,6 +183,13 @@ OzOperands oz_operands(const e2_problem* P, unsigned char* ws, int r, int cls);
 // per 64 x 64 tile, [column tile][row tile] (e2_ozaki.cu)
 void launch_class_oz(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
                      const double* E0p, double b, double* partial);
+// float-float forms of per-row adjoint sums (e2_ozaki.cu): occupation sums of
+// eta given as float-float pairs, and the per-row sums of class (2,2)
+void launch_hocc_df(cudaStream_t st, const float2* H, const DevList& L, int na, int64_t rows, double* Hocc);
+void launch_class22_rows_df(cudaStream_t st, const DevList& L, const DevSpace& sp, const float2* eAdf,
+                            const float2* Udf, const float2* c2df, const double* g2, const double* epsh,
+                            const double* G, const double* E0p, double b, double s, int64_t rows, double* hsum,
+                            double* Hocc, double* P22);
 // its adjoint mode over one row chunk of the backward pass (see AdjOut)
 void launch_class_oz_adj(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
                          const double* E0p, double b, const AdjOut& adj);

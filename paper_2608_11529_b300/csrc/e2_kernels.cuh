@@ -59,7 +59,7 @@ __global__ void k_oz_slice_a(const double2* A, int64_t sam, int64_t sak, int con
                              int64_t Mpad, __nv_bfloat16* out, int* rexp);
 __global__ void k_oz_slice_b(const double2* B, int64_t sbk, int64_t sbn, int conj, int K, int64_t N, int Kq,
                              int64_t Npad, __nv_bfloat16* out, int* cexp, const unsigned long long* cmax, int kchunk);
-__global__ void k_hocc_df(const float2* H, DevList Ls, int na, int64_t rows, double* Hocc);
+__global__ void k_c2df(const double2* c, int64_t n, const double2* g1, float2* out);
 __global__ void k_oz_colmax(const double2* B, int64_t sbk, int64_t sbn, int K, int64_t N, int kchunk,
                             unsigned long long* cmax);
 __global__ void k_oz_tables(const double* eA, const double* U, int64_t n, int64_t rows, float2* eAdf, float2* Udf);

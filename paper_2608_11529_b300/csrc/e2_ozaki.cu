@@ -860,24 +860,166 @@ bool zgemm_sliced(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double
   return true;
 }
 
+// Fixed-order block sum of NV float-float values per thread (warp trees,
+// then warps in order); thread t < nv of the block returns value t.
+template <int NV>
+__device__ __forceinline__ dfl block_df_sums(const dfl (&v)[NV], int nv, float2 (*sred)[NV]) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int t = 0; t < NV; ++t) {
+    const dfl x = warp_df_sum(v[t]);
+    if (lane == 0) sred[warp][t] = make_float2(x.hi, x.lo);
+  }
+  __syncthreads();
+  dfl tot{0.f, 0.f};
+  if ((int)threadIdx.x < nv) {
+    tot = dfl{sred[0][threadIdx.x].x, sred[0][threadIdx.x].y};
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot = df_add(tot, dfl{sred[w][threadIdx.x].x, sred[w][threadIdx.x].y});
+  }
+  return tot;
+}
+
 // Per-row occupation sums of eta stored as float-float pairs (the sliced
-// adjoint's adj.Hm): Hocc[r][t] = sum_A eta[r][A] [t occupied in A].  One warp
-// per row, lane t < na sums its spinor over the row's strings in string order
-// (reads are broadcast across the warp); cascaded float-float sums.
-__global__ void k_hocc_df(const float2* __restrict__ H, DevList Ls, int na, int64_t rows, double* __restrict__ Hocc) {
-  const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int t = threadIdx.x & 31;
-  if (r >= rows) return;
+// adjoint's adj.Hm): Hocc[r][t] = sum_A eta[r][A] [t occupied in A].  One
+// block per row, threads over its strings; per thread NA cascaded sums
+// (unrolled, predicated on the occupation bit), then a fixed-order block sum.
+template <int NA>
+__global__ void __launch_bounds__(256) k_hocc_df(const float2* __restrict__ H, DevList Ls, int na,
+                                                 double* __restrict__ Hocc) {
+  __shared__ float2 sred[8][NA];
+  const int64_t r = blockIdx.x;
   const float2* h = H + r * Ls.n;
-  OzSums acc[2] = {{0.f, 0.f}, {0.f, 0.f}};  // spinors t and t + 32
-  for (int64_t g = 0; g < Ls.n; ++g) {
+  OzSums acc[NA];
+#pragma unroll
+  for (int t = 0; t < NA; ++t) acc[t] = OzSums{0.f, 0.f};
+  for (int64_t g = threadIdx.x; g < Ls.n; g += blockDim.x) {
     const float2 v = h[g];
     const uint64_t A = Ls.str[g];
-    if ((A >> t) & 1) acc[0].add(dfl{v.x, v.y});
-    if (t + 32 < na && ((A >> (t + 32)) & 1)) acc[1].add(dfl{v.x, v.y});
+#pragma unroll
+    for (int t = 0; t < NA; ++t)
+      if ((A >> t) & 1) acc[t].add(dfl{v.x, v.y});
   }
-  if (t < na) Hocc[r * na + t] = df_to_double(acc[0].value());
-  if (t + 32 < na) Hocc[r * na + t + 32] = df_to_double(acc[1].value());
+  dfl vals[NA];
+#pragma unroll
+  for (int t = 0; t < NA; ++t) vals[t] = acc[t].value();
+  const dfl tot = block_df_sums<NA>(vals, na, sred);
+  if ((int)threadIdx.x < na) Hocc[r * na + threadIdx.x] = df_to_double(tot);
+}
+
+void launch_hocc_df(cudaStream_t st, const float2* H, const DevList& L, int na, int64_t rows, double* Hocc) {
+  if (rows <= 0) return;
+  if (na <= 16) (k_hocc_df<16><<<(unsigned)rows, 256, 0, st>>>(H, L, na, Hocc), ++g_launches);
+  else if (na <= 24) (k_hocc_df<24><<<(unsigned)rows, 256, 0, st>>>(H, L, na, Hocc), ++g_launches);
+  else if (na <= 32) (k_hocc_df<32><<<(unsigned)rows, 256, 0, st>>>(H, L, na, Hocc), ++g_launches);
+  else (k_hocc_df<64><<<(unsigned)rows, 256, 0, st>>>(H, L, na, Hocc), ++g_launches);
+}
+
+// |c_A|^2 / <c|c> as float-float pairs (the weights of class (2,2))
+__global__ void k_c2df(const double2* __restrict__ c, int64_t n, const double2* __restrict__ g1,
+                       float2* __restrict__ out) {
+  const int64_t A = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (A >= n) return;
+  const double2 v = c[A];
+  const dfl d = df_from_double((v.x * v.x + v.y * v.y) / g1[0].x);
+  out[A] = make_float2(d.hi, d.lo);
+}
+
+// Class (2,2), per row (i<j, a<b) over all strings A, in float-float (the
+// FP64 kernel k_class22_rows computes the same sums): with w = |<ab||ij>|^2
+// and f = w c2_A g(D), c2_A = |c_A|^2 / n,
+//   hsum[row] = s sum_A df/dD,  P22[row] = s sum_A g c2_A (df/dw),
+//   Hocc[row][t] = s sum_A df/dD [t in A],
+// D = E0' - e_A - chi_ij^ab - U[a,A] - U[b,A] + U[i,A] + U[j,A].
+template <int NA>
+__global__ void __launch_bounds__(256)
+k_class22_rows_df(DevList Ls, DevSpace sp, const float2* __restrict__ eAdf, const float2* __restrict__ Udf,
+                  const float2* __restrict__ c2df, const double* __restrict__ g2, const double* __restrict__ epsh,
+                  const double* __restrict__ G, const double* __restrict__ E0p, double b, double s,
+                  double* __restrict__ hsum, double* __restrict__ Hocc, double* __restrict__ P22) {
+  __shared__ float2 sred[8][NA + 2];
+  __shared__ float2 sRow[2];  // E0' - chi, w
+  const int64_t nvp = pairs(sp.nvc);
+  const int64_t row = blockIdx.x;
+  int iu, ju, au, bu;
+  pair_decode(row / nvp, iu, ju);
+  pair_decode(row % nvp, au, bu);
+  if (threadIdx.x == 0) {
+    const int gi = sp.cc[iu], gj = sp.cc[ju], ga = sp.vc[au], gb = sp.vc[bu];
+    const double chi = -epsh[gi] - epsh[gj] + G[(int64_t)gi * sp.n + gj] + epsh[ga] + epsh[gb] +
+                       G[(int64_t)ga * sp.n + gb] - G[(int64_t)gi * sp.n + ga] - G[(int64_t)gi * sp.n + gb] -
+                       G[(int64_t)gj * sp.n + ga] - G[(int64_t)gj * sp.n + gb];
+    const dfl base = df_from_double(*E0p - chi), w = df_from_double(g2[row]);
+    sRow[0] = make_float2(base.hi, base.lo);
+    sRow[1] = make_float2(w.hi, w.lo);
+  }
+  __syncthreads();
+  const dfl base{sRow[0].x, sRow[0].y}, w{sRow[1].x, sRow[1].y};
+  const bool shifted = b != 0.0;
+  const dfl bb = df_from_double(b * b), b3 = df_from_double(3.0 * b * b);
+  const float2* Ua = Udf + (int64_t)(sp.ncc + au) * Ls.n;
+  const float2* Ub = Udf + (int64_t)(sp.ncc + bu) * Ls.n;
+  const float2* Ui = Udf + (int64_t)iu * Ls.n;
+  const float2* Uj = Udf + (int64_t)ju * Ls.n;
+  OzSums ho[NA], hs{0.f, 0.f}, p22{0.f, 0.f};
+#pragma unroll
+  for (int t = 0; t < NA; ++t) ho[t] = OzSums{0.f, 0.f};
+  for (int64_t A = threadIdx.x; A < Ls.n; A += blockDim.x) {
+    const float2 e = eAdf[A], ua = Ua[A], ub = Ub[A], ui = Ui[A], uj = Uj[A], cc = c2df[A];
+    dfl D = df_sub(base, dfl{e.x, e.y});
+    D = df_sub(D, dfl{ua.x, ua.y});
+    D = df_sub(D, dfl{ub.x, ub.y});
+    D = df_add(D, dfl{ui.x, ui.y});
+    D = df_add(D, dfl{uj.x, uj.y});
+    const dfl c2{cc.x, cc.y};
+    dfl gk, hw;  // g and w dg/dD
+    if (!shifted) {
+      gk = df_rcp(D);
+      hw = df_mul(df_mul(w, gk), gk);
+      hw = dfl{-hw.hi, -hw.lo};
+    } else {
+      const dfl D2 = df_sqr(D), D4 = df_sqr(D2);
+      const dfl rq = df_rcp(df_add(D4, bb));
+      gk = df_mul(df_mul(D, D2), rq);
+      hw = df_mul(df_mul(df_mul(w, D2), df_sub(b3, D4)), df_sqr(rq));
+    }
+    const dfl hk = df_mul(c2, hw);
+    hs.add(hk);
+    p22.add(df_mul(gk, c2));
+    const uint64_t bits = Ls.str[A];
+#pragma unroll
+    for (int t = 0; t < NA; ++t)
+      if ((bits >> t) & 1) ho[t].add(hk);
+  }
+  dfl vals[NA + 2];
+#pragma unroll
+  for (int t = 0; t < NA; ++t) vals[t] = ho[t].value();
+  vals[NA] = hs.value();
+  vals[NA + 1] = p22.value();
+  const int na = sp.n_act;
+  // the block's sums: thread t < na gets Hocc[t]; NA and NA + 1 get hsum, P22
+  const int t = threadIdx.x;
+  const dfl tot = block_df_sums<NA + 2>(vals, NA + 2, sred);
+  const dfl sd = df_from_double(s);
+  if (t < na) Hocc[row * na + t] = df_to_double(df_mul(tot, sd));
+  if (t == NA) hsum[row] = df_to_double(df_mul(tot, sd));
+  if (t == NA + 1) P22[row] = df_to_double(df_mul(tot, sd));
+}
+
+void launch_class22_rows_df(cudaStream_t st, const DevList& L, const DevSpace& sp, const float2* eAdf,
+                            const float2* Udf, const float2* c2df, const double* g2, const double* epsh,
+                            const double* G, const double* E0p, double b, double s, int64_t rows, double* hsum,
+                            double* Hocc, double* P22) {
+  if (rows <= 0) return;
+  const int na = sp.n_act;
+#define E2_R22(NA_)                                                                                             \
+  (k_class22_rows_df<NA_><<<(unsigned)rows, 256, 0, st>>>(L, sp, eAdf, Udf, c2df, g2, epsh, G, E0p, b, s, hsum, \
+                                                          Hocc, P22),                                           \
+   ++g_launches)
+  if (na <= 16) E2_R22(16);
+  else if (na <= 24) E2_R22(24);
+  else if (na <= 32) E2_R22(32);
+  else E2_R22(64);
+#undef E2_R22
 }
 
 }  // namespace e2

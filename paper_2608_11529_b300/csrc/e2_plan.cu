@@ -392,12 +392,17 @@ e2_status build_plan(e2_problem* P) {
       if (!ldf[li]) extra += 8 * (size_t)(P->nx + 2) * P->lists[li].n;
       ldf[li] = true;
     }
+    // the class-(2,2) list's tables too (its float-float adjoint)
+    const int l8 = P->list_of[8];
+    const bool d8 = ((d.class_mask >> 8) & 1u) && P->M[8] > 0 && l8 >= 0 && P->lists[l8].n > 0;
+    if (d8 && !ldf[l8]) extra += 8 * (size_t)(P->nx + 2) * P->lists[l8].n;
     const bool fits = extra <= (size_t(16) << 30);
     for (int c : {2, 5, 7, 6}) {
       P->oz_ok[c] = P->oz_ok[c] && fits;
       P->use_oz[c] = P->oz_ok[c];
       if (P->oz_ok[c]) P->lists[P->list_of[c]].df = true;
     }
+    if (d8 && fits) P->lists[l8].df = true;
   }
   for (HostList& L : P->lists) {
     L.o_str = ws.take(sizeof(uint64_t) * std::max<int64_t>(L.n, 1));
@@ -670,6 +675,7 @@ e2_status build_plan(e2_problem* P) {
       P->bOz_bytes = oz;
       P->use_oz_adj = oz > 0;
       P->o_bOz = ws.take(std::max<size_t>(oz, 256));
+      P->o_bC2 = ws.take(8 * (size_t)std::max<int64_t>(lsize(8), 1));
     }
     P->bwd_bytes = ws.top;
   }
