@@ -287,9 +287,8 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
   // row slices of W for the classes on the sliced contraction
   for (int c : {2, 5, 7, 6})
     if (P->use_oz[c] && P->part_cnt[c] > 0)
-      (k_oz_slice_a<<<(unsigned)(P->oz_mpad[c] / 8), 256, 0, st>>>(
-           (const double2*)(ws + P->o_W[c]), P->Kp[c], 1, 0, P->M[c], P->Kp[c], P->oz_kq[c], P->oz_mpad[c],
-           (__nv_bfloat16*)(ws + P->o_ozA[c]), (int*)(ws + P->o_ozRx[c])), ++g_launches);
+      launch_slice_rows(st, (const double2*)(ws + P->o_W[c]), P->Kp[c], 1, P->M[c], P->Kp[c], P->oz_kq[c],
+                        P->oz_mpad[c], (__nv_bfloat16*)(ws + P->o_ozA[c]), (int*)(ws + P->o_ozRx[c]));
 }
 
 
@@ -329,9 +328,8 @@ void prepare_root(e2_problem* P, unsigned char* ws, cudaStream_t st, const doubl
     if (P->use_oz[cls] && P->part_cnt[cls] > 0) {
       const int64_t N = P->lists[P->list_of[cls]].n;
       unsigned char* sb = slot_base(P, ws, r);
-      (k_oz_slice_b<<<(unsigned)(P->oz_npad[cls] / 32), 256, 0, st>>>(
-           Dcls[cls], N, 1, 0, P->Kp[cls], N, P->oz_kq[cls], P->oz_npad[cls], (__nv_bfloat16*)(sb + P->o_ozB[cls]),
-           (int*)(sb + P->o_ozCx[cls]), nullptr, P->Kp[cls]), ++g_launches);
+      launch_slice_cols(st, Dcls[cls], N, 1, P->Kp[cls], N, P->oz_kq[cls], P->oz_npad[cls],
+                        (__nv_bfloat16*)(sb + P->o_ozB[cls]), (int*)(sb + P->o_ozCx[cls]));
     }
   double2* g1 = (double2*)(ws + P->o_g1 + P->g_stride * r);
   double2* g2 = (double2*)(ws + P->o_g2 + P->g_stride * r);

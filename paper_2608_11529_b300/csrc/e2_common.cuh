@@ -12,6 +12,7 @@ constexpr int kMaxPat = 1024;      // occupation patterns per string list
 constexpr int kMaxKeys = 1 << 20;  // size of the pattern-key table
 constexpr int kBinomN = 65;        // binomial table is [65][65]
 constexpr int OZ_S = 5;            // slices per operand of the sliced bf16 contraction
+constexpr int OZ_ADJ_S = 4;        // slices of the adjoint's products (gradients: 2^-33 of the scales)
 
 // Operands of the sliced (bf16) dense-class contraction: row slices of W
 // [OZ_S][Mpad][Kq] with one exponent per row, string slices of D
@@ -78,6 +79,7 @@ struct AdjOut {
   const double2* g1;
   double* part;
   int64_t rt;
+  int t_df;  // sliced adjoint only: T as float-float quadruples (its consumers slice them)
 };
 
 // Column tiles of a dense class with a compacted contraction.  The coupling

@@ -188,8 +188,14 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       double* part_adj = P->use_oz[cls] ? nullptr : poff(cls);
       for (int64_t m0 = 0; m0 < M; m0 += P->chunk_rows[cls]) {
         const int64_t Mc = std::min<int64_t>(P->chunk_rows[cls], M - m0);
+        // float-float amplitudes when the sliced products will read them: the
+        // class on the sliced contraction, its products on the sliced GEMM, and
+        // their slices within the scratch
+        const bool tdf = P->use_oz[cls] && slg &&
+                         zgemm_sliced_bytes(N, Kp, Mc, OZ_ADJ_S) <= P->bOz_bytes &&
+                         (!want_B || zgemm_sliced_bytes(Mc, Kp, N, OZ_ADJ_S) <= P->bOz_bytes);
         AdjOut adj{(double2*)B(P->o_bT), want_B ? (double*)B(P->o_bHm) : nullptr, (double*)B(P->o_bHrow),
-                   (double*)B(P->o_bHcol), (double*)B(P->o_bScalT), m0, Mc, s, g1, part_adj, rt};
+                   (double*)B(P->o_bHcol), (double*)B(P->o_bScalT), m0, Mc, s, g1, part_adj, rt, tdf ? 1 : 0};
         dim3 grid((unsigned)((Mc + 63) / 64), (unsigned)ct);
         if (P->use_oz[cls])  // the sliced contraction in its adjoint mode (plain columns)
           launch_class_oz_adj(st, cls, oz_operands(P, ws, r, cls), M, N, (const RowInfo*)(ws + P->o_rows[cls]),
@@ -209,7 +215,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         if (tiled)
           zgemm_gd_tiles(st, cp, ctl, W + m0 * Kp, (int)Kp, adj.T, N, Mc, (double2*)B(P->o_bGDc), m0 > 0);
         else if (slg && zgemm_sliced(st, N, Kp, Mc, adj.T, 1, N, 1, W + m0 * Kp, Kp, 1, 0, GDfor[cls], 1, N, 1, -1,
-                                     (unsigned char*)B(P->o_bOz), P->bOz_bytes))
+                                     (unsigned char*)B(P->o_bOz), P->bOz_bytes, 0, false, OZ_ADJ_S, tdf))
           ;  // Gamma_D^T = conj(T)^T W: T is the row operand (sliced without duplication)
         else if (Kp >= 64)
           zgemm(st, Kp, N, Mc, W + m0 * Kp, 1, Kp, 0, adj.T, N, 1, 1, GDfor[cls], N, 1, 1, 64);
@@ -227,7 +233,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
                                                          (int)Kp, (const double2*)B(P->o_bGWc), cp.krows, Mc, GW,
                                                          (int)Kp, Kp), ++g_launches);
           } else if (!(slg && zgemm_sliced(st, Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0, GW, Kp, 1, 0, -1,
-                                           (unsigned char*)B(P->o_bOz), P->bOz_bytes))) {
+                                           (unsigned char*)B(P->o_bOz), P->bOz_bytes, 0, false, OZ_ADJ_S,
+                                           tdf))) {
             zgemm(st, Mc, Kp, N, adj.T, N, 1, 1, Dfor[cls], 1, N, 0, GW, Kp, 1, 0, Kp >= 64 ? 64 : 16);
           }
           if (P->use_oz[cls])  // eta came as float-float pairs from the sliced adjoint
@@ -361,7 +368,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           if (tl)
             zgemm_gd_tiles(st, cpt, ctt, Xr, nx_, Tsh, nb, k, (double2*)B(P->o_bGDc), r0 > 0, 0);
           else if (!(P->use_oz_adj &&  // Gamma_D^T = Tsh^T X: Tsh is the row operand
-                     zgemm_sliced(st, nb, nx_, k, Tsh, 1, nb, 0, Xr, nx_, 1, 0, GD, 1, nb, 1, -1, oz, P->bOz_bytes)))
+                     zgemm_sliced(st, nb, nx_, k, Tsh, 1, nb, 0, Xr, nx_, 1, 0, GD, 1, nb, 1, -1, oz, P->bOz_bytes, 0, false, OZ_ADJ_S)))
             zgemm(st, nx_, nb, k, Xr, 1, nx_, 0, Tsh, nb, 1, 0, GD, nb, 1, 1);
           if (want_B) {
             double2* GXr = GX + (int64_t)r0 * S * nx_;
@@ -375,7 +382,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
                                                            P->Kp[tcls], (const double2*)B(P->o_bGWc), cpt.krows, k,
                                                            GXr, nx_, nx_), ++g_launches);
             } else if (!(P->use_oz_adj && zgemm_sliced(st, k, nx_, nb, Tsh, nb, 1, 0, D, 1, nb, 0, GXr, nx_, 1,
-                                                       gx_beta, -1, oz, P->bOz_bytes))) {
+                                                       gx_beta, -1, oz, P->bOz_bytes, 0, false, OZ_ADJ_S))) {
               zgemm(st, k, nx_, nb, Tsh, nb, 1, 0, D, 1, nb, 0, GXr, nx_, 1, gx_beta, bn);
             }
           }
@@ -431,7 +438,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
     (k_gg<<<blocks((int64_t)n * n), 256, 0, st>>>(X.sp, Nd, Ntt, Ge, Gea, GG), ++g_launches);
     (k_symm<<<blocks(npair * npair), 256, 0, st>>>(Gt, npair, Gh), ++g_launches);
     if (!(P->use_oz_adj && zgemm_sliced(st, Lt, npair, npair, X.Bo, npair, 1, 0, Gh, 1, npair, 0, Cs, npair, 1, 0, -1,
-                                        (unsigned char*)B(P->o_bOz), P->bOz_bytes)))
+                                        (unsigned char*)B(P->o_bOz), P->bOz_bytes, 0, false, OZ_ADJ_S)))
       zgemm(st, Lt, npair, npair, X.Bo, npair, 1, 0, Gh, 1, npair, 0, Cs, npair, 1, 0);
     (k_ftr<<<Lt, 256, 0, st>>>(X.sp, (const double2*)in->B_c, (const double2*)in->B_x, Lc_, Gf, ftr), ++g_launches);
     (k_bcoef<<<blocks((int64_t)Lt * n * n), 256, 0, st>>>(X.sp, (const double2*)in->B_c, (const double2*)in->B_x, Lc_,

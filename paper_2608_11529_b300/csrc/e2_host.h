@@ -193,17 +193,23 @@ void launch_class22_rows_df(cudaStream_t st, const DevList& L, const DevSpace& s
 // its adjoint mode over one row chunk of the backward pass (see AdjOut)
 void launch_class_oz_adj(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
                          const double* E0p, double b, const AdjOut& adj);
-// C (+)= A B (complex, strided as zgemm) through exact bf16 slices with
-// float-float accumulation (e2_ozaki.cu); lower >= 0: only tiles reaching
+// C (+)= A B (complex, strided as zgemm) through exact bf16 slices (4 or 5 per
+// operand) with float-float accumulation (e2_ozaki.cu); lower >= 0: only tiles reaching
 // n <= lower + m.  Needs zgemm_sliced_bytes(M, max(N, Nslice), K) of scratch
 // (returns false, launching nothing, when it is short).  B is sliced over
 // Nslice >= N columns when given, so that reuse_b can keep those slices for
-// a following call on the same scratch and B with a narrower N.
-size_t zgemm_sliced_bytes(int64_t M, int64_t N, int64_t K);
+// a following call on the same scratch and B with a narrower N.  a_df: A holds
+// float-float quadruples (re.hi, re.lo, im.hi, im.lo) instead of FP64 pairs.
+size_t zgemm_sliced_bytes(int64_t M, int64_t N, int64_t K, int slices = OZ_S);
 bool zgemm_sliced(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak,
                   int conjA, const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm,
                   int64_t csn, int beta, int64_t lower, unsigned char* scratch, size_t scratch_bytes,
-                  int64_t Nslice = 0, bool reuse_b = false);
+                  int64_t Nslice = 0, bool reuse_b = false, int slices = OZ_S, bool a_df = false);
+// slices of the dense classes' operands (OZ_S slices): W's rows, a D table's strings
+void launch_slice_rows(cudaStream_t st, const double2* A, int64_t sam, int64_t sak, int64_t M, int K, int Kq,
+                       int64_t Mpad, __nv_bfloat16* out, int* rexp);
+void launch_slice_cols(cudaStream_t st, const double2* B, int64_t sbk, int64_t sbn, int K, int64_t N, int Kq,
+                       int64_t Npad, __nv_bfloat16* out, int* cexp);
 void build_tables(const e2_problem* P, unsigned char* ws, cudaStream_t st, const double2* c, const Tabs& T, bool all);
 int splitk_segments(int64_t tiles, int64_t K, size_t seg_bytes);
 void dgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double* A, int64_t sam, int64_t sak,

@@ -55,10 +55,6 @@ __global__ void k_reduce(const double* partial, const int64_t* off, const int64_
 __global__ void k_finalize(const double* e2c, int n_roots, double* E2, const double* E0in, double* E0out);
 
 // sliced bf16 contraction (e2_ozaki.cu)
-__global__ void k_oz_slice_a(const double2* A, int64_t sam, int64_t sak, int conj, int64_t M, int K, int Kq,
-                             int64_t Mpad, __nv_bfloat16* out, int* rexp);
-__global__ void k_oz_slice_b(const double2* B, int64_t sbk, int64_t sbn, int conj, int K, int64_t N, int Kq,
-                             int64_t Npad, __nv_bfloat16* out, int* cexp, const unsigned long long* cmax, int kchunk);
 __global__ void k_c2df(const double2* c, int64_t n, const double2* g1, float2* out);
 __global__ void k_oz_colmax(const double2* B, int64_t sbk, int64_t sbn, int K, int64_t N, int kchunk,
                             unsigned long long* cmax);

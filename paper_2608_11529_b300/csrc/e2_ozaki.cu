@@ -7,7 +7,8 @@
 // OZ_S slices of 8 significant bits, x = sum_i w_i 2^(-8 i), each w_i an
 // integer of magnitude at most 256 (the first) or 128 (the others): x
 // 2^(8 OZ_S) rounded to an integer, in balanced base-256 digits, so that the
-// remainder after the last slice is at most 2^(-8 OZ_S - 1).  Columns of D are cut the same way with 2^-tau_A.  The
+// remainder after the last slice is at most 2^(-8 OZ_S - 1).  Columns of D
+// are cut the same way with 2^-tau_A.  The
 // slices are exact in bf16, their products exact in FP32, and the sums of
 // level 2 (i + j = 2) and level 3 (i + j = 3) are integers (after a fixed
 // power-of-two scaling) below 2^24 as long as the real contraction length is
@@ -37,24 +38,25 @@ namespace e2 {
 
 namespace {
 
-// The slices of x relative to 2^e (|x| < 2^e), from the bit pattern of x in
-// integer arithmetic (the FP64 pipe of this part is slow): N = x 2^(8 OZ_S - e)
-// rounded to an integer (|N| <= 2^(8 OZ_S)), then balanced base-256 digits
+// The S slices of x relative to 2^e (|x| < 2^e), from the bit pattern of x in
+// integer arithmetic (the FP64 pipe of this part is slow): N = x 2^(8 S - e)
+// rounded to an integer (|N| <= 2^(8 S)), then balanced base-256 digits
 // from the low end, d_i in [-128, 127] for i > 1 and d_1 in [-256, 256];
 // slice i holds d_i 2^(-8 (i - 1)) (exact in bf16).  neg: slices of -x.
-__device__ __forceinline__ void oz_digits(double x, int e, bool neg, float (&s)[OZ_S]) {
+template <int S = OZ_S>
+__device__ __forceinline__ void oz_digits(double x, int e, bool neg, float (&s)[S]) {
   long long bits = __double_as_longlong(x);
   if (neg) bits ^= (long long)0x8000000000000000ULL;
   const int ex = (int)((bits >> 52) & 0x7FF);
   long long N = 0;
   if (ex != 0) {
     const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | 0x10000000000000LL;
-    const int sh = 1075 + e - 8 * OZ_S - ex;  // at least 13 when |x| < 2^e
+    const int sh = 1075 + e - 8 * S - ex;  // at least 13 when |x| < 2^e
     if (sh < 63) N = (mant + (1LL << (sh - 1))) >> sh;
     if (bits < 0) N = -N;
   }
 #pragma unroll
-  for (int i = OZ_S - 1; i >= 1; --i) {
+  for (int i = S - 1; i >= 1; --i) {
     const long long d = ((N + 128) & 255) - 128;
     s[i] = (float)(int)d * __int_as_float((127 - 8 * i) << 23);
     N = (N - d) >> 8;
@@ -69,6 +71,37 @@ __device__ __forceinline__ int oz_exp(unsigned long long maxbits) {
 }
 __device__ __forceinline__ unsigned long long oz_mag(double x) {
   return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+}
+
+// f 2^(8 S - e) rounded to an integer, from the bits of a float (0 for 0)
+template <int S>
+__device__ __forceinline__ long long oz_fixed_f(float f, int e) {
+  const int bits = __float_as_int(f);
+  const int ex = (bits >> 23) & 0xFF;
+  if (ex == 0) return 0;
+  const long long mant = (bits & 0x7FFFFF) | 0x800000;
+  const int sh = ex - 150 + 8 * S - e;  // left shift (at most 8 S - 23 when |f| < 2^e)
+  long long N;
+  if (sh >= 0) N = mant << sh;
+  else if (sh > -40) N = (mant + (1LL << (-sh - 1))) >> (-sh);
+  else N = 0;
+  return bits < 0 ? -N : N;
+}
+
+// The S slices of a float-float value hi + lo relative to 2^e (|hi| < 2^e):
+// N = round(hi 2^(8 S - e)) + round(lo 2^(8 S - e)), within one unit of
+// rounding the sum, then the balanced digits as in oz_digits.
+template <int S>
+__device__ __forceinline__ void oz_digits_df(float hi, float lo, int e, bool neg, float (&s)[S]) {
+  long long N = oz_fixed_f<S>(hi, e) + oz_fixed_f<S>(lo, e);
+  if (neg) N = -N;
+#pragma unroll
+  for (int i = S - 1; i >= 1; --i) {
+    const long long d = ((N + 128) & 255) - 128;
+    s[i] = (float)(int)d * __int_as_float((127 - 8 * i) << 23);
+    N = (N - d) >> 8;
+  }
+  s[0] = (float)(int)N;
 }
 
 // 2^k as a float, k clamped to the normal range
@@ -107,38 +140,61 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
 // ------------------------------------------------------------------ slicing
 
 // Row slices of a complex M x K operand A (element (m, k) at A[m sam + k sak],
-// conjugated if conj): out[s][m][k'] over the real length 2K ([Re | Im],
+// conjugated if conj; FP64 pairs, or float-float quadruples when DF): out[s][m][k'] over the real length 2K ([Re | Im],
 // zero to Kq), one exponent per row.  One warp per row; rows M..Mpad-1 are
 // zero.
-__global__ void k_oz_slice_a(const double2* __restrict__ A, int64_t sam, int64_t sak, int conj, int64_t M, int K,
+template <int S, bool DF>
+__global__ void k_oz_slice_a(const void* __restrict__ Av, int64_t sam, int64_t sak, int conj, int64_t M, int K,
                              int Kq, int64_t Mpad, __nv_bfloat16* __restrict__ out, int* __restrict__ rexp) {
   const int64_t row = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= Mpad) return;
-  const double2* a = A + row * sam;
-  unsigned long long m = 0;
-  if (row < M)
-    for (int k = lane; k < K; k += 32) {
-      const double2 v = a[k * sak];
-      m = max(m, max(oz_mag(v.x), oz_mag(v.y)));
-    }
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  const int e = oz_exp(m);
-  auto cut = [&](int k, float (&sl)[OZ_S]) {
+  // DF: the operand is float-float, (re.hi, re.lo, im.hi, im.lo) per element;
+  // the row scale then comes from the high parts (|hi + lo| < 2^e whenever |hi| < 2^e)
+  const double2* a = (const double2*)Av + row * sam;
+  const float4* a4 = (const float4*)Av + row * sam;
+  int e;
+  if (DF) {
+    unsigned m = 0;
+    if (row < M)
+      for (int k = lane; k < K; k += 32) {
+        const float4 v = a4[k * sak];
+        m = max(m, max((unsigned)__float_as_int(v.x) & 0x7FFFFFFFu, (unsigned)__float_as_int(v.z) & 0x7FFFFFFFu));
+      }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const int ex = (int)(m >> 23);
+    e = ex ? ex - 126 : 0;
+  } else {
+    unsigned long long m = 0;
+    if (row < M)
+      for (int k = lane; k < K; k += 32) {
+        const double2 v = a[k * sak];
+        m = max(m, max(oz_mag(v.x), oz_mag(v.y)));
+      }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    e = oz_exp(m);
+  }
+  auto cut = [&](int k, float (&sl)[S]) {
     if (row < M && k < 2 * K) {
-      if (k < K) oz_digits(a[k * sak].x, e, false, sl);
-      else oz_digits(a[(k - K) * sak].y, e, conj != 0, sl);
+      if (DF) {
+        const float4 v = a4[(k < K ? k : k - K) * sak];
+        if (k < K) oz_digits_df<S>(v.x, v.y, e, false, sl);
+        else oz_digits_df<S>(v.z, v.w, e, conj != 0, sl);
+      } else {
+        if (k < K) oz_digits<S>(a[k * sak].x, e, false, sl);
+        else oz_digits<S>(a[(k - K) * sak].y, e, conj != 0, sl);
+      }
     } else {
 #pragma unroll
-      for (int i = 0; i < OZ_S; ++i) sl[i] = 0.0f;
+      for (int i = 0; i < S; ++i) sl[i] = 0.0f;
     }
   };
   for (int k = 2 * lane; k < Kq; k += 64) {  // two real k per lane: one 4-byte store per slice (Kq is even)
-    float s0[OZ_S], s1[OZ_S];
+    float s0[S], s1[S];
     cut(k, s0);
     cut(k + 1, s1);
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i)
+    for (int i = 0; i < S; ++i)
       *(__nv_bfloat162*)(out + ((int64_t)i * Mpad + row) * Kq + k) = __floats2bfloat162_rn(s0[i], s1[i]);
   }
   if (lane == 0) rexp[row] = e;
@@ -175,6 +231,7 @@ __global__ void k_oz_colmax(const double2* __restrict__ B, int64_t sbk, int64_t 
 // from cmax (k_oz_colmax) or, when cmax is null, found by the block itself
 // (then grid y must be 1).  Block: 32 columns x 8 warps over the rows
 // [blockIdx.y kchunk, +kchunk).
+template <int S>
 __global__ void k_oz_slice_b(const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conj, int K, int64_t N,
                              int Kq, int64_t Npad, __nv_bfloat16* __restrict__ out, int* __restrict__ cexp,
                              const unsigned long long* __restrict__ cmax, int kchunk) {
@@ -210,11 +267,11 @@ __global__ void k_oz_slice_b(const double2* __restrict__ B, int64_t sbk, int64_t
   const int k0 = blockIdx.y * kchunk, k1 = min(K, k0 + kchunk);
   for (int k = k0 + kk; k < k1; k += 8) {
     const double2 d = ok ? B[(int64_t)k * sbk + col * sbn] : make_double2(0.0, 0.0);
-    float sr[OZ_S], sim[OZ_S];
-    oz_digits(d.x, e, false, sr);
-    oz_digits(d.y, e, conj != 0, sim);
+    float sr[S], sim[S];
+    oz_digits<S>(d.x, e, false, sr);
+    oz_digits<S>(d.y, e, conj != 0, sim);
 #pragma unroll
-    for (int i = 0; i < OZ_S; ++i) {
+    for (int i = 0; i < S; ++i) {
       b0[i * ps + k] = __float2bfloat16_rn(sr[i]);
       b0[i * ps + K + k] = __float2bfloat16_rn(-sim[i]);
       b1[i * ps + k] = __float2bfloat16_rn(sim[i]);
@@ -225,7 +282,7 @@ __global__ void k_oz_slice_b(const double2* __restrict__ B, int64_t sbk, int64_t
     const __nv_bfloat16 z = __float2bfloat16_rn(0.0f);
     for (int k = 2 * K + kk; k < Kq; k += 8)
 #pragma unroll
-      for (int i = 0; i < OZ_S; ++i) {
+      for (int i = 0; i < S; ++i) {
         b0[i * ps + k] = z;
         b1[i * ps + k] = z;
       }
@@ -261,7 +318,8 @@ static_assert((size_t)OZ_VROW * 64 * 16 + 64 * 8 + 64 * 16 <= OZ_SMEM, "staged e
 
 // Adjoint epilogue of one staged tile (rows m0.., strings n0..): per coupling
 // f = |V|^2 g(D) / n (n = <c|c>) and, with s the seed,
-//   t = s (2/n) g V                   -> adj.T (FP64, chunk-local rows)
+//   t = s (2/n) g V                   -> adj.T (chunk-local rows; FP64, or float-float
+//                                         quadruples when adj.t_df)
 //   eta = s df/dD = s (|V|^2/n) g'(D)  -> adj.Hm (if set; float-float pairs)
 // and the sums of eta over the tile's strings per row (adj.Hrow), over its
 // rows per string (adj.Hcol), over the tile (scal[2 slot]), and of s f
@@ -356,7 +414,11 @@ __device__ __forceinline__ void oz_adjoint_phase2(const OzOperands& op, int64_t 
       hk = df_mul(hk, sd);
       const dfl w = df_mul(s2n, gk);
       const int64_t o = (row - adj.m_base) * N + colg;
-      adj.T[o] = make_double2(df_to_double(df_mul(w, vr)), df_to_double(df_mul(w, vi)));
+      const dfl tr = df_mul(w, vr), ti = df_mul(w, vi);
+      if (adj.t_df)
+        ((float4*)adj.T)[o] = make_float4(tr.hi, tr.lo, ti.hi, ti.lo);  // float-float, read by the row slicer
+      else
+        adj.T[o] = make_double2(df_to_double(tr), df_to_double(ti));
       if (adj.Hm) ((float2*)adj.Hm)[o] = make_float2(hk.hi, hk.lo);  // float-float, for k_hocc_df
       rs.add(hk);
       col[h].add(hk);
@@ -682,10 +744,10 @@ struct OzGemm {
 };
 
 constexpr int OG_BM = 64, OG_BNR = 64, OG_BK = 32, OG_LD = OG_BK + 8;
-constexpr size_t OG_STAGE = (size_t)OZ_S * (OG_BM + OG_BNR) * OG_LD * 2;
-constexpr size_t OG_SMEM = 2 * OG_STAGE;
 
+template <int S>
 __global__ void __launch_bounds__(256, 2) k_zgemm_sl(OzGemm q) {
+  constexpr size_t og_stage = (size_t)S * (OG_BM + OG_BNR) * OG_LD * 2;
   extern __shared__ __align__(16) unsigned char og_smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 2, wn = warp & 3, g = lane >> 2, t = lane & 3;
@@ -693,18 +755,18 @@ __global__ void __launch_bounds__(256, 2) k_zgemm_sl(OzGemm q) {
   if (q.lower >= 0 && n0 > q.lower + m0 + OG_BM - 1) return;
   const int Kq = q.Kq;
   auto sA = [&](int st, int s, int r, int k) {
-    return (__nv_bfloat16*)(og_smem + st * OG_STAGE) + ((s * OG_BM + r) * OG_LD + k);
+    return (__nv_bfloat16*)(og_smem + st * og_stage) + ((s * OG_BM + r) * OG_LD + k);
   };
   auto sB = [&](int st, int s, int r, int k) {
-    return (__nv_bfloat16*)(og_smem + st * OG_STAGE) + (OZ_S * OG_BM * OG_LD + (s * OG_BNR + r) * OG_LD + k);
+    return (__nv_bfloat16*)(og_smem + st * og_stage) + (S * OG_BM * OG_LD + (s * OG_BNR + r) * OG_LD + k);
   };
   auto load = [&](int st, int kc) {
     const int k0 = kc * OG_BK;
-    for (int i = tid; i < OZ_S * OG_BM * 4; i += 256) {
+    for (int i = tid; i < S * OG_BM * 4; i += 256) {
       const int s = i / (OG_BM * 4), r = (i / 4) % OG_BM, c = i & 3;
       cp_async16(sA(st, s, r, c * 8), q.A + ((int64_t)s * q.Mpad + m0 + r) * Kq + k0 + c * 8);
     }
-    for (int i = tid; i < OZ_S * OG_BNR * 4; i += 256) {
+    for (int i = tid; i < S * OG_BNR * 4; i += 256) {
       const int s = i / (OG_BNR * 4), r = (i / 4) % OG_BNR, c = i & 3;
       cp_async16(sB(st, s, r, c * 8), q.B + ((int64_t)s * 2 * q.Npad + 2 * n0 + r) * Kq + k0 + c * 8);
     }
@@ -752,9 +814,9 @@ __global__ void __launch_bounds__(256, 2) k_zgemm_sl(OzGemm q) {
     __syncthreads();
 #pragma unroll
     for (int ks = 0; ks < OG_BK; ks += 16) {
-      uint32_t bf[OZ_S][2][2];
+      uint32_t bf[S][2][2];
 #pragma unroll
-      for (int s = 0; s < OZ_S; ++s) {
+      for (int s = 0; s < S; ++s) {
         uint32_t r[4];
         ldsm_x4(r, sB(st, s, wn * 16 + (lane & 7) + (lane >> 4) * 8, ks + ((lane >> 3) & 1) * 8));
         bf[s][0][0] = r[0];
@@ -763,12 +825,12 @@ __global__ void __launch_bounds__(256, 2) k_zgemm_sl(OzGemm q) {
         bf[s][1][1] = r[3];
       }
 #pragma unroll
-      for (int sa = 0; sa < OZ_S; ++sa) {
+      for (int sa = 0; sa < S; ++sa) {
         uint32_t af[2][4];
 #pragma unroll
         for (int mi = 0; mi < 2; ++mi) ldsm_x4(af[mi], sA(st, sa, wm * 32 + mi * 16 + (lane & 15), ks + (lane >> 4) * 8));
 #pragma unroll
-        for (int sb = 0; sb < OZ_S - sa; ++sb) {
+        for (int sb = 0; sb < S - sa; ++sb) {
           const int l = sa + sb < 3 ? sa + sb : 3;
 #pragma unroll
           for (int mi = 0; mi < 2; ++mi)
@@ -806,11 +868,11 @@ __global__ void __launch_bounds__(256, 2) k_zgemm_sl(OzGemm q) {
     }
 }
 
-size_t zgemm_sliced_bytes(int64_t M, int64_t N, int64_t K) {
+size_t zgemm_sliced_bytes(int64_t M, int64_t N, int64_t K, int slices) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const int64_t Mpad = (M + OG_BM - 1) / OG_BM * OG_BM, Npad = (N + 31) / 32 * 32;
   const int64_t Kq = (2 * K + 31) / 32 * 32;
-  return al((size_t)2 * OZ_S * Mpad * Kq) + al(4 * (size_t)Mpad) + al((size_t)2 * OZ_S * 2 * Npad * Kq) +
+  return al((size_t)2 * slices * Mpad * Kq) + al(4 * (size_t)Mpad) + al((size_t)2 * slices * 2 * Npad * Kq) +
          al(4 * (size_t)Npad) + al(8 * (size_t)Npad);
 }
 
@@ -818,16 +880,15 @@ size_t zgemm_sliced_bytes(int64_t M, int64_t N, int64_t K) {
 // chunks of 256 (after a column-maximum pass) for a long one
 static constexpr int OZ_KCHUNK = 256;
 
-bool zgemm_sliced(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak,
-                  int conjA, const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm,
-                  int64_t csn, int beta, int64_t lower, unsigned char* scratch, size_t scratch_bytes, int64_t Nslice,
-                  bool reuse_b) {
-  if (M <= 0 || N <= 0) return true;
-  const int64_t Nb = Nslice > N ? Nslice : N;  // columns of B that are sliced
-  if (K <= 0 || zgemm_sliced_bytes(M, Nb, K) > scratch_bytes) return false;
+template <int S>
+static void zgemm_sliced_run(cudaStream_t st, int64_t M, int64_t N, int64_t Nb, int64_t K, const double2* A,
+                             int64_t sam, int64_t sak, int conjA, const double2* B, int64_t sbk, int64_t sbn,
+                             int conjB, double2* C, int64_t csm, int64_t csn, int beta, int64_t lower,
+                             unsigned char* scratch, bool reuse_b, bool a_df) {
+  constexpr size_t smem = 2 * (size_t)S * (OG_BM + OG_BNR) * OG_LD * 2;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_zgemm_sl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OG_SMEM);
+    cudaFuncSetAttribute(k_zgemm_sl<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     attr = true;
   }
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -835,29 +896,60 @@ bool zgemm_sliced(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double
   const int Kq = (int)((2 * K + 31) / 32 * 32);
   // B's slices first, so that a caller reusing them (reuse_b) keeps them in place
   __nv_bfloat16* Bs = (__nv_bfloat16*)scratch;
-  int* cx = (int*)(scratch + al((size_t)2 * OZ_S * 2 * Npad * Kq));
+  int* cx = (int*)(scratch + al((size_t)2 * S * 2 * Npad * Kq));
   unsigned long long* cm = (unsigned long long*)((unsigned char*)cx + al(4 * (size_t)Npad));
   __nv_bfloat16* As = (__nv_bfloat16*)((unsigned char*)cm + al(8 * (size_t)Npad));
-  int* rx = (int*)((unsigned char*)As + al((size_t)2 * OZ_S * Mpad * Kq));
+  int* rx = (int*)((unsigned char*)As + al((size_t)2 * S * Mpad * Kq));
   if (!reuse_b) {
     if (K <= 4 * OZ_KCHUNK) {
-      (k_oz_slice_b<<<(unsigned)(Npad / 32), 256, 0, st>>>(B, sbk, sbn, conjB, (int)K, Nb, Kq, Npad, Bs, cx, nullptr,
-                                                          (int)K), ++g_launches);
+      (k_oz_slice_b<S><<<(unsigned)(Npad / 32), 256, 0, st>>>(B, sbk, sbn, conjB, (int)K, Nb, Kq, Npad, Bs, cx,
+                                                             nullptr, (int)K), ++g_launches);
     } else {  // many rows: the column maxima first, then the slices of each chunk in parallel
       const unsigned kb = (unsigned)((K + OZ_KCHUNK - 1) / OZ_KCHUNK);
       cudaMemsetAsync(cm, 0, 8 * (size_t)Npad, st);
       (k_oz_colmax<<<dim3((unsigned)((Nb + 31) / 32), kb), 256, 0, st>>>(B, sbk, sbn, (int)K, Nb, OZ_KCHUNK, cm),
        ++g_launches);
-      (k_oz_slice_b<<<dim3((unsigned)(Npad / 32), kb), 256, 0, st>>>(B, sbk, sbn, conjB, (int)K, Nb, Kq, Npad, Bs, cx,
-                                                                     cm, OZ_KCHUNK), ++g_launches);
+      (k_oz_slice_b<S><<<dim3((unsigned)(Npad / 32), kb), 256, 0, st>>>(B, sbk, sbn, conjB, (int)K, Nb, Kq, Npad, Bs,
+                                                                        cx, cm, OZ_KCHUNK), ++g_launches);
     }
   }
-  (k_oz_slice_a<<<(unsigned)(Mpad / 8), 256, 0, st>>>(A, sam, sak, conjA, M, (int)K, Kq, Mpad, As, rx),
-   ++g_launches);
+  if (a_df)
+    (k_oz_slice_a<S, true><<<(unsigned)(Mpad / 8), 256, 0, st>>>(A, sam, sak, conjA, M, (int)K, Kq, Mpad, As, rx),
+     ++g_launches);
+  else
+    (k_oz_slice_a<S, false><<<(unsigned)(Mpad / 8), 256, 0, st>>>(A, sam, sak, conjA, M, (int)K, Kq, Mpad, As, rx),
+     ++g_launches);
   OzGemm q{As, Mpad, rx, Bs, Npad, cx, Kq, M, N, C, csm, csn, beta, lower};
   dim3 grid((unsigned)(Mpad / OG_BM), (unsigned)((N + 31) / 32));
-  (k_zgemm_sl<<<grid, 256, OG_SMEM, st>>>(q), ++g_launches);
+  (k_zgemm_sl<S><<<grid, 256, smem, st>>>(q), ++g_launches);
+}
+
+bool zgemm_sliced(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak,
+                  int conjA, const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm,
+                  int64_t csn, int beta, int64_t lower, unsigned char* scratch, size_t scratch_bytes, int64_t Nslice,
+                  bool reuse_b, int slices, bool a_df) {
+  if (M <= 0 || N <= 0) return true;
+  const int64_t Nb = Nslice > N ? Nslice : N;  // columns of B that are sliced
+  if (K <= 0 || (slices != 4 && slices != 5) || zgemm_sliced_bytes(M, Nb, K, slices) > scratch_bytes) return false;
+  if (slices == 4)
+    zgemm_sliced_run<4>(st, M, N, Nb, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, lower, scratch,
+                        reuse_b, a_df);
+  else
+    zgemm_sliced_run<5>(st, M, N, Nb, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, lower, scratch,
+                        reuse_b, a_df);
   return true;
+}
+
+void launch_slice_rows(cudaStream_t st, const double2* A, int64_t sam, int64_t sak, int64_t M, int K, int Kq,
+                       int64_t Mpad, __nv_bfloat16* out, int* rexp) {
+  (k_oz_slice_a<OZ_S, false><<<(unsigned)(Mpad / 8), 256, 0, st>>>(A, sam, sak, 0, M, K, Kq, Mpad, out, rexp),
+   ++g_launches);
+}
+
+void launch_slice_cols(cudaStream_t st, const double2* B, int64_t sbk, int64_t sbn, int K, int64_t N, int Kq,
+                       int64_t Npad, __nv_bfloat16* out, int* cexp) {
+  (k_oz_slice_b<OZ_S><<<(unsigned)(Npad / 32), 256, 0, st>>>(B, sbk, sbn, 0, K, N, Kq, Npad, out, cexp, nullptr, K),
+   ++g_launches);
 }
 
 // Fixed-order block sum of NV float-float values per thread (warp trees,

@@ -654,8 +654,8 @@ e2_status build_plan(e2_problem* P) {
       for (int c : {2, 5, 7, 4, 6}) {
         const int64_t Nc = lsize(c), Mc = P->chunk_rows[c];
         if (P->M[c] == 0 || Nc == 0 || Mc == 0) continue;
-        oz = std::max(oz, zgemm_sliced_bytes(Nc, P->Kp[c], Mc));
-        oz = std::max(oz, zgemm_sliced_bytes(Mc, P->Kp[c], Nc));
+        oz = std::max(oz, zgemm_sliced_bytes(Nc, P->Kp[c], Mc, OZ_ADJ_S));
+        oz = std::max(oz, zgemm_sliced_bytes(Mc, P->Kp[c], Nc, OZ_ADJ_S));
       }
       // shifted amplitudes of the gather classes: (table list, shifts S, width nx, rows)
       struct Sh { int lcls; int64_t S, nx, rows; };
@@ -667,10 +667,10 @@ e2_status build_plan(e2_problem* P) {
         const int64_t k = std::max<int64_t>(
             1, std::min<int64_t>(shs[q].rows * shs[q].S, (int64_t)(P->tsh_bytes / (16 * (size_t)nb))) / shs[q].S *
                    shs[q].S);
-        oz = std::max(oz, zgemm_sliced_bytes(nb, shs[q].nx, k));
-        oz = std::max(oz, zgemm_sliced_bytes(k, shs[q].nx, nb));
+        oz = std::max(oz, zgemm_sliced_bytes(nb, shs[q].nx, k, OZ_ADJ_S));
+        oz = std::max(oz, zgemm_sliced_bytes(k, shs[q].nx, nb, OZ_ADJ_S));
       }
-      const size_t cs = Lt > 0 ? zgemm_sliced_bytes(Lt, npair, npair) : 0;
+      const size_t cs = Lt > 0 ? zgemm_sliced_bytes(Lt, npair, npair, OZ_ADJ_S) : 0;
       if (cs <= (size_t(4) << 30)) oz = std::max(oz, cs);
       P->bOz_bytes = oz;
       P->use_oz_adj = oz > 0;

@@ -5,6 +5,7 @@ entry (the gradient bar), and <c|cbar> = 0."""
 import numpy as np
 import pytest
 
+from fp64_mode import fp64_contraction
 from e2_inputs import make_problem
 from e2_inputs.synth import tiny_problem
 from oracle import Oracle
@@ -106,8 +107,10 @@ def test_adjoint_with_column_tiles_matches_oracle(name):
 def test_adjoint_in_smallest_chunks(name):
     """The adjoint in 64-row chunks of every dense class and one core pair per
     class-(2,2) chunk: per-tile sums reduced chunk by chunk give the oracle's
-    gradients, the planned single-chunk gradients up to summation order, and
-    the forward's E2 bit for bit."""
+    gradients (default, sliced products), and, with every product in FP64,
+    the planned single-chunk gradients up to summation order; the forward's
+    E2 bit for bit.  (Sliced products cut each chunk with its own scales, so
+    between chunkings they agree to the slices' precision, not to rounding.)"""
     import paper_2608_11529_b300 as e2
     from paper_2608_11529_b300 import build as e2build
     e2build.build()
@@ -119,15 +122,21 @@ def test_adjoint_in_smallest_chunks(name):
     gh_o, gB_o, _, gc_o = o.grad(seed=seed)
     plan = e2.E2Problem.from_problem(prob)
     t = e2.device_inputs(prob, c)
-    ref = plan.value_and_grad(seed=seed, **t)
     plan.set_adjoint_chunks(rows=64, core_pairs=1)
     E2, gh, gc, gbc, gbx, dl = plan.value_and_grad(seed=seed, **t)
-    plan.set_adjoint_chunks()
     torch.cuda.synchronize()
     assert torch.equal(E2, plan.forward(**t)[0])
     gB = gbc.cpu().numpy() if gbx is None else np.concatenate([gbc.cpu().numpy(), gbx.cpu().numpy()])
     assert _rel(gh.cpu().numpy(), gh_o) < 1e-7
     assert _rel(gc.cpu().numpy(), gc_o) < 1e-7
     assert _rel(gB, gB_o) < 1e-7
-    for a, b in zip((gh, gc, gbc, dl), (ref[1], ref[2], ref[3], ref[5])):
-        assert _rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-12
+    with fp64_contraction(plan):
+        plan.set_adjoint_chunks()
+        ref = plan.value_and_grad(seed=seed, **t)
+        plan.set_adjoint_chunks(rows=64, core_pairs=1)
+        out = plan.value_and_grad(seed=seed, **t)
+        plan.set_adjoint_chunks()
+    torch.cuda.synchronize()
+    for k in (1, 2, 3, 5):  # g_h, g_c, g_Bc, dE2/dlambda
+        a, b = out[k], ref[k]
+        assert _rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-12, k
