@@ -189,13 +189,50 @@ __global__ void k_oz_slice_a(const void* __restrict__ Av, int64_t sam, int64_t s
       for (int i = 0; i < S; ++i) sl[i] = 0.0f;
     }
   };
-  for (int k = 2 * lane; k < Kq; k += 64) {  // two real k per lane: one 4-byte store per slice (Kq is even)
-    float s0[S], s1[S];
-    cut(k, s0);
-    cut(k + 1, s1);
+  if ((K & 1) == 0) {
+    // even K: each lane loads two complex elements k, k + 1 once and writes
+    // the real halves at k, k + 1 and the imaginary halves at K + k, K + k + 1
+    // (one 4-byte store per slice each)
+    auto both = [&](int k, float (&re)[S], float (&im)[S]) {
+      if (DF) {
+        const float4 v = a4[k * sak];
+        oz_digits_df<S>(v.x, v.y, e, false, re);
+        oz_digits_df<S>(v.z, v.w, e, conj != 0, im);
+      } else {
+        const double2 v = a[k * sak];
+        oz_digits<S>(v.x, e, false, re);
+        oz_digits<S>(v.y, e, conj != 0, im);
+      }
+    };
+    for (int k = 2 * lane; k < K; k += 64) {
+      float r0[S], r1[S], i0[S], i1[S];
+      if (row < M) {
+        both(k, r0, i0);
+        both(k + 1, r1, i1);
+      } else {
 #pragma unroll
-    for (int i = 0; i < S; ++i)
-      *(__nv_bfloat162*)(out + ((int64_t)i * Mpad + row) * Kq + k) = __floats2bfloat162_rn(s0[i], s1[i]);
+        for (int i = 0; i < S; ++i) r0[i] = r1[i] = i0[i] = i1[i] = 0.0f;
+      }
+#pragma unroll
+      for (int i = 0; i < S; ++i) {
+        __nv_bfloat16* o = out + ((int64_t)i * Mpad + row) * Kq;
+        *(__nv_bfloat162*)(o + k) = __floats2bfloat162_rn(r0[i], r1[i]);
+        *(__nv_bfloat162*)(o + K + k) = __floats2bfloat162_rn(i0[i], i1[i]);
+      }
+    }
+    const __nv_bfloat162 z2 = __floats2bfloat162_rn(0.0f, 0.0f);
+    for (int k = 2 * K + 2 * lane; k < Kq; k += 64)
+#pragma unroll
+      for (int i = 0; i < S; ++i) *(__nv_bfloat162*)(out + ((int64_t)i * Mpad + row) * Kq + k) = z2;
+  } else {
+    for (int k = 2 * lane; k < Kq; k += 64) {  // two real k per lane: one 4-byte store per slice (Kq is even)
+      float s0[S], s1[S];
+      cut(k, s0);
+      cut(k + 1, s1);
+#pragma unroll
+      for (int i = 0; i < S; ++i)
+        *(__nv_bfloat162*)(out + ((int64_t)i * Mpad + row) * Kq + k) = __floats2bfloat162_rn(s0[i], s1[i]);
+    }
   }
   if (lane == 0) rexp[row] = e;
 }
