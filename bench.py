@@ -138,7 +138,8 @@ def _traffic(kernel):
     src = open(os.path.join(ROOT, "paper_2608_11529_b300", "csrc", KERNEL_SOURCE[kernel]), "rb").read()
     if rec.get("source_sha256") != hashlib.sha256(src).hexdigest():
         return None
-    return rec.get("bytes_per_launch")
+    # the sliced kernel's roofline is over a step's launches: bytes per step
+    return rec.get("bytes_per_step", rec.get("bytes_per_launch"))
 
 
 def _measured_peaks():
@@ -419,6 +420,7 @@ def run(args):
         achieved = flops / (t_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_bf16, "unit": "TFLOP/s",
                 "frac": achieved / peak_bf16, "traffic": _traffic("k_class_oz"),
+                "traffic_scope": "DRAM bytes per step over the kernel's launches (ncu, the (0,2) and (1,2) launches)",
                 "kernel": "k_class_oz classes " + " ".join(CLASS_NAMES[k] for k in classes),
                 "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"
                                 if mp.get("bf16_tflops_sustained") else "fallback 1.4 PFLOP/s sustained bf16"),
