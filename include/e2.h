@@ -299,6 +299,9 @@ E2_API e2_status e2_set_class_tiles(e2_problem* prob, int cls, int on);
  *                      for (0,2), (1,2), (2,1), (2,0) when the real
  *                      contraction length 2 K is at most 256 and the slices
  *                      fit 16 GiB; the default there.
+ * For class (2,2) (cls 8, elementwise, no contraction) E2_CONTRACT_SLICED
+ * selects the float-float kernel for its denominators and sums (available
+ * when the float-float string tables fit the same 16 GiB; the default then).
  * cls = E2_CONTRACT_SETUP selects the same choice for the products over the
  * factor index that form the integral blocks (step a5: (ai|bt), (at|bu),
  * (av|uw)); there the slices are exact per 256 real terms and the sums over

@@ -264,14 +264,22 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       const DevList& L = Lc[8];
       const int64_t nyb = (int64_t)P->nvb * (P->nvb + 1) / 2;
       c22 = (double*)B(P->o_bC22);
+      if (E2 && P->use_oz[8]) {
+        const HostList& H8 = P->lists[P->list_of[8]];
+        launch_class22_df(st, L, X.sp, (const float2*)(ws + H8.o_eAdf), (const float2*)(ws + H8.o_Udf), c,
+                          (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb, P->ncp, poff(8));
+      }
       // chunks of core pairs: partials of one chunk, reduced before the next
       for (int z0 = 0; z0 < (int)P->ncp; z0 += P->z22_chunk) {
         const int zc = (int)std::min<int64_t>(P->z22_chunk, P->ncp - z0);
         const int64_t yz = nyb * zc;
         dim3 grid(blocks(L.n), (unsigned)nyb, (unsigned)zc);
+        // E2 from the forward's float-float kernel when the class uses it (then
+        // the adjoint kernel writes no partials)
         (k_class22_bwd<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b,
                                              P->nvb, s, g1, (double*)B(P->o_bC22p), (double*)B(P->o_bH22p),
-                                             (double*)B(P->o_bV22), poff(8), z0), ++g_launches);
+                                             (double*)B(P->o_bV22), P->use_oz[8] ? nullptr : poff(8), z0),
+         ++g_launches);
         (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bC22p), yz, L.n, z0 > 0, c22), ++g_launches);
         (k_colsum<<<blocks(L.n), 256, 0, st>>>((const double*)B(P->o_bH22p), yz, L.n, z0 > 0, hA), ++g_launches);
         (k_class22_marg<<<(unsigned)(P->nvc + P->ncc + 1), 256, 0, st>>>((const double*)B(P->o_bV22),

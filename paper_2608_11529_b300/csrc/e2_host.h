@@ -183,6 +183,10 @@ OzOperands oz_operands(const e2_problem* P, unsigned char* ws, int r, int cls);
 // per 64 x 64 tile, [column tile][row tile] (e2_ozaki.cu)
 void launch_class_oz(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
                      const double* E0p, double b, double* partial);
+// class (2,2) in float-float (e2_ozaki.cu), the partials of k_class22
+void launch_class22_df(cudaStream_t st, const DevList& L, const DevSpace& sp, const float2* eAdf, const float2* Udf,
+                       const double2* c, const double* g2, const double* epsh, const double* G, const double* E0p,
+                       double b, int nvb, int64_t ncp, double* partial);
 // float-float forms of per-row adjoint sums (e2_ozaki.cu): occupation sums of
 // eta given as float-float pairs, and the per-row sums of class (2,2)
 void launch_hocc_df(cudaStream_t st, const float2* H, const DevList& L, int na, int64_t rows, double* Hocc);
@@ -238,8 +242,14 @@ void launch_sparse_classes(e2_problem* P, unsigned char* ws, cudaStream_t st, in
     const DevList& L = Lc[8];
     dim3 grid(blocks(L.n), (unsigned)(P->nvb * (P->nvb + 1) / 2), (unsigned)P->ncp);
     mark(8, 0);
-    (k_class22<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb,
-                                    poff(8)), ++g_launches);
+    if (P->use_oz[8]) {  // float-float
+      const HostList& H8 = P->lists[P->list_of[8]];
+      launch_class22_df(st, L, X.sp, (const float2*)(ws + H8.o_eAdf), (const float2*)(ws + H8.o_Udf), c,
+                        (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb, P->ncp, poff(8));
+    } else {
+      (k_class22<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb,
+                                      poff(8)), ++g_launches);
+    }
     mark(8, 1);
   }
   if (P->part_cnt[1] > 0) {

@@ -1151,4 +1151,114 @@ void launch_class22_rows_df(cudaStream_t st, const DevList& L, const DevSpace& s
 #undef E2_R22
 }
 
+// Class (2,2) in float-float (the FP64 kernel k_class22's sum, same tiling
+// and partial layout): per thread one string A, per block a pair of 8-wide
+// virtual blocks and a core pair (i<j);
+//   sum_{a<b in the blocks} |<ab||ij>|^2 |c_A|^2 g(D),
+//   D = E0' - chi_ij - e_A + U[i,A] + U[j,A] - (alpha_a + U[a,A]) - (alpha_b + U[b,A]) - G_ab,
+// the per-row quantities formed once per block in FP64 and kept as
+// float-float pairs, the per-coupling work on the FP32 pipe.
+__global__ void __launch_bounds__(256)
+k_class22_df(DevList Ls, DevSpace sp, const float2* __restrict__ eAdf, const float2* __restrict__ Udf,
+             const double2* __restrict__ c, const double* __restrict__ g2, const double* __restrict__ epsh,
+             const double* __restrict__ G, const double* __restrict__ E0p, double b, int nvb,
+             double* __restrict__ partial) {
+  __shared__ float2 sGab[8][8], sG2[8][8], sAl[2][8], sBase;
+  __shared__ float2 sW[8];
+  int ba = 0, bb = 0;
+  {
+    int yb = blockIdx.y, k = 0;
+    while (yb >= nvb - k) { yb -= nvb - k; ++k; }
+    ba = k;
+    bb = k + yb;
+  }
+  int iu, ju;
+  pair_decode(blockIdx.z, iu, ju);
+  const int gi = sp.cc[iu], gj = sp.cc[ju];
+  const int64_t nvp = pairs(sp.nvc);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < 64) {
+    const int x = tid >> 3, y = tid & 7;
+    const int a = ba * 8 + x, bq = bb * 8 + y;
+    const bool ok = a < sp.nvc && bq < sp.nvc && a < bq;
+    const dfl gab = df_from_double(ok ? G[(int64_t)sp.vc[a] * sp.n + sp.vc[bq]] : 0.0);
+    const dfl w = df_from_double(ok ? g2[(int64_t)blockIdx.z * nvp + pair_index(a, bq)] : 0.0);
+    sGab[x][y] = make_float2(gab.hi, gab.lo);
+    sG2[x][y] = make_float2(w.hi, w.lo);
+  } else if (tid < 80) {
+    const int k = tid - 64, side = k >> 3, x = k & 7;
+    const int a = (side ? bb : ba) * 8 + x;
+    double al = 0.0;
+    if (a < sp.nvc) {
+      const int ga = sp.vc[a];
+      al = epsh[ga] - G[(int64_t)gi * sp.n + ga] - G[(int64_t)gj * sp.n + ga];
+    }
+    const dfl d = df_from_double(al);
+    sAl[side][x] = make_float2(d.hi, d.lo);
+  } else if (tid == 80) {
+    const dfl d = df_from_double(*E0p + epsh[gi] + epsh[gj] - G[(int64_t)gi * sp.n + gj]);  // E0' - chi_ij
+    sBase = make_float2(d.hi, d.lo);
+  }
+  __syncthreads();
+  const int64_t A = blockIdx.x * (int64_t)blockDim.x + tid;
+  dfl acc{0.f, 0.f};
+  if (A < Ls.n) {
+    const bool shifted = b != 0.0;
+    const dfl bbq = df_from_double(b * b);
+    const float2 e = eAdf[A], ui = Udf[(int64_t)iu * Ls.n + A], uj = Udf[(int64_t)ju * Ls.n + A];
+    dfl ct = df_sub(dfl{sBase.x, sBase.y}, dfl{e.x, e.y});
+    ct = df_add(ct, dfl{ui.x, ui.y});
+    ct = df_add(ct, dfl{uj.x, uj.y});
+    dfl pb[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int bq = bb * 8 + k;
+      pb[k] = dfl{0.f, 0.f};
+      if (bq < sp.nvc) {
+        const float2 u = Udf[(int64_t)(sp.ncc + bq) * Ls.n + A];
+        pb[k] = df_add(dfl{sAl[1][k].x, sAl[1][k].y}, dfl{u.x, u.y});
+      }
+    }
+    OzSums inner{0.f, 0.f};
+#pragma unroll
+    for (int x = 0; x < 8; ++x) {
+      const int a = ba * 8 + x;
+      if (a >= sp.nvc) continue;
+      const float2 u = Udf[(int64_t)(sp.ncc + a) * Ls.n + A];
+      const dfl cx = df_sub(ct, df_add(dfl{sAl[0][x].x, sAl[0][x].y}, dfl{u.x, u.y}));
+#pragma unroll
+      for (int y = 0; y < 8; ++y) {
+        const float2 w = sG2[x][y];
+        if (w.x == 0.0f) continue;
+        const dfl D = df_sub(df_sub(cx, pb[y]), dfl{sGab[x][y].x, sGab[x][y].y});
+        dfl g;
+        if (!shifted) {
+          g = df_rcp(D);
+        } else {
+          const dfl D2 = df_sqr(D);
+          g = df_mul(df_mul(D, D2), df_rcp(df_add(df_sqr(D2), bbq)));
+        }
+        inner.add(df_mul(dfl{w.x, w.y}, g));
+      }
+    }
+    const double2 cv = c[A];
+    acc = df_mul(df_from_double(cv.x * cv.x + cv.y * cv.y), inner.value());
+  }
+  acc = warp_df_sum(acc);
+  if (lane == 0) sW[warp] = make_float2(acc.hi, acc.lo);
+  __syncthreads();
+  if (tid == 0) {
+    dfl tot{sW[0].x, sW[0].y};
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot = df_add(tot, dfl{sW[w].x, sW[w].y});
+    partial[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = df_to_double(tot);
+  }
+}
+
+void launch_class22_df(cudaStream_t st, const DevList& L, const DevSpace& sp, const float2* eAdf, const float2* Udf,
+                       const double2* c, const double* g2, const double* epsh, const double* G, const double* E0p,
+                       double b, int nvb, int64_t ncp, double* partial) {
+  dim3 grid((unsigned)((L.n + 255) / 256), (unsigned)(nvb * (nvb + 1) / 2), (unsigned)ncp);
+  (k_class22_df<<<grid, 256, 0, st>>>(L, sp, eAdf, Udf, c, g2, epsh, G, E0p, b, nvb, partial), ++g_launches);
+}
+
 }  // namespace e2

@@ -403,6 +403,7 @@ e2_status build_plan(e2_problem* P) {
       if (P->oz_ok[c]) P->lists[P->list_of[c]].df = true;
     }
     if (d8 && fits) P->lists[l8].df = true;
+    P->oz_ok[8] = P->use_oz[8] = d8 && fits;  // class (2,2) in float-float
   }
   for (HostList& L : P->lists) {
     L.o_str = ws.take(sizeof(uint64_t) * std::max<int64_t>(L.n, 1));

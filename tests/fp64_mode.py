@@ -6,7 +6,7 @@ contraction is smooth to rounding.  The adjoint forms its amplitudes in FP64
 either way, so the finite differences that check it use this mode."""
 from contextlib import contextmanager
 
-DENSE_SLICED = (-2, -1, 2, 5, 6, 7)  # -1, -2: the integral products of the setup, the adjoint products
+DENSE_SLICED = (-2, -1, 2, 5, 6, 7, 8)  # -1, -2: the setup and adjoint products; 8: class (2,2)
 
 
 @contextmanager

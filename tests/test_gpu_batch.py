@@ -39,7 +39,7 @@ def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph(col_tile
         for cls in (2, 4, 5, 6):
             if plan.class_tiles(cls)[0]:
                 plan.set_class_tiles(cls, col_tiles)
-        for cls in (-1, 2, 5, 6, 7):               # sliced classes run beside the persistent FP64 kernel
+        for cls in (-1, 2, 5, 6, 7, 8):            # sliced classes run beside the persistent FP64 kernel
             if plan.contraction(cls)[1]:
                 plan.set_contraction(cls, sliced)
     inputs = [e2.device_inputs(p, c) for p, _, c in jobs]

@@ -28,7 +28,7 @@ def _gpu_e2(prob, c, class_mask=0x1FF, lam=None, col_tiles=None, sliced=None):
             if plan.class_tiles(cls)[0]:
                 plan.set_class_tiles(cls, col_tiles)
     if sliced is not None:                         # force the sliced bf16 (True) or FP64 (False) products
-        for cls in (-1, 2, 5, 6, 7):               # -1: the integral products of the setup
+        for cls in (-1, 2, 5, 6, 7, 8):            # -1: the integral products of the setup; 8: (2,2) in float-float
             if plan.contraction(cls)[1]:
                 plan.set_contraction(cls, sliced)
     t = e2.device_inputs(prob, c)
@@ -97,7 +97,7 @@ def test_contraction_modes_match_oracle(name, sliced):
     prob = CASES[name]()
     c, E0, e2, ec = _oracle(prob)
     g2, gc, g0, plan = _gpu_e2(prob, c, sliced=sliced)
-    for cls in (2, 5, 6, 7):
+    for cls in (2, 5, 6, 7, 8):
         used, avail = plan.contraction(cls)
         assert used == (sliced and avail)
     np.testing.assert_allclose(gc, ec, rtol=0, atol=TOL_E2)
@@ -112,7 +112,7 @@ def test_sliced_contraction_against_fp64(name):
     c, *_ = _oracle(prob)
     _, fp, _, plan = _gpu_e2(prob, c, sliced=False)
     _, sl, _, _ = _gpu_e2(prob, c, sliced=True)
-    on = [cls for cls in (2, 5, 6, 7) if plan.contraction(cls)[1]]
+    on = [cls for cls in (2, 5, 6, 7, 8) if plan.contraction(cls)[1]]
     assert on
     for r in range(fp.shape[0]):
         for cls in on:
