@@ -402,6 +402,8 @@ def run(args):
     ktime = {k: sum(evs[s][k][0].elapsed_time(evs[s][k][1]) for s in range(args.steps)) / args.steps for k in present}
     sliced = {k for k in GEMM_CLASSES if k in present and plan.contraction(k)[0]}
     kern = {k: ("k_class_oz" if k in sliced else KERNEL_OF_CLASS[k]) for k in present}
+    if 8 in present and plan.contraction(8)[0]:
+        kern[8] = "k_class22_df"  # class (2,2) in float-float
     ksum = {}
     for k in present:
         ksum[kern[k]] = ksum.get(kern[k], 0.0) + ktime[k]
