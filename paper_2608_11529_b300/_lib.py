@@ -284,11 +284,15 @@ class E2Problem:
         _check(load().e2_set_class_tiles(self._h, cls, int(bool(on))))
 
     def set_contraction(self, cls, sliced):
-        """Dense class cls on the sliced bf16 contraction (True) or FP64 (False)."""
+        """Arithmetic of part of the path: True for the sliced bf16 tensor-pipe
+        form with float-float epilogues (the default where available), False
+        for FP64.  cls: a dense class (2, 5, 6, 7), 8 for class (2,2) (float-
+        float elementwise kernel), -1 for the integral products of the setup,
+        -2 for the products of the backward pass."""
         _check(load().e2_set_contraction(self._h, cls, 1 if sliced else 0))
 
     def contraction(self, cls):
-        """(sliced in use, sliced available) for class cls."""
+        """(sliced in use, sliced available) for cls as in set_contraction."""
         m, a = C.c_int(), C.c_int()
         _check(load().e2_contraction(self._h, cls, C.byref(m), C.byref(a)))
         return bool(m.value), bool(a.value)
