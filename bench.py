@@ -520,6 +520,14 @@ def run(args):
                            "couplings_per_step": int(couplings),
                            "roots": plan.n_roots, "reference": f"device Davidson, {iters} iterations",
                            "l2": f"inputs larger than L2: the {fbytes / 1e6:.0f} MB factor set is re-read every step",
+                           "arithmetic": {
+                               **{CLASS_NAMES[k]: ("sliced bf16 + float-float epilogue" if plan.contraction(k)[0]
+                                                   else "fp64") for k in present if k in GEMM_CLASSES},
+                               **({"(2,2)": "float-float" if plan.contraction(8)[0] else "fp64"} if 8 in present
+                                  else {}),
+                               "gather classes": "fp64",
+                               "integral products": "sliced bf16" if plan.contraction(-1)[0] else "fp64",
+                               "adjoint products": "sliced bf16 (4 slices)" if plan.contraction(-2)[0] else "fp64"},
                            "column_tiles": col_tiles,
                            "E2": float(E2.cpu()[0]), "E0": float(E0.cpu()[0]),
                            "class_ms": {CLASS_NAMES[k]: ktime[k] for k in present}},
