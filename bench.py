@@ -48,6 +48,18 @@ KERNEL_OF_CLASS = {c: "k_class_gemm" for c in GEMM_CLASSES} | {8: "k_class22", 1
                                                                 0: "k_class00"}
 
 
+def max_over_ranks(ms, ws, dist, device):
+    """The whole job's step time: the slowest rank's.  Every rank brackets its
+    timed region with barriers, so the regions overlap; with one rank this is
+    ms itself (no collective)."""
+    if ws <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -390,11 +402,7 @@ def run(args):
     if ws > 1:
         dist.barrier()
     plan.set_events(None)
-    ms = start.elapsed_time(end) / args.steps
-    ms_all = torch.tensor([ms], device=dev)
-    if ws > 1:
-        dist.all_reduce(ms_all, op=dist.ReduceOp.MAX)
-    ms = float(ms_all.item())
+    ms = max_over_ranks(start.elapsed_time(end) / args.steps, ws, dist, dev)
     E2dev = E2.clone()
 
     # per-class kernel times (root 0) over the timed region, summed per kernel
@@ -462,6 +470,8 @@ def run(args):
         for _ in range(2):
             plan.value_and_grad(**t)
         torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
         b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.nvtx.range_push("fwd_bwd")   # ncu --nvtx --nvtx-include "fwd_bwd/" selects these launches
         b0.record(stream)
@@ -470,7 +480,9 @@ def run(args):
         b1.record(stream)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
-        bms = b0.elapsed_time(b1) / args.steps
+        if ws > 1:
+            dist.barrier()
+        bms = max_over_ranks(b0.elapsed_time(b1) / args.steps, ws, dist, dev)
         same = bool(torch.equal(vg[0], E2dev)) if E2dev is not None else None
         fwdbwd = {"ms_fwd": ms, "ms_fwd_bwd": bms, "ratio_fwd_bwd_over_fwd": bms / ms,
                   "E2_bitwise_equal_to_forward": same,
@@ -495,13 +507,17 @@ def run(args):
         for _ in range(2):
             e2e_step()
         torch.cuda.synchronize()
+        if ws > 1:
+            dist.barrier()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
         for _ in range(args.steps):
             e2e_step()
         s1.record(stream)
         torch.cuda.synchronize()
-        ems = s0.elapsed_time(s1) / args.steps
+        if ws > 1:
+            dist.barrier()
+        ems = max_over_ranks(s0.elapsed_time(s1) / args.steps, ws, dist, dev)
         e2e = {"value": ws * couplings / (ems * 1e-3), "unit": "couplings/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": ems}
 
