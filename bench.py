@@ -6,15 +6,27 @@ determinant K (per root) whose V_K = <K|H|Psi> is formed and whose
 |V_K|^2 / (E0 - H_KK) is reduced.  One step = one full e2_forward over every
 external class of the workload (all of Q), inputs resident in HBM.
 
-Default workload: the Ne-shaped DCG problem (2 core spinors, CAS 8e in 16
-active spinors = 12,870 reference determinants, 200 virtual spinors,
-400 Coulomb + 200 Gaunt factors, one root), 880,539,088 couplings per step.
-Its factor inputs (456 MB) are larger than L2 and every step re-reads them.
+The headline runs the library's default arithmetic, IEEE FP64 throughout
+(`--arith fp64`).  The opt-in emulated arithmetic (bf16 slices on the tensor
+pipe with float-float epilogues, `e2_set_contraction`) is measured on the
+same workload after it and reported under "alt_arithmetic" with its own
+dtype label; `--arith sliced` makes it the headline instead.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Default workload: the Ar-shaped DCB DAS problem (8 core spinors, three
+active subspaces of 8 spinors holding 10 electrons, N_P = 40,608, 400 virtual
+spinors, 600 Coulomb + 300 Breit factors, one root): 1.59e11 couplings per
+step, the largest of the five shapes whose K forwards fit a run of minutes in
+FP64 (the Kr- and Xe-shaped ones take hours per forward at the FP64 rate).
+The fwd+bwd, end-to-end and other-arithmetic timings take fewer steps when a
+step is long (--aux-seconds); each says how many.
 
-Under torchrun each rank runs the same workload on its own GPU (independent
-replicas, weak scaling); no data crosses between ranks.
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--config NAME]
+
+Under torchrun (N > 1) the external space is sharded over the ranks: each
+rank takes an even share of every class's units, the per-tile partials are
+summed by one NCCL all-reduce and reduced in the fixed order, so E2 is
+bitwise the N = 1 value (strong scaling).  --replicas runs N independent
+copies instead (weak scaling, no data-path collective).
 """
 from __future__ import annotations
 
@@ -159,12 +171,15 @@ def _measured_peaks():
     return json.load(open(path)) if os.path.exists(path) else {}
 
 
-def _sample_ks(prob, n, rng):
+def _sample_ks(prob, n, rng, chunk=1 << 19):
     """n random external determinants of the workload, drawn with the class
-    sizes as weights: (holes, particles, active string)."""
+    sizes as weights: (holes, particles, active string), as arrays.  Holes
+    (particles) are distinct correlated core (virtual) spinors; the active
+    string holds the class's electron count on uniformly chosen active
+    spinors."""
     from math import comb
-    nc = [k for k in range(prob.n_core) if not prob.frozen[k]]
-    nv = [v for v in range(prob.n_core + prob.n_act, prob.n) if not prob.frozen[v]]
+    nc = np.array([k for k in range(prob.n_core) if not prob.frozen[k]], np.int32)
+    nv = np.array([v for v in range(prob.n_core + prob.n_act, prob.n) if not prob.frozen[v]], np.int32)
     cls, w = [], []
     for h in range(3):
         for p in range(3):
@@ -174,68 +189,100 @@ def _sample_ks(prob, n, rng):
             cls.append((h, p, ne))
             w.append(comb(len(nc), h) * comb(len(nv), p) * comb(prob.n_act, ne))
     w = np.array(w, float) / sum(w)
+    cls = np.array(cls, np.int32)
     pick = rng.choice(len(cls), size=n, p=w)
-    nh, hs, npp, ps, acts = [], [], [], [], []
-    for k in pick:
-        h, p, ne = cls[k]
-        I = sorted(rng.choice(nc, size=h, replace=False).tolist()) if h else []
-        S = sorted(rng.choice(nv, size=p, replace=False).tolist()) if p else []
-        A = rng.choice(prob.n_act, size=ne, replace=False)
-        nh.append(h), npp.append(p)
-        hs.append(I + [0] * (2 - h)), ps.append(S + [0] * (2 - p))
-        acts.append(int(sum(1 << int(t) for t in A)))
+    nh, npp, ne = cls[pick, 0], cls[pick, 1], cls[pick, 2]
+
+    def tuples(pool, k):   # k[i] distinct members of pool, ascending, padded with 0
+        out = np.zeros((n, 2), np.int32)
+        m = len(pool)
+        if m == 0:
+            return out
+        i1 = rng.integers(0, m, n)
+        i2 = rng.integers(0, max(m - 1, 1), n)
+        i2 = i2 + (i2 >= i1)
+        lo, hi = np.minimum(i1, i2), np.minimum(np.maximum(i1, i2), m - 1)
+        out[:, 0] = np.where(k == 2, pool[lo], np.where(k == 1, pool[i1], 0))
+        out[:, 1] = np.where(k == 2, pool[hi], 0)
+        return out
+
+    hs, ps = tuples(nc, nh), tuples(nv, npp)
+    acts = np.zeros(n, np.uint64)
+    na = prob.n_act
+    for a in range(0, n, chunk):   # a random permutation of the active spinors per determinant, first ne kept
+        b = min(n, a + chunk)
+        order = np.argsort(rng.random((b - a, na)), axis=1).astype(np.uint64)
+        keep = np.arange(na)[None, :] < ne[a:b, None]
+        acts[a:b] = np.where(keep, np.left_shift(np.uint64(1), order), np.uint64(0)).sum(axis=1, dtype=np.uint64)
     return nh, hs, npp, ps, acts
 
 
-def oracle_rate(prob, seconds=15.0, seed=0):
-    """Couplings/s of the oracle on a bounded random sample of the workload's
-    external determinants (V_K from the explicit Q H P row and H_KK), on all
-    host cores."""
-    from oracle import Oracle
-    o = Oracle(prob, use_eri_cache=False)
-    c = prob.X0[:1] / np.linalg.norm(prob.X0[:1])
-    o.set_c(c)
-    rng = np.random.default_rng(seed)
-    E0 = np.zeros(1)
-    n = 256
-    while True:   # calibrate the sample size to about `seconds` of work
-        ks = _sample_ks(prob, n, rng)
+class OracleSampler:
+    """The oracle (V_K from the explicit Q H P row, H_KK from the diagonal
+    rule) on bounded random samples of the workload's external determinants,
+    on all host cores.  The sample size is calibrated once, to about
+    `seconds` of oracle work; each timed sample is drawn before its clock
+    starts."""
+
+    def __init__(self, prob, seconds, seed=0):
+        from oracle import Oracle
+        self.prob = prob
+        self.o = Oracle(prob, use_eri_cache=False)
+        c = prob.X0[:1] / np.linalg.norm(prob.X0[:1])
+        self.o.set_c(c)
+        self.E0 = np.zeros(1)
+        self.rng = np.random.default_rng(seed)
+        n = 256
+        while True:
+            dt = self._time(n)
+            if dt >= 0.2 * seconds or n >= 1 << 21:
+                break
+            n *= 4
+        self.n = int(max(256, min(4_000_000, n * seconds / max(dt, 1e-3))))
+
+    def _time(self, n):
+        ks = _sample_ks(self.prob, n, self.rng)
         t0 = time.perf_counter()
-        o.couplings(E0, *ks)
-        dt = time.perf_counter() - t0
-        if dt >= 0.2 * seconds or n >= 2_000_000:
-            break
-        n *= 4
-    n = int(max(256, min(4_000_000, n * seconds / max(dt, 1e-3))))
-    args = _sample_ks(prob, n, rng)
-    t0 = time.perf_counter()
-    o.couplings(E0, *args)
-    dt = time.perf_counter() - t0
+        self.o.couplings(self.E0, *ks)
+        return time.perf_counter() - t0
+
+    def step(self):
+        """(couplings, seconds) of one timed sample."""
+        return self.n, self._time(self.n)
+
+
+def oracle_rate(prob, seconds=15.0, seed=0):
+    """Couplings/s of the oracle on one calibrated sample (see OracleSampler)."""
+    s = OracleSampler(prob, seconds, seed)
+    n, dt = s.step()
     return n / dt, n, dt
 
 
 def run_reference(args):
-    """The oracle arm: each step times the oracle on a bounded sample of the workload."""
+    """The oracle arm: each step times the oracle on a bounded sample of the
+    workload (calibrated once, in the first warm-up step)."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     from e2_inputs import make_problem
     prob = make_problem(args.config)
     cores = os.cpu_count()
+    sampler = OracleSampler(prob, args.ref_seconds, seed=1)
     for _ in range(args.warmup):
-        oracle_rate(prob, seconds=args.ref_seconds, seed=1)
-    rates, ns, dts = [], [], []
-    for s in range(args.steps):
-        r, n, dt = oracle_rate(prob, seconds=args.ref_seconds, seed=100 + s)
-        rates.append(r), ns.append(n), dts.append(dt)
+        sampler.step()
+    ns, dts = [], []
+    for _ in range(args.steps):
+        n, dt = sampler.step()
+        ns.append(n), dts.append(dt)
     value = sum(ns) / sum(dts)
+    sample = (f"{sampler.n} random external determinants per step (class-size weighted), V_K from the explicit "
+              f"Q H P row and H_KK each, about {args.ref_seconds:.0f} s of oracle work per step")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "couplings/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(dts) / len(dts),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.config], "couplings_per_step": int(sum(ns) / len(ns))},
+            "config": {"workload": WORKLOADS[args.config], "couplings_per_step": sampler.n},
             "cpu_baseline": {"value": value, "unit": "couplings/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{int(sum(ns) / len(ns))} random external determinants per step "
-                                       f"(class-size weighted), V_K and H_KK each"},
+                             "sample": sample},
             "e2e": {"value": value, "unit": "couplings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -334,6 +381,175 @@ def run_batch(args):
     return 0
 
 
+ARITH_DTYPE = {"fp64": "f64", "sliced": "f64-emulated (bf16x5 slices, float-float epilogue)"}
+
+
+def _arith_parts(plan, present):
+    """The arithmetic each part of the path ran in."""
+    return {**{CLASS_NAMES[k]: ("sliced bf16 + float-float epilogue" if plan.contraction(k)[0] else "fp64")
+               for k in present if k in GEMM_CLASSES},
+            **({"(2,2)": "float-float" if plan.contraction(8)[0] else "fp64"} if 8 in present else {}),
+            "gather classes": "fp64",
+            "integral products": "sliced bf16" if plan.contraction(-1)[0] else "fp64",
+            "adjoint products": "sliced bf16 (4 slices)" if plan.contraction(-2)[0] else "fp64"}
+
+
+def _forward_fn(plan, t, shard, dist):
+    """One step: the forward over all of Q; with shards, this rank's share,
+    the ranks' partials summed (NCCL) and the fixed-order reduction."""
+    if shard:
+        return lambda: plan.sharded_forward(dist, **t)
+    return lambda: plan.forward(**t)
+
+
+def _timed_forward(plan, t, steps, warmup, stream, ws, dist, dev, clocks=None, shard=False):
+    """warmup + steps forwards; the timed region is barrier-bracketed and the
+    step time is the slowest rank's.  Per-class kernel times (root 0) come
+    from event pairs the library records around each class kernel."""
+    import torch
+    step = _forward_fn(plan, t, shard, dist)
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize()
+    launches = plan.launch_count()
+    evs = []
+    for _ in range(steps):
+        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(9)]
+        for a, b in pairs:
+            a.record()
+            b.record()
+        evs.append(pairs)
+    torch.cuda.synchronize()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    torch.cuda.nvtx.range_push("forward")   # ncu --nvtx --nvtx-include "forward/" selects these launches
+    start.record(stream)
+    for s in range(steps):
+        plan.set_events(evs[s])
+        E2, E2c, E0 = step()
+    end.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    if ws > 1:
+        dist.barrier()
+    plan.set_events(None)
+    ms = max_over_ranks(start.elapsed_time(end) / steps, ws, dist, dev)
+    present = [k for k in range(9) if plan.q_per_class[k] > 0]
+    ktime = {k: sum(evs[s][k][0].elapsed_time(evs[s][k][1]) for s in range(steps)) / steps for k in present}
+    return dict(ms=ms, ktime=ktime, present=present, E2=E2.clone(), E2c=E2c.clone(), E0=E0.clone(),
+                launches=launches, clocks=clk)
+
+
+def _kernels(plan, present):
+    sliced = {k for k in GEMM_CLASSES if k in present and plan.contraction(k)[0]}
+    kern = {k: ("k_class_oz" if k in sliced else KERNEL_OF_CLASS[k]) for k in present}
+    if 8 in present and plan.contraction(8)[0]:
+        kern[8] = "k_class22_df"  # class (2,2) in float-float
+    return kern
+
+
+def _roofline(prob, plan, fw, peak_dmma, peak_dfma):
+    """Roofline of the dominant kernel over the timed steps (root 0's launches)."""
+    present, ktime = fw["present"], fw["ktime"]
+    kern = _kernels(plan, present)
+    ksum = {}
+    for k in present:
+        ksum[kern[k]] = ksum.get(kern[k], 0.0) + ktime[k]
+    dom_kernel = max(ksum, key=ksum.get)
+    classes = [k for k in present if kern[k] == dom_kernel]
+    t_ms = sum(ktime[k] for k in classes)
+    couplings = sum(plan.q_per_class[k] for k in classes)
+    if dom_kernel == "k_class_oz":
+        # the emulation's tensor work: 15 slice pairs (levels 2..6 of five
+        # slices per operand), each a real product of length 2K into the two
+        # real outputs (Re V, Im V) of a coupling: 120 K bf16 flops per
+        # coupling; peak: the measured bf16 rate, sustained (the kernel runs
+        # inside a long step)
+        mp = _measured_peaks()
+        peak_bf16 = mp.get("bf16_tflops_sustained") or 1400.0
+        flops = sum(120.0 * plan.q_per_class[k] * _kdim(prob, k) for k in classes)
+        achieved = flops / (t_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_bf16, "unit": "TFLOP/s",
+                "frac": achieved / peak_bf16, "traffic": _traffic("k_class_oz"),
+                "traffic_scope": "DRAM bytes per step over the kernel's launches (ncu)",
+                "kernel": "k_class_oz classes " + " ".join(CLASS_NAMES[k] for k in classes),
+                "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop), "
+                                "of measured" if mp.get("bf16_tflops_sustained") else
+                                "fallback 1.4 PFLOP/s sustained bf16, of fallback"),
+                "algorithmic_flops_per_step": flops, "flops_per_coupling": "120 K bf16 (15 slice pairs x 2 real "
+                                                                          "outputs x real length 2K x 2)"}
+    elif dom_kernel == "k_class_gemm":
+        # algorithmic: 8 K real flops per coupling (one complex multiply-add
+        # per contraction index, K = the class's contraction length); the
+        # kernel executes fewer: Gauss's three real products per complex
+        # product (6 real flops) and, with column tiles, only each tile's
+        # compacted rows (the structural zeros of the coupling tables skipped)
+        flops = sum(8.0 * plan.q_per_class[k] * _kdim(prob, k) for k in classes)
+        exe = 0.0
+        for k in classes:
+            f = 6.0 * plan.q_per_class[k] * _kpad(prob, k)
+            tiles, krows, used = plan.class_tiles(k)
+            if used:
+                f = 6.0 * (plan.q_per_class[k] / _ncols(prob, plan, k)) * krows * 64
+            exe += f
+        achieved = flops / (t_ms * 1e-3) / 1e12
+        executed = exe / (t_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_dmma, "unit": "TFLOP/s",
+                "frac": achieved / peak_dmma, "traffic": _traffic("k_class_gemm"),
+                "traffic_scope": "DRAM bytes per launch (ncu)",
+                "kernel": "k_class_gemm classes " + " ".join(CLASS_NAMES[k] for k in classes),
+                "peak_source": "FP64 tensor pipe (mma.sync m16n8k8 f64) measured on this GPU in this run "
+                               "(e2_fp64_peak, burst), of measured; MEASURED_PEAKS.json has no FP64 figure",
+                "peak_nominal_ratio_tflops": (_measured_peaks().get("bf16_tflops") or 1810.3) * 1.25 / 2250.0,
+                "algorithmic_flops_per_step": flops,
+                "flops_per_coupling": "8 K real (complex multiply-add per contraction index)",
+                "executed_tflops": executed, "executed_frac": executed / peak_dmma,
+                "executed_flops_per_step": exe,
+                "executed_note": "6 real flops per complex product (Gauss) over each column tile's compacted "
+                                 "rows; frac above 1 = the algorithmic count includes work the kernel skips"}
+    else:
+        roof = {"bound": "alu", "achieved": None, "peak": peak_dfma, "unit": "TFLOP/s", "frac": None,
+                "traffic": None, "kernel": dom_kernel}
+    roof.update({"ms_per_step": t_ms, "launches_per_step": len(classes),
+                 "couplings_per_s": couplings / (t_ms * 1e-3), "kernel_ms_per_step": ksum})
+    return roof
+
+
+def _timed_fwd_bwd(plan, t, steps, warmup, stream, ws, dist, dev):
+    import torch
+    for _ in range(warmup):
+        plan.value_and_grad(**t)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("fwd_bwd")   # ncu --nvtx --nvtx-include "fwd_bwd/" selects these launches
+    b0.record(stream)
+    for _ in range(steps):
+        vg = plan.value_and_grad(**t)
+    b1.record(stream)
+    torch.cuda.nvtx.range_pop()
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    return max_over_ranks(b0.elapsed_time(b1) / steps, ws, dist, dev), vg[0].clone()
+
+
+def _aux_steps(args, ms):
+    """Steps of the secondary timings (fwd+bwd, end to end, the other
+    arithmetic): the headline's K where a step is short, else as many as fit
+    about --aux-seconds (at least 1)."""
+    if args.aux_steps > 0:
+        return args.aux_steps, 1
+    n = int(max(1, min(args.steps, args.aux_seconds * 1e3 / max(ms, 1e-3))))
+    return n, (2 if ms < 5e3 else 1)
+
+
 def run(args):
     import torch
     import torch.distributed as dist
@@ -342,6 +558,10 @@ def run(args):
     dev = torch.device("cuda", local)
     if ws > 1:
         dist.init_process_group("nccl", device_id=dev)
+    # N > 1: the external space is sharded over the ranks (each class's units
+    # split evenly; partials summed by NCCL, E2 bitwise equal to N = 1); total
+    # work fixed.  --replicas: N independent copies of the whole job instead.
+    shard = ws > 1 and not args.replicas
     import paper_2608_11529_b300 as e2
     from e2_inputs import make_problem
     over = dict(Lc=args.factors, Lx=args.factors // 2) if args.factors else {}
@@ -351,6 +571,7 @@ def run(args):
         over["n_core"] = args.core
     prob = make_problem(args.config, **over)
     plan = e2.E2Problem.from_problem(prob)
+    plan.set_arithmetic(args.arith == "sliced")
     couplings = float(plan.q_per_class.sum()) * plan.n_roots
     fbytes = 16.0 * (prob.Bc.shape[0] + (prob.Bx.shape[0] if prob.ham != "DC" else 0)) * prob.n * prob.n
     t = e2.device_inputs(prob, prob.X0, device=dev)
@@ -366,126 +587,24 @@ def run(args):
         if tiles:
             col_tiles[CLASS_NAMES[k]] = {"used": used, "compacted_share": krows / (tiles * _kpad(prob, k)),
                                          "autotune_ms": list(tune.get(k, ()))}
-
-    # warm-up
-    for _ in range(args.warmup):
-        plan.forward(**t)
-    torch.cuda.synchronize()
-    launches = plan.launch_count()
-
-    # per-step event pairs around each class kernel (handles materialised here)
-    evs = []
-    for _ in range(args.steps):
-        pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(9)]
-        for a, b in pairs:
-            a.record()
-            b.record()
-        evs.append(pairs)
-    torch.cuda.synchronize()
-
-    clocks = ClockSampler(local)
     stream = torch.cuda.current_stream(dev)
-    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if ws > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    torch.cuda.nvtx.range_push("forward")   # ncu --nvtx --nvtx-include "forward/" selects these launches
-    start.record(stream)
-    for s in range(args.steps):
-        plan.set_events(evs[s])
-        E2, E2c, E0 = plan.forward(**t)
-    end.record(stream)
-    torch.cuda.nvtx.range_pop()
-    torch.cuda.synchronize()
-    clk = clocks.stop()
-    if ws > 1:
-        dist.barrier()
-    plan.set_events(None)
-    ms = max_over_ranks(start.elapsed_time(end) / args.steps, ws, dist, dev)
-    E2dev = E2.clone()
 
-    # per-class kernel times (root 0) over the timed region, summed per kernel
-    present = [k for k in range(9) if plan.q_per_class[k] > 0]
-    ktime = {k: sum(evs[s][k][0].elapsed_time(evs[s][k][1]) for s in range(args.steps)) / args.steps for k in present}
-    sliced = {k for k in GEMM_CLASSES if k in present and plan.contraction(k)[0]}
-    kern = {k: ("k_class_oz" if k in sliced else KERNEL_OF_CLASS[k]) for k in present}
-    if 8 in present and plan.contraction(8)[0]:
-        kern[8] = "k_class22_df"  # class (2,2) in float-float
-    ksum = {}
-    for k in present:
-        ksum[kern[k]] = ksum.get(kern[k], 0.0) + ktime[k]
-    dom_kernel = max(ksum, key=ksum.get)
-    classes = [k for k in present if kern[k] == dom_kernel]
-    if dom_kernel == "k_class_oz":
-        # the sliced method's tensor work: 15 slice pairs (levels 2..6 of five
-        # slices per operand), each a real product of length 2K into the two
-        # real outputs (Re V, Im V) of a coupling: 15 * 2 * 2K * 2 = 120 K bf16
-        # flops per coupling; peak: the measured bf16 rate, sustained (the
-        # kernel runs inside a long step)
-        mp = _measured_peaks()
-        peak_bf16 = mp.get("bf16_tflops_sustained") or 1400.0
-        flops = sum(120.0 * plan.q_per_class[k] * _kdim(prob, k) for k in classes)
-        t_ms = sum(ktime[k] for k in classes)
-        achieved = flops / (t_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_bf16, "unit": "TFLOP/s",
-                "frac": achieved / peak_bf16, "traffic": _traffic("k_class_oz"),
-                "traffic_scope": "DRAM bytes per step over the kernel's launches (ncu, the (0,2) and (1,2) launches)",
-                "kernel": "k_class_oz classes " + " ".join(CLASS_NAMES[k] for k in classes),
-                "peak_source": ("MEASURED_PEAKS.json bf16_tflops_sustained (cuBLAS bf16, seconds-long loop)"
-                                if mp.get("bf16_tflops_sustained") else "fallback 1.4 PFLOP/s sustained bf16"),
-                "algorithmic_flops_per_step": flops, "ms_per_step": t_ms,
-                "launches_per_step": len(classes),
-                "couplings_per_s": sum(plan.q_per_class[k] for k in classes) / (t_ms * 1e-3),
-                "flops_per_coupling": "120 K bf16 (15 slice pairs x 2 real outputs x real length 2K x 2)"}
-    elif dom_kernel == "k_class_gemm":
-        # complex products by Gauss's three real products: 6 real flops per
-        # complex multiply-add, K of them per coupling; with column tiles K is
-        # each tile's compacted length (the products the kernel executes)
-        flops = 0.0
-        for k in classes:
-            f = 6.0 * plan.q_per_class[k] * _kdim(prob, k)
-            tiles, krows, used = plan.class_tiles(k)
-            if used:
-                f = 6.0 * (plan.q_per_class[k] / _ncols(prob, plan, k)) * krows * 64
-            flops += f
-        t_ms = sum(ktime[k] for k in classes)
-        achieved = flops / (t_ms * 1e-3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak_dmma, "unit": "TFLOP/s",
-                "frac": achieved / peak_dmma, "traffic": _traffic("k_class_gemm"),
-                "kernel": "k_class_gemm classes " + " ".join(CLASS_NAMES[k] for k in classes), "peak_source":
-                "measured on this GPU: mma.sync m16n8k8 f64 burst (e2_fp64_peak)",
-                "algorithmic_flops_per_step": flops, "ms_per_step": t_ms, "launches_per_step": len(classes),
-                "flops_per_coupling": "6 K (3 real products per complex product, K = contraction length; "
-                                      "with column tiles, each tile's compacted K)"}
-    else:
-        roof = {"bound": "alu", "achieved": None, "peak": peak_dfma, "unit": "TFLOP/s", "frac": None,
-                "traffic": None, "kernel": dom_kernel}
-    roof["kernel_ms_per_step"] = ksum
+    fw = _timed_forward(plan, t, args.steps, args.warmup, stream, ws, dist, dev, clocks=ClockSampler(local),
+                        shard=shard)
+    ms = fw["ms"]
+    jobs = 1 if shard else ws   # whole-job work per step: one job split over the ranks, or ws replicas
+    roof = _roofline(prob, plan, fw, peak_dmma, peak_dfma)
+    aux, aux_warm = _aux_steps(args, ms)
 
     # forward + backward in one pass (E2 and dE2/d(h, c, B, lambda), V formed
     # once) against forward alone
     fwdbwd = None
-    if not args.no_backward:
-        for _ in range(2):
-            plan.value_and_grad(**t)
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push("fwd_bwd")   # ncu --nvtx --nvtx-include "fwd_bwd/" selects these launches
-        b0.record(stream)
-        for _ in range(args.steps):
-            vg = plan.value_and_grad(**t)
-        b1.record(stream)
-        torch.cuda.nvtx.range_pop()
-        torch.cuda.synchronize()
-        if ws > 1:
-            dist.barrier()
-        bms = max_over_ranks(b0.elapsed_time(b1) / args.steps, ws, dist, dev)
-        same = bool(torch.equal(vg[0], E2dev)) if E2dev is not None else None
-        fwdbwd = {"ms_fwd": ms, "ms_fwd_bwd": bms, "ratio_fwd_bwd_over_fwd": bms / ms,
-                  "E2_bitwise_equal_to_forward": same,
+    if not args.no_backward and shard:
+        fwdbwd = {"skipped": "the adjoint runs unsharded; fwd+bwd is measured at N = 1"}
+    elif not args.no_backward:
+        bms, E2vg = _timed_fwd_bwd(plan, t, aux, aux_warm, stream, ws, dist, dev)
+        fwdbwd = {"ms_fwd": ms, "ms_fwd_bwd": bms, "ratio_fwd_bwd_over_fwd": bms / ms, "steps": aux,
+                  "warmup": aux_warm, "E2_bitwise_equal_to_forward": bool(torch.equal(E2vg, fw["E2"])),
                   "gradients": "E2 with dE2/dh, dE2/dB (all factors, Hermitian), dE2/dc, dE2/dlambda from one "
                                "e2_backward call; V recomputed, never stored"}
 
@@ -497,29 +616,51 @@ def run(args):
         dev_in = {k: (torch.empty_like(v, device=dev) if torch.is_tensor(v) else v) for k, v in host.items()}
         out_host = torch.empty(plan.n_roots, dtype=torch.float64).pin_memory()
 
+        fwd_in = _forward_fn(plan, dev_in, shard, dist)
+
         def e2e_step():
             for k, v in host.items():
                 if torch.is_tensor(v):
                     dev_in[k].copy_(v, non_blocking=True)
-            E2_, _, _ = plan.forward(**dev_in)
+            E2_, _, _ = fwd_in()
             out_host.copy_(E2_, non_blocking=True)
 
-        for _ in range(2):
+        for _ in range(aux_warm):
             e2e_step()
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
         s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(aux):
             e2e_step()
         s1.record(stream)
         torch.cuda.synchronize()
         if ws > 1:
             dist.barrier()
-        ems = max_over_ranks(s0.elapsed_time(s1) / args.steps, ws, dist, dev)
-        e2e = {"value": ws * couplings / (ems * 1e-3), "unit": "couplings/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": ems}
+        ems = max_over_ranks(s0.elapsed_time(s1) / aux, ws, dist, dev)
+        e2e = {"value": jobs * couplings / (ems * 1e-3), "unit": "couplings/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": ems, "steps": aux}
+        del dev_in, host
+
+    # the other arithmetic on the same workload (emulated when the headline is FP64)
+    alt = None
+    other = "sliced" if args.arith == "fp64" else "fp64"
+    if not args.no_alt:
+        plan.set_arithmetic(other == "sliced")
+        if plan.arithmetic() == other:
+            fa = _timed_forward(plan, t, aux, aux_warm, stream, ws, dist, dev, shard=shard)
+            alt = {"arith": other, "dtype": ARITH_DTYPE[other], "value": jobs * couplings / (fa["ms"] * 1e-3),
+                   "unit": "couplings/s", "ms_per_step": fa["ms"], "steps": aux, "warmup": aux_warm,
+                   "arithmetic": _arith_parts(plan, fa["present"]),
+                   "E2": float(fa["E2"].cpu()[0]),
+                   "max_abs_dE2_class_vs_headline": float((fa["E2c"] - fw["E2c"]).abs().max()),
+                   "class_ms": {CLASS_NAMES[k]: fa["ktime"][k] for k in fa["present"]},
+                   "roofline": _roofline(prob, plan, fa, peak_dmma, peak_dfma)}
+            if not args.no_backward and not shard:
+                abms, _ = _timed_fwd_bwd(plan, t, aux, aux_warm, stream, ws, dist, dev)
+                alt["fwd_bwd"] = {"ms_fwd_bwd": abms, "ratio_fwd_bwd_over_fwd": abms / fa["ms"], "steps": aux}
+        plan.set_arithmetic(args.arith == "sliced")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
@@ -529,27 +670,25 @@ def run(args):
                          f"V_K from the explicit Q H P row and H_KK each, {dt:.1f} s"}
 
     if rank == 0:
-        line = {"metric": METRIC, "value": ws * couplings / (ms * 1e-3), "unit": "couplings/s", "n_gpus": ws,
+        present = fw["present"]
+        line = {"metric": METRIC, "value": jobs * couplings / (ms * 1e-3), "unit": "couplings/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "scaling": "strong" if shard else "weak", "vs_baseline": None, "dtype": ARITH_DTYPE[args.arith],
+                "data": "synthetic",
                 "config": {"workload": WORKLOADS[args.config] + (f" [profiling variant {over}]" if over else ""),
                            "couplings_per_step": int(couplings),
                            "roots": plan.n_roots, "reference": f"device Davidson, {iters} iterations",
                            "l2": f"inputs larger than L2: the {fbytes / 1e6:.0f} MB factor set is re-read every step",
-                           "arithmetic": {
-                               **{CLASS_NAMES[k]: ("sliced bf16 + float-float epilogue" if plan.contraction(k)[0]
-                                                   else "fp64") for k in present if k in GEMM_CLASSES},
-                               **({"(2,2)": "float-float" if plan.contraction(8)[0] else "fp64"} if 8 in present
-                                  else {}),
-                               "gather classes": "fp64",
-                               "integral products": "sliced bf16" if plan.contraction(-1)[0] else "fp64",
-                               "adjoint products": "sliced bf16 (4 slices)" if plan.contraction(-2)[0] else "fp64"},
+                           "arithmetic": _arith_parts(plan, present),
                            "column_tiles": col_tiles,
-                           "E2": float(E2.cpu()[0]), "E0": float(E0.cpu()[0]),
-                           "class_ms": {CLASS_NAMES[k]: ktime[k] for k in present}},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fwd_bwd": fwdbwd,
-                "gpu_launches": launches * args.steps,
-                "clocks": clk, "fp64_peaks_tflops": {"dmma": peak_dmma, "dfma": peak_dfma}}
+                           "E2": float(fw["E2"].cpu()[0]), "E2_hex": float(fw["E2"].cpu()[0]).hex(),
+                           "E0": float(fw["E0"].cpu()[0]),
+                           "parallelism": (f"external space sharded over {ws} GPUs (NCCL sum of the partials)"
+                                           if shard else f"{ws} independent replica(s)"),
+                           "class_ms": {CLASS_NAMES[k]: fw["ktime"][k] for k in present}},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fwd_bwd": fwdbwd, "alt_arithmetic": alt,
+                "gpu_launches": fw["launches"] * args.steps,
+                "clocks": fw["clocks"], "fp64_peaks_tflops": {"dmma": peak_dmma, "dfma": peak_dfma}}
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
@@ -562,19 +701,29 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
-    ap.add_argument("--config", default="ne_dcg", choices=sorted(WORKLOADS),
-                    help="ne_dcg is the benchmark workload; the others run as evidence / profiling variants")
+    ap.add_argument("--config", default="ar_dcb_das", choices=sorted(WORKLOADS),
+                    help="ar_dcb_das (the largest workload whose K forwards fit the run) is the benchmark workload; "
+                         "the others run as evidence / profiling variants")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default column tiles")
+    ap.add_argument("--arith", default="fp64", choices=["fp64", "sliced"],
+                    help="arithmetic of the headline: fp64 (the library default) or the emulated sliced form")
+    ap.add_argument("--no-alt", action="store_true", help="skip the timing of the other arithmetic")
+    ap.add_argument("--replicas", action="store_true",
+                    help="under torchrun: N independent replicas of the whole job instead of one sharded job")
+    ap.add_argument("--aux-steps", type=int, default=0,
+                    help="steps of the fwd+bwd, end-to-end and other-arithmetic timings (0: automatic)")
+    ap.add_argument("--aux-seconds", type=float, default=30.0,
+                    help="automatic aux steps: the headline's K, capped at about this much timed work")
     ap.add_argument("--roots", type=int, default=0, help="override the root count (batch evidence runs)")
     ap.add_argument("--batch", action="store_true",
                     help="evidence run: the 3 Hamiltonians x 3 frozen cutoffs of --config batched in one "
                          "graph-captured launch against sequential forwards")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="oracle work per cpu_baseline sample (the sample is sized to about this long)")
-    ap.add_argument("--ref-seconds", type=float, default=6.0)
+    ap.add_argument("--ref-seconds", type=float, default=4.0)
     ap.add_argument("--core", type=int, default=0, help="override the core spinor count (slices)")
     ap.add_argument("--virt", type=int, default=0,
                     help="override the virtual spinor count: a smaller variant with the same tile shapes, for "

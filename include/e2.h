@@ -48,7 +48,12 @@
  * allocates no device memory: it works in the caller's workspace, of at least
  * e2_workspace_size() bytes, 256-byte aligned.
  *
- * Complex numbers are interleaved (re, im) doubles.  Everything is FP64.
+ * Complex numbers are interleaved (re, im) doubles.  Arithmetic: by default
+ * every step runs in IEEE FP64 (the dense contractions as complex FP64
+ * products on the FP64 tensor pipe, mma.sync f64; denominators, reciprocals
+ * and sums in FP64).  e2_set_contraction opts parts of the path into an
+ * emulated form (bf16 slices on the tensor pipe, float-float epilogues) that
+ * is faster but not FP64 arithmetic; see there.
  *
  * Errors: argument errors return immediately with a status and enqueue no
  * work.  No C++ exception crosses this interface.  Calls on one e2_problem
@@ -79,7 +84,10 @@ typedef enum {
   E2_ERR_UNSUPPORTED = 3,
   E2_ERR_WORKSPACE = 4,
   E2_ERR_CUDA = 5,
-  E2_ERR_NONFINITE = 6
+  E2_ERR_NONFINITE = 6,  /* device-detected: a non-finite energy (e2_query_status) */
+  E2_ERR_INTRUDER = 7,   /* device-detected: |E0 - H_KK| < 1e-12 Eh with b = 0 (e2_query_status; Sec. 2.6) */
+  E2_ERR_OOM = 8,        /* host memory for a plan could not be allocated */
+  E2_ERR_TIMEOUT = 9     /* reserved for bounded device waits; no kernel of this version waits on another */
 } e2_status;
 
 #define E2_NCLASS 9
@@ -142,6 +150,107 @@ E2_API e2_status e2_workspace_size(const e2_problem* prob, size_t* bytes);
  * The summation order is fixed, so repeated calls give bitwise equal results. */
 E2_API e2_status e2_forward(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
                      void* stream, double* E2, double* E2_class, double* E0);
+
+/* Coupling tensors of one reference state (step a4: the <K|E_pq|L> C_L
+ * factors of Sec. 2.4, Eq. sumsigma, restricted to the active space), for
+ * inspection.  Builds the string lists and root `root`'s tables in
+ * `workspace` as e2_forward does, then copies one family:
+ *   family 0  D^t_A     = <A|a_t|Psi>,             rows t (n_act);          strings of N-1 electrons (class (1,2))
+ *          1  D^{t+}_A  = <A|a+_t|Psi>,            rows t;                  N+1 (class (2,1))
+ *          2  D^{tu}_A  = <A|a_u a_t|Psi>, t < u,  row u(u-1)/2 + t;        N-2 (class (0,2))
+ *          3  D^{t+u+}_A = <A|a+_t a+_u|Psi>, t < u, same rows;            N+2 (class (2,0))
+ *          4  row 0: c_A; row 1 + t n_act + u: <A|a+_t a_u|Psi>;            N   (class (1,1))
+ *   table   device [rows][n_A] complex, or NULL
+ *   strings device [n_A] active-local bitsets (bit t = active spinor t) of
+ *           the class's string list in address order, or NULL
+ *   rows, n_A host, or NULL: the table's shape (both outputs NULL: sizes
+ *           only, no device work)
+ * Every entry is exactly +-c_L of one P determinant L or 0.  Enqueues on
+ * `stream`; inputs and workspace as for e2_forward.  E2_ERR_INVALID_ARG for
+ * a family or root out of range. */
+E2_API e2_status e2_coupling_tables(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                                   void* stream, int root, int family, double* table, uint64_t* strings,
+                                   int64_t* rows, int64_t* n_A);
+
+/* Per-coupling probe (no counterpart in the paper; it lets a caller check
+ * single couplings V_K = <K|H|Psi> and D_K = E0 - H_KK of a full-size run
+ * against an independent evaluation).  Sets up root `root` as e2_forward
+ * does, then runs the FP64 class kernel of class cls (the same device code as
+ * the forward's, whatever arithmetic the class is set to) with its probe
+ * outputs on:
+ *   dense classes (0,2) (1,2) (1,1) (2,0) (2,1): the 64 x 64 tile (tile_m,
+ *     tile_n) as e2_partials numbers tiles; V device [64][64] complex, D
+ *     device [64][64]; entry [i][j]: external row 64 tile_m + i (the row
+ *     order of e2_partials), string = column j of the tile (plain columns:
+ *     list index 64 tile_n + j; column tiles: perm[64 tile_n + j] of
+ *     e2_class_tiles_copy); entries outside the class are 0;
+ *   gather classes (0,1) (1,0) (0,0): the whole class; tile_m, tile_n
+ *     ignored; V device [rows][n_A] complex, D device [rows][n_A], rows = the
+ *     correlated virtuals (0,1), the correlated core spinors (1,0) or one row
+ *     (0,0), strings in the class list's address order.
+ *   shape host [2] or NULL: the shape of V and D; with V and D both NULL
+ *     only the shape is returned (no device work).
+ * V is formed from the unnormalised c (as the partials are).  Class (2,2)
+ * (elementwise, V = <ab||ij> c_A up to sign, never formed) returns
+ * E2_ERR_UNSUPPORTED, as does a class without couplings.  Enqueues on
+ * `stream`; inputs and workspace as for e2_forward (the probe writes the
+ * tile's partial slot too). */
+E2_API e2_status e2_probe_couplings(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                                   void* stream, int root, int cls, int64_t tile_m, int64_t tile_n, double* V,
+                                   double* D, int64_t* shape);
+
+/* Sharding of the external space over ranks (no counterpart in the paper's
+ * method; its sigma-build is distributed over CPU nodes, Sec. 2.4 / 3.1, which
+ * is prior art here).  Every class's work is cut into units -- row tiles of a
+ * dense class, (core pair, 8-wide virtual block pair) units of (2,2), rows
+ * (virtual a / core i) of (0,1) / (1,0), 256-string blocks of (0,0) -- and
+ * rank r of n takes the contiguous units [u r / n, u (r+1) / n) of each class.
+ * Everything else (integrals, string lists, coupling tables, E0) is
+ * replicated.  A sharded e2_forward writes only its own partial slots and
+ * zeroes the others, so the element-wise sum of all ranks' partials is
+ * bit for bit the unsharded set:
+ *   e2_set_shard(prob, rank, n);  e2_forward(...);
+ *   (caller) sum the partials over ranks (e2_shard_buffers gives the device
+ *            array; e.g. an all-reduce SUM) and take the minimum of the |D|
+ *            keys (int64, same call; all-reduce MIN);
+ *   e2_reduce(prob, workspace, ...)  -> E2, E2_class, E0 of the whole space,
+ *            bitwise equal to an unsharded e2_forward for any n.
+ * The E2 output of a sharded e2_forward is this rank's share alone.
+ * e2_backward and e2_batch_forward return E2_ERR_UNSUPPORTED on a sharded
+ * problem; e2_set_shard(prob, 0, 1) undoes the split.
+ *   e2_shard_units   units of class cls and this rank's [first, end)
+ *   e2_shard_buffers device pointers into `workspace`: the partials
+ *                    (n_partials doubles, all roots and classes) and the
+ *                    smallest-|D| keys (n_keys int64, ordered like |D|) */
+E2_API e2_status e2_set_shard(e2_problem* prob, int rank, int n_ranks);
+E2_API e2_status e2_shard_units(const e2_problem* prob, int cls, int64_t* units, int64_t* first, int64_t* end);
+E2_API e2_status e2_shard_buffers(const e2_problem* prob, void* workspace, double** partials, int64_t* n_partials,
+                                  int64_t** min_keys, int64_t* n_keys);
+E2_API e2_status e2_reduce(e2_problem* prob, void* workspace, size_t workspace_bytes, void* stream, double* E2,
+                           double* E2_class, double* E0);
+
+/* Device status word (the conditions of Sec. 2.6 that only the device sees).
+ * Every e2_forward (also e2_forward_noalloc, each job of e2_batch_forward and
+ * e2_backward with an E2 output) clears it at its start and writes it in its
+ * workspace; e2_query_status reads it back after that work:
+ *   flags     bit E2_STATUS_NONFINITE: some class energy or E2 is NaN or
+ *             infinite (a non-finite input propagates into it; on the sliced
+ *             path the slicers turn a non-finite operand into a NaN scale);
+ *             bit E2_STATUS_INTRUDER: with b = 0, some external determinant
+ *             of an evaluated class has |E0 - H_KK| below 1e-12 Eh (an
+ *             intruder state; the imaginary level shift b > 0 of Sec. 2.6 is
+ *             the remedy).  May be NULL.
+ *   min_abs_D host [n_roots][E2_NCLASS] or NULL: the smallest |E0 - H_KK| over
+ *             the couplings of each class (+inf for a class without couplings;
+ *             class (2,2): over its couplings with non-zero <ab||ij>).
+ * Returns E2_ERR_NONFINITE if that flag is set, else E2_ERR_INTRUDER if that
+ * one is, else E2_OK; E2_ERR_CUDA if the read fails.  Synchronises `stream`
+ * (the copy is enqueued on it); `workspace` is the one the work used (for
+ * e2_forward_noalloc pass NULL: the library's own scratch). */
+#define E2_STATUS_NONFINITE 1u
+#define E2_STATUS_INTRUDER 2u
+E2_API e2_status e2_query_status(const e2_problem* prob, const void* workspace, void* stream, uint32_t* flags,
+                                 double* min_abs_D);
 
 /* Batches (no counterpart in the paper: a throughput device).  Several
  * planned problems -- different Hamiltonians, root counts, frozen cutoffs --
@@ -287,28 +396,32 @@ E2_API e2_status e2_class_tiles_copy(const e2_problem* prob, int cls, int32_t* p
 E2_API e2_status e2_set_class_tiles(e2_problem* prob, int cls, int on);
 
 /* Arithmetic of the dense-class contraction (step a7; no counterpart in the
- * paper, which fixes only the FP64 accuracy of the result).
+ * paper, which computes in FP64).  The default everywhere is FP64.
  *   E2_CONTRACT_FP64   complex FP64 products on the FP64 tensor pipe
- *                      (mma.sync f64), plain or column-tiled;
- *   E2_CONTRACT_SLICED the error-free slicing of Ozaki et al.: five 8-bit
- *                      slices of each operand on the bf16 tensor pipe with
- *                      exact FP32 accumulation of the leading levels, and the
- *                      Epstein-Nesbet epilogue in float-float arithmetic
- *                      (each V to about 2^-40 of its row and string scale;
- *                      about 48 significant bits in the epilogue).  Available
- *                      for (0,2), (1,2), (2,1), (2,0) when the real
- *                      contraction length 2 K is at most 256 and the slices
- *                      fit 16 GiB; the default there.
+ *                      (mma.sync f64), plain or column-tiled, FP64 epilogue.
+ *                      The default for every class and product.
+ *   E2_CONTRACT_SLICED opt-in emulation, NOT FP64 arithmetic: the slicing of
+ *                      Ozaki et al.: five 8-bit slices of each operand on the
+ *                      bf16 tensor pipe with exact FP32 accumulation of the
+ *                      leading levels, and the Epstein-Nesbet epilogue in
+ *                      float-float arithmetic (each V to about 2^-40 of its
+ *                      row and string scale; about 48 significant bits in the
+ *                      epilogue; class energies within about 1e-11 relative of
+ *                      the FP64 ones on the tested shapes).  Available for
+ *                      (0,2), (1,2), (2,1), (2,0) when the real contraction
+ *                      length 2 K is at most 256 and the slices fit 16 GiB.
  * For class (2,2) (cls 8, elementwise, no contraction) E2_CONTRACT_SLICED
  * selects the float-float kernel for its denominators and sums (available
- * when the float-float string tables fit the same 16 GiB; the default then).
+ * when the float-float string tables fit the same 16 GiB).
  * cls = E2_CONTRACT_SETUP selects the same choice for the products over the
  * factor index that form the integral blocks (step a5: (ai|bt), (at|bu),
  * (av|uw)); there the slices are exact per 256 real terms and the sums over
- * the factor index accumulate in float-float; the default is sliced.
+ * the factor index accumulate in float-float.
  * cls = E2_CONTRACT_ADJOINT selects it for the products of e2_backward
  * (Gamma_D = W^T conj(T), Gamma_W = conj(T) D^T per row chunk, and
- * Cs = B Gamma^ when its slices fit 4 GiB); the default is sliced.
+ * Cs = B Gamma^ when its slices fit 4 GiB; four slices, 2^-33 of the
+ * scales).  A non-finite operand of a sliced product makes the energies NaN
+ * (the slicers flag it) and sets E2_ERR_NONFINITE in the status word.
  * e2_set_contraction returns E2_ERR_UNSUPPORTED for a class without the
  * sliced plan; e2_contraction reports the mode in use and whether the sliced
  * plan exists (either output may be NULL).  The backward pass forms its
@@ -324,22 +437,24 @@ E2_API e2_status e2_autotune(e2_problem* prob, const e2_inputs* in, void* worksp
                              void* stream, float* ms_out);
 
 /* Allocation-free variant of e2_forward (no counterpart in the paper).
- * Some callers cannot call cudaMalloc: code that enqueues work while a CUDA
- * graph is being captured, plugins living inside a host program that owns
- * the device allocator, and embedded runtimes that forbid allocation after
- * start-up.  This entry point runs exactly the computation of e2_forward, but
- * in a scratch array compiled into the library, E2_STATIC_SCRATCH_BYTES per
- * device, which every device that loads the library holds until the process
- * exits.  It allocates nothing and takes no workspace argument; inputs and
- * outputs are the caller's, as for e2_forward.
+ * Some callers cannot call cudaMalloc: plugins living inside a host program
+ * that owns the device allocator, and embedded runtimes that forbid device
+ * allocation after start-up.  This entry point runs exactly the computation
+ * of e2_forward, but in a scratch array compiled into the library,
+ * E2_STATIC_SCRATCH_BYTES per device, which every device that loads the
+ * library holds until the process exits.  It allocates nothing and takes no
+ * workspace argument; inputs and outputs are the caller's, as for e2_forward.
  *   - A problem whose e2_workspace_size() exceeds E2_STATIC_SCRATCH_BYTES is
  *     rejected with E2_ERR_WORKSPACE before any GPU work.
- *   - The first call on each device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *   - Each call looks up the array's device address on the current device
+ *     (a host-side query), so it runs on whichever device is current.
  *   - All calls, on every problem, share the one array and leave the last
  *     call's contents in it: calls whose GPU work can overlap (other streams,
  *     other host threads) overwrite each other's scratch and give wrong
- *     results; serialise them on one stream. */
+ *     results; serialise them on one stream.
+ *   - Like e2_forward it uploads the plan tables from host memory on every
+ *     call.  Its status word lives in the same array (e2_query_status with a
+ *     NULL workspace). */
 #define E2_STATIC_SCRATCH_BYTES (32u << 20)
 E2_API e2_status e2_forward_noalloc(e2_problem* prob, const e2_inputs* in, void* stream, double* E2,
                                     double* E2_class, double* E0);

@@ -656,6 +656,63 @@ int oracle_couplings(void* vp, const double* E0, int64_t nK, const int* nh, cons
   return 0;
 }
 
+/* Coupling tensors D^x_A = <A|x|Psi_root> (the <K|E_pq|L> C_L factors of
+   Sec. 2.4, Eq. sumsigma, restricted to the active space) for listed active
+   strings A, by generic operator algebra on full bitsets: the determinant
+   |A> (core full, active bits A, virtuals empty) is acted on by x^dagger
+   with the creation / annihilation rules above, and <A|x|L> = conj(<L|x^dagger|A>)
+   = the sign that action produced when it reaches a P determinant L (0
+   otherwise).  Families (rows r):
+     0  x = a_t              r = t
+     1  x = a+_t             r = t
+     2  x = a_u a_t, t < u   r = u (u - 1) / 2 + t
+     3  x = a+_t a+_u, t < u r = u (u - 1) / 2 + t
+     4  r = 0: x = 1; r = 1 + t n_act + u: x = a+_t a_u
+   out: [rows][nA] complex interleaved. */
+int oracle_dtable(void* vp, int family, int root, int64_t nA, const uint64_t* A, double* out) {
+  oracle_t* P = (oracle_t*)vp;
+  const int na = P->n_act;
+  const int rows = family <= 1 ? na : family <= 3 ? na * (na - 1) / 2 : 1 + na * na;
+  const int64_t np = P->pat_off[P->n_pat];
+#pragma omp parallel for schedule(static)
+  for (int64_t g = 0; g < nA; ++g) {
+    for (int r = 0; r < rows; ++r) {
+      /* x^dagger as a list of (creator?, spinor) applied right to left: ops[0] first */
+      int nops = 0, cre[2] = {0, 0}, sp[2] = {0, 0};
+      if (family == 0) { cre[0] = 1; sp[0] = r; nops = 1; }
+      else if (family == 1) { cre[0] = 0; sp[0] = r; nops = 1; }
+      else if (family <= 3) {
+        int u = 1;
+        while (u * (u + 1) / 2 <= r) ++u;
+        const int t = r - u * (u - 1) / 2;
+        if (family == 2) { cre[0] = 1; sp[0] = u; cre[1] = 1; sp[1] = t; }  /* (a_u a_t)^+ = a+_t a+_u */
+        else { cre[0] = 0; sp[0] = t; cre[1] = 0; sp[1] = u; }           /* (a+_t a+_u)^+ = a_u a_t */
+        nops = 2;
+      } else if (r > 0) {
+        const int t = (r - 1) / na, u = (r - 1) % na;                   /* (a+_t a_u)^+ = a+_u a_t */
+        cre[0] = 0; sp[0] = t; cre[1] = 1; sp[1] = u;
+        nops = 2;
+      }
+      det_t d;
+      make_det(P, &d, NULL, 0, A[g], NULL, 0);
+      int sign = 1, ok = 1;
+      for (int k = 0; k < nops && ok; ++k)
+        ok = cre[k] ? apply_cre(&d, P->a0 + sp[k], &sign) : apply_ann(&d, P->a0 + sp[k], &sign);
+      cplx v = 0;
+      if (ok) {
+        uint64_t L = 0;
+        for (int t = 0; t < na; ++t)
+          if (det_get(&d, P->a0 + t)) L |= 1ull << t;
+        const int64_t addr = p_address_active(P, L);
+        if (addr >= 0 && root < P->n_roots) v = sign * P->c[(size_t)root * np + addr];
+      }
+      out[2 * ((size_t)r * nA + g)] = creal(v);
+      out[2 * ((size_t)r * nA + g) + 1] = cimag(v);
+    }
+  }
+  return 0;
+}
+
 /* Size of Q per class by occupation-pattern counting (no determinants are
    built): class (h,p) with active strings of n_elec+h-p electrons whose
    pattern is at most two substitutions from an allowed pattern:

@@ -11,6 +11,10 @@ Functions and the passages they follow:
 * ``Oracle.couplings``     -- V_K = <K|H|Psi> and E0 - H_KK for listed K
 * ``Oracle.count_q``       -- size of Q per class (Sec. 2.3, Table 3)
 * ``Oracle.hmat``          -- generic <K|H|L> between two determinants
+* ``Oracle.dtable``        -- coupling tensors D^x_A = <A|x|Psi> of listed
+                              active strings by generic operator algebra
+                              (Sec. 2.4, Eq. sumsigma: the <K|E_pq|L> C_L
+                              factors restricted to the active space)
 
 Class id = 3 * (core holes) + (virtual particles); class 0 is the pure
 active rearrangement class that only a DAS partition has.
@@ -77,6 +81,7 @@ def _load():
         L.oracle_maxw.restype = C.c_int
         L.oracle_eri.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
         L.oracle_grad.argtypes = [C.c_void_p] + [C.c_void_p] * 6
+        L.oracle_dtable.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -210,6 +215,22 @@ class Oracle:
         gc = np.zeros((self.n_roots, self.n_p), np.complex128)
         self._L.oracle_grad(self._h_ptr, _ptr(E0), _ptr(seed), _ptr(gh), _ptr(gB), _ptr(gw), _ptr(gc))
         return gh, gB, gw, gc
+
+    FAMILIES = {"t": 0, "t+": 1, "tu": 2, "t+u+": 3, "t+u": 4}
+
+    def dtable(self, family, strings, root=0):
+        """D^x_A for the active strings A (active-local bitsets) of one family:
+        "t" <A|a_t|Psi>, "t+" <A|a+_t|Psi>, "tu" <A|a_u a_t|Psi> (t<u, row
+        u(u-1)/2 + t), "t+u+" <A|a+_t a+_u|Psi> (t<u, same rows), "t+u" row 0
+        c_A and row 1 + t n_act + u <A|a+_t a_u|Psi>.  Returns [rows, nA]
+        complex128."""
+        fam = self.FAMILIES[family]
+        na = self.prob.n_act
+        rows = na if fam <= 1 else na * (na - 1) // 2 if fam <= 3 else 1 + na * na
+        A = np.ascontiguousarray(strings, np.uint64)
+        out = np.zeros((rows, len(A)), np.complex128)
+        self._L.oracle_dtable(self._h_ptr, fam, int(root), len(A), _ptr(A), _ptr(out))
+        return out
 
     def count_q(self):
         out = np.zeros(NCLASS)

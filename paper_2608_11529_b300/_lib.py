@@ -99,6 +99,26 @@ def load():
         L.e2_profile_events.restype = C.c_int
         L.e2_fp64_peak.argtypes = [C.c_void_p, C.c_size_t, C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         L.e2_fp64_peak.restype = C.c_int
+        L.e2_query_status.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_uint32), C.c_void_p]
+        L.e2_query_status.restype = C.c_int
+        L.e2_coupling_tables.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p,
+                                         C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_int64)]
+        L.e2_coupling_tables.restype = C.c_int
+        L.e2_probe_couplings.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p,
+                                         C.c_int, C.c_int, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]
+        L.e2_probe_couplings.restype = C.c_int
+        L.e2_set_shard.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        L.e2_set_shard.restype = C.c_int
+        L.e2_shard_units.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                     C.POINTER(C.c_int64)]
+        L.e2_shard_units.restype = C.c_int
+        L.e2_shard_buffers.argtypes = [C.c_void_p, C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_int64),
+                                       C.POINTER(C.c_void_p), C.POINTER(C.c_int64)]
+        L.e2_shard_buffers.restype = C.c_int
+        L.e2_reduce.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.e2_reduce.restype = C.c_int
         L.e2_status_string.argtypes = [C.c_int]
         L.e2_status_string.restype = C.c_char_p
         _lib = L
@@ -263,6 +283,117 @@ class E2Problem:
             perm = self._ws[co:co + 4 * 64 * tiles].view(torch.int32)
         return part, int(rt.value), perm
 
+    def status(self, stream=None, workspace=None):
+        """Device status word of the last forward (or value_and_grad) on this
+        problem's workspace: (code, flags, min_abs_D [roots, 9]) with code the
+        e2_status it reports (0, E2_ERR_NONFINITE = 6 or E2_ERR_INTRUDER = 7),
+        flags its bits (1: non-finite energy, 2: intruder denominator) and
+        min_abs_D the smallest |E0 - H_KK| per root and class.  Synchronises."""
+        import torch
+        ws = self._ws if workspace is None else workspace
+        flags = C.c_uint32()
+        mind = np.zeros((self.n_roots, NCLASS))
+        dev = ws.device if ws is not None else torch.device("cuda", torch.cuda.current_device())
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        code = load().e2_query_status(self._h, C.c_void_p(ws.data_ptr()) if ws is not None else None, C.c_void_p(s),
+                                      C.byref(flags), mind.ctypes.data_as(C.c_void_p))
+        return int(code), int(flags.value), mind
+
+    FAMILIES = {"t": 0, "t+": 1, "tu": 2, "t+u+": 3, "t+u": 4}
+
+    def coupling_tables(self, family, h, B_c, c, B_x=None, w_x=None, lam=1.0, root=0, stream=None):
+        """One coupling-tensor family of root `root` (e2_coupling_tables):
+        returns (table [rows, n_A] complex128 CUDA, strings [n_A] int64 CUDA
+        holding the uint64 bitsets)."""
+        import torch
+        L = load()
+        fam = self.FAMILIES[family]
+        rows, nA = C.c_int64(), C.c_int64()
+        _check(L.e2_coupling_tables(self._h, None, None, 0, None, int(root), fam, None, None, C.byref(rows),
+                                    C.byref(nA)))
+        dev = c.device
+        tab = torch.empty(int(rows.value), int(nA.value), dtype=torch.complex128, device=dev)
+        strs = torch.empty(int(nA.value), dtype=torch.int64, device=dev)
+        if nA.value == 0:
+            return tab, strs
+        ws = self.workspace(dev)
+        inp = _Inputs(h.data_ptr(), B_c.data_ptr(), B_x.data_ptr() if self.L_extra else None,
+                      w_x.data_ptr() if self.L_extra else None, float(lam), c.data_ptr())
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        _check(L.e2_coupling_tables(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s), int(root), fam,
+                                    C.c_void_p(tab.data_ptr()), C.c_void_p(strs.data_ptr()), None, None))
+        return tab, strs
+
+    def probe_couplings(self, cls, h, B_c, c, B_x=None, w_x=None, lam=1.0, root=0, tile_m=0, tile_n=0,
+                        stream=None):
+        """V and D of one tile of a dense class (64 x 64) or of a whole gather
+        class ([rows, n_A]) from the class's FP64 kernel (e2_probe_couplings):
+        returns (V complex128 CUDA, D float64 CUDA)."""
+        import torch
+        L = load()
+        shape = (C.c_int64 * 2)()
+        _check(L.e2_probe_couplings(self._h, None, None, 0, None, int(root), int(cls), 0, 0, None, None, shape))
+        dev = c.device
+        V = torch.zeros((shape[0], shape[1]), dtype=torch.complex128, device=dev)
+        D = torch.zeros((shape[0], shape[1]), dtype=torch.float64, device=dev)
+        ws = self.workspace(dev)
+        inp = _Inputs(h.data_ptr(), B_c.data_ptr(), B_x.data_ptr() if self.L_extra else None,
+                      w_x.data_ptr() if self.L_extra else None, float(lam), c.data_ptr())
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        _check(L.e2_probe_couplings(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s), int(root),
+                                    int(cls), int(tile_m), int(tile_n), C.c_void_p(V.data_ptr()),
+                                    C.c_void_p(D.data_ptr()), None))
+        return V, D
+
+    def set_shard(self, rank, n_ranks):
+        """Take rank `rank`'s share of every class's units out of n_ranks
+        (e2_set_shard; (0, 1) = unsharded)."""
+        _check(load().e2_set_shard(self._h, int(rank), int(n_ranks)))
+
+    def shard_units(self, cls):
+        """(units of class cls, this rank's first, end)."""
+        u, a, b = C.c_int64(), C.c_int64(), C.c_int64()
+        _check(load().e2_shard_units(self._h, int(cls), C.byref(u), C.byref(a), C.byref(b)))
+        return int(u.value), int(a.value), int(b.value)
+
+    def shard_buffers(self):
+        """(partials float64 CUDA view, smallest-|D| keys int64 CUDA view) of
+        the workspace, for the ranks' collective."""
+        import torch
+        ws = self._ws
+        p, n, k, nk = C.c_void_p(), C.c_int64(), C.c_void_p(), C.c_int64()
+        _check(load().e2_shard_buffers(self._h, C.c_void_p(ws.data_ptr()), C.byref(p), C.byref(n), C.byref(k),
+                                       C.byref(nk)))
+        po, ko = p.value - ws.data_ptr(), k.value - ws.data_ptr()
+        return (ws[po:po + 8 * n.value].view(torch.float64), ws[ko:ko + 8 * nk.value].view(torch.int64))
+
+    def reduce(self, stream=None, out=None):
+        """E2, E2_class, E0 from the partials in the workspace (after the
+        ranks' sum): e2_reduce."""
+        import torch
+        dev = self._ws.device
+        if out is None:
+            out = (torch.empty(self.n_roots, dtype=torch.float64, device=dev),
+                   torch.empty(self.n_roots, NCLASS, dtype=torch.float64, device=dev),
+                   torch.empty(self.n_roots, dtype=torch.float64, device=dev))
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        _check(load().e2_reduce(self._h, C.c_void_p(self._ws.data_ptr()), self._ws.numel(), C.c_void_p(s),
+                                C.c_void_p(out[0].data_ptr()), C.c_void_p(out[1].data_ptr()),
+                                C.c_void_p(out[2].data_ptr())))
+        return out
+
+    def sharded_forward(self, dist, h, B_c, c, B_x=None, w_x=None, lam=1.0, group=None):
+        """E2 of the whole external space from this rank's share: e2_forward on
+        the shard, the partials summed and the |D| keys minimised over the
+        ranks of `group` (torch.distributed), then e2_reduce.  Bitwise equal
+        to the unsharded forward for any number of ranks."""
+        self.set_shard(dist.get_rank(group), dist.get_world_size(group))
+        self.forward(h, B_c, c, B_x=B_x, w_x=w_x, lam=lam)
+        part, keys = self.shard_buffers()
+        dist.all_reduce(part, op=dist.ReduceOp.SUM, group=group)
+        dist.all_reduce(keys, op=dist.ReduceOp.MIN, group=group)
+        return self.reduce()
+
     def class_tiles(self, cls):
         """(tiles, compacted rows, in use) of class cls's column tiles."""
         t, k, u = C.c_int64(), C.c_int64(), C.c_int()
@@ -290,6 +421,20 @@ class E2Problem:
         float elementwise kernel), -1 for the integral products of the setup,
         -2 for the products of the backward pass."""
         _check(load().e2_set_contraction(self._h, cls, 1 if sliced else 0))
+
+    SLICEABLE = (2, 5, 6, 7, 8, -1, -2)
+
+    def set_arithmetic(self, sliced):
+        """The whole path in FP64 (sliced=False, the library's default) or, where
+        the plan has it, in the emulated bf16-slice / float-float form
+        (sliced=True); the other parts stay FP64."""
+        for cls in self.SLICEABLE:
+            if not sliced or self.contraction(cls)[1]:
+                self.set_contraction(cls, bool(sliced))
+
+    def arithmetic(self):
+        """"fp64" when every part runs in FP64, else "sliced" (some part emulated)."""
+        return "sliced" if any(self.contraction(cls)[0] for cls in self.SLICEABLE) else "fp64"
 
     def contraction(self, cls):
         """(sliced in use, sliced available) for cls as in set_contraction."""

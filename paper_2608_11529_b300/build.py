@@ -22,13 +22,28 @@ def _stale():
 
 
 def build(force=False, verbose=False):
+    """Compile every source to an object in parallel (one nvcc per unit), then
+    link the shared library."""
     if not force and not _stale():
         return LIB
+    import concurrent.futures as cf
+    import tempfile
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [NVCC, *FLAGS, "-I", os.path.join(ROOT, "include"), "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.check_call(cmd)
+    inc = ["-I", os.path.join(ROOT, "include")]
+    compile_flags = [f for f in FLAGS if f not in ("-shared", "-cudart", "static")]
+    with tempfile.TemporaryDirectory() as td:
+        objs = [os.path.join(td, s.replace(".cu", ".o")) for s in SOURCES]
+        cmds = [[NVCC, *compile_flags, *inc, "-c", os.path.join(CSRC, s), "-o", o] for s, o in zip(SOURCES, objs)]
+        if verbose:
+            for c in cmds:
+                print(" ".join(c))
+        with cf.ThreadPoolExecutor(max_workers=min(len(cmds), os.cpu_count() or 1)) as ex:
+            for f in [ex.submit(subprocess.check_call, c) for c in cmds]:
+                f.result()
+        link = [NVCC, *FLAGS, "-o", tmp] + objs
+        if verbose:
+            print(" ".join(link))
+        subprocess.check_call(link)
     os.replace(tmp, LIB)
     return LIB
 

@@ -3,7 +3,7 @@
 // measurement hooks.  No device allocation.
 #include "e2_host.h"
 
-#include <mutex>
+#include <cstring>
 
 namespace e2 {
 
@@ -180,6 +180,8 @@ e2_status setup_common(e2_problem* P, const e2_inputs* in, unsigned char* ws, cu
   const e2_desc& d = P->d;
   const int n = P->n, nocc = P->nocc, Lt = d.L_coulomb + d.L_extra;
   Ctx X = ctx(P, ws);
+  // status word: no flags, every smallest |D| at the largest key
+  (k_status_init<<<1, 256, 0, st>>>(status_word(P, ws), 1 + d.n_roots * E2_NCLASS), ++g_launches);
   if (upload &&
       cudaMemcpyAsync(ws + P->o_plan, P->plan_blob.data(), P->plan_bytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
     return E2_ERR_CUDA;
@@ -201,7 +203,10 @@ e2_status setup_common(e2_problem* P, const e2_inputs* in, unsigned char* ws, cu
     (k_eA<<<blocks(L.n), 256, 0, st>>>(L, X.epsh, X.G, n, X.sp.a0), ++g_launches);
     (k_U<<<blocks((int64_t)(P->nx + 1) * L.n), 256, 0, st>>>(L, X.sp, X.G), ++g_launches);
     const HostList& H = P->lists[li];
-    if (H.df)
+    // float-float copies of e_A and U, read only by the sliced kernels
+    bool df_used = P->use_oz_adj && (int)li == P->list_of[8];
+    for (int c : {2, 5, 7, 6, 8}) df_used = df_used || (P->use_oz[c] && P->list_of[c] == (int)li);
+    if (H.df && df_used)
       (k_oz_tables<<<blocks((int64_t)(P->nx + 1) * L.n), 256, 0, st>>>(L.eA, L.U, L.n, P->nx + 1,
                                                                       (float2*)(ws + H.o_eAdf),
                                                                       (float2*)(ws + H.o_Udf)), ++g_launches);
@@ -347,7 +352,8 @@ void launch_reduce(e2_problem* P, unsigned char* ws, cudaStream_t st, double* E2
   (k_reduce<<<R * E2_NCLASS, 256, 0, st>>>((const double*)(ws + P->o_part), (const int64_t*)(ws + P->o_partoff),
                                            (const int64_t*)(ws + P->o_partcnt), (const double2*)(ws + P->o_g1),
                                            (int)(P->g_stride / 16), R, e2c), ++g_launches);
-  (k_finalize<<<1, 32, 0, st>>>(e2c, R, E2, (const double*)(ws + P->o_E0), E0), ++g_launches);
+  (k_finalize<<<1, 32, 0, st>>>(e2c, R, E2, (const double*)(ws + P->o_E0), E0, status_word(P, ws),
+                                P->d.level_shift_b), ++g_launches);
 }
 
 }  // namespace e2
@@ -365,6 +371,9 @@ const char* e2_status_string(e2_status s) {
     case E2_ERR_WORKSPACE: return "workspace too small or misaligned";
     case E2_ERR_CUDA: return "CUDA error";
     case E2_ERR_NONFINITE: return "non-finite value";
+    case E2_ERR_INTRUDER: return "intruder state: |E0 - H_KK| below 1e-12 Eh without a level shift";
+    case E2_ERR_OOM: return "out of host memory";
+    case E2_ERR_TIMEOUT: return "device wait timed out";
   }
   return "unknown status";
 }
@@ -389,6 +398,9 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
   DevList Lc[E2_NCLASS];
   for (int c = 0; c < E2_NCLASS; ++c) Lc[c] = dev_list(P, P->list_of[c], ws);
   double* part = (double*)(ws + P->o_part);
+  // with shards every rank writes only its own slots: the others stay 0, so
+  // that a sum of the ranks' partials over ranks is exactly the unsharded set
+  if (P->shard_n > 1) cudaMemsetAsync(part, 0, sizeof(double) * (size_t)part_total(P), st);
   for (int r = 0; r < R; ++r) {
     const double2* c = (const double2*)in->c + (int64_t)r * LP.n;
     Tabs T = tables(P, ws, r);
@@ -400,17 +412,21 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
       if (P->prof_on && r == 0) cudaEventRecord(P->prof[2 * cls + k], st);
     };
     for (int cls : {2, 5, 7, 4, 6}) {
-      if (P->part_cnt[cls] == 0) continue;
+      int64_t u0, u1;  // row tiles of this rank (all of them without shards)
+      shard_range(P, cls, u0, u1);
+      if (u1 <= u0) continue;
       const DevList& L = Lc[cls];
-      dim3 grid((unsigned)((P->M[cls] + 63) / 64), (unsigned)((L.n + 63) / 64));
+      dim3 grid((unsigned)(u1 - u0), (unsigned)((L.n + 63) / 64));
       mark(cls, 0);
       if (P->use_oz[cls])
         launch_class_oz(st, cls, oz_operands(P, ws, r, cls), P->M[cls], L.n, (const RowInfo*)(ws + P->o_rows[cls]),
-                        X.E0p + r, b, poff(cls));
+                        X.E0p + r, b, poff(cls), dmin_slot(P, ws, r, cls), u0, u1 - u0);
       else
         (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Dfor[cls], P->M[cls], L.n, P->Kp[cls],
                                            (const RowInfo*)(ws + P->o_rows[cls]), L.U, L.eA, X.E0p + r, b, poff(cls),
-                                           AdjOut{}, col_tiles(P, ws, r, cls)), ++g_launches);
+                                           AdjOut{}, col_tiles(P, ws, r, cls), dmin_slot(P, ws, r, cls),
+                                           (P->M[cls] + 63) / 64, u0),
+         ++g_launches);
       mark(cls, 1);
     }
     launch_sparse_classes(P, ws, st, r, c, mark);
@@ -418,9 +434,179 @@ e2_status e2_forward(e2_problem* P, const e2_inputs* in, void* workspace, size_t
   double* e2c = E2_class ? E2_class : (double*)(ws + P->o_e2c);
   (k_reduce<<<R * E2_NCLASS, 256, 0, st>>>(part, (const int64_t*)(ws + P->o_partoff), (const int64_t*)(ws + P->o_partcnt),
                                           (const double2*)(ws + P->o_g1), (int)(P->g_stride / 16), R, e2c), ++g_launches);
-  (k_finalize<<<1, 32, 0, st>>>(e2c, R, E2, X.E0d, E0), ++g_launches);
+  (k_finalize<<<1, 32, 0, st>>>(e2c, R, E2, X.E0d, E0, status_word(P, ws), b), ++g_launches);
   P->launches = g_launches;
   if (cudaGetLastError() != cudaSuccess) return E2_ERR_CUDA;
+  return E2_OK;
+}
+
+e2_status e2_coupling_tables(e2_problem* P, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                             void* stream_, int root, int family, double* table, uint64_t* strings, int64_t* rows,
+                             int64_t* n_A) {
+  if (!P || family < 0 || family > 4 || root < 0 || root >= P->d.n_roots) return E2_ERR_INVALID_ARG;
+  const int na = P->na;
+  const int cls_of[5] = {5, 7, 2, 6, 4};  // the class whose list each family's strings form
+  const int64_t nrow = family <= 1 ? na : family <= 3 ? (int64_t)na * (na - 1) / 2 : 1 + (int64_t)na * na;
+  const int li = P->list_of[cls_of[family]];
+  const int64_t n = li >= 0 ? P->lists[li].n : 0;
+  if (rows) *rows = nrow;
+  if (n_A) *n_A = n;
+  if (!table && !strings) return E2_OK;
+  if (!in || !in->h || !in->B_c || !in->c) return E2_ERR_INVALID_ARG;
+  if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < P->ws_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  if (n == 0) return E2_OK;
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  cudaGetLastError();
+  g_launches = 0;
+  if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
+  const DevList LP = dev_list(P, P->listP, ws);
+  const Tabs T = tables(P, ws, root);
+  build_tables(P, ws, st, (const double2*)in->c + (int64_t)root * LP.n, T, true);
+  const double2* src[5] = {T.DT, T.DTD, T.DTU, T.DTDUD, T.DTDU};
+  // rows beyond nrow are padding: the first nrow rows of [Kp][n] are contiguous
+  if (table && cudaMemcpyAsync(table, src[family], 16 * (size_t)nrow * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return E2_ERR_CUDA;
+  if (strings && cudaMemcpyAsync(strings, dev_list(P, li, ws).str, 8 * (size_t)n, cudaMemcpyDeviceToDevice, st) !=
+                     cudaSuccess)
+    return E2_ERR_CUDA;
+  return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
+}
+
+e2_status e2_probe_couplings(e2_problem* P, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                             void* stream_, int root, int cls, int64_t tile_m, int64_t tile_n, double* V, double* D,
+                             int64_t* shape) {
+  if (!P || root < 0 || root >= P->d.n_roots || cls < 0 || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
+  const bool dense = cls == 2 || cls == 5 || cls == 7 || cls == 4 || cls == 6;
+  const bool gather = cls == 0 || cls == 1 || cls == 3;
+  if ((!dense && !gather) || P->part_cnt[cls] == 0) return E2_ERR_UNSUPPORTED;
+  const int64_t nA = P->lists[P->list_of[cls]].n;
+  if (shape) {
+    shape[0] = dense ? 64 : (cls == 1 ? P->nvc : cls == 3 ? P->ncc : 1);
+    shape[1] = dense ? 64 : nA;
+  }
+  if (!V && !D) return E2_OK;
+  if (!in || !in->h || !in->B_c || !in->c || !V || !D) return E2_ERR_INVALID_ARG;
+  if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < P->ws_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  const DevList L = dev_list(P, P->list_of[cls], (unsigned char*)workspace);
+  const int64_t rt = (P->M[cls] + 63) / 64;
+  const int64_t nct = P->use_cols[cls] ? P->cplan[cls].tiles : (L.n + 63) / 64;
+  if (dense && (tile_m < 0 || tile_m >= rt || tile_n < 0 || tile_n >= nct)) return E2_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  cudaGetLastError();
+  g_launches = 0;
+  if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
+  setup_classes(P, ws, st);
+  const DevList LP = dev_list(P, P->listP, ws);
+  const double2* c = (const double2*)in->c + (int64_t)root * LP.n;
+  prepare_root(P, ws, st, c, root);
+  Ctx X = ctx(P, ws);
+  Tabs T = tables(P, ws, root);
+  const double b = P->d.level_shift_b;
+  double* part = (double*)(ws + P->o_part) + P->part_off[root * E2_NCLASS + cls];
+  if (dense) {
+    const double2* Dfor[E2_NCLASS] = {nullptr, nullptr, T.DTU, nullptr, T.DTDU, T.DT, T.DTDUD, T.DTD, nullptr};
+    cudaMemsetAsync(V, 0, 16 * 64 * 64, st);
+    cudaMemsetAsync(D, 0, 8 * 64 * 64, st);
+    AdjOut adj{};
+    adj.probeV = (double2*)V;
+    adj.probeD = D;
+    (k_class_probe<<<1, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Dfor[cls], P->M[cls], L.n, P->Kp[cls],
+                                      (const RowInfo*)(ws + P->o_rows[cls]), L.U, L.eA, X.E0p + root, b,
+                                      part + tile_n * rt + tile_m, adj, col_tiles(P, ws, root, cls), tile_m, tile_n,
+                                      nct),
+     ++g_launches);
+  } else {
+    DevList Lc[E2_NCLASS];
+    for (int k = 0; k < E2_NCLASS; ++k) Lc[k] = dev_list(P, P->list_of[k], ws);
+    if (cls == 1)
+      (k_class01<<<dim3(blocks(Lc[1].n), (unsigned)P->nvc), 256, 0, st>>>(
+           Lc[1], Lc[5], Lc[2], P->das, X.sp, X.binom, T.DT, T.DTU, (const double2*)(ws + P->o_X01), X.f, X.epsh,
+           X.E0p + root, b, part, nullptr, (double2*)V, D, 0),
+       ++g_launches);
+    else if (cls == 3)
+      (k_class10<<<dim3(blocks(Lc[3].n), (unsigned)P->ncc), 256, 0, st>>>(
+           Lc[3], Lc[7], Lc[5], P->das, X.sp, X.binom, T.DTD, T.DT, (const double2*)(ws + P->o_X10), X.f, X.epsh,
+           X.E0p + root, b, part, nullptr, (double2*)V, D, 0),
+       ++g_launches);
+    else
+      (k_class00<<<blocks(Lc[0].n), 256, 0, st>>>(Lc[0], Lc[4], Lc[2], P->das, X.sp, X.binom, T.DTDU, T.DTU,
+                                                  (const double2*)(ws + P->o_X00), X.f, X.E0p + root, b, part,
+                                                  nullptr, (double2*)V, D, 0),
+       ++g_launches);
+  }
+  return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
+}
+
+e2_status e2_set_shard(e2_problem* P, int rank, int n_ranks) {
+  if (!P || n_ranks < 1 || rank < 0 || rank >= n_ranks) return E2_ERR_INVALID_ARG;
+  P->shard_rank = rank;
+  P->shard_n = n_ranks;
+  return E2_OK;
+}
+
+e2_status e2_shard_units(const e2_problem* P, int cls, int64_t* units, int64_t* first, int64_t* end) {
+  if (!P || cls < 0 || cls >= E2_NCLASS) return E2_ERR_INVALID_ARG;
+  int64_t u0, u1;
+  shard_range(P, cls, u0, u1);
+  if (units) *units = shard_units(P, cls);
+  if (first) *first = u0;
+  if (end) *end = u1;
+  return E2_OK;
+}
+
+e2_status e2_shard_buffers(const e2_problem* P, void* workspace, double** partials, int64_t* n_partials,
+                           int64_t** min_keys, int64_t* n_keys) {
+  if (!P || !workspace) return E2_ERR_INVALID_ARG;
+  unsigned char* ws = (unsigned char*)workspace;
+  if (partials) *partials = (double*)(ws + P->o_part);
+  if (n_partials) *n_partials = part_total(P);
+  if (min_keys) *min_keys = (int64_t*)dmin_slot(P, ws, 0, 0);
+  if (n_keys) *n_keys = (int64_t)P->d.n_roots * E2_NCLASS;
+  return E2_OK;
+}
+
+e2_status e2_reduce(e2_problem* P, void* workspace, size_t workspace_bytes, void* stream_, double* E2,
+                    double* E2_class, double* E0) {
+  if (!P || !E2) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < P->ws_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  cudaGetLastError();
+  g_launches = 0;
+  cudaMemsetAsync(status_word(P, ws), 0, sizeof(unsigned long long), st);  // flags again from the summed partials
+  launch_reduce(P, ws, st, E2, E2_class, E0);
+  return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
+}
+
+e2_status e2_query_status(const e2_problem* P, const void* workspace, void* stream_, uint32_t* flags,
+                          double* min_abs_D) {
+  if (!P) return E2_ERR_INVALID_ARG;
+  const unsigned char* ws = (const unsigned char*)workspace;
+  if (!ws) {
+    ws = (const unsigned char*)noalloc_scratch();
+    if (!ws) return E2_ERR_CUDA;
+  }
+  const int R = P->d.n_roots;
+  std::vector<unsigned long long> h((size_t)1 + (size_t)R * E2_NCLASS);
+  cudaStream_t st = (cudaStream_t)stream_;
+  if (cudaMemcpyAsync(h.data(), ws + P->o_status, sizeof(unsigned long long) * h.size(), cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return E2_ERR_CUDA;
+  if (flags) *flags = (uint32_t)h[0];
+  if (min_abs_D)
+    for (int k = 0; k < R * E2_NCLASS; ++k) {
+      const unsigned long long key = h[1 + k];
+      double v;
+      std::memcpy(&v, &key, sizeof v);
+      min_abs_D[k] = key >= 0x7FF0000000000000ULL ? INFINITY : v;
+    }
+  if (h[0] & ST_NONFINITE) return E2_ERR_NONFINITE;
+  if (h[0] & ST_INTRUDER) return E2_ERR_INTRUDER;
   return E2_OK;
 }
 
@@ -473,7 +659,8 @@ e2_status e2_autotune(e2_problem* P, const e2_inputs* in, void* workspace, size_
       auto launch = [&] {
         k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[c]), Dfor[c], P->M[c], L.n, P->Kp[c],
                                            (const RowInfo*)(ws + P->o_rows[c]), L.U, L.eA, X.E0p, P->d.level_shift_b,
-                                           part + P->part_off[c], AdjOut{}, col_tiles(P, ws, 0, c));
+                                           part + P->part_off[c], AdjOut{}, col_tiles(P, ws, 0, c), nullptr,
+                                           (int64_t)grid.x, 0);
       };
       launch();
       cudaEventRecord(e0, st);
@@ -547,32 +734,27 @@ e2_status e2_fp64_peak(void* workspace, size_t workspace_bytes, void* stream_, d
 // Scratch for e2_forward_noalloc, compiled into the library: every device
 // that loads it holds these bytes until the process exits.  Nothing in the
 // forward layout needs to start at zero (every buffer is fully written before
-// it is read), so calls do not clear it; consecutive calls simply overwrite it.
+// it is read; the status word is cleared by the call itself), so calls do not
+// clear it; consecutive calls simply overwrite it.
 static __device__ __align__(256) unsigned char e2_static_scratch[E2_STATIC_SCRATCH_BYTES];
 
-namespace {
-std::mutex g_scratch_mu;
-void* g_scratch_ptr[128] = {};  // device address of e2_static_scratch, per device ordinal
-}  // namespace
+namespace e2 {
+// Device address of the scratch array on the current device.  Looked up on
+// every call, with that device current: the host-side symbol is only a
+// stand-in, and an address kept from an earlier context would not survive a
+// device reset.
+void* noalloc_scratch() {
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, e2_static_scratch) != cudaSuccess) return nullptr;
+  return ptr;
+}
+}  // namespace e2
 
 extern "C" e2_status e2_forward_noalloc(e2_problem* P, const e2_inputs* in, void* stream, double* E2,
                                         double* E2_class, double* E0) {
   if (!P) return E2_ERR_INVALID_ARG;
   if (P->ws_bytes > (size_t)E2_STATIC_SCRATCH_BYTES) return E2_ERR_WORKSPACE;  // before any GPU call
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return E2_ERR_CUDA;
-  void* ptr = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-      // once per device, with that device current: the host-side symbol is only
-      // a stand-in, the kernels need the array's device address
-      if (cudaGetSymbolAddress(&g_scratch_ptr[dev], e2_static_scratch) != cudaSuccess) {
-        g_scratch_ptr[dev] = nullptr;
-        return E2_ERR_CUDA;
-      }
-    }
-    ptr = g_scratch_ptr[dev];
-  }
+  void* ptr = noalloc_scratch();
+  if (!ptr) return E2_ERR_CUDA;
   return e2_forward(P, in, ptr, (size_t)E2_STATIC_SCRATCH_BYTES, stream, E2, E2_class, E0);
 }

@@ -13,7 +13,7 @@ e2_status e2_batch_create(e2_problem* const* jobs, int n_jobs, e2_batch** out) {
   *out = nullptr;
   if (!jobs || n_jobs < 1) return E2_ERR_INVALID_ARG;
   e2_batch* B = new (std::nothrow) e2_batch();
-  if (!B) return E2_ERR_INVALID_ARG;
+  if (!B) return E2_ERR_OOM;
   Layout ws;
   int64_t njc = 0;
   for (int j = 0; j < n_jobs; ++j) {
@@ -91,6 +91,7 @@ e2_status e2_batch_prepare(e2_batch* B, void* workspace, size_t workspace_bytes,
         g.b = P->d.level_shift_b;
         g.partial = (double*)(w + P->o_part) + P->part_off[r * E2_NCLASS + c];
         g.ct = col_tiles(P, w, r, c);
+        g.dmin = dmin_slot(P, w, r, c);
         // longest contraction first: the mean compacted length for a column-tiled class
         const int keff = P->use_cols[c] ? (int)(P->cplan[c].ratio * g.Kp + 0.5) : g.Kp;
         order.push_back({keff, (int)B->gj.size()});
@@ -124,6 +125,7 @@ e2_status e2_batch_forward(e2_batch* B, const e2_inputs* inputs, void* workspace
   if (!B || !inputs || !E2) return E2_ERR_INVALID_ARG;
   if (!workspace || workspace_bytes < B->bytes || workspace != B->prepared) return E2_ERR_WORKSPACE;
   for (size_t j = 0; j < B->jobs.size(); ++j) {
+    if (B->jobs[j]->shard_n > 1) return E2_ERR_UNSUPPORTED;  // batches run unsharded
     const e2_inputs* in = inputs + j;
     if (!E2[j] || !in->h || !in->B_c || !in->c || !std::isfinite(in->lambda)) return E2_ERR_INVALID_ARG;
     if (B->jobs[j]->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
@@ -161,7 +163,8 @@ e2_status e2_batch_forward(e2_batch* B, const e2_inputs* inputs, void* workspace
         for (int r = 0; r < P->d.n_roots; ++r)
           launch_class_oz(st, c, oz_operands(P, w, r, c), P->M[c], P->lists[P->list_of[c]].n,
                           (const RowInfo*)(w + P->o_rows[c]), (const double*)(w + P->o_E0p) + r,
-                          P->d.level_shift_b, (double*)(w + P->o_part) + P->part_off[r * E2_NCLASS + c]);
+                          P->d.level_shift_b, (double*)(w + P->o_part) + P->part_off[r * E2_NCLASS + c],
+                          dmin_slot(P, w, r, c));
     for (int r = 0; r < P->d.n_roots; ++r)
       launch_sparse_classes(P, w, st, r, (const double2*)inputs[j].c + (int64_t)r * P->lists[P->listP].n, nomark);
     launch_reduce(P, w, st, E2[j], E2_class ? E2_class[j] : nullptr, nullptr);

@@ -13,6 +13,14 @@ constexpr int kMaxKeys = 1 << 20;  // size of the pattern-key table
 constexpr int kBinomN = 65;        // binomial table is [65][65]
 constexpr int OZ_S = 5;            // slices per operand of the sliced bf16 contraction
 constexpr int OZ_ADJ_S = 4;        // slices of the adjoint's products (gradients: 2^-33 of the scales)
+// Slice exponent of a row or column that holds a NaN or an infinity: the
+// slices are then zero and the scale 2^(rexp + cexp) becomes NaN / infinite,
+// so the product and every energy formed from it are not finite.
+constexpr int OZ_NONFINITE = 1 << 20;
+// Device status word (workspace, see e2_query_status): flag bits, then the
+// smallest |D| per (root, class) as ordered integer keys.
+constexpr unsigned long long ST_NONFINITE = 1ULL, ST_INTRUDER = 2ULL;
+constexpr double kIntruderD = 1e-12;  // |D| below this with b = 0: an intruder state (Sec. 2.6)
 
 // Operands of the sliced (bf16) dense-class contraction: row slices of W
 // [OZ_S][Mpad][Kq] with one exponent per row, string slices of D
@@ -80,6 +88,11 @@ struct AdjOut {
   double* part;
   int64_t rt;
   int t_df;  // sliced adjoint only: T as float-float quadruples (its consumers slice them)
+  // forward mode only (T == nullptr): when set, the tile also writes each
+  // coupling's V and D at [local row][local column] (64 x 64), for a
+  // per-coupling check of one tile
+  double2* probeV;
+  double* probeD;
 };
 
 // Column tiles of a dense class with a compacted contraction.  The coupling
@@ -112,6 +125,7 @@ struct GemmJob {
   double b;
   double* partial;
   ColTiles ct;
+  unsigned long long* dmin;  // smallest |D| key of the class and root (status word)
 };
 
 struct WorkItem {

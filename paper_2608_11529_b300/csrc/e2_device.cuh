@@ -18,6 +18,29 @@ __device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
+// |x| as an ordered integer key: the bit pattern without its sign (for
+// non-negative doubles the integer order is the numeric order; NaN keys sit
+// above +inf, so they never lower a minimum).
+__device__ __forceinline__ unsigned long long dkey(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFULL;
+}
+// The same for a float (the high part of a float-float denominator).
+__device__ __forceinline__ unsigned fkey(float x) { return __float_as_uint(x) & 0x7FFFFFFFu; }
+
+// Smallest |D| key of the warp into *slot with one atomicMin per warp
+// (slot null: nothing).  Every lane of the warp must call it.
+__device__ __forceinline__ void dmin_flush(unsigned long long* slot, unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (slot && (threadIdx.x & 31) == 0 && v != ~0ULL) atomicMin(slot, v);
+}
+// A float key (fkey) converted to the double key of the same magnitude.
+__device__ __forceinline__ void dmin_flush_f(unsigned long long* slot, unsigned v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if (slot && (threadIdx.x & 31) == 0 && v != 0xFFFFFFFFu) atomicMin(slot, dkey((double)__uint_as_float(v)));
+}
+
 __device__ __forceinline__ int popc_below(uint64_t A, int t) {
   return __popcll(t ? (A & ((1ull << t) - 1)) : 0ull);
 }

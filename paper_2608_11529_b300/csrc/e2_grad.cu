@@ -20,6 +20,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
   if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
   if (!std::isfinite(in->lambda)) return E2_ERR_INVALID_ARG;
   if (!workspace || workspace_bytes < P->bwd_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  if (P->shard_n > 1) return E2_ERR_UNSUPPORTED;  // the adjoint runs unsharded
   cudaStream_t st = (cudaStream_t)stream_;
   unsigned char* ws = (unsigned char*)workspace;
   const e2_desc& d = P->d;
@@ -140,13 +141,14 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           if (!on[cls]) continue;
           if (P->use_oz[cls]) {
             launch_class_oz(st, cls, oz_operands(P, ws, r, cls), P->M[cls], Lc[cls].n,
-                            (const RowInfo*)(ws + P->o_rows[cls]), X.E0p + r, b, poff(cls));
+                            (const RowInfo*)(ws + P->o_rows[cls]), X.E0p + r, b, poff(cls), dmin_slot(P, ws, r, cls));
             continue;
           }
           dim3 grid((unsigned)((P->M[cls] + 63) / 64), (unsigned)((Lc[cls].n + 63) / 64));
           (k_class_gemm<<<grid, 256, 0, st>>>((const double2*)(ws + P->o_W[cls]), Df[cls], P->M[cls], Lc[cls].n,
                                               P->Kp[cls], (const RowInfo*)(ws + P->o_rows[cls]), Lc[cls].U, Lc[cls].eA,
-                                              X.E0p + r, b, poff(cls), AdjOut{}, col_tiles(P, ws, r, cls)), ++g_launches);
+                                              X.E0p + r, b, poff(cls), AdjOut{}, col_tiles(P, ws, r, cls),
+                                              dmin_slot(P, ws, r, cls), (int64_t)grid.x, 0), ++g_launches);
         }
       }
       continue;
@@ -184,7 +186,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       // that the energies equal e2_forward's bit for bit
       if (E2 && P->use_oz[cls])
         launch_class_oz(st, cls, oz_operands(P, ws, r, cls), M, N, (const RowInfo*)(ws + P->o_rows[cls]), X.E0p + r, b,
-                        poff(cls));
+                        poff(cls), dmin_slot(P, ws, r, cls));
       double* part_adj = P->use_oz[cls] ? nullptr : poff(cls);
       for (int64_t m0 = 0; m0 < M; m0 += P->chunk_rows[cls]) {
         const int64_t Mc = std::min<int64_t>(P->chunk_rows[cls], M - m0);
@@ -202,7 +204,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
                               X.E0p + r, b, adj);
         else
           (k_class_gemm<<<grid, 256, 0, st>>>(W, Dfor[cls], M, N, (int)Kp, (const RowInfo*)(ws + P->o_rows[cls]), L.U,
-                                              L.eA, X.E0p + r, b, nullptr, adj, col_tiles(P, ws, r, cls)),
+                                              L.eA, X.E0p + r, b, nullptr, adj, col_tiles(P, ws, r, cls),
+                                              dmin_slot(P, ws, r, cls), (int64_t)grid.x, 0),
            ++g_launches);
         // per-tile sums of this chunk: row sums of eta, column sums per row tile, the scalars
         {
@@ -267,7 +270,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       if (E2 && P->use_oz[8]) {
         const HostList& H8 = P->lists[P->list_of[8]];
         launch_class22_df(st, L, X.sp, (const float2*)(ws + H8.o_eAdf), (const float2*)(ws + H8.o_Udf), c,
-                          (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb, P->ncp, poff(8));
+                          (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb, P->ncp, poff(8),
+                          dmin_slot(P, ws, r, 8));
       }
       // chunks of core pairs: partials of one chunk, reduced before the next
       for (int z0 = 0; z0 < (int)P->ncp; z0 += P->z22_chunk) {

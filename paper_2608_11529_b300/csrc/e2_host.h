@@ -81,6 +81,8 @@ struct e2_problem {
   size_t ws_bytes;
   size_t o_plan, plan_bytes;
   size_t o_binom, o_EO, o_E0p, o_E0, o_G, o_epsh, o_dg, o_wt, o_Bo, o_f, o_cc, o_vc;
+  size_t o_status;  // device status word: flags + smallest |D| key per (root, class)
+  int shard_rank = 0, shard_n = 1;  // e2_set_shard: this rank's share of every class's units
   size_t o_rows[E2_NCLASS], o_W[E2_NCLASS];
   size_t o_G22, o_X01, o_X10, o_X00;
   size_t o_vaY, o_vaZ, o_vaX, va_cap;
@@ -177,16 +179,55 @@ Ctx ctx(const e2_problem* P, unsigned char* ws);
 unsigned char* slot_base(const e2_problem* P, unsigned char* ws, int r);
 Tabs tables(const e2_problem* P, unsigned char* ws, int r);
 ColTiles col_tiles(const e2_problem* P, unsigned char* ws, int r, int cls);
+// the status word (flags, then the smallest |D| key per root and class) and its slots
+// Partial slots of all roots and classes (contiguous from o_part).
+inline int64_t part_total(const e2_problem* P) {
+  int64_t t = 0;
+  for (int c = 0; c < E2_NCLASS; ++c) t += P->part_cnt[c];
+  return t * P->d.n_roots;
+}
+
+// Units of class cls that the forward can split across ranks: row tiles of a
+// dense class, (core pair, virtual block pair) units of (2,2), rows (virtual
+// a or core i) of (0,1) and (1,0), 256-string blocks of (0,0).
+inline int64_t shard_units(const e2_problem* P, int cls) {
+  if (P->part_cnt[cls] == 0) return 0;
+  switch (cls) {
+    case 2: case 4: case 5: case 6: case 7: return (P->M[cls] + 63) / 64;
+    case 8: return P->ncp * ((int64_t)P->nvb * (P->nvb + 1) / 2);
+    case 1: return P->nvc;
+    case 3: return P->ncc;
+    default: return (P->lists[P->list_of[0]].n + 255) / 256;
+  }
+}
+// This rank's contiguous share [u0, u1) of them (all of them without shards).
+inline void shard_range(const e2_problem* P, int cls, int64_t& u0, int64_t& u1) {
+  const int64_t n = shard_units(P, cls);
+  u0 = n * P->shard_rank / P->shard_n;
+  u1 = n * (P->shard_rank + 1) / P->shard_n;
+}
+
+// the device address of e2_forward_noalloc's static scratch on the current device (null on failure)
+void* noalloc_scratch();
+inline unsigned long long* status_word(const e2_problem* P, unsigned char* ws) {
+  return (unsigned long long*)(ws + P->o_status);
+}
+inline unsigned long long* dmin_slot(const e2_problem* P, unsigned char* ws, int r, int cls) {
+  return status_word(P, ws) + 1 + (int64_t)r * E2_NCLASS + cls;
+}
 // operands of the sliced contraction of class cls for root r
 OzOperands oz_operands(const e2_problem* P, unsigned char* ws, int r, int cls);
 // the sliced contraction with its Epstein-Nesbet epilogue; partial: one slot
 // per 64 x 64 tile, [column tile][row tile] (e2_ozaki.cu)
+// (row tiles tm0 .. tm0 + ntm - 1; ntm < 0: to the last)
 void launch_class_oz(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
-                     const double* E0p, double b, double* partial);
+                     const double* E0p, double b, double* partial, unsigned long long* dmin, int64_t tm0 = 0,
+                     int64_t ntm = -1);
 // class (2,2) in float-float (e2_ozaki.cu), the partials of k_class22
 void launch_class22_df(cudaStream_t st, const DevList& L, const DevSpace& sp, const float2* eAdf, const float2* Udf,
                        const double2* c, const double* g2, const double* epsh, const double* G, const double* E0p,
-                       double b, int nvb, int64_t ncp, double* partial);
+                       double b, int nvb, int64_t ncp, double* partial, unsigned long long* dmin, int64_t u0 = 0,
+                       int64_t u1 = -1);
 // float-float forms of per-row adjoint sums (e2_ozaki.cu): occupation sums of
 // eta given as float-float pairs, and the per-row sums of class (2,2)
 void launch_hocc_df(cudaStream_t st, const float2* H, const DevList& L, int na, int64_t rows, double* Hocc);
@@ -238,38 +279,50 @@ void launch_sparse_classes(e2_problem* P, unsigned char* ws, cudaStream_t st, in
   const double b = P->d.level_shift_b;
   double* part = (double*)(ws + P->o_part);
   auto poff = [&](int cls) { return part + P->part_off[r * E2_NCLASS + cls]; };
-  if (P->part_cnt[8] > 0) {
+  int64_t u0, u1;
+  shard_range(P, 8, u0, u1);
+  if (u1 > u0) {
     const DevList& L = Lc[8];
-    dim3 grid(blocks(L.n), (unsigned)(P->nvb * (P->nvb + 1) / 2), (unsigned)P->ncp);
     mark(8, 0);
     if (P->use_oz[8]) {  // float-float
       const HostList& H8 = P->lists[P->list_of[8]];
       launch_class22_df(st, L, X.sp, (const float2*)(ws + H8.o_eAdf), (const float2*)(ws + H8.o_Udf), c,
-                        (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb, P->ncp, poff(8));
+                        (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb, P->ncp, poff(8),
+                        dmin_slot(P, ws, r, 8), u0, u1);
     } else {
-      (k_class22<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, P->nvb,
-                                      poff(8)), ++g_launches);
+      // grid y: at most 65535 units per launch
+      for (int64_t a = u0; a < u1; a += 65535) {
+        dim3 grid(blocks(L.n), (unsigned)std::min<int64_t>(65535, u1 - a));
+        (k_class22<<<grid, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b,
+                                        P->nvb, poff(8), dmin_slot(P, ws, r, 8), a), ++g_launches);
+      }
     }
     mark(8, 1);
   }
-  if (P->part_cnt[1] > 0) {
-    dim3 grid(blocks(Lc[1].n), (unsigned)P->nvc);
+  shard_range(P, 1, u0, u1);
+  if (u1 > u0) {
+    dim3 grid(blocks(Lc[1].n), (unsigned)(u1 - u0));
     mark(1, 0);
     (k_class01<<<grid, 256, 0, st>>>(Lc[1], Lc[5], Lc[2], P->das, X.sp, X.binom, T.DT, T.DTU,
-                                    (const double2*)(ws + P->o_X01), X.f, X.epsh, X.E0p + r, b, poff(1)), ++g_launches);
+                                    (const double2*)(ws + P->o_X01), X.f, X.epsh, X.E0p + r, b, poff(1),
+                                    dmin_slot(P, ws, r, 1), nullptr, nullptr, u0), ++g_launches);
     mark(1, 1);
   }
-  if (P->part_cnt[3] > 0) {
-    dim3 grid(blocks(Lc[3].n), (unsigned)P->ncc);
+  shard_range(P, 3, u0, u1);
+  if (u1 > u0) {
+    dim3 grid(blocks(Lc[3].n), (unsigned)(u1 - u0));
     mark(3, 0);
     (k_class10<<<grid, 256, 0, st>>>(Lc[3], Lc[7], Lc[5], P->das, X.sp, X.binom, T.DTD, T.DT,
-                                    (const double2*)(ws + P->o_X10), X.f, X.epsh, X.E0p + r, b, poff(3)), ++g_launches);
+                                    (const double2*)(ws + P->o_X10), X.f, X.epsh, X.E0p + r, b, poff(3),
+                                    dmin_slot(P, ws, r, 3), nullptr, nullptr, u0), ++g_launches);
     mark(3, 1);
   }
-  if (P->part_cnt[0] > 0) {
+  shard_range(P, 0, u0, u1);
+  if (u1 > u0) {
     mark(0, 0);
-    (k_class00<<<blocks(Lc[0].n), 256, 0, st>>>(Lc[0], Lc[4], Lc[2], P->das, X.sp, X.binom, T.DTDU, T.DTU,
-                                               (const double2*)(ws + P->o_X00), X.f, X.E0p + r, b, poff(0)), ++g_launches);
+    (k_class00<<<(unsigned)(u1 - u0), 256, 0, st>>>(Lc[0], Lc[4], Lc[2], P->das, X.sp, X.binom, T.DTDU, T.DTU,
+                                                   (const double2*)(ws + P->o_X00), X.f, X.E0p + r, b, poff(0),
+                                                   dmin_slot(P, ws, r, 0), nullptr, nullptr, u0), ++g_launches);
     mark(0, 1);
   }
 }

@@ -487,7 +487,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
                                            const double* __restrict__ U, const double* __restrict__ eA,
                                            const double* __restrict__ E0p, double b, double* __restrict__ partial_slot,
                                            const AdjOut& adj, int64_t tile_m, int64_t tile_n, int64_t n_tile_n,
-                                           const ColTiles& ctl) {
+                                           const ColTiles& ctl, unsigned long long* dmin) {
   __shared__ double sWr[GBM][GBK + 1], sWi[GBM][GBK + 1], sWs[GBM][GBK + 1];
   __shared__ double sDr[GBK][GBN + 1], sDi[GBK][GBN + 1], sDs[GBK][GBN + 1];
   __shared__ double sh[32];
@@ -606,6 +606,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
   const int64_t mend = adj.T ? adj.m_base + adj.Mc : M;
   double acc = 0.0, acc2 = 0.0;
   const double inv_n = adj.T ? 1.0 / adj.g1[0].x : 0.0, s2n = 2.0 * adj.s * inv_n;
+  unsigned long long dm = ~0ULL;                                // smallest |D| key of the thread
   double rowp[2][2] = {{0.0, 0.0}, {0.0, 0.0}};                 // adjoint: per-row sums of df/dD
   double colp[2][2] = {{0.0, 0.0}, {0.0, 0.0}};                 // adjoint: per-column sums of df/dD
 #pragma unroll
@@ -630,6 +631,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
           const int kk = ni * 2 + hc;
           Dv[kk] = col >= 0 ? base - eA[col] - U1[col] - U2[col] + U3[col] + U4[col] : 1.0;
           q[kk] = col >= 0 ? en_q(Dv[kk], b) : 1.0;
+          if (col >= 0) dm = min(dm, dkey(Dv[kk]));
         }
       rcp4(q, rq);
 #pragma unroll
@@ -645,6 +647,11 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
           const double v2 = fma(vr, vr, vi * vi);
           if (!adj.T) {
             acc = fma(v2, en_g_r(Dk, b, rq[kk]), acc);  // the E2 term, same rounding in both passes
+            if (adj.probeV) {
+              const int lr = wm * 32 + mi * 16 + g + hr * 8, lc = wn * 16 + ni * 8 + 2 * tq + hc;
+              adj.probeV[lr * GBN + lc] = make_double2(vr, vi);
+              adj.probeD[lr * GBN + lc] = Dk;
+            }
           } else {
             double gk, hk;
             en_derivs_r(v2 * inv_n, Dk, b, rq[kk], gk, hk);
@@ -659,6 +666,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
           }
         }
     }
+  dmin_flush(dmin, dm);
   if (adj.T) {
     // fixed-order per-row / per-column sums over the tile (16 contributors each)
     __shared__ double sRow[GBM][16], sColP[GBN][16];
@@ -718,9 +726,22 @@ __global__ void k_dcompact(const double2* __restrict__ D, int64_t N, ColTiles ct
 __global__ void __launch_bounds__(256, 1)
 k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M, int64_t N, int Kp,
              const RowInfo* __restrict__ rows, const double* __restrict__ U, const double* __restrict__ eA,
-             const double* __restrict__ E0p, double b, double* __restrict__ partial, AdjOut adj, ColTiles ctl) {
-  double* slot = partial ? partial + (int64_t)blockIdx.y * gridDim.x + blockIdx.x : nullptr;
-  class_tile(W, D, M, N, Kp, rows, U, eA, E0p, b, slot, adj, blockIdx.x, blockIdx.y, gridDim.y, ctl);
+             const double* __restrict__ E0p, double b, double* __restrict__ partial, AdjOut adj, ColTiles ctl,
+             unsigned long long* dmin, int64_t rt, int64_t tm0) {
+  // grid x: row tiles tm0 .. tm0 + gridDim.x - 1 of the rt the class has (a shard, or all)
+  const int64_t tm = tm0 + blockIdx.x;
+  double* slot = partial ? partial + (int64_t)blockIdx.y * rt + tm : nullptr;
+  class_tile(W, D, M, N, Kp, rows, U, eA, E0p, b, slot, adj, tm, blockIdx.y, gridDim.y, ctl, dmin);
+}
+
+// One tile (tile_m, tile_n) of the class kernel with its per-coupling probe
+// outputs set (adj.probeV / probeD): the same device code as k_class_gemm.
+__global__ void __launch_bounds__(256, 1)
+k_class_probe(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M, int64_t N, int Kp,
+              const RowInfo* __restrict__ rows, const double* __restrict__ U, const double* __restrict__ eA,
+              const double* __restrict__ E0p, double b, double* __restrict__ partial, AdjOut adj, ColTiles ctl,
+              int64_t tile_m, int64_t tile_n, int64_t n_tile_n) {
+  class_tile(W, D, M, N, Kp, rows, U, eA, E0p, b, partial, adj, tile_m, tile_n, n_tile_n, ctl, nullptr);
 }
 
 // Persistent form: one CTA per SM takes tiles of every (job, class, root) of a
@@ -742,7 +763,8 @@ k_batch_gemm(const GemmJob* __restrict__ jobs, const WorkItem* __restrict__ item
     const GemmJob j = jobs[w.job];
     const int64_t ntm = (j.M + GBM - 1) / GBM;
     class_tile(j.W, j.D, j.M, j.N, j.Kp, j.rows, j.U, j.eA, j.E0p, j.b,
-               j.partial + (int64_t)w.tile_n * ntm + w.tile_m, none, w.tile_m, w.tile_n, (j.N + GBN - 1) / GBN, j.ct);
+               j.partial + (int64_t)w.tile_n * ntm + w.tile_m, none, w.tile_m, w.tile_n, (j.N + GBN - 1) / GBN, j.ct,
+               j.dmin);
   }
 }
 
@@ -756,18 +778,22 @@ k_batch_gemm(const GemmJob* __restrict__ jobs, const WorkItem* __restrict__ item
 __global__ void __launch_bounds__(256)
 k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* __restrict__ g2 /*[ncp][nvp]*/,
           const double* __restrict__ epsh, const double* __restrict__ G, const double* __restrict__ E0p, double b,
-          int nvb, double* __restrict__ partial) {
+          int nvb, double* __restrict__ partial, unsigned long long* dmin, int64_t u0) {
   __shared__ double sGab[8][8], sG2[8][8], sAl[2][8];
   __shared__ double sh[32];
+  // grid y: units u0 + blockIdx.y of (core pair z, virtual block pair y), u = z nyb + y
+  const int64_t nyb = (int64_t)nvb * (nvb + 1) / 2;
+  const int64_t u = u0 + blockIdx.y;
+  const int zp = (int)(u / nyb);
   int ba = 0, bb = 0;
   {
-    int yb = blockIdx.y, k = 0;
+    int yb = (int)(u % nyb), k = 0;
     while (yb >= nvb - k) { yb -= nvb - k; ++k; }
     ba = k;
     bb = k + yb;
   }
   int iu, ju;
-  pair_decode(blockIdx.z, iu, ju);
+  pair_decode(zp, iu, ju);
   const int gi = sp.cc[iu], gj = sp.cc[ju];
   const int64_t nvp = pairs(sp.nvc);
   const int tid = threadIdx.x;
@@ -776,7 +802,7 @@ k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* 
     int a = ba * 8 + x, bq = bb * 8 + y;
     bool ok = a < sp.nvc && bq < sp.nvc && a < bq;
     sGab[x][y] = ok ? G[(int64_t)sp.vc[a] * sp.n + sp.vc[bq]] : 0.0;
-    sG2[x][y] = ok ? g2[(int64_t)blockIdx.z * nvp + pair_index(a, bq)] : 0.0;
+    sG2[x][y] = ok ? g2[(int64_t)zp * nvp + pair_index(a, bq)] : 0.0;
   } else if (tid < 80) {
     int k = tid - 64, side = k >> 3, x = k & 7;
     int a = (side ? bb : ba) * 8 + x;
@@ -790,6 +816,7 @@ k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* 
   __syncthreads();
   const int64_t A = blockIdx.x * (int64_t)blockDim.x + tid;
   double acc = 0.0;
+  unsigned long long dm = ~0ULL;
   if (A < Ls.n) {
     const double chi_ij = -epsh[gi] - epsh[gj] + G[(int64_t)gi * sp.n + gj];
     const double ct = *E0p - Ls.eA[A] + Ls.U[(int64_t)iu * Ls.n + A] + Ls.U[(int64_t)ju * Ls.n + A] - chi_ij;
@@ -811,6 +838,7 @@ k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* 
         for (int k = 0; k < 4; ++k) {
           Dv[k] = cx - pb[y0 + k] - sGab[x][y0 + k];
           q[k] = sG2[x][y0 + k] != 0.0 ? en_q(Dv[k], b) : 1.0;
+          if (sG2[x][y0 + k] != 0.0) dm = min(dm, dkey(Dv[k]));  // the couplings the sum takes
         }
         rcp4(q, rq);
 #pragma unroll
@@ -823,8 +851,9 @@ k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* 
     double2 cv = c[A];
     acc = fma(cv.x, cv.x, cv.y * cv.y) * inner;
   }
+  dmin_flush(dmin, dm);
   double tot = block_sum(acc, sh);
-  if (tid == 0) partial[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = tot;
+  if (tid == 0) partial[u * gridDim.x + blockIdx.x] = tot;
 }
 
 // ------------------------------------------------------------------ gather classes
@@ -833,12 +862,14 @@ k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* 
 __global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
                           const double2* __restrict__ DT /*[KpT][n12]*/, const double2* __restrict__ DTU /*[KpTU][n02]*/,
                           const double2* __restrict__ X01, const double2* __restrict__ f, const double* __restrict__ epsh,
-                          const double* __restrict__ E0p, double b, double* __restrict__ partial) {
+                          const double* __restrict__ E0p, double b, double* __restrict__ partial, unsigned long long* dmin,
+                          double2* __restrict__ probeV, double* __restrict__ probeD, int64_t u0) {
   __shared__ double sh[32];
-  const int a = blockIdx.y;
+  const int a = (int)(u0 + blockIdx.y);  // grid y: virtuals u0 .. (a shard, or all)
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int na = sp.n_act, ntp = (int)pairs(na);
   double acc = 0.0;
+  unsigned long long dm = ~0ULL;
   if (g < L01.n) {
     const uint64_t A = L01.str[g];
     const int ga = sp.vc[a];
@@ -867,21 +898,29 @@ __global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, Dev
     }
     const double Dk = *E0p - L01.eA[g] - epsh[ga] - L01.U[(int64_t)(sp.ncc + a) * L01.n + g];
     acc = fma(V.x, V.x, V.y * V.y) * en_g(Dk, b);
+    dm = dkey(Dk);
+    if (probeV) {  // per-coupling check: row (blockIdx.y) x string
+      probeV[(int64_t)a * L01.n + g] = V;
+      probeD[(int64_t)a * L01.n + g] = Dk;
+    }
   }
+  dmin_flush(dmin, dm);
   double tot = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  if (threadIdx.x == 0) partial[(int64_t)a * gridDim.x + blockIdx.x] = tot;
 }
 
 // (1,0): V[i,A] = sum_t f_ti D^{t+}_A + sum_{t<u in A} s(A;t,u) sum_v <tu||iv> D^v_{A-t-u}
 __global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
                           const double2* __restrict__ DTD /*[Kp][n21]*/, const double2* __restrict__ DT /*[Kp][n12]*/,
                           const double2* __restrict__ X10, const double2* __restrict__ f, const double* __restrict__ epsh,
-                          const double* __restrict__ E0p, double b, double* __restrict__ partial) {
+                          const double* __restrict__ E0p, double b, double* __restrict__ partial, unsigned long long* dmin,
+                          double2* __restrict__ probeV, double* __restrict__ probeD, int64_t u0) {
   __shared__ double sh[32];
-  const int i = blockIdx.y;
+  const int i = (int)(u0 + blockIdx.y);  // grid y: core spinors u0 .. (a shard, or all)
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int na = sp.n_act;
   double acc = 0.0;
+  unsigned long long dm = ~0ULL;
   if (g < L10.n) {
     const uint64_t A = L10.str[g];
     const int gi = sp.cc[i];
@@ -909,26 +948,41 @@ __global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, Dev
     }
     const double Dk = *E0p - L10.eA[g] + epsh[gi] + L10.U[(int64_t)i * L10.n + g];
     acc = fma(V.x, V.x, V.y * V.y) * en_g(Dk, b);
+    dm = dkey(Dk);
+    if (probeV) {  // per-coupling check: row (blockIdx.y) x string
+      probeV[(int64_t)i * L10.n + g] = V;
+      probeD[(int64_t)i * L10.n + g] = Dk;
+    }
   }
+  dmin_flush(dmin, dm);
   double tot = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = tot;
+  if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = tot;
 }
 
 // (0,0), DAS only: V[A] = <A|H - E_O|Psi> for A of a non-reference pattern
 __global__ void k_class00(DevList L00, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
                           const double2* __restrict__ DTDU /*[Kp][n11]*/, const double2* __restrict__ DTU /*[Kp][n02]*/,
                           const double2* __restrict__ X00, const double2* __restrict__ f, const double* __restrict__ E0p,
-                          double b, double* __restrict__ partial) {
+                          double b, double* __restrict__ partial, unsigned long long* dmin,
+                          double2* __restrict__ probeV, double* __restrict__ probeD, int64_t u0) {
   __shared__ double sh[32];
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t blk = u0 + blockIdx.x;  // grid x: string blocks u0 .. (a shard, or all)
+  const int64_t g = blk * (int64_t)blockDim.x + threadIdx.x;
   double acc = 0.0;
+  unsigned long long dm = ~0ULL;
   if (g < L00.n) {
     const double2 V = active_sigma(L00.str[g], L11, L02, das, sp, binom, DTDU, DTU, X00, f);
     const double Dk = *E0p - L00.eA[g];
     acc = fma(V.x, V.x, V.y * V.y) * en_g(Dk, b);
+    dm = dkey(Dk);
+    if (probeV) {  // per-coupling check: row (blockIdx.y) x string
+      probeV[g] = V;
+      probeD[g] = Dk;
+    }
   }
+  dmin_flush(dmin, dm);
   double tot = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+  if (threadIdx.x == 0) partial[blk] = tot;
 }
 
 // ------------------------------------------------------------------ reference solver
@@ -1023,14 +1077,37 @@ __global__ void k_reduce(const double* __restrict__ partial, const int64_t* __re
   if (threadIdx.x == 0) e2c[root * E2_NCLASS + cls] = tot / g1_all[(int64_t)root * g1_stride].x;
 }
 
+// Status word before a pass: no flags; every smallest-|D| key at the largest
+// non-negative int64 (keys stay ordered as signed integers, so ranks can take
+// their minimum with a signed reduction).
+__global__ void k_status_init(unsigned long long* status, int n) {
+  for (int k = threadIdx.x; k < n; k += blockDim.x) status[k] = k ? 0x7FFFFFFFFFFFFFFFULL : 0ULL;
+}
+
+// E2 of each root from its class sums, and the device-detected conditions
+// into the status word (status[0] flags, status[1 + 9 r + cls] the smallest
+// |D| key of the class): a non-finite energy sets ST_NONFINITE; with b = 0 a
+// denominator below kIntruderD sets ST_INTRUDER (an intruder state, Sec. 2.6).
 __global__ void k_finalize(const double* __restrict__ e2c, int n_roots, double* __restrict__ E2,
-                           const double* __restrict__ E0in, double* __restrict__ E0out) {
+                           const double* __restrict__ E0in, double* __restrict__ E0out,
+                           unsigned long long* __restrict__ status, double b) {
   int r = threadIdx.x;
   if (r >= n_roots) return;
   double s = 0.0;
-  for (int k = 0; k < E2_NCLASS; ++k) s += e2c[r * E2_NCLASS + k];
+  bool bad = false;
+  for (int k = 0; k < E2_NCLASS; ++k) {
+    const double v = e2c[r * E2_NCLASS + k];
+    bad = bad || !isfinite(v);
+    s += v;
+  }
   E2[r] = s;
   if (E0out) E0out[r] = E0in[r];
+  if (!status) return;
+  unsigned long long f = (bad || !isfinite(s)) ? ST_NONFINITE : 0ULL;
+  if (b == 0.0)
+    for (int k = 0; k < E2_NCLASS; ++k)
+      if (status[1 + r * E2_NCLASS + k] < dkey(kIntruderD)) f |= ST_INTRUDER;
+  if (f) atomicOr(status, f);
 }
 
 }  // namespace e2

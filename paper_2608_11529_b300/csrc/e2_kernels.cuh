@@ -29,20 +29,30 @@ __global__ void k_gram(const double2* Da, const double2* Db, int64_t n, int ny, 
 __global__ void k_e0(const double2* g1, const double2* g2, const double2* f, const double2* X00, DevSpace sp, int ntp,
                      const double* EO, double* E0p, double* E0);
 __global__ void k_class_gemm(const double2* W, const double2* D, int64_t M, int64_t N, int Kp, const RowInfo* rows,
-                             const double* U, const double* eA, const double* E0p, double b, double* partial, AdjOut adj, ColTiles ctl);
+                             const double* U, const double* eA, const double* E0p, double b, double* partial, AdjOut adj, ColTiles ctl,
+                             unsigned long long* dmin, int64_t rt, int64_t tm0);
 __global__ void k_dcompact(const double2* D, int64_t N, ColTiles ctl, double2* Dc);
+__global__ void k_class_probe(const double2* W, const double2* D, int64_t M, int64_t N, int Kp, const RowInfo* rows,
+                              const double* U, const double* eA, const double* E0p, double b, double* partial,
+                              AdjOut adj, ColTiles ctl, int64_t tile_m, int64_t tile_n, int64_t n_tile_n);
 __global__ void k_batch_gemm(const GemmJob* jobs, const WorkItem* items, int n_items, int* counter);
 __global__ void k_class22(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
-                          const double* G, const double* E0p, double b, int nvb, double* partial);
+                          const double* G, const double* E0p, double b, int nvb, double* partial,
+                          unsigned long long* dmin, int64_t u0);
 __global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, DevSpace sp, const int64_t* binom,
                           const double2* DT, const double2* DTU, const double2* X01, const double2* f,
-                          const double* epsh, const double* E0p, double b, double* partial);
+                          const double* epsh, const double* E0p, double b, double* partial,
+                          unsigned long long* dmin, double2* probeV,
+                          double* probeD, int64_t u0);
 __global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, DevSpace sp, const int64_t* binom,
                           const double2* DTD, const double2* DT, const double2* X10, const double2* f,
-                          const double* epsh, const double* E0p, double b, double* partial);
+                          const double* epsh, const double* E0p, double b, double* partial,
+                          unsigned long long* dmin, double2* probeV,
+                          double* probeD, int64_t u0);
 __global__ void k_class00(DevList L00, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* binom,
                           const double2* DTDU, const double2* DTU, const double2* X00, const double2* f,
-                          const double* E0p, double b, double* partial);
+                          const double* E0p, double b, double* partial, unsigned long long* dmin, double2* probeV,
+                          double* probeD, int64_t u0);
 __global__ void k_sigma(DevList LP, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* binom,
                         const double2* DTDU, const double2* DTU, const double2* X00, const double2* f, double2* sigma);
 __global__ void k_lincomb(const double2* V, int m, int64_t n, const double2* Y, int k, int acc, double2* out);
@@ -52,7 +62,9 @@ __global__ void k_peak_dmma(double* out, int iters);
 __global__ void k_peak_dfma(double* out, int iters);
 __global__ void k_reduce(const double* partial, const int64_t* off, const int64_t* cnt, const double2* g1_all,
                          int g1_stride, int n_roots, double* e2c);
-__global__ void k_finalize(const double* e2c, int n_roots, double* E2, const double* E0in, double* E0out);
+__global__ void k_status_init(unsigned long long* status, int n);
+__global__ void k_finalize(const double* e2c, int n_roots, double* E2, const double* E0in, double* E0out,
+                           unsigned long long* status, double b);
 
 // sliced bf16 contraction (e2_ozaki.cu)
 __global__ void k_c2df(const double2* c, int64_t n, const double2* g1, float2* out);

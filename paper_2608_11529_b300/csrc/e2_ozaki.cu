@@ -30,11 +30,29 @@
 // the level-shifted D^3/(D^4 + b^2), and the tile's sum of |V|^2 g(D).
 #include <cuda_bf16.h>
 
+#include <mutex>
+
 #include "e2_device.cuh"
 #include "e2_df.cuh"
 #include "e2_host.h"
 
 namespace e2 {
+
+// Once-per-device set-up (kernel attributes are per device): true on the
+// first call for the current device, under a lock.
+struct DeviceFlags {
+  std::mutex mu;
+  bool done[128] = {};
+};
+static bool first_use_on_device(DeviceFlags& f) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return true;
+  std::lock_guard<std::mutex> lock(f.mu);
+  if (f.done[dev]) return false;
+  f.done[dev] = true;
+  return true;
+}
+static DeviceFlags g_oz_attr;
 
 namespace {
 
@@ -67,6 +85,7 @@ __device__ __forceinline__ void oz_digits(double x, int e, bool neg, float (&s)[
 // exponent e with |x| < 2^e from the largest magnitude's bit pattern (0 for 0)
 __device__ __forceinline__ int oz_exp(unsigned long long maxbits) {
   const int ex = (int)(maxbits >> 52);
+  if (ex >= 0x7FF) return OZ_NONFINITE;  // a NaN or an infinity in the row / column
   return ex ? ex - 1022 : 0;
 }
 __device__ __forceinline__ unsigned long long oz_mag(double x) {
@@ -104,8 +123,10 @@ __device__ __forceinline__ void oz_digits_df(float hi, float lo, int e, bool neg
   s[0] = (float)(int)N;
 }
 
-// 2^k as a float, k clamped to the normal range
+// 2^k as a float, k clamped to the normal range; NaN for a scale that
+// carries OZ_NONFINITE (a non-finite operand)
 __device__ __forceinline__ float oz_pow2(int k) {
+  if (k > OZ_NONFINITE / 2) return __int_as_float(0x7FC00000);
   k = max(-126, min(127, k));
   return __int_as_float((127 + k) << 23);
 }
@@ -163,7 +184,7 @@ __global__ void k_oz_slice_a(const void* __restrict__ Av, int64_t sam, int64_t s
       }
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     const int ex = (int)(m >> 23);
-    e = ex ? ex - 126 : 0;
+    e = ex >= 0xFF ? OZ_NONFINITE : ex ? ex - 126 : 0;
   } else {
     unsigned long long m = 0;
     if (row < M)
@@ -501,11 +522,13 @@ __device__ __forceinline__ void oz_adjoint_phase2(const OzOperands& op, int64_t 
 template <int NS, int NH, bool ADJ>
 __global__ void __launch_bounds__(256, 1)
 k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows, const double* __restrict__ E0p,
-           double b, double* __restrict__ partial, AdjOut adj) {
+           double b, double* __restrict__ partial, AdjOut adj, unsigned long long* dmin) {
   extern __shared__ __align__(16) unsigned char oz_smem[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp >> 2, wn = warp & 3, g = lane >> 2, t = lane & 3;
-  const int64_t m0 = (ADJ ? adj.m_base : 0) + (int64_t)blockIdx.x * OZ_BM, n0 = (int64_t)blockIdx.y * 64;
+  // rows from adj.m_base: the adjoint's chunk, or in the forward the first row
+  // tile of a shard (0 for all rows)
+  const int64_t m0 = adj.m_base + (int64_t)blockIdx.x * OZ_BM, n0 = (int64_t)blockIdx.y * 64;
   if (ADJ) M = min(M, adj.m_base + adj.Mc);  // the chunk's last row
   const int Kq = op.Kq;
   auto sA = [&](int st, int s, int r, int k) {
@@ -634,6 +657,7 @@ k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows
   const bool shifted = b != 0.0;
   const dfl bb = df_from_double(b * b);  // once per thread
   float shi[8], serr[8];  // per slot: hi parts by two_sum, their errors beside
+  unsigned dmk = 0xFFFFFFFFu;  // smallest |D| (high part) key of the thread
 #pragma unroll
   for (int k = 0; k < 8; ++k) shi[k] = serr[k] = 0.0f;
 #pragma unroll
@@ -676,6 +700,7 @@ k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows
           const float2 u = op.Udf[(int64_t)ri.w * N + col];
           Dk = df_add(Dk, dfl{u.x, u.y});
         }
+        dmk = min(dmk, fkey(Dk.hi));
         dfl gk;
         if (!shifted) {
           gk = df_rcp(Dk);
@@ -690,6 +715,7 @@ k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows
       }
     }
   }
+  dmin_flush_f(dmin, dmk);
   dfl tsum = fast_two_sum(shi[0], serr[0]);
 #pragma unroll
   for (int k = 1; k < 8; ++k) tsum = df_add(tsum, fast_two_sum(shi[k], serr[k]));
@@ -706,7 +732,7 @@ k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows
   if (tid == 0 && partial) {
     dfl tot{sW[0].x, sW[0].y};
     for (int w = 1; w < 8; ++w) tot = df_add(tot, dfl{sW[w].x, sW[w].y});
-    partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = df_to_double(tot);
+    partial[(int64_t)blockIdx.y * adj.rt + adj.m_base / OZ_BM + blockIdx.x] = df_to_double(tot);
   }
 }
 
@@ -722,20 +748,25 @@ static void set_oz_attr() {
 
 static void launch_class_oz_mode(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N,
                                  const RowInfo* rows, const double* E0p, double b, double* partial,
-                                 const AdjOut* adj) {
-  static bool attr = false;
-  if (!attr) {
+                                 const AdjOut* adj, unsigned long long* dmin, int64_t tm0, int64_t ntm) {
+  // the attribute belongs to the device: set it on each device's first launch
+  if (first_use_on_device(g_oz_attr)) {
     set_oz_attr<false>();
     set_oz_attr<true>();
-    attr = true;
   }
-  const AdjOut a = adj ? *adj : AdjOut{};
-  dim3 grid((unsigned)(adj ? (adj->Mc + OZ_BM - 1) / OZ_BM : op.Mpad / OZ_BM), (unsigned)(op.Npad / 64));
+  AdjOut a = adj ? *adj : AdjOut{};
+  if (!adj) {  // forward: row tiles tm0 .. tm0 + ntm - 1 of Mpad / 64, one partial slot each
+    a.m_base = tm0 * OZ_BM;
+    a.rt = op.Mpad / OZ_BM;
+  }
+  dim3 grid((unsigned)(adj ? (adj->Mc + OZ_BM - 1) / OZ_BM : ntm), (unsigned)(op.Npad / 64));
 #define E2_OZ_LAUNCH(NS_, NH_)                                                                                   \
   if (adj)                                                                                                     \
-    (k_class_oz<NS_, NH_, true><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, nullptr, a), ++g_launches);  \
+    (k_class_oz<NS_, NH_, true><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, nullptr, a, nullptr),      \
+     ++g_launches);                                                                                            \
   else                                                                                                         \
-    (k_class_oz<NS_, NH_, false><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial, a), ++g_launches);
+    (k_class_oz<NS_, NH_, false><<<grid, 256, OZ_SMEM, st>>>(op, M, N, rows, E0p, b, partial, a, dmin),         \
+     ++g_launches);
   switch (cls) {  // particles and holes of the rows
     case 2: E2_OZ_LAUNCH(2, 0) break;
     case 5: E2_OZ_LAUNCH(2, 1) break;
@@ -747,13 +778,16 @@ static void launch_class_oz_mode(cudaStream_t st, int cls, const OzOperands& op,
 }
 
 void launch_class_oz(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
-                     const double* E0p, double b, double* partial) {
-  launch_class_oz_mode(st, cls, op, M, N, rows, E0p, b, partial, nullptr);
+                     const double* E0p, double b, double* partial, unsigned long long* dmin, int64_t tm0,
+                     int64_t ntm) {
+  if (ntm < 0) ntm = op.Mpad / OZ_BM - tm0;
+  if (ntm <= 0) return;
+  launch_class_oz_mode(st, cls, op, M, N, rows, E0p, b, partial, nullptr, dmin, tm0, ntm);
 }
 
 void launch_class_oz_adj(cudaStream_t st, int cls, const OzOperands& op, int64_t M, int64_t N, const RowInfo* rows,
                          const double* E0p, double b, const AdjOut& adj) {
-  launch_class_oz_mode(st, cls, op, M, N, rows, E0p, b, nullptr, &adj);
+  launch_class_oz_mode(st, cls, op, M, N, rows, E0p, b, nullptr, &adj, nullptr, 0, 0);
 }
 
 // ------------------------------------------------------------------ general product
@@ -891,7 +925,8 @@ __global__ void __launch_bounds__(256, 2) k_zgemm_sl(OzGemm q) {
       for (int ni = 0; ni < 2; ++ni) {
         const int64_t col = n0 + wn * 8 + ni * 4 + t;
         if (col >= q.N) continue;
-        const double sc = ldexp(1.0, er + q.cexp[col]);
+        const int ek = er + q.cexp[col];
+        const double sc = ek > OZ_NONFINITE / 2 ? __longlong_as_double(0x7FF8000000000000LL) : ldexp(1.0, ek);
         const double re = df_to_double(dfl{dh[mi][ni][2 * hr], dl[mi][ni][2 * hr]}) * sc;
         const double im = df_to_double(dfl{dh[mi][ni][2 * hr + 1], dl[mi][ni][2 * hr + 1]}) * sc;
         double2* c = q.C + row * q.csm + col * q.csn;
@@ -923,11 +958,9 @@ static void zgemm_sliced_run(cudaStream_t st, int64_t M, int64_t N, int64_t Nb, 
                              int conjB, double2* C, int64_t csm, int64_t csn, int beta, int64_t lower,
                              unsigned char* scratch, bool reuse_b, bool a_df) {
   constexpr size_t smem = 2 * (size_t)S * (OG_BM + OG_BNR) * OG_LD * 2;
-  static bool attr = false;
-  if (!attr) {
+  static DeviceFlags attr;  // per device, per slice count
+  if (first_use_on_device(attr))
     cudaFuncSetAttribute(k_zgemm_sl<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    attr = true;
-  }
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const int64_t Mpad = (M + OG_BM - 1) / OG_BM * OG_BM, Npad = (Nb + 31) / 32 * 32;
   const int Kq = (int)((2 * K + 31) / 32 * 32);
@@ -1162,18 +1195,22 @@ __global__ void __launch_bounds__(256)
 k_class22_df(DevList Ls, DevSpace sp, const float2* __restrict__ eAdf, const float2* __restrict__ Udf,
              const double2* __restrict__ c, const double* __restrict__ g2, const double* __restrict__ epsh,
              const double* __restrict__ G, const double* __restrict__ E0p, double b, int nvb,
-             double* __restrict__ partial) {
+             double* __restrict__ partial, unsigned long long* dmin, int64_t u0) {
   __shared__ float2 sGab[8][8], sG2[8][8], sAl[2][8], sBase;
   __shared__ float2 sW[8];
+  // grid y: units u0 + blockIdx.y of (core pair z, virtual block pair y), u = z nyb + y
+  const int64_t nyb = (int64_t)nvb * (nvb + 1) / 2;
+  const int64_t u = u0 + blockIdx.y;
+  const int zp = (int)(u / nyb);
   int ba = 0, bb = 0;
   {
-    int yb = blockIdx.y, k = 0;
+    int yb = (int)(u % nyb), k = 0;
     while (yb >= nvb - k) { yb -= nvb - k; ++k; }
     ba = k;
     bb = k + yb;
   }
   int iu, ju;
-  pair_decode(blockIdx.z, iu, ju);
+  pair_decode(zp, iu, ju);
   const int gi = sp.cc[iu], gj = sp.cc[ju];
   const int64_t nvp = pairs(sp.nvc);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1182,7 +1219,7 @@ k_class22_df(DevList Ls, DevSpace sp, const float2* __restrict__ eAdf, const flo
     const int a = ba * 8 + x, bq = bb * 8 + y;
     const bool ok = a < sp.nvc && bq < sp.nvc && a < bq;
     const dfl gab = df_from_double(ok ? G[(int64_t)sp.vc[a] * sp.n + sp.vc[bq]] : 0.0);
-    const dfl w = df_from_double(ok ? g2[(int64_t)blockIdx.z * nvp + pair_index(a, bq)] : 0.0);
+    const dfl w = df_from_double(ok ? g2[(int64_t)zp * nvp + pair_index(a, bq)] : 0.0);
     sGab[x][y] = make_float2(gab.hi, gab.lo);
     sG2[x][y] = make_float2(w.hi, w.lo);
   } else if (tid < 80) {
@@ -1202,6 +1239,7 @@ k_class22_df(DevList Ls, DevSpace sp, const float2* __restrict__ eAdf, const flo
   __syncthreads();
   const int64_t A = blockIdx.x * (int64_t)blockDim.x + tid;
   dfl acc{0.f, 0.f};
+  unsigned dmk = 0xFFFFFFFFu;
   if (A < Ls.n) {
     const bool shifted = b != 0.0;
     const dfl bbq = df_from_double(b * b);
@@ -1231,6 +1269,7 @@ k_class22_df(DevList Ls, DevSpace sp, const float2* __restrict__ eAdf, const flo
         const float2 w = sG2[x][y];
         if (w.x == 0.0f) continue;
         const dfl D = df_sub(df_sub(cx, pb[y]), dfl{sGab[x][y].x, sGab[x][y].y});
+        dmk = min(dmk, fkey(D.hi));
         dfl g;
         if (!shifted) {
           g = df_rcp(D);
@@ -1244,21 +1283,29 @@ k_class22_df(DevList Ls, DevSpace sp, const float2* __restrict__ eAdf, const flo
     const double2 cv = c[A];
     acc = df_mul(df_from_double(cv.x * cv.x + cv.y * cv.y), inner.value());
   }
+  dmin_flush_f(dmin, dmk);
   acc = warp_df_sum(acc);
   if (lane == 0) sW[warp] = make_float2(acc.hi, acc.lo);
   __syncthreads();
   if (tid == 0) {
     dfl tot{sW[0].x, sW[0].y};
     for (int w = 1; w < (int)(blockDim.x >> 5); ++w) tot = df_add(tot, dfl{sW[w].x, sW[w].y});
-    partial[((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x] = df_to_double(tot);
+    partial[u * gridDim.x + blockIdx.x] = df_to_double(tot);
   }
 }
 
 void launch_class22_df(cudaStream_t st, const DevList& L, const DevSpace& sp, const float2* eAdf, const float2* Udf,
                        const double2* c, const double* g2, const double* epsh, const double* G, const double* E0p,
-                       double b, int nvb, int64_t ncp, double* partial) {
-  dim3 grid((unsigned)((L.n + 255) / 256), (unsigned)(nvb * (nvb + 1) / 2), (unsigned)ncp);
-  (k_class22_df<<<grid, 256, 0, st>>>(L, sp, eAdf, Udf, c, g2, epsh, G, E0p, b, nvb, partial), ++g_launches);
+                       double b, int nvb, int64_t ncp, double* partial, unsigned long long* dmin, int64_t u0,
+                       int64_t u1) {
+  // units u = z nyb + y over (core pair z, virtual block pair y), [u0, u1); y
+  // of the grid holds at most 65535 of them per launch
+  if (u1 < 0) u1 = ncp * ((int64_t)nvb * (nvb + 1) / 2);
+  for (int64_t a = u0; a < u1; a += 65535) {
+    dim3 grid((unsigned)((L.n + 255) / 256), (unsigned)std::min<int64_t>(65535, u1 - a));
+    (k_class22_df<<<grid, 256, 0, st>>>(L, sp, eAdf, Udf, c, g2, epsh, G, E0p, b, nvb, partial, dmin, a),
+     ++g_launches);
+  }
 }
 
 }  // namespace e2

@@ -366,6 +366,7 @@ e2_status build_plan(e2_problem* P) {
   P->plan_bytes = ws.top - P->o_plan;
   // device-computed data
   P->o_binom = ws.take(sizeof(int64_t) * kBinomN * kBinomN);
+  P->o_status = ws.take(sizeof(unsigned long long) * (1 + (size_t)R * E2_NCLASS));
   P->o_EO = ws.take(sizeof(double));
   P->o_E0p = ws.take(sizeof(double) * R);
   P->o_E0 = ws.take(sizeof(double) * R);
@@ -399,11 +400,12 @@ e2_status build_plan(e2_problem* P) {
     const bool fits = extra <= (size_t(16) << 30);
     for (int c : {2, 5, 7, 6}) {
       P->oz_ok[c] = P->oz_ok[c] && fits;
-      P->use_oz[c] = P->oz_ok[c];
+      P->use_oz[c] = false;  // FP64 by default; the sliced form is opt-in
       if (P->oz_ok[c]) P->lists[P->list_of[c]].df = true;
     }
     if (d8 && fits) P->lists[l8].df = true;
-    P->oz_ok[8] = P->use_oz[8] = d8 && fits;  // class (2,2) in float-float
+    P->oz_ok[8] = d8 && fits;  // class (2,2) in float-float (opt-in)
+    P->use_oz[8] = false;
   }
   for (HostList& L : P->lists) {
     L.o_str = ws.take(sizeof(uint64_t) * std::max<int64_t>(L.n, 1));
@@ -513,7 +515,7 @@ e2_status build_plan(e2_problem* P) {
       b = std::max(b, zgemm_sliced_bytes(nva, (int64_t)P->na * P->na, Lt));
       P->o_ozS = P->o_vaX + al(P->va_cap);
       P->ozS_bytes = b;
-      P->use_oz_setup = true;
+      P->use_oz_setup = false;
       ws.top = std::max(ws.top, P->o_ozS + al(b));
     }
   }
@@ -674,7 +676,7 @@ e2_status build_plan(e2_problem* P) {
       const size_t cs = Lt > 0 ? zgemm_sliced_bytes(Lt, npair, npair, OZ_ADJ_S) : 0;
       if (cs <= (size_t(4) << 30)) oz = std::max(oz, cs);
       P->bOz_bytes = oz;
-      P->use_oz_adj = oz > 0;
+      P->use_oz_adj = false;
       P->o_bOz = ws.take(std::max<size_t>(oz, 256));
       P->o_bC2 = ws.take(8 * (size_t)std::max<int64_t>(lsize(8), 1));
     }
@@ -733,7 +735,7 @@ e2_status e2_problem_create(const e2_desc* desc, e2_problem** out) {
   if (sum != d.n_active) return E2_ERR_SHAPE;
   const int n = d.n_core + d.n_active + d.n_virt;
   e2_problem* P = new (std::nothrow) e2_problem();
-  if (!P) return E2_ERR_INVALID_ARG;
+  if (!P) return E2_ERR_OOM;
   P->d = d;
   P->frozen.assign(n, 0);
   if (d.frozen) {
@@ -756,6 +758,8 @@ e2_status e2_problem_create(const e2_desc* desc, e2_problem** out) {
   e2_status st;
   try {
     st = build_plan(P);
+  } catch (const std::bad_alloc&) {
+    st = E2_ERR_OOM;
   } catch (...) {
     st = E2_ERR_UNSUPPORTED;
   }

@@ -19,19 +19,10 @@ import pytest
 from fp64_mode import fp64_contraction
 from e2_inputs import make_problem
 from strings_ref import ClassStrings
+from rows_ref import CLASSES, _row
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-
-
-def _pair(e):
-    """(x, y), x < y, of pair index e = y(y-1)/2 + x."""
-    y = int((1 + (1 + 8 * e) ** 0.5) / 2)
-    while y * (y - 1) // 2 > e:
-        y -= 1
-    while (y + 1) * y // 2 <= e:
-        y += 1
-    return e - y * (y - 1) // 2, y
 
 
 FULLSIZE = {"ne_dcg": True, "ar_dcb_das": os.environ.get("E2_FULLSIZE_DAS") == "1"}
@@ -55,36 +46,6 @@ def run(request):
     plan.forward(**t)
     torch.cuda.synchronize()
     return prob, o, E0, plan, t
-
-
-# class id -> (h, p); rows decoded per e2.h's documented order
-CLASSES = {2: (0, 2), 5: (1, 2), 7: (2, 1), 4: (1, 1), 6: (2, 0), 1: (0, 1), 3: (1, 0), 0: (0, 0)}
-
-
-def _row(cls, row, cc, vc):
-    """(holes, particles) as global spinor indices of external row `row`."""
-    nvc, nvp = len(vc), len(vc) * (len(vc) - 1) // 2
-    if cls == 2:
-        a, b = _pair(row)
-        return [], [vc[a], vc[b]]
-    if cls == 5:
-        a, b = _pair(row % nvp)
-        return [cc[row // nvp]], [vc[a], vc[b]]
-    if cls == 7:
-        i, j = _pair(row // nvc)
-        return [cc[i], cc[j]], [vc[row % nvc]]
-    if cls == 4:
-        return [cc[row // nvc]], [vc[row % nvc]]
-    if cls == 6:
-        i, j = _pair(row)
-        return [cc[i], cc[j]], []
-    if cls == 1:
-        return [], [vc[row]]
-    if cls == 3:
-        return [cc[row]], []
-    if cls == 0:
-        return [], []
-    raise ValueError(cls)
 
 
 def _oracle_block(o, E0, prob, cls, rows, ranks, lists):

@@ -1,7 +1,8 @@
 """Host-side checks of the arithmetic modes (no GPU): which parts of the path
-have the sliced bf16 / float-float form planned, that it is the default
-there, that switching round-trips, and that unavailable or invalid requests
-fail with the documented status codes.  Planning runs on the host only."""
+have the sliced bf16 / float-float form planned, that FP64 is the default
+everywhere, that switching round-trips, and that unavailable or invalid
+requests fail with the documented status codes.  Planning runs on the host
+only."""
 import ctypes as C
 
 import pytest
@@ -24,11 +25,12 @@ def _raw(plan, cls, mode):
     return e2.load().e2_set_contraction(plan._h, cls, mode)
 
 
-def test_sliced_forms_are_planned_and_default_where_the_bound_holds(plan):
+def test_sliced_forms_are_planned_where_the_bound_holds_and_fp64_is_the_default(plan):
     # DC 4 core + CAS(6e,12) + 40 virtual: real contraction lengths 2 K = 2 C(12,2) = 132 ((0,2), (2,0)),
     # 2 x 12 = 24 ((1,2), (2,1)), all within 256; (1,1) has 2 (1 + 12^2) = 290
     for cls in (2, 5, 6, 7, 8, SETUP, ADJOINT):
-        assert plan.contraction(cls) == (True, True), cls
+        assert plan.contraction(cls) == (False, True), cls
+    assert plan.arithmetic() == "fp64"
     assert plan.contraction(4) == (False, False)      # (1,1): beyond the exact-accumulation bound
     for cls in (0, 1, 3):                             # gather classes: FP64 only
         assert plan.contraction(cls) == (False, False)
@@ -36,10 +38,16 @@ def test_sliced_forms_are_planned_and_default_where_the_bound_holds(plan):
 
 def test_modes_round_trip(plan):
     for cls in (2, 5, 6, 7, 8, SETUP, ADJOINT):
-        plan.set_contraction(cls, False)
-        assert plan.contraction(cls) == (False, True)
         plan.set_contraction(cls, True)
         assert plan.contraction(cls) == (True, True)
+        plan.set_contraction(cls, False)
+        assert plan.contraction(cls) == (False, True)
+    plan.set_arithmetic(True)
+    assert plan.arithmetic() == "sliced"
+    assert all(plan.contraction(cls) == (True, True) for cls in (2, 5, 6, 7, 8, SETUP, ADJOINT))
+    assert plan.contraction(4) == (False, False)
+    plan.set_arithmetic(False)
+    assert plan.arithmetic() == "fp64"
 
 
 def test_unavailable_and_invalid_requests(plan):
@@ -61,9 +69,10 @@ def test_adjoint_chunk_setter(plan):
 
 
 def test_sliced_buffers_are_gated_by_size():
-    # the Xe shape's slices and float-float tables exceed 16 GiB: FP64 throughout, setup and adjoint products sliced
+    # the Xe shape's slices and float-float tables exceed 16 GiB: no sliced classes; the setup and adjoint
+    # products keep their (opt-in) sliced form
     p = e2.E2Problem(46, 24, 1000, 8, ham="DCB", L_coulomb=1400, L_extra=700)
     for cls in (2, 5, 6, 7, 8):
         assert p.contraction(cls) == (False, False), cls
-    assert p.contraction(SETUP) == (True, True)
-    assert p.contraction(ADJOINT) == (True, True)
+    assert p.contraction(SETUP) == (False, True)
+    assert p.contraction(ADJOINT) == (False, True)
