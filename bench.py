@@ -540,6 +540,49 @@ def _timed_fwd_bwd(plan, t, steps, warmup, stream, ws, dist, dev):
     return max_over_ranks(b0.elapsed_time(b1) / steps, ws, dist, dev), vg[0].clone()
 
 
+def _integral_flops(prob, plan):
+    """Algorithmic work of the integral formation (step a5): every
+    antisymmetrised integral <pq||rs> = (pr|qs) - (ps|qr) that the classes
+    contract, two complex dot products of length L over the factors each:
+    16 L real flops per integral."""
+    from math import comb
+    nc = sum(1 for k in range(prob.n_core) if not prob.frozen[k])
+    nv = sum(1 for v in range(prob.n_core + prob.n_act, prob.n) if not prob.frozen[v])
+    na = prob.n_act
+    ntp, npv, npc = comb(na, 2), comb(nv, 2), comb(nc, 2)
+    q = plan.q_per_class
+    blocks = {2: npv * ntp, 5: nc * npv * na, 7: npc * nv * na, 4: nc * nv * na * na, 6: npc * ntp, 8: npc * npv,
+              1: nv * na * ntp, 3: nc * ntp * na, 0: ntp * ntp}
+    L = prob.Bc.shape[0] + (prob.Bx.shape[0] if prob.ham != "DC" else 0)
+    n_int = sum(v for k, v in blocks.items() if q[k] > 0) + ntp * ntp   # <tu||vw> enters E0 always
+    return 16.0 * L * n_int, n_int
+
+
+def _timed_integrals(plan, prob, t, steps, warmup, stream, ws, dist, dev, peak_dmma):
+    import torch
+    tin = {k: v for k, v in t.items() if k != "c"}
+    for _ in range(warmup):
+        plan.form_integrals(**tin)
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(steps):
+        plan.form_integrals(**tin)
+    z.record(stream)
+    torch.cuda.synchronize()
+    ims = max_over_ranks(a.elapsed_time(z) / steps, ws, dist, dev)
+    flops, n_int = _integral_flops(prob, plan)
+    ach = flops / (ims * 1e-3) / 1e12
+    return {"ms_per_step": ims, "steps": steps, "warmup": warmup, "integrals_formed": n_int,
+            "algorithmic_flops": flops, "flops_per_integral": "16 L real (two complex dot products over the factors)",
+            "achieved_tflops": ach, "frac_of_fp64_tensor_peak": ach / peak_dmma,
+            "arithmetic": "sliced bf16" if plan.contraction(-1)[0] else "fp64",
+            "what": "e2_form_integrals: compact factors, G, eps^, f^(O), string tables, every integral block "
+                    "of the classes from the factors (step a5; the paper's T_int)"}
+
+
 def _aux_steps(args, ms):
     """Steps of the secondary timings (fwd+bwd, end to end, the other
     arithmetic): the headline's K where a step is short, else as many as fit
@@ -643,6 +686,11 @@ def run(args):
                "d2h_bytes_per_step": int(out_host.numel() * 8), "ms_per_step": ems, "steps": aux}
         del dev_in, host
 
+    # integral formation alone (step a5 as a workload of its own)
+    integ = None
+    if not args.no_integrals:
+        integ = _timed_integrals(plan, prob, t, aux, aux_warm, stream, ws, dist, dev, peak_dmma)
+
     # the other arithmetic on the same workload (emulated when the headline is FP64)
     alt = None
     other = "sliced" if args.arith == "fp64" else "fp64"
@@ -687,6 +735,7 @@ def run(args):
                                            if shard else f"{ws} independent replica(s)"),
                            "class_ms": {CLASS_NAMES[k]: fw["ktime"][k] for k in present}},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fwd_bwd": fwdbwd, "alt_arithmetic": alt,
+                "integrals": integ,
                 "gpu_launches": fw["launches"] * args.steps,
                 "clocks": fw["clocks"], "fp64_peaks_tflops": {"dmma": peak_dmma, "dfma": peak_dfma}}
         print(json.dumps(line), flush=True)
@@ -711,6 +760,7 @@ def main():
     ap.add_argument("--arith", default="fp64", choices=["fp64", "sliced"],
                     help="arithmetic of the headline: fp64 (the library default) or the emulated sliced form")
     ap.add_argument("--no-alt", action="store_true", help="skip the timing of the other arithmetic")
+    ap.add_argument("--no-integrals", action="store_true", help="skip the timing of the integral formation alone")
     ap.add_argument("--replicas", action="store_true",
                     help="under torchrun: N independent replicas of the whole job instead of one sharded job")
     ap.add_argument("--aux-steps", type=int, default=0,

@@ -199,6 +199,31 @@ E2_API e2_status e2_probe_couplings(e2_problem* prob, const e2_inputs* in, void*
                                    void* stream, int root, int cls, int64_t tile_m, int64_t tile_n, double* V,
                                    double* D, int64_t* shape);
 
+/* Intruder diagnostics (Sec. 2.6): how close the denominators D = E0 - H_KK
+ * of root `root` come to zero, per class, as a histogram by decades:
+ *   hist device [E2_NCLASS][E2_DHIST] uint64 (overwritten): bin 0 counts
+ *     |D| < 1e-12 Eh (intruder states when b = 0), bin k = 1..16 counts
+ *     10^(k-13) <= |D| < 10^(k-12) Eh, bin 17 the rest (|D| >= 1e4 Eh or NaN).
+ * Every external determinant of every evaluated class counts once (class
+ * (2,2) also where <ab||ij> vanishes), so row c sums to the class's size.
+ * A diagnostic pass: it sets up root `root` as e2_forward does and evaluates
+ * every denominator (no V).  Enqueues on `stream`; inputs and workspace as
+ * for e2_forward. */
+#define E2_DHIST 18
+E2_API e2_status e2_denominator_histogram(e2_problem* prob, const e2_inputs* in, void* workspace,
+                                          size_t workspace_bytes, void* stream, int root, unsigned long long* hist);
+
+/* Integral formation alone (step a5; the paper's AO -> MO transformation,
+ * T_int of Sec. 3.1 Table 1, here from the factors B^L): everything of
+ * e2_forward that depends only on the Hamiltonian and the partition -- the
+ * compact factor block, G, eps^, f^(O), the string lists with e_A and U, and
+ * every integral block the classes contract: <ab||tu>, <ab||it>, <at||ij>,
+ * <at||iu> with f^(O)_ai, <tu||ij>, |<ab||ij>|^2, <au||vw>, <tu||iv>,
+ * <tu||vw> -- into `workspace`, then stops.  c is not read (may be NULL).
+ * Enqueues on `stream`; workspace as for e2_forward. */
+E2_API e2_status e2_form_integrals(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                                   void* stream);
+
 /* Sharding of the external space over ranks (no counterpart in the paper's
  * method; its sigma-build is distributed over CPU nodes, Sec. 2.4 / 3.1, which
  * is prior art here).  Every class's work is cut into units -- row tiles of a
@@ -276,6 +301,19 @@ E2_API e2_status e2_batch_prepare(e2_batch* batch, void* workspace, size_t works
 E2_API e2_status e2_batch_forward(e2_batch* batch, const e2_inputs* inputs, void* workspace, size_t workspace_bytes,
                                   void* stream, double* const* E2, double* const* E2_class);
 E2_API e2_status e2_batch_launch_count(const e2_batch* batch, int64_t* n);
+/* Adjoint of a batch: each job's e2_backward in turn, in one workspace of
+ * e2_batch_backward_workspace_size() bytes (the largest job's backward
+ * layout; the forward batch's prepared workspace is not needed).  Per job j:
+ * seeds[j] host [n_roots_j]; g_h, g_c, g_Bc, g_Bx, dE2_dlambda, E2: arrays of
+ * n_jobs device pointers as e2_backward takes them (an array, or an entry,
+ * may be NULL to skip that output).  The energies are bitwise equal to
+ * e2_forward's and e2_batch_forward's of the same job.  The passes are
+ * enqueued one after another on `stream` (not merged into one launch). */
+E2_API e2_status e2_batch_backward_workspace_size(const e2_batch* batch, size_t* bytes);
+E2_API e2_status e2_batch_backward(e2_batch* batch, const e2_inputs* inputs, const double* const* seeds,
+                                  void* workspace, size_t workspace_bytes, void* stream, double* const* g_h,
+                                  double* const* g_c, double* const* g_Bc, double* const* g_Bx,
+                                  double* const* dE2_dlambda, double* const* E2);
 
 /* Adjoint of e2_forward (gradients are not in the paper; they follow from
  * differentiating Eq. pt2 with E0 = <Psi|H|Psi>/<Psi|Psi>).  For
@@ -394,6 +432,17 @@ E2_API e2_status e2_class_tiles(const e2_problem* prob, int cls, int64_t* tiles,
  * class has no plan. */
 E2_API e2_status e2_class_tiles_copy(const e2_problem* prob, int cls, int32_t* perm, int32_t* tdesc, int32_t* klist);
 E2_API e2_status e2_set_class_tiles(e2_problem* prob, int cls, int on);
+/* Tuning cache for e2_autotune's choices (no counterpart in the paper): a text
+ * file of lines "<key> | <column-tile choice of the nine classes>", the key
+ * made of every plan input that shapes the classes (spinor counts, DAS
+ * partition, frozen spinors, factor counts, roots, class mask).
+ *   e2_tuning_save appends this problem's current choices (E2_ERR_INVALID_ARG
+ *                  when the file cannot be written);
+ *   e2_tuning_load applies the last line whose key matches; E2_ERR_UNSUPPORTED
+ *                  when the file is missing or holds none (the plan's
+ *                  defaults then stay). */
+E2_API e2_status e2_tuning_save(const e2_problem* prob, const char* path);
+E2_API e2_status e2_tuning_load(e2_problem* prob, const char* path);
 
 /* Arithmetic of the dense-class contraction (step a7; no counterpart in the
  * paper, which computes in FP64).  The default everywhere is FP64.

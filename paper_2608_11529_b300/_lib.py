@@ -119,6 +119,20 @@ def load():
         L.e2_shard_buffers.restype = C.c_int
         L.e2_reduce.argtypes = [C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         L.e2_reduce.restype = C.c_int
+        L.e2_form_integrals.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p]
+        L.e2_form_integrals.restype = C.c_int
+        L.e2_tuning_save.argtypes = [C.c_void_p, C.c_char_p]
+        L.e2_tuning_save.restype = C.c_int
+        L.e2_tuning_load.argtypes = [C.c_void_p, C.c_char_p]
+        L.e2_tuning_load.restype = C.c_int
+        L.e2_batch_backward_workspace_size.argtypes = [C.c_void_p, C.POINTER(C.c_size_t)]
+        L.e2_batch_backward_workspace_size.restype = C.c_int
+        L.e2_batch_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p] + \
+            [C.c_void_p] * 6
+        L.e2_batch_backward.restype = C.c_int
+        L.e2_denominator_histogram.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p,
+                                               C.c_int, C.c_void_p]
+        L.e2_denominator_histogram.restype = C.c_int
         L.e2_status_string.argtypes = [C.c_int]
         L.e2_status_string.restype = C.c_char_p
         _lib = L
@@ -345,6 +359,34 @@ class E2Problem:
                                     C.c_void_p(D.data_ptr()), None))
         return V, D
 
+    DHIST = 18
+
+    def denominator_histogram(self, h, B_c, c, B_x=None, w_x=None, lam=1.0, root=0, stream=None):
+        """Counts of |E0 - H_KK| per class and decade (e2_denominator_histogram):
+        int64 CUDA [9, 18]; bin 0 below 1e-12 Eh, bin k 10^(k-13)..10^(k-12),
+        bin 17 the rest."""
+        import torch
+        dev = c.device
+        hist = torch.zeros(NCLASS, self.DHIST, dtype=torch.int64, device=dev)
+        ws = self.workspace(dev)
+        inp = _Inputs(h.data_ptr(), B_c.data_ptr(), B_x.data_ptr() if self.L_extra else None,
+                      w_x.data_ptr() if self.L_extra else None, float(lam), c.data_ptr())
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        _check(load().e2_denominator_histogram(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s),
+                                               int(root), C.c_void_p(hist.data_ptr())))
+        return hist
+
+    def form_integrals(self, h, B_c, B_x=None, w_x=None, lam=1.0, c=None, stream=None):
+        """The integral blocks of the classes from the factors alone
+        (e2_form_integrals), in the cached workspace."""
+        import torch
+        dev = B_c.device
+        ws = self.workspace(dev)
+        inp = _Inputs(h.data_ptr(), B_c.data_ptr(), B_x.data_ptr() if self.L_extra else None,
+                      w_x.data_ptr() if self.L_extra else None, float(lam), c.data_ptr() if c is not None else None)
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        _check(load().e2_form_integrals(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s)))
+
     def set_shard(self, rank, n_ranks):
         """Take rank `rank`'s share of every class's units out of n_ranks
         (e2_set_shard; (0, 1) = unsharded)."""
@@ -457,6 +499,19 @@ class E2Problem:
         ms = (C.c_float * (2 * NCLASS))()
         _check(load().e2_autotune(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s), ms))
         return {k: (ms[2 * k], ms[2 * k + 1]) for k in range(NCLASS) if ms[2 * k] > 0}
+
+    def tuning_save(self, path):
+        """Append this problem's column-tile choices to the tuning cache file."""
+        _check(load().e2_tuning_save(self._h, os.fsencode(path)))
+
+    def tuning_load(self, path):
+        """Apply the cached choices for this problem's shape; False when the
+        file holds none (the plan's defaults stay)."""
+        st = load().e2_tuning_load(self._h, os.fsencode(path))
+        if st == 3:
+            return False
+        _check(st)
+        return True
 
     def launch_count(self):
         """Kernels enqueued by the last forward()."""
@@ -579,6 +634,40 @@ class E2Batch:
         n = C.c_int64()
         _check(load().e2_batch_launch_count(self._h, C.byref(n)))
         return int(n.value)
+
+    def backward(self, inputs, seeds=None, want_B=True, stream=None):
+        """Every job's adjoint (e2_batch_backward): returns per job (E2, g_h,
+        g_c, g_Bc, g_Bx, dE2/dlambda) as CUDA tensors."""
+        import torch
+        L = load()
+        dev = inputs[0]["c"].device
+        need = C.c_size_t()
+        _check(L.e2_batch_backward_workspace_size(self._h, C.byref(need)))
+        raw = torch.empty(need.value + 256, dtype=torch.uint8, device=dev)
+        off = (-raw.data_ptr()) % 256
+        ws = raw[off:off + need.value]
+        nj = len(self.plans)
+        arr = (_Inputs * nj)()
+        seeds = [np.ones(p.n_roots) if seeds is None else np.ascontiguousarray(seeds[j], np.float64)
+                 for j, p in enumerate(self.plans)]
+        seeds = [np.ascontiguousarray(x, np.float64) for x in seeds]
+        sp = (C.c_void_p * nj)(*[x.ctypes.data for x in seeds])
+        outs = []
+        for k, (p, t) in enumerate(zip(self.plans, inputs)):
+            arr[k] = _Inputs(t["h"].data_ptr(), t["B_c"].data_ptr(), t["B_x"].data_ptr() if p.L_extra else None,
+                             t["w_x"].data_ptr() if p.L_extra else None, float(t["lam"]), t["c"].data_ptr())
+            outs.append((torch.empty(p.n_roots, dtype=torch.float64, device=dev),
+                         torch.empty(p.n, p.n, dtype=torch.complex128, device=dev),
+                         torch.empty(p.n_roots, p.n_p, dtype=torch.complex128, device=dev),
+                         torch.empty(t["B_c"].shape, dtype=torch.complex128, device=dev) if want_B else None,
+                         torch.empty(t["B_x"].shape, dtype=torch.complex128, device=dev)
+                         if (want_B and p.L_extra) else None,
+                         torch.zeros(1, dtype=torch.float64, device=dev)))
+        ptrs = lambda i: (C.c_void_p * nj)(*[o[i].data_ptr() if o[i] is not None else None for o in outs])
+        s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
+        _check(L.e2_batch_backward(self._h, C.cast(arr, C.c_void_p), C.cast(sp, C.c_void_p), ws.data_ptr(),
+                                   ws.numel(), C.c_void_p(s), ptrs(1), ptrs(2), ptrs(3), ptrs(4), ptrs(5), ptrs(0)))
+        return outs
 
 
 def fp64_peak(device="cuda"):

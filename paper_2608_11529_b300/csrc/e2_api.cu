@@ -3,7 +3,9 @@
 // measurement hooks.  No device allocation.
 #include "e2_host.h"
 
+#include <cstdio>
 #include <cstring>
+#include <string>
 
 namespace e2 {
 
@@ -541,6 +543,47 @@ e2_status e2_probe_couplings(e2_problem* P, const e2_inputs* in, void* workspace
   return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
 }
 
+e2_status e2_form_integrals(e2_problem* P, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                            void* stream_) {
+  if (!P || !in || !in->h || !in->B_c) return E2_ERR_INVALID_ARG;
+  if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
+  if (!std::isfinite(in->lambda)) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < P->ws_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  cudaGetLastError();
+  g_launches = 0;
+  if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
+  setup_classes(P, ws, st);
+  P->launches = g_launches;
+  return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
+}
+
+e2_status e2_denominator_histogram(e2_problem* P, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                                   void* stream_, int root, unsigned long long* hist) {
+  if (!P || !in || !in->h || !in->B_c || !in->c || !hist) return E2_ERR_INVALID_ARG;
+  if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
+  if (root < 0 || root >= P->d.n_roots) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < P->ws_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  cudaGetLastError();
+  g_launches = 0;
+  if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
+  setup_classes(P, ws, st);
+  const DevList LP = dev_list(P, P->listP, ws);
+  prepare_root(P, ws, st, (const double2*)in->c + (int64_t)root * LP.n, root);
+  Ctx X = ctx(P, ws);
+  cudaMemsetAsync(hist, 0, sizeof(unsigned long long) * E2_NCLASS * E2_DHIST, st);
+  for (int cls = 0; cls < E2_NCLASS; ++cls) {
+    if (P->part_cnt[cls] == 0) continue;
+    const DevList L = dev_list(P, P->list_of[cls], ws);
+    dim3 grid((unsigned)P->M[cls], (unsigned)((L.n + 4095) / 4096));
+    (k_dhist<<<grid, 256, 0, st>>>(cls, X.sp, L, X.epsh, X.G, X.E0p + root, hist + cls * E2_DHIST), ++g_launches);
+  }
+  return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
+}
+
 e2_status e2_set_shard(e2_problem* P, int rank, int n_ranks) {
   if (!P || n_ranks < 1 || rank < 0 || rank >= n_ranks) return E2_ERR_INVALID_ARG;
   P->shard_rank = rank;
@@ -678,6 +721,55 @@ e2_status e2_autotune(e2_problem* P, const e2_inputs* in, void* workspace, size_
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
+}
+
+// Key of a problem's tuning entry: every plan input that changes the class
+// shapes (spinor counts, partition, frozen spinors, factor counts, roots,
+// class mask), as one text line.
+static std::string tuning_key(const e2_problem* P) {
+  const e2_desc& d = P->d;
+  std::string k = "e2tune1 " + std::to_string(d.n_core) + " " + std::to_string(d.n_active) + " " +
+                  std::to_string(d.n_virt) + " " + std::to_string(d.n_elec) + " das";
+  for (int s = 0; s < d.n_das; ++s)
+    k += " " + std::to_string(P->das_size[s]) + ":" + std::to_string(P->das_min[s]) + ":" + std::to_string(P->das_max[s]);
+  k += " ham " + std::to_string(d.ham) + " L " + std::to_string(d.L_coulomb) + " " + std::to_string(d.L_extra) +
+       " roots " + std::to_string(d.n_roots) + " mask " + std::to_string(d.class_mask) + " frozen ";
+  for (uint8_t f : P->frozen) k += f ? '1' : '0';
+  return k;
+}
+
+e2_status e2_tuning_save(const e2_problem* P, const char* path) {
+  if (!P || !path) return E2_ERR_INVALID_ARG;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return E2_ERR_INVALID_ARG;
+  std::fprintf(f, "%s |", tuning_key(P).c_str());
+  for (int c = 0; c < E2_NCLASS; ++c) std::fprintf(f, " %d", P->use_cols[c] ? 1 : 0);
+  std::fprintf(f, "\n");
+  const bool ok = std::fclose(f) == 0;
+  return ok ? E2_OK : E2_ERR_INVALID_ARG;
+}
+
+e2_status e2_tuning_load(e2_problem* P, const char* path) {
+  if (!P || !path) return E2_ERR_INVALID_ARG;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return E2_ERR_UNSUPPORTED;
+  const std::string key = tuning_key(P) + " |";
+  std::string line, hit;
+  int ch;
+  while (true) {  // the last matching entry wins
+    line.clear();
+    while ((ch = std::fgetc(f)) != EOF && ch != '\n') line.push_back((char)ch);
+    if (line.compare(0, key.size(), key) == 0) hit = line.substr(key.size());
+    if (ch == EOF) break;
+  }
+  std::fclose(f);
+  if (hit.empty()) return E2_ERR_UNSUPPORTED;
+  int v[E2_NCLASS];
+  if (std::sscanf(hit.c_str(), "%d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7],
+                  &v[8]) != E2_NCLASS)
+    return E2_ERR_UNSUPPORTED;
+  for (int c = 0; c < E2_NCLASS; ++c) P->use_cols[c] = v[c] && P->cplan[c].built;
+  return E2_OK;
 }
 
 e2_status e2_launch_count(const e2_problem* P, int64_t* n) {

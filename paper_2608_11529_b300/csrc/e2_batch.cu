@@ -174,6 +174,36 @@ e2_status e2_batch_forward(e2_batch* B, const e2_inputs* inputs, void* workspace
   return E2_OK;
 }
 
+e2_status e2_batch_backward_workspace_size(const e2_batch* B, size_t* bytes) {
+  if (!B || !bytes) return E2_ERR_INVALID_ARG;
+  size_t m = 0;
+  for (const e2_problem* P : B->jobs) m = std::max(m, P->bwd_bytes);
+  *bytes = m;
+  return E2_OK;
+}
+
+e2_status e2_batch_backward(e2_batch* B, const e2_inputs* inputs, const double* const* seeds, void* workspace,
+                            size_t workspace_bytes, void* stream, double* const* g_h, double* const* g_c,
+                            double* const* g_Bc, double* const* g_Bx, double* const* dE2_dlambda,
+                            double* const* E2) {
+  if (!B || !inputs || !seeds) return E2_ERR_INVALID_ARG;
+  size_t need = 0;
+  e2_batch_backward_workspace_size(B, &need);
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  for (size_t j = 0; j < B->jobs.size(); ++j)
+    if (!seeds[j]) return E2_ERR_INVALID_ARG;
+  auto at = [](double* const* a, size_t j) { return a ? a[j] : nullptr; };
+  int64_t launches = 0;
+  for (size_t j = 0; j < B->jobs.size(); ++j) {
+    const e2_status st = e2_backward(B->jobs[j], inputs + j, seeds[j], workspace, workspace_bytes, stream,
+                                     at(g_h, j), at(g_c, j), at(g_Bc, j), at(g_Bx, j), at(dE2_dlambda, j), at(E2, j));
+    if (st != E2_OK) return st;
+    launches += B->jobs[j]->launches;
+  }
+  B->launches = launches;
+  return E2_OK;
+}
+
 e2_status e2_batch_launch_count(const e2_batch* B, int64_t* n) {
   if (!B || !n) return E2_ERR_INVALID_ARG;
   *n = B->launches;

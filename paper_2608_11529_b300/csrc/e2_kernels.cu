@@ -313,10 +313,8 @@ __global__ void k_w02(DevSpace sp, const double2* __restrict__ X, int64_t ldx, i
 
 // Row descriptors of the dense classes: U rows of particles / holes and
 // chi(e) = -sum_I eps^_i + [h=2] G_ij + sum_S eps^_s + [p=2] G_ab - sum_{IxS} G.
-__global__ void k_rows(int cls, DevSpace sp, const double* __restrict__ epsh, const double* __restrict__ G, int64_t M,
-                       RowInfo* __restrict__ out) {
-  int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (row >= M) return;
+__device__ RowInfo row_info(int cls, const DevSpace& sp, const double* __restrict__ epsh,
+                            const double* __restrict__ G, int64_t row) {
   const int nvp = (int)pairs(sp.nvc);
   int I[2] = {-1, -1}, S[2] = {-1, -1}, x, y;
   switch (cls) {
@@ -355,7 +353,54 @@ __global__ void k_rows(int cls, DevSpace sp, const double* __restrict__ epsh, co
   ri.i1 = I[0] >= 0 ? I[0] : sp.nx;
   ri.i2 = I[1] >= 0 ? I[1] : sp.nx;
   ri.chi = chi;
-  out[row] = ri;
+  return ri;
+}
+
+__global__ void k_rows(int cls, DevSpace sp, const double* __restrict__ epsh, const double* __restrict__ G, int64_t M,
+                       RowInfo* __restrict__ out) {
+  int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (row >= M) return;
+  out[row] = row_info(cls, sp, epsh, G, row);
+}
+
+// Histogram of |D|, D = E0' - chi_e - e_A - U[s1,A] - U[s2,A] + U[i1,A] + U[i2,A],
+// over the couplings of one class (intruder diagnostics, Sec. 2.6): bin 0
+// |D| < 1e-12, bin k = 1..DHIST-2: 10^(k-13) <= |D| < 10^(k-12), the last bin
+// the rest (and NaN).  Grid: x = external rows, y = chunks of 4096 strings.
+constexpr int DHIST = 18;
+__global__ void __launch_bounds__(256) k_dhist(int cls, DevSpace sp, DevList L, const double* __restrict__ epsh,
+                                               const double* __restrict__ G, const double* __restrict__ E0p,
+                                               unsigned long long* __restrict__ hist) {
+  __shared__ unsigned sh[DHIST];
+  __shared__ RowInfo sri;
+  if (threadIdx.x < DHIST) sh[threadIdx.x] = 0;
+  if (threadIdx.x == 0) sri = row_info(cls, sp, epsh, G, blockIdx.x);
+  __syncthreads();
+  const RowInfo ri = sri;
+  const double base = *E0p - ri.chi;
+  const double* U1 = L.U + (int64_t)ri.s1 * L.n;
+  const double* U2 = L.U + (int64_t)ri.s2 * L.n;
+  const double* U3 = L.U + (int64_t)ri.i1 * L.n;
+  const double* U4 = L.U + (int64_t)ri.i2 * L.n;
+  const int64_t a0 = (int64_t)blockIdx.y * 4096, a1 = min(L.n, a0 + 4096);
+  for (int64_t A = a0 + threadIdx.x; A < a1; A += blockDim.x) {
+    const double D = fabs(base - L.eA[A] - U1[A] - U2[A] + U3[A] + U4[A]);
+    int k;
+    if (D < 1e-12) {
+      k = 0;
+    } else {
+      k = DHIST - 1;
+      double edge = 1e-11;
+      for (int q = 1; q < DHIST - 1; ++q, edge *= 10.0)
+        if (D < edge) {
+          k = q;
+          break;
+        }
+    }
+    atomicAdd(&sh[k], 1u);
+  }
+  __syncthreads();
+  if (threadIdx.x < DHIST && sh[threadIdx.x]) atomicAdd(hist + threadIdx.x, (unsigned long long)sh[threadIdx.x]);
 }
 
 // ------------------------------------------------------------------ D tables

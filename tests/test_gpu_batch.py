@@ -74,3 +74,31 @@ def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph(col_tile
         for (E2, E2c), (B2, B2c) in zip(single, out):
             assert torch.equal(E2, B2) and torch.equal(E2c, B2c)
     assert batch.launch_count() > 0
+
+
+@pytest.mark.parametrize("sliced", [False, True])
+def test_batch_backward_equals_each_jobs_backward(sliced):
+    """e2_batch_backward: every job's energies and gradients bitwise equal to
+    its own e2_backward, and the energies to its forward."""
+    import paper_2608_11529_b300 as e2
+    from paper_2608_11529_b300 import build as e2build
+    e2build.build()
+    jobs = _jobs()
+    plans = [e2.E2Problem.from_problem(p) for p, _, _ in jobs]
+    for plan in plans:
+        plan.set_arithmetic(sliced)
+    inputs = [e2.device_inputs(p, c) for p, _, c in jobs]
+    seeds = [np.linspace(1.0, 0.5, p.n_roots) for p, _, _ in jobs]
+    ref = []
+    for plan, t, sd in zip(plans, inputs, seeds):
+        E2f = plan.forward(**t)[0].clone()
+        out = plan.value_and_grad(**t, seed=sd)
+        ref.append((E2f, [x.clone() if x is not None else None for x in out]))
+    batch = e2.E2Batch(plans)
+    got = batch.backward(inputs, seeds=seeds)
+    torch.cuda.synchronize()
+    for (E2f, r), g in zip(ref, got):
+        assert torch.equal(g[0], E2f) and torch.equal(g[0], r[0])
+        for k in range(1, 6):
+            if r[k] is not None and g[k] is not None:
+                assert torch.equal(g[k], r[k]), k

@@ -153,3 +153,53 @@ def test_status_is_cleared_by_the_next_call():
     assert plan.status()[0] == E2_ERR_NONFINITE
     plan.forward(**t)
     assert plan.status()[:2] == (E2_OK, 0)
+
+
+def _bins(D):
+    """The documented decade bins of |D| (numpy, from the values the oracle gives)."""
+    a = np.abs(D)
+    k = np.full(a.shape, 17)
+    k[a < 1e-12] = 0
+    for q in range(1, 17):
+        k[(a >= 10.0 ** (q - 13)) & (a < 10.0 ** (q - 12))] = q
+    return k
+
+
+def test_denominator_histogram_matches_the_oracle():
+    """Every external determinant's |E0 - H_KK| counted once per class and
+    decade; against the oracle's D of every determinant (a value within
+    1e-9 relative of a decade edge may fall on either side)."""
+    from itertools import combinations
+    prob = _problem()
+    o = Oracle(prob)
+    c, _ = o.ground_state(1)
+    E0 = o.e0()
+    e2, plan = _plan(prob, c)
+    t = e2.device_inputs(prob, c)
+    hist = plan.denominator_histogram(**t).cpu().numpy()
+    nc = list(range(prob.n_core))
+    nv = list(range(prob.n_core + prob.n_act, prob.n))
+    for cls in range(9):
+        h, p = divmod(cls, 3)
+        ne = prob.n_elec + h - p
+        if cls == 0 or ne < 0 or ne > prob.n_act:
+            assert hist[cls].sum() == 0
+            continue
+        Ks = [(I, S, A) for I in combinations(nc, h) for S in combinations(nv, p)
+              for A in combinations(range(prob.n_act), ne)]
+        _, D = o.couplings(E0, [h] * len(Ks), [list(I) + [0] * (2 - h) for I, _, _ in Ks], [p] * len(Ks),
+                           [list(S) + [0] * (2 - p) for _, S, _ in Ks], [sum(1 << a for a in A) for _, _, A in Ks])
+        ref = np.bincount(_bins(D[:, 0]), minlength=18)
+        assert hist[cls].sum() == len(Ks) == plan.q_per_class[cls]
+        edges = 10.0 ** np.arange(-12, 5)
+        near = int(sum((np.abs(np.abs(D[:, 0]) - e) <= 1e-9 * e).sum() for e in edges))
+        assert np.abs(hist[cls] - ref).sum() <= 2 * near, (cls, hist[cls], ref)
+
+
+def test_denominator_histogram_flags_the_intruder():
+    prob, c = _intruder_inputs()
+    e2, plan = _plan(prob, c)
+    t = e2.device_inputs(prob, c)
+    hist = plan.denominator_histogram(**t).cpu().numpy()
+    assert hist[1, 0] >= 1                     # class (0,1): the crafted |D| < 1e-12
+    assert hist[[2, 4, 5, 6, 7, 8], 0].sum() == 0
