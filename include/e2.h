@@ -253,6 +253,15 @@ E2_API e2_status e2_shard_buffers(const e2_problem* prob, void* workspace, doubl
                                   int64_t** min_keys, int64_t* n_keys);
 E2_API e2_status e2_reduce(e2_problem* prob, void* workspace, size_t workspace_bytes, void* stream, double* E2,
                            double* E2_class, double* E0);
+/* What e2_reduce reads besides the partials -- every root's E0 and <c|c> --
+ * set up in `workspace` without any class work (setup and the coupling
+ * tensors of each root in turn).  With it, partial sets saved piece by piece
+ * (each piece a shard's e2_forward, its partials written to a file) can be
+ * summed back into the workspace by a later process and reduced: a long run
+ * resumes where it stopped, with the result bitwise equal to the unsharded
+ * forward (checkpoint / resume). */
+E2_API e2_status e2_prepare_roots(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                                  void* stream);
 
 /* Device status word (the conditions of Sec. 2.6 that only the device sees).
  * Every e2_forward (also e2_forward_noalloc, each job of e2_batch_forward and
@@ -481,6 +490,24 @@ E2_API e2_status e2_tuning_load(e2_problem* prob, const char* path);
 #define E2_CONTRACT_SETUP (-1)
 #define E2_CONTRACT_ADJOINT (-2)
 E2_API e2_status e2_set_contraction(e2_problem* prob, int cls, int mode);
+
+/* DAS subspaces in the core and virtual spaces (Sec. 2.4, Fig. 1: the core
+ * and external virtual spaces partitioned into further DAS subspaces, each
+ * category characterised by its occupation pattern over them) with per-
+ * subspace limits on the external excitations: at most core_max_holes[s]
+ * holes in core subspace s and virt_max_particles[s] particles in virtual
+ * subspace s, on top of the global two holes / two particles.  Subspaces are
+ * consecutive blocks of the core (sizes summing to n_core) and of the
+ * virtual spinors (summing to n_virt) in global order.  A limit of 2 (or
+ * more) leaves the subspace unrestricted; a limit of 0 is a frozen block and
+ * is given with the frozen mask instead (E2_ERR_INVALID_ARG here).  The
+ * determinants the limits exclude leave Q: they contribute nothing to E2,
+ * the gradients, the status word or the histogram, and the class sizes of
+ * e2_problem_info drop accordingly.  n_cdas = n_vdas = 0 removes all limits.
+ * Host only; takes effect from the next call that uploads the plan. */
+E2_API e2_status e2_set_external_das(e2_problem* prob, int n_cdas, const int32_t* core_size,
+                                     const int32_t* core_max_holes, int n_vdas, const int32_t* virt_size,
+                                     const int32_t* virt_max_particles);
 E2_API e2_status e2_contraction(const e2_problem* prob, int cls, int* mode, int* sliced_available);
 E2_API e2_status e2_autotune(e2_problem* prob, const e2_inputs* in, void* workspace, size_t workspace_bytes,
                              void* stream, float* ms_out);

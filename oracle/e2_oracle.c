@@ -86,6 +86,12 @@ typedef struct {
   int* corr_core;
   int* corr_virt;
   uint64_t* pstr;     /* active string of each P address */
+  /* DAS subspaces of the core and virtual spaces (Sec. 2.4, Fig. 1) with
+     per-subspace limits on holes / particles; xsub[p] = subspace of spinor p
+     (-1: none), xlim[s] its limit */
+  int n_xdas;
+  int* xsub;
+  int xlim[128];
 } oracle_t;
 
 static int64_t binom_tab[72][72];
@@ -363,6 +369,9 @@ void* oracle_create(const oracle_desc* d) {
     if (!P->frozen[k]) P->corr_core[P->ncc++] = k;
   for (int v = P->v0; v < n; ++v)
     if (!P->frozen[v]) P->corr_virt[P->nvc++] = v;
+  P->xsub = (int*)malloc(sizeof(int) * n);
+  for (int p = 0; p < n; ++p) P->xsub[p] = -1;
+  P->n_xdas = 0;
   return P;
 }
 
@@ -370,6 +379,7 @@ void oracle_destroy(void* vp) {
   oracle_t* P = (oracle_t*)vp;
   if (!P) return;
   free(P->frozen);
+  free(P->xsub);
   free(P->h);
   free(P->w);
   free(P->eri);
@@ -410,6 +420,41 @@ static void build_pstr(oracle_t* P) {
     int64_t a = p_address_active(P, A);
     if (a >= 0) P->pstr[a] = A;
   }
+}
+
+/* Core / virtual DAS subspaces with hole / particle limits (Sec. 2.4, Fig. 1;
+   the excitation restrictions of the categories): core subspace s (a block
+   of consecutive core spinors) admits at most cmax[s] holes, virtual
+   subspace s at most vmax[s] particles.  n_c = n_v = 0 removes them. */
+void oracle_set_external_das(void* vp, int n_c, const int* csize, const int* cmax, int n_v, const int* vsize,
+                             const int* vmax) {
+  oracle_t* P = (oracle_t*)vp;
+  for (int p = 0; p < P->n; ++p) P->xsub[p] = -1;
+  int at = 0, s = 0;
+  for (int k = 0; k < n_c; ++k, ++s) {
+    for (int q = 0; q < csize[k]; ++q) P->xsub[at++] = s;
+    P->xlim[s] = cmax[k];
+  }
+  at = P->v0;
+  for (int k = 0; k < n_v; ++k, ++s) {
+    for (int q = 0; q < vsize[k]; ++q) P->xsub[at++] = s;
+    P->xlim[s] = vmax[k];
+  }
+  P->n_xdas = s;
+}
+
+/* Does the external determinant (holes, particles) respect the subspace
+   limits?  Counts the holes / particles that fall in each subspace. */
+static int external_allowed(const oracle_t* P, const int* holes, int nh, const int* parts, int np) {
+  if (P->n_xdas == 0) return 1;
+  int cnt[128] = {0};
+  for (int k = 0; k < nh; ++k)
+    if (P->xsub[holes[k]] >= 0) cnt[P->xsub[holes[k]]]++;
+  for (int k = 0; k < np; ++k)
+    if (P->xsub[parts[k]] >= 0) cnt[P->xsub[parts[k]]]++;
+  for (int s = 0; s < P->n_xdas; ++s)
+    if (cnt[s] > P->xlim[s]) return 0;
+  return 1;
 }
 
 /* P determinants connected to determinant K, for each L: <K|H|L>. */
@@ -603,6 +648,7 @@ int oracle_e2(void* vp, const double* E0, double* e2_class, int64_t* n_coupl) {
         int holes[2], parts[2];
         subset_of(P->corr_core, P->ncc, h, item / nS, holes);
         subset_of(P->corr_virt, P->nvc, p, item % nS, parts);
+        if (!external_allowed(P, holes, h, parts, p)) continue; /* outside Q: subspace limits */
         FOR_STRINGS(A, P->n_act, ne) {
           det_t K;
           make_det(P, &K, holes, h, A, parts, p);
@@ -759,7 +805,16 @@ int oracle_count_q(void* vp, double* counts) {
         }
         if (s < 0) break;
       }
-      counts[cls] = tot * (double)binom(P->ncc, h) * (double)binom(P->nvc, p);
+      /* (hole, particle) tuples that respect the subspace limits */
+      double items = 0;
+      const int64_t nI = binom(P->ncc, h), nS = binom(P->nvc, p);
+      for (int64_t it = 0; it < nI * nS; ++it) {
+        int holes[2], parts[2];
+        subset_of(P->corr_core, P->ncc, h, it / nS, holes);
+        subset_of(P->corr_virt, P->nvc, p, it % nS, parts);
+        items += external_allowed(P, holes, h, parts, p);
+      }
+      counts[cls] = tot * items;
     }
   return 0;
 }
@@ -958,6 +1013,7 @@ int oracle_grad(void* vp, const double* E0, const double* seed, double* gh_out, 
         int holes[2], parts[2];
         subset_of(P->corr_core, P->ncc, h, item / nS, holes);
         subset_of(P->corr_virt, P->nvc, p, item % nS, parts);
+        if (!external_allowed(P, holes, h, parts, p)) continue;
         FOR_STRINGS(A, P->n_act, ne) {
           det_t K;
           make_det(P, &K, holes, h, A, parts, p);

@@ -11,6 +11,8 @@ Functions and the passages they follow:
 * ``Oracle.couplings``     -- V_K = <K|H|Psi> and E0 - H_KK for listed K
 * ``Oracle.count_q``       -- size of Q per class (Sec. 2.3, Table 3)
 * ``Oracle.hmat``          -- generic <K|H|L> between two determinants
+* ``Oracle.set_external_das`` -- core / virtual DAS subspaces with hole /
+                              particle limits restricting Q (Sec. 2.4, Fig. 1)
 * ``Oracle.dtable``        -- coupling tensors D^x_A = <A|x|Psi> of listed
                               active strings by generic operator algebra
                               (Sec. 2.4, Eq. sumsigma: the <K|E_pq|L> C_L
@@ -82,6 +84,8 @@ def _load():
         L.oracle_eri.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p]
         L.oracle_grad.argtypes = [C.c_void_p] + [C.c_void_p] * 6
         L.oracle_dtable.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int64, C.c_void_p, C.c_void_p]
+        L.oracle_set_external_das.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                              C.c_void_p]
         _lib = L
     return _lib
 
@@ -215,6 +219,16 @@ class Oracle:
         gc = np.zeros((self.n_roots, self.n_p), np.complex128)
         self._L.oracle_grad(self._h_ptr, _ptr(E0), _ptr(seed), _ptr(gh), _ptr(gB), _ptr(gw), _ptr(gc))
         return gh, gB, gw, gc
+
+    def set_external_das(self, core_size=(), core_max_holes=(), virt_size=(), virt_max_particles=()):
+        """DAS subspaces of the core / virtual spinors (consecutive blocks) with
+        per-subspace limits on holes / particles (Sec. 2.4, Fig. 1): Q keeps
+        the determinants within every limit."""
+        arrs = [np.ascontiguousarray(x, np.int32) for x in (core_size, core_max_holes, virt_size,
+                                                              virt_max_particles)]
+        self._xdas = arrs
+        self._L.oracle_set_external_das(self._h_ptr, len(arrs[0]), _ptr(arrs[0]), _ptr(arrs[1]), len(arrs[2]),
+                                        _ptr(arrs[2]), _ptr(arrs[3]))
 
     FAMILIES = {"t": 0, "t+": 1, "tu": 2, "t+u+": 3, "t+u": 4}
 

@@ -133,6 +133,11 @@ def load():
         L.e2_denominator_histogram.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p,
                                                C.c_int, C.c_void_p]
         L.e2_denominator_histogram.restype = C.c_int
+        L.e2_prepare_roots.argtypes = [C.c_void_p, C.POINTER(_Inputs), C.c_void_p, C.c_size_t, C.c_void_p]
+        L.e2_prepare_roots.restype = C.c_int
+        L.e2_set_external_das.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                          C.c_void_p]
+        L.e2_set_external_das.restype = C.c_int
         L.e2_status_string.argtypes = [C.c_int]
         L.e2_status_string.restype = C.c_char_p
         _lib = L
@@ -387,6 +392,22 @@ class E2Problem:
         s = torch.cuda.current_stream(dev).cuda_stream if stream is None else stream
         _check(load().e2_form_integrals(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s)))
 
+    def set_external_das(self, core_size=(), core_max_holes=(), virt_size=(), virt_max_particles=()):
+        """Core / virtual DAS subspaces with per-subspace hole / particle limits
+        (e2_set_external_das); empty sequences remove the limits.  Updates
+        q_per_class."""
+        cs = np.ascontiguousarray(core_size, np.int32)
+        ch = np.ascontiguousarray(core_max_holes, np.int32)
+        vs = np.ascontiguousarray(virt_size, np.int32)
+        vp = np.ascontiguousarray(virt_max_particles, np.int32)
+        _check(load().e2_set_external_das(self._h, len(cs), cs.ctypes.data_as(C.c_void_p),
+                                          ch.ctypes.data_as(C.c_void_p), len(vs), vs.ctypes.data_as(C.c_void_p),
+                                          vp.ctypes.data_as(C.c_void_p)))
+        n_p = C.c_int64()
+        q = np.zeros(NCLASS)
+        _check(load().e2_problem_info(self._h, C.byref(n_p), q.ctypes.data_as(C.c_void_p)))
+        self.q_per_class = q
+
     def set_shard(self, rank, n_ranks):
         """Take rank `rank`'s share of every class's units out of n_ranks
         (e2_set_shard; (0, 1) = unsharded)."""
@@ -423,6 +444,63 @@ class E2Problem:
                                 C.c_void_p(out[0].data_ptr()), C.c_void_p(out[1].data_ptr()),
                                 C.c_void_p(out[2].data_ptr())))
         return out
+
+    def checkpointed_forward(self, path, h, B_c, c, B_x=None, w_x=None, lam=1.0, pieces=8, max_pieces=None,
+                             tag=""):
+        """E2 of a long run in `pieces` resumable parts (checkpoint / resume).
+        Part k is shard k of `pieces` (e2_set_shard + e2_forward); as each
+        completes, its partial slots and smallest-|D| keys are saved to
+        `path`/piece_k.npz.  Parts already saved are skipped, so a killed run
+        resumes where it stopped; `max_pieces` bounds the parts computed by
+        this call.  When every part is saved: e2_prepare_roots, the parts'
+        partials summed element-wise into the workspace (disjoint slots, so
+        the sum is exact) and e2_reduce, giving E2, E2_class and E0 bitwise
+        equal to the unsharded forward.  Returns (E2, E2_class, E0) then, else
+        None.  `tag` names the inputs in the manifest: a directory holding
+        parts of another problem or tag is refused."""
+        import json
+        import torch
+        os.makedirs(path, exist_ok=True)
+        ws = self.workspace(c.device)
+        n_part = self.shard_buffers()[0].numel()
+        meta = {"pieces": int(pieces), "partials": int(n_part), "roots": self.n_roots, "tag": str(tag),
+                "q_per_class": [float(x) for x in self.q_per_class]}
+        mpath = os.path.join(path, "manifest.json")
+        if os.path.exists(mpath):
+            if json.load(open(mpath)) != meta:
+                raise E2Error(f"checkpoint directory {path} holds another run")
+        else:
+            json.dump(meta, open(mpath, "w"))
+        kw = dict(B_x=B_x, w_x=w_x, lam=lam)
+        done = 0
+        try:
+            for k in range(pieces):
+                f = os.path.join(path, f"piece_{k}.npz")
+                if os.path.exists(f):
+                    continue
+                if max_pieces is not None and done >= max_pieces:
+                    return None
+                self.set_shard(k, pieces)
+                self.forward(h, B_c, c, **kw)
+                part, keys = self.shard_buffers()
+                tmp = f + ".tmp.npz"
+                np.savez(tmp, part=part.cpu().numpy(), keys=keys.cpu().numpy())
+                os.replace(tmp, f)
+                done += 1
+        finally:
+            self.set_shard(0, 1)
+        inp = _Inputs(h.data_ptr(), B_c.data_ptr(), B_x.data_ptr() if self.L_extra else None,
+                      w_x.data_ptr() if self.L_extra else None, float(lam), c.data_ptr())
+        s = torch.cuda.current_stream(c.device).cuda_stream
+        _check(load().e2_prepare_roots(self._h, C.byref(inp), ws.data_ptr(), ws.numel(), C.c_void_p(s)))
+        part, keys = self.shard_buffers()
+        part.zero_()
+        keys.fill_(0x7FFFFFFFFFFFFFFF)
+        for k in range(pieces):
+            z = np.load(os.path.join(path, f"piece_{k}.npz"))
+            part.add_(torch.from_numpy(z["part"]).to(part.device))
+            torch.minimum(keys, torch.from_numpy(z["keys"]).to(keys.device), out=keys)
+        return self.reduce()
 
     def sharded_forward(self, dist, h, B_c, c, B_x=None, w_x=None, lam=1.0, group=None):
         """E2 of the whole external space from this rank's share: e2_forward on

@@ -53,6 +53,8 @@ Ctx ctx(const e2_problem* P, unsigned char* ws) {
   sp.nx = P->nx;
   sp.cc = (const int32_t*)(ws + P->o_cc);
   sp.vc = (const int32_t*)(ws + P->o_vc);
+  sp.xc = (const int32_t*)(ws + P->o_xc);
+  sp.xv = (const int32_t*)(ws + P->o_xv);
   return X;
 }
 
@@ -291,6 +293,15 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
   if (P->part_cnt[3] > 0)
     (k_integrals<<<blocks((int64_t)P->ncc * P->ntp * na), 256, 0, st>>>(INT_X10, X.sp, X.Bo, X.wt, Lt, X.f, P->ncc,
                                                                        P->ntp * na, P->ntp * na, ws + P->o_X10), ++g_launches);
+  // external subspace limits: the excluded rows' W rows and |<ab||ij>|^2 to zero
+  if (P->ext_das) {
+    for (int c : {2, 5, 7, 6})
+      if (P->M[c] > 0 && P->part_cnt[c] > 0)
+        (k_mask_rows<<<blocks(P->M[c] * P->Kp[c]), 256, 0, st>>>((double2*)(ws + P->o_W[c]), P->M[c], P->Kp[c],
+                                                                (const RowInfo*)(ws + P->o_rows[c])), ++g_launches);
+    if (P->part_cnt[8] > 0)
+      (k_mask22<<<blocks(P->ncp * P->nvp), 256, 0, st>>>(ws + P->o_G22, P->ncp, P->nvp, X.sp, 0), ++g_launches);
+  }
   // row slices of W for the classes on the sliced contraction
   for (int c : {2, 5, 7, 6})
     if (P->use_oz[c] && P->part_cnt[c] > 0)
@@ -581,6 +592,22 @@ e2_status e2_denominator_histogram(e2_problem* P, const e2_inputs* in, void* wor
     dim3 grid((unsigned)P->M[cls], (unsigned)((L.n + 4095) / 4096));
     (k_dhist<<<grid, 256, 0, st>>>(cls, X.sp, L, X.epsh, X.G, X.E0p + root, hist + cls * E2_DHIST), ++g_launches);
   }
+  return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
+}
+
+e2_status e2_prepare_roots(e2_problem* P, const e2_inputs* in, void* workspace, size_t workspace_bytes,
+                           void* stream_) {
+  if (!P || !in || !in->h || !in->B_c || !in->c) return E2_ERR_INVALID_ARG;
+  if (P->d.L_extra > 0 && (!in->B_x || !in->w_x)) return E2_ERR_INVALID_ARG;
+  if (!std::isfinite(in->lambda)) return E2_ERR_INVALID_ARG;
+  if (!workspace || workspace_bytes < P->ws_bytes || ((uintptr_t)workspace & 255)) return E2_ERR_WORKSPACE;
+  cudaStream_t st = (cudaStream_t)stream_;
+  unsigned char* ws = (unsigned char*)workspace;
+  cudaGetLastError();
+  g_launches = 0;
+  if (setup_common(P, in, ws, st) != E2_OK) return E2_ERR_CUDA;
+  const DevList LP = dev_list(P, P->listP, ws);
+  for (int r = 0; r < P->d.n_roots; ++r) prepare_root(P, ws, st, (const double2*)in->c + (int64_t)r * LP.n, r);
   return cudaGetLastError() == cudaSuccess ? E2_OK : E2_ERR_CUDA;
 }
 

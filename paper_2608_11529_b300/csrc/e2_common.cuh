@@ -160,7 +160,18 @@ struct DevSpace {
   int ncc, nvc, nx;        // correlated core / virtual counts, nx = ncc + nvc
   const int32_t* cc;       // [ncc] global index of correlated core spinors
   const int32_t* vc;       // [nvc] global index of correlated virtual spinors
+  // external subspace limits (e2_set_external_das): per correlated core /
+  // virtual spinor, its subspace id when that subspace admits one hole /
+  // particle only, else -1
+  const int32_t* xc;       // [ncc]
+  const int32_t* xv;       // [nvc]
 };
+
+// chi of an external row that the external subspace limits exclude: its W
+// row (or |<ab||ij>|^2) is zeroed, so V = 0, and D = E0' - chi is far from 0
+// and from every real denominator (|D| < 1e4 Eh), so it never reaches the
+// smallest-|D| diagnostics; the denominator histogram skips it.
+constexpr double kExcludedChi = -1e8;
 
 __host__ __device__ inline int64_t pairs(int64_t n) { return n * (n - 1) / 2; }
 

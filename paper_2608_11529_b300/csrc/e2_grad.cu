@@ -310,6 +310,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         const int Lt = d.L_coulomb + d.L_extra;
         (k_integrals<<<blocks(M22), 256, 0, st>>>(INT_G22C, X.sp, X.Bo, X.wt, Lt, X.f, P->ncp, (int)P->nvp,
                                                   (int)P->nvp, B(P->o_bG22c)), ++g_launches);
+        if (P->ext_das)  // rows outside Q take no part in the factor gradient
+          (k_mask22<<<blocks(M22), 256, 0, st>>>(B(P->o_bG22c), P->ncp, P->nvp, X.sp, 1), ++g_launches);
         (k_g22coef<<<blocks(M22), 256, 0, st>>>((const double2*)B(P->o_bG22c), P22, M22, (double2*)B(P->o_bGg22)),
          ++g_launches);
         (k_gint<<<blocks(M22), 256, 0, st>>>(INT_G22C, X.sp, (const double2*)B(P->o_bGg22), P->ncp, (int)P->nvp,

@@ -82,6 +82,10 @@ struct e2_problem {
   size_t o_plan, plan_bytes;
   size_t o_binom, o_EO, o_E0p, o_E0, o_G, o_epsh, o_dg, o_wt, o_Bo, o_f, o_cc, o_vc;
   size_t o_status;  // device status word: flags + smallest |D| key per (root, class)
+  size_t o_xc, o_xv;  // external subspace ids of one-hole / one-particle subspaces (plan region)
+  std::vector<int32_t> xc, xv;  // their host copies (-1: no limit below two)
+  bool ext_das = false;         // some external subspace limit is one
+  double q_full[E2_NCLASS];     // class sizes without external subspace limits
   int shard_rank = 0, shard_n = 1;  // e2_set_shard: this rank's share of every class's units
   size_t o_rows[E2_NCLASS], o_W[E2_NCLASS];
   size_t o_G22, o_X01, o_X10, o_X00;

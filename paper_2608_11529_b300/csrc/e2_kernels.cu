@@ -313,6 +313,14 @@ __global__ void k_w02(DevSpace sp, const double2* __restrict__ X, int64_t ldx, i
 
 // Row descriptors of the dense classes: U rows of particles / holes and
 // chi(e) = -sum_I eps^_i + [h=2] G_ij + sum_S eps^_s + [p=2] G_ab - sum_{IxS} G.
+// Two holes in one core subspace, or two particles in one virtual subspace,
+// whose limit is one (correlated-space indices; -1 = absent).
+__device__ __forceinline__ bool row_excluded(const DevSpace& sp, int i0, int i1, int a0, int a1) {
+  if (i0 >= 0 && i1 >= 0 && sp.xc[i0] >= 0 && sp.xc[i0] == sp.xc[i1]) return true;
+  if (a0 >= 0 && a1 >= 0 && sp.xv[a0] >= 0 && sp.xv[a0] == sp.xv[a1]) return true;
+  return false;
+}
+
 __device__ RowInfo row_info(int cls, const DevSpace& sp, const double* __restrict__ epsh,
                             const double* __restrict__ G, int64_t row) {
   const int nvp = (int)pairs(sp.nvc);
@@ -352,8 +360,28 @@ __device__ RowInfo row_info(int cls, const DevSpace& sp, const double* __restric
   ri.s2 = S[1] >= 0 ? sp.ncc + S[1] : sp.nx;
   ri.i1 = I[0] >= 0 ? I[0] : sp.nx;
   ri.i2 = I[1] >= 0 ? I[1] : sp.nx;
-  ri.chi = chi;
+  ri.chi = row_excluded(sp, I[0], I[1], S[0], S[1]) ? kExcludedChi : chi;
   return ri;
+}
+
+// Zero the W rows of excluded external rows (their V is then 0).
+__global__ void k_mask_rows(double2* __restrict__ W, int64_t M, int Kp, const RowInfo* __restrict__ rows) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= M * Kp) return;
+  if (rows[idx / Kp].chi == kExcludedChi) W[idx] = make_double2(0.0, 0.0);
+}
+
+// Zero the class-(2,2) entries [(i<j)][(a<b)] of excluded rows: |<ab||ij>|^2
+// (cplx = 0) or <ab||ij> (cplx = 1).
+__global__ void k_mask22(void* __restrict__ g, int64_t ncp, int64_t nvp, DevSpace sp, int cplx) {
+  const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (idx >= ncp * nvp) return;
+  int i, j, a, b;
+  pair_decode(idx / nvp, i, j);
+  pair_decode(idx % nvp, a, b);
+  if (!row_excluded(sp, i, j, a, b)) return;
+  if (cplx) ((double2*)g)[idx] = make_double2(0.0, 0.0);
+  else ((double*)g)[idx] = 0.0;
 }
 
 __global__ void k_rows(int cls, DevSpace sp, const double* __restrict__ epsh, const double* __restrict__ G, int64_t M,
@@ -377,6 +405,7 @@ __global__ void __launch_bounds__(256) k_dhist(int cls, DevSpace sp, DevList L, 
   if (threadIdx.x == 0) sri = row_info(cls, sp, epsh, G, blockIdx.x);
   __syncthreads();
   const RowInfo ri = sri;
+  if (ri.chi == kExcludedChi) return;  // not in Q (external subspace limits)
   const double base = *E0p - ri.chi;
   const double* U1 = L.U + (int64_t)ri.s1 * L.n;
   const double* U2 = L.U + (int64_t)ri.s2 * L.n;
@@ -666,6 +695,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
       const double* U3 = U + (int64_t)ri.i1 * N;
       const double* U4 = U + (int64_t)ri.i2 * N;
       const double base = e0p - ri.chi;
+      const bool in_q = ri.chi != kExcludedChi;  // external subspace limits
       // the thread's four denominators of this row, inverted together
       double Dv[4], q[4], rq[4];
 #pragma unroll
@@ -676,7 +706,7 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
           const int kk = ni * 2 + hc;
           Dv[kk] = col >= 0 ? base - eA[col] - U1[col] - U2[col] + U3[col] + U4[col] : 1.0;
           q[kk] = col >= 0 ? en_q(Dv[kk], b) : 1.0;
-          if (col >= 0) dm = min(dm, dkey(Dv[kk]));
+          if (col >= 0 && in_q) dm = min(dm, dkey(Dv[kk]));
         }
       rcp4(q, rq);
 #pragma unroll

@@ -23,6 +23,8 @@ __global__ void k_w12(DevSpace sp, const double2* X, int64_t ldx, int64_t M, int
 __global__ void k_x01(DevSpace sp, const double2* X, double2* X01);
 __global__ void k_w02(DevSpace sp, const double2* X, int64_t ldx, int b0, int b1, int Kp, double2* W);
 __global__ void k_rows(int cls, DevSpace sp, const double* epsh, const double* G, int64_t M, RowInfo* out);
+__global__ void k_mask_rows(double2* W, int64_t M, int Kp, const RowInfo* rows);
+__global__ void k_mask22(void* g, int64_t ncp, int64_t nvp, DevSpace sp, int cplx);
 __global__ void k_dhist(int cls, DevSpace sp, DevList L, const double* epsh, const double* G, const double* E0p,
                         unsigned long long* hist);
 __global__ void k_dtable(int fam, DevList Ls, DevList Pl, DevDas das, const int64_t* binom, const double2* c, int Kp,

@@ -700,7 +700,7 @@ k_class_oz(OzOperands op, int64_t M, int64_t N, const RowInfo* __restrict__ rows
           const float2 u = op.Udf[(int64_t)ri.w * N + col];
           Dk = df_add(Dk, dfl{u.x, u.y});
         }
-        dmk = min(dmk, fkey(Dk.hi));
+        if (bs.x < 1e7f) dmk = min(dmk, fkey(Dk.hi));  // rows outside Q sit at E0' - chi = 1e8
         dfl gk;
         if (!shifted) {
           gk = df_rcp(Dk);

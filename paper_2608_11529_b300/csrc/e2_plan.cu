@@ -2,6 +2,7 @@
 // workspace layout of a problem; the C entry points that create and query it.
 #include "e2_host.h"
 
+#include <cstring>
 #include <new>
 #include <queue>
 
@@ -320,6 +321,7 @@ e2_status build_plan(e2_problem* P) {
   for (int c = 0; c < E2_NCLASS; ++c) {
     P->M[c] = (P->list_of[c] >= 0) ? rows[c] : 0;
     P->q_per_class[c] = (P->list_of[c] >= 0) ? (double)rows[c] * (double)P->lists[P->list_of[c]].n : 0.0;
+    P->q_full[c] = P->q_per_class[c];
   }
   auto pad8 = [](int k) { return (k + 7) / 8 * 8; };
   P->KpT = pad8(P->na);
@@ -349,6 +351,10 @@ e2_status build_plan(e2_problem* P) {
   P->o_plan = ws.take(0);
   P->o_cc = ws.take(sizeof(int32_t) * std::max(1, P->ncc));
   P->o_vc = ws.take(sizeof(int32_t) * std::max(1, P->nvc));
+  P->o_xc = ws.take(sizeof(int32_t) * std::max(1, P->ncc));
+  P->o_xv = ws.take(sizeof(int32_t) * std::max(1, P->nvc));
+  P->xc.assign(std::max(1, P->ncc), -1);
+  P->xv.assign(std::max(1, P->nvc), -1);
   for (HostList& L : P->lists) {
     L.o_key = ws.take(sizeof(int64_t) * P->nkeys);
     L.o_patoff = ws.take(sizeof(int64_t) * L.pats.size());
@@ -688,6 +694,8 @@ e2_status build_plan(e2_problem* P) {
   auto rel = [&](size_t o) { return o - P->o_plan; };
   put(P->plan_blob, rel(P->o_cc), P->cc.data(), P->cc.size());
   put(P->plan_blob, rel(P->o_vc), P->vc.data(), P->vc.size());
+  put(P->plan_blob, rel(P->o_xc), P->xc.data(), P->xc.size());
+  put(P->plan_blob, rel(P->o_xv), P->xv.data(), P->xv.size());
   for (HostList& L : P->lists) {
     put(P->plan_blob, rel(L.o_key), L.key2off.data(), L.key2off.size());
     put(P->plan_blob, rel(L.o_patoff), L.patoff.data(), L.patoff.size());
@@ -806,6 +814,57 @@ e2_status e2_class_tiles_copy(const e2_problem* P, int cls, int32_t* perm, int32
   std::copy(cp.perm.begin(), cp.perm.end(), perm);
   std::copy(cp.tdesc.begin(), cp.tdesc.end(), tdesc);
   std::copy(cp.klist.begin(), cp.klist.end(), klist);
+  return E2_OK;
+}
+
+e2_status e2_set_external_das(e2_problem* P, int n_cdas, const int32_t* core_size, const int32_t* core_max_holes,
+                              int n_vdas, const int32_t* virt_size, const int32_t* virt_max_particles) {
+  if (!P || n_cdas < 0 || n_vdas < 0 || n_cdas > 64 || n_vdas > 64) return E2_ERR_INVALID_ARG;
+  if ((n_cdas && (!core_size || !core_max_holes)) || (n_vdas && (!virt_size || !virt_max_particles)))
+    return E2_ERR_INVALID_ARG;
+  // subspace of every core / virtual spinor (consecutive blocks in global order)
+  std::vector<int32_t> csub(P->d.n_core, -1), vsub(P->d.n_virt, -1);
+  int64_t at = 0;
+  for (int s = 0; s < n_cdas; ++s) {
+    if (core_size[s] < 1 || core_max_holes[s] < 1 || at + core_size[s] > P->d.n_core) return E2_ERR_INVALID_ARG;
+    for (int k = 0; k < core_size[s]; ++k) csub[at++] = core_max_holes[s] == 1 ? s : -1;
+  }
+  if (n_cdas && at != P->d.n_core) return E2_ERR_INVALID_ARG;
+  at = 0;
+  for (int s = 0; s < n_vdas; ++s) {
+    if (virt_size[s] < 1 || virt_max_particles[s] < 1 || at + virt_size[s] > P->d.n_virt) return E2_ERR_INVALID_ARG;
+    for (int k = 0; k < virt_size[s]; ++k) vsub[at++] = virt_max_particles[s] == 1 ? s : -1;
+  }
+  if (n_vdas && at != P->d.n_virt) return E2_ERR_INVALID_ARG;
+  bool any = false;
+  for (int i = 0; i < P->ncc; ++i) {
+    P->xc[i] = csub[P->cc[i]];
+    any = any || P->xc[i] >= 0;
+  }
+  for (int a = 0; a < P->nvc; ++a) {
+    P->xv[a] = vsub[P->vc[a] - P->nocc];
+    any = any || P->xv[a] >= 0;
+  }
+  P->ext_das = any;
+  auto rel = [&](size_t o) { return o - P->o_plan; };
+  std::memcpy(P->plan_blob.data() + rel(P->o_xc), P->xc.data(), sizeof(int32_t) * P->xc.size());
+  std::memcpy(P->plan_blob.data() + rel(P->o_xv), P->xv.data(), sizeof(int32_t) * P->xv.size());
+  // class sizes: allowed hole pairs times allowed particle pairs times strings
+  int64_t hp = 0, pp = 0;  // pairs of one limited subspace
+  for (int i = 0; i < P->ncc; ++i)
+    for (int j = i + 1; j < P->ncc; ++j) hp += P->xc[i] >= 0 && P->xc[i] == P->xc[j];
+  for (int a = 0; a < P->nvc; ++a)
+    for (int b = a + 1; b < P->nvc; ++b) pp += P->xv[a] >= 0 && P->xv[a] == P->xv[b];
+  const double hc = (double)(P->ncp - hp) / std::max<double>((double)P->ncp, 1.0);
+  const double vc = (double)(P->nvp - pp) / std::max<double>((double)P->nvp, 1.0);
+  const double frac[E2_NCLASS] = {1, 1, vc, 1, 1, vc, hc, hc, hc * vc};
+  for (int c = 0; c < E2_NCLASS; ++c) P->q_per_class[c] = P->q_full[c] * frac[c];
+  for (int c : {2, 5, 6, 7, 8})  // exact integers
+    if (P->list_of[c] >= 0)
+      P->q_per_class[c] = (double)(c == 2 ? P->nvp - pp : c == 5 ? (int64_t)P->ncc * (P->nvp - pp)
+                                   : c == 6 ? P->ncp - hp : c == 7 ? (P->ncp - hp) * (int64_t)P->nvc
+                                                          : (P->ncp - hp) * (P->nvp - pp)) *
+                          (double)P->lists[P->list_of[c]].n;
   return E2_OK;
 }
 

@@ -102,10 +102,11 @@ def p_address(prob, act_bits):
     return addr
 
 
-def brute_e2(prob, c, b=0.0):
+def brute_e2(prob, c, b=0.0, allowed=None):
     """E2 per root and class from the Fock-space matrix: Q = determinants of the
     right electron count, not in P, touching no frozen spinor, within two
-    substitutions of some P determinant."""
+    substitutions of some P determinant (and, if given, allowed(K) true for
+    the Fock index K)."""
     n, nc, na = prob.n, prob.n_core, prob.n_act
     a0, v0 = nc, nc + na
     ntot = nc + prob.n_elec
@@ -140,6 +141,8 @@ def brute_e2(prob, c, b=0.0):
             continue
         rank = min(bin(L & ~K).count("1") for L in Pidx)
         if rank > 2:
+            continue
+        if allowed is not None and not allowed(K):
             continue
         h = nc - bin(K & core_mask).count("1")
         p = bin(K >> v0).count("1")

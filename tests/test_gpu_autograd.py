@@ -43,4 +43,4 @@ def test_autograd_function_gives_the_adjoint_gradients():
         d1 = (f(1 + eps) - f(1 - eps)) / (2 * eps)
         d2 = (f(1 + eps / 2) - f(1 - eps / 2)) / eps
     num = (4 * d2 - d1) / 3
-    assert abs(float(gl) - num) <= 1e-6 * abs(num) + 1e-12, (float(gl), num)
+    assert abs(float(gl) - num) <= 1e-7 * abs(num) + 1e-12, (float(gl), num)

@@ -133,10 +133,10 @@ def test_fullsize_gradient_matches_central_differences(run):
         return (4 * d2 - d1) / 3
 
     num_l = richardson(lambda e: f(lam=t["lam"] + e), 1e-2)
-    assert abs(dl - num_l) <= 1e-6 * abs(num_l) + 1e-12, (dl, num_l)
+    assert abs(dl - num_l) <= 1e-7 * abs(num_l) + 1e-12, (dl, num_l)
     d = _herm(np.random.default_rng(11), tuple(t["h"].shape))
     d /= np.linalg.norm(d)
     dd = torch.from_numpy(d).to(t["h"].device)
     num_h = richardson(lambda e: f(h=t["h"] + e * dd), 1e-3)
     ana_h = float(np.real(np.vdot(gh, d)))
-    assert abs(ana_h - num_h) <= 1e-6 * max(abs(num_h), 1e-3 * np.abs(gh).max()), (ana_h, num_h)
+    assert abs(ana_h - num_h) <= 1e-7 * max(abs(num_h), 1e-3 * np.abs(gh).max()), (ana_h, num_h)

@@ -67,3 +67,25 @@ def test_backward_refuses_a_sharded_problem():
         plan.value_and_grad(**t)
     plan.set_shard(0, 1)
     plan.value_and_grad(**t)
+
+
+def test_checkpointed_run_resumes_bitwise(tmp_path):
+    """A run in 4 resumable parts, stopped after 2 and resumed by a fresh plan
+    (as a new process would), gives E2 bitwise equal to the one-piece
+    forward; a directory of another run is refused."""
+    import paper_2608_11529_b300 as e2
+    prob = CASES["das_three_two_roots"]()
+    c, _ = Oracle(prob).ground_state(prob.n_roots)
+    plan = e2.E2Problem.from_problem(prob)
+    t = e2.device_inputs(prob, c)
+    ref = [x.clone() for x in plan.forward(**t)]
+    path = str(tmp_path / "ckpt")
+    assert plan.checkpointed_forward(path, **t, pieces=4, max_pieces=2, tag="das3") is None
+    fresh = e2.E2Problem.from_problem(prob)
+    got = fresh.checkpointed_forward(path, **t, pieces=4, tag="das3")
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(got, ref))
+    again = e2.E2Problem.from_problem(prob).checkpointed_forward(path, **t, pieces=4, tag="das3")  # all saved
+    assert all(torch.equal(a, b) for a, b in zip(again, ref))
+    with pytest.raises(e2.E2Error):
+        fresh.checkpointed_forward(path, **t, pieces=3, tag="das3")

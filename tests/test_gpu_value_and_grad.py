@@ -76,4 +76,4 @@ def test_gradient_matches_central_differences(setup, key):
         eps = {"h": 1e-3, "c": 1e-3, "B_c": 1e-3, "B_x": 1e-2}[key]
         numeric = _fd(plan, t, seed, key, torch.from_numpy(d).to(t[key].device), eps)
         scale = max(abs(numeric), 1e-3 * np.abs(g).max())
-    assert abs(analytic - numeric) <= 1e-6 * scale, (key, analytic, numeric)
+    assert abs(analytic - numeric) <= 1e-7 * scale, (key, analytic, numeric)
