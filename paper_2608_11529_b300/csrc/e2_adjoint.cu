@@ -197,12 +197,16 @@ k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_
 constexpr int kTileRows = 80;
 __global__ void __launch_bounds__(256, 1)
 k_zgemm_gd_tiles(ColTiles ctl, const double2* __restrict__ W, int Kp, const double2* __restrict__ T, int64_t N,
-                 int64_t Mc, double2* __restrict__ GDc, int beta, int64_t kseg, int64_t czs, int conjT) {
+                 int64_t Mc, double2* __restrict__ GDc, int beta, int64_t kseg, int64_t czs, int conjT,
+                 int64_t t_ld) {
   const int j = blockIdx.y;
   const int4 td = ctl.tdesc[j];
   if ((int64_t)blockIdx.x * kTileRows >= td.y) return;
-  zgemm_body<64, kTileRows, 4>(64, td.y, Mc, T, 1, N, conjT, W, Kp, 1, 0, GDc + (int64_t)td.x * 64, 1, 64, beta, kseg, czs,
-                               -1, 0, blockIdx.x, blockIdx.z, ctl.perm + (int64_t)j * 64, nullptr, ctl.klist + td.x);
+  // T in tile order (t_ld > 0): the tile's 64 columns are contiguous in each row
+  const double2* A = t_ld ? T + (int64_t)j * 64 : T;
+  zgemm_body<64, kTileRows, 4>(64, td.y, Mc, A, 1, t_ld ? t_ld : N, conjT, W, Kp, 1, 0, GDc + (int64_t)td.x * 64, 1, 64,
+                               beta, kseg, czs, -1, 0, blockIdx.x, blockIdx.z,
+                               t_ld ? nullptr : ctl.perm + (int64_t)j * 64, nullptr, ctl.klist + td.x);
 }
 
 // Gamma_W of a column-tiled class in compacted form (tile j = blockIdx.z):
@@ -210,12 +214,14 @@ k_zgemm_gd_tiles(ColTiles ctl, const double2* __restrict__ W, int Kp, const doub
 // (T itself when conjT == 0)
 __global__ void __launch_bounds__(256, 1)
 k_zgemm_gw_tiles(ColTiles ctl, const double2* __restrict__ T, int64_t N, int64_t Mc, int64_t krows,
-                 double2* __restrict__ GWc, int conjT) {
+                 double2* __restrict__ GWc, int conjT, int64_t t_ld) {
   const int j = blockIdx.z;
   const int4 td = ctl.tdesc[j];
   if ((int64_t)blockIdx.y * kTileRows >= td.y) return;
-  zgemm_body<64, kTileRows, 4>(Mc, td.y, 64, T, N, 1, conjT, ctl.Dc + (int64_t)td.x * 64, 1, 64, 0, GWc + td.x, krows, 1,
-                               0, 64, 0, -1, blockIdx.x, blockIdx.y, 0, nullptr, ctl.perm + (int64_t)j * 64, nullptr);
+  const double2* A = t_ld ? T + (int64_t)j * 64 : T;  // tile order: contiguous row segments
+  zgemm_body<64, kTileRows, 4>(Mc, td.y, 64, A, t_ld ? t_ld : N, 1, conjT, ctl.Dc + (int64_t)td.x * 64, 1, 64, 0,
+                               GWc + td.x, krows, 1, 0, 64, 0, -1, blockIdx.x, blockIdx.y, 0, nullptr,
+                               t_ld ? nullptr : ctl.perm + (int64_t)j * 64, nullptr);
 }
 
 // GD[klist[koff + k]][perm[64 j + c]] += GDc[(koff + k) * 64 + c], k < ktrue (one block per tile)
@@ -340,14 +346,19 @@ k_dgemm(int64_t M, int64_t N, int64_t K, const double* __restrict__ A, int64_t s
 }
 
 // Hocc[r][t] = sum_A H[r][A] [t in A]  (one block per row of the chunk)
-__global__ void k_hocc(const double* __restrict__ H, DevList Ls, int na, double* __restrict__ Hocc) {
+__global__ void k_hocc(const double* __restrict__ H, DevList Ls, int na, double* __restrict__ Hocc,
+                       const int32_t* __restrict__ perm, int64_t ld) {
   __shared__ double sh[32];
   const int64_t r = blockIdx.x;
   double acc[64];
   for (int t = 0; t < na; ++t) acc[t] = 0.0;
-  for (int64_t g = threadIdx.x; g < Ls.n; g += blockDim.x) {
-    const double h = H[r * Ls.n + g];
-    for (uint64_t x = Ls.str[g]; x; x &= x - 1) acc[__ffsll((long long)x) - 1] += h;
+  // perm: H in tile order ([r][slot], slot -> string perm[slot], -1 padding), row stride ld
+  const int64_t ncol = perm ? ld : Ls.n;
+  for (int64_t g = threadIdx.x; g < ncol; g += blockDim.x) {
+    const int64_t a = perm ? (int64_t)perm[g] : g;
+    if (a < 0) continue;
+    const double h = H[r * ncol + g];
+    for (uint64_t x = Ls.str[a]; x; x &= x - 1) acc[__ffsll((long long)x) - 1] += h;
   }
   for (int t = 0; t < na; ++t) {
     const double v = block_sum(acc[t], sh);
@@ -490,11 +501,16 @@ __global__ void k_amarg(DevList Ls, const double* __restrict__ hA, double* __res
 
 // out[e] = sum_A conj(T[e][A]) d[A]  (one block per row)
 __global__ void k_rowdot(const double2* __restrict__ T, const double2* __restrict__ d, int64_t N,
-                         double2* __restrict__ out) {
+                         double2* __restrict__ out, const int32_t* __restrict__ perm, int64_t ld) {
   __shared__ double sh[32];
   const int64_t e = blockIdx.x;
   double2 acc = make_double2(0.0, 0.0);
-  for (int64_t A = threadIdx.x; A < N; A += blockDim.x) acc = cfma(cconj(T[e * N + A]), d[A], acc);
+  // perm: T in tile order (slot -> string perm[slot], -1 padding), row stride ld
+  const int64_t ncol = perm ? ld : N;
+  for (int64_t s = threadIdx.x; s < ncol; s += blockDim.x) {
+    const int64_t A = perm ? (int64_t)perm[s] : s;
+    if (A >= 0) acc = cfma(cconj(T[e * ncol + s]), d[A], acc);
+  }
   const double re = block_sum(acc.x, sh), im = block_sum(acc.y, sh);
   if (threadIdx.x == 0) out[e] = make_double2(re, im);
 }

@@ -313,17 +313,17 @@ void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st) {
 // Gamma_D of a column-tiled class in compacted form, GDc (+)= per tile
 // W[:, klist]^T conj(T[:, perm]) over the chunk's Mc rows, split-K as zgemm.
 void zgemm_gd_tiles(cudaStream_t st, const ColPlan& cp, const ColTiles& ctl, const double2* W, int Kp,
-                    const double2* T, int64_t N, int64_t Mc, double2* GDc, int beta, int conjT) {
+                    const double2* T, int64_t N, int64_t Mc, double2* GDc, int beta, int conjT, int64_t t_ld) {
   const int64_t czs = cp.krows * 64;
   const int nseg = splitk_segments(cp.gd_ctas, Mc, 16 * (size_t)czs);
   const int64_t kseg = (Mc + nseg - 1) / nseg;
   dim3 grid((unsigned)((cp.maxklen + 79) / 80), (unsigned)cp.tiles, (unsigned)nseg);
   if (nseg == 1) {
-    (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, GDc, beta, kseg, 0, conjT), ++g_launches);
+    (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, GDc, beta, kseg, 0, conjT, t_ld), ++g_launches);
     return;
   }
   double2* part = (double2*)g_splitk;
-  (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, part, 0, kseg, czs, conjT), ++g_launches);
+  (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, part, 0, kseg, czs, conjT, t_ld), ++g_launches);
   (k_zacc<<<blocks(czs), 256, 0, st>>>(part, nseg, czs, cp.krows, 64, GDc, 64, 1, beta), ++g_launches);
 }
 

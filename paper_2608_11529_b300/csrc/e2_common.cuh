@@ -88,6 +88,12 @@ struct AdjOut {
   double* part;
   int64_t rt;
   int t_df;  // sliced adjoint only: T as float-float quadruples (its consumers slice them)
+  // FP64 adjoint of a column-tiled class: T and Hm in tile column order,
+  // element (row, tile j, column c) at [row - m_base][64 j + c] (row stride
+  // t_ld = 64 x tiles; padding columns hold 0), so that the tile products
+  // read contiguous row segments; otherwise [row - m_base][string] (stride N)
+  int t_tile;
+  int64_t t_ld;
   // forward mode only (T == nullptr): when set, the tile also writes each
   // coupling's V and D at [local row][local column] (64 x 64), for a
   // per-coupling check of one tile

@@ -198,6 +198,11 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
                          (!want_B || zgemm_sliced_bytes(Mc, Kp, N, OZ_ADJ_S) <= P->bOz_bytes);
         AdjOut adj{(double2*)B(P->o_bT), want_B ? (double*)B(P->o_bHm) : nullptr, (double*)B(P->o_bHrow),
                    (double*)B(P->o_bHcol), (double*)B(P->o_bScalT), m0, Mc, s, g1, part_adj, rt, tdf ? 1 : 0};
+        // FP64 products over column tiles read T (and Hm) in tile column order
+        const bool tile_order = tiled && !P->use_oz[cls];
+        adj.t_tile = tile_order ? 1 : 0;
+        adj.t_ld = tile_order ? 64 * cp.tiles : 0;
+        const int32_t* tperm = tile_order ? ctl.perm : nullptr;
         dim3 grid((unsigned)((Mc + 63) / 64), (unsigned)ct);
         if (P->use_oz[cls])  // the sliced contraction in its adjoint mode (plain columns)
           launch_class_oz_adj(st, cls, oz_operands(P, ws, r, cls), M, N, (const RowInfo*)(ws + P->o_rows[cls]),
@@ -216,7 +221,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         }
         // Gamma_D[x][A] += sum_e W[e][x] conj(T[e][A]) (split over the rows of the chunk)
         if (tiled)
-          zgemm_gd_tiles(st, cp, ctl, W + m0 * Kp, (int)Kp, adj.T, N, Mc, (double2*)B(P->o_bGDc), m0 > 0);
+          zgemm_gd_tiles(st, cp, ctl, W + m0 * Kp, (int)Kp, adj.T, N, Mc, (double2*)B(P->o_bGDc), m0 > 0, 1, adj.t_ld);
         else if (slg && zgemm_sliced(st, N, Kp, Mc, adj.T, 1, N, 1, W + m0 * Kp, Kp, 1, 0, GDfor[cls], 1, N, 1, -1,
                                      (unsigned char*)B(P->o_bOz), P->bOz_bytes, 0, false, OZ_ADJ_S, tdf))
           ;  // Gamma_D^T = conj(T)^T W: T is the row operand (sliced without duplication)
@@ -225,12 +230,13 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         else
           zgemm(st, N, Kp, Mc, adj.T, 1, N, 1, W + m0 * Kp, Kp, 1, 0, GDfor[cls], 1, N, 1, 16);
         if (cls == 4)
-          (k_rowdot<<<(unsigned)Mc, 256, 0, st>>>(adj.T, T.DTDU, N, (double2*)B(P->o_bRowdot) + m0), ++g_launches);
+          (k_rowdot<<<(unsigned)Mc, 256, 0, st>>>(adj.T, T.DTDU, N, (double2*)B(P->o_bRowdot) + m0, tperm, adj.t_ld),
+           ++g_launches);
         if (want_B) {  // Gamma_W = conj(T) D^T and the per-row occupation sums of eta
           double2* GW = (double2*)B(P->o_bGW[cls]) + m0 * Kp;
           if (tiled) {  // per tile over its compacted rows, then summed per table row in tile order
             dim3 g((unsigned)((Mc + 63) / 64), (unsigned)((cp.maxklen + 79) / 80), (unsigned)cp.tiles);
-            (k_zgemm_gw_tiles<<<g, 256, 0, st>>>(ctl, adj.T, N, Mc, cp.krows, (double2*)B(P->o_bGWc), 1),
+            (k_zgemm_gw_tiles<<<g, 256, 0, st>>>(ctl, adj.T, N, Mc, cp.krows, (double2*)B(P->o_bGWc), 1, adj.t_ld),
              ++g_launches);
             (k_gw_reduce<<<blocks(Mc * Kp), 256, 0, st>>>(ctl.tdesc, (const int32_t*)(ws + cp.o_pos), cp.tiles,
                                                          (int)Kp, (const double2*)B(P->o_bGWc), cp.krows, Mc, GW,
@@ -243,7 +249,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           if (P->use_oz[cls])  // eta came as float-float pairs from the sliced adjoint
             launch_hocc_df(st, (const float2*)adj.Hm, L, na, Mc, Hocc + m0 * na);
           else
-            (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na), ++g_launches);
+            (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na, tperm, adj.t_ld), ++g_launches);
         }
       }
       if (tiled)
@@ -352,7 +358,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       //   Gamma_X[row][...][x] = sum_B Tsh[row][B] D[x][B]            (integral coefficients)
       if (want_B) {
         (k_rowsum_wide<<<(unsigned)nrow, 256, 0, st>>>(Hg, L.n, 0, hsum), ++g_launches);
-        (k_hocc<<<(unsigned)nrow, 256, 0, st>>>(Hg, L, na, Hocc), ++g_launches);
+        (k_hocc<<<(unsigned)nrow, 256, 0, st>>>(Hg, L, na, Hocc, nullptr, 0), ++g_launches);
         zpair(cls, hsum, Hocc);
         (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
       }
@@ -388,7 +394,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
             double2* GXr = GX + (int64_t)r0 * S * nx_;
             if (tl) {
               dim3 g((unsigned)((k + 63) / 64), (unsigned)((cpt.maxklen + 79) / 80), (unsigned)cpt.tiles);
-              (k_zgemm_gw_tiles<<<g, 256, 0, st>>>(ctt, Tsh, nb, k, cpt.krows, (double2*)B(P->o_bGWc), 0),
+              (k_zgemm_gw_tiles<<<g, 256, 0, st>>>(ctt, Tsh, nb, k, cpt.krows, (double2*)B(P->o_bGWc), 0, 0),
                ++g_launches);
               // written, not accumulated: gx_beta is set only for class (0,0),
               // one row, whose target is still zero here

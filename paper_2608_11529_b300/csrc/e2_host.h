@@ -269,7 +269,8 @@ void zgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, i
 e2_status setup_common(e2_problem* P, const e2_inputs* in, unsigned char* ws, cudaStream_t st, bool upload = true);
 void setup_classes(e2_problem* P, unsigned char* ws, cudaStream_t st);
 void zgemm_gd_tiles(cudaStream_t st, const ColPlan& cp, const ColTiles& ctl, const double2* W, int Kp,
-                    const double2* T, int64_t N, int64_t Mc, double2* GDc, int beta, int conjT = 1);
+                    const double2* T, int64_t N, int64_t Mc, double2* GDc, int beta, int conjT = 1,
+                    int64_t t_ld = 0);
 void prepare_root(e2_problem* P, unsigned char* ws, cudaStream_t st, const double2* c, int r);
 void launch_reduce(e2_problem* P, unsigned char* ws, cudaStream_t st, double* E2, double* E2_class, double* E0);
 

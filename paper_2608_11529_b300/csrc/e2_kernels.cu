@@ -714,7 +714,15 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
 #pragma unroll
         for (int hc = 0; hc < 2; ++hc) {
           const int64_t col = sCol[wn * 16 + ni * 8 + 2 * tq + hc];
-          if (col < 0) continue;
+          const int64_t slot = adj.t_tile ? (row - adj.m_base) * adj.t_ld + n0 + wn * 16 + ni * 8 + 2 * tq + hc
+                                          : (row - adj.m_base) * N + col;
+          if (col < 0) {
+            if (adj.T && adj.t_tile) {  // padding column of a tile-ordered amplitude row
+              adj.T[slot] = make_double2(0.0, 0.0);
+              if (adj.Hm) adj.Hm[slot] = 0.0;
+            }
+            continue;
+          }
           const int e = hr * 2 + hc, kk = ni * 2 + hc;
           const double vr = t1[mi][ni][e] - t2[mi][ni][e];
           const double vi = t3[mi][ni][e] - t1[mi][ni][e] - t2[mi][ni][e];
@@ -731,9 +739,9 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
             double gk, hk;
             en_derivs_r(v2 * inv_n, Dk, b, rq[kk], gk, hk);
             const double w = s2n * gk;  // t = s (2/n) g V
-            adj.T[(row - adj.m_base) * N + col] = make_double2(w * vr, w * vi);
+            adj.T[slot] = make_double2(w * vr, w * vi);
             hk *= adj.s;
-            if (adj.Hm) adj.Hm[(row - adj.m_base) * N + col] = hk;
+            if (adj.Hm) adj.Hm[slot] = hk;
             rowp[mi][hr] += hk;
             colp[ni][hc] += hk;
             acc += hk;

@@ -84,9 +84,11 @@ __global__ void k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* A, int
                           const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn,
                           int beta, int64_t kseg, int64_t czs, int64_t lower);
 __global__ void k_zgemm_gd_tiles(ColTiles ctl, const double2* W, int Kp, const double2* T, int64_t N, int64_t Mc,
-                                 double2* GDc, int beta, int64_t kseg, int64_t czs, int conjT);
+                                 double2* GDc, int beta, int64_t kseg, int64_t czs, int conjT,
+                                 int64_t t_ld);
 __global__ void k_zgemm_gw_tiles(ColTiles ctl, const double2* T, int64_t N, int64_t Mc, int64_t krows, double2* GWc,
-                                 int conjT);
+                                 int conjT,
+                                 int64_t t_ld);
 __global__ void k_gd_scatter(ColTiles ctl, const double2* GDc, int64_t N, double2* GD);
 __global__ void k_gw_reduce(const int4* tdesc, const int32_t* pos, int64_t tiles, int Kp, const double2* GWc,
                             int64_t krows, int64_t Mc, double2* GW, int nxo, int64_t ldo);
@@ -98,7 +100,8 @@ __global__ void k_colsum(const double* in, int64_t nrow, int64_t ncol, int acc, 
 __global__ void k_scalsum(const double* in, int64_t n, double* scal_out);
 __global__ void k_xmarg(const RowInfo* rows, const double* hsum, int64_t M, int nx, double* Nx);
 __global__ void k_amarg(DevList Ls, const double* hA, double* Nt);
-__global__ void k_rowdot(const double2* T, const double2* d, int64_t N, double2* out);
+__global__ void k_rowdot(const double2* T, const double2* d, int64_t N, double2* out, const int32_t* perm,
+                         int64_t ld);
 __global__ void k_fock11(const double2* rowdot, DevSpace sp, double2* Gf);
 __global__ void k_class22_bwd(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
                               const double* G, const double* E0p, double b, int nvb, double s, const double2* g1,
@@ -128,7 +131,8 @@ __global__ void k_hbar(DevSpace sp, const double2* Gf, const double* Nd, double2
 __global__ void k_dgemm(int64_t M, int64_t N, int64_t K, const double* A, int64_t sam, int64_t sak, const double* B,
                         int64_t sbk, int64_t sbn, double* C, int64_t ldc, int beta, int64_t kseg, int64_t czs);
 __global__ void k_dacc(const double* part, int nseg, int64_t ps, int64_t count, double* out);
-__global__ void k_hocc(const double* H, DevList Ls, int na, double* Hocc);
+__global__ void k_hocc(const double* H, DevList Ls, int na, double* Hocc, const int32_t* perm,
+                       int64_t ld);
 __global__ void k_tmarg(const double* in, int64_t nb, int64_t nt, int w, int arity, int ns, double sign, int acc,
                         double* out, int64_t ob, int64_t os, int64_t oc);
 __global__ void k_pairplace(const double* in, int ns, double* out, int64_t ldo);

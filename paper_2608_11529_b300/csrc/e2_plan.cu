@@ -546,13 +546,14 @@ e2_status build_plan(e2_problem* P) {
       const int64_t Mc = P->M[c], Nc = lsize(c);
       P->chunk_rows[c] = 0;
       if (Mc == 0 || Nc == 0) continue;
-      int64_t rows_fit = (int64_t)(tbudget / (16 * (size_t)Nc)) / 64 * 64;
+      const int64_t Nt = (Nc + 63) / 64 * 64;  // amplitude rows in tile order are 64 x tiles wide
+      int64_t rows_fit = (int64_t)(tbudget / (16 * (size_t)Nt)) / 64 * 64;
       if (P->cplan[c].built)  // compacted Gamma_W of a chunk: rows x compacted columns
         rows_fit = std::min<int64_t>(rows_fit, (int64_t)(gwbudget / (16 * (size_t)P->cplan[c].krows)) / 64 * 64);
       rows_fit = std::max<int64_t>(64, rows_fit);
       P->chunk_rows[c] = std::min<int64_t>(rows_fit, (Mc + 63) / 64 * 64);
       const int64_t ct = (Nc + 63) / 64;
-      tmax = std::max(tmax, (size_t)16 * P->chunk_rows[c] * Nc);
+      tmax = std::max(tmax, (size_t)16 * P->chunk_rows[c] * Nt);
       if (P->cplan[c].built) {
         gdc = std::max(gdc, (size_t)16 * P->cplan[c].krows * 64);
         gwc = std::max(gwc, (size_t)16 * P->chunk_rows[c] * P->cplan[c].krows);
@@ -611,7 +612,7 @@ e2_status build_plan(e2_problem* P) {
       const int64_t Mc = P->M[c], Nc = lsize(c);
       if (Mc == 0 || Nc == 0) continue;
       P->o_bGW[c] = ws.take(16 * (size_t)Mc * P->Kp[c]);
-      hm = std::max(hm, (size_t)8 * P->chunk_rows[c] * Nc);
+      hm = std::max(hm, (size_t)8 * P->chunk_rows[c] * ((Nc + 63) / 64 * 64));
       hocc = std::max(hocc, (size_t)8 * Mc * P->na);
     }
     const int64_t M22 = P->ncp * P->nvp;

@@ -11,10 +11,12 @@ indices), and |D_gpu - D| <= 1e-10 Eh (the E0 bar).  Row and string orders
 are the documented ones (rows_ref, strings_ref); a column-tiled class maps its
 tile columns through the plan's column map.
 
-Cases: the small CAS / DAS / frozen / two-root shapes, and sampled tiles of
-the full-size Ne-shaped DCG and Ar-shaped DCB DAS workloads (the benchmark's
-launch configurations) with a seeded reference vector concentrated on the
-P determinant of address 0 (no eigen-solve on either side)."""
+Cases: the small CAS / DAS / frozen / two-root shapes, sampled tiles of the
+full-size Ne-shaped DCG and Ar-shaped DCB DAS workloads (the benchmark's
+launch configuration), and the Kr/Xe-shaped active space CAS(8e,24) with a
+reduced core and virtual space, the last three with a seeded reference
+vector concentrated on the P determinant of address 0 (no eigen-solve on
+either side)."""
 import numpy as np
 import pytest
 
@@ -145,3 +147,13 @@ def _concentrated_c(prob, seed):
 def test_single_couplings_at_full_size(config):
     prob = make_problem(config)
     assert _run(prob, _concentrated_c(prob, 17), tiles_per_class=3) > 20000
+
+
+def test_single_couplings_at_the_kr_xe_active_shape():
+    """The Kr- and Xe-shaped active space CAS(8e,24) (735,471 reference
+    determinants, 1.96 million strings in the (2,0) list) with a reduced core
+    (4) and virtual (16) space and factor set (8 + 4): sampled tiles of every
+    dense class and samples of the gather classes."""
+    prob = tiny_problem(4, 24, 16, 8, Lc=8, Lx=4, ham="DCB", x_scale=4e-3, core_ends=(-1280.0, -2.5),
+                        virt_ends=(0.1, 800.0), seed=68)
+    assert _run(prob, _concentrated_c(prob, 19), tiles_per_class=3) > 20000
