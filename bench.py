@@ -290,9 +290,11 @@ def run_reference(args):
 
 def run_batch(args):
     """Batched evidence run: the 3 Hamiltonians x 3 frozen cutoffs of a workload
-    shape (all roots of each) in one e2_batch_forward, captured in a CUDA
-    graph and replayed, against the same jobs' e2_forward calls one after
-    another.  Prints one JSON line with "mode": "batch"."""
+    shape (all roots of each) in one e2_batch_forward -- every class of every
+    job-root in one persistent launch, or one per group of --roots-per-launch
+    roots -- captured in a CUDA graph and replayed, against the same jobs'
+    e2_forward calls one after another.  Prints one JSON line with
+    "mode": "batch"."""
     import torch
     import paper_2608_11529_b300 as e2
     from e2_inputs import make_problem
@@ -345,7 +347,7 @@ def run_batch(args):
     ms_seq = a.elapsed_time(z) / args.steps
     ref = [(E2, E2c) for E2, E2c, _ in ref]
     torch.cuda.empty_cache()   # the batch holds all jobs' layouts in one workspace
-    batch = e2.E2Batch([p for *_, p, _ in jobs])
+    batch = e2.E2Batch([p for *_, p, _ in jobs], roots_per_launch=args.roots_per_launch)
     batch.prepare(dev)
     inputs = [t for *_, t in jobs]
     for _ in range(args.warmup):
@@ -376,7 +378,11 @@ def run_batch(args):
                        "couplings_per_step": couplings},
             "sequential_ms": ms_seq, "sequential_couplings_per_s": couplings / (ms_seq * 1e-3),
             "graph_replay": True, "bitwise_equal_to_sequential": same,
-            "gpu_launches": sum(p.launch_count() for *_, p, _ in jobs)}
+            "job_roots": sum(p.n_roots for *_, p, _ in jobs),
+            "persistent_launches": (-(-max(p.n_roots for *_, p, _ in jobs) // args.roots_per_launch)
+                                    if args.roots_per_launch else 1),
+            "batch_workspace_gb": batch.workspace_bytes / 1e9,
+            "gpu_launches": batch.launch_count()}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -518,6 +524,34 @@ def _roofline(prob, plan, fw, peak_dmma, peak_dfma):
     roof.update({"ms_per_step": t_ms, "launches_per_step": len(classes),
                  "couplings_per_s": couplings / (t_ms * 1e-3), "kernel_ms_per_step": ksum})
     return roof
+
+
+def _per_class(prob, plan, fw, peak_dmma, peak_dfma):
+    """Per class: couplings, event-timed ms, couplings/s; the dense classes'
+    achieved FP64 tensor rate (8 K real flops per coupling, and the executed
+    6 K' of the compacted Gauss products) against the measured DMMA peak;
+    class (2,2)'s FP64 ALU rate (7 FP64 arithmetic instructions per
+    coupling: two adds for the denominator, a quarter of the 15-operation
+    four-way inversion, one FMA; compares and conversions not counted, so the
+    fraction is a lower bound) against the measured FP64 FMA instruction
+    rate."""
+    out = {}
+    for k in fw["present"]:
+        ms, q = fw["ktime"][k], float(plan.q_per_class[k]) * plan.n_roots
+        row = {"couplings": q, "ms": ms, "couplings_per_s": q / (ms * 1e-3) if ms > 0 else None}
+        if k in GEMM_CLASSES and not plan.contraction(k)[0] and ms > 0:
+            alg = 8.0 * q * _kdim(prob, k) / (ms * 1e-3) / 1e12
+            tiles, krows, used = plan.class_tiles(k)
+            kx = krows * 64 / (tiles * 64) if used and tiles else _kpad(prob, k)
+            exe = 6.0 * q * kx / (ms * 1e-3) / 1e12
+            row.update({"kernel": "k_class_gemm", "algorithmic_tflops": alg, "executed_tflops": exe,
+                        "executed_frac_of_dmma_peak": exe / peak_dmma})
+        elif k == 8 and not plan.contraction(8)[0] and ms > 0:
+            ops = 7.0 * q / (ms * 1e-3)
+            row.update({"kernel": "k_class22", "fp64_instructions_per_s": ops,
+                        "frac_of_fp64_fma_instruction_peak": ops / (peak_dfma * 1e12 / 2.0)})
+        out[CLASS_NAMES[k]] = row
+    return out
 
 
 def _timed_fwd_bwd(plan, t, steps, warmup, stream, ws, dist, dev):
@@ -733,7 +767,8 @@ def run(args):
                            "E0": float(fw["E0"].cpu()[0]),
                            "parallelism": (f"external space sharded over {ws} GPUs (NCCL sum of the partials)"
                                            if shard else f"{ws} independent replica(s)"),
-                           "class_ms": {CLASS_NAMES[k]: fw["ktime"][k] for k in present}},
+                           "class_ms": {CLASS_NAMES[k]: fw["ktime"][k] for k in present},
+                           "per_class": _per_class(prob, plan, fw, peak_dmma, peak_dfma)},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fwd_bwd": fwdbwd, "alt_arithmetic": alt,
                 "integrals": integ,
                 "gpu_launches": fw["launches"] * args.steps,
@@ -771,6 +806,8 @@ def main():
     ap.add_argument("--batch", action="store_true",
                     help="evidence run: the 3 Hamiltonians x 3 frozen cutoffs of --config batched in one "
                          "graph-captured launch against sequential forwards")
+    ap.add_argument("--roots-per-launch", type=int, default=0,
+                    help="batch evidence run: roots of every job per persistent launch (0: all in one)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0,
                     help="oracle work per cpu_baseline sample (the sample is sized to about this long)")
     ap.add_argument("--ref-seconds", type=float, default=4.0)

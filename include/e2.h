@@ -287,19 +287,24 @@ E2_API e2_status e2_query_status(const e2_problem* prob, const void* workspace, 
                                  double* min_abs_D);
 
 /* Batches (no counterpart in the paper: a throughput device).  Several
- * planned problems -- different Hamiltonians, root counts, frozen cutoffs --
- * evaluated together: their dense-class tiles (all jobs, all roots) run in
- * ONE persistent launch that takes tiles from an integer work counter,
- * longest contraction first; the other classes and the reductions follow per
- * job.  Results equal those of e2_forward job by job (same partial slots, same
- * fixed reduction order).
+ * planned problems -- different Hamiltonians, root counts, frozen cutoffs,
+ * CAS or DAS references -- evaluated together: every class of every job and
+ * root (the dense-class tiles, the (2,2) blocks and the gather-class blocks)
+ * runs in ONE persistent launch, one CTA per SM, that takes work items from
+ * an integer counter, longest item first; only the per-job set-up before it
+ * and the reductions after it are separate launches (and the classes a job
+ * opted into the emulated arithmetic, which keep their own kernels).  Results
+ * equal those of e2_forward job by job (same partial slots, same fixed
+ * reduction order).  Every root of every job keeps its coupling tables until
+ * the one launch, so the workspace grows with the roots (e2_batch_workspace_size).
  *   e2_batch_create   host only; the problems must outlive the batch.
  *   e2_batch_prepare  uploads plan tables and the work list into `workspace`
  *                     and synchronises `stream`; call it once per workspace,
  *                     outside stream capture.
- *   e2_batch_forward  kernels and memsets only (no host synchronisation, no
- *                     host-to-device copies): it can be captured in a CUDA
- *                     graph and replayed.  `workspace` must be the prepared one.
+ *   e2_batch_forward  kernels, memsets and device-to-device copies only (no
+ *                     host synchronisation, no host-to-device copies): it can
+ *                     be captured in a CUDA graph and replayed.  `workspace`
+ *                     must be the prepared one.
  *                     inputs [n_jobs]; E2 [n_jobs] device pointers ([n_roots_j]
  *                     each); E2_class [n_jobs] or NULL. */
 typedef struct e2_batch e2_batch;
@@ -310,6 +315,16 @@ E2_API e2_status e2_batch_prepare(e2_batch* batch, void* workspace, size_t works
 E2_API e2_status e2_batch_forward(e2_batch* batch, const e2_inputs* inputs, void* workspace, size_t workspace_bytes,
                                   void* stream, double* const* E2, double* const* E2_class);
 E2_API e2_status e2_batch_launch_count(const e2_batch* batch, int64_t* n);
+/* Root groups: with k > 0, the batch runs its roots in groups -- roots
+ * 0..k-1 of every job in the first persistent launch, k..2k-1 in the next --
+ * and keeps only k coupling-table slots per job (root r in slot r mod k),
+ * rebuilt before each launch; k = 0 (the default) runs every root in one
+ * launch.  This bounds the workspace when the tables of all job-roots do not
+ * fit the device together (at a CAS(8e,24) active space one root's tables
+ * take about 17 GB).  Results are unchanged (bitwise).  Host only; call it
+ * before e2_batch_workspace_size and e2_batch_prepare (it re-lays the
+ * workspace). */
+E2_API e2_status e2_batch_set_roots_per_launch(e2_batch* batch, int k);
 /* Adjoint of a batch: each job's e2_backward in turn, in one workspace of
  * e2_batch_backward_workspace_size() bytes (the largest job's backward
  * layout; the forward batch's prepared workspace is not needed).  Per job j:

@@ -93,6 +93,8 @@ def load():
         L.e2_batch_forward.restype = C.c_int
         L.e2_batch_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
         L.e2_batch_launch_count.restype = C.c_int
+        L.e2_batch_set_roots_per_launch.argtypes = [C.c_void_p, C.c_int]
+        L.e2_batch_set_roots_per_launch.restype = C.c_int
         L.e2_launch_count.argtypes = [C.c_void_p, C.POINTER(C.c_int64)]
         L.e2_launch_count.restype = C.c_int
         L.e2_profile_events.argtypes = [C.c_void_p, C.c_void_p]
@@ -655,17 +657,20 @@ class E2Problem:
 
 
 class E2Batch:
-    """Several planned problems evaluated with one persistent launch for their
-    dense classes (e2_batch_*).  forward() enqueues kernels only, so it can be
-    captured in a CUDA graph after prepare()."""
+    """Several planned problems whose classes (every job, root and class) are
+    evaluated by one persistent launch (e2_batch_*), or one per group of
+    roots_per_launch roots.  forward() enqueues kernels and device copies
+    only, so it can be captured in a CUDA graph after prepare()."""
 
-    def __init__(self, plans):
+    def __init__(self, plans, roots_per_launch=0):
         L = load()
         self.plans = list(plans)
         arr = (C.c_void_p * len(self.plans))(*[p._h for p in self.plans])
         h = C.c_void_p()
         _check(L.e2_batch_create(arr, len(self.plans), C.byref(h)))
         self._h = h
+        if roots_per_launch:
+            _check(L.e2_batch_set_roots_per_launch(self._h, int(roots_per_launch)))
         ws = C.c_size_t()
         _check(L.e2_batch_workspace_size(self._h, C.byref(ws)))
         self.workspace_bytes = int(ws.value)

@@ -14,6 +14,7 @@
 #include "e2_common.cuh"
 #include "e2_device.cuh"
 #include "e2_kernels.cuh"
+#include "e2_host.h"
 
 namespace e2 {
 
@@ -188,40 +189,78 @@ k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_
                          blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
+// 24-wide outputs: the classes whose contraction is one active index at 24
+// active spinors (a 16-wide tiling computes 32 columns for 24)
+__global__ void __launch_bounds__(256, 1)
+k_zgemm24(int64_t M, int64_t N, int64_t K, const double2* __restrict__ A, int64_t sam, int64_t sak, int conjA,
+          const double2* __restrict__ B, int64_t sbk, int64_t sbn, int conjB, double2* __restrict__ C, int64_t csm,
+          int64_t csn, int beta, int64_t kseg, int64_t czs, int64_t lower) {
+  zgemm_body<128, 24, 8>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, C, csm, csn, beta, kseg, czs, lower,
+                         blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // Gamma_D of a column-tiled class in compacted form (tile j = blockIdx.y,
-// 80 compacted rows per blockIdx.x, K segment blockIdx.z):
+// BN compacted rows per blockIdx.x, K segment blockIdx.z):
 //   GDc[(koff + k) * 64 + c] (+)= sum_e conj(T[e][perm[64 j + c]]) W[e][klist[koff + k]]
 // (T itself instead of conj(T) when conjT == 0: shifted amplitudes arrive conjugated)
 // over the chunk's rows e, as the 64 x klen product of the tile's strings
-// with its compacted rows; same split-K segments as the plain product.
-constexpr int kTileRows = 80;
+// with its compacted rows; same split-K segments as the plain product.  The
+// product width BN (32, 48, 64 or 80) is the plan's: the one that pads the
+// class's compacted lengths least, since every padded row is a full row of
+// FP64 tensor work.
+template <int BN>
 __global__ void __launch_bounds__(256, 1)
 k_zgemm_gd_tiles(ColTiles ctl, const double2* __restrict__ W, int Kp, const double2* __restrict__ T, int64_t N,
                  int64_t Mc, double2* __restrict__ GDc, int beta, int64_t kseg, int64_t czs, int conjT,
                  int64_t t_ld) {
   const int j = blockIdx.y;
   const int4 td = ctl.tdesc[j];
-  if ((int64_t)blockIdx.x * kTileRows >= td.y) return;
+  if ((int64_t)blockIdx.x * BN >= td.y) return;
   // T in tile order (t_ld > 0): the tile's 64 columns are contiguous in each row
   const double2* A = t_ld ? T + (int64_t)j * 64 : T;
-  zgemm_body<64, kTileRows, 4>(64, td.y, Mc, A, 1, t_ld ? t_ld : N, conjT, W, Kp, 1, 0, GDc + (int64_t)td.x * 64, 1, 64,
-                               beta, kseg, czs, -1, 0, blockIdx.x, blockIdx.z,
-                               t_ld ? nullptr : ctl.perm + (int64_t)j * 64, nullptr, ctl.klist + td.x);
+  zgemm_body<64, BN, 4>(64, td.y, Mc, A, 1, t_ld ? t_ld : N, conjT, W, Kp, 1, 0, GDc + (int64_t)td.x * 64, 1, 64,
+                        beta, kseg, czs, -1, 0, blockIdx.x, blockIdx.z,
+                        t_ld ? nullptr : ctl.perm + (int64_t)j * 64, nullptr, ctl.klist + td.x);
 }
 
 // Gamma_W of a column-tiled class in compacted form (tile j = blockIdx.z):
 //   GWc[e * krows + koff + k] = sum_c conj(T[e][perm[64 j + c]]) Dc[(koff + k) * 64 + c]
-// (T itself when conjT == 0)
+// (T itself when conjT == 0); product width BN as above.
+template <int BN>
 __global__ void __launch_bounds__(256, 1)
 k_zgemm_gw_tiles(ColTiles ctl, const double2* __restrict__ T, int64_t N, int64_t Mc, int64_t krows,
                  double2* __restrict__ GWc, int conjT, int64_t t_ld) {
   const int j = blockIdx.z;
   const int4 td = ctl.tdesc[j];
-  if ((int64_t)blockIdx.y * kTileRows >= td.y) return;
+  if ((int64_t)blockIdx.y * BN >= td.y) return;
   const double2* A = t_ld ? T + (int64_t)j * 64 : T;  // tile order: contiguous row segments
-  zgemm_body<64, kTileRows, 4>(Mc, td.y, 64, A, t_ld ? t_ld : N, 1, conjT, ctl.Dc + (int64_t)td.x * 64, 1, 64, 0,
-                               GWc + td.x, krows, 1, 0, 64, 0, -1, blockIdx.x, blockIdx.y, 0, nullptr,
-                               t_ld ? nullptr : ctl.perm + (int64_t)j * 64, nullptr);
+  zgemm_body<64, BN, 4>(Mc, td.y, 64, A, t_ld ? t_ld : N, 1, conjT, ctl.Dc + (int64_t)td.x * 64, 1, 64, 0,
+                        GWc + td.x, krows, 1, 0, 64, 0, -1, blockIdx.x, blockIdx.y, 0, nullptr,
+                        t_ld ? nullptr : ctl.perm + (int64_t)j * 64, nullptr);
+}
+
+void launch_gd_tiles(int bn, dim3 grid, cudaStream_t st, const ColTiles& ctl, const double2* W, int Kp,
+                     const double2* T, int64_t N, int64_t Mc, double2* GDc, int beta, int64_t kseg, int64_t czs,
+                     int conjT, int64_t t_ld) {
+  switch (bn) {
+    case 32: k_zgemm_gd_tiles<32><<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, GDc, beta, kseg, czs, conjT, t_ld); break;
+    case 48: k_zgemm_gd_tiles<48><<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, GDc, beta, kseg, czs, conjT, t_ld); break;
+    case 64: k_zgemm_gd_tiles<64><<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, GDc, beta, kseg, czs, conjT, t_ld); break;
+    default: k_zgemm_gd_tiles<80><<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, GDc, beta, kseg, czs, conjT, t_ld); break;
+  }
+  ++g_launches;
+}
+
+void launch_gw_tiles(int bn, int64_t Mc, int maxklen, int64_t tiles, cudaStream_t st, const ColTiles& ctl,
+                     const double2* T, int64_t N, int64_t krows, double2* GWc, int conjT, int64_t t_ld) {
+  const dim3 g((unsigned)((Mc + 63) / 64), (unsigned)((maxklen + bn - 1) / bn), (unsigned)tiles);
+  switch (bn) {
+    case 32: k_zgemm_gw_tiles<32><<<g, 256, 0, st>>>(ctl, T, N, Mc, krows, GWc, conjT, t_ld); break;
+    case 48: k_zgemm_gw_tiles<48><<<g, 256, 0, st>>>(ctl, T, N, Mc, krows, GWc, conjT, t_ld); break;
+    case 64: k_zgemm_gw_tiles<64><<<g, 256, 0, st>>>(ctl, T, N, Mc, krows, GWc, conjT, t_ld); break;
+    default: k_zgemm_gw_tiles<80><<<g, 256, 0, st>>>(ctl, T, N, Mc, krows, GWc, conjT, t_ld); break;
+  }
+  ++g_launches;
 }
 
 // GD[klist[koff + k]][perm[64 j + c]] += GDc[(koff + k) * 64 + c], k < ktrue (one block per tile)

@@ -61,8 +61,10 @@ Ctx ctx(const e2_problem* P, unsigned char* ws) {
 // Base of root r's D-table slot (offsets o_DT... apply to it): slot 0 inside
 // the layout, or for a batch slot r >= 1 after the job's forward layout.
 unsigned char* slot_base(const e2_problem* P, unsigned char* ws, int r) {
-  if (!P->multi_slot || r == 0) return ws;
-  return ws + P->ws_bytes + (size_t)(r - 1) * P->d_stride - P->o_dstart;
+  if (!P->multi_slot) return ws;
+  const int s = P->slots > 0 ? r % P->slots : r;
+  if (s == 0) return ws;
+  return ws + P->ws_bytes + (size_t)(s - 1) * P->d_stride - P->o_dstart;
 }
 
 Tabs tables(const e2_problem* P, unsigned char* ws, int r) {
@@ -151,14 +153,15 @@ void dgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double* A, in
 }
 
 // C(m,n) = beta C(m,n) + sum_k opA(m,k) opB(k,n) (complex, tensor pipe), C(m,n)
-// at C[m*csm + n*csn].  Tile width bn = 64 or 16.  With `part` given and few
+// at C[m*csm + n*csn].  Tile width bn = 64, 16 or 24.  With `part` given and few
 // output tiles, K is split into segments summed in a fixed order (the output
 // region C[0 .. M*N) must then be dense in C's layout).
 void zgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
            const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn, int beta,
            int bn) {
   if (M <= 0 || N <= 0) return;
-  const int bm = bn == 16 ? 128 : 64;  // tiles 64 x 64 or 128 x 16
+  if (bn == 16 && N % 24 == 0 && N % 16 != 0) bn = 24;  // 24 active spinors: no padded columns
+  const int bm = bn == 64 ? 64 : 128;  // tiles 64 x 64, 128 x 16 or 128 x 24
   const int64_t tiles = ((M + bm - 1) / bm) * ((N + bn - 1) / bn);
   const int nseg = splitk_segments(tiles, K, 16 * (size_t)M * N);
   const int64_t kseg = (K + nseg - 1) / nseg;
@@ -170,6 +173,9 @@ void zgemm(cudaStream_t st, int64_t M, int64_t N, int64_t K, const double2* A, i
   const int64_t czs = M * N;
   if (bn == 16)
     (k_zgemm16<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, om, on, b, kseg, czs, -1),
+     ++g_launches);
+  else if (bn == 24)
+    (k_zgemm24<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, om, on, b, kseg, czs, -1),
      ++g_launches);
   else
     (k_zgemm64<<<grid, 256, 0, st>>>(M, N, K, A, sam, sak, conjA, B, sbk, sbn, conjB, out, om, on, b, kseg, czs, -1),
@@ -317,13 +323,13 @@ void zgemm_gd_tiles(cudaStream_t st, const ColPlan& cp, const ColTiles& ctl, con
   const int64_t czs = cp.krows * 64;
   const int nseg = splitk_segments(cp.gd_ctas, Mc, 16 * (size_t)czs);
   const int64_t kseg = (Mc + nseg - 1) / nseg;
-  dim3 grid((unsigned)((cp.maxklen + 79) / 80), (unsigned)cp.tiles, (unsigned)nseg);
+  dim3 grid((unsigned)((cp.maxklen + cp.pbn - 1) / cp.pbn), (unsigned)cp.tiles, (unsigned)nseg);
   if (nseg == 1) {
-    (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, GDc, beta, kseg, 0, conjT, t_ld), ++g_launches);
+    launch_gd_tiles(cp.pbn, grid, st, ctl, W, Kp, T, N, Mc, GDc, beta, kseg, 0, conjT, t_ld);
     return;
   }
   double2* part = (double2*)g_splitk;
-  (k_zgemm_gd_tiles<<<grid, 256, 0, st>>>(ctl, W, Kp, T, N, Mc, part, 0, kseg, czs, conjT, t_ld), ++g_launches);
+  launch_gd_tiles(cp.pbn, grid, st, ctl, W, Kp, T, N, Mc, part, 0, kseg, czs, conjT, t_ld);
   (k_zacc<<<blocks(czs), 256, 0, st>>>(part, nseg, czs, cp.krows, 64, GDc, 64, 1, beta), ++g_launches);
 }
 

@@ -134,10 +134,6 @@ struct GemmJob {
   unsigned long long* dmin;  // smallest |D| key of the class and root (status word)
 };
 
-struct WorkItem {
-  int job;
-  int tile_m, tile_n;
-};
 
 enum IntMode : int {
   INT_W02 = 0,  // <ab||tu>          rows (a<b), cols (t<u)
@@ -171,6 +167,33 @@ struct DevSpace {
   // particle only, else -1
   const int32_t* xc;       // [ncc]
   const int32_t* xv;       // [nvc]
+};
+
+// One (job, root) of a batch's element-wise classes: (2,2) and the gather
+// classes (0,1), (1,0), (0,0) (absolute device pointers).  L<c> is the string
+// list of class c; part / dmin hold the partial slots and smallest-|D| slots
+// of classes (2,2), (0,1), (1,0), (0,0) in that order.
+struct SparseJob {
+  DevList L8, L1, L3, L0, L2, L4, L5, L7;
+  DevDas das;
+  DevSpace sp;
+  const int64_t* binom;
+  const double2 *c, *DT, *DTU, *DTD, *DTDU, *X01, *X10, *X00, *f;
+  const double *g2, *epsh, *G, *E0p;
+  double b;
+  int nvb;
+  double* part[4];
+  unsigned long long* dmin[4];
+};
+
+// A run of work items of one kind in the persistent batch launch: items
+// [first, first + count), item k of the run being tile (k / gx, k % gx) of a
+// dense class (GemmJob job), or block (row or unit k / gx, string tile
+// k % gx) of an element-wise class (SparseJob job; (0,0): block k).
+enum WorkKind : int { WORK_TILE = 0, WORK_C22 = 1, WORK_C01 = 2, WORK_C10 = 3, WORK_C00 = 4 };
+struct WorkSeg {
+  int kind, job;
+  int64_t first, count, gx;
 };
 
 // chi of an external row that the external subspace limits exclude: its W

@@ -235,9 +235,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
         if (want_B) {  // Gamma_W = conj(T) D^T and the per-row occupation sums of eta
           double2* GW = (double2*)B(P->o_bGW[cls]) + m0 * Kp;
           if (tiled) {  // per tile over its compacted rows, then summed per table row in tile order
-            dim3 g((unsigned)((Mc + 63) / 64), (unsigned)((cp.maxklen + 79) / 80), (unsigned)cp.tiles);
-            (k_zgemm_gw_tiles<<<g, 256, 0, st>>>(ctl, adj.T, N, Mc, cp.krows, (double2*)B(P->o_bGWc), 1, adj.t_ld),
-             ++g_launches);
+            launch_gw_tiles(cp.pbn, Mc, cp.maxklen, cp.tiles, st, ctl, adj.T, N, cp.krows, (double2*)B(P->o_bGWc), 1,
+                            adj.t_ld);
             (k_gw_reduce<<<blocks(Mc * Kp), 256, 0, st>>>(ctl.tdesc, (const int32_t*)(ws + cp.o_pos), cp.tiles,
                                                          (int)Kp, (const double2*)B(P->o_bGWc), cp.krows, Mc, GW,
                                                          (int)Kp, Kp), ++g_launches);
@@ -393,9 +392,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           if (want_B) {
             double2* GXr = GX + (int64_t)r0 * S * nx_;
             if (tl) {
-              dim3 g((unsigned)((k + 63) / 64), (unsigned)((cpt.maxklen + 79) / 80), (unsigned)cpt.tiles);
-              (k_zgemm_gw_tiles<<<g, 256, 0, st>>>(ctt, Tsh, nb, k, cpt.krows, (double2*)B(P->o_bGWc), 0, 0),
-               ++g_launches);
+              launch_gw_tiles(cpt.pbn, k, cpt.maxklen, cpt.tiles, st, ctt, Tsh, nb, cpt.krows,
+                              (double2*)B(P->o_bGWc), 0, 0);
               // written, not accumulated: gx_beta is set only for class (0,0),
               // one row, whose target is still zero here
               (k_gw_reduce<<<blocks(k * nx_), 256, 0, st>>>(ctt.tdesc, (const int32_t*)(ws + cpt.o_pos), cpt.tiles,

@@ -41,7 +41,8 @@ struct ColPlan {
   int64_t tiles = 0, krows = 0;
   int maxklen = 0;             // longest compacted contraction of a tile
   int gran = 8;                // contraction granularity of the tiles (4: a k = 4 tail step)
-  int64_t gd_ctas = 0;         // sum over tiles of ceil(klen / 64)
+  int pbn = 80;                // width of the backward's compacted product tiles (32, 48, 64 or 80)
+  int64_t gd_ctas = 0;         // sum over tiles of ceil(klen / pbn)
   double ratio = 1.0;          // krows / (tiles * Kp): share of the dense contraction
   size_t o_perm = 0, o_tdesc = 0, o_klist = 0, o_pos = 0, o_Dc = 0;  // o_Dc: per-root D region
 };
@@ -93,7 +94,8 @@ struct e2_problem {
   size_t o_xYc, o_xZaa, o_x12, o_x01;
   size_t o_DT, o_DTD, o_DTU, o_DTDUD, o_DTDU;  // per-root stride below
   size_t d_stride;                              // bytes of one root's D tables
-  bool multi_slot = false;                      // set while a batch uses the job: one slot per root
+  bool multi_slot = false;                      // set while a batch uses the job: a table slot per root
+  int slots = 0;                                // with multi_slot: slots in use (root r in slot r % slots; 0 = n_roots)
   size_t o_g1, o_g2, g_stride;                  // gram outputs per root
   size_t o_part, o_partoff, o_partcnt, o_e2c;
   int64_t part_cnt[E2_NCLASS];
@@ -144,10 +146,16 @@ struct e2_problem {
 struct e2_batch {
   std::vector<e2_problem*> jobs;
   std::vector<size_t> off;          // workspace offset of each job's forward layout
-  size_t o_jobs = 0, o_items = 0, o_counter = 0, bytes = 0;
-  std::vector<e2::GemmJob> gj;          // absolute pointers, built by e2_batch_prepare
-  std::vector<e2::WorkItem> items;
+  std::vector<size_t> o_c;          // per job: device copy of its reference coefficients (all roots)
+  size_t o_jobs = 0, o_sjobs = 0, o_segs = 0, o_counter = 0, bytes = 0;  // o_counter: one per launch
+  std::vector<e2::GemmJob> gj;      // absolute pointers, built by e2_batch_prepare
+  std::vector<e2::SparseJob> sj;
+  std::vector<e2::WorkSeg> segs;      // runs of every launch, launch after launch
+  std::vector<int64_t> seg0, nseg, items;  // per launch: first run, runs, items
   int64_t n_items = 0;
+  int64_t max_gj = 0, max_sj = 0, max_segs = 0;
+  int roots_per_launch = 0;           // 0: every root of every job in one launch
+  int n_launch = 1;                   // persistent launches (root groups)
   const void* prepared = nullptr;
   int64_t launches = 0;
 };

@@ -827,30 +827,6 @@ k_class_probe(const double2* __restrict__ W, const double2* __restrict__ D, int6
   class_tile(W, D, M, N, Kp, rows, U, eA, E0p, b, partial, adj, tile_m, tile_n, n_tile_n, ctl, nullptr);
 }
 
-// Persistent form: one CTA per SM takes tiles of every (job, class, root) of a
-// batch from an integer work counter; items are ordered longest first
-// (contraction length times tile area).  Each tile writes the same partial
-// slot as the one-launch-per-class form, so the reduction order is unchanged.
-__global__ void __launch_bounds__(256, 1)
-k_batch_gemm(const GemmJob* __restrict__ jobs, const WorkItem* __restrict__ items, int n_items,
-             int* __restrict__ counter) {
-  __shared__ int s_item;
-  const AdjOut none{};
-  for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();
-    const int it = s_item;
-    if (it >= n_items) break;
-    const WorkItem w = items[it];
-    const GemmJob j = jobs[w.job];
-    const int64_t ntm = (j.M + GBM - 1) / GBM;
-    class_tile(j.W, j.D, j.M, j.N, j.Kp, j.rows, j.U, j.eA, j.E0p, j.b,
-               j.partial + (int64_t)w.tile_n * ntm + w.tile_m, none, w.tile_m, w.tile_n, (j.N + GBN - 1) / GBN, j.ct,
-               j.dmin);
-  }
-}
-
 // ------------------------------------------------------------------ class (2,2)
 
 // sum_{i<j, a<b, A} |<ab||ij>|^2 |c_A|^2 / D  with
@@ -858,15 +834,17 @@ k_batch_gemm(const GemmJob* __restrict__ jobs, const WorkItem* __restrict__ item
 // chi_ij = -eps^_i - eps^_j + G_ij, alpha_a = eps^_a - G_ia - G_ja.
 // Grid: x = A tiles (one A per thread), y = ordered pairs of 8-wide virtual
 // blocks, z = (i<j).  One partial per CTA.
-__global__ void __launch_bounds__(256)
-k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* __restrict__ g2 /*[ncp][nvp]*/,
-          const double* __restrict__ epsh, const double* __restrict__ G, const double* __restrict__ E0p, double b,
-          int nvb, double* __restrict__ partial, unsigned long long* dmin, int64_t u0) {
+// One block (string tile bx of gx, unit u) of the class; the kernel below and
+// the persistent batch kernel run it with the same partial slot.
+__device__ __forceinline__ void class22_block(const DevList& Ls, const DevSpace& sp, const double2* __restrict__ c,
+                                              const double* __restrict__ g2, const double* __restrict__ epsh,
+                                              const double* __restrict__ G, const double* __restrict__ E0p, double b,
+                                              int nvb, double* __restrict__ partial, unsigned long long* dmin,
+                                              int64_t u, int64_t bx, int64_t gx) {
   __shared__ double sGab[8][8], sG2[8][8], sAl[2][8];
   __shared__ double sh[32];
-  // grid y: units u0 + blockIdx.y of (core pair z, virtual block pair y), u = z nyb + y
+  // unit u = (core pair z, virtual block pair y), u = z nyb + y
   const int64_t nyb = (int64_t)nvb * (nvb + 1) / 2;
-  const int64_t u = u0 + blockIdx.y;
   const int zp = (int)(u / nyb);
   int ba = 0, bb = 0;
   {
@@ -897,7 +875,7 @@ k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* 
     sAl[side][x] = al;
   }
   __syncthreads();
-  const int64_t A = blockIdx.x * (int64_t)blockDim.x + tid;
+  const int64_t A = bx * (int64_t)blockDim.x + tid;
   double acc = 0.0;
   unsigned long long dm = ~0ULL;
   if (A < Ls.n) {
@@ -936,20 +914,31 @@ k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* 
   }
   dmin_flush(dmin, dm);
   double tot = block_sum(acc, sh);
-  if (tid == 0) partial[u * gridDim.x + blockIdx.x] = tot;
+  if (tid == 0) partial[u * gx + bx] = tot;
+}
+
+// Grid: x = A tiles (one A per thread), y = units u0 + blockIdx.y.  One partial per CTA.
+__global__ void __launch_bounds__(256)
+k_class22(DevList Ls, DevSpace sp, const double2* __restrict__ c, const double* __restrict__ g2 /*[ncp][nvp]*/,
+          const double* __restrict__ epsh, const double* __restrict__ G, const double* __restrict__ E0p, double b,
+          int nvb, double* __restrict__ partial, unsigned long long* dmin, int64_t u0) {
+  class22_block(Ls, sp, c, g2, epsh, G, E0p, b, nvb, partial, dmin, u0 + blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------------ gather classes
 
 // (0,1): V[a,A] = sum_t f_at D^t_A + sum_{u in A} (-1)^{#A<u} sum_{v<w} <au||vw> D^{vw}_{A-u}
-__global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
-                          const double2* __restrict__ DT /*[KpT][n12]*/, const double2* __restrict__ DTU /*[KpTU][n02]*/,
-                          const double2* __restrict__ X01, const double2* __restrict__ f, const double* __restrict__ epsh,
-                          const double* __restrict__ E0p, double b, double* __restrict__ partial, unsigned long long* dmin,
-                          double2* __restrict__ probeV, double* __restrict__ probeD, int64_t u0) {
+// One block (string tile bx of gx, virtual a) of the class.
+__device__ __forceinline__ void class01_block(const DevList& L01, const DevList& L12, const DevList& L02,
+                                              const DevDas& das, const DevSpace& sp, const int64_t* __restrict__ binom,
+                                              const double2* __restrict__ DT, const double2* __restrict__ DTU,
+                                              const double2* __restrict__ X01, const double2* __restrict__ f,
+                                              const double* __restrict__ epsh, const double* __restrict__ E0p,
+                                              double b, double* __restrict__ partial, unsigned long long* dmin,
+                                              double2* __restrict__ probeV, double* __restrict__ probeD, int a,
+                                              int64_t bx, int64_t gx) {
   __shared__ double sh[32];
-  const int a = (int)(u0 + blockIdx.y);  // grid y: virtuals u0 .. (a shard, or all)
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t g = bx * (int64_t)blockDim.x + threadIdx.x;
   const int na = sp.n_act, ntp = (int)pairs(na);
   double acc = 0.0;
   unsigned long long dm = ~0ULL;
@@ -989,18 +978,31 @@ __global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, Dev
   }
   dmin_flush(dmin, dm);
   double tot = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[(int64_t)a * gridDim.x + blockIdx.x] = tot;
+  if (threadIdx.x == 0) partial[(int64_t)a * gx + bx] = tot;
+}
+
+// grid x: string tiles, y: virtuals u0 + blockIdx.y (a shard, or all)
+__global__ void k_class01(DevList L01, DevList L12, DevList L02, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
+                          const double2* __restrict__ DT /*[KpT][n12]*/, const double2* __restrict__ DTU /*[KpTU][n02]*/,
+                          const double2* __restrict__ X01, const double2* __restrict__ f, const double* __restrict__ epsh,
+                          const double* __restrict__ E0p, double b, double* __restrict__ partial, unsigned long long* dmin,
+                          double2* __restrict__ probeV, double* __restrict__ probeD, int64_t u0) {
+  class01_block(L01, L12, L02, das, sp, binom, DT, DTU, X01, f, epsh, E0p, b, partial, dmin, probeV, probeD,
+                (int)(u0 + blockIdx.y), blockIdx.x, gridDim.x);
 }
 
 // (1,0): V[i,A] = sum_t f_ti D^{t+}_A + sum_{t<u in A} s(A;t,u) sum_v <tu||iv> D^v_{A-t-u}
-__global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
-                          const double2* __restrict__ DTD /*[Kp][n21]*/, const double2* __restrict__ DT /*[Kp][n12]*/,
-                          const double2* __restrict__ X10, const double2* __restrict__ f, const double* __restrict__ epsh,
-                          const double* __restrict__ E0p, double b, double* __restrict__ partial, unsigned long long* dmin,
-                          double2* __restrict__ probeV, double* __restrict__ probeD, int64_t u0) {
+// One block (string tile bx of gx, core spinor i) of the class.
+__device__ __forceinline__ void class10_block(const DevList& L10, const DevList& L21, const DevList& L12,
+                                              const DevDas& das, const DevSpace& sp, const int64_t* __restrict__ binom,
+                                              const double2* __restrict__ DTD, const double2* __restrict__ DT,
+                                              const double2* __restrict__ X10, const double2* __restrict__ f,
+                                              const double* __restrict__ epsh, const double* __restrict__ E0p,
+                                              double b, double* __restrict__ partial, unsigned long long* dmin,
+                                              double2* __restrict__ probeV, double* __restrict__ probeD, int i,
+                                              int64_t bx, int64_t gx) {
   __shared__ double sh[32];
-  const int i = (int)(u0 + blockIdx.y);  // grid y: core spinors u0 .. (a shard, or all)
-  const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t g = bx * (int64_t)blockDim.x + threadIdx.x;
   const int na = sp.n_act;
   double acc = 0.0;
   unsigned long long dm = ~0ULL;
@@ -1039,17 +1041,29 @@ __global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, Dev
   }
   dmin_flush(dmin, dm);
   double tot = block_sum(acc, sh);
-  if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = tot;
+  if (threadIdx.x == 0) partial[(int64_t)i * gx + bx] = tot;
+}
+
+// grid x: string tiles, y: core spinors u0 + blockIdx.y (a shard, or all)
+__global__ void k_class10(DevList L10, DevList L21, DevList L12, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
+                          const double2* __restrict__ DTD /*[Kp][n21]*/, const double2* __restrict__ DT /*[Kp][n12]*/,
+                          const double2* __restrict__ X10, const double2* __restrict__ f, const double* __restrict__ epsh,
+                          const double* __restrict__ E0p, double b, double* __restrict__ partial, unsigned long long* dmin,
+                          double2* __restrict__ probeV, double* __restrict__ probeD, int64_t u0) {
+  class10_block(L10, L21, L12, das, sp, binom, DTD, DT, X10, f, epsh, E0p, b, partial, dmin, probeV, probeD,
+                (int)(u0 + blockIdx.y), blockIdx.x, gridDim.x);
 }
 
 // (0,0), DAS only: V[A] = <A|H - E_O|Psi> for A of a non-reference pattern
-__global__ void k_class00(DevList L00, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
-                          const double2* __restrict__ DTDU /*[Kp][n11]*/, const double2* __restrict__ DTU /*[Kp][n02]*/,
-                          const double2* __restrict__ X00, const double2* __restrict__ f, const double* __restrict__ E0p,
-                          double b, double* __restrict__ partial, unsigned long long* dmin,
-                          double2* __restrict__ probeV, double* __restrict__ probeD, int64_t u0) {
+// One block (string block blk) of the class.
+__device__ __forceinline__ void class00_block(const DevList& L00, const DevList& L11, const DevList& L02,
+                                              const DevDas& das, const DevSpace& sp, const int64_t* __restrict__ binom,
+                                              const double2* __restrict__ DTDU, const double2* __restrict__ DTU,
+                                              const double2* __restrict__ X00, const double2* __restrict__ f,
+                                              const double* __restrict__ E0p, double b, double* __restrict__ partial,
+                                              unsigned long long* dmin, double2* __restrict__ probeV,
+                                              double* __restrict__ probeD, int64_t blk) {
   __shared__ double sh[32];
-  const int64_t blk = u0 + blockIdx.x;  // grid x: string blocks u0 .. (a shard, or all)
   const int64_t g = blk * (int64_t)blockDim.x + threadIdx.x;
   double acc = 0.0;
   unsigned long long dm = ~0ULL;
@@ -1066,6 +1080,67 @@ __global__ void k_class00(DevList L00, DevList L11, DevList L02, DevDas das, Dev
   dmin_flush(dmin, dm);
   double tot = block_sum(acc, sh);
   if (threadIdx.x == 0) partial[blk] = tot;
+}
+
+// grid x: string blocks u0 + blockIdx.x (a shard, or all)
+__global__ void k_class00(DevList L00, DevList L11, DevList L02, DevDas das, DevSpace sp, const int64_t* __restrict__ binom,
+                          const double2* __restrict__ DTDU /*[Kp][n11]*/, const double2* __restrict__ DTU /*[Kp][n02]*/,
+                          const double2* __restrict__ X00, const double2* __restrict__ f, const double* __restrict__ E0p,
+                          double b, double* __restrict__ partial, unsigned long long* dmin,
+                          double2* __restrict__ probeV, double* __restrict__ probeD, int64_t u0) {
+  class00_block(L00, L11, L02, das, sp, binom, DTDU, DTU, X00, f, E0p, b, partial, dmin, probeV, probeD,
+                u0 + blockIdx.x);
+}
+
+// ------------------------------------------------------------------ persistent batch launch
+
+// One launch for every class of every (job, root) of a batch: one CTA per SM
+// takes work items from an integer counter.  The items form runs (WorkSeg) of
+// one kind each: the 64 x 64 tiles of a dense class, or the blocks of class
+// (2,2) or of a gather class; runs are ordered longest item first, so that
+// the short (2,2) blocks fill the tail.  Every item writes the same partial
+// slot as the one-launch-per-class form, so the reduction order is unchanged
+// and the energies are bitwise those of e2_forward.
+__global__ void __launch_bounds__(256, 1)
+k_batch(const WorkSeg* __restrict__ segs, int nseg, const GemmJob* __restrict__ gjobs,
+        const SparseJob* __restrict__ sjobs, int64_t total, unsigned long long* __restrict__ counter) {
+  __shared__ long long s_item;
+  const AdjOut none{};
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_item = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+    const int64_t it = s_item;
+    if (it >= total) break;
+    int lo = 0, hi = nseg - 1;  // the run holding item it
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (segs[mid].first <= it) lo = mid;
+      else hi = mid - 1;
+    }
+    const WorkSeg w = segs[lo];
+    const int64_t k = it - w.first;
+    if (w.kind == WORK_TILE) {
+      const GemmJob& j = gjobs[w.job];
+      const int64_t ntm = (j.M + GBM - 1) / GBM, tm = k / w.gx, tn = k % w.gx;
+      class_tile(j.W, j.D, j.M, j.N, j.Kp, j.rows, j.U, j.eA, j.E0p, j.b, j.partial + tn * ntm + tm, none, tm, tn,
+                 w.gx, j.ct, j.dmin);
+      continue;
+    }
+    const SparseJob& j = sjobs[w.job];
+    if (w.kind == WORK_C22)
+      class22_block(j.L8, j.sp, j.c, j.g2, j.epsh, j.G, j.E0p, j.b, j.nvb, j.part[0], j.dmin[0], k / w.gx, k % w.gx,
+                    w.gx);
+    else if (w.kind == WORK_C01)
+      class01_block(j.L1, j.L5, j.L2, j.das, j.sp, j.binom, j.DT, j.DTU, j.X01, j.f, j.epsh, j.E0p, j.b, j.part[1],
+                    j.dmin[1], nullptr, nullptr, (int)(k / w.gx), k % w.gx, w.gx);
+    else if (w.kind == WORK_C10)
+      class10_block(j.L3, j.L7, j.L5, j.das, j.sp, j.binom, j.DTD, j.DT, j.X10, j.f, j.epsh, j.E0p, j.b, j.part[2],
+                    j.dmin[2], nullptr, nullptr, (int)(k / w.gx), k % w.gx, w.gx);
+    else
+      class00_block(j.L0, j.L4, j.L2, j.das, j.sp, j.binom, j.DTDU, j.DTU, j.X00, j.f, j.E0p, j.b, j.part[3],
+                    j.dmin[3], nullptr, nullptr, k);
+  }
 }
 
 // ------------------------------------------------------------------ reference solver

@@ -39,7 +39,8 @@ __global__ void k_dcompact(const double2* D, int64_t N, ColTiles ctl, double2* D
 __global__ void k_class_probe(const double2* W, const double2* D, int64_t M, int64_t N, int Kp, const RowInfo* rows,
                               const double* U, const double* eA, const double* E0p, double b, double* partial,
                               AdjOut adj, ColTiles ctl, int64_t tile_m, int64_t tile_n, int64_t n_tile_n);
-__global__ void k_batch_gemm(const GemmJob* jobs, const WorkItem* items, int n_items, int* counter);
+__global__ void k_batch(const WorkSeg* segs, int nseg, const GemmJob* gjobs, const SparseJob* sjobs, int64_t total,
+                        unsigned long long* counter);
 __global__ void k_class22(DevList Ls, DevSpace sp, const double2* c, const double* g2, const double* epsh,
                           const double* G, const double* E0p, double b, int nvb, double* partial,
                           unsigned long long* dmin, int64_t u0);
@@ -83,12 +84,15 @@ __global__ void k_zgemm64(int64_t M, int64_t N, int64_t K, const double2* A, int
 __global__ void k_zgemm16(int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
                           const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn,
                           int beta, int64_t kseg, int64_t czs, int64_t lower);
-__global__ void k_zgemm_gd_tiles(ColTiles ctl, const double2* W, int Kp, const double2* T, int64_t N, int64_t Mc,
-                                 double2* GDc, int beta, int64_t kseg, int64_t czs, int conjT,
-                                 int64_t t_ld);
-__global__ void k_zgemm_gw_tiles(ColTiles ctl, const double2* T, int64_t N, int64_t Mc, int64_t krows, double2* GWc,
-                                 int conjT,
-                                 int64_t t_ld);
+__global__ void k_zgemm24(int64_t M, int64_t N, int64_t K, const double2* A, int64_t sam, int64_t sak, int conjA,
+                          const double2* B, int64_t sbk, int64_t sbn, int conjB, double2* C, int64_t csm, int64_t csn,
+                          int beta, int64_t kseg, int64_t czs, int64_t lower);
+// compacted Gamma products of a column-tiled class at product width bn (32, 48, 64, 80)
+void launch_gd_tiles(int bn, dim3 grid, cudaStream_t st, const ColTiles& ctl, const double2* W, int Kp,
+                     const double2* T, int64_t N, int64_t Mc, double2* GDc, int beta, int64_t kseg, int64_t czs,
+                     int conjT, int64_t t_ld);
+void launch_gw_tiles(int bn, int64_t Mc, int maxklen, int64_t tiles, cudaStream_t st, const ColTiles& ctl,
+                     const double2* T, int64_t N, int64_t krows, double2* GWc, int conjT, int64_t t_ld);
 __global__ void k_gd_scatter(ColTiles ctl, const double2* GDc, int64_t N, double2* GD);
 __global__ void k_gw_reduce(const int4* tdesc, const int32_t* pos, int64_t tiles, int Kp, const double2* GWc,
                             int64_t krows, int64_t Mc, double2* GW, int nxo, int64_t ldo);

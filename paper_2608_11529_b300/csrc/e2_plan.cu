@@ -248,7 +248,22 @@ void build_colplan(e2_problem* P, int cls, int fam, int kvalid, int fs = 3, int 
     for (int x = ktrue; x < klen; ++x) cp.klist.push_back(0);
     cp.tdesc.insert(cp.tdesc.end(), {koff, klen, ktrue, 0});
     cp.maxklen = std::max(cp.maxklen, klen);
-    cp.gd_ctas += (klen + 79) / 80;  // 64 x 80 product tiles of the compacted backward products
+  }
+  // width of the backward's compacted product tiles: every padded row is a
+  // full row of FP64 tensor work, so take the width that pads the tiles'
+  // lengths least (the widest of those within 1% of the least)
+  {
+    int64_t best = -1;
+    for (int bn : {80, 64, 48, 32}) {
+      int64_t padded = 0;
+      for (int64_t j = 0; j < cp.tiles; ++j) padded += (cp.tdesc[4 * j + 1] + bn - 1) / bn * bn;
+      if (best < 0 || padded * 100 < best * 99) {
+        best = padded;
+        cp.pbn = bn;
+      }
+    }
+    cp.gd_ctas = 0;
+    for (int64_t j = 0; j < cp.tiles; ++j) cp.gd_ctas += (cp.tdesc[4 * j + 1] + cp.pbn - 1) / cp.pbn;
   }
   cp.pos.assign((size_t)cp.tiles * Kp, -1);
   for (int64_t j = 0; j < cp.tiles; ++j)

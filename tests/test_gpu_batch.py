@@ -1,7 +1,7 @@
-"""Batched evaluation: one persistent launch for the dense classes of several
-jobs (different Hamiltonians, root counts and frozen cutoffs), plain and
-captured in a CUDA graph, against e2_forward job by job (bitwise: same
-partial slots, same reduction order) and the oracle."""
+"""Batched evaluation: one persistent launch for every class of several jobs
+(different Hamiltonians, root counts, frozen cutoffs, a CAS and a DAS
+reference), plain and captured in a CUDA graph, against e2_forward job by job
+(bitwise: same partial slots, same reduction order) and the oracle."""
 import numpy as np
 import pytest
 
@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 def _jobs():
     base = dict(n_core=6, n_act=10, n_virt=16, n_elec=5, Lc=6, Lx=3, x_scale=0.05, seed=61)
     specs = [dict(ham="DC", n_roots=1), dict(ham="DCG", n_roots=2, n_frozen_core=2),
-             dict(ham="DCB", n_roots=2, n_frozen_core=2, n_frozen_virt=4)]
+             dict(ham="DCB", n_roots=2, n_frozen_core=2, n_frozen_virt=4),
+             dict(ham="DCB", n_roots=1, das_size=[4, 6], das_min=[2, 0], das_max=[4, 3], n_frozen_virt=2)]
     out = []
     for sp in specs:
         kw = dict(base)
@@ -27,9 +28,10 @@ def _jobs():
     return out
 
 
+@pytest.mark.parametrize("roots_per_launch", [0, 1])
 @pytest.mark.parametrize("col_tiles", [False, True])
 @pytest.mark.parametrize("sliced", [True, False])
-def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph(col_tiles, sliced):
+def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph(col_tiles, sliced, roots_per_launch):
     import paper_2608_11529_b300 as e2
     from paper_2608_11529_b300 import build as e2build
     e2build.build()
@@ -47,7 +49,9 @@ def test_batch_matches_single_forward_and_oracle_and_replays_in_a_graph(col_tile
     for plan, t in zip(plans, inputs):
         E2, E2c, _ = plan.forward(**t)
         single.append((E2.clone(), E2c.clone()))
-    batch = e2.E2Batch(plans)
+    # roots_per_launch = 1: the two-root jobs run in two persistent launches
+    # that reuse one coupling-table slot per job
+    batch = e2.E2Batch(plans, roots_per_launch=roots_per_launch)
     batch.prepare(torch.device("cuda"))
     out = batch.forward(inputs)
     torch.cuda.synchronize()
