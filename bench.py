@@ -295,6 +295,9 @@ def run_batch(args):
     roots -- captured in a CUDA graph and replayed, against the same jobs'
     e2_forward calls one after another.  Prints one JSON line with
     "mode": "batch"."""
+    # the batch keeps every job's layout in one large workspace: let freed
+    # memory of the set-up go back to the device (set before CUDA starts)
+    os.environ.setdefault("PYTORCH_CUDA_ALLOC_CONF", "expandable_segments:True")
     import torch
     import paper_2608_11529_b300 as e2
     from e2_inputs import make_problem
@@ -324,6 +327,13 @@ def run_batch(args):
                 plan.autotune(**t)
             jobs.append((ham, fc, fv, plan, t))
     couplings = sum(float(p.q_per_class.sum()) * p.n_roots for *_, p, _ in jobs)
+    for *_, p, _ in jobs:   # the solve / tuning workspaces of every job
+        p.release()
+    torch.cuda.empty_cache()
+    # the batch's workspace first (all jobs' layouts at once); the sequential
+    # forwards then take one job's workspace at a time beside it
+    batch = e2.E2Batch([p for *_, p, _ in jobs], roots_per_launch=args.roots_per_launch)
+    batch.prepare(dev)
     stream = torch.cuda.current_stream(dev)
     ev = lambda: torch.cuda.Event(enable_timing=True)
 
@@ -346,9 +356,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     ms_seq = a.elapsed_time(z) / args.steps
     ref = [(E2, E2c) for E2, E2c, _ in ref]
-    torch.cuda.empty_cache()   # the batch holds all jobs' layouts in one workspace
-    batch = e2.E2Batch([p for *_, p, _ in jobs], roots_per_launch=args.roots_per_launch)
-    batch.prepare(dev)
+    torch.cuda.empty_cache()
     inputs = [t for *_, t in jobs]
     for _ in range(args.warmup):
         batch.forward(inputs)

@@ -675,9 +675,38 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
     __syncthreads();
   }
 
-  // epilogue: D_K = E0' - chi(e) - e_A - U[s1,A] - U[s2,A] + U[i1,A] + U[i2,A]
+  // epilogue: D_K = E0' - chi(e) - e_A - U[s1,A] - U[s2,A] + U[i1,A] + U[i2,A].
+  // The U rows that every row of the tile shares (a row tile of pairs (a<b)
+  // mostly shares b, of (i, a<b) shares i and b) are summed once per column
+  // into y_A = e_A + U[s1,A] + U[s2,A] - U[i1,A] - U[i2,A] over those slots;
+  // each coupling then adds only its row's own rows: D_K = (E0' - chi(e)) - y_A - ...
   const double e0p = *E0p;
   const int64_t mend = adj.T ? adj.m_base + adj.Mc : M;
+  __shared__ double sY[GBN];
+  int cm = 0;  // bit k: slot k (s1, s2, i1, i2) is the same in every row of the tile
+  {
+    const RowInfo r0 = rows[m0];
+    const int64_t rr = m0 + tid;
+    const bool own = tid < GBM && rr < mend;
+    const RowInfo ri = own ? rows[rr] : r0;
+    cm |= __syncthreads_and(ri.s1 == r0.s1) ? 1 : 0;
+    cm |= __syncthreads_and(ri.s2 == r0.s2) ? 2 : 0;
+    cm |= __syncthreads_and(ri.i1 == r0.i1) ? 4 : 0;
+    cm |= __syncthreads_and(ri.i2 == r0.i2) ? 8 : 0;
+    if (tid < GBN) {
+      const int64_t col = sCol[tid];
+      double y = 0.0;
+      if (col >= 0) {
+        y = eA[col];
+        if (cm & 1) y += U[(int64_t)r0.s1 * N + col];
+        if (cm & 2) y += U[(int64_t)r0.s2 * N + col];
+        if (cm & 4) y -= U[(int64_t)r0.i1 * N + col];
+        if (cm & 8) y -= U[(int64_t)r0.i2 * N + col];
+      }
+      sY[tid] = y;
+    }
+    __syncthreads();
+  }
   double acc = 0.0, acc2 = 0.0;
   const double inv_n = adj.T ? 1.0 / adj.g1[0].x : 0.0, s2n = 2.0 * adj.s * inv_n;
   unsigned long long dm = ~0ULL;                                // smallest |D| key of the thread
@@ -702,9 +731,19 @@ __device__ __forceinline__ void class_tile(const double2* __restrict__ W, const 
       for (int ni = 0; ni < 2; ++ni)
 #pragma unroll
         for (int hc = 0; hc < 2; ++hc) {
-          const int64_t col = sCol[wn * 16 + ni * 8 + 2 * tq + hc];
+          const int lc = wn * 16 + ni * 8 + 2 * tq + hc;
+          const int64_t col = sCol[lc];
           const int kk = ni * 2 + hc;
-          Dv[kk] = col >= 0 ? base - eA[col] - U1[col] - U2[col] + U3[col] + U4[col] : 1.0;
+          if (col >= 0) {  // tile-uniform branches
+            double d = base - sY[lc];
+            if (!(cm & 1)) d -= U1[col];
+            if (!(cm & 2)) d -= U2[col];
+            if (!(cm & 4)) d += U3[col];
+            if (!(cm & 8)) d += U4[col];
+            Dv[kk] = d;
+          } else {
+            Dv[kk] = 1.0;
+          }
           q[kk] = col >= 0 ? en_q(Dv[kk], b) : 1.0;
           if (col >= 0 && in_q) dm = min(dm, dkey(Dv[kk]));
         }
