@@ -385,24 +385,36 @@ k_dgemm(int64_t M, int64_t N, int64_t K, const double* __restrict__ A, int64_t s
 }
 
 // Hocc[r][t] = sum_A H[r][A] [t in A]  (one block per row of the chunk)
+// Per-spinor occupation sums of one row, reduced from thread-private columns
+// sacc[t * blockDim + thread]: spinor t by warp t mod (warps), lanes over the
+// columns in a fixed order, then a shuffle tree; out[t] = the sum.
+__device__ __forceinline__ void occ_rows_out(const double* sacc, int na, double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5, nt = blockDim.x;
+  for (int t = warp; t < na; t += nw) {
+    double v = 0.0;
+    for (int k = lane; k < nt; k += 32) v += sacc[t * nt + k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) out[t] = v;
+  }
+}
+
 __global__ void k_hocc(const double* __restrict__ H, DevList Ls, int na, double* __restrict__ Hocc,
                        const int32_t* __restrict__ perm, int64_t ld) {
-  __shared__ double sh[32];
+  // thread-private columns of the per-spinor sums: sacc[t * blockDim + thread]
+  extern __shared__ double sacc[];
   const int64_t r = blockIdx.x;
-  double acc[64];
-  for (int t = 0; t < na; ++t) acc[t] = 0.0;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = 0; t < na; ++t) sacc[t * nt + tid] = 0.0;
   // perm: H in tile order ([r][slot], slot -> string perm[slot], -1 padding), row stride ld
   const int64_t ncol = perm ? ld : Ls.n;
-  for (int64_t g = threadIdx.x; g < ncol; g += blockDim.x) {
+  for (int64_t g = tid; g < ncol; g += nt) {
     const int64_t a = perm ? (int64_t)perm[g] : g;
     if (a < 0) continue;
     const double h = H[r * ncol + g];
-    for (uint64_t x = Ls.str[a]; x; x &= x - 1) acc[__ffsll((long long)x) - 1] += h;
+    for (uint64_t x = Ls.str[a]; x; x &= x - 1) sacc[(__ffsll((long long)x) - 1) * nt + tid] += h;
   }
-  for (int t = 0; t < na; ++t) {
-    const double v = block_sum(acc[t], sh);
-    if (threadIdx.x == 0) Hocc[r * na + t] = v;
-  }
+  __syncthreads();
+  occ_rows_out(sacc, na, Hocc + r * na);
 }
 
 // Rows of every class with external spinors are tuples (h, p): a hole tuple h
@@ -673,18 +685,30 @@ k_class22_bwd(DevList Ls, DevSpace sp, const double2* __restrict__ c, const doub
     hpart[yz * Ls.n + A] = hsum;
   }
   const int64_t cta = yz * gridDim.x + blockIdx.x;
-  for (int k = 0; k < 8; ++k) {
-    double v = block_sum(ha[k], sh);
-    if (tid == 0) vpart[cta * 19 + k] = v;
-    v = block_sum(hb[k], sh);
-    if (tid == 0) vpart[cta * 19 + 8 + k] = v;
-  }
-  double v = block_sum(hsum, sh);
-  double w2 = block_sum(gv, sh);
-  if (tid == 0) {
-    vpart[cta * 19 + 16] = v;
-    vpart[cta * 19 + 17] = v;
-    vpart[cta * 19 + 18] = w2;
+  {
+    // the block's 18 sums at once: thread-private columns, then warp w sums
+    // rows w, w + 8, w + 16 (lanes over the columns in a fixed order, a
+    // shuffle tree)
+    __shared__ double sv[18][256];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      sv[k][tid] = ha[k];
+      sv[8 + k][tid] = hb[k];
+    }
+    sv[16][tid] = hsum;
+    sv[17][tid] = gv;
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int k = warp; k < 18; k += 8) {
+      double v = 0.0;
+      for (int q = lane; q < 256; q += 32) v += sv[k][q];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) {
+        if (k < 16) vpart[cta * 19 + k] = v;
+        else if (k == 16) vpart[cta * 19 + 16] = vpart[cta * 19 + 17] = v;
+        else vpart[cta * 19 + 18] = v;
+      }
+    }
   }
   if (part) {  // the forward's E2 partial of this block (global core-pair index)
     const double tot = block_sum(acc, sh);
@@ -1179,8 +1203,10 @@ k_class22_rows(DevList Ls, DevSpace sp, const double2* __restrict__ c, const dou
                      G[(int64_t)gj * sp.n + gb];
   const double e0p = *E0p;
   const int na = sp.n_act;
-  double hs = 0.0, p22 = 0.0, ho[64];
-  for (int t = 0; t < na; ++t) ho[t] = 0.0;
+  extern __shared__ double sacc[];  // thread-private columns of the occupation sums
+  const int nt = blockDim.x;
+  double hs = 0.0, p22 = 0.0;
+  for (int t = 0; t < na; ++t) sacc[t * nt + threadIdx.x] = 0.0;
   const double* Ua = Ls.U + (int64_t)(sp.ncc + au) * Ls.n;
   const double* Ub = Ls.U + (int64_t)(sp.ncc + bu) * Ls.n;
   const double* Ui = Ls.U + (int64_t)iu * Ls.n;
@@ -1208,20 +1234,17 @@ k_class22_rows(DevList Ls, DevSpace sp, const double2* __restrict__ c, const dou
       const double hk = c2[k] * hw;
       hs += hk;
       p22 = fma(gk, c2[k], p22);
-      for (uint64_t x = Ls.str[A]; x; x &= x - 1) ho[__ffsll((long long)x) - 1] += hk;
+      for (uint64_t x = Ls.str[A]; x; x &= x - 1) sacc[(__ffsll((long long)x) - 1) * nt + threadIdx.x] += hk;
     }
   }
   hs *= s;
   p22 *= s;
-  for (int t = 0; t < na; ++t) ho[t] *= s;
+  for (int t = 0; t < na; ++t) sacc[t * nt + threadIdx.x] *= s;
   double v = block_sum(hs, sh);
   if (threadIdx.x == 0) hsum[row] = v;
-  v = block_sum(p22, sh);
+  v = block_sum(p22, sh);  // (its barriers also order the column writes above)
   if (threadIdx.x == 0) P22[row] = v;
-  for (int t = 0; t < na; ++t) {
-    v = block_sum(ho[t], sh);
-    if (threadIdx.x == 0) Hocc[row * na + t] = v;
-  }
+  occ_rows_out(sacc, na, Hocc + row * na);
 }
 
 // Gamma of <ab||ij>: 2 conj(g) P22

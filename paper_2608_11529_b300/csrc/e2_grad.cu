@@ -248,7 +248,8 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           if (P->use_oz[cls])  // eta came as float-float pairs from the sliced adjoint
             launch_hocc_df(st, (const float2*)adj.Hm, L, na, Mc, Hocc + m0 * na);
           else
-            (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na, tperm, adj.t_ld), ++g_launches);
+            (k_hocc<<<(unsigned)Mc, occ_threads(na), occ_smem(na), st>>>(adj.Hm, L, na, Hocc + m0 * na, tperm, adj.t_ld),
+             ++g_launches);
         }
       }
       if (tiled)
@@ -307,8 +308,9 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           launch_class22_rows_df(st, L, X.sp, (const float2*)(ws + H8.o_eAdf), (const float2*)(ws + H8.o_Udf), c2,
                                  (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, s, M22, hs22, Hocc, P22);
         } else {
-          (k_class22_rows<<<(unsigned)M22, 256, 0, st>>>(L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G,
-                                                         X.E0p + r, b, s, g1, hs22, Hocc, P22), ++g_launches);
+          (k_class22_rows<<<(unsigned)M22, occ_threads(na), occ_smem(na), st>>>(
+               L, X.sp, c, (const double*)(ws + P->o_G22), X.epsh, X.G, X.E0p + r, b, s, g1, hs22, Hocc, P22),
+           ++g_launches);
         }
         zpair(8, hs22, Hocc);
         (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
@@ -357,7 +359,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       //   Gamma_X[row][...][x] = sum_B Tsh[row][B] D[x][B]            (integral coefficients)
       if (want_B) {
         (k_rowsum_wide<<<(unsigned)nrow, 256, 0, st>>>(Hg, L.n, 0, hsum), ++g_launches);
-        (k_hocc<<<(unsigned)nrow, 256, 0, st>>>(Hg, L, na, Hocc, nullptr, 0), ++g_launches);
+        (k_hocc<<<(unsigned)nrow, occ_threads(na), occ_smem(na), st>>>(Hg, L, na, Hocc, nullptr, 0), ++g_launches);
         zpair(cls, hsum, Hocc);
         (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
       }

@@ -20,6 +20,9 @@ CASES = {
     "das": lambda: tiny_problem(2, 8, 8, 4, Lc=4, das_size=[4, 4], das_min=[1, 1], das_max=[3, 3], seed=53),
     "level_shift": lambda: tiny_problem(4, 6, 10, 3, Lc=4, level_shift_b=0.05, seed=54),
     "mid_dcb": lambda: tiny_problem(4, 10, 18, 5, Lc=6, Lx=3, ham="DCB", x_scale=0.05, seed=55),
+    # 24 active spinors, as in the Ar- to Xe-shaped workloads (the per-row
+    # occupation sums then run at another block size)
+    "wide_active": lambda: tiny_problem(4, 24, 6, 3, Lc=4, Lx=2, ham="DCB", x_scale=0.05, seed=56),
 }
 
 
