@@ -67,12 +67,14 @@ __device__ __forceinline__ double en_g(double D, double b) {
 
 // Reciprocals of four values with one reciprocal (simultaneous inversion:
 // prefix products, one rcp_nr, back-substitution; 15 FP64 operations for
-// four instead of 24).  When the product leaves [1e-30, 1e30] (rcp_nr seeds
-// in single precision) the four are inverted one by one.
+// four instead of 24).  When the product's magnitude leaves [2^-99, 2^99)
+// (rcp_nr seeds in single precision; a NaN or an infinity also leaves it)
+// the four are inverted one by one.  The range test reads the exponent
+// field with integer operations, off the FP64 pipe.
 __device__ __forceinline__ void rcp4(const double (&q)[4], double (&r)[4]) {
   const double p1 = q[0] * q[1], p2 = p1 * q[2], p3 = p2 * q[3];
-  const double ap = fabs(p3);
-  if (ap > 1e-30 && ap < 1e30) {
+  const unsigned ex = ((unsigned)__double2hiint(p3) >> 20) & 0x7FFu;  // biased exponent
+  if (ex - 924u < 1122u - 924u) {
     double s = rcp_nr(p3);
     r[3] = s * p2;
     s *= q[3];
