@@ -400,21 +400,22 @@ __device__ __forceinline__ void occ_rows_out(const double* sacc, int na, double*
 
 __global__ void k_hocc(const double* __restrict__ H, DevList Ls, int na, double* __restrict__ Hocc,
                        const int32_t* __restrict__ perm, int64_t ld) {
-  // thread-private columns of the per-spinor sums: sacc[t * blockDim + thread]
-  extern __shared__ double sacc[];
+  __shared__ double sh[32];
   const int64_t r = blockIdx.x;
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int t = 0; t < na; ++t) sacc[t * nt + tid] = 0.0;
+  double acc[64];
+  for (int t = 0; t < na; ++t) acc[t] = 0.0;
   // perm: H in tile order ([r][slot], slot -> string perm[slot], -1 padding), row stride ld
   const int64_t ncol = perm ? ld : Ls.n;
-  for (int64_t g = tid; g < ncol; g += nt) {
+  for (int64_t g = threadIdx.x; g < ncol; g += blockDim.x) {
     const int64_t a = perm ? (int64_t)perm[g] : g;
     if (a < 0) continue;
     const double h = H[r * ncol + g];
-    for (uint64_t x = Ls.str[a]; x; x &= x - 1) sacc[(__ffsll((long long)x) - 1) * nt + tid] += h;
+    for (uint64_t x = Ls.str[a]; x; x &= x - 1) acc[__ffsll((long long)x) - 1] += h;
   }
-  __syncthreads();
-  occ_rows_out(sacc, na, Hocc + r * na);
+  for (int t = 0; t < na; ++t) {
+    const double v = block_sum(acc[t], sh);
+    if (threadIdx.x == 0) Hocc[r * na + t] = v;
+  }
 }
 
 // Rows of every class with external spinors are tuples (h, p): a hole tuple h

@@ -248,8 +248,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
           if (P->use_oz[cls])  // eta came as float-float pairs from the sliced adjoint
             launch_hocc_df(st, (const float2*)adj.Hm, L, na, Mc, Hocc + m0 * na);
           else
-            (k_hocc<<<(unsigned)Mc, occ_threads(na), occ_smem(na), st>>>(adj.Hm, L, na, Hocc + m0 * na, tperm, adj.t_ld),
-             ++g_launches);
+            (k_hocc<<<(unsigned)Mc, 256, 0, st>>>(adj.Hm, L, na, Hocc + m0 * na, tperm, adj.t_ld), ++g_launches);
         }
       }
       if (tiled)
@@ -359,7 +358,7 @@ e2_status e2_backward(e2_problem* P, const e2_inputs* in, const double* seed, vo
       //   Gamma_X[row][...][x] = sum_B Tsh[row][B] D[x][B]            (integral coefficients)
       if (want_B) {
         (k_rowsum_wide<<<(unsigned)nrow, 256, 0, st>>>(Hg, L.n, 0, hsum), ++g_launches);
-        (k_hocc<<<(unsigned)nrow, occ_threads(na), occ_smem(na), st>>>(Hg, L, na, Hocc, nullptr, 0), ++g_launches);
+        (k_hocc<<<(unsigned)nrow, 256, 0, st>>>(Hg, L, na, Hocc, nullptr, 0), ++g_launches);
         zpair(cls, hsum, Hocc);
         (k_ntt<<<na * na, 256, 0, st>>>(L, hA, na, Ntt), ++g_launches);
       }

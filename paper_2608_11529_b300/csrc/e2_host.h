@@ -167,9 +167,9 @@ e2_status build_plan(e2_problem* P);
 
 // ---- launch helpers (e2_api.cu)
 inline unsigned blocks(int64_t n, int t = 256) { return (unsigned)((n + t - 1) / t); }
-// threads and dynamic shared memory of the per-row occupation-sum kernels
-// (k_hocc, k_class22_rows: one column of na doubles per thread, at most
-// 40 KiB, under the 48 KiB a block may take without opting in)
+// threads and dynamic shared memory of k_class22_rows's per-row occupation
+// sums (one column of na doubles per thread, at most 40 KiB, under the
+// 48 KiB a block may take without opting in)
 inline int occ_threads(int na) { return na <= 20 ? 256 : na <= 40 ? 128 : 64; }
 inline size_t occ_smem(int na) { return (size_t)na * occ_threads(na) * sizeof(double); }
 
