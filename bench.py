@@ -524,7 +524,8 @@ def _roofline(prob, plan, fw, peak_dmma, peak_dfma):
         executed = exe / (t_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak_dmma, "unit": "TFLOP/s",
                 "frac": achieved / peak_dmma, "traffic": _traffic("k_class_gemm"),
-                "traffic_scope": "DRAM bytes per launch (ncu)",
+                "traffic_scope": "DRAM bytes read + written per step over the kernel's class launches (ncu, one "
+                                 "pass, full-size capture of the benchmark workload)",
                 "kernel": "k_class_gemm classes " + " ".join(CLASS_NAMES[k] for k in classes),
                 "peak_source": "FP64 tensor pipe (mma.sync m16n8k8 f64) measured on this GPU in this run "
                                "(e2_fp64_peak, burst), of measured; MEASURED_PEAKS.json has no FP64 figure",

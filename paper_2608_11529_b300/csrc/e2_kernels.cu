@@ -843,17 +843,29 @@ __global__ void k_dcompact(const double2* __restrict__ D, int64_t N, ColTiles ct
   }
 }
 
-// One CTA per 64x64 tile; grid x = row tiles (of the chunk from adj.m_base),
-// y = column tiles.  Forward: one partial per tile in partial[y * gridDim.x + x].
+// One CTA per 64x64 tile: gridDim.x row tiles (of the chunk from adj.m_base,
+// or tm0 .. tm0 + gridDim.x - 1 of the rt the class has: a shard, or all)
+// times gridDim.y column tiles.  Forward: one partial per tile, in
+// partial[column tile * rt + row tile].
+// Rasterisation in bands of kBand row tiles: the CTAs in flight share a band's
+// integral rows (W, 64 rows x Kp each), which stay in L2 while the band
+// sweeps every column tile, so W is read from DRAM about once instead of
+// once per column tile (at the Ar shape 0.36 GB against 686 GB for class
+// (0,2)); the coupling-table blocks are read once per band.
+constexpr int64_t kBand = 32;
 __global__ void __launch_bounds__(256, 1)
 k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M, int64_t N, int Kp,
              const RowInfo* __restrict__ rows, const double* __restrict__ U, const double* __restrict__ eA,
              const double* __restrict__ E0p, double b, double* __restrict__ partial, AdjOut adj, ColTiles ctl,
              unsigned long long* dmin, int64_t rt, int64_t tm0) {
-  // grid x: row tiles tm0 .. tm0 + gridDim.x - 1 of the rt the class has (a shard, or all)
-  const int64_t tm = tm0 + blockIdx.x;
-  double* slot = partial ? partial + (int64_t)blockIdx.y * rt + tm : nullptr;
-  class_tile(W, D, M, N, Kp, rows, U, eA, E0p, b, slot, adj, tm, blockIdx.y, gridDim.y, ctl, dmin);
+  const int64_t gx = gridDim.x, gy = gridDim.y;
+  const int64_t L = (int64_t)blockIdx.y * gx + blockIdx.x;  // launch order
+  const int64_t band = L / (kBand * gy), b0 = band * kBand;
+  const int64_t bsz = gx - b0 < kBand ? gx - b0 : kBand;    // the last band may be narrower
+  const int64_t r = L - b0 * gy;
+  const int64_t tm = tm0 + b0 + r % bsz, tn = r / bsz;
+  double* slot = partial ? partial + tn * rt + tm : nullptr;
+  class_tile(W, D, M, N, Kp, rows, U, eA, E0p, b, slot, adj, tm, tn, gy, ctl, dmin);
 }
 
 // One tile (tile_m, tile_n) of the class kernel with its per-coupling probe
