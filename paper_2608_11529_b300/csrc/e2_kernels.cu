@@ -847,21 +847,25 @@ __global__ void k_dcompact(const double2* __restrict__ D, int64_t N, ColTiles ct
 // or tm0 .. tm0 + gridDim.x - 1 of the rt the class has: a shard, or all)
 // times gridDim.y column tiles.  Forward: one partial per tile, in
 // partial[column tile * rt + row tile].
-// Rasterisation in bands of kBand row tiles: the CTAs in flight share a band's
+// Rasterisation in bands of row tiles: the CTAs in flight share a band's
 // integral rows (W, 64 rows x Kp each), which stay in L2 while the band
 // sweeps every column tile, so W is read from DRAM about once instead of
 // once per column tile (at the Ar shape 0.36 GB against 686 GB for class
-// (0,2)); the coupling-table blocks are read once per band.
-constexpr int64_t kBand = 32;
+// (0,2)); the coupling-table blocks and the epilogue's U rows are read once
+// per band.  A band holds about 24 MiB of W (8 to 512 row tiles).
+__device__ __forceinline__ int64_t class_band(int Kp) {
+  const int64_t b = ((int64_t)24 << 20) / ((int64_t)GBM * 16 * Kp);
+  return b < 8 ? 8 : b > 512 ? 512 : b;
+}
 __global__ void __launch_bounds__(256, 1)
 k_class_gemm(const double2* __restrict__ W, const double2* __restrict__ D, int64_t M, int64_t N, int Kp,
              const RowInfo* __restrict__ rows, const double* __restrict__ U, const double* __restrict__ eA,
              const double* __restrict__ E0p, double b, double* __restrict__ partial, AdjOut adj, ColTiles ctl,
              unsigned long long* dmin, int64_t rt, int64_t tm0) {
-  const int64_t gx = gridDim.x, gy = gridDim.y;
+  const int64_t gx = gridDim.x, gy = gridDim.y, kB = class_band(Kp);
   const int64_t L = (int64_t)blockIdx.y * gx + blockIdx.x;  // launch order
-  const int64_t band = L / (kBand * gy), b0 = band * kBand;
-  const int64_t bsz = gx - b0 < kBand ? gx - b0 : kBand;    // the last band may be narrower
+  const int64_t band = L / (kB * gy), b0 = band * kB;
+  const int64_t bsz = gx - b0 < kB ? gx - b0 : kB;          // the last band may be narrower
   const int64_t r = L - b0 * gy;
   const int64_t tm = tm0 + b0 + r % bsz, tn = r / bsz;
   double* slot = partial ? partial + tn * rt + tm : nullptr;
