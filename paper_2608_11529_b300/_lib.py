@@ -684,6 +684,34 @@ class E2Batch:
         except Exception:
             pass
 
+    @staticmethod
+    def plan_batches(plans, budget_bytes):
+        """Split planned jobs into batches whose workspaces fit budget_bytes
+        (host only; the sizes come from e2_batch_workspace_size).  Jobs are
+        taken in order; each batch gets the most jobs that fit with one table
+        slot per job (roots_per_launch = 1), then the largest roots_per_launch
+        that still fits (0 when every root fits in one launch).  Returns
+        [(jobs, roots_per_launch)]; raises E2Error if one job alone does not
+        fit."""
+        def size(group, k):
+            return E2Batch(group, roots_per_launch=k).workspace_bytes
+
+        out, i = [], 0
+        plans = list(plans)
+        while i < len(plans):
+            j = i + 1
+            if size(plans[i:j], 1) > budget_bytes:
+                raise E2Error("a job does not fit the budget even with one coupling-table slot")
+            while j < len(plans) and size(plans[i:j + 1], 1) <= budget_bytes:
+                j += 1
+            group = plans[i:j]
+            roots = max(p.n_roots for p in group)
+            k = 0 if size(group, 0) <= budget_bytes else max(
+                kk for kk in range(1, roots + 1) if size(group, kk) <= budget_bytes)
+            out.append((group, k))
+            i = j
+        return out
+
     def prepare(self, device, stream=None):
         import torch
         raw = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8, device=device)

@@ -2,7 +2,8 @@
 (e2_batch_set_roots_per_launch) each job keeps one coupling-table slot per
 root of a launch instead of one per root, so the workspace shrinks by the
 table slots it no longer holds and never grows; a negative group size is
-refused; jobs with fewer roots than the group size keep all of theirs."""
+refused; jobs with fewer roots than the group size keep all of theirs; and
+E2Batch.plan_batches splits jobs into batches that fit a memory budget."""
 import ctypes as C
 
 import pytest
@@ -42,3 +43,24 @@ def test_negative_root_group_is_refused():
     assert st != 0
     with pytest.raises(e2.E2Error):
         e2.E2Batch(plans, roots_per_launch=-2)
+
+
+def test_plan_batches_fits_the_budget():
+    plans = _plans()
+    one = [_ws([p], 1) for p in plans]
+    # a budget that holds the first two jobs with one slot each, not all three
+    budget = _ws(plans[:2], 1) + 1
+    assert _ws(plans, 1) > budget
+    out = e2.E2Batch.plan_batches(plans, budget)
+    assert [len(g) for g, _ in out] == [2, 1]
+    assert sum(len(g) for g, _ in out) == len(plans)
+    for g, k in out:
+        assert _ws(g, k) <= budget
+        if k:   # the largest group size that fits
+            assert k == max(p.n_roots for p in g) or _ws(g, k + 1) > budget
+    # a budget for everything at once: one batch, every root in one launch
+    out = e2.E2Batch.plan_batches(plans, _ws(plans, 0))
+    assert len(out) == 1 and out[0][1] == 0
+    # a job that cannot fit alone
+    with pytest.raises(e2.E2Error):
+        e2.E2Batch.plan_batches(plans, min(one) - 1)
